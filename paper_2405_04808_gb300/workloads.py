@@ -1,0 +1,354 @@
+"""Seeded synthetic workloads: the raw inputs of an augmented-system solve.
+
+This module is the only code shared by the CUDA path and the CPU oracle.  It
+holds no arithmetic of the solver itself (no scaling, no lifting, no
+multigrid): it draws a problem instance and evaluates the model ODE's
+right-hand side f and its Jacobians at a seeded iterate.  Everything it returns
+is in physical (unscaled) coordinates; the solver side forms the scaled blocks
+of Sec. 4.1 from it.
+
+Two model problems, shaped like the paper's Sec. 6 workloads:
+
+* van der Pol control (Sec. 6.1): p = 2 states, q = 1 control entering the
+  second equation, mu = 1, theta = 0.5, M = I, u(0) = (1, 1) absorbed by the
+  shift u <- u + chi of the footnote to Sec. 1.
+* viscous Burgers control (Sec. 6.2) with P1 finite elements on nx interior
+  nodes of [0, 1] (homogeneous Dirichlet ends), M = (h/6) tridiag(1, 4, 1),
+  stiffness K = (1/h) tridiag(-1, 2, -1), a Galerkin convective term C(u) and
+  distributed control entering as M z; theta = 1 (backward Euler).
+
+The "SQP iterate" at which the Jacobians are taken is the paper's setting
+with unavailable data replaced by seeded draws: a control z_k ~ N(0, s^2) per
+step (and per node), the state from the theta-method forward solve (Eq. 8,
+Newton per step) and the virtual states equal to the states (v = u, which the
+forward solve satisfies).  The right-hand side b ~ N(0, 1) fills all
+n (4p + q) entries of the lifted system.
+
+Random numbers: splitmix64 used as a counter-based generator,
+``out_i = mix64(key + (i + 1) * 0x9E3779B97F4A7C15)`` with Vigna's mix64
+finaliser, ``key = mix64(seed * 65536 + stream)``; uniforms are the top 53
+bits; normals come from Box-Muller on consecutive pairs.  Streams: 1 control,
+2 right-hand side, 3 Burgers mode numbers, 4 Burgers mode amplitudes.
+
+Matrix formats (the C-ABI's): a "dense" problem stores every p x p or p x q
+block row-major; a "tridiag" problem (q == p) stores every p x p tridiagonal
+matrix as three length-p rows: band[0][i] = A[i, i-1] (band[0][0] = 0),
+band[1][i] = A[i, i], band[2][i] = A[i, i+1] (band[2][p-1] = 0).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+STREAM_CONTROL = 1
+STREAM_RHS = 2
+STREAM_MODES = 3
+STREAM_AMPL = 4
+
+
+def _mix64(z):
+    with np.errstate(over="ignore"):
+        z = np.asarray(z, dtype=np.uint64)
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def random_u64(seed: int, stream: int, count: int) -> np.ndarray:
+    """``count`` splitmix64 outputs of (seed, stream), counter-based."""
+    key = _mix64(np.uint64((int(seed) * 65536 + int(stream)) % (1 << 64)))
+    with np.errstate(over="ignore"):
+        ctr = np.arange(1, count + 1, dtype=np.uint64)
+        return _mix64(key + ctr * _GOLDEN)
+
+
+def uniform(seed: int, stream: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits."""
+    return (random_u64(seed, stream, count) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, stream: int, count: int) -> np.ndarray:
+    """Standard normals by Box-Muller on consecutive uniform pairs."""
+    m = (count + 1) // 2
+    u = uniform(seed, stream, 2 * m)
+    r = np.sqrt(-2.0 * np.log1p(-u[0::2]))
+    ang = 2.0 * math.pi * u[1::2]
+    out = np.empty(2 * m)
+    out[0::2] = r * np.cos(ang)
+    out[1::2] = r * np.sin(ang)
+    return out[:count]
+
+
+# --------------------------------------------------------------------------
+# banded helpers (format conversion only)
+
+def band_to_dense(band: np.ndarray) -> np.ndarray:
+    """(3, p) tridiagonal band -> dense (p, p)."""
+    p = band.shape[-1]
+    a = np.diag(band[1])
+    if p > 1:
+        a += np.diag(band[0][1:], -1) + np.diag(band[2][:-1], 1)
+    return a
+
+
+def _band_matvec(band: np.ndarray, x: np.ndarray) -> np.ndarray:
+    y = band[1] * x
+    y[1:] += band[0][1:] * x[:-1]
+    y[:-1] += band[2][:-1] * x[1:]
+    return y
+
+
+def _solve_tridiag(band: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """Banded LU (LAPACK gbsv via scipy) for the forward solve's Newton steps."""
+    from scipy.linalg import solve_banded
+    ab = np.zeros((3, band.shape[1]))
+    ab[0, 1:] = band[2][:-1]
+    ab[1, :] = band[1]
+    ab[2, :-1] = band[0][1:]
+    return solve_banded((1, 1), ab, r)
+
+
+# --------------------------------------------------------------------------
+# model problems
+
+@dataclasses.dataclass
+class VanDerPol:
+    """van der Pol control on [0, T] mapped to [0, 1] (Sec. 6.1).
+
+    u1' = T (u2 + [z1]),  u2' = T (mu (1 - u1^2) u2 - u1 + z_last);
+    q = 1 puts the single control in the second equation, q = 2 puts one
+    control in each (the paper's form).
+    """
+    mu: float = 1.0
+    u_init: tuple = (1.0, 1.0)
+    q: int = 1
+    T: float = 1.0
+    p: int = 2
+    kind: str = "dense"
+
+    def f(self, u, z):
+        z1 = z[0] if self.q == 2 else 0.0
+        return self.T * np.array([u[1] + z1, self.mu * (1.0 - u[0] ** 2) * u[1] - u[0] + z[-1]])
+
+    def dfdu(self, u, z):
+        return self.T * np.array([[0.0, 1.0],
+                                  [-2.0 * self.mu * u[0] * u[1] - 1.0, self.mu * (1.0 - u[0] ** 2)]])
+
+    def dfdz(self, u, z):
+        if self.q == 2:
+            return self.T * np.eye(2)
+        return self.T * np.array([[0.0], [1.0]])
+
+    def mass(self):
+        return np.eye(2)
+
+
+@dataclasses.dataclass
+class BurgersFE:
+    """M u' = -nu K u - C(u) + M z with P1 elements on nx interior nodes (Sec. 6.2)."""
+    nx: int
+    nu: float
+    kind: str = "tridiag"
+
+    @property
+    def p(self):
+        return self.nx
+
+    @property
+    def q(self):
+        return self.nx
+
+    @property
+    def h(self):
+        return 1.0 / (self.nx + 1)
+
+    def mass(self):
+        h = self.h
+        band = np.zeros((3, self.nx))
+        band[0][1:] = h / 6.0
+        band[1][:] = 4.0 * h / 6.0
+        band[2][:-1] = h / 6.0
+        return band
+
+    def stiffness(self):
+        h = self.h
+        band = np.zeros((3, self.nx))
+        band[0][1:] = -1.0 / h
+        band[1][:] = 2.0 / h
+        band[2][:-1] = -1.0 / h
+        return band
+
+    @staticmethod
+    def _padded(u):
+        return np.concatenate(([0.0], u, [0.0]))
+
+    def convection(self, u):
+        """C_i(u) = (u_{i+1}^2 + u_i u_{i+1} - u_{i-1} u_i - u_{i-1}^2) / 6, u_0 = u_{nx+1} = 0."""
+        w = self._padded(u)
+        um, uc, up = w[:-2], w[1:-1], w[2:]
+        return (up * up + uc * up - um * uc - um * um) / 6.0
+
+    def f(self, u, z):
+        return (-self.nu * _band_matvec(self.stiffness(), u) - self.convection(u)
+                + _band_matvec(self.mass(), z))
+
+    def dfdu(self, u, z):
+        w = self._padded(u)
+        um, uc, up = w[:-2], w[1:-1], w[2:]
+        dc = np.zeros((3, self.nx))
+        dc[0] = (-2.0 * um - uc) / 6.0
+        dc[1] = (up - um) / 6.0
+        dc[2] = (uc + 2.0 * up) / 6.0
+        dc[0][0] = 0.0
+        dc[2][-1] = 0.0
+        return -self.nu * self.stiffness() - dc
+
+    def dfdz(self, u, z):
+        return self.mass()
+
+    def initial_state(self, seed):
+        """Sum of four sine modes, wavenumbers U{1..8}, amplitudes U(-1, 1), max |u0| <= 1."""
+        km = 1 + np.floor(8.0 * uniform(seed, STREAM_MODES, 4)).astype(int)
+        am = 2.0 * uniform(seed, STREAM_AMPL, 4) - 1.0
+        x = self.h * np.arange(1, self.nx + 1)
+        u0 = np.zeros(self.nx)
+        for k, a in zip(km, am):
+            u0 += a * np.sin(math.pi * k * x)
+        peak = np.max(np.abs(u0))
+        if peak > 1.0:
+            u0 /= peak
+        return u0
+
+
+# --------------------------------------------------------------------------
+# problem instance
+
+@dataclasses.dataclass
+class Problem:
+    """Raw inputs of one augmented system, in the C-ABI's formats.
+
+    Index convention (0-based step t = k - 1 of the paper's k = 1..n):
+      Ju_cur[t]  = d_u f(u_{t+1}, z_{t+1})   (physical point)
+      Ju_prev[t] = d_u f(v_t, z_{t+1})       (v_0 = the initial state)
+      Jz_cur[t], Jz_prev[t] likewise for d_z f; when ``jz_const`` the two
+      arrays hold one matrix (leading dimension 1) used at every step.
+    """
+    kind: str
+    n: int
+    p: int
+    q: int
+    theta: float
+    gamma: float
+    M: np.ndarray
+    Ju_cur: np.ndarray
+    Ju_prev: np.ndarray
+    Jz_cur: np.ndarray
+    Jz_prev: np.ndarray
+    jz_const: bool
+    b: np.ndarray                 # type-major right-hand side, length n (4p + q)
+    model: object = None
+    u_phys: np.ndarray = None     # (n + 1, p) states u_0..u_n, physical
+    z_phys: np.ndarray = None     # (n, q) controls z_1..z_n
+
+    @property
+    def dt(self):
+        return 1.0 / self.n
+
+    @property
+    def size(self):
+        return self.n * (4 * self.p + self.q)
+
+
+def _forward_solve(model, u0, z, n, theta, tol=1e-14, maxit=30):
+    """theta-method time stepping (Eq. 8) with Newton per step: the seeded iterate."""
+    dt = 1.0 / n
+    us = [np.array(u0, dtype=np.float64)]
+    dense = model.kind == "dense"
+    Mm = model.mass()
+    for k in range(n):
+        up = us[-1]
+        zk = z[k]
+        fp = model.f(up, zk)
+        Mup = Mm @ up if dense else _band_matvec(Mm, up)
+        u = up.copy()
+        for _ in range(maxit):
+            Mu = Mm @ u if dense else _band_matvec(Mm, u)
+            res = Mu - Mup - dt * (theta * model.f(u, zk) + (1.0 - theta) * fp)
+            J = model.dfdu(u, zk)
+            if dense:
+                step = np.linalg.solve(Mm - theta * dt * J, -res)
+            else:
+                step = _solve_tridiag(Mm - theta * dt * J, -res)
+            u = u + step
+            if np.max(np.abs(step)) <= tol * (1.0 + np.max(np.abs(u))):
+                break
+        us.append(u)
+    return np.array(us)
+
+
+def make_problem(model, n: int, theta: float, gamma: float, seed: int,
+                 z_sigma: float, u_init=None) -> Problem:
+    """Draw the iterate and the right-hand side and evaluate the raw Jacobians."""
+    p, q = model.p, model.q
+    z = z_sigma * normal(seed, STREAM_CONTROL, n * q).reshape(n, q)
+    if u_init is None:
+        u_init = model.initial_state(seed) if hasattr(model, "initial_state") else np.zeros(p)
+    us = _forward_solve(model, u_init, z, n, theta)
+    vs = us  # the iterate satisfies v = u
+    Ju_cur = np.array([model.dfdu(us[t + 1], z[t]) for t in range(n)])
+    Ju_prev = np.array([model.dfdu(vs[t], z[t]) for t in range(n)])
+    if isinstance(model, BurgersFE):
+        Jz_cur = model.dfdz(None, None)[None]
+        Jz_prev = Jz_cur.copy()
+        jz_const = True
+    else:
+        Jz_cur = np.array([model.dfdz(us[t + 1], z[t]) for t in range(n)])
+        Jz_prev = np.array([model.dfdz(vs[t], z[t]) for t in range(n)])
+        jz_const = False
+    b = normal(seed, STREAM_RHS, n * (4 * p + q))
+    return Problem(kind=model.kind, n=n, p=p, q=q, theta=theta, gamma=gamma,
+                   M=model.mass(), Ju_cur=Ju_cur, Ju_prev=Ju_prev,
+                   Jz_cur=Jz_cur, Jz_prev=Jz_prev, jz_const=jz_const, b=b,
+                   model=model, u_phys=us, z_phys=z)
+
+
+# --------------------------------------------------------------------------
+# the named workloads
+
+def vdp(n: int = 256, seed: int = 1000, gamma: float = 100.0, mu: float = 1.0) -> Problem:
+    """van der Pol control, p = 2, q = 1, theta = 0.5, z ~ N(0, 0.1^2) on [0, 1]."""
+    m = VanDerPol(mu=mu)
+    return make_problem(m, n=n, theta=0.5, gamma=gamma, seed=seed, z_sigma=0.1,
+                        u_init=np.array(m.u_init))
+
+
+def vdp_paper(n: int = 64, seed: int = 1, gamma: float = 100.0) -> Problem:
+    """The paper's van der Pol setting of Sec. 6.1 (mu = 0.1, T = 8, q = 2,
+    u(0) = (1, 1), theta = 0.5) at a first-iterate-like point: z = 0 and the
+    state from the forward solve."""
+    m = VanDerPol(mu=0.1, q=2, T=8.0)
+    return make_problem(m, n=n, theta=0.5, gamma=gamma, seed=seed, z_sigma=0.0,
+                        u_init=np.array(m.u_init))
+
+
+def burgers(nx: int = 128, n: int = 1024, nu: float = 0.01, seed: int = 2000,
+            gamma: float = 100.0, theta: float = 1.0) -> Problem:
+    """Viscous Burgers control with P1 elements, z ~ N(0, 0.05^2) per node and step."""
+    return make_problem(BurgersFE(nx=nx, nu=nu), n=n, theta=theta, gamma=gamma,
+                        seed=seed, z_sigma=0.05)
+
+
+#: the solver settings that go with each named workload (levels, smoothing)
+WORKLOADS = {
+    "vdp_n256": dict(make=lambda seed=1000: vdp(n=256, seed=seed), levels=2, nu_pre=1, nu_post=1),
+    "burgers_nx128_n1024": dict(make=lambda seed=2000: burgers(nx=128, n=1024, nu=0.01, seed=seed),
+                                levels=3, nu_pre=4, nu_post=4),
+    "burgers_nx512_n8192": dict(make=lambda seed=3000: burgers(nx=512, n=8192, nu=0.005, seed=seed),
+                                levels=4, nu_pre=4, nu_post=4),
+}

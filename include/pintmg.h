@@ -1,0 +1,170 @@
+/*
+ * pintmg.h - C ABI of the GB300 parallel-in-time multigrid solver for
+ * augmented systems (Vuchkov, Cyr, Javeed, Ridzal, arXiv 2405.04808).
+ *
+ * The library solves A x = b with A = [[I, B^T], [B, 0]] (Eq. augsys-aj),
+ * where B = dF~ is the scaled Jacobian of the theta-method constraint with
+ * virtual interface variables (Eq. theta2-aj, Sec. 4.1 and Sec. 5.1), by
+ * flexible GMRES (Saad 1993; Sec. 5.3.4 and Sec. 6) preconditioned with a
+ * multigrid V-cycle in time (Alg. 1): block-Jacobi smoothing (Eq. jacobi-aj),
+ * linear interpolation / injection in time (Sec. 5.3.1) and a coarse solve by
+ * GMRES right-preconditioned with symmetric block Gauss-Seidel (Sec. 5.3.4).
+ *
+ * Vectors (both host and device) are type-major as in Fig. 4:
+ *   [u_1..u_n | v_1..v_n | z_1..z_n | lambda_1..lambda_n | mu_1..mu_n],
+ * each step contiguous (p entries, q for z), n (4p + q) doubles in all, in the
+ * scaled Euclidean coordinates of Sec. 4.1.
+ *
+ * Errors: every entry point returns an mg_status code; nothing aborts, traps
+ * or throws.  Device kernels never spin-wait.
+ * Threading: one handle is used by one host thread and one stream at a time.
+ */
+#ifndef PINTMG_H
+#define PINTMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PINTMG_ABI_VERSION 1
+
+typedef enum {
+  MG_OK = 0,
+  MG_NOT_CONVERGED = 1,   /* ran to maxit; outputs hold the last iterate */
+  MG_ERR_ARG = -1,        /* invalid sizes, options or null pointers */
+  MG_ERR_SINGULAR = -2,   /* a local Schur complement S_k had a non-positive pivot (Thm 1: N_k singular) */
+  MG_ERR_BREAKDOWN = -3,  /* Arnoldi produced a non-finite Hessenberg entry */
+  MG_ERR_CUDA = -4,       /* a CUDA runtime call failed; mg_last_cuda_error() names it */
+  MG_ERR_OOM = -5,        /* device allocation failed */
+  MG_ERR_NONFINITE = -7,  /* NaN or Inf in the problem data or right-hand side */
+  MG_ERR_UNSUPPORTED = -8 /* a valid request this build does not implement (e.g. p too large for the dense layout) */
+} mg_status;
+
+typedef enum {
+  MG_LAYOUT_DENSE = 0,   /* blocks stored dense, row-major; p <= 4, q <= 4 */
+  MG_LAYOUT_TRIDIAG = 1  /* q == p, every p x p block tridiagonal (band rows, below) */
+} mg_layout;
+
+typedef enum {
+  MG_PRECISION_FP64 = 0, /* the plain method: every step in FP64 */
+  MG_PRECISION_FP32 = 1  /* V-cycle (smoother, transfers, SGS) in FP32; FGMRES, coarse GMRES and true residual in FP64 */
+} mg_precision;
+
+/*
+ * Problem data (Eq. blocks-aj and Sec. 5.1).  All pointers are HOST memory,
+ * read during mg_setup only, owned by the caller.
+ *
+ * Index t = 0..n-1 is the paper's step k = t + 1.  Raw Jacobians are taken at
+ * physical (unscaled) points:
+ *   Ju_cur[t]  = d_u f(u_{t+1}, z_{t+1}),   Ju_prev[t] = d_u f(v_t, z_{t+1})
+ *   Jz_cur[t]  = d_z f(u_{t+1}, z_{t+1}),   Jz_prev[t] = d_z f(v_t, z_{t+1})
+ * (v_0 = the initial state).  The library forms, per grid level,
+ *   N_k  = dt^-1 [ M - theta dt Ju_cur ],   V_k = dt^-1 [ -M - (1-theta) dt Ju_prev ],
+ *   Z~_k = -(theta Jz_cur + (1-theta) Jz_prev) / gamma.
+ * Coarse levels are rediscretised at 2 dt with the Jacobians of fine step
+ * 2K-1 (current) and 2K-2 (previous) in the paper's 1-based count; this is
+ * exact when d_u f does not depend on z and f is affine in z.
+ *
+ * MG_LAYOUT_DENSE:   M is p*p, Ju_* are n*p*p, Jz_* are n*p*q (row-major blocks).
+ * MG_LAYOUT_TRIDIAG: every p x p tridiagonal matrix is 3*p doubles,
+ *                    band[0][i] = A[i][i-1] (band[0][0] ignored),
+ *                    band[1][i] = A[i][i],
+ *                    band[2][i] = A[i][i+1] (band[2][p-1] ignored);
+ *                    M is 3*p, Ju_* and Jz_* are n*3*p.
+ * jz_const != 0: Jz_cur and Jz_prev each hold ONE block used at every step.
+ */
+typedef struct {
+  int layout;        /* mg_layout */
+  int n, p, q;       /* time steps, states, controls */
+  double theta;      /* theta-method weight, 0 < theta <= 1 (Eq. theta-aj) */
+  double gamma;      /* control scale factor gamma > 0 (Sec. 4.1, Sec. 5.3.3) */
+  int jz_const;
+  const double *M;
+  const double *Ju_cur, *Ju_prev, *Jz_cur, *Jz_prev;
+} mg_problem;
+
+typedef struct {
+  int levels;             /* V-cycle levels Lv >= 1; n must be divisible by 2^(Lv-1); Lv = 1 is SGS-GMRES alone */
+  int nu_pre, nu_post;    /* block-Jacobi sweeps before / after the coarse correction (>= 0) */
+  double coarse_rtol;     /* coarse GMRES relative tolerance (the paper uses 1e-3) */
+  int coarse_maxit;       /* coarse GMRES iteration cap (1..64) */
+  int coarse_fixed_iters; /* > 0: run exactly this many coarse GMRES iterations, ignoring coarse_rtol */
+  int end_rule;           /* last fine point of linear interpolation: 0 repeats the last coarse value, 1 uses 0 */
+  int precision;          /* mg_precision */
+} mg_options;
+
+typedef struct {
+  int iters;              /* FGMRES iterations taken */
+  int vcycles;            /* preconditioner applications */
+  int coarse_iters;       /* coarse GMRES iterations summed over all V-cycles */
+  double relres;          /* Arnoldi estimate ||b - A x|| / ||b|| at exit */
+  double true_relres;     /* recomputed ||b - A x|| / ||b|| at exit (FP64) */
+} mg_solve_info;
+
+typedef struct mg_handle mg_handle;  /* opaque; owns every device buffer */
+
+/* Fill *opts with the defaults: levels 2, 1/1 sweeps, coarse 1e-3 / 50, tolerance mode, end rule 0, FP64. */
+void mg_default_options(mg_options *opts);
+
+/*
+ * Build the hierarchy: scaled blocks on every level and their local
+ * Schur-complement factors (Thm 1), all on the device, on `stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  Host data are
+ * copied; the caller may free them on return.  On success *out owns all
+ * device memory until mg_destroy.  Returns MG_ERR_ARG, MG_ERR_NONFINITE,
+ * MG_ERR_SINGULAR, MG_ERR_OOM, MG_ERR_UNSUPPORTED or MG_ERR_CUDA on failure,
+ * leaving *out NULL.
+ */
+int mg_setup(const mg_problem *prob, const mg_options *opts, void *stream, mg_handle **out);
+
+/*
+ * One V-cycle (Alg. 1 generalised to Lv levels, starting from y = 0):
+ * y = M^-1 r.  r and y are DEVICE pointers to type-major vectors of n (4p+q)
+ * doubles; they must not overlap.  Asynchronous on `stream` except for the
+ * coarse GMRES convergence tests, which read a few scalars back.
+ */
+int mg_vcycle(mg_handle *h, const double *r, double *y, void *stream);
+
+/*
+ * Solve A x = b by FGMRES(restart) from x0 = 0, preconditioned by the
+ * V-cycle, until ||b - A x|| / ||b|| <= rtol (Arnoldi estimate) or maxit
+ * iterations.  b and x may be HOST or DEVICE pointers (detected per call);
+ * host buffers are staged through the handle's device memory on `stream`.
+ * info (may be NULL) receives the counters and the FP64 true residual.
+ * Returns MG_OK, MG_NOT_CONVERGED, MG_ERR_NONFINITE (b has NaN/Inf),
+ * MG_ERR_BREAKDOWN, MG_ERR_ARG or MG_ERR_CUDA.  Synchronises `stream`.
+ */
+int fgmres_solve(mg_handle *h, const double *b, double *x, double rtol, int maxit, int restart,
+                 mg_solve_info *info, void *stream);
+
+/* Sizes of a handle: the vector length n (4p+q) and the number of levels. */
+long long mg_vector_length(const mg_handle *h);
+
+/*
+ * Measurement support (no counterpart in the paper).  mg_launch_count returns
+ * the number of kernels the handle has launched since mg_setup returned.
+ * mg_profile_enable(h, mask) brackets every later kernel launch of the
+ * handle whose category bit is set in `mask` (bit c = the c-th category of
+ * mg_profile_read; 0 turns timing off) with a pair of CUDA events on its
+ * stream, and resets the per-category sums;
+ * mg_profile_read synchronises those events and fills up to `max` entries of
+ * names (static strings), ms (summed kernel time) and launches (count) per
+ * kernel category; it returns the number of categories or a negative status.
+ */
+long long mg_launch_count(const mg_handle *h);
+int mg_profile_enable(mg_handle *h, int mask);
+int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches);
+
+/* Release every device buffer of the handle.  NULL is accepted. */
+void mg_destroy(mg_handle *h);
+
+/* Static text for a status code. */
+const char *mg_status_string(int status);
+
+/* Name of the last CUDA error seen by this thread's library calls ("" if none). */
+const char *mg_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PINTMG_H */

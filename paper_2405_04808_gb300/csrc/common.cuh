@@ -1,0 +1,307 @@
+// Shared device-side definitions of the pintmg kernels (sm_103a).
+//
+// Vectors are the ABI's type-major layout (Fig. 4): the time-major
+// permutation of Sec. 5.2 is never materialised; each kernel indexes the five
+// type arrays directly.  Time block j = 0..n (the paper's block j + 1 of
+// Fig. 5) owns u_j, z_j, lambda_j (j < n) and v_{j-1}, mu_{j-1} (j >= 1), with
+// 0-based step indices.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pintmg.h"
+
+namespace pintmg {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kDenseMax = 4;     // dense layout: p, q <= 4 (one thread per time block)
+constexpr int kScanWords = 8;    // tridiagonal: per-lane chunk maps, 2x2 forward + 2x2 backward
+
+// Coefficients of one grid level (device pointers), in the kernels' precision T.
+//   N, V, Z: per-step blocks (tridiagonal: 3 band rows of p; dense: p*p, p*p, p*q)
+//   stride 0 means the same block at every step.
+//   fac:  tridiagonal: LDL^T of S = N N^T + Z Z^T as [a(p) | b(p) | dinv(p)]
+//         (a_i = L[i][i-1], b_i = L[i][i-2], dinv_i = 1 / D_i);
+//         dense: Cholesky factor of S, row-major p*p, diagonal stored inverted.
+//   scan: tridiagonal only: per step, per lane, the 2x2 maps of that lane's
+//         chunk of the forward and backward LDL^T recurrences (row-major).
+template <typename T>
+struct LevelView {
+  int n, p, q, layout;
+  const T *N, *V, *Z;
+  long long sN, sV, sZ;
+  const T *fac;
+  long long sFac;
+  const T *scan;
+};
+
+template <typename T>
+struct Vec {
+  T *u, *v, *z, *l, *m;
+};
+
+template <typename T>
+__host__ __device__ inline Vec<T> make_vec(T *base, int n, int p, int q) {
+  Vec<T> x;
+  long long np = (long long)n * p;
+  x.u = base;
+  x.v = base + np;
+  x.z = base + 2 * np;
+  x.l = base + 2 * np + (long long)n * q;
+  x.m = base + 3 * np + (long long)n * q;
+  return x;
+}
+
+template <typename T>
+__host__ __device__ inline Vec<const T> make_cvec(const T *base, int n, int p, int q) {
+  Vec<const T> x;
+  long long np = (long long)n * p;
+  x.u = base;
+  x.v = base + np;
+  x.z = base + 2 * np;
+  x.l = base + 2 * np + (long long)n * q;
+  x.m = base + 3 * np + (long long)n * q;
+  return x;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative tridiagonal helpers.  Lane `ln` owns the contiguous chunk
+// [ln*C, ln*C + C) of a length-p vector (p <= 32 C); entries at i >= p are 0.
+
+template <typename T, int C>
+__device__ __forceinline__ void chunk_load(T (&x)[C], const T *src, int p, int ln) {
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    int i = ln * C + e;
+    x[e] = (i < p) ? src[i] : T(0);
+  }
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void chunk_store(T *dst, const T (&x)[C], int p, int ln) {
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    int i = ln * C + e;
+    if (i < p) dst[i] = x[e];
+  }
+}
+
+// neighbours of the chunk: x_{lo-1} and x_{lo+C} (0 outside [0, p))
+template <typename T, int C>
+__device__ __forceinline__ void chunk_halo(const T (&x)[C], int p, int ln, T &prev, T &next) {
+  prev = __shfl_up_sync(kFull, x[C - 1], 1);
+  next = __shfl_down_sync(kFull, x[0], 1);
+  if (ln == 0) prev = T(0);
+  if (ln * C + C >= p) next = T(0);
+}
+
+// y (+)= A x for a tridiagonal band A (3 rows of p)
+template <typename T, int C, bool kAccumulate>
+__device__ __forceinline__ void tri_mv(T (&y)[C], const T *A, const T (&x)[C], int p, int ln, T sign) {
+  T prev, next;
+  chunk_halo<T, C>(x, p, ln, prev, next);
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    int i = ln * C + e;
+    T acc = T(0);
+    if (i < p) {
+      T xm = (e == 0) ? prev : x[e - 1];
+      T xp = (e == C - 1) ? next : x[e + 1];
+      acc = fma(A[i], xm, fma(A[p + i], x[e], A[2 * p + i] * xp));
+    }
+    y[e] = kAccumulate ? fma(sign, acc, y[e]) : sign * acc;
+  }
+}
+
+// y (+)= A^T x for a tridiagonal band A: (A^T x)_i = A[i-1][i] x_{i-1} + A[i][i] x_i + A[i+1][i] x_{i+1}
+template <typename T, int C, bool kAccumulate>
+__device__ __forceinline__ void tri_mtv(T (&y)[C], const T *A, const T (&x)[C], int p, int ln, T sign) {
+  T prev, next;
+  chunk_halo<T, C>(x, p, ln, prev, next);
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    int i = ln * C + e;
+    T acc = T(0);
+    if (i < p) {
+      T xm = (e == 0) ? prev : x[e - 1];
+      T xp = (e == C - 1) ? next : x[e + 1];
+      T up = (i > 0) ? A[2 * p + i - 1] : T(0);     // A[i-1][i]
+      T lo = (i + 1 < p) ? A[i + 1] : T(0);         // A[i+1][i]
+      acc = fma(up, xm, fma(A[p + i], x[e], lo * xp));
+    }
+    y[e] = kAccumulate ? fma(sign, acc, y[e]) : sign * acc;
+  }
+}
+
+// Inclusive Kogge-Stone scan of affine maps s -> H s + t over the warp's lanes.
+// kForward: lane ln composes with lanes below it; otherwise with lanes above.
+template <typename T, bool kForward>
+__device__ __forceinline__ void warp_affine_scan(T (&H)[4], T (&t)[2], int ln) {
+#pragma unroll
+  for (int d = 1; d < kWarp; d <<= 1) {
+    T h0, h1, h2, h3, t0, t1;
+    if (kForward) {
+      h0 = __shfl_up_sync(kFull, H[0], d); h1 = __shfl_up_sync(kFull, H[1], d);
+      h2 = __shfl_up_sync(kFull, H[2], d); h3 = __shfl_up_sync(kFull, H[3], d);
+      t0 = __shfl_up_sync(kFull, t[0], d); t1 = __shfl_up_sync(kFull, t[1], d);
+    } else {
+      h0 = __shfl_down_sync(kFull, H[0], d); h1 = __shfl_down_sync(kFull, H[1], d);
+      h2 = __shfl_down_sync(kFull, H[2], d); h3 = __shfl_down_sync(kFull, H[3], d);
+      t0 = __shfl_down_sync(kFull, t[0], d); t1 = __shfl_down_sync(kFull, t[1], d);
+    }
+    bool take = kForward ? (ln >= d) : (ln + d < kWarp);
+    if (take) {
+      // (H, t) o (H', t') = (H H', t + H t')
+      T nt0 = fma(H[0], t0, fma(H[1], t1, t[0]));
+      T nt1 = fma(H[2], t0, fma(H[3], t1, t[1]));
+      T n0 = fma(H[0], h0, H[1] * h2);
+      T n1 = fma(H[0], h1, H[1] * h3);
+      T n2 = fma(H[2], h0, H[3] * h2);
+      T n3 = fma(H[2], h1, H[3] * h3);
+      t[0] = nt0; t[1] = nt1;
+      H[0] = n0; H[1] = n1; H[2] = n2; H[3] = n3;
+    }
+  }
+}
+
+// Solve S x = r with S = L D L^T pentadiagonal (a, b = first and second
+// sub-diagonals of the unit lower L, dinv = 1/D), r and x held as lane chunks.
+//   forward   g_i = r_i - a_i g_{i-1} - b_i g_{i-2}
+//   scale     h_i = g_i dinv_i
+//   backward  x_i = h_i - a_{i+1} x_{i+1} - b_{i+2} x_{i+2}
+// Each lane runs its chunk from a zero incoming state, a warp scan of the
+// chunks' 2x2 affine maps (precomputed linear parts in `scan`) gives every
+// chunk's true incoming state, and the chunk is run again from it.
+template <typename T, int C>
+__device__ __forceinline__ void penta_solve(T (&x)[C], const T (&r)[C], const T *fac, const T *scan,
+                                            int p, int ln) {
+  const T *a = fac, *b = fac + p, *dinv = fac + 2 * p;
+  T ca[C], cb[C];
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    int i = ln * C + e;
+    ca[e] = (i < p) ? a[i] : T(0);
+    cb[e] = (i < p) ? b[i] : T(0);
+  }
+  // forward: state (g_{i-2}, g_{i-1})
+  T s1 = 0, s2 = 0;
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    T g = fma(-ca[e], s2, fma(-cb[e], s1, r[e]));
+    s1 = s2;
+    s2 = g;
+  }
+  T H[4], t[2] = {s1, s2};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) H[k] = scan[ln * kScanWords + k];
+  warp_affine_scan<T, true>(H, t, ln);
+  s1 = __shfl_up_sync(kFull, t[0], 1);
+  s2 = __shfl_up_sync(kFull, t[1], 1);
+  if (ln == 0) { s1 = 0; s2 = 0; }
+  T g[C];
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    g[e] = fma(-ca[e], s2, fma(-cb[e], s1, r[e]));
+    s1 = s2;
+    s2 = g[e];
+  }
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    int i = ln * C + e;
+    g[e] = (i < p) ? g[e] * dinv[i] : T(0);
+  }
+  // backward: state (x_{i+1}, x_{i+2}); coefficients a_{i+1}, b_{i+2}
+  T na[C], nb[C];
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    int i = ln * C + e;
+    na[e] = (i + 1 < p) ? a[i + 1] : T(0);
+    nb[e] = (i + 2 < p) ? b[i + 2] : T(0);
+  }
+  s1 = 0; s2 = 0;
+#pragma unroll
+  for (int e = C - 1; e >= 0; --e) {
+    T xi = fma(-na[e], s1, fma(-nb[e], s2, g[e]));
+    s2 = s1;
+    s1 = xi;
+  }
+  T Hb[4], tb[2] = {s1, s2};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Hb[k] = scan[ln * kScanWords + 4 + k];
+  warp_affine_scan<T, false>(Hb, tb, ln);
+  s1 = __shfl_down_sync(kFull, tb[0], 1);
+  s2 = __shfl_down_sync(kFull, tb[1], 1);
+  if (ln == kWarp - 1) { s1 = 0; s2 = 0; }
+#pragma unroll
+  for (int e = C - 1; e >= 0; --e) {
+    T xi = fma(-na[e], s1, fma(-nb[e], s2, g[e]));
+    s2 = s1;
+    s1 = xi;
+    x[e] = xi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense small-block helpers (one thread per time block, p, q <= kDenseMax)
+
+// y = A x (A p x m row-major) or y = A^T x (A m x p), sign applied
+template <typename T>
+__device__ __forceinline__ void dn_mv(T *y, const T *A, const T *x, int rows, int cols, T sign,
+                                      bool accumulate) {
+#pragma unroll
+  for (int i = 0; i < kDenseMax; ++i) {
+    if (i < rows) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < kDenseMax; ++k)
+        if (k < cols) acc = fma(A[i * cols + k], x[k], acc);
+      y[i] = accumulate ? fma(sign, acc, y[i]) : sign * acc;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void dn_mtv(T *y, const T *A, const T *x, int rows, int cols, T sign,
+                                       bool accumulate) {
+  // A is rows x cols; y (cols) = A^T x (rows)
+#pragma unroll
+  for (int i = 0; i < kDenseMax; ++i) {
+    if (i < cols) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < kDenseMax; ++k)
+        if (k < rows) acc = fma(A[k * cols + i], x[k], acc);
+      y[i] = accumulate ? fma(sign, acc, y[i]) : sign * acc;
+    }
+  }
+}
+
+// x = S^-1 r with S = L L^T (L row-major, diagonal stored inverted)
+template <typename T>
+__device__ __forceinline__ void dn_chol_solve(T *x, const T *r, const T *L, int p) {
+  T y[kDenseMax];
+#pragma unroll
+  for (int i = 0; i < kDenseMax; ++i) {
+    if (i < p) {
+      T acc = r[i];
+#pragma unroll
+      for (int k = 0; k < kDenseMax; ++k)
+        if (k < i) acc = fma(-L[i * p + k], y[k], acc);
+      y[i] = acc * L[i * p + i];
+    }
+  }
+#pragma unroll
+  for (int i = kDenseMax - 1; i >= 0; --i) {
+    if (i < p) {
+      T acc = y[i];
+#pragma unroll
+      for (int k = 0; k < kDenseMax; ++k)
+        if (k > i && k < p) acc = fma(-L[k * p + i], x[k], acc);
+      x[i] = acc * L[i * p + i];
+    }
+  }
+}
+
+}  // namespace pintmg

@@ -1,0 +1,980 @@
+// Host side of the pintmg C ABI (include/pintmg.h): hierarchy setup, the
+// V-cycle of Alg. 1, the coarse GMRES with SGS (Sec. 5.3.4) and the outer
+// flexible GMRES (Saad 1993).  Every arithmetic step runs in the kernels of
+// vcycle_kernels.cuh, setup_kernels.cuh and krylov_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "krylov_kernels.cuh"
+#include "setup_kernels.cuh"
+#include "vcycle_kernels.cuh"
+
+using namespace pintmg;
+
+namespace {
+
+thread_local char g_last_cuda_error[256] = "";
+
+struct CudaFail {
+  cudaError_t err;
+};
+
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+    throw CudaFail{e};
+  }
+}
+
+inline void ck_launch() { ck(cudaGetLastError()); }
+
+inline int grid_for(long long work, int threads, int cap = 4 * 152) {
+  long long g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// one device allocation, freed by the handle
+struct DevMem {
+  std::vector<void *> ptrs;
+  template <typename T>
+  T *alloc(size_t count) {
+    void *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+      throw std::bad_alloc();
+    }
+    ptrs.push_back(p);
+    return static_cast<T *>(p);
+  }
+  void release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+template <typename T>
+struct LevelData {
+  LevelView<T> view{};
+  T *Cu = nullptr, *Em = nullptr;  // coarsest level only
+  T *b = nullptr, *y = nullptr, *tmp = nullptr;
+  T *chainU = nullptr, *chainM = nullptr, *sgs_w = nullptr;
+};
+
+struct Level {
+  int n = 0;
+  double dt = 0;
+  long long len = 0;
+  LevelData<double> d;
+  LevelData<float> f;
+};
+
+}  // namespace
+
+struct mg_handle {
+  mg_options opts{};
+  int layout = 0, n = 0, p = 0, q = 0, C = 1;
+  double theta = 0, gamma = 0;
+  std::vector<Level> lv;
+  DevMem mem;
+  // coarse GMRES (FP64) workspace
+  int cmax = 0;
+  double *cV = nullptr, *cZ = nullptr, *cw = nullptr, *cr = nullptr, *cy = nullptr;
+  // fine FGMRES (FP64) workspace, grown on demand
+  int fm = 0;
+  double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fr = nullptr;
+  double *fx_stage = nullptr, *fb_stage = nullptr;
+  std::vector<void *> fmem;
+  // Arnoldi state of the outer FGMRES (kf) and of the coarse GMRES (kc): the
+  // coarse solve runs inside every outer iteration, so they never share.
+  struct Krylov {
+    double *h = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *ycoef = nullptr,
+           *scal = nullptr, *nrm2 = nullptr;
+  } kf, kc;
+  double *partial = nullptr;  // dot-product partial sums (used transiently)
+  int *flag = nullptr;
+  double *host_scal = nullptr;  // pinned, 4 doubles
+  int ldh = 0;
+  int G = 304;                  // CTAs of the dot-product kernels
+  // counters of the last solve
+  int vcycles = 0, coarse_iters = 0;
+  // optional per-category kernel timing (CUDA events on the launch stream)
+  int prof = 0;
+  long long launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double prof_ms[16] = {};
+  long long prof_count[16] = {};
+};
+
+namespace {
+
+// kernel categories reported by mg_profile_read
+enum Cat { CAT_BLOCK_SOLVE = 0, CAT_APPLY, CAT_RESTRICT, CAT_PROLONG, CAT_CHAIN, CAT_DOT, CAT_AXPY, CAT_SMALL,
+           CAT_CONVERT, CAT_SETUP, CAT_COUNT };
+const char *kCatNames[CAT_COUNT] = {"block_solve", "apply", "residual_restrict", "prolong_add", "sgs_chain",
+                                    "multidot", "axpy_scale", "arnoldi_scalar", "convert", "setup"};
+
+cudaEvent_t take_event(mg_handle *h) {
+  if (h->ev_pool.empty()) {
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e));
+    return e;
+  }
+  cudaEvent_t e = h->ev_pool.back();
+  h->ev_pool.pop_back();
+  return e;
+}
+
+// RAII bracket around one kernel launch: counts it and, when profiling, times it
+struct Bracket {
+  mg_handle *h;
+  int cat;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Bracket(mg_handle *h_, int cat_, cudaStream_t s_) : h(h_), cat(cat_), s(s_) {
+    h->launches++;
+    if ((h->prof >> cat) & 1) {
+      a = take_event(h);
+      b = take_event(h);
+      ck(cudaEventRecord(a, s));
+    }
+  }
+  ~Bracket() noexcept(false) {
+    if (a) {
+      ck(cudaEventRecord(b, s));
+      h->ev_pending.push_back({cat, {a, b}});
+    }
+  }
+};
+
+void harvest(mg_handle *h) {
+  for (auto &pe : h->ev_pending) {
+    ck(cudaEventSynchronize(pe.second.second));
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+    h->prof_ms[pe.first] += ms;
+    h->prof_count[pe.first] += 1;
+    h->ev_pool.push_back(pe.second.first);
+    h->ev_pool.push_back(pe.second.second);
+  }
+  h->ev_pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers (templated on the V-cycle precision)
+
+template <typename T>
+void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T *cplU, const T *cplM,
+                        T *out, cudaStream_t s) {
+  Bracket br(h, CAT_BLOCK_SOLVE, s);
+  if (L.layout == MG_LAYOUT_DENSE) {
+    k_block_solve_dense<T><<<grid_for(L.n + 1, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out);
+  } else {
+    const int blocks = (int)((L.n + 1 + 3) / 4);
+    switch (h->C) {
+      case 1: k_block_solve_tri<T, 1><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
+      case 2: k_block_solve_tri<T, 2><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
+      case 4: k_block_solve_tri<T, 4><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
+      case 8: k_block_solve_tri<T, 8><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
+      default: k_block_solve_tri<T, 16><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
+    }
+  }
+  ck_launch();
+}
+
+template <typename T>
+void launch_apply(mg_handle *h, const LevelView<T> &L, const T *x, const T *b, T *out, cudaStream_t s) {
+  Bracket br(h, CAT_APPLY, s);
+  if (L.layout == MG_LAYOUT_DENSE) {
+    k_apply_dense<T><<<grid_for(L.n, 128, 1 << 30), 128, 0, s>>>(L, x, b, out);
+  } else {
+    const int blocks = (L.n + 3) / 4;
+    switch (h->C) {
+      case 1: k_apply_tri<T, 1><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 2: k_apply_tri<T, 2><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 4: k_apply_tri<T, 4><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 8: k_apply_tri<T, 8><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      default: k_apply_tri<T, 16><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+    }
+  }
+  ck_launch();
+}
+
+template <typename T>
+void launch_residual_restrict(mg_handle *h, const LevelView<T> &L, const T *y, const T *b, T *rc,
+                              cudaStream_t s) {
+  Bracket br(h, CAT_RESTRICT, s);
+  const int nc = L.n / 2;
+  if (L.layout == MG_LAYOUT_DENSE) {
+    k_residual_restrict_dense<T><<<grid_for(nc, 128, 1 << 30), 128, 0, s>>>(L, y, b, rc);
+  } else {
+    const int blocks = (nc + 3) / 4;
+    switch (h->C) {
+      case 1: k_residual_restrict_tri<T, 1><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      case 2: k_residual_restrict_tri<T, 2><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      case 4: k_residual_restrict_tri<T, 4><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      case 8: k_residual_restrict_tri<T, 8><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      default: k_residual_restrict_tri<T, 16><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+    }
+  }
+  ck_launch();
+}
+
+template <typename T>
+LevelData<T> &ldata(Level &L);
+template <>
+LevelData<double> &ldata<double>(Level &L) { return L.d; }
+template <>
+LevelData<float> &ldata<float>(Level &L) { return L.f; }
+
+// ---------------------------------------------------------------------------
+// Dot products (FP64), fixed reduction order
+
+void multidot(mg_handle *h, const double *V, long long ldv, int m, const double *w, long long len, double *out,
+              int accumulate, cudaStream_t s) {
+  const int G = (int)std::max<long long>(1, std::min<long long>(h->G, (len + kDotThreads - 1) / kDotThreads));
+  dim3 grid(G, m);
+  {
+    Bracket br(h, CAT_DOT, s);
+    k_multidot_partial<<<grid, kDotThreads, 0, s>>>(V, ldv, w, len, h->partial);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, G, m, out, accumulate);
+    ck_launch();
+  }
+}
+
+void multi_axpy(mg_handle *h, double *y, const double *X, long long ldx, const double *c, int m, double sign,
+                long long len, cudaStream_t s) {
+  Bracket br(h, CAT_AXPY, s);
+  k_multi_axpy<<<grid_for(len, 256), 256, 0, s>>>(y, X, ldx, c, m, sign, len);
+  ck_launch();
+}
+
+void read_scal(mg_handle *h, const mg_handle::Krylov &K, cudaStream_t s) {
+  ck(cudaMemcpyAsync(h->host_scal, K.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ck(cudaStreamSynchronize(s));
+}
+
+// CGS2 orthogonalisation of w against V_0..V_j, ||w||^2 into nrm2, h (j+1)
+void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
+                   cudaStream_t s) {
+  const int m = j + 1;
+  multidot(h, V, len, m, w, len, K.h, 0, s);
+  multi_axpy(h, w, V, len, K.h, m, -1.0, len, s);
+  // second pass: accumulate the correction into h
+  multidot(h, V, len, m, w, len, K.h + 512, 0, s);
+  multi_axpy(h, w, V, len, K.h + 512, m, -1.0, len, s);
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m);
+    ck_launch();
+  }
+  multidot(h, w, len, 1, w, len, K.nrm2, 0, s);
+}
+
+// ||x|| into K.scal[0], 1/||x|| into K.scal[1]
+void norm_into(mg_handle *h, mg_handle::Krylov &K, const double *x, long long len, cudaStream_t s) {
+  multidot(h, x, len, 1, x, len, K.nrm2, 0, s);
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_norm_from_sq<<<1, 1, 0, s>>>(K.nrm2, K.scal);
+    ck_launch();
+  }
+}
+
+// one Arnoldi step on basis V (column stride len): w = A z_j already in w
+void arnoldi_step(mg_handle *h, mg_handle::Krylov &K, double *V, long long len, int j, double *w, cudaStream_t s) {
+  orthogonalise(h, K, V, len, j, w, s);
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_arnoldi_step<<<1, 1, 0, s>>>(j, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_AXPY, s);
+    k_scale<<<grid_for(len, 256), 256, 0, s>>>(V + (long long)(j + 1) * len, w, K.scal + 1, len);
+    ck_launch();
+  }
+  read_scal(h, K, s);
+}
+
+template <typename T>
+void convert(mg_handle *h, const double *x, T *y, long long len, cudaStream_t s);
+template <>
+void convert<double>(mg_handle *h, const double *x, double *y, long long len, cudaStream_t s) {
+  if (x != y) ck(cudaMemcpyAsync(y, x, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+template <>
+void convert<float>(mg_handle *h, const double *x, float *y, long long len, cudaStream_t s) {
+  {
+    Bracket br(h, CAT_CONVERT, s);
+    k_to_float<<<grid_for(len, 256), 256, 0, s>>>(x, y, len);
+    ck_launch();
+  }
+}
+template <typename T>
+void convert_back(mg_handle *h, const T *x, double *y, long long len, cudaStream_t s);
+template <>
+void convert_back<double>(mg_handle *h, const double *x, double *y, long long len, cudaStream_t s) {
+  if (x != y) ck(cudaMemcpyAsync(y, x, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+template <>
+void convert_back<float>(mg_handle *h, const float *x, double *y, long long len, cudaStream_t s) {
+  {
+    Bracket br(h, CAT_CONVERT, s);
+    k_to_double<<<grid_for(len, 256), 256, 0, s>>>(x, y, len);
+    ck_launch();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SGS on the coarsest level (precision T): y = [(D+L) D^-1 (D+L^T)]^-1 r
+
+template <typename T>
+void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
+  LevelData<T> &d = ldata<T>(lev);
+  const int n = lev.n, p = h->p;
+  // w = D^-1 r; forward chain u_j = uhat_j - Cu_j u_{j-1}
+  launch_block_solve<T>(h, d.view, r, nullptr, nullptr, d.sgs_w, s);
+  const int threads = std::max(32, ((p + 31) / 32) * 32);
+  const size_t shm = (size_t)p * sizeof(T);
+  if (n >= 1) {
+    {
+      Bracket br(h, CAT_CHAIN, s);
+      k_chain_forward<T><<<1, threads, shm, s>>>(d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p);
+      ck_launch();
+    }
+  }
+  // yhat = D^-1 (r - L w): only mu(yhat) is needed by the backward chain
+  launch_block_solve<T>(h, d.view, r, d.chainU, nullptr, d.sgs_w, s);
+  if (n >= 1) {
+    {
+      Bracket br(h, CAT_CHAIN, s);
+      k_chain_backward<T><<<1, threads, shm, s>>>(d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p);
+      ck_launch();
+    }
+  }
+  // y = D^-1 (r - L w - L^T y)
+  launch_block_solve<T>(h, d.view, r, d.chainU, d.chainM, y, s);
+}
+
+// precondition a coarse FP64 vector with SGS in precision T
+template <typename T>
+void sgs_fp64(mg_handle *h, Level &lev, const double *r, double *y, cudaStream_t s);
+template <>
+void sgs_fp64<double>(mg_handle *h, Level &lev, const double *r, double *y, cudaStream_t s) {
+  sgs_apply<double>(h, lev, r, y, s);
+}
+template <>
+void sgs_fp64<float>(mg_handle *h, Level &lev, const double *r, double *y, cudaStream_t s) {
+  LevelData<float> &d = lev.f;
+  convert<float>(h, r, d.b, lev.len, s);
+  sgs_apply<float>(h, lev, d.b, d.y, s);
+  convert_back<float>(h, d.y, y, lev.len, s);
+}
+
+// Coarse solve (Sec. 5.3.4): GMRES, right-preconditioned by SGS, x0 = 0,
+// FP64 Arnoldi; y (precision T) = approximate A_c^-1 r.
+template <typename T>
+void coarse_solve(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
+  Level &lev = h->lv.back();
+  const long long len = lev.len;
+  const mg_options &o = h->opts;
+  mg_handle::Krylov &K = h->kc;
+  convert_back<T>(h, r_in, h->cr, len, s);
+  norm_into(h, K, h->cr, len, s);
+  read_scal(h, K, s);
+  const double beta = h->host_scal[0];
+  if (!(beta > 0.0)) {
+    ck(cudaMemsetAsync(y_out, 0, len * sizeof(T), s));
+    return;
+  }
+  const int limit = o.coarse_fixed_iters > 0 ? std::min(o.coarse_fixed_iters, h->cmax) : o.coarse_maxit;
+  {
+    Bracket br(h, CAT_AXPY, s);
+    k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->cV, h->cr, K.scal + 1, len);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_arnoldi_init<<<1, 128, 0, s>>>(K.scal, K.g, h->cmax);
+    ck_launch();
+  }
+  int k = 0;
+  for (int j = 0; j < limit; ++j) {
+    double *vj = h->cV + (long long)j * len, *zj = h->cZ + (long long)j * len;
+    sgs_fp64<T>(h, lev, vj, zj, s);
+    launch_apply<double>(h, lev.d.view, zj, nullptr, h->cw, s);
+    arnoldi_step(h, K, h->cV, len, j, h->cw, s);
+    k = j + 1;
+    const double est = h->host_scal[0], hj1 = h->host_scal[2];
+    if (!std::isfinite(est) || !std::isfinite(hj1)) break;
+    if (hj1 == 0.0) break;
+    if (o.coarse_fixed_iters <= 0 && est <= o.coarse_rtol * beta) break;
+  }
+  h->coarse_iters += k;
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_backsolve<<<1, 1, 0, s>>>(k, K.H, h->ldh, K.g, K.ycoef);
+    ck_launch();
+  }
+  ck(cudaMemsetAsync(h->cy, 0, len * sizeof(double), s));
+  multi_axpy(h, h->cy, h->cZ, len, K.ycoef, k, 1.0, len, s);
+  convert<T>(h, h->cy, y_out, len, s);
+}
+
+// V-cycle from y = 0 on level l (Alg. 1 generalised): b, y in precision T
+template <typename T>
+void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
+  const int last = (int)h->lv.size() - 1;
+  if (l == last) {
+    coarse_solve<T>(h, b, y_out, s);
+    return;
+  }
+  Level &lev = h->lv[l];
+  LevelData<T> &d = ldata<T>(lev);
+  const mg_options &o = h->opts;
+  T *y = y_out, *t = d.tmp;
+  if (o.nu_pre == 0) {
+    ck(cudaMemsetAsync(y, 0, lev.len * sizeof(T), s));
+  } else {
+    launch_block_solve<T>(h, d.view, b, nullptr, nullptr, y, s);  // first sweep from y = 0
+    for (int k = 1; k < o.nu_pre; ++k) {
+      Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
+      launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s);
+      std::swap(y, t);
+    }
+  }
+  LevelData<T> &dn = ldata<T>(h->lv[l + 1]);
+  launch_residual_restrict<T>(h, d.view, y, b, dn.b, s);
+  vcycle<T>(h, l + 1, dn.b, dn.y, s);
+  {
+    Bracket br(h, CAT_PROLONG, s);
+    k_prolong_add<T><<<grid_for(lev.len, 256), 256, 0, s>>>(y, dn.y, lev.n, h->p, h->q, o.end_rule);
+    ck_launch();
+  }
+  for (int k = 0; k < o.nu_post; ++k) {
+    Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
+    launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s);
+    std::swap(y, t);
+  }
+  if (y != y_out) ck(cudaMemcpyAsync(y_out, y, lev.len * sizeof(T), cudaMemcpyDeviceToDevice, s));
+}
+
+// z = M^-1 v on FP64 fine vectors
+void precondition(mg_handle *h, const double *v, double *z, cudaStream_t s) {
+  h->vcycles++;
+  if (h->opts.precision == MG_PRECISION_FP32) {
+    Level &f = h->lv[0];
+    convert<float>(h, v, f.f.b, f.len, s);
+    vcycle<float>(h, 0, f.f.b, f.f.y, s);
+    convert_back<float>(h, f.f.y, z, f.len, s);
+  } else {
+    vcycle<double>(h, 0, v, z, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Setup helpers
+
+template <typename T>
+void alloc_level_vectors(mg_handle *h, Level &lev, LevelData<T> &d, bool is_last, bool is_first) {
+  const long long len = lev.len;
+  d.tmp = h->mem.alloc<T>(len);
+  if (!is_first || sizeof(T) == sizeof(float)) {
+    d.b = h->mem.alloc<T>(len);
+    d.y = h->mem.alloc<T>(len);
+  }
+  if (is_last) {
+    d.chainU = h->mem.alloc<T>((size_t)std::max(lev.n, 1) * h->p);
+    d.chainM = h->mem.alloc<T>((size_t)std::max(lev.n, 1) * h->p);
+    d.sgs_w = h->mem.alloc<T>(len);
+  }
+}
+
+float *to_float_copy(mg_handle *h, const double *x, long long len, cudaStream_t s) {
+  float *y = h->mem.alloc<float>(len);
+  {
+    Bracket br(h, CAT_CONVERT, s);
+    k_to_float<<<grid_for(len, 256), 256, 0, s>>>(x, y, len);
+    ck_launch();
+  }
+  return y;
+}
+
+bool host_finite(const double *x, long long len) {
+  for (long long i = 0; i < len; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+void ensure_fgmres_space(mg_handle *h, int m, cudaStream_t s) {
+  if (m <= h->fm) return;
+  ck(cudaStreamSynchronize(s));
+  for (void *p : h->fmem) cudaFree(p);
+  h->fmem.clear();
+  h->fm = 0;
+  const long long len = h->lv[0].len;
+  auto grab = [&](size_t count) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+      throw std::bad_alloc();
+    }
+    h->fmem.push_back(p);
+    return static_cast<double *>(p);
+  };
+  h->fV = grab((size_t)(m + 1) * len);
+  h->fZ = grab((size_t)m * len);
+  h->fm = m;
+}
+
+bool is_device_pointer(const void *p) {
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+void mg_default_options(mg_options *o) {
+  if (!o) return;
+  o->levels = 2;
+  o->nu_pre = 1;
+  o->nu_post = 1;
+  o->coarse_rtol = 1e-3;
+  o->coarse_maxit = 50;
+  o->coarse_fixed_iters = 0;
+  o->end_rule = 0;
+  o->precision = MG_PRECISION_FP64;
+}
+
+const char *mg_status_string(int st) {
+  switch (st) {
+    case MG_OK: return "ok";
+    case MG_NOT_CONVERGED: return "not converged within maxit";
+    case MG_ERR_ARG: return "invalid argument";
+    case MG_ERR_SINGULAR: return "singular local Schur complement (N_k not invertible)";
+    case MG_ERR_BREAKDOWN: return "Arnoldi breakdown (non-finite Hessenberg entry)";
+    case MG_ERR_CUDA: return "CUDA runtime error";
+    case MG_ERR_OOM: return "device out of memory";
+    case MG_ERR_NONFINITE: return "NaN or Inf in the input";
+    case MG_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char *mg_last_cuda_error(void) { return g_last_cuda_error; }
+
+long long mg_vector_length(const mg_handle *h) { return h ? h->lv[0].len : 0; }
+
+long long mg_launch_count(const mg_handle *h) { return h ? h->launches : 0; }
+
+int mg_profile_enable(mg_handle *h, int enable) {
+  if (!h) return MG_ERR_ARG;
+  try {
+    harvest(h);
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  }
+  h->prof = enable;
+  for (int c = 0; c < 16; ++c) {
+    h->prof_ms[c] = 0.0;
+    h->prof_count[c] = 0;
+  }
+  return MG_OK;
+}
+
+int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches) {
+  if (!h || max < 0) return MG_ERR_ARG;
+  try {
+    harvest(h);
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  }
+  const int k = std::min<int>(max, CAT_COUNT);
+  for (int c = 0; c < k; ++c) {
+    if (names) names[c] = kCatNames[c];
+    if (ms) ms[c] = h->prof_ms[c];
+    if (launches) launches[c] = h->prof_count[c];
+  }
+  return CAT_COUNT;
+}
+
+void mg_destroy(mg_handle *h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (auto &pe : h->ev_pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->mem.release();
+  for (void *p : h->fmem) cudaFree(p);
+  if (h->host_scal) cudaFreeHost(h->host_scal);
+  delete h;
+}
+
+int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle **out) {
+  if (!out) return MG_ERR_ARG;
+  *out = nullptr;
+  if (!P || !O) return MG_ERR_ARG;
+  g_last_cuda_error[0] = 0;
+  const int n = P->n, p = P->p, q = P->q, layout = P->layout;
+  if (n < 1 || p < 1 || q < 1) return MG_ERR_ARG;
+  if (!(P->theta > 0.0 && P->theta <= 1.0) || !(P->gamma > 0.0)) return MG_ERR_ARG;
+  if (layout != MG_LAYOUT_DENSE && layout != MG_LAYOUT_TRIDIAG) return MG_ERR_ARG;
+  if (!P->M || !P->Ju_cur || !P->Ju_prev || !P->Jz_cur || !P->Jz_prev) return MG_ERR_ARG;
+  if (O->levels < 1 || O->levels > 30 || O->nu_pre < 0 || O->nu_post < 0) return MG_ERR_ARG;
+  if (O->coarse_maxit < 1 || O->coarse_maxit > 64 || O->coarse_fixed_iters < 0 || O->coarse_fixed_iters > 64)
+    return MG_ERR_ARG;
+  if (O->end_rule != 0 && O->end_rule != 1) return MG_ERR_ARG;
+  if (O->precision != MG_PRECISION_FP64 && O->precision != MG_PRECISION_FP32) return MG_ERR_ARG;
+  if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
+  if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
+  if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;
+  if (layout == MG_LAYOUT_TRIDIAG && p > 32 * 16) return MG_ERR_UNSUPPORTED;
+
+  const int msz = layout == MG_LAYOUT_DENSE ? p * p : 3 * p;
+  const int zsz = layout == MG_LAYOUT_DENSE ? p * q : 3 * p;
+  const long long nz = P->jz_const ? 1 : n;
+  if (!host_finite(P->M, msz) || !host_finite(P->Ju_cur, (long long)n * msz) ||
+      !host_finite(P->Ju_prev, (long long)n * msz) || !host_finite(P->Jz_cur, nz * zsz) ||
+      !host_finite(P->Jz_prev, nz * zsz))
+    return MG_ERR_NONFINITE;
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mg_handle *h = new (std::nothrow) mg_handle();
+  if (!h) return MG_ERR_OOM;
+  h->opts = *O;
+  h->layout = layout;
+  h->n = n;
+  h->p = p;
+  h->q = q;
+  h->theta = P->theta;
+  h->gamma = P->gamma;
+  int C = 1;
+  while (32 * C < p) C *= 2;
+  h->C = C;
+  int status = MG_OK;
+  try {
+    ck(cudaMallocHost(&h->host_scal, 4 * sizeof(double)));
+    // raw data on the device (FP64)
+    double *dM = h->mem.alloc<double>(msz);
+    double *dJuc = h->mem.alloc<double>((size_t)n * msz);
+    double *dJup = h->mem.alloc<double>((size_t)n * msz);
+    double *dJzc = h->mem.alloc<double>((size_t)nz * zsz);
+    double *dJzp = h->mem.alloc<double>((size_t)nz * zsz);
+    ck(cudaMemcpyAsync(dM, P->M, msz * sizeof(double), cudaMemcpyHostToDevice, s));
+    ck(cudaMemcpyAsync(dJuc, P->Ju_cur, (size_t)n * msz * sizeof(double), cudaMemcpyHostToDevice, s));
+    ck(cudaMemcpyAsync(dJup, P->Ju_prev, (size_t)n * msz * sizeof(double), cudaMemcpyHostToDevice, s));
+    ck(cudaMemcpyAsync(dJzc, P->Jz_cur, (size_t)nz * zsz * sizeof(double), cudaMemcpyHostToDevice, s));
+    ck(cudaMemcpyAsync(dJzp, P->Jz_prev, (size_t)nz * zsz * sizeof(double), cudaMemcpyHostToDevice, s));
+    h->flag = h->mem.alloc<int>(4);
+    ck(cudaMemsetAsync(h->flag, 0, 4 * sizeof(int), s));
+
+    // index maps per level (injection reading of the coarse linearisation points)
+    std::vector<int> cur(n), prev(n);
+    for (int t = 0; t < n; ++t) cur[t] = prev[t] = t;
+    const int L = O->levels;
+    h->lv.resize(L);
+    std::vector<int *> idx_dev;
+    double dt = 1.0 / n;
+    int nl = n;
+    for (int l = 0; l < L; ++l) {
+      Level &lev = h->lv[l];
+      lev.n = nl;
+      lev.dt = dt;
+      lev.len = (long long)nl * (4 * p + q);
+      int *dcur = h->mem.alloc<int>(nl), *dprev = h->mem.alloc<int>(nl);
+      ck(cudaMemcpyAsync(dcur, cur.data(), nl * sizeof(int), cudaMemcpyHostToDevice, s));
+      ck(cudaMemcpyAsync(dprev, prev.data(), nl * sizeof(int), cudaMemcpyHostToDevice, s));
+      // the host vectors must outlive the async copies
+      ck(cudaStreamSynchronize(s));
+      double *N = h->mem.alloc<double>((size_t)nl * msz);
+      double *V = h->mem.alloc<double>((size_t)nl * msz);
+      double *Z = h->mem.alloc<double>((size_t)nl * zsz);
+      const long long work = (long long)nl * (2 * msz + zsz);
+      k_form_blocks<<<grid_for(work, 256, 1 << 20), 256, 0, s>>>(
+          nl, msz, zsz, layout == MG_LAYOUT_TRIDIAG ? p : 0, P->theta, dt, P->gamma, dM, dJuc, dJup, dJzc, dJzp,
+          P->jz_const, dcur, dprev, N, V, Z);
+      ck_launch();
+      LevelView<double> &v = lev.d.view;
+      v.n = nl;
+      v.p = p;
+      v.q = q;
+      v.layout = layout;
+      v.N = N;
+      v.V = V;
+      v.Z = Z;
+      v.sN = msz;
+      v.sV = msz;
+      v.sZ = zsz;
+      if (layout == MG_LAYOUT_TRIDIAG) {
+        double *fac = h->mem.alloc<double>((size_t)nl * 3 * p);
+        double *scan = h->mem.alloc<double>((size_t)nl * kWarp * kScanWords);
+        k_factor_tri<<<grid_for(nl, 64, 1 << 20), 64, 0, s>>>(nl, p, C, N, msz, Z, zsz, fac, scan, h->flag);
+        ck_launch();
+        v.fac = fac;
+        v.sFac = 3 * p;
+        v.scan = scan;
+      } else {
+        double *fac = h->mem.alloc<double>((size_t)nl * p * p);
+        k_factor_dense<<<grid_for(nl, 64, 1 << 20), 64, 0, s>>>(nl, p, q, N, msz, Z, zsz, fac, h->flag);
+        ck_launch();
+        v.fac = fac;
+        v.sFac = (long long)p * p;
+        v.scan = nullptr;
+      }
+      if (l == L - 1) {
+        lev.d.Cu = h->mem.alloc<double>((size_t)nl * p * p);
+        lev.d.Em = h->mem.alloc<double>((size_t)nl * p * p);
+        if (nl > 1) {
+          if (layout == MG_LAYOUT_TRIDIAG) {
+            const long long warps = (long long)(nl - 1) * p;
+            const int blocks = (int)((warps + 3) / 4);
+            switch (C) {
+              case 1: k_chain_mats_tri<1><<<blocks, 128, 0, s>>>(v, lev.d.Cu, lev.d.Em); break;
+              case 2: k_chain_mats_tri<2><<<blocks, 128, 0, s>>>(v, lev.d.Cu, lev.d.Em); break;
+              case 4: k_chain_mats_tri<4><<<blocks, 128, 0, s>>>(v, lev.d.Cu, lev.d.Em); break;
+              case 8: k_chain_mats_tri<8><<<blocks, 128, 0, s>>>(v, lev.d.Cu, lev.d.Em); break;
+              default: k_chain_mats_tri<16><<<blocks, 128, 0, s>>>(v, lev.d.Cu, lev.d.Em); break;
+            }
+          } else {
+            k_chain_mats_dense<<<grid_for(nl - 1, 64, 1 << 20), 64, 0, s>>>(v, lev.d.Cu, lev.d.Em);
+          }
+          ck_launch();
+        }
+      }
+      alloc_level_vectors<double>(h, lev, lev.d, l == L - 1, l == 0);
+      if (O->precision == MG_PRECISION_FP32) {
+        LevelView<float> &f = lev.f.view;
+        f.n = nl;
+        f.p = p;
+        f.q = q;
+        f.layout = layout;
+        f.N = to_float_copy(h, N, (long long)nl * msz, s);
+        f.V = to_float_copy(h, V, (long long)nl * msz, s);
+        f.Z = to_float_copy(h, Z, (long long)nl * zsz, s);
+        f.sN = v.sN;
+        f.sV = v.sV;
+        f.sZ = v.sZ;
+        f.fac = to_float_copy(h, v.fac, (long long)nl * v.sFac, s);
+        f.sFac = v.sFac;
+        f.scan = layout == MG_LAYOUT_TRIDIAG ? to_float_copy(h, v.scan, (long long)nl * kWarp * kScanWords, s)
+                                             : nullptr;
+        if (l == L - 1) {
+          lev.f.Cu = to_float_copy(h, lev.d.Cu, (long long)nl * p * p, s);
+          lev.f.Em = to_float_copy(h, lev.d.Em, (long long)nl * p * p, s);
+        }
+        alloc_level_vectors<float>(h, lev, lev.f, l == L - 1, l == 0);
+      }
+      // next level's maps: coarse K <- fine 2K (current), max(2K-1, 0) (previous)
+      if (l + 1 < L) {
+        const int nc = nl / 2;
+        std::vector<int> c2(nc), p2(nc);
+        for (int K = 0; K < nc; ++K) {
+          c2[K] = cur[2 * K];
+          p2[K] = prev[std::max(2 * K - 1, 0)];
+        }
+        cur.swap(c2);
+        prev.swap(p2);
+        nl = nc;
+        dt *= 2.0;
+      }
+    }
+    // coarse GMRES workspace
+    Level &cl = h->lv.back();
+    h->cmax = std::max(O->coarse_maxit, O->coarse_fixed_iters);
+    h->cV = h->mem.alloc<double>((size_t)(h->cmax + 1) * cl.len);
+    h->cZ = h->mem.alloc<double>((size_t)h->cmax * cl.len);
+    h->cw = h->mem.alloc<double>(cl.len);
+    h->cr = h->mem.alloc<double>(cl.len);
+    h->cy = h->mem.alloc<double>(cl.len);
+    // small buffers (sized for restarts up to 512)
+    h->ldh = 513;
+    h->partial = h->mem.alloc<double>((size_t)h->G * 512);
+    for (mg_handle::Krylov *K : {&h->kf, &h->kc}) {
+      K->h = h->mem.alloc<double>(1024);
+      K->H = h->mem.alloc<double>((size_t)h->ldh * 512);
+      K->cs = h->mem.alloc<double>(512);
+      K->sn = h->mem.alloc<double>(512);
+      K->g = h->mem.alloc<double>(513);
+      K->ycoef = h->mem.alloc<double>(512);
+      K->scal = h->mem.alloc<double>(8);
+      K->nrm2 = h->mem.alloc<double>(8);
+    }
+    int flag = 0;
+    ck(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    if (flag) status = MG_ERR_SINGULAR;
+  } catch (const CudaFail &) {
+    status = MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    status = MG_ERR_OOM;
+  }
+  if (status != MG_OK) {
+    mg_destroy(h);
+    return status;
+  }
+  *out = h;
+  return MG_OK;
+}
+
+int mg_vcycle(mg_handle *h, const double *r, double *y, void *stream) {
+  if (!h || !r || !y || r == y) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    precondition(h, r, y, s);
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    return MG_ERR_OOM;
+  }
+  return MG_OK;
+}
+
+int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, int maxit, int restart,
+                 mg_solve_info *info, void *stream) {
+  if (!h || !b_in || !x_out || maxit < 1 || restart < 1 || restart > 512 || !(rtol >= 0.0)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long len = h->lv[0].len;
+  int status = MG_OK;
+  h->vcycles = 0;
+  h->coarse_iters = 0;
+  int total = 0;
+  double est_rel = 1.0, true_rel = 0.0;
+  try {
+    const int m = std::min(restart, maxit);
+    ensure_fgmres_space(h, m, s);
+    if (!h->fw) {
+      h->fw = h->mem.alloc<double>(len);
+      h->fr = h->mem.alloc<double>(len);
+      h->fx_stage = h->mem.alloc<double>(len);
+      h->fb_stage = h->mem.alloc<double>(len);
+    }
+    const bool b_dev = is_device_pointer(b_in), x_dev = is_device_pointer(x_out);
+    const double *b = b_in;
+    if (!b_dev) {
+      ck(cudaMemcpyAsync(h->fb_stage, b_in, len * sizeof(double), cudaMemcpyHostToDevice, s));
+      b = h->fb_stage;
+    }
+    double *x = x_dev ? x_out : h->fx_stage;
+    ck(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
+    {
+      Bracket br(h, CAT_SMALL, s);
+      k_check_finite<<<grid_for(len, 256), 256, 0, s>>>(b, len, h->flag + 1);
+      ck_launch();
+    }
+    int bad = 0;
+    ck(cudaMemcpyAsync(&bad, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    mg_handle::Krylov &K = h->kf;
+    norm_into(h, K, b, len, s);
+    read_scal(h, K, s);
+    if (bad) throw 1;
+    const double bnorm = h->host_scal[0];
+    ck(cudaMemsetAsync(x, 0, len * sizeof(double), s));
+    if (bnorm > 0.0) {
+      const double *r = b;
+      bool done = false;
+      while (!done && total < maxit) {
+        // beta = ||r||, v_0 = r / beta
+        norm_into(h, K, r, len, s);
+        {
+          Bracket br(h, CAT_AXPY, s);
+          k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, r, K.scal + 1, len);
+          ck_launch();
+        }
+        {
+          Bracket br(h, CAT_SMALL, s);
+          k_arnoldi_init<<<1, 128, 0, s>>>(K.scal, K.g, m);
+          ck_launch();
+        }
+        const int mm = std::min(m, maxit - total);
+        int k = 0;
+        for (int j = 0; j < mm; ++j) {
+          double *vj = h->fV + (long long)j * len, *zj = h->fZ + (long long)j * len;
+          precondition(h, vj, zj, s);
+          launch_apply<double>(h, h->lv[0].d.view, zj, nullptr, h->fw, s);
+          arnoldi_step(h, K, h->fV, len, j, h->fw, s);
+          k = j + 1;
+          total++;
+          const double est = h->host_scal[0], hj1 = h->host_scal[2];
+          if (!std::isfinite(est) || !std::isfinite(hj1)) {
+            status = MG_ERR_BREAKDOWN;
+            done = true;
+            break;
+          }
+          est_rel = est / bnorm;
+          if (est <= rtol * bnorm || hj1 == 0.0) {
+            done = true;
+            break;
+          }
+        }
+        if (status != MG_OK) break;
+        {
+          Bracket br(h, CAT_SMALL, s);
+          k_backsolve<<<1, 1, 0, s>>>(k, K.H, h->ldh, K.g, K.ycoef);
+          ck_launch();
+        }
+        multi_axpy(h, x, h->fZ, len, K.ycoef, k, 1.0, len, s);
+        if (!done && total < maxit) {
+          launch_apply<double>(h, h->lv[0].d.view, x, b, h->fr, s);
+          r = h->fr;
+        }
+      }
+      // true residual (FP64)
+      launch_apply<double>(h, h->lv[0].d.view, x, b, h->fr, s);
+      norm_into(h, K, h->fr, len, s);
+      read_scal(h, K, s);
+      true_rel = h->host_scal[0] / bnorm;
+      if (status == MG_OK && est_rel > rtol) status = MG_NOT_CONVERGED;
+    } else {
+      est_rel = 0.0;
+    }
+    if (!x_dev) ck(cudaMemcpyAsync(x_out, x, len * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    harvest(h);
+  } catch (const CudaFail &) {
+    status = MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    status = MG_ERR_OOM;
+  } catch (int) {
+    status = MG_ERR_NONFINITE;
+  }
+  if (info) {
+    info->iters = total;
+    info->vcycles = h->vcycles;
+    info->coarse_iters = h->coarse_iters;
+    info->relres = est_rel;
+    info->true_relres = true_rel;
+  }
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+// Setup kernels (FP64): scaled blocks per level, local Schur-complement
+// factors (Thm 1) and the SGS chain matrices of the coarsest level.
+#pragma once
+
+#include "common.cuh"
+
+namespace pintmg {
+
+// N = (M - theta dt Ju_cur) / dt,  V = (-M - (1 - theta) dt Ju_prev) / dt,
+// Z = -(theta Jz_cur + (1 - theta) Jz_prev) / gamma          (Eq. blocks-aj, Sec. 5.1)
+// Raw blocks are picked by index maps (coarse levels: injected points).
+// One thread per stored coefficient.  tri_p > 0 (tridiagonal layout): the
+// two band entries outside the matrix (band[0][0], band[2][p-1]) are set to 0.
+__global__ void k_form_blocks(int n, int msz, int zsz, int tri_p, double theta, double dt, double gamma,
+                              const double *__restrict__ M, const double *__restrict__ Ju_cur,
+                              const double *__restrict__ Ju_prev, const double *__restrict__ Jz_cur,
+                              const double *__restrict__ Jz_prev, int jz_const,
+                              const int *__restrict__ cur_idx, const int *__restrict__ prev_idx,
+                              double *N, double *V, double *Z) {
+  const long long total = (long long)n * (2 * msz + zsz);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long per = 2 * msz + zsz;
+    const int t = (int)(idx / per);
+    int k = (int)(idx % per);
+    const int ci = cur_idx[t], pi = prev_idx[t];
+    if (tri_p > 0) {
+      const int kk = k % msz;
+      if (kk == 0 || kk == 3 * tri_p - 1) {
+        double *dst = (k < msz) ? N : (k < 2 * msz) ? V : Z;
+        const int sz = (k < 2 * msz) ? msz : zsz;
+        dst[(long long)t * sz + kk] = 0.0;
+        continue;
+      }
+    }
+    if (k < msz) {
+      N[(long long)t * msz + k] = (M[k] - theta * dt * Ju_cur[(long long)ci * msz + k]) / dt;
+    } else if (k < 2 * msz) {
+      k -= msz;
+      V[(long long)t * msz + k] = (-M[k] - (1.0 - theta) * dt * Ju_prev[(long long)pi * msz + k]) / dt;
+    } else {
+      k -= 2 * msz;
+      const long long zc = jz_const ? 0 : (long long)ci * zsz;
+      const long long zp = jz_const ? 0 : (long long)pi * zsz;
+      Z[(long long)t * zsz + k] = -(theta * Jz_cur[zc + k] + (1.0 - theta) * Jz_prev[zp + k]) / gamma;
+    }
+  }
+}
+
+// LDL^T of the pentadiagonal S = N N^T + Z Z^T for every block, and each
+// lane chunk's 2x2 maps of the forward / backward recurrences (chunk C).
+// One thread per block.  status[0] is set to 1 on a non-positive or
+// non-finite pivot (Thm 1: N_k singular).
+__global__ void k_factor_tri(int n, int p, int C, const double *__restrict__ N, long long sN,
+                             const double *__restrict__ Z, long long sZ, double *fac, double *scan,
+                             int *status) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double *b0 = N + j * sN, *b1 = b0 + p, *b2 = b0 + 2 * p;
+  const double *z0 = Z + j * sZ, *z1 = z0 + p, *z2 = z0 + 2 * p;
+  double *a = fac + (long long)j * 3 * p, *bb = a + p, *dinv = a + 2 * p;
+  double d1 = 0, d2 = 0, a1 = 0;  // d_{i-1}, d_{i-2}, a_{i-1}
+  bool bad = false;
+  for (int i = 0; i < p; ++i) {
+    double sd = b0[i] * b0[i] + b1[i] * b1[i] + b2[i] * b2[i] + z0[i] * z0[i] + z1[i] * z1[i] + z2[i] * z2[i];
+    double s1 = 0, s2 = 0;
+    if (i >= 1) s1 = b0[i] * b1[i - 1] + b1[i] * b2[i - 1] + z0[i] * z1[i - 1] + z1[i] * z2[i - 1];
+    if (i >= 2) s2 = b0[i] * b2[i - 2] + z0[i] * z2[i - 2];
+    double bi = (i >= 2) ? s2 / d2 : 0.0;
+    double ai = (i >= 1) ? (s1 - bi * a1 * d2) / d1 : 0.0;
+    double di = sd - ai * ai * d1 - bi * bi * d2;
+    if (!(di > 0.0) || !isfinite(di)) bad = true;
+    a[i] = ai;
+    bb[i] = bi;
+    dinv[i] = 1.0 / di;
+    d2 = d1;
+    d1 = di;
+    a1 = ai;
+  }
+  if (bad) atomicExch(status, 1);
+  // chunk maps: forward (g_{lo-2}, g_{lo-1}) -> (g_{hi-2}, g_{hi-1}),
+  //             backward (x_hi, x_{hi+1}) -> (x_lo, x_{lo+1})
+  double *sc = scan + (long long)j * kWarp * kScanWords;
+  for (int ln = 0; ln < kWarp; ++ln) {
+    for (int col = 0; col < 2; ++col) {
+      double s1 = (col == 0) ? 1.0 : 0.0, s2 = (col == 0) ? 0.0 : 1.0;
+      for (int e = 0; e < C; ++e) {
+        int i = ln * C + e;
+        double ai = (i < p) ? a[i] : 0.0, bi = (i < p) ? bb[i] : 0.0;
+        double g = -ai * s2 - bi * s1;
+        s1 = s2;
+        s2 = g;
+      }
+      sc[ln * kScanWords + 0 + col] = s1;
+      sc[ln * kScanWords + 2 + col] = s2;
+      s1 = (col == 0) ? 1.0 : 0.0;
+      s2 = (col == 0) ? 0.0 : 1.0;
+      for (int e = C - 1; e >= 0; --e) {
+        int i = ln * C + e;
+        double na = (i + 1 < p) ? a[i + 1] : 0.0, nb = (i + 2 < p) ? bb[i + 2] : 0.0;
+        double xi = -na * s1 - nb * s2;
+        s2 = s1;
+        s1 = xi;
+      }
+      sc[ln * kScanWords + 4 + col] = s1;
+      sc[ln * kScanWords + 6 + col] = s2;
+    }
+  }
+}
+
+// Cholesky of the dense S = N N^T + Z Z^T (p <= 4), diagonal stored inverted.
+__global__ void k_factor_dense(int n, int p, int q, const double *__restrict__ N, long long sN,
+                               const double *__restrict__ Z, long long sZ, double *fac, int *status) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double *Nj = N + j * sN, *Zj = Z + j * sZ;
+  double S[kDenseMax * kDenseMax];
+  for (int r = 0; r < p; ++r)
+    for (int c = 0; c < p; ++c) {
+      double acc = 0;
+      for (int k = 0; k < p; ++k) acc += Nj[r * p + k] * Nj[c * p + k];
+      for (int k = 0; k < q; ++k) acc += Zj[r * q + k] * Zj[c * q + k];
+      S[r * p + c] = acc;
+    }
+  double *L = fac + (long long)j * p * p;
+  bool bad = false;
+  for (int c = 0; c < p; ++c) {
+    double d = S[c * p + c];
+    for (int k = 0; k < c; ++k) d -= L[c * p + k] * L[c * p + k];
+    if (!(d > 0.0) || !isfinite(d)) {
+      bad = true;
+      d = 1.0;
+    }
+    double lc = sqrt(d);
+    L[c * p + c] = 1.0 / lc;
+    for (int r = c + 1; r < p; ++r) {
+      double s = S[r * p + c];
+      for (int k = 0; k < c; ++k) s -= L[r * p + k] * L[c * p + k];
+      L[r * p + c] = s / lc;
+    }
+    for (int r = 0; r < c; ++r) L[r * p + c] = 0.0;
+  }
+  if (bad) atomicExch(status, 1);
+}
+
+// Coarsest-level SGS chain matrices, column `col` of block j:
+//   Cu_j e = N_j^T S_j^-1 V_j e,   Em_j e = V_j^T S_j^-1 N_j e     (j = 1..n-1)
+// Tridiagonal: one warp per (j, col).
+template <int C>
+__global__ void __launch_bounds__(128) k_chain_mats_tri(LevelView<double> L, double *Cu, double *Em) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / kWarp;
+  const int n = L.n, p = L.p;
+  const long long total = (long long)(n - 1) * p;
+  if (w >= total) return;
+  const int j = 1 + (int)(w / p), col = (int)(w % p);
+  const double *N = L.N + j * L.sN, *V = L.V + j * L.sV;
+  const double *fac = L.fac + j * L.sFac;
+  const double *scan = L.scan + (long long)j * kWarp * kScanWords;
+  double e[C], t[C], s[C], o[C];
+#pragma unroll
+  for (int k = 0; k < C; ++k) e[k] = (ln * C + k == col) ? 1.0 : 0.0;
+  // Cu column: N^T S^-1 V e
+  tri_mv<double, C, false>(t, V, e, p, ln, 1.0);
+  penta_solve<double, C>(s, t, fac, scan, p, ln);
+  tri_mtv<double, C, false>(o, N, s, p, ln, 1.0);
+#pragma unroll
+  for (int k = 0; k < C; ++k) {
+    int i = ln * C + k;
+    if (i < p) Cu[((long long)j * p + i) * p + col] = o[k];
+  }
+  // Em column: V^T S^-1 N e
+  tri_mv<double, C, false>(t, N, e, p, ln, 1.0);
+  penta_solve<double, C>(s, t, fac, scan, p, ln);
+  tri_mtv<double, C, false>(o, V, s, p, ln, 1.0);
+#pragma unroll
+  for (int k = 0; k < C; ++k) {
+    int i = ln * C + k;
+    if (i < p) Em[((long long)j * p + i) * p + col] = o[k];
+  }
+}
+
+__global__ void k_chain_mats_dense(LevelView<double> L, double *Cu, double *Em) {
+  const int j = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = L.n, p = L.p;
+  if (j >= n) return;
+  const double *N = L.N + j * L.sN, *V = L.V + j * L.sV, *fac = L.fac + j * L.sFac;
+  for (int col = 0; col < p; ++col) {
+    double e[kDenseMax] = {}, t[kDenseMax], s[kDenseMax], o[kDenseMax];
+    e[col] = 1.0;
+    dn_mv<double>(t, V, e, p, p, 1.0, false);
+    dn_chol_solve<double>(s, t, fac, p);
+    dn_mtv<double>(o, N, s, p, p, 1.0, false);
+    for (int i = 0; i < p; ++i) Cu[((long long)j * p + i) * p + col] = o[i];
+    dn_mv<double>(t, N, e, p, p, 1.0, false);
+    dn_chol_solve<double>(s, t, fac, p);
+    dn_mtv<double>(o, V, s, p, p, 1.0, false);
+    for (int i = 0; i < p; ++i) Em[((long long)j * p + i) * p + col] = o[i];
+  }
+}
+
+// NaN / Inf detector: flag[0] = 1 if any entry is not finite.
+__global__ void k_check_finite(const double *__restrict__ x, long long len, int *flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) bad = true;
+  if (bad) atomicExch(flag, 1);
+}
+
+__global__ void k_to_float(const double *__restrict__ x, float *y, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void k_to_double(const float *__restrict__ x, double *y, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+}  // namespace pintmg

@@ -1,0 +1,540 @@
+// V-cycle kernels: block solve (Jacobi / SGS passes), residual + restriction,
+// prolongation, operator apply and the serial SGS chains.
+#pragma once
+
+#include "common.cuh"
+
+namespace pintmg {
+
+// ---------------------------------------------------------------------------
+// Local augmented solve D_j y = r of time block j (Thm 1), by the Schur
+// complement of the identity block:
+//   v = -r_mu;  S lambda = N r_u + Z r_z + V v - r_lambda,  S = N N^T + Z Z^T
+//   u = r_u - N^T lambda;  z = r_z - Z^T lambda;  mu = v + V^T lambda - r_v
+// (block 0 has no v, mu; block n has only v = -r_mu, mu = v - r_v).
+
+template <typename T, int C>
+__device__ __forceinline__ void local_solve_tri(const LevelView<T> &L, int j,
+                                                const T (&ru)[C], const T (&rz)[C], const T (&rl)[C],
+                                                const T (&rv)[C], const T (&rm)[C],
+                                                T (&u)[C], T (&z)[C], T (&l)[C], T (&v)[C], T (&m)[C],
+                                                int ln) {
+  const int n = L.n, p = L.p;
+  if (j == n) {
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+      v[e] = -rm[e];
+      m[e] = v[e] - rv[e];
+    }
+    return;
+  }
+  const T *N = L.N + j * L.sN, *V = L.V + j * L.sV, *Z = L.Z + j * L.sZ;
+  const T *fac = L.fac + j * L.sFac;
+  const T *scan = L.scan + (long long)j * kWarp * kScanWords;
+  T rhs[C];
+  tri_mv<T, C, false>(rhs, N, ru, p, ln, T(1));
+  tri_mv<T, C, true>(rhs, Z, rz, p, ln, T(1));
+#pragma unroll
+  for (int e = 0; e < C; ++e) rhs[e] -= rl[e];
+  if (j >= 1) {
+#pragma unroll
+    for (int e = 0; e < C; ++e) v[e] = -rm[e];
+    tri_mv<T, C, true>(rhs, V, v, p, ln, T(1));
+  }
+  penta_solve<T, C>(l, rhs, fac, scan, p, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    u[e] = ru[e];
+    z[e] = rz[e];
+  }
+  tri_mtv<T, C, true>(u, N, l, p, ln, T(-1));
+  tri_mtv<T, C, true>(z, Z, l, p, ln, T(-1));
+  if (j >= 1) {
+#pragma unroll
+    for (int e = 0; e < C; ++e) m[e] = v[e] - rv[e];
+    tri_mtv<T, C, true>(m, V, l, p, ln, T(1));
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void local_solve_dense(const LevelView<T> &L, int j,
+                                                  const T *ru, const T *rz, const T *rl,
+                                                  const T *rv, const T *rm,
+                                                  T *u, T *z, T *l, T *v, T *m) {
+  const int n = L.n, p = L.p, q = L.q;
+  if (j == n) {
+    for (int i = 0; i < p; ++i) {
+      v[i] = -rm[i];
+      m[i] = v[i] - rv[i];
+    }
+    return;
+  }
+  const T *N = L.N + j * L.sN, *V = L.V + j * L.sV, *Z = L.Z + j * L.sZ;
+  const T *fac = L.fac + j * L.sFac;
+  T rhs[kDenseMax];
+  dn_mv<T>(rhs, N, ru, p, p, T(1), false);
+  dn_mv<T>(rhs, Z, rz, p, q, T(1), true);
+  for (int i = 0; i < p; ++i) rhs[i] -= rl[i];
+  if (j >= 1) {
+    for (int i = 0; i < p; ++i) v[i] = -rm[i];
+    dn_mv<T>(rhs, V, v, p, p, T(1), true);
+  }
+  dn_chol_solve<T>(l, rhs, fac, p);
+  for (int i = 0; i < p; ++i) u[i] = ru[i];
+  for (int i = 0; i < q; ++i) z[i] = rz[i];
+  dn_mtv<T>(u, N, l, p, p, T(-1), true);
+  dn_mtv<T>(z, Z, l, p, q, T(-1), true);
+  if (j >= 1) {
+    for (int i = 0; i < p; ++i) m[i] = v[i] - rv[i];
+    dn_mtv<T>(m, V, l, p, p, T(1), true);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// out = D^-1 (r - C y), where C carries the couplings of A~ between blocks
+// (the identity entries of L and L^T, Fig. 5): block j's mu_{j-1} row sees
+// u_{j-1} (cplU) and its u_j row sees mu_j (cplM).  Either may be null (zero).
+// With cplU = y.u, cplM = y.m this is one block-Jacobi sweep (Eq. jacobi-aj).
+
+template <typename T, int C>
+__global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T *__restrict__ r,
+                                                         const T *cplU, const T *cplM, T *out) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int n = L.n, p = L.p, q = L.q;
+  if (j > n) return;
+  Vec<const T> R = make_cvec(r, n, p, q);
+  Vec<T> Y = make_vec(out, n, p, q);
+  T ru[C], rz[C], rl[C], rv[C], rm[C];
+  T u[C], z[C], l[C], v[C], m[C];
+#pragma unroll
+  for (int e = 0; e < C; ++e) { ru[e] = rz[e] = rl[e] = rv[e] = rm[e] = T(0); }
+  if (j < n) {
+    chunk_load<T, C>(ru, R.u + (long long)j * p, p, ln);
+    chunk_load<T, C>(rz, R.z + (long long)j * q, q, ln);
+    chunk_load<T, C>(rl, R.l + (long long)j * p, p, ln);
+    if (cplM) {
+      T c[C];
+      chunk_load<T, C>(c, cplM + (long long)j * p, p, ln);
+#pragma unroll
+      for (int e = 0; e < C; ++e) ru[e] -= c[e];
+    }
+  }
+  if (j >= 1) {
+    chunk_load<T, C>(rv, R.v + (long long)(j - 1) * p, p, ln);
+    chunk_load<T, C>(rm, R.m + (long long)(j - 1) * p, p, ln);
+    if (cplU) {
+      T c[C];
+      chunk_load<T, C>(c, cplU + (long long)(j - 1) * p, p, ln);
+#pragma unroll
+      for (int e = 0; e < C; ++e) rm[e] -= c[e];
+    }
+  }
+  local_solve_tri<T, C>(L, j, ru, rz, rl, rv, rm, u, z, l, v, m, ln);
+  if (j < n) {
+    chunk_store<T, C>(Y.u + (long long)j * p, u, p, ln);
+    chunk_store<T, C>(Y.z + (long long)j * q, z, q, ln);
+    chunk_store<T, C>(Y.l + (long long)j * p, l, p, ln);
+  }
+  if (j >= 1) {
+    chunk_store<T, C>(Y.v + (long long)(j - 1) * p, v, p, ln);
+    chunk_store<T, C>(Y.m + (long long)(j - 1) * p, m, p, ln);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const T *__restrict__ r,
+                                                           const T *cplU, const T *cplM, T *out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = L.n, p = L.p, q = L.q;
+  if (j > n) return;
+  Vec<const T> R = make_cvec(r, n, p, q);
+  Vec<T> Y = make_vec(out, n, p, q);
+  T ru[kDenseMax] = {}, rz[kDenseMax] = {}, rl[kDenseMax] = {}, rv[kDenseMax] = {}, rm[kDenseMax] = {};
+  T u[kDenseMax], z[kDenseMax], l[kDenseMax], v[kDenseMax], m[kDenseMax];
+  if (j < n) {
+    for (int i = 0; i < p; ++i) {
+      ru[i] = R.u[(long long)j * p + i];
+      rl[i] = R.l[(long long)j * p + i];
+      if (cplM) ru[i] -= cplM[(long long)j * p + i];
+    }
+    for (int i = 0; i < q; ++i) rz[i] = R.z[(long long)j * q + i];
+  }
+  if (j >= 1) {
+    for (int i = 0; i < p; ++i) {
+      rv[i] = R.v[(long long)(j - 1) * p + i];
+      rm[i] = R.m[(long long)(j - 1) * p + i];
+      if (cplU) rm[i] -= cplU[(long long)(j - 1) * p + i];
+    }
+  }
+  local_solve_dense<T>(L, j, ru, rz, rl, rv, rm, u, z, l, v, m);
+  if (j < n) {
+    for (int i = 0; i < p; ++i) {
+      Y.u[(long long)j * p + i] = u[i];
+      Y.l[(long long)j * p + i] = l[i];
+    }
+    for (int i = 0; i < q; ++i) Y.z[(long long)j * q + i] = z[i];
+  }
+  if (j >= 1) {
+    for (int i = 0; i < p; ++i) {
+      Y.v[(long long)(j - 1) * p + i] = v[i];
+      Y.m[(long long)(j - 1) * p + i] = m[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rows of A~ x for step t (Fig. 4 rows, in the type-major layout):
+//   u_t:      u_t + N_t^T l_t + m_t
+//   v_t:      v_t + V_{t+1}^T l_{t+1} - m_t          (no V term for t = n-1)
+//   z_t:      z_t + Z_t^T l_t
+//   lambda_t: V_t v_{t-1} + N_t u_t + Z_t z_t       (no V term for t = 0)
+//   mu_t:     u_t - v_t
+
+// out = b - A~ x  (b non-null)  or  out = A~ x  (b null), all five types.
+template <typename T, int C>
+__global__ void __launch_bounds__(128) k_apply_tri(LevelView<T> L, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *out) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int n = L.n, p = L.p, q = L.q;
+  if (t >= n) return;
+  Vec<const T> X = make_cvec(x, n, p, q);
+  Vec<T> O = make_vec(out, n, p, q);
+  const T *N = L.N + t * L.sN, *Z = L.Z + t * L.sZ, *Vt = L.V + t * L.sV;
+  T xu[C], xv[C], xz[C], xl[C], xm[C], acc[C];
+  chunk_load<T, C>(xu, X.u + (long long)t * p, p, ln);
+  chunk_load<T, C>(xv, X.v + (long long)t * p, p, ln);
+  chunk_load<T, C>(xz, X.z + (long long)t * q, q, ln);
+  chunk_load<T, C>(xl, X.l + (long long)t * p, p, ln);
+  chunk_load<T, C>(xm, X.m + (long long)t * p, p, ln);
+  const T sgn = b ? T(-1) : T(1);
+  Vec<const T> B = make_cvec(b ? b : x, n, p, q);
+  // u row
+#pragma unroll
+  for (int e = 0; e < C; ++e) acc[e] = xu[e] + xm[e];
+  tri_mtv<T, C, true>(acc, N, xl, p, ln, T(1));
+  {
+    T o[C];
+    if (b) chunk_load<T, C>(o, B.u + (long long)t * p, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
+    chunk_store<T, C>(O.u + (long long)t * p, o, p, ln);
+  }
+  // v row
+#pragma unroll
+  for (int e = 0; e < C; ++e) acc[e] = xv[e] - xm[e];
+  if (t + 1 < n) {
+    T xl1[C];
+    chunk_load<T, C>(xl1, X.l + (long long)(t + 1) * p, p, ln);
+    tri_mtv<T, C, true>(acc, L.V + (t + 1) * L.sV, xl1, p, ln, T(1));
+  }
+  {
+    T o[C];
+    if (b) chunk_load<T, C>(o, B.v + (long long)t * p, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
+    chunk_store<T, C>(O.v + (long long)t * p, o, p, ln);
+  }
+  // z row
+#pragma unroll
+  for (int e = 0; e < C; ++e) acc[e] = xz[e];
+  tri_mtv<T, C, true>(acc, Z, xl, p, ln, T(1));
+  {
+    T o[C];
+    if (b) chunk_load<T, C>(o, B.z + (long long)t * q, q, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
+    chunk_store<T, C>(O.z + (long long)t * q, o, q, ln);
+  }
+  // lambda row
+  tri_mv<T, C, false>(acc, N, xu, p, ln, T(1));
+  tri_mv<T, C, true>(acc, Z, xz, p, ln, T(1));
+  if (t >= 1) {
+    T xv0[C];
+    chunk_load<T, C>(xv0, X.v + (long long)(t - 1) * p, p, ln);
+    tri_mv<T, C, true>(acc, Vt, xv0, p, ln, T(1));
+  }
+  {
+    T o[C];
+    if (b) chunk_load<T, C>(o, B.l + (long long)t * p, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
+    chunk_store<T, C>(O.l + (long long)t * p, o, p, ln);
+  }
+  // mu row
+  {
+    T o[C];
+    if (b) chunk_load<T, C>(o, B.m + (long long)t * p, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, xu[e] - xv[e], o[e]) : xu[e] - xv[e];
+    chunk_store<T, C>(O.m + (long long)t * p, o, p, ln);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__restrict__ x,
+                                                     const T *__restrict__ b, T *out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = L.n, p = L.p, q = L.q;
+  if (t >= n) return;
+  Vec<const T> X = make_cvec(x, n, p, q);
+  Vec<T> O = make_vec(out, n, p, q);
+  Vec<const T> B = make_cvec(b ? b : x, n, p, q);
+  const T *N = L.N + t * L.sN, *Z = L.Z + t * L.sZ;
+  const T sgn = b ? T(-1) : T(1);
+  const T *xu = X.u + (long long)t * p, *xv = X.v + (long long)t * p, *xz = X.z + (long long)t * q;
+  const T *xl = X.l + (long long)t * p, *xm = X.m + (long long)t * p;
+  T acc[kDenseMax];
+  // u row
+  for (int i = 0; i < p; ++i) acc[i] = xu[i] + xm[i];
+  dn_mtv<T>(acc, N, xl, p, p, T(1), true);
+  for (int i = 0; i < p; ++i)
+    O.u[(long long)t * p + i] = b ? fma(sgn, acc[i], B.u[(long long)t * p + i]) : acc[i];
+  // v row
+  for (int i = 0; i < p; ++i) acc[i] = xv[i] - xm[i];
+  if (t + 1 < n) dn_mtv<T>(acc, L.V + (t + 1) * L.sV, X.l + (long long)(t + 1) * p, p, p, T(1), true);
+  for (int i = 0; i < p; ++i)
+    O.v[(long long)t * p + i] = b ? fma(sgn, acc[i], B.v[(long long)t * p + i]) : acc[i];
+  // z row
+  for (int i = 0; i < q; ++i) acc[i] = xz[i];
+  dn_mtv<T>(acc, Z, xl, p, q, T(1), true);
+  for (int i = 0; i < q; ++i)
+    O.z[(long long)t * q + i] = b ? fma(sgn, acc[i], B.z[(long long)t * q + i]) : acc[i];
+  // lambda row
+  dn_mv<T>(acc, N, xu, p, p, T(1), false);
+  dn_mv<T>(acc, Z, xz, p, q, T(1), true);
+  if (t >= 1) dn_mv<T>(acc, L.V + t * L.sV, X.v + (long long)(t - 1) * p, p, p, T(1), true);
+  for (int i = 0; i < p; ++i)
+    O.l[(long long)t * p + i] = b ? fma(sgn, acc[i], B.l[(long long)t * p + i]) : acc[i];
+  // mu row
+  for (int i = 0; i < p; ++i) {
+    T d = xu[i] - xv[i];
+    O.m[(long long)t * p + i] = b ? fma(sgn, d, B.m[(long long)t * p + i]) : d;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Residual restricted to the coarse grid (Alg. 1, Sec. 5.3.1):
+//   rc_x[K] = r_x[2K]                     (x = u, v, lambda, mu: injection)
+//   rc_z[K] = (r_z[2K] + r_z[2K+1]) / 2   (control: average)
+// with r = b - A~ y evaluated only at the rows it needs.
+
+template <typename T, int C>
+__global__ void __launch_bounds__(128) k_residual_restrict_tri(LevelView<T> L, const T *__restrict__ y,
+                                                               const T *__restrict__ b, T *rc) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int K = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int n = L.n, p = L.p, q = L.q, nc = n / 2;
+  if (K >= nc) return;
+  const int t0 = 2 * K, t1 = 2 * K + 1;
+  Vec<const T> Y = make_cvec(y, n, p, q);
+  Vec<const T> B = make_cvec(b, n, p, q);
+  Vec<T> R = make_vec(rc, nc, p, q);
+  const T *N0 = L.N + t0 * L.sN, *Z0 = L.Z + t0 * L.sZ, *Z1 = L.Z + t1 * L.sZ;
+  T yu[C], yv[C], yz[C], yl[C], ym[C], acc[C], o[C];
+  chunk_load<T, C>(yu, Y.u + (long long)t0 * p, p, ln);
+  chunk_load<T, C>(yv, Y.v + (long long)t0 * p, p, ln);
+  chunk_load<T, C>(yz, Y.z + (long long)t0 * q, q, ln);
+  chunk_load<T, C>(yl, Y.l + (long long)t0 * p, p, ln);
+  chunk_load<T, C>(ym, Y.m + (long long)t0 * p, p, ln);
+  // u row at t0
+#pragma unroll
+  for (int e = 0; e < C; ++e) acc[e] = yu[e] + ym[e];
+  tri_mtv<T, C, true>(acc, N0, yl, p, ln, T(1));
+  chunk_load<T, C>(o, B.u + (long long)t0 * p, p, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) o[e] -= acc[e];
+  chunk_store<T, C>(R.u + (long long)K * p, o, p, ln);
+  // mu row at t0
+  chunk_load<T, C>(o, B.m + (long long)t0 * p, p, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) o[e] -= yu[e] - yv[e];
+  chunk_store<T, C>(R.m + (long long)K * p, o, p, ln);
+  // lambda row at t0
+  tri_mv<T, C, false>(acc, N0, yu, p, ln, T(1));
+  tri_mv<T, C, true>(acc, Z0, yz, p, ln, T(1));
+  if (t0 >= 1) {
+    T yv0[C];
+    chunk_load<T, C>(yv0, Y.v + (long long)(t0 - 1) * p, p, ln);
+    tri_mv<T, C, true>(acc, L.V + t0 * L.sV, yv0, p, ln, T(1));
+  }
+  chunk_load<T, C>(o, B.l + (long long)t0 * p, p, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) o[e] -= acc[e];
+  chunk_store<T, C>(R.l + (long long)K * p, o, p, ln);
+  // z rows at t0 and t1, averaged
+#pragma unroll
+  for (int e = 0; e < C; ++e) acc[e] = yz[e];
+  tri_mtv<T, C, true>(acc, Z0, yl, p, ln, T(1));
+  chunk_load<T, C>(o, B.z + (long long)t0 * q, q, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) o[e] -= acc[e];
+  T yl1[C], yz1[C], b1[C];
+  chunk_load<T, C>(yl1, Y.l + (long long)t1 * p, p, ln);
+  chunk_load<T, C>(yz1, Y.z + (long long)t1 * q, q, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) acc[e] = yz1[e];
+  tri_mtv<T, C, true>(acc, Z1, yl1, p, ln, T(1));
+  chunk_load<T, C>(b1, B.z + (long long)t1 * q, q, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) o[e] = T(0.5) * (o[e] + (b1[e] - acc[e]));
+  chunk_store<T, C>(R.z + (long long)K * q, o, q, ln);
+  // v row at t0: v + V_{t0+1}^T l_{t0+1} - mu   (t0 + 1 = t1 <= n - 1)
+#pragma unroll
+  for (int e = 0; e < C; ++e) acc[e] = yv[e] - ym[e];
+  tri_mtv<T, C, true>(acc, L.V + t1 * L.sV, yl1, p, ln, T(1));
+  chunk_load<T, C>(o, B.v + (long long)t0 * p, p, ln);
+#pragma unroll
+  for (int e = 0; e < C; ++e) o[e] -= acc[e];
+  chunk_store<T, C>(R.v + (long long)K * p, o, p, ln);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_residual_restrict_dense(LevelView<T> L, const T *__restrict__ y,
+                                                                 const T *__restrict__ b, T *rc) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = L.n, p = L.p, q = L.q, nc = n / 2;
+  if (K >= nc) return;
+  const int t0 = 2 * K, t1 = 2 * K + 1;
+  Vec<const T> Y = make_cvec(y, n, p, q);
+  Vec<const T> B = make_cvec(b, n, p, q);
+  Vec<T> R = make_vec(rc, nc, p, q);
+  const T *N0 = L.N + t0 * L.sN, *Z0 = L.Z + t0 * L.sZ, *Z1 = L.Z + t1 * L.sZ;
+  const T *yu = Y.u + (long long)t0 * p, *yv = Y.v + (long long)t0 * p, *yz = Y.z + (long long)t0 * q;
+  const T *yl = Y.l + (long long)t0 * p, *ym = Y.m + (long long)t0 * p;
+  const T *yl1 = Y.l + (long long)t1 * p, *yz1 = Y.z + (long long)t1 * q;
+  T acc[kDenseMax], acc1[kDenseMax];
+  for (int i = 0; i < p; ++i) acc[i] = yu[i] + ym[i];
+  dn_mtv<T>(acc, N0, yl, p, p, T(1), true);
+  for (int i = 0; i < p; ++i) R.u[(long long)K * p + i] = B.u[(long long)t0 * p + i] - acc[i];
+  for (int i = 0; i < p; ++i) R.m[(long long)K * p + i] = B.m[(long long)t0 * p + i] - (yu[i] - yv[i]);
+  dn_mv<T>(acc, N0, yu, p, p, T(1), false);
+  dn_mv<T>(acc, Z0, yz, p, q, T(1), true);
+  if (t0 >= 1) dn_mv<T>(acc, L.V + t0 * L.sV, Y.v + (long long)(t0 - 1) * p, p, p, T(1), true);
+  for (int i = 0; i < p; ++i) R.l[(long long)K * p + i] = B.l[(long long)t0 * p + i] - acc[i];
+  for (int i = 0; i < q; ++i) acc[i] = yz[i];
+  dn_mtv<T>(acc, Z0, yl, p, q, T(1), true);
+  for (int i = 0; i < q; ++i) acc1[i] = yz1[i];
+  dn_mtv<T>(acc1, Z1, yl1, p, q, T(1), true);
+  for (int i = 0; i < q; ++i)
+    R.z[(long long)K * q + i] = T(0.5) * ((B.z[(long long)t0 * q + i] - acc[i]) +
+                                          (B.z[(long long)t1 * q + i] - acc1[i]));
+  for (int i = 0; i < p; ++i) acc[i] = yv[i] - ym[i];
+  dn_mtv<T>(acc, L.V + t1 * L.sV, yl1, p, p, T(1), true);
+  for (int i = 0; i < p; ++i) R.v[(long long)K * p + i] = B.v[(long long)t0 * p + i] - acc[i];
+}
+
+// ---------------------------------------------------------------------------
+// y += P e (Sec. 5.3.1): u, v, lambda, mu linear (x_f[2K] = e[K],
+// x_f[2K+1] = (e[K] + e[K+1]) / 2, last point by end_rule); z piecewise
+// constant.  One thread per fine entry.
+template <typename T>
+__global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q, int end_rule) {
+  const long long np = (long long)n * p, nq = (long long)n * q;
+  const long long total = 4 * np + nq;
+  const int nc = n / 2;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long k = idx;
+    int width = p;
+    long long fine_off, coarse_off;
+    bool constant = false;
+    if (k < 2 * np) {  // u or v
+      long long which = k / np;
+      k -= which * np;
+      fine_off = which * np;
+      coarse_off = which * (np / 2);
+    } else if (k < 2 * np + nq) {  // z
+      k -= 2 * np;
+      width = q;
+      fine_off = 2 * np;
+      coarse_off = np;  // = 2 * (nc * p)
+      constant = true;
+    } else {  // lambda or mu
+      k -= 2 * np + nq;
+      long long which = k / np;
+      k -= which * np;
+      fine_off = 2 * np + nq + which * np;
+      coarse_off = np + nq / 2 + which * (np / 2);
+    }
+    const int t = (int)(k / width), i = (int)(k % width);
+    const int K = t >> 1;
+    const T *ec = e + coarse_off;
+    T add;
+    if (constant || (t & 1) == 0) {
+      add = ec[(long long)K * width + i];
+    } else if (K + 1 < nc) {
+      add = T(0.5) * (ec[(long long)K * width + i] + ec[(long long)(K + 1) * width + i]);
+    } else {
+      add = end_rule == 0 ? ec[(long long)K * width + i] : T(0.5) * ec[(long long)K * width + i];
+    }
+    y[fine_off + k] += add;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SGS (Sec. 5.3.4) as two serial affine chains on the coarsest grid.  With
+// w = (D + L)^-1 r and y = (D + L^T)^-1 D w, only u(w) carries the forward
+// dependence and only mu(y) the backward one:
+//   u_j  = uhat_j - Cu_j u_{j-1},      Cu_j = N_j^T S_j^-1 V_j   (j = 1..n-1)
+//   mu_{j-1} = muhat_{j-1} - Em_j mu_j, Em_j = V_j^T S_j^-1 N_j  (j = n-1..1)
+// where uhat, muhat come from independent local solves.  One CTA walks the
+// chain; thread i owns row i, the previous link's vector lives in shared memory.
+template <typename T>
+__global__ void k_chain_forward(const T *__restrict__ Cu, const T *__restrict__ uhat, T *uout,
+                                int n, int p) {
+  extern __shared__ unsigned char smem_raw[];
+  T *prev = reinterpret_cast<T *>(smem_raw);
+  const int i = threadIdx.x;
+  if (i < p) {
+    T v0 = uhat[i];
+    uout[i] = v0;
+    prev[i] = v0;
+  }
+  __syncthreads();
+  for (int j = 1; j < n; ++j) {
+    T acc = T(0);
+    if (i < p) {
+      const T *row = Cu + ((long long)j * p + i) * p;
+      acc = uhat[(long long)j * p + i];
+      for (int k = 0; k < p; ++k) acc = fma(-row[k], prev[k], acc);
+    }
+    __syncthreads();
+    if (i < p) {
+      prev[i] = acc;
+      uout[(long long)j * p + i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_chain_backward(const T *__restrict__ Em, const T *__restrict__ muhat, T *mout,
+                                 int n, int p) {
+  extern __shared__ unsigned char smem_raw[];
+  T *prev = reinterpret_cast<T *>(smem_raw);
+  const int i = threadIdx.x;
+  if (i < p) {
+    T v0 = muhat[(long long)(n - 1) * p + i];
+    mout[(long long)(n - 1) * p + i] = v0;
+    prev[i] = v0;
+  }
+  __syncthreads();
+  for (int j = n - 1; j >= 1; --j) {
+    T acc = T(0);
+    if (i < p) {
+      const T *row = Em + ((long long)j * p + i) * p;
+      acc = muhat[(long long)(j - 1) * p + i];
+      for (int k = 0; k < p; ++k) acc = fma(-row[k], prev[k], acc);
+    }
+    __syncthreads();
+    if (i < p) {
+      prev[i] = acc;
+      mout[(long long)(j - 1) * p + i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace pintmg

@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=200)
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--allow-partial", action="store_true",
+                    help="accept solves stopped by --maxit (bounded profiler captures only)")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     return ap.parse_args()
 
@@ -158,7 +160,7 @@ def run_native(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev).cuda_stream
     wl = W.WORKLOADS[args.workload]
-    prob = wl["make"](seed=2000 + 17 * rank) if "burgers" in args.workload else wl["make"]()
+    prob = wl["make"](seed=2000 + 17 * rank) if rank else wl["make"]()
     precision = P.MG_PRECISION_FP64 if args.precision == "fp64" else P.MG_PRECISION_FP32
     t0 = time.perf_counter()
     h = P.mg_setup(prob, levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=precision,
@@ -172,7 +174,7 @@ def run_native(args):
 
     def solve():
         code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
-        if code != P.MG_OK:
+        if code != P.MG_OK and not (args.allow_partial and code == P.MG_NOT_CONVERGED):
             raise RuntimeError(f"fgmres_solve: {P.mg_status_string(code)} (iters {info.iters}, "
                                f"relres {info.relres:.2e}, true {info.true_relres:.2e})")
         return info
@@ -224,7 +226,7 @@ def run_native(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         code, info = P.fgmres_solve(h, bh.data_ptr(), xh.data_ptr(), RTOL, args.maxit, args.restart, stream)
-        if code != P.MG_OK:
+        if code != P.MG_OK and not (args.allow_partial and code == P.MG_NOT_CONVERGED):
             raise RuntimeError("e2e solve failed")
     e2e_s = time.perf_counter() - t0
     e2e_value = world * args.steps / e2e_s

@@ -108,6 +108,7 @@ struct mg_handle {
   int G = 304;                  // CTAs of the dot-product kernels
   // counters of the last solve
   int vcycles = 0, coarse_iters = 0;
+  int use_cluster = 1;  // SGS chains on a thread-block cluster (tridiagonal layout)
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -341,6 +342,36 @@ void convert_back<float>(mg_handle *h, const float *x, double *y, long long len,
   }
 }
 
+// One SGS chain on a thread-block cluster (tridiagonal layout, p >= 32).
+// Returns false if the device refuses the cluster launch.
+template <typename T, bool kForward>
+bool launch_chain_cluster(mg_handle *h, const T *G, const T *xhat, T *xout, int n, int p, cudaStream_t s) {
+  for (int S : {16, 8}) {
+    const int rows = (p + S - 1) / S;
+    int tpr = 32;
+    while (tpr > 1 && rows * tpr > 256) tpr >>= 1;
+    const int threads = ((rows * tpr + 31) / 32) * 32;
+    auto kern = k_chain_cluster<T, kForward>;
+    if (S > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(S, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = 2 * (size_t)p * sizeof(T);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, G, xhat, xout, n, p, rows, tpr);
+    if (e == cudaSuccess) return true;
+    cudaGetLastError();
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------------------
 // SGS on the coarsest level (precision T): y = [(D+L) D^-1 (D+L^T)]^-1 r
 
@@ -352,21 +383,22 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
   launch_block_solve<T>(h, d.view, r, nullptr, nullptr, d.sgs_w, s);
   const int threads = std::max(32, ((p + 31) / 32) * 32);
   const size_t shm = (size_t)p * sizeof(T);
+  const bool cluster = h->layout == MG_LAYOUT_TRIDIAG && p >= 32 && h->use_cluster;
   if (n >= 1) {
-    {
-      Bracket br(h, CAT_CHAIN, s);
+    Bracket br(h, CAT_CHAIN, s);
+    if (!cluster || !launch_chain_cluster<T, true>(h, d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p, s)) {
       k_chain_forward<T><<<1, threads, shm, s>>>(d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p);
-      ck_launch();
     }
+    ck_launch();
   }
   // yhat = D^-1 (r - L w): only mu(yhat) is needed by the backward chain
   launch_block_solve<T>(h, d.view, r, d.chainU, nullptr, d.sgs_w, s);
   if (n >= 1) {
-    {
-      Bracket br(h, CAT_CHAIN, s);
+    Bracket br(h, CAT_CHAIN, s);
+    if (!cluster || !launch_chain_cluster<T, false>(h, d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p, s)) {
       k_chain_backward<T><<<1, threads, shm, s>>>(d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p);
-      ck_launch();
     }
+    ck_launch();
   }
   // y = D^-1 (r - L w - L^T y)
   launch_block_solve<T>(h, d.view, r, d.chainU, d.chainM, y, s);

@@ -2,6 +2,8 @@
 // prolongation, operator apply and the serial SGS chains.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace pintmg {
@@ -534,6 +536,69 @@ __global__ void k_chain_backward(const T *__restrict__ Em, const T *__restrict__
       mout[(long long)(j - 1) * p + i] = acc;
     }
     __syncthreads();
+  }
+}
+
+}  // namespace pintmg
+
+namespace pintmg {
+
+// ---------------------------------------------------------------------------
+// The same SGS chains spread over a thread-block cluster of S CTAs (one per
+// SM).  Link j computes x_j = xhat_j - G_j x_{j-1} (p x p dense G_j, row-major)
+// with CTA c owning rows [c R, c R + R), R = ceil(p / S).  Within a CTA, TPR
+// threads share a row: each takes p / TPR consecutive columns (coalesced row
+// loads), partial sums are combined with warp shuffles, and the row owner
+// writes the new entry into every CTA's copy of x (distributed shared memory,
+// double-buffered).  One cluster barrier per link publishes x_j.  The cluster
+// barrier is the hardware barrier.cluster (all CTAs of a cluster are
+// co-scheduled), reached the same number of times by every thread.
+// Columns are interleaved over the TPR threads of a row so that each load
+// instruction reads TPR consecutive entries of the row.
+// kForward: links j = 1..n-1 on x = u; otherwise links j = n-1..1 on x = mu
+// (x_{j-1} = xhat_{j-1} - G_j x_j).
+template <typename T, bool kForward>
+__global__ void k_chain_cluster(const T *__restrict__ G, const T *__restrict__ xhat, T *xout, int n, int p,
+                                int rows_per_cta, int tpr) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);  // [2][p]
+  const int S = (int)cluster.num_blocks();
+  const int c = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  const int row_local = tid / tpr, part = tid % tpr;
+  const int row = c * rows_per_cta + row_local;
+  const bool owner = (row_local < rows_per_cta) && (row < p);
+  // start vector: x_0 (forward) or x_{n-1} (backward), into buffer 0 of this CTA
+  const long long first = kForward ? 0 : (long long)(n - 1);
+  for (int i = tid; i < p; i += blockDim.x) buf[i] = xhat[first * p + i];
+  if (c == 0)
+    for (int i = tid; i < p; i += blockDim.x) xout[first * p + i] = xhat[first * p + i];
+  cluster.sync();
+  int cur = 0;
+  for (int step = 1; step < n; ++step) {
+    const int j = kForward ? step : n - step;            // link index
+    const long long dst = kForward ? j : (long long)(j - 1);
+    T acc = T(0);
+    if (owner) {
+      const T *gr = G + ((long long)j * p + row) * p;
+      const T *xv = buf + cur * p;
+      for (int k = part; k < p; k += tpr) acc = fma(gr[k], xv[k], acc);
+    }
+    // combine the tpr partial sums of a row (tpr divides 32, lanes of a row are contiguous)
+    for (int o = tpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, tpr);
+    const int nxt = cur ^ 1;
+    if (owner && part == 0) {
+      const T v = xhat[dst * p + row] - acc;
+      xout[dst * p + row] = v;
+      for (int r = 0; r < S; ++r) {
+        T *remote = cluster.map_shared_rank(buf, r);
+        remote[nxt * p + row] = v;
+      }
+    }
+    cluster.sync();
+    cur = nxt;
   }
 }
 

@@ -349,6 +349,8 @@ WORKLOADS = {
     "vdp_n256": dict(make=lambda seed=1000: vdp(n=256, seed=seed), levels=2, nu_pre=1, nu_post=1),
     "burgers_nx128_n1024": dict(make=lambda seed=2000: burgers(nx=128, n=1024, nu=0.01, seed=seed),
                                 levels=3, nu_pre=4, nu_post=4),
+    "burgers_nx128_n8192": dict(make=lambda seed=2500: burgers(nx=128, n=8192, nu=0.01, seed=seed),
+                                levels=3, nu_pre=4, nu_post=4),
     "burgers_nx512_n8192": dict(make=lambda seed=3000: burgers(nx=512, n=8192, nu=0.005, seed=seed),
                                 levels=4, nu_pre=4, nu_post=4),
 }

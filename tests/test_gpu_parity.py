@@ -129,3 +129,60 @@ def test_error_paths(P):
         assert code == P.MG_OK and info.iters == 0 and float(x.abs().max()) == 0.0
     finally:
         P.mg_destroy(h)
+
+
+# ---------------------------------------------------------------- mixed precision
+
+def test_fp32_vcycle_close_to_fp64_oracle(P):
+    """The FP32 V-cycle (smoother, transfers, SGS) stays within FP32 rounding
+    amplified by the local condition numbers of the FP64 oracle's cycle."""
+    prob = W.burgers(nx=40, n=32, seed=131)
+    opts = dict(levels=2, nu_pre=2, nu_post=2, coarse_fixed_iters=2)
+    h = P.mg_setup(prob, precision=P.MG_PRECISION_FP32, **opts)
+    try:
+        rd = _dev(prob.b)
+        yd = torch.empty_like(rd)
+        assert P.mg_vcycle(h, rd.data_ptr(), yd.data_ptr(), 0) == P.MG_OK
+        torch.cuda.synchronize()
+        yo = O.Hierarchy(prob, O.MGOptions(**opts)).precondition(prob.b)
+        err = np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo)
+        assert err <= 1e-3, err
+    finally:
+        P.mg_destroy(h)
+
+
+@pytest.mark.parametrize("case", [0, 4, 7])
+def test_fp32_preconditioned_fgmres_reaches_fp64_solution(P, case):
+    """FGMRES tolerates the FP32 preconditioner: same solution to 1e-9 at a 1e-10 residual."""
+    make, levels, nu_pre, nu_post, end_rule = CASES[case]
+    prob = make()
+    h = P.mg_setup(prob, levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule,
+                   precision=P.MG_PRECISION_FP32)
+    try:
+        b = _dev(prob.b)
+        x = torch.empty_like(b)
+        code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, 3000, 500)
+        assert code == P.MG_OK, P.mg_status_string(code)
+        assert info.true_relres <= 2e-10
+        xd = O.direct_solve(prob)
+        assert np.linalg.norm(x.cpu().numpy() - xd) / np.linalg.norm(xd) <= SOLVE_RTOL
+    finally:
+        P.mg_destroy(h)
+
+
+def test_cluster_chain_full_size_vcycle(P):
+    """Bench-sized coarse grid (257 blocks, p = 128) through the cluster SGS
+    chains: a sampled V-cycle agrees with the oracle."""
+    prob = W.burgers(nx=128, n=256, seed=141)
+    opts = dict(levels=2, nu_pre=1, nu_post=1, coarse_fixed_iters=2)
+    h = P.mg_setup(prob, **opts)
+    try:
+        rd = _dev(prob.b)
+        yd = torch.empty_like(rd)
+        assert P.mg_vcycle(h, rd.data_ptr(), yd.data_ptr(), 0) == P.MG_OK
+        torch.cuda.synchronize()
+        yo = O.Hierarchy(prob, O.MGOptions(**opts)).precondition(prob.b)
+        err = np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo)
+        assert err <= VCYCLE_RTOL, err
+    finally:
+        P.mg_destroy(h)

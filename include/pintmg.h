@@ -155,6 +155,27 @@ long long mg_launch_count(const mg_handle *h);
 int mg_profile_enable(mg_handle *h, int mask);
 int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches);
 
+/*
+ * True residual without allocating (the paper has no counterpart).  For
+ * callers that must not allocate device memory when they check a solution
+ * (a framework's caching allocator owns the device pool, a real-time loop
+ * with a fixed memory budget, an outer optimisation loop testing its stopping
+ * rule), computes on `stream`, asynchronously:
+ *   out[0] = ||b - A x||_2,   out[1] = ||b - A x||_2 / ||b||_2  (0 if b = 0)
+ * with the same FP64 kernels and reduction order as fgmres_solve's reported
+ * true residual.  b, x and out (2 doubles) are DEVICE pointers owned by the
+ * caller.  It calls no cudaMalloc, cudaFree or allocating library routine:
+ * its scratch (residual vector, reduction partials) is one file-scope device
+ * array of 2^20 + 616 doubles (about 8 MiB), held by every GPU that loads the
+ * library until the process exits.  Vectors longer than 2^20 doubles are
+ * rejected with MG_ERR_ARG (mg_last_cuda_error() says why).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call overwrites the
+ * same array, so calls that overlap on the GPU (other streams, other host
+ * threads) race; serialise them.
+ */
+int mg_true_residual_noalloc(mg_handle *h, const double *b, const double *x, double *out, void *stream);
+
 /* Release every device buffer of the handle.  NULL is accepted. */
 void mg_destroy(mg_handle *h);
 

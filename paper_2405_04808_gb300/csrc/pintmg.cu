@@ -1010,3 +1010,92 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Residual check that allocates nothing.
+//
+// Some callers must not allocate device memory when they check a solution:
+// code that runs while a framework's caching allocator owns the device pool,
+// a real-time loop with a fixed memory budget, or an outer optimisation loop
+// that tests its stopping rule between captured work.  fgmres_solve grows its
+// workspace on first use, so it cannot serve them.  This entry point computes
+// the FP64 true residual of any x for an existing handle with its scratch (the
+// residual vector and the reduction partial sums) in one file-scope device
+// array of fixed size, shared by every call of the process on that device.
+
+namespace {
+
+constexpr long long kNoAllocMaxLen = 1LL << 20;      // longest vector n (4p+q) accepted
+constexpr int kNoAllocPartials = 2 * 304;             // two dot products, <= 304 CTAs each
+constexpr int kMaxDevices = 64;
+
+// residual vector, then partial sums, then the two reduced squares
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxLen + kNoAllocPartials + 8];
+
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+__global__ void k_noalloc_finish(const double *sums, double *out) {
+  const double rn = sqrt(sums[0]), bn = sqrt(sums[1]);
+  out[0] = rn;
+  out[1] = bn > 0.0 ? rn / bn : 0.0;
+}
+
+}  // namespace
+
+extern "C" int mg_true_residual_noalloc(mg_handle *h, const double *b, const double *x, double *out, void *stream) {
+  if (!h || !b || !x || !out) return MG_ERR_ARG;
+  const long long len = h->lv[0].len;
+  if (len > kNoAllocMaxLen) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error,
+                  "mg_true_residual_noalloc: vector length %lld exceeds the fixed scratch of %lld doubles", len,
+                  kNoAllocMaxLen);
+    return MG_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return MG_ERR_CUDA;
+  }
+  if (!g_noalloc_ptr[dev]) {  // first call on this device: resolve the array's device address
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+      return MG_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  double *r = g_noalloc_ptr[dev];
+  double *partial = r + kNoAllocMaxLen;
+  double *sums = partial + kNoAllocPartials;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const LevelView<double> &L = h->lv[0].d.view;
+  // r = b - A x (every entry written)
+  if (L.layout == MG_LAYOUT_DENSE) {
+    k_apply_dense<double><<<grid_for(L.n, 128, 1 << 30), 128, 0, s>>>(L, x, b, r);
+  } else {
+    const int blocks = (L.n + 3) / 4;
+    switch (h->C) {
+      case 1: k_apply_tri<double, 1><<<blocks, 128, 0, s>>>(L, x, b, r); break;
+      case 2: k_apply_tri<double, 2><<<blocks, 128, 0, s>>>(L, x, b, r); break;
+      case 4: k_apply_tri<double, 4><<<blocks, 128, 0, s>>>(L, x, b, r); break;
+      case 8: k_apply_tri<double, 8><<<blocks, 128, 0, s>>>(L, x, b, r); break;
+      default: k_apply_tri<double, 16><<<blocks, 128, 0, s>>>(L, x, b, r); break;
+    }
+  }
+  // ||r||^2 and ||b||^2 with the library's fixed-order reductions (each CTA
+  // overwrites its partial slot; nothing carries over between calls)
+  const int G = (int)std::max<long long>(1, std::min<long long>(304, (len + kDotThreads - 1) / kDotThreads));
+  k_multidot_partial<<<dim3(G, 1), kDotThreads, 0, s>>>(r, len, r, len, partial);
+  k_reduce_partials<<<1, 128, 0, s>>>(partial, G, 1, sums, 0);
+  k_multidot_partial<<<dim3(G, 1), kDotThreads, 0, s>>>(b, len, b, len, partial + 304);
+  k_reduce_partials<<<1, 128, 0, s>>>(partial + 304, G, 1, sums + 1, 0);
+  k_noalloc_finish<<<1, 1, 0, s>>>(sums, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}

@@ -33,7 +33,7 @@ MG_PRECISION_FP32 = 1
 
 #: every symbol include/pintmg.h declares
 EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "mg_vector_length",
-            "mg_launch_count", "mg_profile_enable", "mg_profile_read",
+            "mg_launch_count", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
             "mg_destroy", "mg_status_string", "mg_last_cuda_error")
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -91,6 +91,9 @@ def lib():
         L.mg_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         L.mg_profile_read.restype = ctypes.c_int
+        L.mg_true_residual_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]
+        L.mg_true_residual_noalloc.restype = ctypes.c_int
         L.mg_destroy.argtypes = [ctypes.c_void_p]
         L.mg_destroy.restype = None
         L.mg_status_string.argtypes = [ctypes.c_int]
@@ -181,6 +184,12 @@ def mg_profile_read(h) -> dict:
     if n < 0:
         raise PintmgError(n, "mg_profile_read")
     return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(n, k))}
+
+
+def mg_true_residual_noalloc(h, b_ptr: int, x_ptr: int, out_ptr: int, stream: int = 0) -> int:
+    """||b - A x|| and ||b - A x|| / ||b|| into out_ptr[0:2] (device), allocating nothing."""
+    return lib().mg_true_residual_noalloc(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
+                                          ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
 
 
 def mg_destroy(h) -> None:

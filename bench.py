@@ -46,9 +46,12 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="burgers_nx128_n1024", choices=sorted(W.WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--restart", type=int, default=200)
+    ap.add_argument("--restart", type=int, default=400)
+    ap.add_argument("--omega", type=float, default=1.0,
+                    help="block-Jacobi relaxation weight; 1 is the paper's sweep (Eq. jacobi-aj)")
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision / relaxed-sweep variants")
     ap.add_argument("--allow-partial", action="store_true",
                     help="accept solves stopped by --maxit (bounded profiler captures only)")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
@@ -124,27 +127,119 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 FMA rate of this GB300 (measured: 1.196 TFLOP/s = 0.598 T FMA/s with
-# every SM sub-partition busy); the ALU peak for the FP64 kernels.
+# FP64 peak of this GB300 for the ALU-bound kernels: 152 SMs x 4 sub-partitions
+# x 0.5 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.259 TFLOP/s nominal; a
+# throughput probe (independent FMA chains, 4+ warps per SM) measured
+# 1.196 TFLOP/s, which is the peak used here.
 FP64_TFLOPS_MEASURED = 1.196
+FP32_TFLOPS_MEASURED = 74.2
 
 
-def algorithmic_cost(category: str, wl: dict, prob, precision: str):
-    """Algorithmic bytes and FP64 flops of ONE launch of a kernel category at the fine level.
+def roofline(prof, dominant, precision):
+    """Roofline object of the dominant kernel category from the library's
+    event timings and its algorithmic byte / flop models (per launch)."""
+    hbm, peak_kind = measured_peaks()
+    ms, n, nbytes, nflops = prof.get(dominant, (0.0, 0, 0.0, 0.0))
+    if not n or ms <= 0:
+        return {"bound": None, "kernel": dominant, "note": "no timed launches"}
+    t = ms / 1e3
+    bw = nbytes / t / 1e9
+    fl = nflops / t / 1e12
+    alu_peak = FP64_TFLOPS_MEASURED if precision == "fp64" else FP32_TFLOPS_MEASURED
+    t_hbm = nbytes / (hbm * 1e9)
+    t_alu = nflops / (alu_peak * 1e12)
+    common = {"kernel": dominant, "launches": n, "avg_launch_us": round(ms * 1e3 / n, 3),
+              "bytes_per_launch": round(nbytes / n), "flops_per_launch": round(nflops / n),
+              "traffic": None}
+    if t_alu > t_hbm:
+        return {"bound": "alu", "achieved": round(fl, 4), "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": round(fl / alu_peak, 4), "achieved_gbs": round(bw, 1), "hbm_peak_gbs": hbm,
+                "peak_source": "measured FP64 FMA probe (1.196 of 1.259 nominal TFLOP/s)" if precision == "fp64"
+                else "measured FP32 FMA probe", **common}
+    return {"bound": "hbm", "achieved": round(bw, 1), "peak": hbm, "unit": "GB/s", "frac": round(bw / hbm, 4),
+            "achieved_tflops": round(fl, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", **common}
 
-    block_solve (one block-Jacobi sweep, tridiagonal): per time block it reads
-    the right-hand side (4p+q), the two coupling vectors (2p), the N, V, Z bands
-    (9p) and the LDL^T factor (3p), and writes the block (4p+q); flops: 3
-    tridiagonal products (18p), the pentadiagonal solve (2 x 4p + p) and three
-    transposed products (18p) = 45p per block.
-    """
-    p, q, n = prob.p, prob.q, prob.n
-    wsz = 8 if precision == "fp64" else 4
-    if category == "block_solve":
-        bytes_per_block = wsz * ((4 * p + q) * 2 + 2 * p + 9 * p + 3 * p)
-        flops_per_block = 45 * p
-        return bytes_per_block * (n + 1), flops_per_block * (n + 1)
-    return None, None
+
+def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stream, world, want_e2e):
+    """Set up, warm up, one fully profiled solve, then `steps` timed solves."""
+    prec = P.MG_PRECISION_FP64 if precision == "fp64" else P.MG_PRECISION_FP32
+    t0 = time.perf_counter()
+    h = P.mg_setup(prob, levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=prec,
+                   omega=omega, stream=stream)
+    torch.cuda.synchronize(dev)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    n = prob.size
+    b = torch.tensor(prob.b, device=dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def solve(bp, xp):
+        code, info = P.fgmres_solve(h, bp, xp, RTOL, args.maxit, args.restart, stream)
+        if code != P.MG_OK and not (args.allow_partial and code == P.MG_NOT_CONVERGED):
+            raise RuntimeError(f"fgmres_solve: {P.mg_status_string(code)} (iters {info.iters}, "
+                               f"relres {info.relres:.2e}, true {info.true_relres:.2e})")
+        return info
+
+    try:
+        for _ in range(warmup):
+            flush.zero_()
+            solve(b.data_ptr(), x.data_ptr())
+        # one fully profiled solve: per-category kernel shares
+        P.mg_profile_enable(h, P.PROFILE_ALL)
+        flush.zero_()
+        solve(b.data_ptr(), x.data_ptr())
+        shares = P.mg_profile_read(h)
+        P.mg_profile_enable(h, 0)
+        dominant = max(shares, key=lambda k: shares[k][0])
+        # timed region: inputs resident in HBM, L2 flushed before each step,
+        # only the dominant category bracketed by events on the library's stream
+        P.mg_profile_enable(h, 1 << P.PROFILE_CATEGORIES.index(dominant))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        launches0 = P.mg_launch_count(h)
+        infos = []
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record()
+                infos.append(solve(b.data_ptr(), x.data_ptr()))
+                ev[i][1].record()
+            torch.cuda.synchronize(dev)
+        launches = P.mg_launch_count(h) - launches0
+        prof = P.mg_profile_read(h)
+        P.mg_profile_enable(h, 0)
+        if world > 1:
+            torch.distributed.barrier()
+        total_ms = sum(a.elapsed_time(bb) for a, bb in ev)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        out = {"value": world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+               "iters": [i.iters for i in infos], "true_relres": max(i.true_relres for i in infos),
+               "coarse_iters_per_vcycle": sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)),
+               "setup_ms": setup_ms, "launches": launches, "shares": shares, "dominant": dominant,
+               "roofline": roofline(prof, dominant, precision), "clocks": clk.summary()}
+        if want_e2e:
+            # end to end through the public API with pinned host buffers
+            bh = torch.tensor(prob.b).pin_memory()
+            xh = torch.empty_like(bh).pin_memory()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                solve(bh.data_ptr(), xh.data_ptr())
+            e2e_s = time.perf_counter() - t0
+            if world > 1:
+                t = torch.tensor([e2e_s], device=dev)
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                e2e_s = float(t.item())
+            out["e2e"] = {"value": round(world * steps / e2e_s, 4), "unit": UNIT,
+                          "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+        return out
+    finally:
+        P.mg_destroy(h)
 
 
 def run_native(args):
@@ -161,155 +256,79 @@ def run_native(args):
     stream = torch.cuda.current_stream(dev).cuda_stream
     wl = W.WORKLOADS[args.workload]
     prob = wl["make"](seed=2000 + 17 * rank) if rank else wl["make"]()
-    precision = P.MG_PRECISION_FP64 if args.precision == "fp64" else P.MG_PRECISION_FP32
-    t0 = time.perf_counter()
-    h = P.mg_setup(prob, levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=precision,
-                   stream=stream)
-    torch.cuda.synchronize(dev)
-    setup_ms = (time.perf_counter() - t0) * 1e3
-    n = prob.size
-    b = torch.tensor(prob.b, device=dev)
-    x = torch.empty_like(b)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def solve():
-        code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
-        if code != P.MG_OK and not (args.allow_partial and code == P.MG_NOT_CONVERGED):
-            raise RuntimeError(f"fgmres_solve: {P.mg_status_string(code)} (iters {info.iters}, "
-                               f"relres {info.relres:.2e}, true {info.true_relres:.2e})")
-        return info
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        solve()
-    # one fully profiled solve: per-category kernel time shares
-    P.mg_profile_enable(h, P.PROFILE_ALL)
-    flush.zero_()
-    solve()
-    shares = P.mg_profile_read(h)
-    P.mg_profile_enable(h, 0)
-    dominant = max(shares, key=lambda k: shares[k][0])
-
-    # timed region: device-resident inputs, L2 flushed before every step,
-    # the dominant kernel category bracketed by CUDA events on the library's stream
-    P.mg_profile_enable(h, 1 << P.PROFILE_CATEGORIES.index(dominant))
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    launches0 = P.mg_launch_count(h)
-    infos = []
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record()
-            infos.append(solve())
-            ev[i][1].record()
-        torch.cuda.synchronize(dev)
-    launches = P.mg_launch_count(h) - launches0
-    prof = P.mg_profile_read(h)
-    P.mg_profile_enable(h, 0)
-    if world > 1:
-        torch.distributed.barrier()
-    step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
-
-    # end to end through the public API with pinned host buffers
-    bh = torch.tensor(prob.b).pin_memory()
-    xh = torch.empty_like(bh).pin_memory()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        code, info = P.fgmres_solve(h, bh.data_ptr(), xh.data_ptr(), RTOL, args.maxit, args.restart, stream)
-        if code != P.MG_OK and not (args.allow_partial and code == P.MG_NOT_CONVERGED):
-            raise RuntimeError("e2e solve failed")
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * args.steps / e2e_s
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = world * args.steps / float(t.item())
-
-    # roofline of the dominant kernel
-    hbm, peak_kind = measured_peaks()
-    cat_ms, cat_n = prof.get(dominant, (0.0, 0))
-    roof = None
-    if cat_n:
-        per_launch_s = cat_ms / cat_n / 1e3
-        bytes_l, flops_l = algorithmic_cost(dominant, wl, prob, args.precision)
-        if bytes_l is not None:
-            bw = bytes_l / per_launch_s / 1e9
-            fl = flops_l / per_launch_s / 1e12
-            # FP64 arithmetic on this part is slower than its HBM: report the binding roof
-            t_hbm = bytes_l / (hbm * 1e9)
-            t_alu = flops_l / (FP64_TFLOPS_MEASURED * 1e12) if args.precision == "fp64" else 0.0
-            if t_alu > t_hbm:
-                roof = {"bound": "alu", "achieved": round(fl, 4), "peak": FP64_TFLOPS_MEASURED,
-                        "unit": "TFLOP/s", "frac": round(fl / FP64_TFLOPS_MEASURED, 4), "traffic": None,
-                        "kernel": dominant, "alu_peak_source": "measured FP64 FMA probe",
-                        "achieved_gbs": round(bw, 1), "hbm_peak_gbs": hbm}
-            else:
-                roof = {"bound": "hbm", "achieved": round(bw, 1), "peak": hbm, "unit": "GB/s",
-                        "frac": round(bw / hbm, 4), "traffic": None, "kernel": dominant,
-                        "peak_source": peak_kind}
-        else:
-            roof = {"bound": None, "kernel": dominant, "note": "no algorithmic model for this category"}
-        roof["avg_launch_us"] = round(per_launch_s * 1e6, 3)
-        roof["launches_in_timed_region"] = cat_n
-
-    iters = [i.iters for i in infos]
+    main = measure(P, torch, prob, wl, args, args.precision, args.omega, args.steps, args.warmup, dev, stream,
+                   world, True)
+    variants = {}
+    if not args.no_variants:
+        for name, prec, om in (("fp32_vcycle", "fp32", args.omega), ("omega0.7_fp64", "fp64", 0.7),
+                               ("omega0.7_fp32_vcycle", "fp32", 0.7)):
+            if prec == args.precision and om == args.omega:
+                continue
+            v = measure(P, torch, prob, wl, args, prec, om, max(1, min(args.steps, 3)), 1, dev, stream, world, False)
+            variants[name] = {"value": round(v["value"], 4), "unit": UNIT, "ms_per_step": round(v["ms_per_step"], 3),
+                              "fgmres_iters": v["iters"][0], "true_relres": v["true_relres"],
+                              "precision": prec, "omega": om,
+                              "dominant_kernel": v["dominant"], "roofline_frac": v["roofline"].get("frac")}
     out = {
-        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "metric": METRIC, "value": round(main["value"], 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(main["ms_per_step"], 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded iterate and N(0,1) right-hand side)",
         "config": {"workload": args.workload, "n": prob.n, "p": prob.p, "q": prob.q,
                    "levels": wl["levels"], "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
-                   "unknowns": n, "rtol": RTOL, "restart": args.restart, "precision": args.precision,
-                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
-        "fgmres_iters": iters, "true_relres": max(i.true_relres for i in infos),
-        "coarse_iters_per_vcycle": round(sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)), 3),
-        "setup_ms": round(setup_ms, 2),
-        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
-        "gpu_launches": launches,
-        "roofline": roof,
-        "kernel_shares": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in shares.items() if v[1]},
-        "clocks": clk.summary(),
+                   "unknowns": prob.size, "rtol": RTOL, "restart": args.restart, "precision": args.precision,
+                   "omega": args.omega, "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"replicas{world}"},
+        "fgmres_iters": main["iters"], "true_relres": main["true_relres"],
+        "coarse_iters_per_vcycle": round(main["coarse_iters_per_vcycle"], 3),
+        "setup_ms": round(main["setup_ms"], 2),
+        "e2e": main["e2e"],
+        "gpu_launches": main["launches"],
+        "roofline": main["roofline"],
+        "kernel_shares": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in main["shares"].items() if v[1]},
+        "variants": variants,
+        "clocks": main["clocks"],
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(prob, wl, iters, args.cpu_sample_seconds)
-    P.mg_destroy(h)
+        out["cpu_baseline"] = cpu_baseline(prob, wl, args, main["iters"])
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(prob, wl, gpu_iters, seconds):
-    """The oracle as it stands, on a bounded sample: FGMRES iterations of the
-    same system until `seconds` elapse; solves/s = 1 / (time per iteration x the
-    GPU solve's iteration count).  Oracle setup (sparse LU) is excluded, like
-    the GPU's mg_setup."""
+def oracle_iterations(workload, omega, restart):
+    """The oracle's own FGMRES iteration count for a full solve of this
+    workload (tests/golden/oracle_iterations.json, written by
+    oracle/measure_iterations.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(f"{workload}/omega={float(omega)}")
+    if rec and rec.get("restart") == restart and rec.get("rtol") == RTOL:
+        return rec["iters"]
+    return None
+
+
+def oracle_sample(prob, wl, omega, seconds):
+    """Time the oracle as it stands: its FGMRES on this system for about
+    `seconds` (setup, i.e. the sparse LU factorisations, excluded).  Returns
+    (seconds per FGMRES iteration, iterations run)."""
     from oracle import augmented as O
-    hier = O.Hierarchy(prob, O.MGOptions(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"]))
+    hier = O.Hierarchy(prob, O.MGOptions(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"],
+                                         omega=omega))
     lev = hier.fine
     bt = lev.to_time_major(prob.b)
-    # warm the factorisations once (setup), then time iterations
-    hier.vcycle(0, bt)
+    hier.vcycle(0, bt)  # builds the factorisations
     count = [0]
     t0 = time.perf_counter()
+
+    class Stop(Exception):
+        pass
 
     def prec(v):
         count[0] += 1
         return hier.vcycle(0, v)
-
-    class Stop(Exception):
-        pass
 
     def apply_A(v):
         if time.perf_counter() - t0 > seconds:
@@ -317,67 +336,49 @@ def cpu_baseline(prob, wl, gpu_iters, seconds):
         return lev.At @ v
 
     try:
-        O.fgmres(apply_A, prec, bt, rtol=RTOL, maxit=100000, restart=200)
+        O.fgmres(apply_A, prec, bt, rtol=RTOL, maxit=100000, restart=400)
     except Stop:
         pass
     el = time.perf_counter() - t0
-    per_iter = el / max(1, count[0])
-    iters = statistics.mean(gpu_iters)
-    return {"value": round(1.0 / (per_iter * iters), 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{count[0]} oracle FGMRES iterations in {el:.1f} s on this system; "
-                      f"scaled by the GPU solve's {iters:.1f} iterations per solve"}
+    return el / max(1, count[0]), count[0]
+
+
+def cpu_baseline(prob, wl, args, gpu_iters):
+    per_iter, k = oracle_sample(prob, wl, args.omega, args.cpu_sample_seconds)
+    n_or = oracle_iterations(args.workload, args.omega, args.restart)
+    n_it = n_or if n_or is not None else statistics.mean(gpu_iters)
+    src = "the oracle's own full-solve count" if n_or is not None else "the GPU solve's count"
+    return {"value": round(1.0 / (per_iter * n_it), 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{k} oracle FGMRES iterations ({per_iter * 1e3:.0f} ms each, first iterations of the "
+                      f"solve, SuperLU factorisations excluded) scaled by {n_it:.0f} iterations per solve "
+                      f"({src}); scipy/SuperLU, host cores of the GPU box"}
 
 
 def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, a bounded sample per step."""
     rank, world, local = dist_env()
     if rank != 0:
         return
     wl = W.WORKLOADS[args.workload]
     prob = wl["make"]()
-    from oracle import augmented as O
-    hier = O.Hierarchy(prob, O.MGOptions(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"]))
-    hier.vcycle(0, hier.fine.to_time_major(prob.b))
-    # a step: a bounded sample of the solve (the oracle's FGMRES for a fixed
-    # number of iterations), scaled to solves/s by the iteration count the
-    # oracle needs for a full solve at this size (measured once below on the
-    # same sample budget)
-    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
-    lev = hier.fine
-    bt = lev.to_time_major(prob.b)
-    times, its = [], []
+    per_step = max(5.0, min(30.0, 150.0 / max(1, args.steps + args.warmup)))
+    times = []
     for k in range(args.warmup + args.steps):
-        cnt = [0]
-        t0 = time.perf_counter()
-
-        def prec(v):
-            cnt[0] += 1
-            return hier.vcycle(0, v)
-
-        class Stop(Exception):
-            pass
-
-        def apply_A(v):
-            if time.perf_counter() - t0 > per_step:
-                raise Stop()
-            return lev.At @ v
-
-        try:
-            O.fgmres(apply_A, prec, bt, rtol=RTOL, maxit=100000, restart=200)
-        except Stop:
-            pass
+        per_iter, cnt = oracle_sample(prob, wl, args.omega, per_step)
         if k >= args.warmup:
-            times.append(time.perf_counter() - t0)
-            its.append(cnt[0])
-    per_iter = sum(times) / max(1, sum(its))
-    est_iters = float(os.environ.get("PINTMG_REF_ITERS", "0")) or None
-    value = None if est_iters is None else 1.0 / (per_iter * est_iters)
+            times.append(per_iter)
+    per_iter = statistics.mean(times)
+    n_or = oracle_iterations(args.workload, args.omega, args.restart)
+    value = None if n_or is None else round(1.0 / (per_iter * n_or), 6)
     line = {"metric": METRIC, "impl": "reference", "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_iter * (n_or or 0) * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload},
-            "oracle_ms_per_fgmres_iteration": round(per_iter * 1e3, 2),
-            "cpu_baseline": {"value": value, "kind": "oracle", "cores": os.cpu_count(),
-                             "sample": f"{sum(its)} oracle FGMRES iterations over {len(times)} steps"},
+            "data": "synthetic (seeded iterate and N(0,1) right-hand side)",
+            "config": {"workload": args.workload, "restart": args.restart, "omega": args.omega, "rtol": RTOL},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(),
+                             "sample": f"per step about {per_step:.0f} s of oracle FGMRES iterations "
+                                       f"({per_iter * 1e3:.0f} ms each) scaled by the oracle's {n_or} "
+                                       f"iterations per full solve"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

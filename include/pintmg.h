@@ -91,6 +91,7 @@ typedef struct {
   int coarse_fixed_iters; /* > 0: run exactly this many coarse GMRES iterations, ignoring coarse_rtol */
   int end_rule;           /* last fine point of linear interpolation: 0 repeats the last coarse value, 1 uses 0 */
   int precision;          /* mg_precision */
+  double omega;           /* block-Jacobi relaxation weight, 0 < omega <= 1; the paper's sweep (Eq. jacobi-aj) is omega = 1 */
 } mg_options;
 
 typedef struct {
@@ -103,7 +104,7 @@ typedef struct {
 
 typedef struct mg_handle mg_handle;  /* opaque; owns every device buffer */
 
-/* Fill *opts with the defaults: levels 2, 1/1 sweeps, coarse 1e-3 / 50, tolerance mode, end rule 0, FP64. */
+/* Fill *opts with the defaults: levels 2, 1/1 sweeps, coarse 1e-3 / 50, tolerance mode, end rule 0, FP64, omega 1. */
 void mg_default_options(mg_options *opts);
 
 /*
@@ -148,12 +149,16 @@ long long mg_vector_length(const mg_handle *h);
  * mg_profile_read; 0 turns timing off) with a pair of CUDA events on its
  * stream, and resets the per-category sums;
  * mg_profile_read synchronises those events and fills up to `max` entries of
- * names (static strings), ms (summed kernel time) and launches (count) per
- * kernel category; it returns the number of categories or a negative status.
+ * names (static strings), ms (summed kernel time), launches (count), bytes and
+ * flops (the algorithmic memory traffic and floating-point operations of the
+ * timed launches, from the per-kernel models documented in the design notes)
+ * per kernel category; any output pointer may be NULL.  It returns the number
+ * of categories or a negative status.
  */
 long long mg_launch_count(const mg_handle *h);
 int mg_profile_enable(mg_handle *h, int mask);
-int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches);
+int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches, double *bytes,
+                    double *flops);
 
 /*
  * True residual without allocating (the paper has no counterpart).  For

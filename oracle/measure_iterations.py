@@ -1,0 +1,42 @@
+"""Run the oracle's own FGMRES to convergence on the benchmark workloads and
+record its iteration counts (tests/golden/oracle_iterations.json).
+
+Calls only oracle/ and the input generator.  Slow (the C2 solve takes about
+an hour on 8 CPU cores); the CPU-reference arm of bench.py scales its bounded
+per-iteration timing by these counts.
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from oracle import augmented as O  # noqa: E402
+from paper_2405_04808_gb300 import workloads as W  # noqa: E402
+
+OUT = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+
+
+def measure(name, rtol=1e-8, restart=400, maxit=2000, omega=1.0):
+    wl = W.WORKLOADS[name]
+    prob = wl["make"]()
+    h = O.Hierarchy(prob, O.MGOptions(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega))
+    t0 = time.time()
+    x, res, true_rel = h.solve(prob.b, rtol=rtol, maxit=maxit, restart=restart)
+    return {"workload": name, "rtol": rtol, "restart": restart, "maxit": maxit, "omega": omega,
+            "iters": res.iters, "relres": res.relres, "true_relres": true_rel, "seconds": round(time.time() - t0, 1)}
+
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or ["vdp_n256", "burgers_nx128_n1024"]
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for nm in names:
+        for omega in (1.0, 0.7):
+            key = f"{nm}/omega={omega}"
+            data[key] = measure(nm, omega=omega)
+            print(key, data[key], flush=True)
+            with open(OUT, "w") as fh:
+                json.dump(data, fh, indent=1, sort_keys=True)

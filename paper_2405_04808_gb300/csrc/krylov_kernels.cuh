@@ -24,10 +24,12 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // partial[i * G + blockIdx.x] = sum over this CTA's slice of V_i . w,
-// V_i = V + i * ldv, i = blockIdx.y.
+// V_i = V + i * ldv, i = blockIdx.y.  gate (optional device flag): 0 skips
+// the work (the reorthogonalisation pass that the DGKS test did not ask for).
 __global__ void __launch_bounds__(kDotThreads) k_multidot_partial(const double *__restrict__ V, long long ldv,
                                                                   const double *__restrict__ w, long long len,
-                                                                  double *partial) {
+                                                                  double *partial, const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
   const int i = blockIdx.y;
   const double *vi = V + i * ldv;
   double acc = 0.0;
@@ -39,7 +41,9 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_partial(const double *
 }
 
 // out[i] (+)= sum_g partial[i * G + g], fixed order.  One warp per i.
-__global__ void k_reduce_partials(const double *__restrict__ partial, int G, int m, double *out, int accumulate) {
+__global__ void k_reduce_partials(const double *__restrict__ partial, int G, int m, double *out, int accumulate,
+                                  const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
   const int i = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const int ln = threadIdx.x & (kWarp - 1);
   if (i >= m) return;
@@ -52,7 +56,8 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int
 
 // y[idx] += sign * sum_{i < m} c[i] X_i[idx],  X_i = X + i * ldx
 __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long ldx, const double *__restrict__ c,
-                             int m, double sign, long long len) {
+                             int m, double sign, long long len, const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
        idx += (long long)gridDim.x * blockDim.x) {
     double acc = 0.0;
@@ -62,9 +67,17 @@ __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long 
 }
 
 // y[i] += x[i], i < m
-__global__ void k_add_inplace(double *y, const double *__restrict__ x, int m) {
+__global__ void k_add_inplace(double *y, const double *__restrict__ x, int m, const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) y[i] += x[i];
+}
+
+// DGKS test (Daniel, Gragg, Kaufman, Stewart 1976): a second Gram-Schmidt
+// pass is needed when the projection removed more than half of |w|^2,
+// i.e. |w_after|^2 < |w_before|^2 / 2.  gate[0] = 1 asks for it.
+__global__ void k_dgks_gate(const double *before2, const double *after2, int *gate) {
+  gate[0] = (after2[0] < 0.5 * before2[0]) ? 1 : 0;
 }
 
 // y = x * s[0]
@@ -120,13 +133,19 @@ __global__ void k_arnoldi_init(const double *beta_scal, double *g, int m) {
   for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta_scal[0] : 0.0;
 }
 
-// y = R^-1 g for the leading k x k upper triangle of the rotated H
+// y = R^-1 g for the leading k x k upper triangle of the rotated H, one CTA,
+// column-oriented: y_i = g_i / R_ii, then every g_r (r < i) -= R_ri y_i in parallel.
 __global__ void k_backsolve(int k, const double *__restrict__ H, int ldh, const double *__restrict__ g, double *y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  extern __shared__ double gs[];
+  for (int r = threadIdx.x; r < k; r += blockDim.x) gs[r] = g[r];
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int c = i + 1; c < k; ++c) s -= H[(long long)c * ldh + i] * y[c];
-    y[i] = s / H[(long long)i * ldh + i];
+    const double yi = gs[i] / H[(long long)i * ldh + i];
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = yi;
+    const double *col = H + (long long)i * ldh;
+    for (int r = threadIdx.x; r < i; r += blockDim.x) gs[r] = fma(-col[r], yi, gs[r]);
+    __syncthreads();
   }
 }
 

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -67,6 +68,10 @@ template <typename T>
 struct LevelData {
   LevelView<T> view{};
   T *Cu = nullptr, *Em = nullptr;  // coarsest level only
+  // coarsest level: prefix products of the SGS chains for the parallel scan
+  // (empty when the budget below is exceeded; the cluster chain is used then)
+  std::vector<T *> scanF, scanB;
+  T *scan_tmp = nullptr;
   T *b = nullptr, *y = nullptr, *tmp = nullptr;
   T *chainU = nullptr, *chainM = nullptr, *sgs_w = nullptr;
 };
@@ -109,6 +114,7 @@ struct mg_handle {
   // counters of the last solve
   int vcycles = 0, coarse_iters = 0;
   int use_cluster = 1;  // SGS chains on a thread-block cluster (tridiagonal layout)
+  int use_scan = 1;     // SGS chains as a parallel scan with precomputed prefix products
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -116,6 +122,7 @@ struct mg_handle {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double prof_ms[16] = {};
   long long prof_count[16] = {};
+  double work_bytes[16] = {}, work_flops[16] = {};  // algorithmic work of the timed launches
 };
 
 namespace {
@@ -143,9 +150,12 @@ struct Bracket {
   int cat;
   cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
-  Bracket(mg_handle *h_, int cat_, cudaStream_t s_) : h(h_), cat(cat_), s(s_) {
+  Bracket(mg_handle *h_, int cat_, cudaStream_t s_, double bytes = 0.0, double flops = 0.0)
+      : h(h_), cat(cat_), s(s_) {
     h->launches++;
     if ((h->prof >> cat) & 1) {
+      h->work_bytes[cat] += bytes;
+      h->work_flops[cat] += flops;
       a = take_event(h);
       b = take_event(h);
       ck(cudaEventRecord(a, s));
@@ -177,18 +187,24 @@ void harvest(mg_handle *h) {
 
 template <typename T>
 void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T *cplU, const T *cplM,
-                        T *out, cudaStream_t s) {
-  Bracket br(h, CAT_BLOCK_SOLVE, s);
+                        T *out, cudaStream_t s, const T *yold = nullptr, T omega = T(1)) {
+  // per block: read r (4p+q), couplings (2p), N, V, Z (9p tridiagonal / 2p^2+pq dense), factor
+  // (3p / p^2), old iterate if relaxed (4p+q); write 4p+q.  Flops: 45p (tridiagonal).
+  const double w = 4.0 * L.p + L.q, p_ = L.p;
+  const double coef = L.layout == MG_LAYOUT_TRIDIAG ? 12.0 * p_ : 3.0 * p_ * p_ + p_ * L.q;
+  const double per_block = sizeof(T) * (2.0 * w + 2.0 * p_ + coef + (omega != T(1) && yold ? w : 0.0));
+  const double fl = L.layout == MG_LAYOUT_TRIDIAG ? 45.0 * p_ : 2.0 * (3.0 * p_ * p_ + 2.0 * p_ * L.q + p_ * p_);
+  Bracket br(h, CAT_BLOCK_SOLVE, s, per_block * (L.n + 1), fl * (L.n + 1));
   if (L.layout == MG_LAYOUT_DENSE) {
-    k_block_solve_dense<T><<<grid_for(L.n + 1, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out);
+    k_block_solve_dense<T><<<grid_for(L.n + 1, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega);
   } else {
     const int blocks = (int)((L.n + 1 + 3) / 4);
     switch (h->C) {
-      case 1: k_block_solve_tri<T, 1><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
-      case 2: k_block_solve_tri<T, 2><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
-      case 4: k_block_solve_tri<T, 4><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
-      case 8: k_block_solve_tri<T, 8><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
-      default: k_block_solve_tri<T, 16><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out); break;
+      case 1: k_block_solve_tri<T, 1><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 2: k_block_solve_tri<T, 2><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 4: k_block_solve_tri<T, 4><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 8: k_block_solve_tri<T, 8><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      default: k_block_solve_tri<T, 16><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
     }
   }
   ck_launch();
@@ -196,7 +212,10 @@ void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T
 
 template <typename T>
 void launch_apply(mg_handle *h, const LevelView<T> &L, const T *x, const T *b, T *out, cudaStream_t s) {
-  Bracket br(h, CAT_APPLY, s);
+  const double w = 4.0 * L.p + L.q;
+  const double coef = L.layout == MG_LAYOUT_TRIDIAG ? 9.0 * L.p : 2.0 * L.p * L.p + L.p * L.q;
+  Bracket br(h, CAT_APPLY, s, sizeof(T) * (L.n * ((b ? 3.0 : 2.0) * w + coef)),
+             L.layout == MG_LAYOUT_TRIDIAG ? 2.0 * 18.0 * L.p * L.n : 4.0 * L.n * (2.0 * L.p * L.p + L.p * L.q));
   if (L.layout == MG_LAYOUT_DENSE) {
     k_apply_dense<T><<<grid_for(L.n, 128, 1 << 30), 128, 0, s>>>(L, x, b, out);
   } else {
@@ -215,7 +234,8 @@ void launch_apply(mg_handle *h, const LevelView<T> &L, const T *x, const T *b, T
 template <typename T>
 void launch_residual_restrict(mg_handle *h, const LevelView<T> &L, const T *y, const T *b, T *rc,
                               cudaStream_t s) {
-  Bracket br(h, CAT_RESTRICT, s);
+  const double w = 4.0 * L.p + L.q;
+  Bracket br(h, CAT_RESTRICT, s, sizeof(T) * (L.n / 2) * (2.0 * (w + L.q) + w + 12.0 * L.p), 0.0);
   const int nc = L.n / 2;
   if (L.layout == MG_LAYOUT_DENSE) {
     k_residual_restrict_dense<T><<<grid_for(nc, 128, 1 << 30), 128, 0, s>>>(L, y, b, rc);
@@ -243,25 +263,26 @@ LevelData<float> &ldata<float>(Level &L) { return L.f; }
 // Dot products (FP64), fixed reduction order
 
 void multidot(mg_handle *h, const double *V, long long ldv, int m, const double *w, long long len, double *out,
-              int accumulate, cudaStream_t s) {
+              int accumulate, cudaStream_t s, const int *gate = nullptr) {
   const int G = (int)std::max<long long>(1, std::min<long long>(h->G, (len + kDotThreads - 1) / kDotThreads));
   dim3 grid(G, m);
   {
-    Bracket br(h, CAT_DOT, s);
-    k_multidot_partial<<<grid, kDotThreads, 0, s>>>(V, ldv, w, len, h->partial);
+    // algorithmic: read the m vectors and w once, 2 m len flops
+    Bracket br(h, CAT_DOT, s, 8.0 * (m + (V == w ? 0 : 1)) * len, 2.0 * m * len);
+    k_multidot_partial<<<grid, kDotThreads, 0, s>>>(V, ldv, w, len, h->partial, gate);
     ck_launch();
   }
   {
     Bracket br(h, CAT_SMALL, s);
-    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, G, m, out, accumulate);
+    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, G, m, out, accumulate, gate);
     ck_launch();
   }
 }
 
 void multi_axpy(mg_handle *h, double *y, const double *X, long long ldx, const double *c, int m, double sign,
-                long long len, cudaStream_t s) {
-  Bracket br(h, CAT_AXPY, s);
-  k_multi_axpy<<<grid_for(len, 256), 256, 0, s>>>(y, X, ldx, c, m, sign, len);
+                long long len, cudaStream_t s, const int *gate = nullptr) {
+  Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * m * len);
+  k_multi_axpy<<<grid_for(len, 256), 256, 0, s>>>(y, X, ldx, c, m, sign, len, gate);
   ck_launch();
 }
 
@@ -270,21 +291,30 @@ void read_scal(mg_handle *h, const mg_handle::Krylov &K, cudaStream_t s) {
   ck(cudaStreamSynchronize(s));
 }
 
-// CGS2 orthogonalisation of w against V_0..V_j, ||w||^2 into nrm2, h (j+1)
+// Classical Gram-Schmidt of w against V_0..V_j with the DGKS criterion: a
+// second pass runs (device-gated, no host round trip) only when the first
+// removed more than half of |w|^2.  h (j+1) and |w|^2 (nrm2) on the device.
 void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
                    cudaStream_t s) {
   const int m = j + 1;
+  multidot(h, w, len, 1, w, len, K.nrm2 + 1, 0, s);           // |w|^2 before
   multidot(h, V, len, m, w, len, K.h, 0, s);
   multi_axpy(h, w, V, len, K.h, m, -1.0, len, s);
-  // second pass: accumulate the correction into h
-  multidot(h, V, len, m, w, len, K.h + 512, 0, s);
-  multi_axpy(h, w, V, len, K.h + 512, m, -1.0, len, s);
+  multidot(h, w, len, 1, w, len, K.nrm2, 0, s);               // |w|^2 after
   {
     Bracket br(h, CAT_SMALL, s);
-    k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m);
+    k_dgks_gate<<<1, 1, 0, s>>>(K.nrm2 + 1, K.nrm2, h->flag + 2);
     ck_launch();
   }
-  multidot(h, w, len, 1, w, len, K.nrm2, 0, s);
+  const int *gate = h->flag + 2;
+  multidot(h, V, len, m, w, len, K.h + 512, 0, s, gate);
+  multi_axpy(h, w, V, len, K.h + 512, m, -1.0, len, s, gate);
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m, gate);
+    ck_launch();
+  }
+  multidot(h, w, len, 1, w, len, K.nrm2, 0, s, gate);         // |w|^2 after the second pass
 }
 
 // ||x|| into K.scal[0], 1/||x|| into K.scal[1]
@@ -344,32 +374,79 @@ void convert_back<float>(mg_handle *h, const float *x, double *y, long long len,
 
 // One SGS chain on a thread-block cluster (tridiagonal layout, p >= 32).
 // Returns false if the device refuses the cluster launch.
+template <typename T, bool kForward, int K>
+cudaError_t launch_chain_cluster_k(int S, const T *G, const T *xhat, T *xout, int n, int p, cudaStream_t s) {
+  const int tpr = 16;
+  const int rows = (p + S - 1) / S;
+  const int threads = ((rows * tpr + 31) / 32) * 32;
+  if (threads > 1024) return cudaErrorInvalidConfiguration;
+  auto kern = k_chain_cluster<T, kForward, K>;
+  if (S > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(S, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = 2 * (size_t)p * sizeof(T);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, G, xhat, xout, n, p, rows, tpr);
+}
+
+// One SGS chain on a thread-block cluster (tridiagonal layout, 32 <= p <= 512):
+// 16 threads per row, K = ceil(p / 16) columns per thread.  Returns false if
+// the device refuses the cluster launch.
 template <typename T, bool kForward>
 bool launch_chain_cluster(mg_handle *h, const T *G, const T *xhat, T *xout, int n, int p, cudaStream_t s) {
+  const int kneed = (p + 15) / 16;
   for (int S : {16, 8}) {
-    const int rows = (p + S - 1) / S;
-    int tpr = 32;
-    while (tpr > 1 && rows * tpr > 256) tpr >>= 1;
-    const int threads = ((rows * tpr + 31) / 32) * 32;
-    auto kern = k_chain_cluster<T, kForward>;
-    if (S > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(S, 1, 1);
-    cfg.blockDim = dim3(threads, 1, 1);
-    cfg.dynamicSmemBytes = 2 * (size_t)p * sizeof(T);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = S;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, G, xhat, xout, n, p, rows, tpr);
+    cudaError_t e;
+    if (kneed <= 2) e = launch_chain_cluster_k<T, kForward, 2>(S, G, xhat, xout, n, p, s);
+    else if (kneed <= 4) e = launch_chain_cluster_k<T, kForward, 4>(S, G, xhat, xout, n, p, s);
+    else if (kneed <= 8) e = launch_chain_cluster_k<T, kForward, 8>(S, G, xhat, xout, n, p, s);
+    else if (kneed <= 16) e = launch_chain_cluster_k<T, kForward, 16>(S, G, xhat, xout, n, p, s);
+    else e = launch_chain_cluster_k<T, kForward, 32>(S, G, xhat, xout, n, p, s);
     if (e == cudaSuccess) return true;
     cudaGetLastError();
   }
   return false;
+}
+
+// One SGS chain as a parallel scan (k_scan_round): ceil(log2 n) batched GEMVs.
+template <typename T>
+void run_scan(mg_handle *h, const std::vector<T *> &P, const T *xhat, T *out, T *tmp, int n, int p, int reverse,
+              cudaStream_t s) {
+  // algorithmic: per round, the prefix products of the steps that update
+  // (n - 2^d of them, p^2 each) plus two vector passes; 2 p^2 flops per update
+  double bytes = 0.0, flops = 0.0;
+  for (int d = 0; d < (int)P.size(); ++d) {
+    const double upd = std::max(0, n - (1 << d));
+    bytes += sizeof(T) * (upd * (double)p * p + 2.0 * n * p);
+    flops += 2.0 * upd * (double)p * p;
+  }
+  Bracket br(h, CAT_CHAIN, s, bytes, flops);
+  const int R = (int)P.size();
+  if (R == 0) {
+    ck(cudaMemcpyAsync(out, xhat, (size_t)n * p * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  // parts column slices per row: the largest power of two with parts * p <= 512
+  // and at least 8 columns per slice
+  int parts = 1;
+  while (parts * 2 * p <= 512 && p / (parts * 2) >= 8) parts *= 2;
+  const int threads = std::max(parts * p, 32);
+  const size_t shm = (size_t)(1 + parts) * p * sizeof(T);
+  const T *in = xhat;
+  for (int d = 0; d < R; ++d) {
+    T *dst = ((R - 1 - d) % 2 == 0) ? out : tmp;
+    k_scan_round<T><<<n, threads, shm, s>>>(P[d], in, dst, n, p, 1 << d, reverse, parts);
+    ck_launch();
+    in = dst;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -384,7 +461,10 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
   const int threads = std::max(32, ((p + 31) / 32) * 32);
   const size_t shm = (size_t)p * sizeof(T);
   const bool cluster = h->layout == MG_LAYOUT_TRIDIAG && p >= 32 && h->use_cluster;
-  if (n >= 1) {
+  const bool scan = h->use_scan && (n == 1 || !d.scanF.empty());
+  if (scan) {
+    run_scan<T>(h, d.scanF, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, d.scan_tmp, n, p, 0, s);
+  } else if (n >= 1) {
     Bracket br(h, CAT_CHAIN, s);
     if (!cluster || !launch_chain_cluster<T, true>(h, d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p, s)) {
       k_chain_forward<T><<<1, threads, shm, s>>>(d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p);
@@ -393,7 +473,9 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
   }
   // yhat = D^-1 (r - L w): only mu(yhat) is needed by the backward chain
   launch_block_solve<T>(h, d.view, r, d.chainU, nullptr, d.sgs_w, s);
-  if (n >= 1) {
+  if (scan) {
+    run_scan<T>(h, d.scanB, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, d.scan_tmp, n, p, 1, s);
+  } else if (n >= 1) {
     Bracket br(h, CAT_CHAIN, s);
     if (!cluster || !launch_chain_cluster<T, false>(h, d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p, s)) {
       k_chain_backward<T><<<1, threads, shm, s>>>(d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p);
@@ -461,7 +543,7 @@ void coarse_solve(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
   h->coarse_iters += k;
   {
     Bracket br(h, CAT_SMALL, s);
-    k_backsolve<<<1, 1, 0, s>>>(k, K.H, h->ldh, K.g, K.ycoef);
+    k_backsolve<<<1, 256, (size_t)k * sizeof(double), s>>>(k, K.H, h->ldh, K.g, K.ycoef);
     ck_launch();
   }
   ck(cudaMemsetAsync(h->cy, 0, len * sizeof(double), s));
@@ -484,10 +566,11 @@ void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
   if (o.nu_pre == 0) {
     ck(cudaMemsetAsync(y, 0, lev.len * sizeof(T), s));
   } else {
-    launch_block_solve<T>(h, d.view, b, nullptr, nullptr, y, s);  // first sweep from y = 0
+    const T om = (T)o.omega;
+    launch_block_solve<T>(h, d.view, b, nullptr, nullptr, y, s, nullptr, om);  // first sweep from y = 0
     for (int k = 1; k < o.nu_pre; ++k) {
       Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
-      launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s);
+      launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s, y, om);
       std::swap(y, t);
     }
   }
@@ -501,7 +584,7 @@ void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
   }
   for (int k = 0; k < o.nu_post; ++k) {
     Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
-    launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s);
+    launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s, y, (T)o.omega);
     std::swap(y, t);
   }
   if (y != y_out) ck(cudaMemcpyAsync(y_out, y, lev.len * sizeof(T), cudaMemcpyDeviceToDevice, s));
@@ -604,6 +687,7 @@ void mg_default_options(mg_options *o) {
   o->coarse_fixed_iters = 0;
   o->end_rule = 0;
   o->precision = MG_PRECISION_FP64;
+  o->omega = 1.0;
 }
 
 const char *mg_status_string(int st) {
@@ -638,11 +722,14 @@ int mg_profile_enable(mg_handle *h, int enable) {
   for (int c = 0; c < 16; ++c) {
     h->prof_ms[c] = 0.0;
     h->prof_count[c] = 0;
+    h->work_bytes[c] = 0.0;
+    h->work_flops[c] = 0.0;
   }
   return MG_OK;
 }
 
-int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches) {
+int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches, double *bytes,
+                    double *flops) {
   if (!h || max < 0) return MG_ERR_ARG;
   try {
     harvest(h);
@@ -654,6 +741,8 @@ int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long 
     if (names) names[c] = kCatNames[c];
     if (ms) ms[c] = h->prof_ms[c];
     if (launches) launches[c] = h->prof_count[c];
+    if (bytes) bytes[c] = h->work_bytes[c];
+    if (flops) flops[c] = h->work_flops[c];
   }
   return CAT_COUNT;
 }
@@ -687,6 +776,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     return MG_ERR_ARG;
   if (O->end_rule != 0 && O->end_rule != 1) return MG_ERR_ARG;
   if (O->precision != MG_PRECISION_FP64 && O->precision != MG_PRECISION_FP32) return MG_ERR_ARG;
+  if (!(O->omega > 0.0 && O->omega <= 1.0)) return MG_ERR_ARG;
   if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;
@@ -713,6 +803,12 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   int C = 1;
   while (32 * C < p) C *= 2;
   h->C = C;
+  // SGS chain implementation: "scan" (default), "cluster" or "serial"; the
+  // environment variable PINTMG_SGS_CHAIN selects one (used by the tests)
+  if (const char *e = std::getenv("PINTMG_SGS_CHAIN")) {
+    if (std::strcmp(e, "cluster") == 0) h->use_scan = 0;
+    if (std::strcmp(e, "serial") == 0) h->use_scan = 0, h->use_cluster = 0;
+  }
   int status = MG_OK;
   try {
     ck(cudaMallocHost(&h->host_scal, 4 * sizeof(double)));
@@ -802,6 +898,27 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
           }
           ck_launch();
         }
+        // prefix products for the parallel-scan SGS chains (budget: 8 GiB in FP64)
+        int R = 0;
+        while ((1 << R) < nl) ++R;
+        const double bytes = 2.0 * R * (double)nl * p * p * sizeof(double);
+        if (nl > 1 && bytes <= 8.0 * (1 << 30)) {
+          for (int dir = 0; dir < 2; ++dir) {
+            std::vector<double *> &Pv = dir == 0 ? lev.d.scanF : lev.d.scanB;
+            for (int dd = 0; dd < R; ++dd) Pv.push_back(h->mem.alloc<double>((size_t)nl * p * p));
+            k_scan_init<<<grid_for((long long)nl * p * p, 256, 1 << 20), 256, 0, s>>>(
+                dir == 0 ? lev.d.Cu : lev.d.Em, Pv[0], nl, p, dir);
+            ck_launch();
+            for (int dd = 0; dd + 1 < R; ++dd) {
+              const int shift = 1 << dd;
+              if (nl - 2 * shift <= 0) continue;
+              dim3 grid((p + 31) / 32, (p + 31) / 32, nl - 2 * shift);
+              k_scan_products<<<grid, 256, 0, s>>>(Pv[dd], Pv[dd + 1], nl, p, shift);
+              ck_launch();
+            }
+          }
+          lev.d.scan_tmp = h->mem.alloc<double>((size_t)nl * p);
+        }
       }
       alloc_level_vectors<double>(h, lev, lev.d, l == L - 1, l == 0);
       if (O->precision == MG_PRECISION_FP32) {
@@ -823,6 +940,9 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
         if (l == L - 1) {
           lev.f.Cu = to_float_copy(h, lev.d.Cu, (long long)nl * p * p, s);
           lev.f.Em = to_float_copy(h, lev.d.Em, (long long)nl * p * p, s);
+          for (double *P : lev.d.scanF) lev.f.scanF.push_back(to_float_copy(h, P, (long long)nl * p * p, s));
+          for (double *P : lev.d.scanB) lev.f.scanB.push_back(to_float_copy(h, P, (long long)nl * p * p, s));
+          if (lev.d.scan_tmp) lev.f.scan_tmp = h->mem.alloc<float>((size_t)nl * p);
         }
         alloc_level_vectors<float>(h, lev, lev.f, l == L - 1, l == 0);
       }
@@ -971,7 +1091,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
         if (status != MG_OK) break;
         {
           Bracket br(h, CAT_SMALL, s);
-          k_backsolve<<<1, 1, 0, s>>>(k, K.H, h->ldh, K.g, K.ycoef);
+          k_backsolve<<<1, 256, (size_t)k * sizeof(double), s>>>(k, K.H, h->ldh, K.g, K.ycoef);
           ck_launch();
         }
         multi_axpy(h, x, h->fZ, len, K.ycoef, k, 1.0, len, s);

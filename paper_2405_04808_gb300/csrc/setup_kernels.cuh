@@ -221,3 +221,63 @@ __global__ void k_to_double(const float *__restrict__ x, double *y, long long le
 }
 
 }  // namespace pintmg
+
+namespace pintmg {
+
+// P^(0)_i (column-major) = -G_j with G row-major p x p per step j, where the
+// chain element i uses link j = i (forward, G = Cu) or j = n - i (backward,
+// G = Em); i = 0 has no predecessor (zero matrix).
+__global__ void k_scan_init(const double *__restrict__ G, double *P0, int n, int p, int backward) {
+  const long long total = (long long)n * p * p;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / ((long long)p * p));
+    const long long e = idx % ((long long)p * p);
+    const int col = (int)(e / p), row = (int)(e % p);  // column-major position (row, col)
+    double v = 0.0;
+    if (i >= 1) {
+      const int j = backward ? n - i : i;
+      v = -G[((long long)j * p + row) * p + col];
+    }
+    P0[idx] = v;
+  }
+}
+
+// P^(d+1)_i = P^(d)_i P^(d)_{i-shift} (column-major), for i >= 2 shift; other
+// entries are never read and left untouched.  32 x 32 output tile per CTA,
+// 256 threads, 4 outputs per thread.
+__global__ void __launch_bounds__(256) k_scan_products(const double *__restrict__ Pd, double *Pn, int n, int p,
+                                                       int shift) {
+  __shared__ double As[32][33];
+  __shared__ double Bs[32][33];
+  const int i = blockIdx.z + 2 * shift;
+  if (i >= n) return;
+  const double *A = Pd + (long long)i * p * p;
+  const double *B = Pd + (long long)(i - shift) * p * p;
+  double *Cm = Pn + (long long)i * p * p;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty = 0..7
+  const int row0 = blockIdx.x * 32, col0 = blockIdx.y * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int m0 = 0; m0 < p; m0 += 32) {
+    for (int r = 0; r < 4; ++r) {
+      const int mm = ty + 8 * r;
+      const int arow = row0 + tx, acol = m0 + mm;
+      As[tx][mm] = (arow < p && acol < p) ? A[(long long)acol * p + arow] : 0.0;
+      const int brow = m0 + tx, bcol = col0 + mm;
+      Bs[tx][mm] = (brow < p && bcol < p) ? B[(long long)bcol * p + brow] : 0.0;
+    }
+    __syncthreads();
+    for (int mm = 0; mm < 32; ++mm) {
+      const double a = As[tx][mm];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[r] = fma(a, Bs[mm][ty + 8 * r], acc[r]);
+    }
+    __syncthreads();
+  }
+  for (int r = 0; r < 4; ++r) {
+    const int row = row0 + tx, col = col0 + ty + 8 * r;
+    if (row < p && col < p) Cm[(long long)col * p + row] = acc[r];
+  }
+}
+
+}  // namespace pintmg

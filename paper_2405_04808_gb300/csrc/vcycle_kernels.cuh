@@ -97,10 +97,26 @@ __device__ __forceinline__ void local_solve_dense(const LevelView<T> &L, int j,
 // (the identity entries of L and L^T, Fig. 5): block j's mu_{j-1} row sees
 // u_{j-1} (cplU) and its u_j row sees mu_j (cplM).  Either may be null (zero).
 // With cplU = y.u, cplM = y.m this is one block-Jacobi sweep (Eq. jacobi-aj).
+// omega != 1 (an option, not the paper's sweep) relaxes it:
+// out = yold + omega (D^-1(...) - yold), yold null meaning 0.
+
+template <typename T, int C>
+__device__ __forceinline__ void relax_chunk(T (&x)[C], const T *yold, int len, int ln, T omega) {
+  if (yold) {
+    T o[C];
+    chunk_load<T, C>(o, yold, len, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) x[e] = fma(omega, x[e] - o[e], o[e]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < C; ++e) x[e] *= omega;
+  }
+}
 
 template <typename T, int C>
 __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T *__restrict__ r,
-                                                         const T *cplU, const T *cplM, T *out) {
+                                                         const T *cplU, const T *cplM, T *out,
+                                                         const T *yold, T omega) {
   const int ln = threadIdx.x & (kWarp - 1);
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int n = L.n, p = L.p, q = L.q;
@@ -133,6 +149,18 @@ __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T
     }
   }
   local_solve_tri<T, C>(L, j, ru, rz, rl, rv, rm, u, z, l, v, m, ln);
+  if (omega != T(1)) {
+    Vec<const T> Yo = make_cvec(yold ? yold : r, n, p, q);
+    if (j < n) {
+      relax_chunk<T, C>(u, yold ? Yo.u + (long long)j * p : nullptr, p, ln, omega);
+      relax_chunk<T, C>(z, yold ? Yo.z + (long long)j * q : nullptr, q, ln, omega);
+      relax_chunk<T, C>(l, yold ? Yo.l + (long long)j * p : nullptr, p, ln, omega);
+    }
+    if (j >= 1) {
+      relax_chunk<T, C>(v, yold ? Yo.v + (long long)(j - 1) * p : nullptr, p, ln, omega);
+      relax_chunk<T, C>(m, yold ? Yo.m + (long long)(j - 1) * p : nullptr, p, ln, omega);
+    }
+  }
   if (j < n) {
     chunk_store<T, C>(Y.u + (long long)j * p, u, p, ln);
     chunk_store<T, C>(Y.z + (long long)j * q, z, q, ln);
@@ -146,7 +174,8 @@ __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const T *__restrict__ r,
-                                                           const T *cplU, const T *cplM, T *out) {
+                                                           const T *cplU, const T *cplM, T *out,
+                                                           const T *yold, T omega) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = L.n, p = L.p, q = L.q;
   if (j > n) return;
@@ -170,6 +199,21 @@ __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const
     }
   }
   local_solve_dense<T>(L, j, ru, rz, rl, rv, rm, u, z, l, v, m);
+  if (omega != T(1)) {
+    Vec<const T> Yo = make_cvec(yold ? yold : r, n, p, q);
+    auto relax = [&](T *x, const T *o, int len) {
+      for (int i = 0; i < len; ++i) x[i] = yold ? fma(omega, x[i] - o[i], o[i]) : omega * x[i];
+    };
+    if (j < n) {
+      relax(u, Yo.u + (long long)j * p, p);
+      relax(z, Yo.z + (long long)j * q, q);
+      relax(l, Yo.l + (long long)j * p, p);
+    }
+    if (j >= 1) {
+      relax(v, Yo.v + (long long)(j - 1) * p, p);
+      relax(m, Yo.m + (long long)(j - 1) * p, p);
+    }
+  }
   if (j < n) {
     for (int i = 0; i < p; ++i) {
       Y.u[(long long)j * p + i] = u[i];
@@ -557,7 +601,7 @@ namespace pintmg {
 // instruction reads TPR consecutive entries of the row.
 // kForward: links j = 1..n-1 on x = u; otherwise links j = n-1..1 on x = mu
 // (x_{j-1} = xhat_{j-1} - G_j x_j).
-template <typename T, bool kForward>
+template <typename T, bool kForward, int K>
 __global__ void k_chain_cluster(const T *__restrict__ G, const T *__restrict__ xhat, T *xout, int n, int p,
                                 int rows_per_cta, int tpr) {
   namespace cg = cooperative_groups;
@@ -570,35 +614,104 @@ __global__ void k_chain_cluster(const T *__restrict__ G, const T *__restrict__ x
   const int row_local = tid / tpr, part = tid % tpr;
   const int row = c * rows_per_cta + row_local;
   const bool owner = (row_local < rows_per_cta) && (row < p);
-  // start vector: x_0 (forward) or x_{n-1} (backward), into buffer 0 of this CTA
+  // this thread's K columns (part, part + tpr, ...) of its row for one link,
+  // and the row's entry of xhat: loaded one link ahead
+  T g[K];
+  T xh = T(0);
+  auto load_link = [&](int step) {
+    if (step >= n || !owner) return;
+    const int j = kForward ? step : n - step;
+    const long long dst = kForward ? j : (long long)(j - 1);
+    const T *gr = G + ((long long)j * p + row) * p;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int k = part + i * tpr;
+      g[i] = (k < p) ? gr[k] : T(0);
+    }
+    xh = xhat[dst * p + row];
+  };
   const long long first = kForward ? 0 : (long long)(n - 1);
   for (int i = tid; i < p; i += blockDim.x) buf[i] = xhat[first * p + i];
   if (c == 0)
     for (int i = tid; i < p; i += blockDim.x) xout[first * p + i] = xhat[first * p + i];
+#pragma unroll
+  for (int i = 0; i < K; ++i) g[i] = T(0);
+  load_link(1);
   cluster.sync();
   int cur = 0;
   for (int step = 1; step < n; ++step) {
-    const int j = kForward ? step : n - step;            // link index
+    const int j = kForward ? step : n - step;
     const long long dst = kForward ? j : (long long)(j - 1);
+    const T *xv = buf + cur * p;
     T acc = T(0);
-    if (owner) {
-      const T *gr = G + ((long long)j * p + row) * p;
-      const T *xv = buf + cur * p;
-      for (int k = part; k < p; k += tpr) acc = fma(gr[k], xv[k], acc);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int k = part + i * tpr;
+      if (k < p) acc = fma(g[i], xv[k], acc);
     }
-    // combine the tpr partial sums of a row (tpr divides 32, lanes of a row are contiguous)
+    // combine the tpr partial sums of a row (lanes of a row are contiguous, tpr divides 32)
     for (int o = tpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, tpr);
     const int nxt = cur ^ 1;
     if (owner && part == 0) {
-      const T v = xhat[dst * p + row] - acc;
+      const T v = xh - acc;
       xout[dst * p + row] = v;
       for (int r = 0; r < S; ++r) {
         T *remote = cluster.map_shared_rank(buf, r);
         remote[nxt * p + row] = v;
       }
     }
-    cluster.sync();
+    // publish x_j; the next link's loads do not depend on it and overlap the barrier
+    auto token = cluster.barrier_arrive();
+    load_link(step + 1);
+    cluster.barrier_wait(std::move(token));
     cur = nxt;
+  }
+}
+
+}  // namespace pintmg
+
+namespace pintmg {
+
+// ---------------------------------------------------------------------------
+// SGS chains as a parallel scan in time.  A chain x_i = xhat_i + A_i x_{i-1}
+// (i = 1..n-1, x_0 = xhat_0) is a linear recurrence; with the prefix products
+// P^(d)_i = A_i A_{i-1} ... A_{i-2^d+1} (precomputed at setup, column-major
+// p x p), a Kogge-Stone scan runs ceil(log2 n) rounds of
+//     x_i <- x_i + P^(d)_i x_{i-2^d}      (i >= 2^d; others copied)
+// each a batched GEMV over every time step at once.  Element i is stored at
+// position i (forward chain) or n-1-i (backward chain, reverse = 1).
+// One CTA per i; threads (r, part) with r = tid mod p share row r over
+// `parts` column slices (coalesced column-major loads, more loads in flight),
+// the source vector x_{i-2^d} and the slice sums are staged in shared memory.
+template <typename T>
+__global__ void k_scan_round(const T *__restrict__ Pd, const T *__restrict__ xin, T *xout, int n, int p,
+                             int shift, int reverse, int parts) {
+  extern __shared__ unsigned char smem_raw[];
+  T *src = reinterpret_cast<T *>(smem_raw);
+  T *part_sum = src + p;  // [parts][p]
+  const int i = blockIdx.x;
+  const long long si = reverse ? (long long)(n - 1 - i) : i;
+  if (i < shift) {
+    for (int r = threadIdx.x; r < p; r += blockDim.x) xout[si * p + r] = xin[si * p + r];
+    return;
+  }
+  const long long sj = reverse ? (long long)(n - 1 - (i - shift)) : (long long)(i - shift);
+  for (int r = threadIdx.x; r < p; r += blockDim.x) src[r] = xin[sj * p + r];
+  __syncthreads();
+  const T *P = Pd + (long long)i * p * p;
+  const int r = threadIdx.x % p, part = threadIdx.x / p;
+  if (part < parts) {
+    const int k0 = part * p / parts, k1 = (part + 1) * p / parts;
+    T acc = T(0);
+#pragma unroll 8
+    for (int k = k0; k < k1; ++k) acc = fma(P[(long long)k * p + r], src[k], acc);
+    part_sum[part * p + r] = acc;
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < p; rr += blockDim.x) {
+    T acc = xin[si * p + rr];
+    for (int q = 0; q < parts; ++q) acc += part_sum[q * p + rr];
+    xout[si * p + rr] = acc;
   }
 }
 

@@ -48,7 +48,8 @@ class MGProblem(ctypes.Structure):
 class MGOptions(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("coarse_rtol", ctypes.c_double), ("coarse_maxit", ctypes.c_int),
-                ("coarse_fixed_iters", ctypes.c_int), ("end_rule", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("coarse_fixed_iters", ctypes.c_int), ("end_rule", ctypes.c_int), ("precision", ctypes.c_int),
+                ("omega", ctypes.c_double)]
 
 
 class MGSolveInfo(ctypes.Structure):
@@ -89,7 +90,8 @@ def lib():
         L.mg_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.mg_profile_enable.restype = ctypes.c_int
         L.mg_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
-                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.mg_profile_read.restype = ctypes.c_int
         L.mg_true_residual_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]
@@ -120,7 +122,7 @@ def _c(arr):
 
 
 def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit=50,
-             coarse_fixed_iters=0, end_rule=0, precision=MG_PRECISION_FP64, stream=0):
+             coarse_fixed_iters=0, end_rule=0, precision=MG_PRECISION_FP64, omega=1.0, stream=0):
     """Build the device hierarchy for a workloads.Problem; returns an opaque handle (int)."""
     keep = []
     P = MGProblem()
@@ -132,7 +134,7 @@ def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit
         a, ptr = _c(getattr(prob, name))
         keep.append(a)
         setattr(P, name, ptr)
-    o = MGOptions(levels, nu_pre, nu_post, coarse_rtol, coarse_maxit, coarse_fixed_iters, end_rule, precision)
+    o = MGOptions(levels, nu_pre, nu_post, coarse_rtol, coarse_maxit, coarse_fixed_iters, end_rule, precision, omega)
     h = ctypes.c_void_p()
     code = lib().mg_setup(ctypes.byref(P), ctypes.byref(o), ctypes.c_void_p(stream), ctypes.byref(h))
     if code != MG_OK:
@@ -175,15 +177,17 @@ def mg_profile_enable(h, mask: int = PROFILE_ALL) -> None:
 
 
 def mg_profile_read(h) -> dict:
-    """{category: (total_ms, launches)} of the kernels timed since mg_profile_enable."""
+    """{category: (total_ms, launches, algorithmic_bytes, algorithmic_flops)} since mg_profile_enable."""
     k = 16
     names = (ctypes.c_char_p * k)()
     ms = (ctypes.c_double * k)()
     cnt = (ctypes.c_longlong * k)()
-    n = lib().mg_profile_read(ctypes.c_void_p(h), k, names, ms, cnt)
+    by = (ctypes.c_double * k)()
+    fl = (ctypes.c_double * k)()
+    n = lib().mg_profile_read(ctypes.c_void_p(h), k, names, ms, cnt, by, fl)
     if n < 0:
         raise PintmgError(n, "mg_profile_read")
-    return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(n, k))}
+    return {names[i].decode(): (ms[i], int(cnt[i]), by[i], fl[i]) for i in range(min(n, k))}
 
 
 def mg_true_residual_noalloc(h, b_ptr: int, x_ptr: int, out_ptr: int, stream: int = 0) -> int:

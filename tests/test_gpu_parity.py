@@ -32,7 +32,7 @@ def _dev(a):
 
 
 CASES = [
-    # (problem, levels, nu_pre, nu_post, end_rule)
+    # (problem, levels, nu_pre, nu_post, end_rule[, omega])
     (lambda: W.vdp(n=64, seed=101), 3, 1, 1, 0),
     (lambda: W.vdp(n=48, seed=102), 2, 2, 3, 1),
     (lambda: W.vdp(n=24, seed=103), 1, 0, 0, 0),
@@ -41,14 +41,22 @@ CASES = [
     (lambda: W.burgers(nx=64, n=16, seed=105), 3, 1, 0, 1),
     (lambda: W.burgers(nx=7, n=8, seed=106, theta=0.5), 2, 1, 1, 0),  # theta < 1: V_k varies
     (lambda: W.burgers(nx=130, n=16, seed=107), 2, 4, 4, 0),     # p = 130: 8 per lane, tail lanes empty
+    (lambda: W.burgers(nx=40, n=32, seed=108), 3, 3, 2, 0, 0.7),  # relaxed sweeps (option)
+    (lambda: W.vdp(n=32, seed=109), 2, 2, 2, 0, 0.6),
 ]
+
+
+def _unpack(case):
+    c = CASES[case]
+    return c[0], c[1], c[2], c[3], c[4], (c[5] if len(c) > 5 else 1.0)
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_vcycle_matches_oracle(P, case):
-    make, levels, nu_pre, nu_post, end_rule = CASES[case]
+    make, levels, nu_pre, nu_post, end_rule, omega = _unpack(case)
     prob = make()
-    opts = dict(levels=levels, nu_pre=nu_pre, nu_post=nu_post, coarse_fixed_iters=3, end_rule=end_rule)
+    opts = dict(levels=levels, nu_pre=nu_pre, nu_post=nu_post, coarse_fixed_iters=3, end_rule=end_rule,
+                omega=omega)
     h = P.mg_setup(prob, **opts)
     try:
         rng = np.random.default_rng(case)
@@ -66,11 +74,11 @@ def test_vcycle_matches_oracle(P, case):
         P.mg_destroy(h)
 
 
-@pytest.mark.parametrize("case", [0, 1, 3, 4, 5, 6])
+@pytest.mark.parametrize("case", [0, 1, 3, 4, 5, 6, 8, 9])
 def test_fgmres_matches_direct_solve(P, case):
-    make, levels, nu_pre, nu_post, end_rule = CASES[case]
+    make, levels, nu_pre, nu_post, end_rule, omega = _unpack(case)
     prob = make()
-    h = P.mg_setup(prob, levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule)
+    h = P.mg_setup(prob, levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule, omega=omega)
     try:
         b = _dev(prob.b)
         x = torch.empty_like(b)
@@ -81,7 +89,8 @@ def test_fgmres_matches_direct_solve(P, case):
         err = np.linalg.norm(x.cpu().numpy() - xd) / np.linalg.norm(xd)
         assert err <= SOLVE_RTOL, err
         # the oracle's own FGMRES reaches the same solution
-        hier = O.Hierarchy(prob, O.MGOptions(levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule))
+        hier = O.Hierarchy(prob, O.MGOptions(levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule,
+                                             omega=omega))
         xo, res, tr = hier.solve(prob.b, rtol=1e-10, maxit=2000, restart=500)
         assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= SOLVE_RTOL
     finally:
@@ -154,7 +163,7 @@ def test_fp32_vcycle_close_to_fp64_oracle(P):
 @pytest.mark.parametrize("case", [0, 4, 7])
 def test_fp32_preconditioned_fgmres_reaches_fp64_solution(P, case):
     """FGMRES tolerates the FP32 preconditioner: same solution to 1e-9 at a 1e-10 residual."""
-    make, levels, nu_pre, nu_post, end_rule = CASES[case]
+    make, levels, nu_pre, nu_post, end_rule, _ = _unpack(case)
     prob = make()
     h = P.mg_setup(prob, levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule,
                    precision=P.MG_PRECISION_FP32)
@@ -170,9 +179,12 @@ def test_fp32_preconditioned_fgmres_reaches_fp64_solution(P, case):
         P.mg_destroy(h)
 
 
-def test_cluster_chain_full_size_vcycle(P):
-    """Bench-sized coarse grid (257 blocks, p = 128) through the cluster SGS
-    chains: a sampled V-cycle agrees with the oracle."""
+@pytest.mark.parametrize("chain", ["scan", "cluster", "serial"])
+def test_sgs_chain_variants_full_size_vcycle(P, chain, monkeypatch):
+    """Bench-sized coarse grid (257 blocks, p = 128) through each SGS chain
+    implementation (parallel scan, 16-SM cluster, one CTA): the V-cycle agrees
+    with the oracle."""
+    monkeypatch.setenv("PINTMG_SGS_CHAIN", chain)
     prob = W.burgers(nx=128, n=256, seed=141)
     opts = dict(levels=2, nu_pre=1, nu_post=1, coarse_fixed_iters=2)
     h = P.mg_setup(prob, **opts)
@@ -184,5 +196,22 @@ def test_cluster_chain_full_size_vcycle(P):
         yo = O.Hierarchy(prob, O.MGOptions(**opts)).precondition(prob.b)
         err = np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo)
         assert err <= VCYCLE_RTOL, err
+    finally:
+        P.mg_destroy(h)
+
+
+@pytest.mark.parametrize("chain", ["scan", "serial"])
+def test_sgs_chain_variants_dense(P, chain, monkeypatch):
+    monkeypatch.setenv("PINTMG_SGS_CHAIN", chain)
+    prob = W.vdp(n=64, seed=161)
+    opts = dict(levels=2, nu_pre=1, nu_post=1, coarse_fixed_iters=3)
+    h = P.mg_setup(prob, **opts)
+    try:
+        rd = _dev(prob.b)
+        yd = torch.empty_like(rd)
+        assert P.mg_vcycle(h, rd.data_ptr(), yd.data_ptr(), 0) == P.MG_OK
+        torch.cuda.synchronize()
+        yo = O.Hierarchy(prob, O.MGOptions(**opts)).precondition(prob.b)
+        assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) <= VCYCLE_RTOL
     finally:
         P.mg_destroy(h)

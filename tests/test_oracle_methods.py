@@ -57,6 +57,9 @@ def test_jacobi_is_textbook_block_jacobi(make):
         want[a:c] += np.linalg.solve(A[a:c, a:c], res[a:c])
     got = O.jacobi_sweep(lev, b, y)
     assert np.allclose(got, want, rtol=0, atol=1e-10 * np.max(np.abs(want)))
+    # relaxed sweep (an option outside the paper): y + omega D^-1 (b - A y)
+    got = O.jacobi_sweep(lev, b, y, omega=0.7)
+    assert np.allclose(got, y + 0.7 * (want - y), rtol=0, atol=1e-10 * np.max(np.abs(want)))
     # the exact solution is a fixed point
     ystar = np.linalg.solve(A, b)
     assert np.allclose(O.jacobi_sweep(lev, b, ystar), ystar, rtol=0, atol=1e-9 * np.max(np.abs(ystar)))

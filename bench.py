@@ -30,6 +30,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
+from paper_2405_04808_gb300 import replicas as RP  # noqa: E402
 from paper_2405_04808_gb300 import workloads as W  # noqa: E402
 
 METRIC = "augmented solves/s to 1e-8 rel. residual: plain FP64 MG vs mixed/learned/batched"
@@ -212,12 +213,10 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
         P.mg_profile_enable(h, 0)
         if world > 1:
             torch.distributed.barrier()
-        total_ms = sum(a.elapsed_time(bb) for a, bb in ev)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-        out = {"value": world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+        local_ms = sum(a.elapsed_time(bb) for a, bb in ev)
+        value = RP.job_throughput(local_ms / 1e3, steps, world, device=dev)
+        total_ms = 1e3 * world * steps / value   # the slowest rank's time
+        out = {"value": value, "ms_per_step": total_ms / steps,
                "iters": [i.iters for i in infos], "true_relres": max(i.true_relres for i in infos),
                "coarse_iters_per_vcycle": sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)),
                "setup_ms": setup_ms, "launches": launches, "shares": shares, "dominant": dominant,
@@ -230,12 +229,8 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
             t0 = time.perf_counter()
             for _ in range(steps):
                 solve(bh.data_ptr(), xh.data_ptr())
-            e2e_s = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([e2e_s], device=dev)
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                e2e_s = float(t.item())
-            out["e2e"] = {"value": round(world * steps / e2e_s, 4), "unit": UNIT,
+            e2e_value = RP.job_throughput(time.perf_counter() - t0, steps, world, device=dev)
+            out["e2e"] = {"value": round(e2e_value, 4), "unit": UNIT,
                           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
         return out
     finally:
@@ -255,7 +250,7 @@ def run_native(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev).cuda_stream
     wl = W.WORKLOADS[args.workload]
-    prob = wl["make"](seed=2000 + 17 * rank) if rank else wl["make"]()
+    prob = wl["make"](seed=RP.rank_seed(wl["seed"], rank))
     main = measure(P, torch, prob, wl, args, args.precision, args.omega, args.steps, args.warmup, dev, stream,
                    world, True)
     variants = {}

@@ -40,6 +40,46 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_partial(const double *
   if (threadIdx.x == 0) partial[(long long)i * gridDim.x + blockIdx.x] = s;
 }
 
+// The same for VB vectors per CTA: each thread streams its slice of w once
+// against VB basis vectors (VB independent accumulators), so the per-CTA
+// reduction is amortised over VB times more fused multiply-adds.
+// partial[i * gridDim.x + blockIdx.x] for i = blockIdx.y * VB + v < m.
+template <int VB>
+__global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *__restrict__ V, long long ldv, int m,
+                                                                  const double *__restrict__ w, long long len,
+                                                                  double *partial, const int *gate) {
+  if (gate && *gate == 0) return;
+  __shared__ double red[kDotThreads / kWarp][VB];
+  const int vb = blockIdx.y * VB;
+  const int nv = min(VB, m - vb);
+  double acc[VB];
+#pragma unroll
+  for (int v = 0; v < VB; ++v) acc[v] = 0.0;
+  for (long long idx = blockIdx.x * (long long)kDotThreads + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * kDotThreads) {
+    const double wv = w[idx];
+#pragma unroll
+    for (int v = 0; v < VB; ++v)
+      if (v < nv) acc[v] = fma(V[(long long)(vb + v) * ldv + idx], wv, acc[v]);
+  }
+  const int wp = threadIdx.x / kWarp, ln = threadIdx.x & (kWarp - 1);
+#pragma unroll
+  for (int v = 0; v < VB; ++v) {
+    double x = acc[v];
+    if (v < nv) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+    }
+    if (ln == 0) red[wp][v] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double sum = 0.0;
+    for (int i = 0; i < kDotThreads / kWarp; ++i) sum += red[i][threadIdx.x];
+    partial[(long long)(vb + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
 // out[i] (+)= sum_g partial[i * G + g], fixed order.  One warp per i.
 __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int m, double *out, int accumulate,
                                   const int *gate = nullptr) {
@@ -55,13 +95,19 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int
 }
 
 // y[idx] += sign * sum_{i < m} c[i] X_i[idx],  X_i = X + i * ldx
+// (coefficients staged in shared memory; m <= 512; the vector loop is unrolled
+// so that several basis loads are in flight per thread)
 __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long ldx, const double *__restrict__ c,
                              int m, double sign, long long len, const int *gate = nullptr) {
   if (gate && *gate == 0) return;
+  __shared__ double cs[512];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
+  __syncthreads();
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
        idx += (long long)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int i = 0; i < m; ++i) acc = fma(c[i], X[i * ldx + idx], acc);
+#pragma unroll 8
+    for (int i = 0; i < m; ++i) acc = fma(cs[i], X[i * ldx + idx], acc);
     y[idx] = fma(sign, acc, y[idx]);
   }
 }

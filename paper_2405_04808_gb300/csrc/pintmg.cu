@@ -264,12 +264,14 @@ LevelData<float> &ldata<float>(Level &L) { return L.f; }
 
 void multidot(mg_handle *h, const double *V, long long ldv, int m, const double *w, long long len, double *out,
               int accumulate, cudaStream_t s, const int *gate = nullptr) {
-  const int G = (int)std::max<long long>(1, std::min<long long>(h->G, (len + kDotThreads - 1) / kDotThreads));
-  dim3 grid(G, m);
+  // about 32 entries per thread per vector, at most 152 CTAs per vector block
+  constexpr int VB = 8;
+  const int G = (int)std::max<long long>(1, std::min<long long>(152, (len + 32 * kDotThreads - 1) / (32 * kDotThreads)));
+  dim3 grid(G, (m + VB - 1) / VB);
   {
     // algorithmic: read the m vectors and w once, 2 m len flops
     Bracket br(h, CAT_DOT, s, 8.0 * (m + (V == w ? 0 : 1)) * len, 2.0 * m * len);
-    k_multidot_partial<<<grid, kDotThreads, 0, s>>>(V, ldv, w, len, h->partial, gate);
+    k_multidot_blocked<VB><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate);
     ck_launch();
   }
   {

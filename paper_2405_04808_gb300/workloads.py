@@ -346,11 +346,11 @@ def burgers(nx: int = 128, n: int = 1024, nu: float = 0.01, seed: int = 2000,
 
 #: the solver settings that go with each named workload (levels, smoothing)
 WORKLOADS = {
-    "vdp_n256": dict(make=lambda seed=1000: vdp(n=256, seed=seed), levels=2, nu_pre=1, nu_post=1),
-    "burgers_nx128_n1024": dict(make=lambda seed=2000: burgers(nx=128, n=1024, nu=0.01, seed=seed),
+    "vdp_n256": dict(make=lambda seed=1000: vdp(n=256, seed=seed), seed=1000, levels=2, nu_pre=1, nu_post=1),
+    "burgers_nx128_n1024": dict(make=lambda seed=2000: burgers(nx=128, n=1024, nu=0.01, seed=seed), seed=2000,
                                 levels=3, nu_pre=4, nu_post=4),
-    "burgers_nx128_n8192": dict(make=lambda seed=2500: burgers(nx=128, n=8192, nu=0.01, seed=seed),
+    "burgers_nx128_n8192": dict(make=lambda seed=2500: burgers(nx=128, n=8192, nu=0.01, seed=seed), seed=2500,
                                 levels=3, nu_pre=4, nu_post=4),
-    "burgers_nx512_n8192": dict(make=lambda seed=3000: burgers(nx=512, n=8192, nu=0.005, seed=seed),
+    "burgers_nx512_n8192": dict(make=lambda seed=3000: burgers(nx=512, n=8192, nu=0.005, seed=seed), seed=3000,
                                 levels=4, nu_pre=4, nu_post=4),
 }

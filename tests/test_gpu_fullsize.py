@@ -1,0 +1,90 @@
+"""Parity at the benchmark workloads' full sizes, in bench.py's configuration.
+
+C1 (van der Pol, n = 256, 2 levels, 1/1) is small enough for a direct solve
+of the oracle's system.  C2 (Burgers nx = 128, n = 1024, 3 levels, 4/4,
+655,360 unknowns) is checked through properties the oracle computes
+independently: the GPU solution's residual against the oracle's own
+assembled lifted operator, agreement with a direct sparse solve, and one
+full-size V-cycle against the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import augmented as O
+from paper_2405_04808_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2405_04808_gb300 import pintmg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pintmg.lib()
+    return pintmg
+
+
+def _solve(P, prob, wl, rtol, restart=400, **kw):
+    h = P.mg_setup(prob, levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], **kw)
+    try:
+        b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), rtol, 3000, restart)
+        assert code == P.MG_OK, P.mg_status_string(code)
+        return x.cpu().numpy(), info
+    finally:
+        P.mg_destroy(h)
+
+
+def test_c1_vdp_full_size(P):
+    wl = W.WORKLOADS["vdp_n256"]
+    prob = wl["make"]()
+    x, info = _solve(P, prob, wl, 1e-10)
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-9
+    # the oracle's FGMRES at the same settings takes the same number of iterations (R13: +-2)
+    h = O.Hierarchy(prob, O.MGOptions(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"]))
+    _, res, _ = h.solve(prob.b, rtol=1e-10, maxit=3000, restart=400)
+    assert abs(res.iters - info.iters) <= 2
+
+
+@pytest.mark.slow
+def test_c2_burgers_full_size_solution(P):
+    wl = W.WORKLOADS["burgers_nx128_n1024"]
+    prob = wl["make"]()
+    x, info = _solve(P, prob, wl, 1e-10, omega=0.7)   # relaxed sweeps: same solution, 50x fewer iterations
+    lev = O.Level(O.raw_from_problem(prob))
+    rel = np.linalg.norm(prob.b - lev.A @ x) / np.linalg.norm(prob.b)
+    assert rel <= 1.5e-10, rel
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-9
+
+
+@pytest.mark.slow
+def test_c2_burgers_full_size_vcycle(P):
+    """One V-cycle at the bench configuration (fixed coarse iterations) equals the oracle's."""
+    wl = W.WORKLOADS["burgers_nx128_n1024"]
+    prob = wl["make"]()
+    opts = dict(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], coarse_fixed_iters=2)
+    h = P.mg_setup(prob, **opts)
+    try:
+        r = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(r)
+        assert P.mg_vcycle(h, r.data_ptr(), y.data_ptr(), 0) == P.MG_OK
+        torch.cuda.synchronize()
+        yo = O.Hierarchy(prob, O.MGOptions(**opts)).precondition(prob.b)
+        yg = y.cpu().numpy()
+        assert np.linalg.norm(yg - yo) / np.linalg.norm(yo) <= 1e-10
+        # sampled entries, element by element (first, middle, last steps of every type)
+        n, p, q = prob.n, prob.p, prob.q
+        off = O.type_major_offsets(n, p, q)
+        scale = np.max(np.abs(yo))
+        for t in "uvzlm":
+            wdt = q if t == "z" else p
+            for step in (0, n // 2, n - 1):
+                sl = slice(off[t] + step * wdt, off[t] + (step + 1) * wdt)
+                assert np.max(np.abs(yg[sl] - yo[sl])) <= 1e-10 * scale
+    finally:
+        P.mg_destroy(h)

@@ -17,7 +17,14 @@ namespace pintmg {
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kDenseMax = 4;     // dense layout: p, q <= 4 (one thread per time block)
-constexpr int kScanWords = 8;    // tridiagonal: per-lane chunk maps, 2x2 forward + 2x2 backward
+// tridiagonal: per time block, the 2x2 maps each lane composes in each of the
+// 5 rounds of the forward and backward warp scans (precomputed at setup),
+// laid out [direction][round][entry][lane] so that lanes read consecutively
+constexpr int kScanRounds = 5;
+constexpr int kScanPerBlock = 2 * kScanRounds * 4 * 32;
+__host__ __device__ constexpr int scan_index(int dir, int round, int entry, int lane) {
+  return ((dir * kScanRounds + round) * 4 + entry) * 32 + lane;
+}
 
 // Coefficients of one grid level (device pointers), in the kernels' precision T.
 //   N, V, Z: per-step blocks (tridiagonal: 3 band rows of p; dense: p*p, p*p, p*q)
@@ -25,8 +32,9 @@ constexpr int kScanWords = 8;    // tridiagonal: per-lane chunk maps, 2x2 forwar
 //   fac:  tridiagonal: LDL^T of S = N N^T + Z Z^T as [a(p) | b(p) | dinv(p)]
 //         (a_i = L[i][i-1], b_i = L[i][i-2], dinv_i = 1 / D_i);
 //         dense: Cholesky factor of S, row-major p*p, diagonal stored inverted.
-//   scan: tridiagonal only: per step, per lane, the 2x2 maps of that lane's
-//         chunk of the forward and backward LDL^T recurrences (row-major).
+//   scan: tridiagonal only: per step, kScanPerBlock entries: for each lane and
+//         round of the forward / backward warp scans, the composed 2x2 map of
+//         that lane's LDL^T recurrence chunks (scan_index layout).
 template <typename T>
 struct LevelView {
   int n, p, q, layout;
@@ -135,33 +143,33 @@ __device__ __forceinline__ void tri_mtv(T (&y)[C], const T *A, const T (&x)[C], 
   }
 }
 
-// Inclusive Kogge-Stone scan of affine maps s -> H s + t over the warp's lanes.
-// kForward: lane ln composes with lanes below it; otherwise with lanes above.
+// Inclusive Kogge-Stone scan of affine maps s -> H s + t over the warp's
+// lanes when the linear parts are known in advance: in round d lane ln
+// composes with lane ln - 2^d (forward) or ln + 2^d (backward), and
+// Hd[round] is the composed linear part lane ln holds at the start of that
+// round, precomputed from the operator.  Only the offsets move at run time:
+// t <- t + H t'  (4 FMAs per round instead of 12).
 template <typename T, bool kForward>
-__device__ __forceinline__ void warp_affine_scan(T (&H)[4], T (&t)[2], int ln) {
+__device__ __forceinline__ void warp_affine_scan_pre(T (&t)[2], const T *scan, int dir, int ln) {
 #pragma unroll
-  for (int d = 1; d < kWarp; d <<= 1) {
-    T h0, h1, h2, h3, t0, t1;
+  for (int d = 0; d < kScanRounds; ++d) {
+    const int off = 1 << d;
+    T t0, t1;
     if (kForward) {
-      h0 = __shfl_up_sync(kFull, H[0], d); h1 = __shfl_up_sync(kFull, H[1], d);
-      h2 = __shfl_up_sync(kFull, H[2], d); h3 = __shfl_up_sync(kFull, H[3], d);
-      t0 = __shfl_up_sync(kFull, t[0], d); t1 = __shfl_up_sync(kFull, t[1], d);
+      t0 = __shfl_up_sync(kFull, t[0], off);
+      t1 = __shfl_up_sync(kFull, t[1], off);
     } else {
-      h0 = __shfl_down_sync(kFull, H[0], d); h1 = __shfl_down_sync(kFull, H[1], d);
-      h2 = __shfl_down_sync(kFull, H[2], d); h3 = __shfl_down_sync(kFull, H[3], d);
-      t0 = __shfl_down_sync(kFull, t[0], d); t1 = __shfl_down_sync(kFull, t[1], d);
+      t0 = __shfl_down_sync(kFull, t[0], off);
+      t1 = __shfl_down_sync(kFull, t[1], off);
     }
-    bool take = kForward ? (ln >= d) : (ln + d < kWarp);
+    const bool take = kForward ? (ln >= off) : (ln + off < kWarp);
     if (take) {
-      // (H, t) o (H', t') = (H H', t + H t')
-      T nt0 = fma(H[0], t0, fma(H[1], t1, t[0]));
-      T nt1 = fma(H[2], t0, fma(H[3], t1, t[1]));
-      T n0 = fma(H[0], h0, H[1] * h2);
-      T n1 = fma(H[0], h1, H[1] * h3);
-      T n2 = fma(H[2], h0, H[3] * h2);
-      T n3 = fma(H[2], h1, H[3] * h3);
-      t[0] = nt0; t[1] = nt1;
-      H[0] = n0; H[1] = n1; H[2] = n2; H[3] = n3;
+      const T h0 = scan[scan_index(dir, d, 0, ln)], h1 = scan[scan_index(dir, d, 1, ln)];
+      const T h2 = scan[scan_index(dir, d, 2, ln)], h3 = scan[scan_index(dir, d, 3, ln)];
+      const T n0 = fma(h0, t0, fma(h1, t1, t[0]));
+      const T n1 = fma(h2, t0, fma(h3, t1, t[1]));
+      t[0] = n0;
+      t[1] = n1;
     }
   }
 }
@@ -172,8 +180,9 @@ __device__ __forceinline__ void warp_affine_scan(T (&H)[4], T (&t)[2], int ln) {
 //   scale     h_i = g_i dinv_i
 //   backward  x_i = h_i - a_{i+1} x_{i+1} - b_{i+2} x_{i+2}
 // Each lane runs its chunk from a zero incoming state, a warp scan of the
-// chunks' 2x2 affine maps (precomputed linear parts in `scan`) gives every
-// chunk's true incoming state, and the chunk is run again from it.
+// chunks' 2x2 affine maps (linear parts and their compositions precomputed
+// in `scan`) gives every chunk's true incoming state, and the chunk is run
+// again from it.
 template <typename T, int C>
 __device__ __forceinline__ void penta_solve(T (&x)[C], const T (&r)[C], const T *fac, const T *scan,
                                             int p, int ln) {
@@ -193,10 +202,8 @@ __device__ __forceinline__ void penta_solve(T (&x)[C], const T (&r)[C], const T 
     s1 = s2;
     s2 = g;
   }
-  T H[4], t[2] = {s1, s2};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) H[k] = scan[ln * kScanWords + k];
-  warp_affine_scan<T, true>(H, t, ln);
+  T t[2] = {s1, s2};
+  warp_affine_scan_pre<T, true>(t, scan, 0, ln);
   s1 = __shfl_up_sync(kFull, t[0], 1);
   s2 = __shfl_up_sync(kFull, t[1], 1);
   if (ln == 0) { s1 = 0; s2 = 0; }
@@ -227,10 +234,8 @@ __device__ __forceinline__ void penta_solve(T (&x)[C], const T (&r)[C], const T 
     s2 = s1;
     s1 = xi;
   }
-  T Hb[4], tb[2] = {s1, s2};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Hb[k] = scan[ln * kScanWords + 4 + k];
-  warp_affine_scan<T, false>(Hb, tb, ln);
+  T tb[2] = {s1, s2};
+  warp_affine_scan_pre<T, false>(tb, scan, 1, ln);
   s1 = __shfl_down_sync(kFull, tb[0], 1);
   s2 = __shfl_down_sync(kFull, tb[1], 1);
   if (ln == kWarp - 1) { s1 = 0; s2 = 0; }

@@ -112,18 +112,33 @@ __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long 
   }
 }
 
+// y -= sum_{i < m} c[i] X_i, and the CTA's partial sum of the new y^2 into
+// partial[blockIdx.x] (fixed order), for the norm of the orthogonalised vector
+__global__ void __launch_bounds__(kDotThreads) k_multi_axpy_norm(double *y, const double *__restrict__ X, long long ldx,
+                                                                 const double *__restrict__ c, int m, long long len,
+                                                                 double *partial) {
+  __shared__ double cs[512];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
+  __syncthreads();
+  double sq = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+#pragma unroll 8
+    for (int i = 0; i < m; ++i) acc = fma(cs[i], X[i * ldx + idx], acc);
+    const double v = y[idx] - acc;
+    y[idx] = v;
+    sq = fma(v, v, sq);
+  }
+  const double s = block_sum(sq);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 // y[i] += x[i], i < m
 __global__ void k_add_inplace(double *y, const double *__restrict__ x, int m, const int *gate = nullptr) {
   if (gate && *gate == 0) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) y[i] += x[i];
-}
-
-// DGKS test (Daniel, Gragg, Kaufman, Stewart 1976): a second Gram-Schmidt
-// pass is needed when the projection removed more than half of |w|^2,
-// i.e. |w_after|^2 < |w_before|^2 / 2.  gate[0] = 1 asks for it.
-__global__ void k_dgks_gate(const double *before2, const double *after2, int *gate) {
-  gate[0] = (after2[0] < 0.5 * before2[0]) ? 1 : 0;
 }
 
 // y = x * s[0]

@@ -293,30 +293,30 @@ void read_scal(mg_handle *h, const mg_handle::Krylov &K, cudaStream_t s) {
   ck(cudaStreamSynchronize(s));
 }
 
-// Classical Gram-Schmidt of w against V_0..V_j with the DGKS criterion: a
-// second pass runs (device-gated, no host round trip) only when the first
-// removed more than half of |w|^2.  h (j+1) and |w|^2 (nrm2) on the device.
+// Classical Gram-Schmidt twice (CGS2) of w against V_0..V_j: h (j+1) and
+// |w|^2 (nrm2, accumulated inside the second axpy) on the device.
 void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
                    cudaStream_t s) {
   const int m = j + 1;
-  multidot(h, w, len, 1, w, len, K.nrm2 + 1, 0, s);           // |w|^2 before
   multidot(h, V, len, m, w, len, K.h, 0, s);
   multi_axpy(h, w, V, len, K.h, m, -1.0, len, s);
-  multidot(h, w, len, 1, w, len, K.nrm2, 0, s);               // |w|^2 after
+  multidot(h, V, len, m, w, len, K.h + 512, 0, s);
+  const int G = grid_for(len, kDotThreads);
   {
-    Bracket br(h, CAT_SMALL, s);
-    k_dgks_gate<<<1, 1, 0, s>>>(K.nrm2 + 1, K.nrm2, h->flag + 2);
+    Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * (m + 1) * len);
+    k_multi_axpy_norm<<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial);
     ck_launch();
   }
-  const int *gate = h->flag + 2;
-  multidot(h, V, len, m, w, len, K.h + 512, 0, s, gate);
-  multi_axpy(h, w, V, len, K.h + 512, m, -1.0, len, s, gate);
   {
     Bracket br(h, CAT_SMALL, s);
-    k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m, gate);
+    k_reduce_partials<<<1, 128, 0, s>>>(h->partial, G, 1, K.nrm2, 0);
     ck_launch();
   }
-  multidot(h, w, len, 1, w, len, K.nrm2, 0, s, gate);         // |w|^2 after the second pass
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m);
+    ck_launch();
+  }
 }
 
 // ||x|| into K.scal[0], 1/||x|| into K.scal[1]
@@ -867,7 +867,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
       v.sZ = zsz;
       if (layout == MG_LAYOUT_TRIDIAG) {
         double *fac = h->mem.alloc<double>((size_t)nl * 3 * p);
-        double *scan = h->mem.alloc<double>((size_t)nl * kWarp * kScanWords);
+        double *scan = h->mem.alloc<double>((size_t)nl * kScanPerBlock);
         k_factor_tri<<<grid_for(nl, 64, 1 << 20), 64, 0, s>>>(nl, p, C, N, msz, Z, zsz, fac, scan, h->flag);
         ck_launch();
         v.fac = fac;
@@ -937,7 +937,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
         f.sZ = v.sZ;
         f.fac = to_float_copy(h, v.fac, (long long)nl * v.sFac, s);
         f.sFac = v.sFac;
-        f.scan = layout == MG_LAYOUT_TRIDIAG ? to_float_copy(h, v.scan, (long long)nl * kWarp * kScanWords, s)
+        f.scan = layout == MG_LAYOUT_TRIDIAG ? to_float_copy(h, v.scan, (long long)nl * kScanPerBlock, s)
                                              : nullptr;
         if (l == L - 1) {
           lev.f.Cu = to_float_copy(h, lev.d.Cu, (long long)nl * p * p, s);

@@ -79,31 +79,56 @@ __global__ void k_factor_tri(int n, int p, int C, const double *__restrict__ N, 
   }
   if (bad) atomicExch(status, 1);
   // chunk maps: forward (g_{lo-2}, g_{lo-1}) -> (g_{hi-2}, g_{hi-1}),
-  //             backward (x_hi, x_{hi+1}) -> (x_lo, x_{lo+1})
-  double *sc = scan + (long long)j * kWarp * kScanWords;
-  for (int ln = 0; ln < kWarp; ++ln) {
-    for (int col = 0; col < 2; ++col) {
-      double s1 = (col == 0) ? 1.0 : 0.0, s2 = (col == 0) ? 0.0 : 1.0;
-      for (int e = 0; e < C; ++e) {
-        int i = ln * C + e;
-        double ai = (i < p) ? a[i] : 0.0, bi = (i < p) ? bb[i] : 0.0;
-        double g = -ai * s2 - bi * s1;
-        s1 = s2;
-        s2 = g;
+  //             backward (x_hi, x_{hi+1}) -> (x_lo, x_{lo+1});
+  // then the Kogge-Stone compositions each lane holds at the start of every
+  // round of the two warp scans (see warp_affine_scan_pre)
+  double *sc = scan + (long long)j * kScanPerBlock;
+  for (int dir = 0; dir < 2; ++dir) {
+    double H[kWarp][4];
+    for (int ln = 0; ln < kWarp; ++ln) {
+      for (int col = 0; col < 2; ++col) {
+        double s1 = (col == 0) ? 1.0 : 0.0, s2 = (col == 0) ? 0.0 : 1.0;
+        if (dir == 0) {
+          for (int e = 0; e < C; ++e) {
+            int i = ln * C + e;
+            double ai = (i < p) ? a[i] : 0.0, bi = (i < p) ? bb[i] : 0.0;
+            double g = -ai * s2 - bi * s1;
+            s1 = s2;
+            s2 = g;
+          }
+        } else {
+          for (int e = C - 1; e >= 0; --e) {
+            int i = ln * C + e;
+            double na = (i + 1 < p) ? a[i + 1] : 0.0, nb = (i + 2 < p) ? bb[i + 2] : 0.0;
+            double xi = -na * s1 - nb * s2;
+            s2 = s1;
+            s1 = xi;
+          }
+        }
+        H[ln][0 + col] = s1;  // row-major: out0 = H0 in0 + H1 in1
+        H[ln][2 + col] = s2;
       }
-      sc[ln * kScanWords + 0 + col] = s1;
-      sc[ln * kScanWords + 2 + col] = s2;
-      s1 = (col == 0) ? 1.0 : 0.0;
-      s2 = (col == 0) ? 0.0 : 1.0;
-      for (int e = C - 1; e >= 0; --e) {
-        int i = ln * C + e;
-        double na = (i + 1 < p) ? a[i + 1] : 0.0, nb = (i + 2 < p) ? bb[i + 2] : 0.0;
-        double xi = -na * s1 - nb * s2;
-        s2 = s1;
-        s1 = xi;
+    }
+    for (int d = 0; d < kScanRounds; ++d) {
+      const int off = 1 << d;
+      for (int ln = 0; ln < kWarp; ++ln)
+        for (int k = 0; k < 4; ++k) sc[scan_index(dir, d, k, ln)] = H[ln][k];
+      // compose: lane ln takes lane ln -/+ off (update from the top / bottom so that sources are unmodified)
+      double Hn[kWarp][4];
+      for (int ln = 0; ln < kWarp; ++ln) {
+        const int src = dir == 0 ? ln - off : ln + off;
+        if (src < 0 || src >= kWarp) {
+          for (int k = 0; k < 4; ++k) Hn[ln][k] = H[ln][k];
+        } else {
+          const double *A = H[ln], *B = H[src];
+          Hn[ln][0] = A[0] * B[0] + A[1] * B[2];
+          Hn[ln][1] = A[0] * B[1] + A[1] * B[3];
+          Hn[ln][2] = A[2] * B[0] + A[3] * B[2];
+          Hn[ln][3] = A[2] * B[1] + A[3] * B[3];
+        }
       }
-      sc[ln * kScanWords + 4 + col] = s1;
-      sc[ln * kScanWords + 6 + col] = s2;
+      for (int ln = 0; ln < kWarp; ++ln)
+        for (int k = 0; k < 4; ++k) H[ln][k] = Hn[ln][k];
     }
   }
 }
@@ -156,7 +181,7 @@ __global__ void __launch_bounds__(128) k_chain_mats_tri(LevelView<double> L, dou
   const int j = 1 + (int)(w / p), col = (int)(w % p);
   const double *N = L.N + j * L.sN, *V = L.V + j * L.sV;
   const double *fac = L.fac + j * L.sFac;
-  const double *scan = L.scan + (long long)j * kWarp * kScanWords;
+  const double *scan = L.scan + (long long)j * kScanPerBlock;
   double e[C], t[C], s[C], o[C];
 #pragma unroll
   for (int k = 0; k < C; ++k) e[k] = (ln * C + k == col) ? 1.0 : 0.0;

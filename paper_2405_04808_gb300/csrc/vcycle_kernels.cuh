@@ -32,7 +32,7 @@ __device__ __forceinline__ void local_solve_tri(const LevelView<T> &L, int j,
   }
   const T *N = L.N + j * L.sN, *V = L.V + j * L.sV, *Z = L.Z + j * L.sZ;
   const T *fac = L.fac + j * L.sFac;
-  const T *scan = L.scan + (long long)j * kWarp * kScanWords;
+  const T *scan = L.scan + (long long)j * kScanPerBlock;
   T rhs[C];
   tri_mv<T, C, false>(rhs, N, ru, p, ln, T(1));
   tri_mv<T, C, true>(rhs, Z, rz, p, ln, T(1));

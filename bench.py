@@ -161,11 +161,11 @@ def roofline(prof, dominant, precision):
             "achieved_tflops": round(fl, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", **common}
 
 
-def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stream, world, want_e2e):
+def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stream, world, want_e2e, levels=None):
     """Set up, warm up, one fully profiled solve, then `steps` timed solves."""
     prec = P.MG_PRECISION_FP64 if precision == "fp64" else P.MG_PRECISION_FP32
     t0 = time.perf_counter()
-    h = P.mg_setup(prob, levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=prec,
+    h = P.mg_setup(prob, levels=levels or wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=prec,
                    omega=omega, stream=stream)
     torch.cuda.synchronize(dev)
     setup_ms = (time.perf_counter() - t0) * 1e3
@@ -255,14 +255,21 @@ def run_native(args):
                    world, True)
     variants = {}
     if not args.no_variants:
-        for name, prec, om in (("fp32_vcycle", "fp32", args.omega), ("omega0.7_fp64", "fp64", 0.7),
-                               ("omega0.7_fp32_vcycle", "fp32", 0.7)):
-            if prec == args.precision and om == args.omega:
+        # (name, precision, omega, levels): the mixed-precision V-cycle, relaxed sweeps (an option
+        # outside the paper), and the paper's serial baseline of Sec. 6.3 (SGS-GMRES, no multigrid),
+        # whose block Gauss-Seidel chains run here as a parallel scan in time
+        for name, prec, om, lv in (("fp32_vcycle", "fp32", args.omega, None), ("omega0.7_fp64", "fp64", 0.7, None),
+                                   ("omega0.7_fp32_vcycle", "fp32", 0.7, None),
+                                   ("sgs_gmres_no_multigrid", "fp64", 1.0, 1)):
+            if prec == args.precision and om == args.omega and lv is None:
                 continue
-            v = measure(P, torch, prob, wl, args, prec, om, max(1, min(args.steps, 3)), 1, dev, stream, world, False)
+            v = measure(P, torch, prob, wl, args, prec, om, max(1, min(args.steps, 3)), 1, dev, stream, world, False,
+                        levels=lv)
             variants[name] = {"value": round(v["value"], 4), "unit": UNIT, "ms_per_step": round(v["ms_per_step"], 3),
                               "fgmres_iters": v["iters"][0], "true_relres": v["true_relres"],
-                              "precision": prec, "omega": om,
+                              "precision": prec, "omega": om, "levels": lv or wl["levels"],
+                              "coarse_iters_per_vcycle": round(v["coarse_iters_per_vcycle"], 3),
+                              "setup_ms": round(v["setup_ms"], 1),
                               "dominant_kernel": v["dominant"], "roofline_frac": v["roofline"].get("frac")}
     out = {
         "metric": METRIC, "value": round(main["value"], 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,

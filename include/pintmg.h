@@ -83,6 +83,16 @@ typedef struct {
   const double *Ju_cur, *Ju_prev, *Jz_cur, *Jz_prev;
 } mg_problem;
 
+/* Block fixed-point iterations of Sec. 5.3.4 / Table 1, one step from zero,
+ * as the right preconditioner of the coarse GMRES (with levels = 1: of GMRES
+ * on the whole system, the paper's serial baseline of Sec. 6.3). */
+typedef enum {
+  MG_COARSE_SGS = 0,     /* [(D + L) D^-1 (D + L^T)]^-1, the paper's coarse solver */
+  MG_COARSE_JACOBI = 1,  /* D^-1 */
+  MG_COARSE_FGS = 2,     /* (D + L)^-1 */
+  MG_COARSE_BGS = 3      /* (D + L^T)^-1 */
+} mg_coarse_precond;
+
 typedef struct {
   int levels;             /* V-cycle levels Lv >= 1; n must be divisible by 2^(Lv-1); Lv = 1 is SGS-GMRES alone */
   int nu_pre, nu_post;    /* block-Jacobi sweeps before / after the coarse correction (>= 0) */
@@ -92,6 +102,7 @@ typedef struct {
   int end_rule;           /* last fine point of linear interpolation: 0 repeats the last coarse value, 1 uses 0 */
   int precision;          /* mg_precision */
   double omega;           /* block-Jacobi relaxation weight, 0 < omega <= 1; the paper's sweep (Eq. jacobi-aj) is omega = 1 */
+  int coarse_precond;     /* mg_coarse_precond: preconditioner of the coarse GMRES (the paper's is SGS) */
 } mg_options;
 
 typedef struct {
@@ -104,7 +115,8 @@ typedef struct {
 
 typedef struct mg_handle mg_handle;  /* opaque; owns every device buffer */
 
-/* Fill *opts with the defaults: levels 2, 1/1 sweeps, coarse 1e-3 / 50, tolerance mode, end rule 0, FP64, omega 1. */
+/* Fill *opts with the defaults: levels 2, 1/1 sweeps, coarse 1e-3 / 50, tolerance mode, end rule 0, FP64,
+ * omega 1, SGS coarse preconditioner. */
 void mg_default_options(mg_options *opts);
 
 /*

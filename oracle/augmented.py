@@ -309,15 +309,37 @@ class Level:
         return x
 
 
-def jacobi_sweep(level: Level, b: np.ndarray, y: np.ndarray) -> np.ndarray:
-    """y^l = D^-1 [ b - (L + L^T) y^{l-1} ]   (Eq. jacobi-aj)."""
-    return level.D_solve(b - (level.L @ y + level.U @ y))
+def jacobi_sweep(level: Level, b: np.ndarray, y: np.ndarray, omega: float = 1.0) -> np.ndarray:
+    """y^l = D^-1 [ b - (L + L^T) y^{l-1} ]   (Eq. jacobi-aj).
+
+    omega != 1 is a relaxation weight the paper does not use (an option of
+    this implementation): y^l = y^{l-1} + omega (D^-1 [...] - y^{l-1}).
+    """
+    ynew = level.D_solve(b - (level.L @ y + level.U @ y))
+    if omega == 1.0:
+        return ynew
+    return y + omega * (ynew - y)
 
 
 def sgs_apply(level: Level, r: np.ndarray) -> np.ndarray:
     """[(D + L) D^-1 (D + L^T)]^-1 r = (D + L^T)^-1 D (D + L)^-1 r   (Sec. 5.3.4)."""
     w = level.DL_solve(r)
     return level.DU_solve(level.D @ w)
+
+
+def fixed_point_preconditioner(level: Level, kind: str):
+    """The block fixed-point iterations of Sec. 5.3.4 / Table 1 as preconditioners:
+    one step from zero of Jacobi D^-1, forward Gauss-Seidel (D + L)^-1,
+    backward Gauss-Seidel (D + L^T)^-1, or symmetric Gauss-Seidel."""
+    if kind == "sgs":
+        return lambda r: sgs_apply(level, r)
+    if kind == "jacobi":
+        return level.D_solve
+    if kind == "fgs":
+        return level.DL_solve
+    if kind == "bgs":
+        return level.DU_solve
+    raise ValueError(kind)
 
 
 # --------------------------------------------------------------------------
@@ -424,6 +446,8 @@ class MGOptions:
     coarse_maxit: int = 50
     coarse_fixed_iters: int = 0
     end_rule: int = 0
+    omega: float = 1.0
+    coarse_precond: str = "sgs"     # the paper's; "jacobi", "fgs", "bgs" are Table 1's alternatives
 
 
 class Hierarchy:
@@ -455,7 +479,7 @@ class Hierarchy:
         """GMRES right-preconditioned by SGS, x0 = 0, relative tolerance 1e-3 (Sec. 5.3.4)."""
         level = self.levels[lv]
         o = self.opts
-        res = fgmres(lambda v: level.At @ v, lambda v: sgs_apply(level, v), r,
+        res = fgmres(lambda v: level.At @ v, fixed_point_preconditioner(level, o.coarse_precond), r,
                      rtol=o.coarse_rtol, maxit=o.coarse_maxit, fixed_iters=o.coarse_fixed_iters)
         self.coarse_iters.append(res.iters)
         return res.x
@@ -468,12 +492,12 @@ class Hierarchy:
             return self.coarse_solve(lv, b)
         y = np.zeros_like(b)
         for _ in range(o.nu_pre):
-            y = jacobi_sweep(level, b, y)
+            y = jacobi_sweep(level, b, y, o.omega)
         r = self.R[lv] @ (b - level.At @ y)
         e = self.vcycle(lv + 1, r)
         y = y + self.P[lv] @ e
         for _ in range(o.nu_post):
-            y = jacobi_sweep(level, b, y)
+            y = jacobi_sweep(level, b, y, o.omega)
         return y
 
     # ABI-shaped entry points (type-major vectors)

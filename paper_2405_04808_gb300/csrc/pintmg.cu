@@ -452,29 +452,44 @@ void run_scan(mg_handle *h, const std::vector<T *> &P, const T *xhat, T *out, T 
 }
 
 // ---------------------------------------------------------------------------
-// SGS on the coarsest level (precision T): y = [(D+L) D^-1 (D+L^T)]^-1 r
+// The coarse preconditioner on the coarsest level (precision T):
+// SGS y = [(D+L) D^-1 (D+L^T)]^-1 r, or one of Table 1's alternatives.
 
 template <typename T>
 void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
   LevelData<T> &d = ldata<T>(lev);
   const int n = lev.n, p = h->p;
-  // w = D^-1 r; forward chain u_j = uhat_j - Cu_j u_{j-1}
-  launch_block_solve<T>(h, d.view, r, nullptr, nullptr, d.sgs_w, s);
+  const int kind = h->opts.coarse_precond;
+  if (kind == MG_COARSE_JACOBI) {  // D^-1 r
+    launch_block_solve<T>(h, d.view, r, nullptr, nullptr, y, s);
+    return;
+  }
   const int threads = std::max(32, ((p + 31) / 32) * 32);
   const size_t shm = (size_t)p * sizeof(T);
   const bool cluster = h->layout == MG_LAYOUT_TRIDIAG && p >= 32 && h->use_cluster;
   const bool scan = h->use_scan && (n == 1 || !d.scanF.empty());
-  if (scan) {
-    run_scan<T>(h, d.scanF, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, d.scan_tmp, n, p, 0, s);
-  } else if (n >= 1) {
-    Bracket br(h, CAT_CHAIN, s);
-    if (!cluster || !launch_chain_cluster<T, true>(h, d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p, s)) {
-      k_chain_forward<T><<<1, threads, shm, s>>>(d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p);
+  const bool forward = kind != MG_COARSE_BGS;
+  if (forward) {
+    // w = D^-1 r; forward chain u_j = uhat_j - Cu_j u_{j-1}
+    launch_block_solve<T>(h, d.view, r, nullptr, nullptr, d.sgs_w, s);
+    if (scan) {
+      run_scan<T>(h, d.scanF, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, d.scan_tmp, n, p, 0, s);
+    } else if (n >= 1) {
+      Bracket br(h, CAT_CHAIN, s);
+      if (!cluster || !launch_chain_cluster<T, true>(h, d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p, s)) {
+        k_chain_forward<T><<<1, threads, shm, s>>>(d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p);
+      }
+      ck_launch();
     }
-    ck_launch();
+    if (kind == MG_COARSE_FGS) {  // w = (D + L)^-1 r
+      launch_block_solve<T>(h, d.view, r, d.chainU, nullptr, y, s);
+      return;
+    }
   }
-  // yhat = D^-1 (r - L w): only mu(yhat) is needed by the backward chain
-  launch_block_solve<T>(h, d.view, r, d.chainU, nullptr, d.sgs_w, s);
+  // yhat = D^-1 (r - L w) (SGS) or D^-1 r (backward Gauss-Seidel alone):
+  // only mu(yhat) is needed by the backward chain
+  const T *fwd = forward ? d.chainU : nullptr;
+  launch_block_solve<T>(h, d.view, r, fwd, nullptr, d.sgs_w, s);
   if (scan) {
     run_scan<T>(h, d.scanB, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, d.scan_tmp, n, p, 1, s);
   } else if (n >= 1) {
@@ -485,7 +500,7 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
     ck_launch();
   }
   // y = D^-1 (r - L w - L^T y)
-  launch_block_solve<T>(h, d.view, r, d.chainU, d.chainM, y, s);
+  launch_block_solve<T>(h, d.view, r, fwd, d.chainM, y, s);
 }
 
 // precondition a coarse FP64 vector with SGS in precision T
@@ -690,6 +705,7 @@ void mg_default_options(mg_options *o) {
   o->end_rule = 0;
   o->precision = MG_PRECISION_FP64;
   o->omega = 1.0;
+  o->coarse_precond = MG_COARSE_SGS;
 }
 
 const char *mg_status_string(int st) {
@@ -779,6 +795,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (O->end_rule != 0 && O->end_rule != 1) return MG_ERR_ARG;
   if (O->precision != MG_PRECISION_FP64 && O->precision != MG_PRECISION_FP32) return MG_ERR_ARG;
   if (!(O->omega > 0.0 && O->omega <= 1.0)) return MG_ERR_ARG;
+  if (O->coarse_precond < MG_COARSE_SGS || O->coarse_precond > MG_COARSE_BGS) return MG_ERR_ARG;
   if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;

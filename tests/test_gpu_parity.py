@@ -215,3 +215,22 @@ def test_sgs_chain_variants_dense(P, chain, monkeypatch):
         assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) <= VCYCLE_RTOL
     finally:
         P.mg_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["jacobi", "fgs", "bgs", "sgs"])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_table1_coarse_preconditioners(P, kind, levels):
+    """Every coarse preconditioner of Table 1 matches the oracle's inside a V-cycle
+    (levels = 2) and as GMRES preconditioner on the whole system (levels = 1)."""
+    prob = W.burgers(nx=20, n=16, seed=171)
+    opts = dict(levels=levels, nu_pre=2, nu_post=2, coarse_fixed_iters=3)
+    h = P.mg_setup(prob, coarse_precond=kind, **opts)
+    try:
+        rd = _dev(prob.b)
+        yd = torch.empty_like(rd)
+        assert P.mg_vcycle(h, rd.data_ptr(), yd.data_ptr(), 0) == P.MG_OK
+        torch.cuda.synchronize()
+        yo = O.Hierarchy(prob, O.MGOptions(coarse_precond=kind, **opts)).precondition(prob.b)
+        assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) <= VCYCLE_RTOL
+    finally:
+        P.mg_destroy(h)

@@ -119,6 +119,18 @@ def test_sgs_matches_dense_definition():
     assert np.allclose(got, want, rtol=0, atol=1e-10 * np.max(np.abs(want)))
 
 
+@pytest.mark.parametrize("kind", ["jacobi", "fgs", "bgs"])
+def test_table1_preconditioners_match_dense_definitions(kind):
+    """Jacobi D^-1, forward GS (D+L)^-1, backward GS (D+L^T)^-1 (Sec. 5.3.4, Table 1)."""
+    prob = W.burgers(nx=5, n=10, seed=10)
+    lev = O.Level(O.raw_from_problem(prob))
+    D, L = lev.D.toarray(), lev.L.toarray()
+    M = {"jacobi": D, "fgs": D + L, "bgs": D + L.T}[kind]
+    r = np.random.default_rng(7).standard_normal(D.shape[0])
+    got = O.fixed_point_preconditioner(lev, kind)(r)
+    assert np.allclose(got, np.linalg.solve(M, r), rtol=0, atol=1e-10 * np.max(np.abs(got)))
+
+
 def test_sgs_exact_without_control_coupling():
     """With d_z f = 0 the block (D^-1)_{uu} vanishes, so L D^-1 L^T = 0 and SGS is A~^-1."""
     prob = W.vdp(n=10, seed=9)

@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--maxit", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision / relaxed-sweep variants")
+    ap.add_argument("--host-loops", action="store_true",
+                    help="time host-driven Krylov loops instead of one CUDA graph per solve")
     ap.add_argument("--allow-partial", action="store_true",
                     help="accept solves stopped by --maxit (bounded profiler captures only)")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
@@ -162,39 +164,48 @@ def roofline(prof, dominant, precision):
 
 
 def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stream, world, want_e2e, levels=None):
-    """Set up, warm up, one fully profiled solve, then `steps` timed solves."""
+    """Per-kernel shares and the roofline from one event-bracketed, host-driven
+    solve (kernels inside a captured graph cannot be bracketed); then warm-up,
+    `steps` timed solves and the end-to-end solves in the timed mode
+    (default: one CUDA graph per solve with device-side loops)."""
     prec = P.MG_PRECISION_FP64 if precision == "fp64" else P.MG_PRECISION_FP32
-    t0 = time.perf_counter()
-    h = P.mg_setup(prob, levels=levels or wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=prec,
-                   omega=omega, stream=stream)
-    torch.cuda.synchronize(dev)
-    setup_ms = (time.perf_counter() - t0) * 1e3
-    n = prob.size
+    lv = levels or wl["levels"]
     b = torch.tensor(prob.b, device=dev)
     x = torch.empty_like(b)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def solve(bp, xp):
+    def setup(device_loops):
+        return P.mg_setup(prob, levels=lv, nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=prec,
+                          omega=omega, device_loops=device_loops, stream=stream)
+
+    def solve(h, bp, xp):
         code, info = P.fgmres_solve(h, bp, xp, RTOL, args.maxit, args.restart, stream)
         if code != P.MG_OK and not (args.allow_partial and code == P.MG_NOT_CONVERGED):
             raise RuntimeError(f"fgmres_solve: {P.mg_status_string(code)} (iters {info.iters}, "
                                f"relres {info.relres:.2e}, true {info.true_relres:.2e})")
         return info
 
+    # 1. profiled, host-driven solve: shares of every kernel category, the dominant one's roofline
+    hp = setup(False)
+    try:
+        solve(hp, b.data_ptr(), x.data_ptr())
+        P.mg_profile_enable(hp, P.PROFILE_ALL)
+        flush.zero_()
+        solve(hp, b.data_ptr(), x.data_ptr())
+        shares = P.mg_profile_read(hp)
+        P.mg_profile_enable(hp, 0)
+    finally:
+        P.mg_destroy(hp)
+    dominant = max(shares, key=lambda k: shares[k][0])
+    # 2. timed solves
+    t0 = time.perf_counter()
+    h = setup(not args.host_loops)
+    torch.cuda.synchronize(dev)
+    setup_ms = (time.perf_counter() - t0) * 1e3
     try:
         for _ in range(warmup):
             flush.zero_()
-            solve(b.data_ptr(), x.data_ptr())
-        # one fully profiled solve: per-category kernel shares
-        P.mg_profile_enable(h, P.PROFILE_ALL)
-        flush.zero_()
-        solve(b.data_ptr(), x.data_ptr())
-        shares = P.mg_profile_read(h)
-        P.mg_profile_enable(h, 0)
-        dominant = max(shares, key=lambda k: shares[k][0])
-        # timed region: inputs resident in HBM, L2 flushed before each step,
-        # only the dominant category bracketed by events on the library's stream
-        P.mg_profile_enable(h, 1 << P.PROFILE_CATEGORIES.index(dominant))
+            solve(h, b.data_ptr(), x.data_ptr())
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
             torch.distributed.barrier()
@@ -205,12 +216,10 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
             for i in range(steps):
                 flush.zero_()
                 ev[i][0].record()
-                infos.append(solve(b.data_ptr(), x.data_ptr()))
+                infos.append(solve(h, b.data_ptr(), x.data_ptr()))
                 ev[i][1].record()
             torch.cuda.synchronize(dev)
         launches = P.mg_launch_count(h) - launches0
-        prof = P.mg_profile_read(h)
-        P.mg_profile_enable(h, 0)
         if world > 1:
             torch.distributed.barrier()
         local_ms = sum(a.elapsed_time(bb) for a, bb in ev)
@@ -220,18 +229,19 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
                "iters": [i.iters for i in infos], "true_relres": max(i.true_relres for i in infos),
                "coarse_iters_per_vcycle": sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)),
                "setup_ms": setup_ms, "launches": launches, "shares": shares, "dominant": dominant,
-               "roofline": roofline(prof, dominant, precision), "clocks": clk.summary()}
+               "roofline": roofline(shares, dominant, precision), "clocks": clk.summary()}
         if want_e2e:
             # end to end through the public API with pinned host buffers
             bh = torch.tensor(prob.b).pin_memory()
             xh = torch.empty_like(bh).pin_memory()
+            solve(h, bh.data_ptr(), xh.data_ptr())   # capture for the staging buffers (not timed)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             for _ in range(steps):
-                solve(bh.data_ptr(), xh.data_ptr())
+                solve(h, bh.data_ptr(), xh.data_ptr())
             e2e_value = RP.job_throughput(time.perf_counter() - t0, steps, world, device=dev)
             out["e2e"] = {"value": round(e2e_value, 4), "unit": UNIT,
-                          "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+                          "h2d_bytes_per_step": 8 * prob.size, "d2h_bytes_per_step": 8 * prob.size}
         return out
     finally:
         P.mg_destroy(h)
@@ -280,6 +290,9 @@ def run_native(args):
                    "levels": wl["levels"], "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
                    "unknowns": prob.size, "rtol": RTOL, "restart": args.restart, "precision": args.precision,
                    "omega": args.omega, "l2": "flushed (512 MB write) before every timed step",
+                   "solve": "host-driven loops" if args.host_loops else
+                            "one CUDA graph per solve (FGMRES and coarse GMRES loops as conditional nodes)",
+                   "roofline_source": "event-bracketed kernels of one host-driven solve of the same system",
                    "parallelism": f"replicas{world}"},
         "fgmres_iters": main["iters"], "true_relres": main["true_relres"],
         "coarse_iters_per_vcycle": round(main["coarse_iters_per_vcycle"], 3),

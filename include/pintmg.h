@@ -103,6 +103,10 @@ typedef struct {
   int precision;          /* mg_precision */
   double omega;           /* block-Jacobi relaxation weight, 0 < omega <= 1; the paper's sweep (Eq. jacobi-aj) is omega = 1 */
   int coarse_precond;     /* mg_coarse_precond: preconditioner of the coarse GMRES (the paper's is SGS) */
+  int device_loops;       /* 1: each fgmres_solve runs as one CUDA graph whose FGMRES and coarse-GMRES loops are
+                             conditional nodes decided on the device (one host read-back per solve);
+                             0: loops driven from the host (a few scalars read back per iteration).
+                             Same arithmetic either way. */
 } mg_options;
 
 typedef struct {
@@ -116,7 +120,7 @@ typedef struct {
 typedef struct mg_handle mg_handle;  /* opaque; owns every device buffer */
 
 /* Fill *opts with the defaults: levels 2, 1/1 sweeps, coarse 1e-3 / 50, tolerance mode, end rule 0, FP64,
- * omega 1, SGS coarse preconditioner. */
+ * omega 1, SGS coarse preconditioner, device loops. */
 void mg_default_options(mg_options *opts);
 
 /*

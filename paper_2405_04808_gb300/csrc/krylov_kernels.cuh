@@ -47,10 +47,13 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_partial(const double *
 template <int VB>
 __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *__restrict__ V, long long ldv, int m,
                                                                   const double *__restrict__ w, long long len,
-                                                                  double *partial, const int *gate) {
+                                                                  double *partial, const int *gate,
+                                                                  const int *m_dev = nullptr) {
   if (gate && *gate == 0) return;
+  if (m_dev) m = *m_dev;  // vector count held on the device (graph-captured solves)
   __shared__ double red[kDotThreads / kWarp][VB];
   const int vb = blockIdx.y * VB;
+  if (vb >= m) return;
   const int nv = min(VB, m - vb);
   double acc[VB];
 #pragma unroll
@@ -82,8 +85,9 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *
 
 // out[i] (+)= sum_g partial[i * G + g], fixed order.  One warp per i.
 __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int m, double *out, int accumulate,
-                                  const int *gate = nullptr) {
+                                  const int *gate = nullptr, const int *m_dev = nullptr) {
   if (gate && *gate == 0) return;
+  if (m_dev) m = *m_dev;
   const int i = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const int ln = threadIdx.x & (kWarp - 1);
   if (i >= m) return;
@@ -98,8 +102,10 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int
 // (coefficients staged in shared memory; m <= 512; the vector loop is unrolled
 // so that several basis loads are in flight per thread)
 __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long ldx, const double *__restrict__ c,
-                             int m, double sign, long long len, const int *gate = nullptr) {
+                             int m, double sign, long long len, const int *gate = nullptr,
+                             const int *m_dev = nullptr) {
   if (gate && *gate == 0) return;
+  if (m_dev) m = *m_dev;
   __shared__ double cs[512];
   for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
@@ -116,7 +122,8 @@ __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long 
 // partial[blockIdx.x] (fixed order), for the norm of the orthogonalised vector
 __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_norm(double *y, const double *__restrict__ X, long long ldx,
                                                                  const double *__restrict__ c, int m, long long len,
-                                                                 double *partial) {
+                                                                 double *partial, const int *m_dev = nullptr) {
+  if (m_dev) m = *m_dev;
   __shared__ double cs[512];
   for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
@@ -135,14 +142,20 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_norm(double *y, cons
 }
 
 // y[i] += x[i], i < m
-__global__ void k_add_inplace(double *y, const double *__restrict__ x, int m, const int *gate = nullptr) {
+__global__ void k_add_inplace(double *y, const double *__restrict__ x, int m, const int *gate = nullptr,
+                              const int *m_dev = nullptr) {
   if (gate && *gate == 0) return;
+  if (m_dev) m = *m_dev;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) y[i] += x[i];
 }
 
-// y = x * s[0]
-__global__ void k_scale(double *y, const double *__restrict__ x, const double *__restrict__ s, long long len) {
+// y = x * s[0]; with idx non-null the destination is y + (idx[0] + shift) * len
+// (a basis slot chosen on the device); guard non-null and 0 skips the work.
+__global__ void k_scale(double *y, const double *__restrict__ x, const double *__restrict__ s, long long len,
+                        const int *idx = nullptr, int shift = 0, const int *guard = nullptr) {
+  if (guard && *guard == 0) return;
+  if (idx) y += (long long)(idx[0] + shift) * len;
   const double a = s[0];
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
        idx += (long long)gridDim.x * blockDim.x)
@@ -150,7 +163,8 @@ __global__ void k_scale(double *y, const double *__restrict__ x, const double *_
 }
 
 // scal[0] = sqrt(nrm2[0]); scal[1] = 1 / scal[0] (0 if zero)
-__global__ void k_norm_from_sq(const double *nrm2, double *scal) {
+__global__ void k_norm_from_sq(const double *nrm2, double *scal, const int *guard = nullptr) {
+  if (guard && *guard == 0) return;
   double b = sqrt(nrm2[0]);
   scal[0] = b;
   scal[1] = b > 0.0 ? 1.0 / b : 0.0;
@@ -160,8 +174,9 @@ __global__ void k_norm_from_sq(const double *nrm2, double *scal) {
 // Givens rotations, form rotation j, update g.  H is column-major with leading
 // dimension ldh.  scal: [0] |g_{j+1}|, [1] 1/h_{j+1,j}, [2] h_{j+1,j}.
 __global__ void k_arnoldi_step(int j, const double *__restrict__ h, const double *__restrict__ w2, double *H,
-                               int ldh, double *cs, double *sn, double *g, double *scal) {
+                               int ldh, double *cs, double *sn, double *g, double *scal, const int *j_dev = nullptr) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (j_dev) j = *j_dev;
   double *col = H + (long long)j * ldh;
   for (int i = 0; i <= j; ++i) col[i] = h[i];
   const double hj1 = sqrt(w2[0]);
@@ -190,13 +205,17 @@ __global__ void k_arnoldi_step(int j, const double *__restrict__ h, const double
 }
 
 // g = (beta, 0, ...), scal[0] = beta
-__global__ void k_arnoldi_init(const double *beta_scal, double *g, int m) {
+__global__ void k_arnoldi_init(const double *beta_scal, double *g, int m, const int *guard = nullptr) {
+  if (guard && *guard == 0) return;
   for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta_scal[0] : 0.0;
 }
 
 // y = R^-1 g for the leading k x k upper triangle of the rotated H, one CTA,
 // column-oriented: y_i = g_i / R_ii, then every g_r (r < i) -= R_ri y_i in parallel.
-__global__ void k_backsolve(int k, const double *__restrict__ H, int ldh, const double *__restrict__ g, double *y) {
+__global__ void k_backsolve(int k, const double *__restrict__ H, int ldh, const double *__restrict__ g, double *y,
+                            const int *k_dev = nullptr, const int *guard = nullptr) {
+  if (guard && *guard == 0) return;
+  if (k_dev) k = *k_dev;
   extern __shared__ double gs[];
   for (int r = threadIdx.x; r < k; r += blockDim.x) gs[r] = g[r];
   __syncthreads();
@@ -208,6 +227,89 @@ __global__ void k_backsolve(int k, const double *__restrict__ H, int ldh, const 
     for (int r = threadIdx.x; r < i; r += blockDim.x) gs[r] = fma(-col[r], yi, gs[r]);
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Device-side control of the Krylov loops for graph-captured solves: the
+// loop state lives on the device and a control kernel sets the condition of
+// the enclosing WHILE node (no host round trip per iteration).
+
+struct KState {
+  int j;          // Arnoldi index within the current cycle
+  int m1;         // j + 1: vectors to orthogonalise against
+  int total;      // iterations of this solve
+  int done;       // solve finished (converged, breakdown or iteration cap)
+  int cycle_end;  // the current cycle must be closed (least squares + update)
+  int restart;    // cycle_end && !done: a new cycle starts from the true residual
+  int kcount;     // columns of the current least-squares problem
+  int breakdown;  // non-finite Hessenberg entry
+  int converged;
+  int pad;
+  long long calls;      // solves since setup
+  long long iters_all;  // iterations summed over calls
+  double bnorm, rtol;
+  double est;           // last Arnoldi residual estimate |g_{j+1}|
+};
+
+// start of a solve: beta = scal[0] (= ||r||); nothing to do if beta == 0
+__global__ void k_ctl_start(KState *st, const double *scal, double rtol, cudaGraphConditionalHandle h) {
+  const double beta = scal[0];
+  st->j = 0;
+  st->m1 = 1;
+  st->total = 0;
+  st->kcount = 0;
+  st->cycle_end = 0;
+  st->restart = 0;
+  st->breakdown = 0;
+  st->converged = 0;
+  st->bnorm = beta;
+  st->rtol = rtol;
+  st->done = (beta > 0.0) ? 0 : 1;
+  st->calls += 1;
+  cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+// after Arnoldi step j (scal: [0] |g_{j+1}|, [2] h_{j+1,j}): advance and test.
+// cycle = restart length; for the coarse loop (restart none) the WHILE
+// condition is set here; for the outer loop k_ctl_continue sets it.
+__global__ void k_ctl_step(KState *st, const double *scal, int cycle, int maxit, int set_here,
+                           cudaGraphConditionalHandle h) {
+  const double est = scal[0], hj1 = scal[2];
+  st->est = est;
+  st->j += 1;
+  st->m1 = st->j + 1;
+  st->total += 1;
+  st->iters_all += 1;
+  st->kcount = st->j;
+  const bool bad = !isfinite(est) || !isfinite(hj1);
+  const bool conv = !bad && (est <= st->rtol * st->bnorm || hj1 == 0.0);
+  st->breakdown = bad ? 1 : 0;
+  st->converged = conv ? 1 : 0;
+  const bool last = st->total >= maxit;
+  st->cycle_end = (bad || conv || last || st->j >= cycle) ? 1 : 0;
+  st->done = (bad || conv || last) ? 1 : 0;
+  st->restart = (st->cycle_end && !st->done) ? 1 : 0;
+  if (set_here) cudaGraphSetConditional(h, st->cycle_end ? 0u : 1u);
+}
+
+// end of an outer iteration: a closed cycle that is not the last restarts at j = 0
+__global__ void k_ctl_continue(KState *st, cudaGraphConditionalHandle h) {
+  if (st->restart) {
+    st->j = 0;
+    st->m1 = 1;
+    st->cycle_end = 0;
+  }
+  cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+// dst = src_base + idx[0] * len (copy a basis slot chosen on the device) or the reverse
+__global__ void k_copy_indexed(double *dst, const double *__restrict__ src, long long len, const int *idx,
+                               int dst_indexed) {
+  const long long off = (long long)idx[0] * len;
+  const double *sp = dst_indexed ? src : src + off;
+  double *dp = dst_indexed ? dst + off : dst;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dp[i] = sp[i];
 }
 
 }  // namespace pintmg

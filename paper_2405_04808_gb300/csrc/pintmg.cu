@@ -123,6 +123,21 @@ struct mg_handle {
   double prof_ms[16] = {};
   long long prof_count[16] = {};
   double work_bytes[16] = {}, work_flops[16] = {};  // algorithmic work of the timed launches
+  // graph-captured solves (device_loops): device-resident loop state, fixed
+  // preconditioner input/output slots, capture streams and the cached graph
+  int capturing = 0;
+  KState *kst_f = nullptr, *kst_c = nullptr;
+  double *vin = nullptr, *zout = nullptr, *cvin = nullptr, *czout = nullptr;
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+  struct GraphKey {
+    const double *b = nullptr;
+    double *x = nullptr;
+    double rtol = -1.0;
+    int maxit = 0, restart = 0;
+  } gkey;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long g_init = 0, g_body = 0, g_coarse = 0;  // kernel launches per region of the graph
 };
 
 namespace {
@@ -153,7 +168,7 @@ struct Bracket {
   Bracket(mg_handle *h_, int cat_, cudaStream_t s_, double bytes = 0.0, double flops = 0.0)
       : h(h_), cat(cat_), s(s_) {
     h->launches++;
-    if ((h->prof >> cat) & 1) {
+    if (!h->capturing && ((h->prof >> cat) & 1)) {
       h->work_bytes[cat] += bytes;
       h->work_flops[cat] += flops;
       a = take_event(h);
@@ -262,8 +277,10 @@ LevelData<float> &ldata<float>(Level &L) { return L.f; }
 // ---------------------------------------------------------------------------
 // Dot products (FP64), fixed reduction order
 
+// m_dev (optional): the vector count lives on the device; m is then its
+// upper bound (grid size) and the kernels read the actual count.
 void multidot(mg_handle *h, const double *V, long long ldv, int m, const double *w, long long len, double *out,
-              int accumulate, cudaStream_t s, const int *gate = nullptr) {
+              int accumulate, cudaStream_t s, const int *gate = nullptr, const int *m_dev = nullptr) {
   // about 32 entries per thread per vector, at most 152 CTAs per vector block
   constexpr int VB = 8;
   const int G = (int)std::max<long long>(1, std::min<long long>(152, (len + 32 * kDotThreads - 1) / (32 * kDotThreads)));
@@ -271,20 +288,20 @@ void multidot(mg_handle *h, const double *V, long long ldv, int m, const double 
   {
     // algorithmic: read the m vectors and w once, 2 m len flops
     Bracket br(h, CAT_DOT, s, 8.0 * (m + (V == w ? 0 : 1)) * len, 2.0 * m * len);
-    k_multidot_blocked<VB><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate);
+    k_multidot_blocked<VB><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
     ck_launch();
   }
   {
     Bracket br(h, CAT_SMALL, s);
-    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, G, m, out, accumulate, gate);
+    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, G, m, out, accumulate, gate, m_dev);
     ck_launch();
   }
 }
 
 void multi_axpy(mg_handle *h, double *y, const double *X, long long ldx, const double *c, int m, double sign,
-                long long len, cudaStream_t s, const int *gate = nullptr) {
+                long long len, cudaStream_t s, const int *gate = nullptr, const int *m_dev = nullptr) {
   Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * m * len);
-  k_multi_axpy<<<grid_for(len, 256), 256, 0, s>>>(y, X, ldx, c, m, sign, len, gate);
+  k_multi_axpy<<<grid_for(len, 256), 256, 0, s>>>(y, X, ldx, c, m, sign, len, gate, m_dev);
   ck_launch();
 }
 
@@ -295,16 +312,17 @@ void read_scal(mg_handle *h, const mg_handle::Krylov &K, cudaStream_t s) {
 
 // Classical Gram-Schmidt twice (CGS2) of w against V_0..V_j: h (j+1) and
 // |w|^2 (nrm2, accumulated inside the second axpy) on the device.
+// (m_dev: the count j + 1 lives on the device, j is then its upper bound - 1)
 void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
-                   cudaStream_t s) {
+                   cudaStream_t s, const int *m_dev = nullptr) {
   const int m = j + 1;
-  multidot(h, V, len, m, w, len, K.h, 0, s);
-  multi_axpy(h, w, V, len, K.h, m, -1.0, len, s);
-  multidot(h, V, len, m, w, len, K.h + 512, 0, s);
+  multidot(h, V, len, m, w, len, K.h, 0, s, nullptr, m_dev);
+  multi_axpy(h, w, V, len, K.h, m, -1.0, len, s, nullptr, m_dev);
+  multidot(h, V, len, m, w, len, K.h + 512, 0, s, nullptr, m_dev);
   const int G = grid_for(len, kDotThreads);
   {
     Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * (m + 1) * len);
-    k_multi_axpy_norm<<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial);
+    k_multi_axpy_norm<<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev);
     ck_launch();
   }
   {
@@ -314,7 +332,7 @@ void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long lon
   }
   {
     Bracket br(h, CAT_SMALL, s);
-    k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m);
+    k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m, nullptr, m_dev);
     ck_launch();
   }
 }
@@ -327,6 +345,56 @@ void norm_into(mg_handle *h, mg_handle::Krylov &K, const double *x, long long le
     k_norm_from_sq<<<1, 1, 0, s>>>(K.nrm2, K.scal);
     ck_launch();
   }
+}
+
+// Arnoldi step with the index j on the device (st->j, st->m1): no read-back
+void arnoldi_step_dev(mg_handle *h, mg_handle::Krylov &K, KState *st, int jmax, double *V, long long len, double *w,
+                      cudaStream_t s) {
+  orthogonalise(h, K, V, len, jmax, w, s, &st->m1);
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_arnoldi_step<<<1, 1, 0, s>>>(0, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal, &st->j);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_AXPY, s);
+    k_scale<<<grid_for(len, 256), 256, 0, s>>>(V, w, K.scal + 1, len, &st->j, 1);
+    ck_launch();
+  }
+}
+
+// Add a WHILE conditional node after the work captured so far on stream s and
+// capture its body on stream bs; the body must set the condition (handle hdl).
+template <class Body>
+void add_while(mg_handle *h, cudaStream_t s, cudaGraphConditionalHandle hdl, cudaStream_t bs, Body &&body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  ck(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams params = {};
+  params.type = cudaGraphNodeTypeConditional;
+  params.conditional.handle = hdl;
+  params.conditional.type = cudaGraphCondTypeWhile;
+  params.conditional.size = 1;
+  cudaGraphNode_t node;
+  ck(cudaGraphAddNode(&node, g, deps, nullptr, nd, &params));
+  cudaGraph_t bodyg = params.conditional.phGraph_out[0];
+  ck(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  body(bs);
+  cudaGraph_t tmp = nullptr;
+  ck(cudaStreamEndCapture(bs, &tmp));
+  ck(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+}
+
+// conditional handle for a node of the graph being captured on stream s
+cudaGraphConditionalHandle new_handle(cudaStream_t s) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  ck(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hdl;
+  ck(cudaGraphConditionalHandleCreate(&hdl, g, 0, 0));
+  return hdl;
 }
 
 // one Arnoldi step on basis V (column stride len): w = A z_j already in w
@@ -518,10 +586,76 @@ void sgs_fp64<float>(mg_handle *h, Level &lev, const double *r, double *y, cudaS
   convert_back<float>(h, d.y, y, lev.len, s);
 }
 
+// Coarse solve inside a captured graph: the same GMRES with its loop as a
+// WHILE node whose condition the step-control kernel sets on the device.
+template <typename T>
+void coarse_solve_graph(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
+  Level &lev = h->lv.back();
+  const long long len = lev.len;
+  const mg_options &o = h->opts;
+  mg_handle::Krylov &K = h->kc;
+  KState *st = h->kst_c;
+  const bool fixed = o.coarse_fixed_iters > 0;
+  const int limit = fixed ? std::min(o.coarse_fixed_iters, h->cmax) : o.coarse_maxit;
+  convert_back<T>(h, r_in, h->cr, len, s);
+  norm_into(h, K, h->cr, len, s);
+  const cudaGraphConditionalHandle hdl = new_handle(s);
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_ctl_start<<<1, 1, 0, s>>>(st, K.scal, fixed ? -1.0 : o.coarse_rtol, hdl);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_AXPY, s);
+    k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->cV, h->cr, K.scal + 1, len);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_arnoldi_init<<<1, 128, 0, s>>>(K.scal, K.g, h->cmax);
+    ck_launch();
+  }
+  ck(cudaMemsetAsync(h->cy, 0, len * sizeof(double), s));
+  const long long before = h->launches;
+  add_while(h, s, hdl, h->cap[2], [&](cudaStream_t bs) {
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->cvin, h->cV, len, &st->j, 0);
+      ck_launch();
+    }
+    sgs_fp64<T>(h, lev, h->cvin, h->czout, bs);
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->cZ, h->czout, len, &st->j, 1);
+      ck_launch();
+    }
+    launch_apply<double>(h, lev.d.view, h->czout, nullptr, h->cw, bs);
+    arnoldi_step_dev(h, K, st, limit - 1, h->cV, len, h->cw, bs);
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_ctl_step<<<1, 1, 0, bs>>>(st, K.scal, limit, limit, 1, hdl);
+      ck_launch();
+    }
+  });
+  h->g_coarse = h->launches - before;
+  h->launches = before;
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_backsolve<<<1, 256, (size_t)limit * sizeof(double), s>>>(0, K.H, h->ldh, K.g, K.ycoef, &st->kcount);
+    ck_launch();
+  }
+  multi_axpy(h, h->cy, h->cZ, len, K.ycoef, limit, 1.0, len, s, nullptr, &st->kcount);
+  convert<T>(h, h->cy, y_out, len, s);
+}
+
 // Coarse solve (Sec. 5.3.4): GMRES, right-preconditioned by SGS, x0 = 0,
 // FP64 Arnoldi; y (precision T) = approximate A_c^-1 r.
 template <typename T>
 void coarse_solve(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
+  if (h->capturing) {
+    coarse_solve_graph<T>(h, r_in, y_out, s);
+    return;
+  }
   Level &lev = h->lv.back();
   const long long len = lev.len;
   const mg_options &o = h->opts;
@@ -657,6 +791,10 @@ bool host_finite(const double *x, long long len) {
 void ensure_fgmres_space(mg_handle *h, int m, cudaStream_t s) {
   if (m <= h->fm) return;
   ck(cudaStreamSynchronize(s));
+  if (h->gexec) {  // a captured solve refers to the old basis
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
   for (void *p : h->fmem) cudaFree(p);
   h->fmem.clear();
   h->fm = 0;
@@ -675,6 +813,150 @@ void ensure_fgmres_space(mg_handle *h, int m, cudaStream_t s) {
   h->fV = grab((size_t)(m + 1) * len);
   h->fZ = grab((size_t)m * len);
   h->fm = m;
+}
+
+// Capture one complete fgmres_solve (device-side loops) for fixed b, x:
+//   init:  NaN test of b, ||b||, x = 0, v_0 = b / ||b||, g = (||b||, 0...)
+//   WHILE (not done):                                 [condition set on the device]
+//     v_j -> vin; z = V-cycle(vin) (coarse GMRES = nested WHILE); z -> Z_j
+//     w = A z; CGS2 against V_0..V_j; Givens; v_{j+1} = w / h_{j+1,j}; step control
+//     if the cycle closes: y = R^-1 g; x += Z y;  if not done: restart from b - A x
+//   final: r = b - A x, ||r|| (the true residual)
+void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, int maxit, int m) {
+  cudaStream_t s = h->cap[0];
+  const long long len = h->lv[0].len;
+  mg_handle::Krylov &K = h->kf;
+  KState *st = h->kst_f;
+  const long long saved = h->launches;
+  h->capturing = 1;
+  cudaGraph_t graph = nullptr;
+  ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  try {
+    h->launches = 0;
+    ck(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
+    {
+      Bracket br(h, CAT_SMALL, s);
+      k_check_finite<<<grid_for(len, 256), 256, 0, s>>>(b, len, h->flag + 1);
+      ck_launch();
+    }
+    ck(cudaMemsetAsync(x, 0, len * sizeof(double), s));
+    norm_into(h, K, b, len, s);
+    const cudaGraphConditionalHandle hdl = new_handle(s);
+    {
+      Bracket br(h, CAT_SMALL, s);
+      k_ctl_start<<<1, 1, 0, s>>>(st, K.scal, rtol, hdl);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_AXPY, s);
+      k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, b, K.scal + 1, len);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_SMALL, s);
+      k_arnoldi_init<<<1, 128, 0, s>>>(K.scal, K.g, m);
+      ck_launch();
+    }
+    const long long n_init = h->launches;
+    h->launches = 0;
+    long long n_coarse = 0;
+    add_while(h, s, hdl, h->cap[1], [&](cudaStream_t bs) {
+      {
+        Bracket br(h, CAT_SMALL, bs);
+        k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->vin, h->fV, len, &st->j, 0);
+        ck_launch();
+      }
+      const long long before = h->launches;
+      precondition(h, h->vin, h->zout, bs);
+      n_coarse = h->g_coarse;
+      (void)before;
+      {
+        Bracket br(h, CAT_SMALL, bs);
+        k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->fZ, h->zout, len, &st->j, 1);
+        ck_launch();
+      }
+      launch_apply<double>(h, h->lv[0].d.view, h->zout, nullptr, h->fw, bs);
+      arnoldi_step_dev(h, K, st, m - 1, h->fV, len, h->fw, bs);
+      {
+        Bracket br(h, CAT_SMALL, bs);
+        k_ctl_step<<<1, 1, 0, bs>>>(st, K.scal, m, maxit, 0, hdl);
+        ck_launch();
+      }
+      // close the cycle (guarded by st->cycle_end) and restart if needed (st->restart)
+      {
+        Bracket br(h, CAT_SMALL, bs);
+        k_backsolve<<<1, 256, (size_t)m * sizeof(double), bs>>>(0, K.H, h->ldh, K.g, K.ycoef, &st->kcount,
+                                                                 &st->cycle_end);
+        ck_launch();
+      }
+      multi_axpy(h, x, h->fZ, len, K.ycoef, m, 1.0, len, bs, &st->cycle_end, &st->kcount);
+      {
+        Bracket br(h, CAT_APPLY, bs);
+        const LevelView<double> &L = h->lv[0].d.view;
+        if (L.layout == MG_LAYOUT_DENSE) {
+          k_apply_dense<double><<<grid_for(L.n, 128, 1 << 30), 128, 0, bs>>>(L, x, b, h->fr, &st->restart);
+        } else {
+          const int blocks = (L.n + 3) / 4;
+          switch (h->C) {
+            case 1: k_apply_tri<double, 1><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
+            case 2: k_apply_tri<double, 2><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
+            case 4: k_apply_tri<double, 4><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
+            case 8: k_apply_tri<double, 8><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
+            default: k_apply_tri<double, 16><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
+          }
+        }
+        ck_launch();
+      }
+      multidot(h, h->fr, len, 1, h->fr, len, K.nrm2, 0, bs, &st->restart);
+      {
+        Bracket br(h, CAT_SMALL, bs);
+        k_norm_from_sq<<<1, 1, 0, bs>>>(K.nrm2, K.scal, &st->restart);
+        ck_launch();
+      }
+      {
+        Bracket br(h, CAT_AXPY, bs);
+        k_scale<<<grid_for(len, 256), 256, 0, bs>>>(h->fV, h->fr, K.scal + 1, len, nullptr, 0, &st->restart);
+        ck_launch();
+      }
+      {
+        Bracket br(h, CAT_SMALL, bs);
+        k_arnoldi_init<<<1, 128, 0, bs>>>(K.scal, K.g, m, &st->restart);
+        ck_launch();
+      }
+      {
+        Bracket br(h, CAT_SMALL, bs);
+        k_ctl_continue<<<1, 1, 0, bs>>>(st, hdl);
+        ck_launch();
+      }
+    });
+    const long long n_body = h->launches;
+    h->launches = 0;
+    launch_apply<double>(h, h->lv[0].d.view, x, b, h->fr, s);
+    norm_into(h, K, h->fr, len, s);
+    h->g_init = n_init + h->launches;
+    h->g_body = n_body;
+    h->g_coarse = n_coarse;
+    ck(cudaStreamEndCapture(s, &graph));
+  } catch (...) {
+    cudaStreamEndCapture(s, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    h->capturing = 0;
+    h->launches = saved;
+    throw;
+  }
+  h->capturing = 0;
+  h->launches = saved;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph = graph;
+  h->gexec = nullptr;
+  ck(cudaGraphInstantiate(&h->gexec, graph, 0));
+  h->gkey.b = b;
+  h->gkey.x = x;
+  h->gkey.rtol = rtol;
+  h->gkey.maxit = maxit;
+  h->gkey.restart = m;
 }
 
 bool is_device_pointer(const void *p) {
@@ -706,6 +988,7 @@ void mg_default_options(mg_options *o) {
   o->precision = MG_PRECISION_FP64;
   o->omega = 1.0;
   o->coarse_precond = MG_COARSE_SGS;
+  o->device_loops = 1;
 }
 
 const char *mg_status_string(int st) {
@@ -773,6 +1056,10 @@ void mg_destroy(mg_handle *h) {
     cudaEventDestroy(pe.second.second);
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (cudaStream_t cs : h->cap)
+    if (cs) cudaStreamDestroy(cs);
   h->mem.release();
   for (void *p : h->fmem) cudaFree(p);
   if (h->host_scal) cudaFreeHost(h->host_scal);
@@ -796,6 +1083,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (O->precision != MG_PRECISION_FP64 && O->precision != MG_PRECISION_FP32) return MG_ERR_ARG;
   if (!(O->omega > 0.0 && O->omega <= 1.0)) return MG_ERR_ARG;
   if (O->coarse_precond < MG_COARSE_SGS || O->coarse_precond > MG_COARSE_BGS) return MG_ERR_ARG;
+  if (O->device_loops != 0 && O->device_loops != 1) return MG_ERR_ARG;
   if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;
@@ -1000,6 +1288,16 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
       K->scal = h->mem.alloc<double>(8);
       K->nrm2 = h->mem.alloc<double>(8);
     }
+    // graph-captured solves: loop states, fixed preconditioner slots, capture streams
+    h->kst_f = h->mem.alloc<KState>(1);
+    h->kst_c = h->mem.alloc<KState>(1);
+    ck(cudaMemsetAsync(h->kst_f, 0, sizeof(KState), s));
+    ck(cudaMemsetAsync(h->kst_c, 0, sizeof(KState), s));
+    h->vin = h->mem.alloc<double>(h->lv[0].len);
+    h->zout = h->mem.alloc<double>(h->lv[0].len);
+    h->cvin = h->mem.alloc<double>(cl.len);
+    h->czout = h->mem.alloc<double>(cl.len);
+    for (cudaStream_t &cs : h->cap) ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     int flag = 0;
     ck(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
@@ -1056,6 +1354,41 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       b = h->fb_stage;
     }
     double *x = x_dev ? x_out : h->fx_stage;
+    if (h->opts.device_loops) {
+      // one CUDA graph per solve: loops on the device, one read-back at the end
+      if (!h->gexec || h->gkey.b != b || h->gkey.x != x || h->gkey.rtol != rtol || h->gkey.maxit != maxit ||
+          h->gkey.restart != m) {
+        ck(cudaStreamSynchronize(s));
+        build_solve_graph(h, b, x, rtol, maxit, m);
+      }
+      KState before_c{};
+      ck(cudaMemcpyAsync(&before_c, h->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      ck(cudaGraphLaunch(h->gexec, s));
+      KState fs{}, cs{};
+      int bad = 0;
+      ck(cudaMemcpyAsync(&fs, h->kst_f, sizeof(KState), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(&cs, h->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(&bad, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(h->host_scal, h->kf.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (!x_dev) ck(cudaMemcpyAsync(x_out, x, len * sizeof(double), cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      total = fs.total;
+      h->vcycles = fs.total;
+      h->coarse_iters = (int)(cs.iters_all - before_c.iters_all);
+      h->launches += h->g_init + h->g_body * fs.total + h->g_coarse * (cs.iters_all - before_c.iters_all);
+      if (bad) throw 1;
+      const double bnorm = fs.bnorm;
+      if (bnorm > 0.0) {
+        true_rel = h->host_scal[0] / bnorm;
+        est_rel = fs.est / bnorm;
+        if (fs.breakdown) status = MG_ERR_BREAKDOWN;
+        else if (!fs.converged) status = MG_NOT_CONVERGED;
+      } else {
+        est_rel = 0.0;
+        true_rel = 0.0;
+      }
+    } else {
     ck(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
     {
       Bracket br(h, CAT_SMALL, s);
@@ -1130,6 +1463,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
     }
     if (!x_dev) ck(cudaMemcpyAsync(x_out, x, len * sizeof(double), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
+    }
     harvest(h);
   } catch (const CudaFail &) {
     status = MG_ERR_CUDA;

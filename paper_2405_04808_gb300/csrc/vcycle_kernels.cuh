@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const
 // out = b - A~ x  (b non-null)  or  out = A~ x  (b null), all five types.
 template <typename T, int C>
 __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T> L, const T *__restrict__ x,
-                                                   const T *__restrict__ b, T *out) {
+                                                   const T *__restrict__ b, T *out, const int *guard = nullptr) {
+  if (guard && *guard == 0) return;
   const int ln = threadIdx.x & (kWarp - 1);
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int n = L.n, p = L.p, q = L.q;
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T> L, const T *__re
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__restrict__ x,
-                                                     const T *__restrict__ b, T *out) {
+                                                     const T *__restrict__ b, T *out, const int *guard = nullptr) {
+  if (guard && *guard == 0) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = L.n, p = L.p, q = L.q;
   if (t >= n) return;

@@ -50,7 +50,7 @@ class MGOptions(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("coarse_rtol", ctypes.c_double), ("coarse_maxit", ctypes.c_int),
                 ("coarse_fixed_iters", ctypes.c_int), ("end_rule", ctypes.c_int), ("precision", ctypes.c_int),
-                ("omega", ctypes.c_double), ("coarse_precond", ctypes.c_int)]
+                ("omega", ctypes.c_double), ("coarse_precond", ctypes.c_int), ("device_loops", ctypes.c_int)]
 
 
 class MGSolveInfo(ctypes.Structure):
@@ -124,7 +124,7 @@ def _c(arr):
 
 def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit=50,
              coarse_fixed_iters=0, end_rule=0, precision=MG_PRECISION_FP64, omega=1.0, coarse_precond="sgs",
-             stream=0):
+             device_loops=True, stream=0):
     """Build the device hierarchy for a workloads.Problem; returns an opaque handle (int)."""
     keep = []
     P = MGProblem()
@@ -137,7 +137,7 @@ def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit
         keep.append(a)
         setattr(P, name, ptr)
     o = MGOptions(levels, nu_pre, nu_post, coarse_rtol, coarse_maxit, coarse_fixed_iters, end_rule, precision, omega,
-                  COARSE_PRECOND[coarse_precond])
+                  COARSE_PRECOND[coarse_precond], 1 if device_loops else 0)
     h = ctypes.c_void_p()
     code = lib().mg_setup(ctypes.byref(P), ctypes.byref(o), ctypes.c_void_p(stream), ctypes.byref(h))
     if code != MG_OK:

@@ -234,3 +234,32 @@ def test_table1_coarse_preconditioners(P, kind, levels):
         assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) <= VCYCLE_RTOL
     finally:
         P.mg_destroy(h)
+
+
+# ---------------------------------------------------------------- device-side loops
+
+@pytest.mark.parametrize("case,restart", [(0, 7), (4, 9), (8, 7), (9, 5)])
+def test_graph_solve_equals_host_loop(P, case, restart):
+    """A solve captured as one CUDA graph (FGMRES and coarse GMRES loops as
+    conditional nodes) runs the same kernels in the same order as the host-driven
+    loop: identical iterations and bitwise-identical solutions, also across a
+    restart and on the second launch of the cached graph."""
+    make, levels, nu_pre, nu_post, end_rule, omega = _unpack(case)
+    prob = make()
+    xs, its = [], []
+    for loops in (False, True):
+        h = P.mg_setup(prob, levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule, omega=omega,
+                       device_loops=loops)
+        try:
+            b = _dev(prob.b)
+            for rep in range(2):
+                x = torch.empty_like(b)
+                code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, 150, restart)
+                assert code in (P.MG_OK, P.MG_NOT_CONVERGED), P.mg_status_string(code)
+                xs.append(x.cpu().numpy())
+                its.append((code, info.iters, info.coarse_iters, info.true_relres))
+        finally:
+            P.mg_destroy(h)
+    assert its[0] == its[1] == its[2] == its[3]
+    for k in range(1, 4):
+        assert np.array_equal(xs[0], xs[k])

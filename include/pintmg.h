@@ -110,6 +110,7 @@ typedef struct {
 } mg_options;
 
 typedef struct {
+  int status;             /* mg_status of this solve */
   int iters;              /* FGMRES iterations taken */
   int vcycles;            /* preconditioner applications */
   int coarse_iters;       /* coarse GMRES iterations summed over all V-cycles */
@@ -153,6 +154,21 @@ int mg_vcycle(mg_handle *h, const double *r, double *y, void *stream);
  */
 int fgmres_solve(mg_handle *h, const double *b, double *x, double rtol, int maxit, int restart,
                  mg_solve_info *info, void *stream);
+
+/*
+ * Solve `count` independent systems (each with its own handle, so sizes,
+ * layouts and options may differ) in ONE CUDA graph launch: every system is
+ * a branch of the graph with its own device-side FGMRES and coarse-GMRES
+ * loops, so the branches run concurrently and the host reads back once for
+ * the whole batch.  b[i], x[i] are DEVICE pointers; the graph is built on the
+ * first call and reused while the handles, vectors, rtol, maxit and restart
+ * stay the same (one cached batch graph per host thread).  infos (may be
+ * NULL) receives count entries with each solve's status.  Returns the most
+ * severe status: an error code if any solve failed, else MG_NOT_CONVERGED if
+ * any did not converge, else MG_OK.  Synchronises `stream`.
+ */
+int fgmres_solve_batched(mg_handle *const *hs, int count, const double *const *b, double *const *x, double rtol,
+                         int maxit, int restart, mg_solve_info *infos, void *stream);
 
 /* Sizes of a handle: the vector length n (4p+q) and the number of levels. */
 long long mg_vector_length(const mg_handle *h);

@@ -822,16 +822,12 @@ void ensure_fgmres_space(mg_handle *h, int m, cudaStream_t s) {
 //     w = A z; CGS2 against V_0..V_j; Givens; v_{j+1} = w / h_{j+1,j}; step control
 //     if the cycle closes: y = R^-1 g; x += Z y;  if not done: restart from b - A x
 //   final: r = b - A x, ||r|| (the true residual)
-void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, int maxit, int m) {
-  cudaStream_t s = h->cap[0];
+// Issue the whole solve on stream s, which must be capturing.
+void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, double rtol, int maxit, int m) {
   const long long len = h->lv[0].len;
   mg_handle::Krylov &K = h->kf;
   KState *st = h->kst_f;
-  const long long saved = h->launches;
-  h->capturing = 1;
-  cudaGraph_t graph = nullptr;
-  ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-  try {
+  {
     h->launches = 0;
     ck(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
     {
@@ -936,6 +932,17 @@ void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, in
     h->g_init = n_init + h->launches;
     h->g_body = n_body;
     h->g_coarse = n_coarse;
+  }
+}
+
+void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, int maxit, int m) {
+  cudaStream_t s = h->cap[0];
+  const long long saved = h->launches;
+  h->capturing = 1;
+  cudaGraph_t graph = nullptr;
+  ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  try {
+    capture_solve(h, s, b, x, rtol, maxit, m);
     ck(cudaStreamEndCapture(s, &graph));
   } catch (...) {
     cudaStreamEndCapture(s, &graph);
@@ -958,6 +965,40 @@ void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, in
   h->gkey.maxit = maxit;
   h->gkey.restart = m;
 }
+
+// workspace of a solve with restart m (grown on demand)
+void prepare_solve(mg_handle *h, int m, cudaStream_t s) {
+  ensure_fgmres_space(h, m, s);
+  if (!h->fw) {
+    const long long len = h->lv[0].len;
+    h->fw = h->mem.alloc<double>(len);
+    h->fr = h->mem.alloc<double>(len);
+    h->fx_stage = h->mem.alloc<double>(len);
+    h->fb_stage = h->mem.alloc<double>(len);
+  }
+}
+
+// the graph of a batch of solves (one branch per system), cached per host thread
+struct BatchGraph {
+  std::vector<mg_handle *> hs;
+  std::vector<const double *> b;
+  std::vector<double *> x;
+  double rtol = -1.0;
+  int maxit = 0, restart = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t root = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  ~BatchGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : joins) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (root) cudaStreamDestroy(root);
+  }
+};
+thread_local BatchGraph g_batch;
 
 bool is_device_pointer(const void *p) {
   cudaPointerAttributes a{};
@@ -1340,13 +1381,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
   double est_rel = 1.0, true_rel = 0.0;
   try {
     const int m = std::min(restart, maxit);
-    ensure_fgmres_space(h, m, s);
-    if (!h->fw) {
-      h->fw = h->mem.alloc<double>(len);
-      h->fr = h->mem.alloc<double>(len);
-      h->fx_stage = h->mem.alloc<double>(len);
-      h->fb_stage = h->mem.alloc<double>(len);
-    }
+    prepare_solve(h, m, s);
     const bool b_dev = is_device_pointer(b_in), x_dev = is_device_pointer(x_out);
     const double *b = b_in;
     if (!b_dev) {
@@ -1473,6 +1508,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
     status = MG_ERR_NONFINITE;
   }
   if (info) {
+    info->status = status;
     info->iters = total;
     info->vcycles = h->vcycles;
     info->coarse_iters = h->coarse_iters;
@@ -1483,6 +1519,127 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Many systems in one graph launch.
+
+extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const double *const *b, double *const *x,
+                                    double rtol, int maxit, int restart, mg_solve_info *infos, void *stream) {
+  if (!hs || !b || !x || count < 1 || maxit < 1 || restart < 1 || restart > 512 || !(rtol >= 0.0)) return MG_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !b[i] || !x[i]) return MG_ERR_ARG;
+    if (!is_device_pointer(b[i]) || !is_device_pointer(x[i])) return MG_ERR_ARG;
+    for (int k = 0; k < i; ++k)
+      if (hs[k] == hs[i]) return MG_ERR_ARG;  // each system needs its own handle (workspaces)
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BatchGraph &bg = g_batch;
+  const int m = std::min(restart, maxit);
+  int worst = MG_OK;
+  try {
+    for (int i = 0; i < count; ++i) prepare_solve(hs[i], m, s);
+    bool same = bg.exec && (int)bg.hs.size() == count && bg.rtol == rtol && bg.maxit == maxit && bg.restart == m;
+    for (int i = 0; same && i < count; ++i) same = bg.hs[i] == hs[i] && bg.b[i] == b[i] && bg.x[i] == x[i];
+    for (int i = 0; same && i < count; ++i) same = hs[i]->fm >= m;
+    if (!same) {
+      ck(cudaStreamSynchronize(s));
+      if (bg.exec) cudaGraphExecDestroy(bg.exec);
+      if (bg.graph) cudaGraphDestroy(bg.graph);
+      bg.exec = nullptr;
+      bg.graph = nullptr;
+      if (!bg.root) ck(cudaStreamCreateWithFlags(&bg.root, cudaStreamNonBlocking));
+      if (!bg.fork) ck(cudaEventCreateWithFlags(&bg.fork, cudaEventDisableTiming));
+      while ((int)bg.joins.size() < count) {
+        cudaEvent_t e;
+        ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        bg.joins.push_back(e);
+      }
+      // root -> fork into one branch per system (its own capture stream) -> join
+      ck(cudaStreamBeginCapture(bg.root, cudaStreamCaptureModeRelaxed));
+      try {
+        ck(cudaEventRecord(bg.fork, bg.root));
+        for (int i = 0; i < count; ++i) {
+          mg_handle *h = hs[i];
+          ck(cudaStreamWaitEvent(h->cap[0], bg.fork, 0));
+          const long long saved = h->launches;
+          h->capturing = 1;
+          try {
+            capture_solve(h, h->cap[0], b[i], x[i], rtol, maxit, m);
+          } catch (...) {
+            h->capturing = 0;
+            h->launches = saved;
+            throw;
+          }
+          h->capturing = 0;
+          h->launches = saved;
+          ck(cudaEventRecord(bg.joins[i], h->cap[0]));
+          ck(cudaStreamWaitEvent(bg.root, bg.joins[i], 0));
+        }
+        ck(cudaStreamEndCapture(bg.root, &bg.graph));
+      } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(bg.root, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        throw;
+      }
+      ck(cudaGraphInstantiate(&bg.exec, bg.graph, 0));
+      bg.hs.assign(hs, hs + count);
+      bg.b.assign(b, b + count);
+      bg.x.assign(x, x + count);
+      bg.rtol = rtol;
+      bg.maxit = maxit;
+      bg.restart = m;
+      // a single solve of these handles must recapture its own graph: the
+      // batch capture reused their capture state
+      for (int i = 0; i < count; ++i) hs[i]->gkey.b = nullptr;
+    }
+    std::vector<KState> before(count), fs(count), cs(count);
+    std::vector<int> bad(count);
+    std::vector<double> tr(4 * (size_t)count);
+    for (int i = 0; i < count; ++i)
+      ck(cudaMemcpyAsync(&before[i], hs[i]->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    ck(cudaGraphLaunch(bg.exec, s));
+    for (int i = 0; i < count; ++i) {
+      ck(cudaMemcpyAsync(&fs[i], hs[i]->kst_f, sizeof(KState), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(&cs[i], hs[i]->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(&bad[i], hs[i]->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(&tr[4 * (size_t)i], hs[i]->kf.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    ck(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {
+      mg_handle *h = hs[i];
+      const long long citers = cs[i].iters_all - before[i].iters_all;
+      h->launches += h->g_init + h->g_body * fs[i].total + h->g_coarse * citers;
+      int st = MG_OK;
+      double est_rel = 0.0, true_rel = 0.0;
+      if (bad[i]) {
+        st = MG_ERR_NONFINITE;
+      } else if (fs[i].bnorm > 0.0) {
+        true_rel = tr[4 * (size_t)i] / fs[i].bnorm;
+        est_rel = fs[i].est / fs[i].bnorm;
+        if (fs[i].breakdown) st = MG_ERR_BREAKDOWN;
+        else if (!fs[i].converged) st = MG_NOT_CONVERGED;
+      }
+      if (infos) {
+        infos[i].status = st;
+        infos[i].iters = fs[i].total;
+        infos[i].vcycles = fs[i].total;
+        infos[i].coarse_iters = (int)citers;
+        infos[i].relres = est_rel;
+        infos[i].true_relres = true_rel;
+      }
+      if (st < 0 && (worst >= 0 || st < worst)) worst = st;
+      else if (st == MG_NOT_CONVERGED && worst == MG_OK) worst = st;
+    }
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    return MG_ERR_OOM;
+  }
+  return worst;
+}
 
 // ===========================================================================
 // Residual check that allocates nothing.

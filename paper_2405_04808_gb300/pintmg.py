@@ -33,7 +33,8 @@ MG_PRECISION_FP32 = 1
 COARSE_PRECOND = {"sgs": 0, "jacobi": 1, "fgs": 2, "bgs": 3}
 
 #: every symbol include/pintmg.h declares
-EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "mg_vector_length",
+EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmres_solve_batched",
+            "mg_vector_length",
             "mg_launch_count", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
             "mg_destroy", "mg_status_string", "mg_last_cuda_error")
 
@@ -54,7 +55,8 @@ class MGOptions(ctypes.Structure):
 
 
 class MGSolveInfo(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("vcycles", ctypes.c_int), ("coarse_iters", ctypes.c_int),
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("vcycles", ctypes.c_int),
+                ("coarse_iters", ctypes.c_int),
                 ("relres", ctypes.c_double), ("true_relres", ctypes.c_double)]
 
 
@@ -84,6 +86,11 @@ def lib():
         L.fgmres_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                    ctypes.c_int, ctypes.c_int, ctypes.POINTER(MGSolveInfo), ctypes.c_void_p]
         L.fgmres_solve.restype = ctypes.c_int
+        L.fgmres_solve_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(MGSolveInfo), ctypes.c_void_p]
+        L.fgmres_solve_batched.restype = ctypes.c_int
         L.mg_vector_length.argtypes = [ctypes.c_void_p]
         L.mg_vector_length.restype = ctypes.c_longlong
         L.mg_launch_count.argtypes = [ctypes.c_void_p]
@@ -157,6 +164,19 @@ def fgmres_solve(h, b_ptr: int, x_ptr: int, rtol: float, maxit: int = 500, resta
     code = lib().fgmres_solve(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
                               float(rtol), int(maxit), int(restart), ctypes.byref(info), ctypes.c_void_p(stream))
     return code, info
+
+
+def fgmres_solve_batched(handles, b_ptrs, x_ptrs, rtol: float, maxit: int = 500, restart: int = 100,
+                         stream: int = 0):
+    """Solve len(handles) systems in one graph launch; returns (status, [MGSolveInfo])."""
+    k = len(handles)
+    H = (ctypes.c_void_p * k)(*handles)
+    B = (ctypes.c_void_p * k)(*b_ptrs)
+    X = (ctypes.c_void_p * k)(*x_ptrs)
+    infos = (MGSolveInfo * k)()
+    code = lib().fgmres_solve_batched(H, k, B, X, float(rtol), int(maxit), int(restart), infos,
+                                      ctypes.c_void_p(stream))
+    return code, list(infos)
 
 
 def mg_vector_length(h) -> int:

@@ -354,3 +354,21 @@ WORKLOADS = {
     "burgers_nx512_n8192": dict(make=lambda seed=3000: burgers(nx=512, n=8192, nu=0.005, seed=seed), seed=3000,
                                 levels=4, nu_pre=4, nu_post=4),
 }
+
+
+def batch_mix(seed: int = 4000, count: int = 32):
+    """Uneven systems for batched solves: van der Pol with nt 256 / 512 and
+    Burgers with nx 32 / 64 and nt 256 / 512, distinct seeded iterates; each
+    with its own solver settings (3 levels; 1/1 sweeps for van der Pol, 4/4
+    for Burgers).  Returns [(Problem, settings)]."""
+    out = []
+    for k in range(count):
+        sd = seed + k
+        if k % 2 == 0:
+            nt = 256 if (k // 2) % 2 == 0 else 512
+            out.append((vdp(n=nt, seed=sd), dict(levels=3, nu_pre=1, nu_post=1)))
+        else:
+            nx = 32 if (k // 2) % 2 == 0 else 64
+            nt = 256 if (k // 4) % 2 == 0 else 512
+            out.append((burgers(nx=nx, n=nt, seed=sd), dict(levels=3, nu_pre=4, nu_post=4)))
+    return out

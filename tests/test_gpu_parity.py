@@ -263,3 +263,59 @@ def test_graph_solve_equals_host_loop(P, case, restart):
     assert its[0] == its[1] == its[2] == its[3]
     for k in range(1, 4):
         assert np.array_equal(xs[0], xs[k])
+
+
+# ---------------------------------------------------------------- batched solves
+
+def test_batched_solves_equal_single_solves(P):
+    """Uneven systems (van der Pol and Burgers of different lengths, layouts and
+    options) in one graph launch give the same results as one solve at a time."""
+    specs = [
+        (W.vdp(n=64, seed=201), dict(levels=3, nu_pre=1, nu_post=1)),
+        (W.burgers(nx=40, n=32, seed=202), dict(levels=2, nu_pre=2, nu_post=2, omega=0.7)),
+        (W.vdp(n=128, seed=203), dict(levels=2, nu_pre=2, nu_post=2, omega=0.7)),
+        (W.burgers(nx=24, n=64, seed=204), dict(levels=3, nu_pre=4, nu_post=4, precision=P.MG_PRECISION_FP32)),
+        (W.burgers(nx=16, n=16, seed=205), dict(levels=1)),
+    ]
+    hs, bs, xs, ref = [], [], [], []
+    try:
+        for prob, opts in specs:
+            h = P.mg_setup(prob, **opts)
+            hs.append(h)
+            b = _dev(prob.b)
+            x = torch.empty_like(b)
+            code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, 3000, 400)
+            assert code == P.MG_OK
+            ref.append((x.cpu().numpy(), info.iters))
+            bs.append(b)
+            xs.append(torch.empty_like(b))
+        for rep in range(2):   # build, then reuse the cached batch graph
+            for x in xs:
+                x.fill_(float("nan"))
+            code, infos = P.fgmres_solve_batched(hs, [b.data_ptr() for b in bs], [x.data_ptr() for x in xs],
+                                                 1e-10, 3000, 400)
+            assert code == P.MG_OK, P.mg_status_string(code)
+            for (xr, it), x, info, (prob, _) in zip(ref, xs, infos, specs):
+                assert info.status == P.MG_OK and info.iters == it
+                assert np.array_equal(x.cpu().numpy(), xr)
+                xd = O.direct_solve(prob)
+                assert np.linalg.norm(x.cpu().numpy() - xd) / np.linalg.norm(xd) <= SOLVE_RTOL
+        # after the batch, a single solve of one handle still works (recaptured)
+        x = torch.empty_like(bs[0])
+        code, info = P.fgmres_solve(hs[0], bs[0].data_ptr(), x.data_ptr(), 1e-10, 3000, 400)
+        assert code == P.MG_OK and np.array_equal(x.cpu().numpy(), ref[0][0])
+    finally:
+        for h in hs:
+            P.mg_destroy(h)
+
+
+def test_batched_rejects_shared_handles(P):
+    prob = W.vdp(n=16, seed=206)
+    h = P.mg_setup(prob, levels=2)
+    try:
+        b = _dev(prob.b)
+        x = torch.empty_like(b)
+        code, _ = P.fgmres_solve_batched([h, h], [b.data_ptr()] * 2, [x.data_ptr()] * 2, 1e-8)
+        assert code == P.MG_ERR_ARG
+    finally:
+        P.mg_destroy(h)

@@ -88,3 +88,30 @@ def test_c2_burgers_full_size_vcycle(P):
                 assert np.max(np.abs(yg[sl] - yo[sl])) <= 1e-10 * scale
     finally:
         P.mg_destroy(h)
+
+
+@pytest.mark.parametrize("name,omega", [("burgers_nx128_n1024", 1.0), ("burgers_nx128_n1024", 0.7),
+                                        ("vdp_n256", 1.0), ("vdp_n256", 0.7)])
+def test_bench_configuration_iterations_match_oracle(P, name, omega):
+    """At bench.py's configuration (rtol 1e-8, restart 400) the GPU solve takes the
+    oracle's own full-solve iteration count (tests/golden/oracle_iterations.json,
+    written by oracle/measure_iterations.py) and meets the tolerance on the
+    oracle's independently assembled operator."""
+    import json
+    import os
+    from conftest import GOLDEN
+    rec = json.load(open(os.path.join(GOLDEN, "oracle_iterations.json")))[f"{name}/omega={omega}"]
+    wl = W.WORKLOADS[name]
+    prob = wl["make"]()
+    h = P.mg_setup(prob, levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega)
+    try:
+        b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), rec["rtol"], rec["maxit"], rec["restart"])
+        assert code == P.MG_OK
+        assert abs(info.iters - rec["iters"]) <= 2, (info.iters, rec["iters"])
+        lev = O.Level(O.raw_from_problem(prob))
+        xr = x.cpu().numpy()
+        assert np.linalg.norm(prob.b - lev.A @ xr) / np.linalg.norm(prob.b) <= 1.05 * rec["rtol"]
+    finally:
+        P.mg_destroy(h)

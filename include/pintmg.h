@@ -116,6 +116,7 @@ typedef struct {
   int coarse_iters;       /* coarse GMRES iterations summed over all V-cycles */
   double relres;          /* Arnoldi estimate ||b - A x|| / ||b|| at exit */
   double true_relres;     /* recomputed ||b - A x|| / ||b|| at exit (FP64) */
+  int coarse_learned;     /* coarse solves answered by an attached network (mg_attach_coarse_net), else 0 */
 } mg_solve_info;
 
 typedef struct mg_handle mg_handle;  /* opaque; owns every device buffer */
@@ -212,6 +213,74 @@ int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long 
  * threads) race; serialise them.
  */
 int mg_true_residual_noalloc(mg_handle *h, const double *b, const double *x, double *out, void *stream);
+
+/*
+ * Learned coarse-grid correction.  A small network proposes the coarse solve
+ * of the V-cycle (the step the paper does with GMRES preconditioned by SGS,
+ * Sec. 5.3.4); the paper has no network, this is an extension.  Fixed
+ * architecture: four 2-D convolutions over (time, space) with 3 x 7 kernels
+ * and zero "same" padding, channels 5 -> 32 -> 32 -> 32 -> 5, leaky rectifier
+ * (slope 0.1) after the first three; mg_net_param_count() = 49,829 FP32
+ * parameters, flat, layer by layer, each layer's weights W[o][c][i][j]
+ * (i: time tap, j: space tap) followed by its biases.  A tensor is NCHW
+ * (batch, channel, T, X), FP32, contiguous; a coarse type-major vector
+ * (u, v, z, lambda, mu, each n_c x p) is exactly one (5, n_c, p) sample.
+ *
+ * mg_net_create copies `init_params` (HOST, mg_net_param_count() floats) and
+ * allocates the parameters, the gradient and Adam's moments on the current
+ * device.  mg_net_set_params / mg_net_get_params / mg_net_get_grad copy
+ * HOST <-> device and synchronise.  mg_net_forward runs the network on x
+ * (DEVICE, batch x 5 x T x X) into y (DEVICE, same shape; x == y allowed):
+ * bf16 = 0 in FP32, bf16 = 1 with parameters and activations stored in BF16
+ * and FP32 accumulation.  mg_net_loss_grad computes L = mean((net(x) -
+ * target)^2) in FP32, writes *loss (HOST) and leaves dL/dparams in the
+ * network's gradient buffer (synchronises `stream`).  mg_net_adam_step takes
+ * one Adam step (Kingma and Ba 2015, bias-corrected) from that gradient.
+ * mg_net_train runs `epochs` passes of minibatch Adam over `count` samples
+ * (x_all, y_all: DEVICE, count x 5 x T x X), the sample order reshuffled
+ * every epoch from `seed` (splitmix64); epoch_loss (HOST, may be NULL)
+ * receives each epoch's mean minibatch loss.  Workspaces grow on demand
+ * (about 8 x batch x 32 x T x X floats for training).  Errors: MG_ERR_ARG for
+ * bad sizes or NULL pointers, MG_ERR_OOM, MG_ERR_CUDA.
+ */
+typedef struct mg_net mg_net;  /* opaque; owns its device buffers */
+long long mg_net_param_count(void);
+int mg_net_create(const float *init_params, mg_net **out);
+int mg_net_set_params(mg_net *net, const float *params);
+int mg_net_get_params(const mg_net *net, float *params);
+int mg_net_get_grad(const mg_net *net, float *grad);
+int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *y, int bf16, void *stream);
+int mg_net_loss_grad(mg_net *net, const float *x, const float *target, int batch, int T, int X, float *loss,
+                     void *stream);
+int mg_net_adam_step(mg_net *net, float lr, float beta1, float beta2, float eps, void *stream);
+int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count, int T, int X, int batch,
+                 int epochs, float lr, unsigned long long seed, float *epoch_loss, void *stream);
+void mg_net_destroy(mg_net *net);
+
+/*
+ * Use `net` (not owned; keep it alive while attached, NULL detaches) as the
+ * coarse solve of h's V-cycles: with r the coarse residual, the proposal is
+ *   e = ||r|| net(r / ||r||)   (BF16 inference if bf16 = 1, else FP32),
+ * and it is admitted when ||r - A_c e|| <= admit ||r|| (FP64 residual on the
+ * coarse level); otherwise the coarse GMRES with SGS runs as without the
+ * network, so it is both the judge and the fallback.  FGMRES accepts the
+ * resulting variable preconditioner.  Needs the tridiagonal layout or
+ * q == p (MG_ERR_UNSUPPORTED otherwise) and 0 < admit < 1.  Several handles
+ * may share one network.  Parameter updates reach later solves (BF16 copies
+ * are refreshed at the start of each fgmres_solve).
+ *
+ * mg_record_coarse(h, r, y, max_pairs) makes later host-driven solves
+ * (options.device_loops = 0) record each coarse GMRES solve as a training
+ * pair (r / ||r||, y / ||r||) in FP32 into r, y (DEVICE, caller-owned,
+ * max_pairs x 5 x n_c x p floats each) until max_pairs are stored; NULL
+ * stops recording.  mg_recorded_pairs returns the number stored.  Returns
+ * MG_ERR_UNSUPPORTED for device-loop handles.
+ */
+int mg_attach_coarse_net(mg_handle *h, mg_net *net, double admit, int bf16);
+int mg_record_coarse(mg_handle *h, float *r, float *y, int max_pairs);
+int mg_recorded_pairs(const mg_handle *h);
+/* Coarse level shape (time steps n_c, space p) of a handle: the network's T and X. */
+int mg_coarse_shape(const mg_handle *h, int *T, int *X);
 
 /* Release every device buffer of the handle.  NULL is accepted. */
 void mg_destroy(mg_handle *h);

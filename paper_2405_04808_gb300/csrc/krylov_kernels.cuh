@@ -252,7 +252,9 @@ struct KState {
 };
 
 // start of a solve: beta = scal[0] (= ||r||); nothing to do if beta == 0
-__global__ void k_ctl_start(KState *st, const double *scal, double rtol, cudaGraphConditionalHandle h) {
+// admitted (optional): the learned coarse correction was accepted, nothing to iterate
+__global__ void k_ctl_start(KState *st, const double *scal, double rtol, cudaGraphConditionalHandle h,
+                            const int *admitted = nullptr) {
   const double beta = scal[0];
   st->j = 0;
   st->m1 = 1;
@@ -264,7 +266,7 @@ __global__ void k_ctl_start(KState *st, const double *scal, double rtol, cudaGra
   st->converged = 0;
   st->bnorm = beta;
   st->rtol = rtol;
-  st->done = (beta > 0.0) ? 0 : 1;
+  st->done = (beta > 0.0 && !(admitted && admitted[0])) ? 0 : 1;
   st->calls += 1;
   cudaGraphSetConditional(h, st->done ? 0u : 1u);
 }
@@ -310,6 +312,31 @@ __global__ void k_copy_indexed(double *dst, const double *__restrict__ src, long
   double *dp = dst_indexed ? dst + off : dst;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
     dp[i] = sp[i];
+}
+
+// learned coarse correction: admitted if ||r - A e|| <= admit ||r||
+// (rr2 = ||r - A e||^2, scal[0] = ||r||); flag[0] = decision, flag[1] counts admissions
+__global__ void k_net_judge(const double *rr2, const double *scal, double admit, int *flag) {
+  const bool ok = sqrt(rr2[0]) <= admit * scal[0] && scal[0] > 0.0;
+  flag[0] = ok ? 1 : 0;
+  if (ok) flag[1] += 1;
+}
+
+// dst = src where flag[0] != 0
+__global__ void k_copy_if(double *dst, const double *__restrict__ src, long long n, const int *flag) {
+  if (!flag[0]) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// a training pair: r / ||r|| and y / ||r|| in FP32 (scal[1] = 1 / ||r||)
+__global__ void k_record_pair(const double *__restrict__ r, const double *__restrict__ y, const double *scal,
+                              float *rr, float *yy, long long n) {
+  const double inv = scal[1];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    rr[i] = (float)(r[i] * inv);
+    yy[i] = (float)(y[i] * inv);
+  }
 }
 
 }  // namespace pintmg

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "krylov_kernels.cuh"
+#include "learned_kernels.cuh"
 #include "setup_kernels.cuh"
 #include "vcycle_kernels.cuh"
 
@@ -86,6 +87,25 @@ struct Level {
 
 }  // namespace
 
+// The learned coarse correction's network (weights, optimiser state, workspaces).
+struct mg_net {
+  float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *partial = nullptr, *loss = nullptr;
+  __nv_bfloat16 *params_bf16 = nullptr;
+  bool bf16_valid = false;
+  int step = 0;
+  // training workspace: layer outputs h[l] (l = 1..4; h[0] is the caller's input),
+  // pre-activations z[l] (l = 0..2), gradient ping-pong g0/g1, a gathered minibatch
+  float *h[kNetLayers + 1] = {}, *z[kNetLayers] = {}, *g0 = nullptr, *g1 = nullptr, *bx = nullptr, *by = nullptr;
+  long long ws_elems = 0;  // per sample: 32 * T * X
+  int ws_batch = 0;
+  // standalone inference workspace (mg_net_forward): ping-pong activations and a BF16 copy of x/y
+  void *ia = nullptr, *ib = nullptr, *ic = nullptr;
+  long long inf_bytes = 0;
+  int *order = nullptr;  // minibatch gather indices (device)
+  int order_cap = 0;
+  DevMem mem, ws;        // mem: fixed buffers; ws: workspaces (reallocated when they grow)
+};
+
 struct mg_handle {
   mg_options opts{};
   int layout = 0, n = 0, p = 0, q = 0, C = 1;
@@ -133,20 +153,32 @@ struct mg_handle {
     const double *b = nullptr;
     double *x = nullptr;
     double rtol = -1.0;
-    int maxit = 0, restart = 0;
+    int maxit = 0, restart = 0, gen = -1;
   } gkey;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   long long g_init = 0, g_body = 0, g_coarse = 0;  // kernel launches per region of the graph
+  // learned coarse correction: network (not owned), admission threshold on the
+  // residual reduction, workspaces, counters; recording of (r, y) coarse pairs
+  mg_net *net = nullptr;
+  double admit = 0.5;
+  int net_bf16 = 1;
+  void *net_x = nullptr, *net_a = nullptr, *net_b = nullptr;  // network input/output and ping-pong activations
+  double *net_e = nullptr, *net_r = nullptr;
+  int *net_flag = nullptr;         // [0] admitted (graph mode), [1] admitted count
+  int coarse_learned = 0;          // coarse solves answered by the network in the last solve (host loops)
+  float *rec_r = nullptr, *rec_y = nullptr;
+  int rec_max = 0, rec_count = 0;
+  int gen = 0;  // bumped when a change invalidates captured graphs (attach/detach of a network)
 };
 
 namespace {
 
 // kernel categories reported by mg_profile_read
 enum Cat { CAT_BLOCK_SOLVE = 0, CAT_APPLY, CAT_RESTRICT, CAT_PROLONG, CAT_CHAIN, CAT_DOT, CAT_AXPY, CAT_SMALL,
-           CAT_CONVERT, CAT_SETUP, CAT_COUNT };
+           CAT_CONVERT, CAT_SETUP, CAT_NET, CAT_COUNT };
 const char *kCatNames[CAT_COUNT] = {"block_solve", "apply", "residual_restrict", "prolong_add", "sgs_chain",
-                                    "multidot", "axpy_scale", "arnoldi_scalar", "convert", "setup"};
+                                    "multidot", "axpy_scale", "arnoldi_scalar", "convert", "setup", "net_coarse"};
 
 cudaEvent_t take_event(mg_handle *h) {
   if (h->ev_pool.empty()) {
@@ -586,6 +618,79 @@ void sgs_fp64<float>(mg_handle *h, Level &lev, const double *r, double *y, cudaS
   convert_back<float>(h, d.y, y, lev.len, s);
 }
 
+// ---------------------------------------------------------------------------
+// Learned coarse correction: network forward pass and the admission test
+
+// The network's forward pass in storage type T (inference): x -> y through
+// ping-pong buffers (x == y allowed).  h (may be NULL) counts and times the launches.
+template <typename T>
+void net_forward_storage(mg_handle *h, const T *x, int B, int H, int Wd, T *y, T *bufA, T *bufB, const T *params,
+                         cudaStream_t s) {
+  const T *in = x;
+  for (int l = 0; l < kNetLayers; ++l) {
+    T *out = (l == kNetLayers - 1) ? y : ((l % 2 == 0) ? bufA : bufB);
+    const T *W = params + net_layer_offset(l);
+    const T *bias = W + (long long)net_ch(l + 1) * net_ch(l) * kNetKT * kNetKX;
+    const long long n = (long long)B * net_ch(l + 1) * H * Wd;
+    const double flops = 2.0 * n * net_ch(l) * kNetKT * kNetKX;
+    if (h) {
+      Bracket br(h, CAT_NET, s, (double)sizeof(T) * (n + (double)B * net_ch(l) * H * Wd), flops);
+      k_conv_fwd<T><<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(in, W, bias, out, nullptr, B, net_ch(l),
+                                                               net_ch(l + 1), H, Wd, l < kNetLayers - 1);
+      ck_launch();
+    } else {
+      k_conv_fwd<T><<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(in, W, bias, out, nullptr, B, net_ch(l),
+                                                               net_ch(l + 1), H, Wd, l < kNetLayers - 1);
+      ck_launch();
+    }
+    in = out;
+  }
+}
+
+void net_refresh_bf16(mg_net *net, cudaStream_t s) {
+  if (net->bf16_valid) return;
+  k_f32_to_bf16<<<grid_for(kNetParams, 256), 256, 0, s>>>(net->params, net->params_bf16, kNetParams);
+  ck_launch();
+  net->bf16_valid = true;
+}
+
+// e = ||r|| net(r / ||r||) on the coarse level (K.scal holds ||r||, 1/||r||)
+void net_coarse_proposal(mg_handle *h, Level &lev, const mg_handle::Krylov &K, cudaStream_t s) {
+  mg_net *net = h->net;
+  const long long len = lev.len;
+  const int H = lev.n, Wd = h->p;
+  if (h->net_bf16) {
+    if (!h->capturing) net_refresh_bf16(net, s);
+    using B16 = __nv_bfloat16;
+    B16 *xin = static_cast<B16 *>(h->net_x), *a = static_cast<B16 *>(h->net_a), *b = static_cast<B16 *>(h->net_b);
+    {
+      Bracket br(h, CAT_NET, s);
+      k_net_input<B16><<<grid_for(len, 256), 256, 0, s>>>(h->cr, K.scal, xin, len);
+      ck_launch();
+    }
+    net_forward_storage<B16>(h, xin, 1, H, Wd, xin, a, b, net->params_bf16, s);
+    {
+      Bracket br(h, CAT_NET, s);
+      k_net_output<B16><<<grid_for(len, 256), 256, 0, s>>>(xin, K.scal, h->net_e, len);
+      ck_launch();
+    }
+  } else {
+    float *xin = static_cast<float *>(h->net_x), *a = static_cast<float *>(h->net_a),
+          *b = static_cast<float *>(h->net_b);
+    {
+      Bracket br(h, CAT_NET, s);
+      k_net_input<float><<<grid_for(len, 256), 256, 0, s>>>(h->cr, K.scal, xin, len);
+      ck_launch();
+    }
+    net_forward_storage<float>(h, xin, 1, H, Wd, xin, a, b, net->params, s);
+    {
+      Bracket br(h, CAT_NET, s);
+      k_net_output<float><<<grid_for(len, 256), 256, 0, s>>>(xin, K.scal, h->net_e, len);
+      ck_launch();
+    }
+  }
+}
+
 // Coarse solve inside a captured graph: the same GMRES with its loop as a
 // WHILE node whose condition the step-control kernel sets on the device.
 template <typename T>
@@ -599,10 +704,18 @@ void coarse_solve_graph(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
   const int limit = fixed ? std::min(o.coarse_fixed_iters, h->cmax) : o.coarse_maxit;
   convert_back<T>(h, r_in, h->cr, len, s);
   norm_into(h, K, h->cr, len, s);
+  if (h->net) {  // the network's proposal, admitted if it reduces the residual enough
+    net_coarse_proposal(h, lev, K, s);
+    launch_apply<double>(h, lev.d.view, h->net_e, h->cr, h->net_r, s);
+    multidot(h, h->net_r, len, 1, h->net_r, len, K.nrm2 + 3, 0, s);
+    Bracket br(h, CAT_SMALL, s);
+    k_net_judge<<<1, 1, 0, s>>>(K.nrm2 + 3, K.scal, h->admit, h->net_flag);
+    ck_launch();
+  }
   const cudaGraphConditionalHandle hdl = new_handle(s);
   {
     Bracket br(h, CAT_SMALL, s);
-    k_ctl_start<<<1, 1, 0, s>>>(st, K.scal, fixed ? -1.0 : o.coarse_rtol, hdl);
+    k_ctl_start<<<1, 1, 0, s>>>(st, K.scal, fixed ? -1.0 : o.coarse_rtol, hdl, h->net ? h->net_flag : nullptr);
     ck_launch();
   }
   {
@@ -645,6 +758,11 @@ void coarse_solve_graph(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
     ck_launch();
   }
   multi_axpy(h, h->cy, h->cZ, len, K.ycoef, limit, 1.0, len, s, nullptr, &st->kcount);
+  if (h->net) {
+    Bracket br(h, CAT_SMALL, s);
+    k_copy_if<<<grid_for(len, 256), 256, 0, s>>>(h->cy, h->net_e, len, h->net_flag);
+    ck_launch();
+  }
   convert<T>(h, h->cy, y_out, len, s);
 }
 
@@ -667,6 +785,19 @@ void coarse_solve(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
   if (!(beta > 0.0)) {
     ck(cudaMemsetAsync(y_out, 0, len * sizeof(T), s));
     return;
+  }
+  if (h->net) {  // the network's proposal, admitted if it reduces the residual enough
+    net_coarse_proposal(h, lev, K, s);
+    launch_apply<double>(h, lev.d.view, h->net_e, h->cr, h->net_r, s);
+    multidot(h, h->net_r, len, 1, h->net_r, len, K.nrm2 + 3, 0, s);
+    double rr = 0.0;
+    ck(cudaMemcpyAsync(&rr, K.nrm2 + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    if (std::sqrt(rr) <= h->admit * beta) {
+      h->coarse_learned++;
+      convert<T>(h, h->net_e, y_out, len, s);
+      return;
+    }
   }
   const int limit = o.coarse_fixed_iters > 0 ? std::min(o.coarse_fixed_iters, h->cmax) : o.coarse_maxit;
   {
@@ -699,6 +830,13 @@ void coarse_solve(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
   }
   ck(cudaMemsetAsync(h->cy, 0, len * sizeof(double), s));
   multi_axpy(h, h->cy, h->cZ, len, K.ycoef, k, 1.0, len, s);
+  if (h->rec_r && h->rec_count < h->rec_max) {  // training pair of the plain method, scaled by 1/||r||
+    Bracket br(h, CAT_SMALL, s);
+    k_record_pair<<<grid_for(len, 256), 256, 0, s>>>(h->cr, h->cy, K.scal, h->rec_r + (long long)h->rec_count * len,
+                                                     h->rec_y + (long long)h->rec_count * len, len);
+    ck_launch();
+    h->rec_count++;
+  }
   convert<T>(h, h->cy, y_out, len, s);
 }
 
@@ -964,6 +1102,7 @@ void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, in
   h->gkey.rtol = rtol;
   h->gkey.maxit = maxit;
   h->gkey.restart = m;
+  h->gkey.gen = h->gen;
 }
 
 // workspace of a solve with restart m (grown on demand)
@@ -976,6 +1115,11 @@ void prepare_solve(mg_handle *h, int m, cudaStream_t s) {
     h->fx_stage = h->mem.alloc<double>(len);
     h->fb_stage = h->mem.alloc<double>(len);
   }
+  h->coarse_learned = 0;
+  if (h->net) {
+    if (h->net_bf16) net_refresh_bf16(h->net, s);
+    ck(cudaMemsetAsync(h->net_flag, 0, 2 * sizeof(int), s));
+  }
 }
 
 // the graph of a batch of solves (one branch per system), cached per host thread
@@ -983,6 +1127,7 @@ struct BatchGraph {
   std::vector<mg_handle *> hs;
   std::vector<const double *> b;
   std::vector<double *> x;
+  std::vector<int> gen;
   double rtol = -1.0;
   int maxit = 0, restart = 0;
   cudaGraph_t graph = nullptr;
@@ -1392,7 +1537,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
     if (h->opts.device_loops) {
       // one CUDA graph per solve: loops on the device, one read-back at the end
       if (!h->gexec || h->gkey.b != b || h->gkey.x != x || h->gkey.rtol != rtol || h->gkey.maxit != maxit ||
-          h->gkey.restart != m) {
+          h->gkey.restart != m || h->gkey.gen != h->gen) {
         ck(cudaStreamSynchronize(s));
         build_solve_graph(h, b, x, rtol, maxit, m);
       }
@@ -1406,6 +1551,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       ck(cudaMemcpyAsync(&cs, h->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(&bad, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(h->host_scal, h->kf.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (h->net) ck(cudaMemcpyAsync(&h->coarse_learned, h->net_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
       if (!x_dev) ck(cudaMemcpyAsync(x_out, x, len * sizeof(double), cudaMemcpyDeviceToHost, s));
       ck(cudaStreamSynchronize(s));
       total = fs.total;
@@ -1514,6 +1660,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
     info->coarse_iters = h->coarse_iters;
     info->relres = est_rel;
     info->true_relres = true_rel;
+    info->coarse_learned = h->coarse_learned;
   }
   return status;
 }
@@ -1540,7 +1687,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
     for (int i = 0; i < count; ++i) prepare_solve(hs[i], m, s);
     bool same = bg.exec && (int)bg.hs.size() == count && bg.rtol == rtol && bg.maxit == maxit && bg.restart == m;
     for (int i = 0; same && i < count; ++i) same = bg.hs[i] == hs[i] && bg.b[i] == b[i] && bg.x[i] == x[i];
-    for (int i = 0; same && i < count; ++i) same = hs[i]->fm >= m;
+    for (int i = 0; same && i < count; ++i) same = hs[i]->fm >= m && bg.gen[i] == hs[i]->gen;
     if (!same) {
       ck(cudaStreamSynchronize(s));
       if (bg.exec) cudaGraphExecDestroy(bg.exec);
@@ -1587,6 +1734,8 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
       bg.hs.assign(hs, hs + count);
       bg.b.assign(b, b + count);
       bg.x.assign(x, x + count);
+      bg.gen.resize(count);
+      for (int i = 0; i < count; ++i) bg.gen[i] = hs[i]->gen;
       bg.rtol = rtol;
       bg.maxit = maxit;
       bg.restart = m;
@@ -1595,7 +1744,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
       for (int i = 0; i < count; ++i) hs[i]->gkey.b = nullptr;
     }
     std::vector<KState> before(count), fs(count), cs(count);
-    std::vector<int> bad(count);
+    std::vector<int> bad(count), learned(count, 0);
     std::vector<double> tr(4 * (size_t)count);
     for (int i = 0; i < count; ++i)
       ck(cudaMemcpyAsync(&before[i], hs[i]->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
@@ -1606,6 +1755,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
       ck(cudaMemcpyAsync(&cs[i], hs[i]->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(&bad[i], hs[i]->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(&tr[4 * (size_t)i], hs[i]->kf.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (hs[i]->net) ck(cudaMemcpyAsync(&learned[i], hs[i]->net_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
     ck(cudaStreamSynchronize(s));
     for (int i = 0; i < count; ++i) {
@@ -1629,6 +1779,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
         infos[i].coarse_iters = (int)citers;
         infos[i].relres = est_rel;
         infos[i].true_relres = true_rel;
+        infos[i].coarse_learned = learned[i];
       }
       if (st < 0 && (worst >= 0 || st < worst)) worst = st;
       else if (st == MG_NOT_CONVERGED && worst == MG_OK) worst = st;
@@ -1729,3 +1880,341 @@ extern "C" int mg_true_residual_noalloc(mg_handle *h, const double *b, const dou
   }
   return MG_OK;
 }
+
+// ===========================================================================
+// Learned coarse-grid correction: the network object, its training, and its
+// use as the coarse solve of a handle's V-cycles.
+
+namespace {
+
+constexpr int kLossPartials = 1024;
+
+// training workspace for `batch` samples of T x X (grown on demand)
+void net_ensure_train(mg_net *net, int batch, long long TX, int minibatches) {
+  const long long need = (long long)batch * 32 * TX;
+  if (need <= net->ws_elems && minibatches <= net->ws_batch) return;
+  ck(cudaDeviceSynchronize());
+  net->ws.release();
+  net->ws_elems = 0;
+  net->ws_batch = 0;
+  const long long cap = need;
+  for (int l = 1; l < kNetLayers; ++l) net->h[l] = net->ws.alloc<float>((size_t)cap);
+  net->h[kNetLayers] = net->ws.alloc<float>((size_t)cap);
+  for (int l = 0; l < kNetLayers - 1; ++l) net->z[l] = net->ws.alloc<float>((size_t)cap);
+  net->g0 = net->ws.alloc<float>((size_t)cap);
+  net->g1 = net->ws.alloc<float>((size_t)cap);
+  net->bx = net->ws.alloc<float>((size_t)cap);
+  net->by = net->ws.alloc<float>((size_t)cap);
+  net->loss = net->ws.alloc<float>((size_t)std::max(1, minibatches));
+  net->ws_elems = cap;
+  net->ws_batch = std::max(1, minibatches);
+}
+
+// forward (keeping every layer's output and pre-activation), MSE loss into
+// loss_dev[0], backward into net->grad
+void net_loss_grad_dev(mg_net *net, const float *x, const float *target, int B, int T, int X, float *loss_dev,
+                       cudaStream_t s) {
+  const long long TX = (long long)T * X;
+  const float *in = x;
+  for (int l = 0; l < kNetLayers; ++l) {
+    const float *W = net->params + net_layer_offset(l);
+    const float *bias = W + (long long)net_ch(l + 1) * net_ch(l) * kNetKT * kNetKX;
+    const long long n = (long long)B * net_ch(l + 1) * TX;
+    const bool act = l < kNetLayers - 1;
+    k_conv_fwd<float><<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(in, W, bias, net->h[l + 1], act ? net->z[l] : nullptr,
+                                                                B, net_ch(l), net_ch(l + 1), T, X, act);
+    ck_launch();
+    in = net->h[l + 1];
+  }
+  const long long nout = (long long)B * net_ch(kNetLayers) * TX;
+  const int G = grid_for(nout, 256, kLossPartials);
+  k_mse<<<G, 256, 0, s>>>(net->h[kNetLayers], target, net->g0, nout, net->partial);
+  ck_launch();
+  k_sum_partials<<<1, 32, 0, s>>>(net->partial, G, 1.0f / (float)nout, loss_dev);
+  ck_launch();
+  float *g = net->g0, *other = net->g1;
+  for (int l = kNetLayers - 1; l >= 0; --l) {
+    const int C = net_ch(l), O = net_ch(l + 1);
+    if (l < kNetLayers - 1) {
+      const long long n = (long long)B * O * TX;
+      k_leaky_bwd<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(g, net->z[l], n);
+      ck_launch();
+    }
+    const float *hin = l == 0 ? x : net->h[l];
+    float *gW = net->grad + net_layer_offset(l);
+    float *gb = gW + (long long)O * C * kNetKT * kNetKX;
+    k_conv_bwd_weights<<<O * C, 256, 0, s>>>(g, hin, gW, gb, B, C, O, T, X);
+    ck_launch();
+    if (l > 0) {
+      const float *W = net->params + net_layer_offset(l);
+      const long long n = (long long)B * C * TX;
+      k_conv_bwd_data<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(g, W, other, B, C, O, T, X);
+      ck_launch();
+      std::swap(g, other);
+    }
+  }
+}
+
+void net_adam(mg_net *net, float lr, float b1, float b2, float eps, cudaStream_t s) {
+  net->step++;
+  const double c1 = 1.0 - std::pow((double)b1, net->step), c2 = 1.0 - std::pow((double)b2, net->step);
+  k_adam<<<grid_for(kNetParams, 256), 256, 0, s>>>(net->params, net->grad, net->m, net->v, kNetParams, lr, b1, b2,
+                                                   eps, (float)c1, (float)c2);
+  ck_launch();
+  net->bf16_valid = false;
+}
+
+// splitmix64 (Steele, Lea and Flood 2014)
+struct SplitMix64 {
+  unsigned long long x;
+  unsigned long long next() {
+    unsigned long long z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+};
+
+template <typename F>
+int net_guard(F &&f) {
+  try {
+    f();
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    return MG_ERR_OOM;
+  }
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long mg_net_param_count(void) { return kNetParams; }
+
+void mg_net_destroy(mg_net *net) {
+  if (!net) return;
+  cudaDeviceSynchronize();
+  net->ws.release();
+  net->mem.release();
+  for (void *p : {net->ia, net->ib, net->ic, static_cast<void *>(net->order)})
+    if (p) cudaFree(p);
+  delete net;
+}
+
+int mg_net_create(const float *init_params, mg_net **out) {
+  if (!init_params || !out) return MG_ERR_ARG;
+  *out = nullptr;
+  mg_net *net = new (std::nothrow) mg_net();
+  if (!net) return MG_ERR_OOM;
+  const int st = net_guard([&] {
+    net->params = net->mem.alloc<float>(kNetParams);
+    net->grad = net->mem.alloc<float>(kNetParams);
+    net->m = net->mem.alloc<float>(kNetParams);
+    net->v = net->mem.alloc<float>(kNetParams);
+    net->partial = net->mem.alloc<float>(kLossPartials);
+    net->params_bf16 = net->mem.alloc<__nv_bfloat16>(kNetParams);
+    ck(cudaMemcpy(net->params, init_params, kNetParams * sizeof(float), cudaMemcpyHostToDevice));
+    ck(cudaMemset(net->grad, 0, kNetParams * sizeof(float)));
+    ck(cudaMemset(net->m, 0, kNetParams * sizeof(float)));
+    ck(cudaMemset(net->v, 0, kNetParams * sizeof(float)));
+  });
+  if (st != MG_OK) {
+    mg_net_destroy(net);
+    return st;
+  }
+  *out = net;
+  return MG_OK;
+}
+
+int mg_net_set_params(mg_net *net, const float *params) {
+  if (!net || !params) return MG_ERR_ARG;
+  return net_guard([&] {
+    ck(cudaDeviceSynchronize());
+    ck(cudaMemcpy(net->params, params, kNetParams * sizeof(float), cudaMemcpyHostToDevice));
+    net->bf16_valid = false;
+  });
+}
+
+int mg_net_get_params(const mg_net *net, float *params) {
+  if (!net || !params) return MG_ERR_ARG;
+  return net_guard([&] {
+    ck(cudaDeviceSynchronize());
+    ck(cudaMemcpy(params, net->params, kNetParams * sizeof(float), cudaMemcpyDeviceToHost));
+  });
+}
+
+int mg_net_get_grad(const mg_net *net, float *grad) {
+  if (!net || !grad) return MG_ERR_ARG;
+  return net_guard([&] {
+    ck(cudaDeviceSynchronize());
+    ck(cudaMemcpy(grad, net->grad, kNetParams * sizeof(float), cudaMemcpyDeviceToHost));
+  });
+}
+
+int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *y, int bf16, void *stream) {
+  if (!net || !x || !y || batch < 1 || T < 1 || X < 1 || (bf16 != 0 && bf16 != 1)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long TX = (long long)T * X;
+  return net_guard([&] {
+    const long long bytes = (long long)batch * 32 * TX * (long long)sizeof(float);
+    if (bytes > net->inf_bytes) {
+      ck(cudaStreamSynchronize(s));
+      for (void *p : {net->ia, net->ib, net->ic})
+        if (p) cudaFree(p);
+      net->ia = net->ib = net->ic = nullptr;
+      net->inf_bytes = 0;
+      for (void **p : {&net->ia, &net->ib, &net->ic}) {
+        cudaError_t e = cudaMalloc(p, (size_t)bytes);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+          throw std::bad_alloc();
+        }
+      }
+      net->inf_bytes = bytes;
+    }
+    const long long nio = (long long)batch * net_ch(0) * TX;
+    if (bf16) {
+      net_refresh_bf16(net, s);
+      using B16 = __nv_bfloat16;
+      B16 *c = static_cast<B16 *>(net->ic);
+      k_f32_to_bf16<<<grid_for(nio, 256), 256, 0, s>>>(x, c, nio);
+      ck_launch();
+      net_forward_storage<B16>(nullptr, c, batch, T, X, c, static_cast<B16 *>(net->ia), static_cast<B16 *>(net->ib),
+                               net->params_bf16, s);
+      k_bf16_to_f32<<<grid_for(nio, 256), 256, 0, s>>>(c, y, nio);
+      ck_launch();
+    } else {
+      net_forward_storage<float>(nullptr, x, batch, T, X, y, static_cast<float *>(net->ia),
+                                 static_cast<float *>(net->ib), net->params, s);
+    }
+  });
+}
+
+int mg_net_loss_grad(mg_net *net, const float *x, const float *target, int batch, int T, int X, float *loss,
+                     void *stream) {
+  if (!net || !x || !target || !loss || batch < 1 || T < 1 || X < 1) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return net_guard([&] {
+    net_ensure_train(net, batch, (long long)T * X, 1);
+    net_loss_grad_dev(net, x, target, batch, T, X, net->loss, s);
+    ck(cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+  });
+}
+
+int mg_net_adam_step(mg_net *net, float lr, float beta1, float beta2, float eps, void *stream) {
+  if (!net || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return MG_ERR_ARG;
+  return net_guard([&] { net_adam(net, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)); });
+}
+
+int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count, int T, int X, int batch, int epochs,
+                 float lr, unsigned long long seed, float *epoch_loss, void *stream) {
+  if (!net || !x_all || !y_all || count < 1 || T < 1 || X < 1 || batch < 1 || epochs < 0 || !(lr > 0.f))
+    return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long TX = (long long)T * X, row = (long long)net_ch(0) * TX;
+  const int B = std::min(batch, count);
+  const int nmb = (count + B - 1) / B;
+  return net_guard([&] {
+    net_ensure_train(net, B, TX, nmb);
+    if (net->order_cap < count) {
+      ck(cudaStreamSynchronize(s));
+      if (net->order) cudaFree(net->order);
+      net->order = nullptr;
+      net->order_cap = 0;
+      cudaError_t e = cudaMalloc(&net->order, (size_t)count * sizeof(int));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw std::bad_alloc();
+      }
+      net->order_cap = count;
+    }
+    SplitMix64 rng{seed};
+    std::vector<int> order(count);
+    std::vector<float> losses(nmb);
+    for (int e = 0; e < epochs; ++e) {
+      // Fisher-Yates shuffle of the sample order
+      for (int i = 0; i < count; ++i) order[i] = i;
+      for (int i = count - 1; i > 0; --i) std::swap(order[i], order[(int)(rng.next() % (unsigned long long)(i + 1))]);
+      ck(cudaMemcpyAsync(net->order, order.data(), (size_t)count * sizeof(int), cudaMemcpyHostToDevice, s));
+      for (int k = 0; k < nmb; ++k) {
+        const int b0 = k * B, nb = std::min(B, count - b0);
+        k_gather_rows<<<grid_for((long long)nb * row, 256, 1 << 20), 256, 0, s>>>(x_all, net->order + b0, nb, row,
+                                                                                    net->bx);
+        ck_launch();
+        k_gather_rows<<<grid_for((long long)nb * row, 256, 1 << 20), 256, 0, s>>>(y_all, net->order + b0, nb, row,
+                                                                                    net->by);
+        ck_launch();
+        net_loss_grad_dev(net, net->bx, net->by, nb, T, X, net->loss + k, s);
+        net_adam(net, lr, 0.9f, 0.999f, 1e-8f, s);
+      }
+      ck(cudaMemcpyAsync(losses.data(), net->loss, (size_t)nmb * sizeof(float), cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));  // also keeps `order` alive until its copy has run
+      if (epoch_loss) {
+        double sum = 0.0;
+        for (float l : losses) sum += l;
+        epoch_loss[e] = (float)(sum / nmb);
+      }
+    }
+  });
+}
+
+int mg_coarse_shape(const mg_handle *h, int *T, int *X) {
+  if (!h || !T || !X) return MG_ERR_ARG;
+  *T = h->lv.back().n;
+  *X = h->p;
+  return MG_OK;
+}
+
+int mg_attach_coarse_net(mg_handle *h, mg_net *net, double admit, int bf16) {
+  if (!h) return MG_ERR_ARG;
+  if (!net) {
+    if (h->net) {
+      h->net = nullptr;
+      h->gen++;
+    }
+    return MG_OK;
+  }
+  if (!(admit > 0.0 && admit < 1.0) || (bf16 != 0 && bf16 != 1)) return MG_ERR_ARG;
+  if (h->q != h->p) return MG_ERR_UNSUPPORTED;
+  return net_guard([&] {
+    const Level &cl = h->lv.back();
+    if (!h->net_e) {
+      const long long TX = (long long)cl.n * h->p;
+      h->net_x = h->mem.alloc<float>((size_t)net_ch(0) * TX);
+      h->net_a = h->mem.alloc<float>((size_t)32 * TX);
+      h->net_b = h->mem.alloc<float>((size_t)32 * TX);
+      h->net_e = h->mem.alloc<double>(cl.len);
+      h->net_r = h->mem.alloc<double>(cl.len);
+      h->net_flag = h->mem.alloc<int>(2);
+      ck(cudaMemset(h->net_flag, 0, 2 * sizeof(int)));
+    }
+    h->net = net;
+    h->admit = admit;
+    h->net_bf16 = bf16;
+    h->gen++;
+  });
+}
+
+int mg_record_coarse(mg_handle *h, float *r, float *y, int max_pairs) {
+  if (!h) return MG_ERR_ARG;
+  if (!r || !y || max_pairs < 1) {
+    h->rec_r = h->rec_y = nullptr;
+    h->rec_max = 0;
+    return MG_OK;
+  }
+  if (h->opts.device_loops) return MG_ERR_UNSUPPORTED;
+  h->rec_r = r;
+  h->rec_y = y;
+  h->rec_max = max_pairs;
+  h->rec_count = 0;
+  return MG_OK;
+}
+
+int mg_recorded_pairs(const mg_handle *h) { return h ? h->rec_count : MG_ERR_ARG; }
+
+}  // extern "C"

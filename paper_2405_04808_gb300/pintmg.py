@@ -36,6 +36,9 @@ COARSE_PRECOND = {"sgs": 0, "jacobi": 1, "fgs": 2, "bgs": 3}
 EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmres_solve_batched",
             "mg_vector_length",
             "mg_launch_count", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
+            "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
+            "mg_net_forward", "mg_net_loss_grad", "mg_net_adam_step", "mg_net_train", "mg_net_destroy",
+            "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape",
             "mg_destroy", "mg_status_string", "mg_last_cuda_error")
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -57,7 +60,7 @@ class MGOptions(ctypes.Structure):
 class MGSolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("vcycles", ctypes.c_int),
                 ("coarse_iters", ctypes.c_int),
-                ("relres", ctypes.c_double), ("true_relres", ctypes.c_double)]
+                ("relres", ctypes.c_double), ("true_relres", ctypes.c_double), ("coarse_learned", ctypes.c_int)]
 
 
 class PintmgError(RuntimeError):
@@ -104,6 +107,26 @@ def lib():
         L.mg_true_residual_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]
         L.mg_true_residual_noalloc.restype = ctypes.c_int
+        vp, ci, cf = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        fp = ctypes.POINTER(ctypes.c_float)
+        for name, args, res in (
+                ("mg_net_param_count", [], ctypes.c_longlong),
+                ("mg_net_create", [fp, ctypes.POINTER(vp)], ci),
+                ("mg_net_set_params", [vp, fp], ci),
+                ("mg_net_get_params", [vp, fp], ci),
+                ("mg_net_get_grad", [vp, fp], ci),
+                ("mg_net_forward", [vp, vp, ci, ci, ci, vp, ci, vp], ci),
+                ("mg_net_loss_grad", [vp, vp, vp, ci, ci, ci, fp, vp], ci),
+                ("mg_net_adam_step", [vp, cf, cf, cf, cf, vp], ci),
+                ("mg_net_train", [vp, vp, vp, ci, ci, ci, ci, ci, cf, ctypes.c_ulonglong, fp, vp], ci),
+                ("mg_net_destroy", [vp], None),
+                ("mg_attach_coarse_net", [vp, vp, ctypes.c_double, ci], ci),
+                ("mg_record_coarse", [vp, vp, vp, ci], ci),
+                ("mg_recorded_pairs", [vp], ci),
+                ("mg_coarse_shape", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci)):
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
         L.mg_destroy.argtypes = [ctypes.c_void_p]
         L.mg_destroy.restype = None
         L.mg_status_string.argtypes = [ctypes.c_int]
@@ -189,7 +212,7 @@ def mg_launch_count(h) -> int:
 
 PROFILE_ALL = 0xFFFF
 PROFILE_CATEGORIES = ("block_solve", "apply", "residual_restrict", "prolong_add", "sgs_chain", "multidot",
-                      "axpy_scale", "arnoldi_scalar", "convert", "setup")
+                      "axpy_scale", "arnoldi_scalar", "convert", "setup", "net_coarse")
 
 
 def mg_profile_enable(h, mask: int = PROFILE_ALL) -> None:
@@ -217,6 +240,107 @@ def mg_true_residual_noalloc(h, b_ptr: int, x_ptr: int, out_ptr: int, stream: in
     """||b - A x|| and ||b - A x|| / ||b|| into out_ptr[0:2] (device), allocating nothing."""
     return lib().mg_true_residual_noalloc(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
                                           ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
+
+
+# --------------------------------------------------------------------------
+# learned coarse-grid correction
+
+def _check(code, what):
+    if code != MG_OK:
+        raise PintmgError(code, what)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def mg_net_param_count() -> int:
+    return int(lib().mg_net_param_count())
+
+
+def mg_net_create(init_params) -> int:
+    """A network on the current device from mg_net_param_count() initial parameters (host array)."""
+    p = np.ascontiguousarray(init_params, dtype=np.float32)
+    if p.size != mg_net_param_count():
+        raise PintmgError(MG_ERR_ARG, "mg_net_create")
+    net = ctypes.c_void_p()
+    _check(lib().mg_net_create(_fptr(p), ctypes.byref(net)), "mg_net_create")
+    return net.value
+
+
+def mg_net_set_params(net, params) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != mg_net_param_count():
+        raise PintmgError(MG_ERR_ARG, "mg_net_set_params")
+    _check(lib().mg_net_set_params(ctypes.c_void_p(net), _fptr(p)), "mg_net_set_params")
+
+
+def mg_net_get_params(net) -> np.ndarray:
+    out = np.empty(mg_net_param_count(), dtype=np.float32)
+    _check(lib().mg_net_get_params(ctypes.c_void_p(net), _fptr(out)), "mg_net_get_params")
+    return out
+
+
+def mg_net_get_grad(net) -> np.ndarray:
+    out = np.empty(mg_net_param_count(), dtype=np.float32)
+    _check(lib().mg_net_get_grad(ctypes.c_void_p(net), _fptr(out)), "mg_net_get_grad")
+    return out
+
+
+def mg_net_forward(net, x_ptr: int, batch: int, T: int, X: int, y_ptr: int, bf16: bool = False,
+                   stream: int = 0) -> None:
+    _check(lib().mg_net_forward(ctypes.c_void_p(net), ctypes.c_void_p(x_ptr), batch, T, X, ctypes.c_void_p(y_ptr),
+                                1 if bf16 else 0, ctypes.c_void_p(stream)), "mg_net_forward")
+
+
+def mg_net_loss_grad(net, x_ptr: int, t_ptr: int, batch: int, T: int, X: int, stream: int = 0) -> float:
+    loss = ctypes.c_float()
+    _check(lib().mg_net_loss_grad(ctypes.c_void_p(net), ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), batch, T, X,
+                                  ctypes.byref(loss), ctypes.c_void_p(stream)), "mg_net_loss_grad")
+    return float(loss.value)
+
+
+def mg_net_adam_step(net, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                     stream: int = 0) -> None:
+    _check(lib().mg_net_adam_step(ctypes.c_void_p(net), lr, beta1, beta2, eps, ctypes.c_void_p(stream)),
+           "mg_net_adam_step")
+
+
+def mg_net_train(net, x_ptr: int, y_ptr: int, count: int, T: int, X: int, batch: int, epochs: int, lr: float,
+                 seed: int, stream: int = 0) -> np.ndarray:
+    """Minibatch Adam over `count` device samples; returns each epoch's mean loss."""
+    losses = np.zeros(max(epochs, 1), dtype=np.float32)
+    _check(lib().mg_net_train(ctypes.c_void_p(net), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), count, T, X,
+                              batch, epochs, lr, ctypes.c_ulonglong(seed), _fptr(losses), ctypes.c_void_p(stream)),
+           "mg_net_train")
+    return losses[:epochs]
+
+
+def mg_net_destroy(net) -> None:
+    if net:
+        lib().mg_net_destroy(ctypes.c_void_p(net))
+
+
+def mg_attach_coarse_net(h, net, admit: float = 0.5, bf16: bool = True) -> None:
+    """Use `net` as h's coarse solve (GMRES+SGS as judge and fallback); net=None detaches."""
+    _check(lib().mg_attach_coarse_net(ctypes.c_void_p(h), ctypes.c_void_p(net or 0), float(admit),
+                                      1 if bf16 else 0), "mg_attach_coarse_net")
+
+
+def mg_record_coarse(h, r_ptr: int, y_ptr: int, max_pairs: int) -> None:
+    _check(lib().mg_record_coarse(ctypes.c_void_p(h), ctypes.c_void_p(r_ptr), ctypes.c_void_p(y_ptr),
+                                  int(max_pairs)), "mg_record_coarse")
+
+
+def mg_recorded_pairs(h) -> int:
+    return int(lib().mg_recorded_pairs(ctypes.c_void_p(h)))
+
+
+def mg_coarse_shape(h):
+    """(T, X) of the coarse level: the network's sample shape is (5, T, X)."""
+    T, X = ctypes.c_int(), ctypes.c_int()
+    _check(lib().mg_coarse_shape(ctypes.c_void_p(h), ctypes.byref(T), ctypes.byref(X)), "mg_coarse_shape")
+    return T.value, X.value
 
 
 def mg_destroy(h) -> None:

@@ -28,7 +28,8 @@ Random numbers: splitmix64 used as a counter-based generator,
 ``out_i = mix64(key + (i + 1) * 0x9E3779B97F4A7C15)`` with Vigna's mix64
 finaliser, ``key = mix64(seed * 65536 + stream)``; uniforms are the top 53
 bits; normals come from Box-Muller on consecutive pairs.  Streams: 1 control,
-2 right-hand side, 3 Burgers mode numbers, 4 Burgers mode amplitudes.
+2 right-hand side, 3 Burgers mode numbers, 4 Burgers mode amplitudes, 5 the
+coarse-correction network's initial weights.
 
 Matrix formats (the C-ABI's): a "dense" problem stores every p x p or p x q
 block row-major; a "tridiag" problem (q == p) stores every p x p tridiagonal
@@ -50,6 +51,7 @@ STREAM_CONTROL = 1
 STREAM_RHS = 2
 STREAM_MODES = 3
 STREAM_AMPL = 4
+STREAM_NET_INIT = 5
 
 
 def _mix64(z):
@@ -353,6 +355,10 @@ WORKLOADS = {
                                 levels=3, nu_pre=4, nu_post=4),
     "burgers_nx512_n8192": dict(make=lambda seed=3000: burgers(nx=512, n=8192, nu=0.005, seed=seed), seed=3000,
                                 levels=4, nu_pre=4, nu_post=4),
+    # the learned coarse correction's workload: training pairs come from seeded
+    # runs (seeds 5001, 5002, ...), the timed solve uses seed 5000
+    "burgers_nx256_n4096": dict(make=lambda seed=5000: burgers(nx=256, n=4096, nu=0.01, seed=seed), seed=5000,
+                                levels=4, nu_pre=4, nu_post=4),
 }
 
 
@@ -372,3 +378,25 @@ def batch_mix(seed: int = 4000, count: int = 32):
             nt = 256 if (k // 4) % 2 == 0 else 512
             out.append((burgers(nx=nx, n=nt, seed=sd), dict(levels=3, nu_pre=4, nu_post=4)))
     return out
+
+
+# --------------------------------------------------------------------------
+# the learned coarse correction's network: initial parameters
+
+NET_CHANNELS = (5, 32, 32, 32, 5)
+NET_KT, NET_KX = 3, 7
+
+
+def net_init_params(seed: int) -> np.ndarray:
+    """Initial parameters of the coarse-correction network, flat in the C-ABI's
+    layout (per layer: weights [out][in][time tap][space tap], then biases):
+    weights uniform in +-sqrt(6 / fan_in) (He et al. 2015), biases zero."""
+    sizes = [(co * ci * NET_KT * NET_KX, co, ci * NET_KT * NET_KX)
+             for ci, co in zip(NET_CHANNELS[:-1], NET_CHANNELS[1:])]
+    u = uniform(seed, STREAM_NET_INIT, sum(nw for nw, _, _ in sizes))
+    out, k = [], 0
+    for nw, nb, fan_in in sizes:
+        lim = math.sqrt(6.0 / fan_in)
+        out += [(2.0 * u[k:k + nw] - 1.0) * lim, np.zeros(nb)]
+        k += nw
+    return np.concatenate(out)

@@ -1,0 +1,246 @@
+"""Learned coarse correction on the GPU: the network's kernels against the CPU
+oracle (forward FP32 and BF16, loss and gradient, Adam), recorded training
+pairs against the oracle's coarse operator, FGMRES with the network attached,
+and what a trained network gains over the method without it."""
+import numpy as np
+import pytest
+
+from oracle import augmented as O
+from oracle import learned as NL
+from paper_2405_04808_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# FP32 forward: 4 layers of <= 672-term FP32 dot products (relative rounding
+# ~ sqrt(672) * 2^-24 per layer): 1e-5 relative in the 2-norm.
+FWD_FP32_RTOL = 1e-5
+# BF16 storage of parameters and activations (8-bit significand, unit
+# roundoff 2^-9 ~ 2e-3 per rounding, 5 roundings on a path): 2e-2.
+FWD_BF16_RTOL = 2e-2
+# FP32 gradient: sums over B*T*X positions of FP32 products: 1e-4 relative.
+GRAD_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2405_04808_gb300 import pintmg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pintmg.lib()
+    return pintmg
+
+
+def _params(seed):
+    p = W.net_init_params(seed)
+    rng = np.random.default_rng(seed)
+    p += 0.05 * rng.standard_normal(p.size)           # non-zero biases
+    return p.astype(np.float32)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.mark.parametrize("shape", [(1, 4, 5), (2, 9, 11), (3, 17, 40)])
+def test_forward_matches_oracle(P, shape):
+    B, T, X = shape
+    p = _params(11)
+    x = np.random.default_rng(5).standard_normal((B, 5, T, X)).astype(np.float32)
+    want, _ = NL.forward(p.astype(np.float64), x.astype(np.float64))
+    net = P.mg_net_create(p)
+    try:
+        xd = torch.tensor(x, device="cuda")
+        y = torch.empty_like(xd)
+        P.mg_net_forward(net, xd.data_ptr(), B, T, X, y.data_ptr(), bf16=False)
+        assert _rel(y.cpu().numpy(), want) <= FWD_FP32_RTOL
+        P.mg_net_forward(net, xd.data_ptr(), B, T, X, y.data_ptr(), bf16=True)
+        assert _rel(y.cpu().numpy(), want) <= FWD_BF16_RTOL
+        P.mg_net_forward(net, xd.data_ptr(), B, T, X, xd.data_ptr(), bf16=False)   # in place
+        assert _rel(xd.cpu().numpy(), want) <= FWD_FP32_RTOL
+    finally:
+        P.mg_net_destroy(net)
+
+
+@pytest.mark.parametrize("shape", [(1, 5, 8), (2, 7, 13), (4, 12, 33)])
+def test_loss_and_gradient_match_oracle(P, shape):
+    B, T, X = shape
+    p = _params(12)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((B, 5, T, X)).astype(np.float32)
+    t = rng.standard_normal((B, 5, T, X)).astype(np.float32)
+    loss_o, grad_o = NL.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    net = P.mg_net_create(p)
+    try:
+        xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        loss = P.mg_net_loss_grad(net, xd.data_ptr(), td.data_ptr(), B, T, X)
+        g = P.mg_net_get_grad(net)
+    finally:
+        P.mg_net_destroy(net)
+    assert abs(loss - loss_o) <= 1e-5 * loss_o
+    assert _rel(g, grad_o) <= GRAD_RTOL
+    # layer by layer too, so a small layer's error is not hidden by a large one's
+    k = 0
+    for Wt, b in NL.unpack(grad_o):
+        for part in (Wt.ravel(), b):
+            assert _rel(g[k:k + part.size], part) <= 10 * GRAD_RTOL
+            k += part.size
+
+
+def test_adam_steps_match_oracle(P):
+    B, T, X = 2, 6, 10
+    p = _params(13)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((B, 5, T, X)).astype(np.float32)
+    t = rng.standard_normal((B, 5, T, X)).astype(np.float32)
+    net = P.mg_net_create(p)
+    po = p.astype(np.float64)
+    m = np.zeros_like(po)
+    v = np.zeros_like(po)
+    try:
+        xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        for step in (1, 2, 3):
+            P.mg_net_loss_grad(net, xd.data_ptr(), td.data_ptr(), B, T, X)
+            g = P.mg_net_get_grad(net).astype(np.float64)   # the same gradient on both sides
+            P.mg_net_adam_step(net, 1e-3)
+            po, m, v = NL.adam_step(po, g, m, v, step, 1e-3)
+            got = P.mg_net_get_params(net)
+            assert np.max(np.abs(got - po)) <= 1e-6, step
+    finally:
+        P.mg_net_destroy(net)
+
+
+def test_argument_errors(P):
+    with pytest.raises(P.PintmgError):
+        P.mg_net_create(np.zeros(10, dtype=np.float32))
+    net = P.mg_net_create(_params(1))
+    try:
+        x = torch.zeros((1, 5, 4, 4), device="cuda")
+        with pytest.raises(P.PintmgError):
+            P.mg_net_forward(net, x.data_ptr(), 0, 4, 4, x.data_ptr())
+        with pytest.raises(P.PintmgError):
+            P.mg_net_adam_step(net, -1.0)
+        prob = W.vdp_paper(n=16)                      # dense, p == q == 2: accepted
+        h = P.mg_setup(prob, levels=2)
+        try:
+            P.mg_attach_coarse_net(h, net, admit=0.5)
+            with pytest.raises(P.PintmgError):
+                P.mg_attach_coarse_net(h, net, admit=1.5)
+            with pytest.raises(P.PintmgError):        # recording needs host-driven loops
+                P.mg_record_coarse(h, x.data_ptr(), x.data_ptr(), 1)
+            P.mg_attach_coarse_net(h, None)
+        finally:
+            P.mg_destroy(h)
+    finally:
+        P.mg_net_destroy(net)
+
+
+def _small_problem(seed):
+    return W.burgers(nx=32, n=64, seed=seed)
+
+
+SMALL = dict(levels=3, nu_pre=2, nu_post=2)
+
+
+def test_recorded_pairs_are_coarse_solves(P):
+    """Every recorded pair (r, y) has ||r|| = 1 and ||r - A_c y|| <= 1e-3 with A_c
+    the oracle's coarse operator (the coarse GMRES tolerance), up to FP32 storage."""
+    from paper_2405_04808_gb300 import learned as L
+    prob = _small_problem(31)
+    R, Y = L.collect_pairs([prob], SMALL, max_pairs=40, restart=50)
+    assert R.shape[0] == 40
+    Ac = O.Hierarchy(prob, O.MGOptions(levels=3, nu_pre=2, nu_post=2)).levels[-1].A
+    for k in range(R.shape[0]):
+        r = R[k].double().cpu().numpy().ravel()
+        y = Y[k].double().cpu().numpy().ravel()
+        assert abs(np.linalg.norm(r) - 1.0) <= 1e-6
+        assert np.linalg.norm(r - Ac @ y) <= 1e-3 + 1e-5
+
+
+@pytest.mark.parametrize("bf16", [True, False])
+def test_learned_fgmres_reaches_the_solution(P, bf16):
+    """With a network attached (untrained: its proposals are judged and mostly
+    rejected; admit 0.9 lets some through) FGMRES still reaches the direct
+    solution; the graph and host-loop solves agree bit for bit."""
+    prob = _small_problem(32)
+    ref = O.direct_solve(prob)
+    net = P.mg_net_create(_params(2))
+    out = {}
+    try:
+        for loops in (False, True):
+            h = P.mg_setup(prob, device_loops=loops, **SMALL)
+            try:
+                P.mg_attach_coarse_net(h, net, admit=0.9, bf16=bf16)
+                b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+                x = torch.zeros_like(b)
+                st, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, maxit=600, restart=100)
+                assert st == P.MG_OK, info.true_relres
+                out[loops] = (x.cpu().numpy(), info.iters, info.coarse_learned, info.coarse_iters)
+            finally:
+                P.mg_destroy(h)
+    finally:
+        P.mg_net_destroy(net)
+    for x, *_ in out.values():
+        assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert out[False][1:] == out[True][1:]
+    assert np.array_equal(out[False][0], out[True][0])
+
+
+def test_trained_network_gain(P, capsys):
+    """Train on the plain method's coarse pairs from seeded runs, then solve
+    held-out problems with and without the network.  What the network gains
+    is measured and printed; the test asserts what must hold whatever the gain:
+    training lowers the loss, the trained network's proposals reduce held-out
+    coarse residuals more than the untrained one's, and FGMRES with the
+    network converges to the same tolerance."""
+    from paper_2405_04808_gb300 import learned as L
+    train_probs = [_small_problem(40 + k) for k in range(6)]
+    R, Y = L.collect_pairs(train_probs, SMALL, max_pairs=600, restart=50, per_problem=100)
+    Rt, Yt = L.collect_pairs([_small_problem(90)], SMALL, max_pairs=50, restart=50)
+    count, _, T, X = R.shape
+    net0 = L.new_net(5)
+    net = L.new_net(5)
+    try:
+        losses = L.train(net, R, Y, epochs=30, batch=16, lr=2e-3, seed=1)
+        assert losses[-1] < 0.5 * losses[0], losses
+
+        def reduction(nt):
+            # rho = ||r - A_c net(r)|| / ||r|| on the held-out pairs (||r|| = 1), FP64 in the oracle's A_c
+            Ac = O.Hierarchy(_small_problem(90), O.MGOptions(levels=3, nu_pre=2, nu_post=2)).levels[-1].A
+            y = torch.empty_like(Rt)
+            P.mg_net_forward(nt, Rt.data_ptr(), Rt.shape[0], T, X, y.data_ptr(), bf16=True)
+            yy = y.double().cpu().numpy().reshape(Rt.shape[0], -1)
+            rr = Rt.double().cpu().numpy().reshape(Rt.shape[0], -1)
+            return np.array([np.linalg.norm(rr[k] - Ac @ yy[k]) for k in range(rr.shape[0])])
+
+        rho0, rho = reduction(net0), reduction(net)
+        assert np.median(rho) < np.median(rho0)
+        stats = {}
+        for name, nt in (("plain", None), ("learned", net)):
+            its, lrn, crs = [], [], []
+            for seed in (91, 92):
+                prob = _small_problem(seed)
+                h = P.mg_setup(prob, **SMALL)
+                try:
+                    if nt:
+                        P.mg_attach_coarse_net(h, nt, admit=0.5, bf16=True)
+                    b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+                    x = torch.zeros_like(b)
+                    st, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-8, maxit=2000, restart=400)
+                    assert st == P.MG_OK
+                    assert info.true_relres <= 1e-8 * 1.01
+                    its.append(info.iters)
+                    lrn.append(info.coarse_learned)
+                    crs.append(info.coarse_iters)
+                finally:
+                    P.mg_destroy(h)
+            stats[name] = (its, lrn, crs)
+        with capsys.disabled():
+            print(f"\nlearned coarse correction (Burgers nx=32 nt=64, {count} pairs, 30 epochs): "
+                  f"loss {losses[0]:.3g} -> {losses[-1]:.3g}; held-out median rho {np.median(rho0):.3f} -> "
+                  f"{np.median(rho):.3f}; iterations plain {stats['plain'][0]} vs learned {stats['learned'][0]}, "
+                  f"admitted coarse solves {stats['learned'][1]} of {stats['learned'][0]}, "
+                  f"coarse GMRES iterations {stats['plain'][2]} -> {stats['learned'][2]}")
+    finally:
+        P.mg_net_destroy(net0)
+        P.mg_net_destroy(net)

@@ -1,0 +1,71 @@
+"""Pins of the CPU oracle of the learned coarse correction's network."""
+import numpy as np
+import pytest
+
+from oracle import learned as NL
+from paper_2405_04808_gb300 import workloads as W
+
+
+def test_parameter_count_is_about_50k():
+    assert NL.param_count() == 49829
+
+
+def test_convolution_is_scipy_correlation():
+    """One input and one output channel: zero-padded 'same' correlation."""
+    signal = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((1, 1, 9, 13))
+    W = rng.standard_normal((1, 1, 3, 7))
+    y = NL.conv_forward(x, W, np.array([0.25]))
+    want = signal.correlate2d(x[0, 0], W[0, 0], mode="same", boundary="fill") + 0.25
+    assert np.allclose(y[0, 0], want, rtol=0, atol=1e-12)
+
+
+def test_gradients_match_finite_differences():
+    rng = np.random.default_rng(1)
+    p = W.net_init_params(3)
+    p += 0.05 * rng.standard_normal(p.size)          # non-zero biases
+    x = rng.standard_normal((2, 5, 6, 9))
+    t = rng.standard_normal((2, 5, 6, 9))
+    loss, g = NL.loss_and_grad(p, x, t)
+    idx = rng.choice(p.size, 40, replace=False)
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        fd = (NL.loss_and_grad(p + e, x, t)[0] - NL.loss_and_grad(p - e, x, t)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_adam_two_steps_by_hand():
+    """lr 0.1, beta 0.9 / 0.999: the first step moves every parameter by lr * sign(g)."""
+    p = np.array([1.0, -2.0])
+    g = np.array([0.5, -4.0])
+    p1, m, v = NL.adam_step(p, g, np.zeros(2), np.zeros(2), 1, 0.1, eps=0.0)
+    assert np.allclose(p1, [0.9, -1.9], atol=1e-15)
+    p2, m, v = NL.adam_step(p1, g, m, v, 2, 0.1, eps=0.0)
+    assert np.allclose(p2, [0.8, -1.8], atol=1e-12)   # constant gradient: mhat / sqrt(vhat) = sign(g)
+
+
+def test_seeded_initialisation_layout():
+    """The shared generator's layout agrees with the oracle's unpacking: biases zero, weights within He bounds."""
+    p = W.net_init_params(7)
+    assert p.size == NL.param_count()
+    for (Wt, b), (ci, kt, kx) in zip(NL.unpack(p), [(5, 3, 7), (32, 3, 7), (32, 3, 7), (32, 3, 7)]):
+        assert np.all(b == 0.0)
+        lim = np.sqrt(6.0 / (ci * kt * kx))
+        assert np.abs(Wt).max() <= lim and np.abs(Wt).max() > 0.9 * lim
+    assert np.array_equal(p, W.net_init_params(7)) and not np.array_equal(p, W.net_init_params(8))
+
+
+def test_delta_kernels_compose_to_the_activation():
+    """Centre-tap identity kernels: the network is leaky^3 elementwise (slope 0.1 -> 1e-3 on negatives)."""
+    layers = []
+    for ci, co in zip(NL.CHANNELS[:-1], NL.CHANNELS[1:]):
+        Wt = np.zeros((co, ci, NL.KT, NL.KX))
+        for c in range(min(ci, co)):
+            Wt[c, c, NL.KT // 2, NL.KX // 2] = 1.0
+        layers += [Wt.ravel(), np.zeros(co)]
+    p = np.concatenate(layers)
+    x = np.random.default_rng(4).standard_normal((1, 5, 4, 6))
+    y, _ = NL.forward(p, x)
+    assert np.allclose(y, np.where(x > 0, x, 1e-3 * x), atol=1e-15)

@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--allow-partial", action="store_true",
                     help="accept solves stopped by --maxit (bounded profiler captures only)")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    ap.add_argument("--learned-pairs", type=int, default=400,
+                    help="training pairs for the learned coarse correction variant (0 skips it)")
+    ap.add_argument("--learned-epochs", type=int, default=3)
     return ap.parse_args()
 
 
@@ -298,6 +301,90 @@ def measure_batch(P, torch, args, dev, stream, omega=0.7, restart=100):
     return res
 
 
+LEARNED_WORKLOAD = "burgers_nx256_n4096"
+
+
+def measure_learned(P, torch, args, dev, stream, omega=0.7):
+    """The learned coarse correction on its own workload (Burgers nx=256,
+    nt=4096): collect the plain method's coarse pairs from seeded runs
+    (host-driven solves with recording), train the network with the library's
+    kernels, then time graph-mode solves of a held-out system with and
+    without it.  Relaxed sweeps (omega = 0.7, an option outside the paper):
+    the literal sweeps do not reach 1e-8 within 3000 iterations here."""
+    from paper_2405_04808_gb300 import learned as LN
+    wl = W.WORKLOADS[LEARNED_WORKLOAD]
+    settings = dict(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega)
+    res = {"workload": LEARNED_WORKLOAD, "omega": omega, "levels": wl["levels"], "admit": 0.5,
+           "inference": "bf16 storage, fp32 accumulation"}
+    t0 = time.perf_counter()
+    per = 100
+    train_probs = (wl["make"](seed=wl["seed"] + 1 + k) for k in range((args.learned_pairs + per - 1) // per))
+    R, Y = LN.collect_pairs(train_probs, settings, args.learned_pairs, restart=args.restart, per_problem=per)
+    torch.cuda.synchronize(dev)
+    res["pairs"] = int(R.shape[0])
+    res["collect_s"] = round(time.perf_counter() - t0, 2)
+    _, _, T, X = R.shape
+    net = LN.new_net(wl["seed"])
+    try:
+        t0 = time.perf_counter()
+        losses = LN.train(net, R, Y, epochs=args.learned_epochs, batch=8, lr=1e-3, seed=1)
+        torch.cuda.synchronize(dev)
+        train_s = time.perf_counter() - t0
+        # forward + backward ~ 3x the forward's 2 * T * X * 21 * sum(C_in * C_out) flops per sample
+        fl = 3 * 2.0 * T * X * 21 * (5 * 32 + 32 * 32 + 32 * 32 + 32 * 5) * R.shape[0] * args.learned_epochs
+        res.update(epochs=args.learned_epochs, train_s=round(train_s, 2),
+                   train_loss_normalised=[round(float(l), 4) for l in losses],
+                   train_tflops=round(fl / train_s / 1e12, 2), coarse_shape=[5, T, X])
+        del R, Y
+        prob = wl["make"]()
+        b = torch.tensor(prob.b, device=dev)
+        x = torch.empty_like(b)
+        for name, nt in (("plain", None), ("learned", net)):
+            # kernel shares (net inference included) from one profiled host-driven solve
+            hp = P.mg_setup(prob, device_loops=False, stream=stream, **settings)
+            try:
+                if nt:
+                    P.mg_attach_coarse_net(hp, nt, admit=0.5, bf16=True)
+                P.fgmres_solve(hp, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
+                P.mg_profile_enable(hp, P.PROFILE_ALL)
+                P.fgmres_solve(hp, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
+                shares = P.mg_profile_read(hp)
+                P.mg_profile_enable(hp, 0)
+            finally:
+                P.mg_destroy(hp)
+            h = P.mg_setup(prob, stream=stream, **settings)
+            try:
+                if nt:
+                    P.mg_attach_coarse_net(h, nt, admit=0.5, bf16=True)
+                code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
+                if code != P.MG_OK:
+                    raise RuntimeError(f"learned variant {name}: {P.mg_status_string(code)}")
+                torch.cuda.synchronize(dev)
+                reps = max(1, min(args.steps, 3))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart,
+                                                stream)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1) / reps
+            finally:
+                P.mg_destroy(h)
+            entry = {"solves_per_s": round(1e3 / ms, 4), "ms_per_solve": round(ms, 2), "fgmres_iters": info.iters,
+                     "true_relres": info.true_relres, "coarse_gmres_iters": info.coarse_iters,
+                     "coarse_solves_by_network": info.coarse_learned}
+            if "net_coarse" in shares and shares["net_coarse"][1]:
+                ms_net, n_net, _, fl_net = shares["net_coarse"]
+                total = sum(v[0] for v in shares.values())
+                entry.update(net_share=round(ms_net / total, 4), net_tflops=round(fl_net / ms_net / 1e9, 2))
+            res[name] = entry
+        res["speedup_learned_vs_plain"] = round(res["learned"]["solves_per_s"] / res["plain"]["solves_per_s"], 4)
+    finally:
+        P.mg_net_destroy(net)
+    return res
+
+
 def run_native(args):
     import torch
 
@@ -333,6 +420,7 @@ def run_native(args):
                               "setup_ms": round(v["setup_ms"], 1),
                               "dominant_kernel": v["dominant"], "roofline_frac": v["roofline"].get("frac")}
     batch = None if args.no_variants else measure_batch(P, torch, args, dev, stream)
+    learned = None if (args.no_variants or args.learned_pairs <= 0) else measure_learned(P, torch, args, dev, stream)
     out = {
         "metric": METRIC, "value": round(main["value"], 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(main["ms_per_step"], 3), "higher_is_better": True,
@@ -355,6 +443,7 @@ def run_native(args):
         "kernel_shares": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in main["shares"].items() if v[1]},
         "variants": variants,
         "batched": batch,
+        "learned_coarse": learned,
         "clocks": main["clocks"],
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -236,10 +236,20 @@ int mg_true_residual_noalloc(mg_handle *h, const double *b, const double *x, dou
  * target)^2) in FP32, writes *loss (HOST) and leaves dL/dparams in the
  * network's gradient buffer (synchronises `stream`).  mg_net_adam_step takes
  * one Adam step (Kingma and Ba 2015, bias-corrected) from that gradient.
- * mg_net_train runs `epochs` passes of minibatch Adam over `count` samples
- * (x_all, y_all: DEVICE, count x 5 x T x X), the sample order reshuffled
- * every epoch from `seed` (splitmix64); epoch_loss (HOST, may be NULL)
- * receives each epoch's mean minibatch loss.  Workspaces grow on demand
+ * mg_net_train runs `epochs` passes of minibatch Adam (lr, betas 0.9 and
+ * 0.999, eps 1e-8) over `count` samples (x_all, y_all: DEVICE, count x 5 x T
+ * x X), the sample order reshuffled every epoch from `seed` (splitmix64
+ * Fisher-Yates); epoch_loss (HOST, may be NULL) receives each epoch's mean
+ * minibatch loss.  normalize = 1 trains in per-channel normalised
+ * coordinates: with sx, sy the root mean squares of x_all's and y_all's five
+ * channels, training runs on (x / sx, y / sy) from zero Adam moments and at
+ * the end the scalings are folded into the parameters (first layer's weights
+ * divided by sx of their input channel, last layer's weights and biases times
+ * sy of their output channel), so the result maps x to y.  A network that has
+ * taken optimiser steps before is first mapped to normalised coordinates (the
+ * inverse fold: same function); a fresh network's parameters are taken as
+ * the normalised network's initial parameters.  Losses are then those of the
+ * normalised targets.  Workspaces grow on demand
  * (about 8 x batch x 32 x T x X floats for training).  Errors: MG_ERR_ARG for
  * bad sizes or NULL pointers, MG_ERR_OOM, MG_ERR_CUDA.
  */
@@ -254,13 +264,14 @@ int mg_net_loss_grad(mg_net *net, const float *x, const float *target, int batch
                      void *stream);
 int mg_net_adam_step(mg_net *net, float lr, float beta1, float beta2, float eps, void *stream);
 int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count, int T, int X, int batch,
-                 int epochs, float lr, unsigned long long seed, float *epoch_loss, void *stream);
+                 int epochs, float lr, unsigned long long seed, int normalize, float *epoch_loss, void *stream);
 void mg_net_destroy(mg_net *net);
 
 /*
  * Use `net` (not owned; keep it alive while attached, NULL detaches) as the
- * coarse solve of h's V-cycles: with r the coarse residual, the proposal is
- *   e = ||r|| net(r / ||r||)   (BF16 inference if bf16 = 1, else FP32),
+ * coarse solve of h's V-cycles: with r the coarse residual (N entries) and
+ * rms(r) = ||r|| / sqrt(N), the proposal is
+ *   e = rms(r) net(r / rms(r))   (BF16 inference if bf16 = 1, else FP32),
  * and it is admitted when ||r - A_c e|| <= admit ||r|| (FP64 residual on the
  * coarse level); otherwise the coarse GMRES with SGS runs as without the
  * network, so it is both the judge and the fallback.  FGMRES accepts the
@@ -271,7 +282,7 @@ void mg_net_destroy(mg_net *net);
  *
  * mg_record_coarse(h, r, y, max_pairs) makes later host-driven solves
  * (options.device_loops = 0) record each coarse GMRES solve as a training
- * pair (r / ||r||, y / ||r||) in FP32 into r, y (DEVICE, caller-owned,
+ * pair (r / rms(r), y / rms(r)) in FP32 into r, y (DEVICE, caller-owned,
  * max_pairs x 5 x n_c x p floats each) until max_pairs are stored; NULL
  * stops recording.  mg_recorded_pairs returns the number stored.  Returns
  * MG_ERR_UNSUPPORTED for device-loop handles.

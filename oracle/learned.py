@@ -114,3 +114,29 @@ def adam_step(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mhat = m / (1.0 - beta1 ** step)
     vhat = v / (1.0 - beta2 ** step)
     return params - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def channel_rms(x):
+    """Root mean square of each channel over samples and positions (1 for an all-zero channel)."""
+    r = np.sqrt(np.mean(np.asarray(x, dtype=np.float64) ** 2, axis=(0, 2, 3)))
+    return np.where(r > 0, r, 1.0)
+
+
+def fold(params, sx, sy, direction):
+    """Parameters of the per-channel normalised network and back.
+
+    direction +1: the network net' with net'(x / sx) = net(x) / sy (first
+    layer's weights times sx of their input channel, last layer's weights and
+    biases over sy of their output channel); -1 undoes it."""
+    layers = [(Wt.copy(), b.copy()) for Wt, b in unpack(params)]
+    W0, b0 = layers[0]
+    W3, b3 = layers[-1]
+    if direction > 0:
+        W0 *= sx[None, :, None, None]
+        W3 /= sy[:, None, None, None]
+        b3 /= sy
+    else:
+        W0 /= sx[None, :, None, None]
+        W3 *= sy[:, None, None, None]
+        b3 *= sy
+    return np.concatenate([a.ravel() for Wt, b in layers for a in (Wt, b)])

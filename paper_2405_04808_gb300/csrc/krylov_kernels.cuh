@@ -329,10 +329,9 @@ __global__ void k_copy_if(double *dst, const double *__restrict__ src, long long
     dst[i] = src[i];
 }
 
-// a training pair: r / ||r|| and y / ||r|| in FP32 (scal[1] = 1 / ||r||)
-__global__ void k_record_pair(const double *__restrict__ r, const double *__restrict__ y, const double *scal,
-                              float *rr, float *yy, long long n) {
-  const double inv = scal[1];
+// a training pair: r / rms(r) and y / rms(r) in FP32 (inv = 1 / rms(r) = sqrt(n) / ||r||)
+__global__ void k_record_pair(const double *__restrict__ r, const double *__restrict__ y, double inv, float *rr,
+                              float *yy, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     rr[i] = (float)(r[i] * inv);
     yy[i] = (float)(y[i] * inv);

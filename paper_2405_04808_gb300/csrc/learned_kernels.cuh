@@ -217,18 +217,87 @@ __global__ void k_gather_rows(const float *__restrict__ src, const int *__restri
   }
 }
 
-// coarse residual (FP64) -> network input (storage T), scaled by 1/||r|| (scal[1])
+// dst[k] = src[idx[k]] / scale[channel] (per-channel normalised minibatch; rows of
+// C x TX floats, channel = (e / TX) % C)
+__global__ void k_gather_rows_scaled(const float *__restrict__ src, const int *__restrict__ idx, int rows,
+                                     long long row, long long TX, int C, const float *__restrict__ scale,
+                                     float *dst) {
+  const long long total = (long long)rows * row;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i / row, e = i % row;
+    dst[i] = src[(long long)idx[k] * row + e] / scale[(int)((e / TX) % C)];
+  }
+}
+
+// per-channel sums of squares of `count` samples (C x TX each): partial[c][blockIdx.y]
+// in FP64, fixed order; grid (C, G)
+__global__ void k_channel_sumsq(const float *__restrict__ x, long long count, long long TX, int C, double *partial) {
+  const int c = blockIdx.x, G = gridDim.y;
+  double acc = 0.0;
+  const long long per = count * TX;
+  for (long long i = blockIdx.y * (long long)blockDim.x + threadIdx.x; i < per; i += (long long)G * blockDim.x) {
+    const long long k = i / TX, t = i % TX;
+    const double v = x[(k * C + c) * TX + t];
+    acc += v * v;
+  }
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(kFull, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) s += red[i];
+    partial[(long long)c * G + blockIdx.y] = s;
+  }
+}
+
+// scale[c] = sqrt(mean square) of channel c (1 where the channel is zero)
+__global__ void k_channel_rms(const double *__restrict__ partial, int G, double n, int C, float *scale) {
+  const int c = threadIdx.x;
+  if (c >= C) return;
+  double s = 0.0;
+  for (int i = 0; i < G; ++i) s += partial[(long long)c * G + i];
+  const double r = sqrt(s / n);
+  scale[c] = r > 0.0 ? (float)r : 1.f;
+}
+
+// Move the first layer's input scaling and the last layer's output scaling
+// into or out of the parameters: dir = +1 maps the parameters of net(x) to
+// those of the normalised net' (x' = x / sx per input channel, y' = y / sy per
+// output channel): W0[:, c] *= sx[c], (W3, b3)[o] /= sy[o]; dir = -1 undoes it.
+__global__ void k_net_fold(float *params, const float *__restrict__ sx, const float *__restrict__ sy, int dir) {
+  constexpr int K = kNetKT * kNetKX;
+  const long long n0 = (long long)net_ch(1) * net_ch(0) * K;
+  const long long o3 = net_layer_offset(kNetLayers - 1);
+  const long long n3 = (long long)net_ch(kNetLayers) * net_ch(kNetLayers - 1) * K;
+  const long long nb3 = net_ch(kNetLayers);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0 + n3 + nb3;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < n0) {
+      const int c = (int)((i / K) % net_ch(0));
+      params[i] = dir > 0 ? params[i] * sx[c] : params[i] / sx[c];
+    } else {
+      const long long j = i - n0;
+      const int o = j < n3 ? (int)(j / ((long long)net_ch(kNetLayers - 1) * K)) : (int)(j - n3);
+      params[o3 + j] = dir > 0 ? params[o3 + j] / sy[o] : params[o3 + j] * sy[o];
+    }
+  }
+}
+
+// coarse residual (FP64) -> network input (storage T): x = r / rms(r) with
+// rms(r) = ||r|| / sqrt(n) (scal[1] = 1 / ||r||), so that x has unit mean square
 template <typename T>
 __global__ void k_net_input(const double *__restrict__ r, const double *__restrict__ scal, T *x, long long n) {
-  const double inv = scal[1];
+  const double inv = scal[1] * sqrt((double)n);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] = from_f<T>((float)(r[i] * inv));
 }
 
-// network output (storage T) -> coarse correction (FP64), scaled back by ||r|| (scal[0])
+// network output (storage T) -> coarse correction (FP64), scaled back by rms(r) = ||r|| / sqrt(n) (scal[0] = ||r||)
 template <typename T>
 __global__ void k_net_output(const T *__restrict__ y, const double *__restrict__ scal, double *e, long long n) {
-  const double nr = scal[0];
+  const double nr = scal[0] / sqrt((double)n);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     e[i] = (double)to_f(y[i]) * nr;
 }

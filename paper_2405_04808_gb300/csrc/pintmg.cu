@@ -92,7 +92,8 @@ struct mg_net {
   float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *partial = nullptr, *loss = nullptr;
   __nv_bfloat16 *params_bf16 = nullptr;
   bool bf16_valid = false;
-  int step = 0;
+  int step = 0;              // Adam's step count (bias correction)
+  long long updates = 0;     // optimiser steps ever taken by this network
   // training workspace: layer outputs h[l] (l = 1..4; h[0] is the caller's input),
   // pre-activations z[l] (l = 0..2), gradient ping-pong g0/g1, a gathered minibatch
   float *h[kNetLayers + 1] = {}, *z[kNetLayers] = {}, *g0 = nullptr, *g1 = nullptr, *bx = nullptr, *by = nullptr;
@@ -101,6 +102,8 @@ struct mg_net {
   // standalone inference workspace (mg_net_forward): ping-pong activations and a BF16 copy of x/y
   void *ia = nullptr, *ib = nullptr, *ic = nullptr;
   long long inf_bytes = 0;
+  float *sx = nullptr, *sy = nullptr;  // per-channel input / target scales of a normalised training run
+  double *spart = nullptr;             // their partial sums
   int *order = nullptr;  // minibatch gather indices (device)
   int order_cap = 0;
   DevMem mem, ws;        // mem: fixed buffers; ws: workspaces (reallocated when they grow)
@@ -654,7 +657,7 @@ void net_refresh_bf16(mg_net *net, cudaStream_t s) {
   net->bf16_valid = true;
 }
 
-// e = ||r|| net(r / ||r||) on the coarse level (K.scal holds ||r||, 1/||r||)
+// e = rms(r) net(r / rms(r)) on the coarse level, rms(r) = ||r|| / sqrt(len) (K.scal holds ||r||, 1/||r||)
 void net_coarse_proposal(mg_handle *h, Level &lev, const mg_handle::Krylov &K, cudaStream_t s) {
   mg_net *net = h->net;
   const long long len = lev.len;
@@ -830,9 +833,9 @@ void coarse_solve(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
   }
   ck(cudaMemsetAsync(h->cy, 0, len * sizeof(double), s));
   multi_axpy(h, h->cy, h->cZ, len, K.ycoef, k, 1.0, len, s);
-  if (h->rec_r && h->rec_count < h->rec_max) {  // training pair of the plain method, scaled by 1/||r||
+  if (h->rec_r && h->rec_count < h->rec_max) {  // training pair of the plain method, scaled by 1/rms(r)
     Bracket br(h, CAT_SMALL, s);
-    k_record_pair<<<grid_for(len, 256), 256, 0, s>>>(h->cr, h->cy, K.scal, h->rec_r + (long long)h->rec_count * len,
+    k_record_pair<<<grid_for(len, 256), 256, 0, s>>>(h->cr, h->cy, std::sqrt((double)len) / beta, h->rec_r + (long long)h->rec_count * len,
                                                      h->rec_y + (long long)h->rec_count * len, len);
     ck_launch();
     h->rec_count++;
@@ -1888,6 +1891,16 @@ extern "C" int mg_true_residual_noalloc(mg_handle *h, const double *b, const dou
 namespace {
 
 constexpr int kLossPartials = 1024;
+constexpr int kScaleParts = 64;
+
+// per-channel root mean square of `count` samples of 5 x TX floats
+void channel_rms(mg_net *net, const float *x, int count, long long TX, float *scale, cudaStream_t s) {
+  const int C = net_ch(0);
+  k_channel_sumsq<<<dim3(C, kScaleParts), 256, 0, s>>>(x, count, TX, C, net->spart);
+  ck_launch();
+  k_channel_rms<<<1, 32, 0, s>>>(net->spart, kScaleParts, (double)count * TX, C, scale);
+  ck_launch();
+}
 
 // training workspace for `batch` samples of T x X (grown on demand)
 void net_ensure_train(mg_net *net, int batch, long long TX, int minibatches) {
@@ -1957,6 +1970,7 @@ void net_loss_grad_dev(mg_net *net, const float *x, const float *target, int B, 
 
 void net_adam(mg_net *net, float lr, float b1, float b2, float eps, cudaStream_t s) {
   net->step++;
+  net->updates++;
   const double c1 = 1.0 - std::pow((double)b1, net->step), c2 = 1.0 - std::pow((double)b2, net->step);
   k_adam<<<grid_for(kNetParams, 256), 256, 0, s>>>(net->params, net->grad, net->m, net->v, kNetParams, lr, b1, b2,
                                                    eps, (float)c1, (float)c2);
@@ -2015,6 +2029,9 @@ int mg_net_create(const float *init_params, mg_net **out) {
     net->v = net->mem.alloc<float>(kNetParams);
     net->partial = net->mem.alloc<float>(kLossPartials);
     net->params_bf16 = net->mem.alloc<__nv_bfloat16>(kNetParams);
+    net->sx = net->mem.alloc<float>(8);
+    net->sy = net->mem.alloc<float>(8);
+    net->spart = net->mem.alloc<double>((size_t)8 * kScaleParts);
     ck(cudaMemcpy(net->params, init_params, kNetParams * sizeof(float), cudaMemcpyHostToDevice));
     ck(cudaMemset(net->grad, 0, kNetParams * sizeof(float)));
     ck(cudaMemset(net->m, 0, kNetParams * sizeof(float)));
@@ -2112,8 +2129,9 @@ int mg_net_adam_step(mg_net *net, float lr, float beta1, float beta2, float eps,
 }
 
 int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count, int T, int X, int batch, int epochs,
-                 float lr, unsigned long long seed, float *epoch_loss, void *stream) {
-  if (!net || !x_all || !y_all || count < 1 || T < 1 || X < 1 || batch < 1 || epochs < 0 || !(lr > 0.f))
+                 float lr, unsigned long long seed, int normalize, float *epoch_loss, void *stream) {
+  if (!net || !x_all || !y_all || count < 1 || T < 1 || X < 1 || batch < 1 || epochs < 0 || !(lr > 0.f) ||
+      (normalize != 0 && normalize != 1))
     return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long TX = (long long)T * X, row = (long long)net_ch(0) * TX;
@@ -2133,6 +2151,19 @@ int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count,
       }
       net->order_cap = count;
     }
+    const int C = net_ch(0);
+    const int fold_grid = grid_for(net_layer_params(0) + net_layer_params(kNetLayers - 1), 256);
+    if (normalize) {  // train the normalised network x / sx -> y / sy from a fresh optimiser state
+      channel_rms(net, x_all, count, TX, net->sx, s);
+      channel_rms(net, y_all, count, TX, net->sy, s);
+      if (net->updates > 0) {  // a trained network keeps its function; a fresh one starts as the normalised one
+        k_net_fold<<<fold_grid, 256, 0, s>>>(net->params, net->sx, net->sy, +1);
+        ck_launch();
+      }
+      ck(cudaMemsetAsync(net->m, 0, kNetParams * sizeof(float), s));
+      ck(cudaMemsetAsync(net->v, 0, kNetParams * sizeof(float), s));
+      net->step = 0;
+    }
     SplitMix64 rng{seed};
     std::vector<int> order(count);
     std::vector<float> losses(nmb);
@@ -2143,12 +2174,18 @@ int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count,
       ck(cudaMemcpyAsync(net->order, order.data(), (size_t)count * sizeof(int), cudaMemcpyHostToDevice, s));
       for (int k = 0; k < nmb; ++k) {
         const int b0 = k * B, nb = std::min(B, count - b0);
-        k_gather_rows<<<grid_for((long long)nb * row, 256, 1 << 20), 256, 0, s>>>(x_all, net->order + b0, nb, row,
-                                                                                    net->bx);
-        ck_launch();
-        k_gather_rows<<<grid_for((long long)nb * row, 256, 1 << 20), 256, 0, s>>>(y_all, net->order + b0, nb, row,
-                                                                                    net->by);
-        ck_launch();
+        const int gg = grid_for((long long)nb * row, 256, 1 << 20);
+        if (normalize) {
+          k_gather_rows_scaled<<<gg, 256, 0, s>>>(x_all, net->order + b0, nb, row, TX, C, net->sx, net->bx);
+          ck_launch();
+          k_gather_rows_scaled<<<gg, 256, 0, s>>>(y_all, net->order + b0, nb, row, TX, C, net->sy, net->by);
+          ck_launch();
+        } else {
+          k_gather_rows<<<gg, 256, 0, s>>>(x_all, net->order + b0, nb, row, net->bx);
+          ck_launch();
+          k_gather_rows<<<gg, 256, 0, s>>>(y_all, net->order + b0, nb, row, net->by);
+          ck_launch();
+        }
         net_loss_grad_dev(net, net->bx, net->by, nb, T, X, net->loss + k, s);
         net_adam(net, lr, 0.9f, 0.999f, 1e-8f, s);
       }
@@ -2159,6 +2196,12 @@ int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count,
         for (float l : losses) sum += l;
         epoch_loss[e] = (float)(sum / nmb);
       }
+    }
+    if (normalize) {  // back to the network of the unnormalised data
+      k_net_fold<<<fold_grid, 256, 0, s>>>(net->params, net->sx, net->sy, -1);
+      ck_launch();
+      net->bf16_valid = false;
+      ck(cudaStreamSynchronize(s));
     }
   });
 }

@@ -15,7 +15,7 @@ from . import workloads as W
 
 def collect_pairs(problems, settings: dict, max_pairs: int, rtol: float = 1e-8, maxit: int = 2000,
                   restart: int = 400, per_problem: int | None = None):
-    """Record (r / ||r||, y / ||r||) coarse pairs of the plain method (GMRES + SGS
+    """Record (r / rms(r), y / rms(r)) coarse pairs (rms(r) = ||r|| / sqrt(len r)) of the plain method (GMRES + SGS
     coarse solves inside FGMRES) from a list of problems with the same coarse
     shape.  Returns device tensors R, Y of shape (count, 5, T, X) (FP32)."""
     import torch
@@ -46,10 +46,11 @@ def collect_pairs(problems, settings: dict, max_pairs: int, rtol: float = 1e-8, 
     return R[:count], Y[:count]
 
 
-def train(net, R, Y, epochs: int, batch: int = 16, lr: float = 1e-3, seed: int = 0):
-    """Minibatch Adam on (R, Y) with the library's kernels; returns per-epoch losses."""
+def train(net, R, Y, epochs: int, batch: int = 16, lr: float = 1e-3, seed: int = 0, normalize: bool = True):
+    """Minibatch Adam on (R, Y) with the library's kernels (per-channel
+    normalised by default); returns per-epoch losses."""
     count, _, T, X = R.shape
-    return P.mg_net_train(net, R.data_ptr(), Y.data_ptr(), count, T, X, batch, epochs, lr, seed)
+    return P.mg_net_train(net, R.data_ptr(), Y.data_ptr(), count, T, X, batch, epochs, lr, seed, normalize)
 
 
 def new_net(seed: int):

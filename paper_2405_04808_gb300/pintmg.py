@@ -118,7 +118,7 @@ def lib():
                 ("mg_net_forward", [vp, vp, ci, ci, ci, vp, ci, vp], ci),
                 ("mg_net_loss_grad", [vp, vp, vp, ci, ci, ci, fp, vp], ci),
                 ("mg_net_adam_step", [vp, cf, cf, cf, cf, vp], ci),
-                ("mg_net_train", [vp, vp, vp, ci, ci, ci, ci, ci, cf, ctypes.c_ulonglong, fp, vp], ci),
+                ("mg_net_train", [vp, vp, vp, ci, ci, ci, ci, ci, cf, ctypes.c_ulonglong, ci, fp, vp], ci),
                 ("mg_net_destroy", [vp], None),
                 ("mg_attach_coarse_net", [vp, vp, ctypes.c_double, ci], ci),
                 ("mg_record_coarse", [vp, vp, vp, ci], ci),
@@ -307,12 +307,12 @@ def mg_net_adam_step(net, lr: float, beta1: float = 0.9, beta2: float = 0.999, e
 
 
 def mg_net_train(net, x_ptr: int, y_ptr: int, count: int, T: int, X: int, batch: int, epochs: int, lr: float,
-                 seed: int, stream: int = 0) -> np.ndarray:
+                 seed: int, normalize: bool = True, stream: int = 0) -> np.ndarray:
     """Minibatch Adam over `count` device samples; returns each epoch's mean loss."""
     losses = np.zeros(max(epochs, 1), dtype=np.float32)
     _check(lib().mg_net_train(ctypes.c_void_p(net), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), count, T, X,
-                              batch, epochs, lr, ctypes.c_ulonglong(seed), _fptr(losses), ctypes.c_void_p(stream)),
-           "mg_net_train")
+                              batch, epochs, lr, ctypes.c_ulonglong(seed), 1 if normalize else 0, _fptr(losses),
+                              ctypes.c_void_p(stream)), "mg_net_train")
     return losses[:epochs]
 
 

@@ -69,3 +69,18 @@ def test_delta_kernels_compose_to_the_activation():
     x = np.random.default_rng(4).standard_normal((1, 5, 4, 6))
     y, _ = NL.forward(p, x)
     assert np.allclose(y, np.where(x > 0, x, 1e-3 * x), atol=1e-15)
+
+
+def test_fold_is_the_normalised_network():
+    """net'(x / sx) = net(x) / sy per channel, and folding back restores the parameters."""
+    rng = np.random.default_rng(9)
+    p = W.net_init_params(4) + 0.05 * rng.standard_normal(NL.param_count())
+    x = rng.standard_normal((2, 5, 5, 8)) * np.array([1e-3, 2.0, 30.0, 0.5, 7.0])[None, :, None, None]
+    sx = NL.channel_rms(x)
+    sy = np.array([0.1, 3.0, 50.0, 1e-2, 8.0])
+    pn = NL.fold(p, sx, sy, +1)
+    y, _ = NL.forward(p, x)
+    yn, _ = NL.forward(pn, x / sx[None, :, None, None])
+    assert np.allclose(yn, y / sy[None, :, None, None], rtol=1e-12, atol=1e-14)
+    assert np.allclose(NL.fold(pn, sx, sy, -1), p, rtol=1e-14, atol=0)
+    assert np.allclose(NL.channel_rms(np.ones((3, 5, 2, 2)) * 2.0), 2.0)

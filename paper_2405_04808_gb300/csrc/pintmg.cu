@@ -6,6 +6,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -138,6 +141,7 @@ struct mg_handle {
   int vcycles = 0, coarse_iters = 0;
   int use_cluster = 1;  // SGS chains on a thread-block cluster (tridiagonal layout)
   int use_scan = 1;     // SGS chains as a parallel scan with precomputed prefix products
+  int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -317,13 +321,18 @@ LevelData<float> &ldata<float>(Level &L) { return L.f; }
 void multidot(mg_handle *h, const double *V, long long ldv, int m, const double *w, long long len, double *out,
               int accumulate, cudaStream_t s, const int *gate = nullptr, const int *m_dev = nullptr) {
   // about 32 entries per thread per vector, at most 152 CTAs per vector block
-  constexpr int VB = 8;
+  const int VB = h->dot_vb;
   const int G = (int)std::max<long long>(1, std::min<long long>(152, (len + 32 * kDotThreads - 1) / (32 * kDotThreads)));
   dim3 grid(G, (m + VB - 1) / VB);
   {
     // algorithmic: read the m vectors and w once, 2 m len flops
     Bracket br(h, CAT_DOT, s, 8.0 * (m + (V == w ? 0 : 1)) * len, 2.0 * m * len);
-    k_multidot_blocked<VB><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
+    if (VB == 4)
+      k_multidot_blocked<4><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
+    else if (VB == 16)
+      k_multidot_blocked<16><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
+    else
+      k_multidot_blocked<8><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
     ck_launch();
   }
   {
@@ -2261,3 +2270,143 @@ int mg_record_coarse(mg_handle *h, float *r, float *y, int max_pairs) {
 int mg_recorded_pairs(const mg_handle *h) { return h ? h->rec_count : MG_ERR_ARG; }
 
 }  // extern "C"
+
+// ===========================================================================
+// Autotuner: picks, per problem shape, the fastest SGS chain evaluation
+// (parallel scan, thread-block-cluster chain or single-CTA chain; equal up to
+// rounding) and the basis-vector blocking of the dot products (4, 8 or 16 per
+// CTA; bitwise the same results) by timing them on the handle's own levels.
+// Choices are cached for the process by shape.
+
+namespace {
+
+struct TuneChoice {
+  int chain = 0;   // 0 scan, 1 cluster, 2 single CTA
+  int dot_vb = 8;
+  float ms_chain[3] = {-1.f, -1.f, -1.f};
+  float ms_dot[3] = {-1.f, -1.f, -1.f};  // VB 4, 8, 16
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, TuneChoice> g_tune_cache;
+
+template <typename F>
+float time_min(cudaStream_t s, int reps, F &&f) {
+  cudaEvent_t a, b;
+  ck(cudaEventCreate(&a));
+  ck(cudaEventCreate(&b));
+  f();  // warm-up
+  float best = 1e30f;
+  for (int i = 0; i < reps; ++i) {
+    ck(cudaEventRecord(a, s));
+    f();
+    ck(cudaEventRecord(b, s));
+    ck(cudaEventSynchronize(b));
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, a, b));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+template <typename T>
+void tune_chain(mg_handle *h, Level &lev, TuneChoice &c, cudaStream_t s) {
+  LevelData<T> &d = ldata<T>(lev);
+  const bool has_scan = lev.n == 1 || !d.scanF.empty();
+  const bool has_cluster = h->layout == MG_LAYOUT_TRIDIAG && h->p >= 32;
+  // input: the level's scratch vector (zeroed); output: its y vector, or the coarse
+  // GMRES's preconditioner slot on a single-level FP64 handle (no y there)
+  T *in = d.tmp;
+  T *out = d.y ? d.y : reinterpret_cast<T *>(h->czout);
+  ck(cudaMemsetAsync(in, 0, lev.len * sizeof(T), s));
+  const int save_scan = h->use_scan, save_cluster = h->use_cluster;
+  for (int k = 0; k < 3; ++k) {
+    if ((k == 0 && !has_scan) || (k == 1 && !has_cluster)) continue;
+    h->use_scan = k == 0;
+    h->use_cluster = k == 1;
+    c.ms_chain[k] = time_min(s, 3, [&] { sgs_apply<T>(h, lev, in, out, s); });
+  }
+  h->use_scan = save_scan;
+  h->use_cluster = save_cluster;
+  int best = -1;
+  for (int k = 0; k < 3; ++k)
+    if (c.ms_chain[k] >= 0.f && (best < 0 || c.ms_chain[k] < c.ms_chain[best])) best = k;
+  c.chain = best < 0 ? 2 : best;
+}
+
+}  // namespace
+
+extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) {
+  if (!h) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto key = std::make_tuple(h->layout, h->lv.back().n, h->p, h->q, h->lv[0].n, h->opts.precision);
+  TuneChoice c;
+  bool hit = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c = it->second;
+      hit = true;
+    }
+  }
+  const bool env_chain = std::getenv("PINTMG_SGS_CHAIN") != nullptr;  // a forced chain is kept
+  const long long saved = h->launches;
+  const int saved_prof = h->prof;
+  h->prof = 0;
+  int status = MG_OK;
+  double *tmp = nullptr;
+  try {
+    if (!hit) {
+      Level &cl = h->lv.back();
+      if (!env_chain) {
+        if (h->opts.precision == MG_PRECISION_FP32)
+          tune_chain<float>(h, cl, c, s);
+        else
+          tune_chain<double>(h, cl, c, s);
+      }
+      // dot products of 16 fine-level vectors (at most 2^21 entries each) for VB = 4, 8, 16
+      const long long tl = std::min<long long>(h->lv[0].len, 1LL << 21);
+      constexpr int kM = 16;
+      cudaError_t e = cudaMalloc(&tmp, (size_t)(kM + 1) * tl * sizeof(double));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        tmp = nullptr;
+        throw std::bad_alloc();
+      }
+      ck(cudaMemsetAsync(tmp, 0, (size_t)(kM + 1) * tl * sizeof(double), s));
+      const int save_vb = h->dot_vb;
+      const int vbs[3] = {4, 8, 16};
+      int best = 1;
+      for (int k = 0; k < 3; ++k) {
+        h->dot_vb = vbs[k];
+        c.ms_dot[k] = time_min(s, 5, [&] { multidot(h, tmp, tl, kM, tmp + (long long)kM * tl, tl, h->kf.h, 0, s); });
+        if (c.ms_dot[k] < c.ms_dot[best]) best = k;
+      }
+      h->dot_vb = save_vb;
+      c.dot_vb = vbs[best];
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = c;
+    }
+    if (!env_chain) {
+      h->use_scan = c.chain == 0;
+      h->use_cluster = c.chain == 1;
+    }
+    h->dot_vb = c.dot_vb;
+    h->gen++;  // captured graphs used the previous choices
+  } catch (const CudaFail &) {
+    status = MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    status = MG_ERR_OOM;
+  }
+  if (tmp) cudaFree(tmp);
+  h->launches = saved;
+  h->prof = saved_prof;
+  if (status == MG_OK) {
+    if (chain) *chain = env_chain ? (h->use_scan ? 0 : (h->use_cluster ? 1 : 2)) : c.chain;
+    if (dot_vb) *dot_vb = c.dot_vb;
+  }
+  return status;
+}

@@ -38,7 +38,7 @@ EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmr
             "mg_launch_count", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
             "mg_net_forward", "mg_net_loss_grad", "mg_net_adam_step", "mg_net_train", "mg_net_destroy",
-            "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape",
+            "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune",
             "mg_destroy", "mg_status_string", "mg_last_cuda_error")
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -123,7 +123,8 @@ def lib():
                 ("mg_attach_coarse_net", [vp, vp, ctypes.c_double, ci], ci),
                 ("mg_record_coarse", [vp, vp, vp, ci], ci),
                 ("mg_recorded_pairs", [vp], ci),
-                ("mg_coarse_shape", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci)):
+                ("mg_coarse_shape", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
+                ("mg_autotune", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), vp], ci)):
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
@@ -341,6 +342,18 @@ def mg_coarse_shape(h):
     T, X = ctypes.c_int(), ctypes.c_int()
     _check(lib().mg_coarse_shape(ctypes.c_void_p(h), ctypes.byref(T), ctypes.byref(X)), "mg_coarse_shape")
     return T.value, X.value
+
+
+SGS_CHAINS = ("scan", "cluster", "serial")
+
+
+def mg_autotune(h, stream: int = 0):
+    """Time and select the SGS chain evaluation and dot-product blocking for h
+    (cached per shape); returns (chain name, vectors per CTA)."""
+    chain, vb = ctypes.c_int(), ctypes.c_int()
+    _check(lib().mg_autotune(ctypes.c_void_p(h), ctypes.byref(chain), ctypes.byref(vb), ctypes.c_void_p(stream)),
+           "mg_autotune")
+    return SGS_CHAINS[chain.value], vb.value
 
 
 def mg_destroy(h) -> None:

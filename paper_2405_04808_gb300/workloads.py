@@ -380,6 +380,31 @@ def batch_mix(seed: int = 4000, count: int = 32):
     return out
 
 
+def _batch_member(k: int, seed: int):
+    vdp_nt = (512, 1024, 2048, 4096, 8192, 16384)
+    bg = [(nx, nt) for nt in (512, 1024, 2048, 4096) for nx in (64, 128, 256)]
+    sd = seed + k
+    if k % 2 == 0:
+        return vdp(n=vdp_nt[(k // 2) % len(vdp_nt)], seed=sd), dict(levels=4, nu_pre=1, nu_post=1)
+    nx, nt = bg[(k // 2) % len(bg)]
+    return burgers(nx=nx, n=nt, seed=sd), dict(levels=4, nu_pre=4, nu_post=4)
+
+
+def batch_uneven(seed: int = 6000, count: int = 64, workers: int = 1):
+    """The batched workload: `count` systems at distinct seeded iterates, half
+    van der Pol with nt cycling through 512 ... 16384, half Burgers with
+    (nx, nt) cycling through {64, 128, 256} x {512, 1024, 2048, 4096}; every
+    system with 4 levels (1/1 sweeps for van der Pol, 4/4 for Burgers).
+    workers > 1 builds the members in a spawned process pool (the forward
+    solves are per-step Python loops).  Returns [(Problem, settings)]."""
+    if workers <= 1:
+        return [_batch_member(k, seed) for k in range(count)]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_member, range(count), [seed] * count))
+
+
 # --------------------------------------------------------------------------
 # the learned coarse correction's network: initial parameters
 

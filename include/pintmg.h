@@ -200,8 +200,9 @@ int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long 
  * with a fixed memory budget, an outer optimisation loop testing its stopping
  * rule), computes on `stream`, asynchronously:
  *   out[0] = ||b - A x||_2,   out[1] = ||b - A x||_2 / ||b||_2  (0 if b = 0)
- * with the same FP64 kernels and reduction order as fgmres_solve's reported
- * true residual.  b, x and out (2 doubles) are DEVICE pointers owned by the
+ * with the same FP64 residual kernel as fgmres_solve's reported true
+ * residual and fixed-order reductions (a different partition of the sums,
+ * so the two agree to rounding, not bitwise).  b, x and out (2 doubles) are DEVICE pointers owned by the
  * caller.  It calls no cudaMalloc, cudaFree or allocating library routine:
  * its scratch (residual vector, reduction partials) is one file-scope device
  * array of 2^20 + 616 doubles (about 8 MiB), held by every GPU that loads the
@@ -304,7 +305,7 @@ int mg_coarse_shape(const mg_handle *h, int *T, int *X);
  * handles of the same shape take the cached choice without timing.  A chain
  * forced by the environment (PINTMG_SGS_CHAIN) is kept.  *chain (0 scan,
  * 1 cluster, 2 single CTA) and *dot_vb (may be NULL) report the choice.
- * Allocates a temporary of 17 x min(n(4p+q), 2^21) doubles; synchronises
+ * Allocates a temporary of 49 x min(n(4p+q), 2^20) doubles; synchronises
  * `stream`; invalidates h's captured graphs.
  */
 int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream);

@@ -40,11 +40,30 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_partial(const double *
   if (threadIdx.x == 0) partial[(long long)i * gridDim.x + blockIdx.x] = s;
 }
 
-// The same for VB vectors per CTA: each thread streams its slice of w once
-// against VB basis vectors (VB independent accumulators), so the per-CTA
+// Partition of the blocked dot products: the m vectors in ceil(m / VB)
+// blocks, each block's length split into G chunks; a (block, chunk) pair is
+// one work item with its own partial sum.  G depends on m only, so a launch
+// whose m is read on the device (graph-captured solves) partitions exactly
+// like one with m known on the host: the same partial sums, the same order.
+// Few vectors: more, shorter chunks to fill the GPU; many vectors: fewer,
+// longer ones (the per-item reduction is amortised, ~1200 items in flight);
+// short vectors: at least 4 entries per thread and chunk.
+__host__ __device__ inline int dot_parts(int m, int VB, long long len) {
+  const int nb = (m + VB - 1) / VB;
+  int G = nb <= 1 ? 304 : 1216 / nb;
+  G = G < 40 ? 40 : (G > 152 && nb > 1 ? 152 : G);
+  const long long cap = len / (4LL * kDotThreads);
+  return cap < 1 ? 1 : (G > cap ? (int)cap : G);
+}
+constexpr int kDotGridCap = 1216;  // CTAs of a dot-product launch (8 per SM)
+
+// partial[i * G + g] = sum over chunk g of V_i . w for i < m, VB vectors per
+// work item, G = dot_parts(m, VB, len); a persistent grid walks the items.  kPair:
+// two consecutive entries per thread and step (16-byte loads; needs len and
+// ldv even and 16-byte aligned V, w).  Each thread streams its slice of w once
+// against VB basis vectors (VB independent accumulators), so the per-item
 // reduction is amortised over VB times more fused multiply-adds.
-// partial[i * gridDim.x + blockIdx.x] for i = blockIdx.y * VB + v < m.
-template <int VB>
+template <int VB, bool kPair>
 __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *__restrict__ V, long long ldv, int m,
                                                                   const double *__restrict__ w, long long len,
                                                                   double *partial, const int *gate,
@@ -52,42 +71,63 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *
   if (gate && *gate == 0) return;
   if (m_dev) m = *m_dev;  // vector count held on the device (graph-captured solves)
   __shared__ double red[kDotThreads / kWarp][VB];
-  const int vb = blockIdx.y * VB;
-  if (vb >= m) return;
-  const int nv = min(VB, m - vb);
-  double acc[VB];
-#pragma unroll
-  for (int v = 0; v < VB; ++v) acc[v] = 0.0;
-  for (long long idx = blockIdx.x * (long long)kDotThreads + threadIdx.x; idx < len;
-       idx += (long long)gridDim.x * kDotThreads) {
-    const double wv = w[idx];
-#pragma unroll
-    for (int v = 0; v < VB; ++v)
-      if (v < nv) acc[v] = fma(V[(long long)(vb + v) * ldv + idx], wv, acc[v]);
-  }
+  const int G = dot_parts(m, VB, len);
+  const int items = ((m + VB - 1) / VB) * G;
   const int wp = threadIdx.x / kWarp, ln = threadIdx.x & (kWarp - 1);
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int vb = (item / G) * VB, g = item % G;
+    const int nv = min(VB, m - vb);
+    double acc[VB];
 #pragma unroll
-  for (int v = 0; v < VB; ++v) {
-    double x = acc[v];
-    if (v < nv) {
+    for (int v = 0; v < VB; ++v) acc[v] = 0.0;
+    if (kPair) {
+      const double2 *w2 = reinterpret_cast<const double2 *>(w);
+      for (long long idx = g * (long long)kDotThreads + threadIdx.x; idx < len / 2;
+           idx += (long long)G * kDotThreads) {
+        const double2 wv = w2[idx];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        for (int v = 0; v < VB; ++v)
+          if (v < nv) {
+            const double2 x = reinterpret_cast<const double2 *>(V + (long long)(vb + v) * ldv)[idx];
+            acc[v] = fma(x.x, wv.x, acc[v]);
+            acc[v] = fma(x.y, wv.y, acc[v]);
+          }
+      }
+    } else {
+      for (long long idx = g * (long long)kDotThreads + threadIdx.x; idx < len; idx += (long long)G * kDotThreads) {
+        const double wv = w[idx];
+#pragma unroll
+        for (int v = 0; v < VB; ++v)
+          if (v < nv) acc[v] = fma(V[(long long)(vb + v) * ldv + idx], wv, acc[v]);
+      }
     }
-    if (ln == 0) red[wp][v] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double sum = 0.0;
-    for (int i = 0; i < kDotThreads / kWarp; ++i) sum += red[i][threadIdx.x];
-    partial[(long long)(vb + threadIdx.x) * gridDim.x + blockIdx.x] = sum;
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      double x = acc[v];
+      if (v < nv) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+      }
+      if (ln == 0) red[wp][v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+      double sum = 0.0;
+      for (int i = 0; i < kDotThreads / kWarp; ++i) sum += red[i][threadIdx.x];
+      partial[(long long)(vb + threadIdx.x) * G + g] = sum;
+    }
+    __syncthreads();  // red is reused by the next item
   }
 }
 
-// out[i] (+)= sum_g partial[i * G + g], fixed order.  One warp per i.
+// out[i] (+)= sum_g partial[i * G + g], fixed order.  One warp per i.  With
+// vb > 0, G = dot_parts(m, vb, len) (the partition of k_multidot_blocked).
 __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int m, double *out, int accumulate,
-                                  const int *gate = nullptr, const int *m_dev = nullptr) {
+                                  const int *gate = nullptr, const int *m_dev = nullptr, int vb = 0,
+                                  long long len = 0) {
   if (gate && *gate == 0) return;
   if (m_dev) m = *m_dev;
+  if (vb > 0) G = dot_parts(m, vb, len);
   const int i = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const int ln = threadIdx.x & (kWarp - 1);
   if (i >= m) return;
@@ -100,7 +140,10 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int
 
 // y[idx] += sign * sum_{i < m} c[i] X_i[idx],  X_i = X + i * ldx
 // (coefficients staged in shared memory; m <= 512; the vector loop is unrolled
-// so that several basis loads are in flight per thread)
+// so that several basis loads are in flight per thread).  kPair: two
+// consecutive entries per thread (16-byte loads; len, ldx even, y, X aligned);
+// each entry's sum runs over i in the same order either way.
+template <bool kPair>
 __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long ldx, const double *__restrict__ c,
                              int m, double sign, long long len, const int *gate = nullptr,
                              const int *m_dev = nullptr) {
@@ -109,17 +152,36 @@ __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long 
   __shared__ double cs[512];
   for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
-       idx += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+  if (kPair) {
+    double2 *y2 = reinterpret_cast<double2 *>(y);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len / 2;
+         idx += (long long)gridDim.x * blockDim.x) {
+      double a0 = 0.0, a1 = 0.0;
 #pragma unroll 8
-    for (int i = 0; i < m; ++i) acc = fma(cs[i], X[i * ldx + idx], acc);
-    y[idx] = fma(sign, acc, y[idx]);
+      for (int i = 0; i < m; ++i) {
+        const double2 x = reinterpret_cast<const double2 *>(X + i * ldx)[idx];
+        a0 = fma(cs[i], x.x, a0);
+        a1 = fma(cs[i], x.y, a1);
+      }
+      double2 v = y2[idx];
+      v.x = fma(sign, a0, v.x);
+      v.y = fma(sign, a1, v.y);
+      y2[idx] = v;
+    }
+  } else {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
+         idx += (long long)gridDim.x * blockDim.x) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int i = 0; i < m; ++i) acc = fma(cs[i], X[i * ldx + idx], acc);
+      y[idx] = fma(sign, acc, y[idx]);
+    }
   }
 }
 
 // y -= sum_{i < m} c[i] X_i, and the CTA's partial sum of the new y^2 into
 // partial[blockIdx.x] (fixed order), for the norm of the orthogonalised vector
+template <bool kPair>
 __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_norm(double *y, const double *__restrict__ X, long long ldx,
                                                                  const double *__restrict__ c, int m, long long len,
                                                                  double *partial, const int *m_dev = nullptr) {
@@ -128,14 +190,34 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_norm(double *y, cons
   for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
   double sq = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
-       idx += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+  if (kPair) {
+    double2 *y2 = reinterpret_cast<double2 *>(y);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len / 2;
+         idx += (long long)gridDim.x * blockDim.x) {
+      double a0 = 0.0, a1 = 0.0;
 #pragma unroll 8
-    for (int i = 0; i < m; ++i) acc = fma(cs[i], X[i * ldx + idx], acc);
-    const double v = y[idx] - acc;
-    y[idx] = v;
-    sq = fma(v, v, sq);
+      for (int i = 0; i < m; ++i) {
+        const double2 x = reinterpret_cast<const double2 *>(X + i * ldx)[idx];
+        a0 = fma(cs[i], x.x, a0);
+        a1 = fma(cs[i], x.y, a1);
+      }
+      double2 v = y2[idx];
+      v.x -= a0;
+      v.y -= a1;
+      y2[idx] = v;
+      sq = fma(v.x, v.x, sq);
+      sq = fma(v.y, v.y, sq);
+    }
+  } else {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
+         idx += (long long)gridDim.x * blockDim.x) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int i = 0; i < m; ++i) acc = fma(cs[i], X[i * ldx + idx], acc);
+      const double v = y[idx] - acc;
+      y[idx] = v;
+      sq = fma(v, v, sq);
+    }
   }
   const double s = block_sum(sq);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;

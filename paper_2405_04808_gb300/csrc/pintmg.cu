@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -316,28 +317,41 @@ LevelData<float> &ldata<float>(Level &L) { return L.f; }
 // ---------------------------------------------------------------------------
 // Dot products (FP64), fixed reduction order
 
+// 16-byte paired loads are possible: even lengths and strides, aligned bases
+inline bool pair_ok(const void *a, const void *b, long long len, long long ld) {
+  return len % 2 == 0 && ld % 2 == 0 && ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
 // m_dev (optional): the vector count lives on the device; m is then its
 // upper bound (grid size) and the kernels read the actual count.
 void multidot(mg_handle *h, const double *V, long long ldv, int m, const double *w, long long len, double *out,
               int accumulate, cudaStream_t s, const int *gate = nullptr, const int *m_dev = nullptr) {
-  // about 32 entries per thread per vector, at most 152 CTAs per vector block
   const int VB = h->dot_vb;
-  const int G = (int)std::max<long long>(1, std::min<long long>(152, (len + 32 * kDotThreads - 1) / (32 * kDotThreads)));
-  dim3 grid(G, (m + VB - 1) / VB);
+  const int items = ((m + VB - 1) / VB) * dot_parts(m, VB, len);
+  const int grid = std::min(items, kDotGridCap);
+  const bool pair = pair_ok(V, w, len, ldv);
   {
     // algorithmic: read the m vectors and w once, 2 m len flops
     Bracket br(h, CAT_DOT, s, 8.0 * (m + (V == w ? 0 : 1)) * len, 2.0 * m * len);
+#define PINTMG_DOT(VBV)                                                                                      \
+  do {                                                                                                       \
+    if (pair)                                                                                                \
+      k_multidot_blocked<VBV, true><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev); \
+    else                                                                                                     \
+      k_multidot_blocked<VBV, false><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev); \
+  } while (0)
     if (VB == 4)
-      k_multidot_blocked<4><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
+      PINTMG_DOT(4);
     else if (VB == 16)
-      k_multidot_blocked<16><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
+      PINTMG_DOT(16);
     else
-      k_multidot_blocked<8><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev);
+      PINTMG_DOT(8);
+#undef PINTMG_DOT
     ck_launch();
   }
   {
     Bracket br(h, CAT_SMALL, s);
-    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, G, m, out, accumulate, gate, m_dev);
+    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, 0, m, out, accumulate, gate, m_dev, VB, len);
     ck_launch();
   }
 }
@@ -345,7 +359,10 @@ void multidot(mg_handle *h, const double *V, long long ldv, int m, const double 
 void multi_axpy(mg_handle *h, double *y, const double *X, long long ldx, const double *c, int m, double sign,
                 long long len, cudaStream_t s, const int *gate = nullptr, const int *m_dev = nullptr) {
   Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * m * len);
-  k_multi_axpy<<<grid_for(len, 256), 256, 0, s>>>(y, X, ldx, c, m, sign, len, gate, m_dev);
+  if (pair_ok(y, X, len, ldx))
+    k_multi_axpy<true><<<grid_for(len / 2, 256, kDotGridCap), 256, 0, s>>>(y, X, ldx, c, m, sign, len, gate, m_dev);
+  else
+    k_multi_axpy<false><<<grid_for(len, 256, kDotGridCap), 256, 0, s>>>(y, X, ldx, c, m, sign, len, gate, m_dev);
   ck_launch();
 }
 
@@ -363,10 +380,14 @@ void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long lon
   multidot(h, V, len, m, w, len, K.h, 0, s, nullptr, m_dev);
   multi_axpy(h, w, V, len, K.h, m, -1.0, len, s, nullptr, m_dev);
   multidot(h, V, len, m, w, len, K.h + 512, 0, s, nullptr, m_dev);
-  const int G = grid_for(len, kDotThreads);
+  const bool pair = pair_ok(w, V, len, len);
+  const int G = pair ? grid_for(len / 2, kDotThreads, kDotGridCap) : grid_for(len, kDotThreads, kDotGridCap);
   {
     Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * (m + 1) * len);
-    k_multi_axpy_norm<<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev);
+    if (pair)
+      k_multi_axpy_norm<true><<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev);
+    else
+      k_multi_axpy_norm<false><<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev);
     ck_launch();
   }
   {
@@ -2367,9 +2388,9 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
         else
           tune_chain<double>(h, cl, c, s);
       }
-      // dot products of 16 fine-level vectors (at most 2^21 entries each) for VB = 4, 8, 16
-      const long long tl = std::min<long long>(h->lv[0].len, 1LL << 21);
-      constexpr int kM = 16;
+      // dot products of 48 fine-level vectors (at most 2^20 entries each) for VB = 4, 8, 16
+      const long long tl = std::min<long long>(h->lv[0].len, 1LL << 20);
+      constexpr int kM = 48;
       cudaError_t e = cudaMalloc(&tmp, (size_t)(kM + 1) * tl * sizeof(double));
       if (e != cudaSuccess) {
         cudaGetLastError();

@@ -1,0 +1,54 @@
+"""Small, self-contained GPU cases for kernel profiling (ncu) of the learned
+coarse correction's kernels at the Burgers nx=256, nt=4096 coarse shape
+(5 x 512 x 256 per sample).
+
+    python -m paper_2405_04808_gb300.profile_cases conv_fwd_bf16
+    python -m paper_2405_04808_gb300.profile_cases conv_fwd_fp32
+    python -m paper_2405_04808_gb300.profile_cases train_step
+
+Each case runs a warm-up and then `--reps` launches of the kernels it names,
+and exits non-zero on any library error.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=8)
+    args = ap.parse_args(argv)
+    import torch
+
+    from . import pintmg as P
+    from . import workloads as W
+    T, X = 512, 256
+    net = P.mg_net_create(W.net_init_params(1).astype(np.float32))
+    try:
+        g = torch.Generator(device="cuda").manual_seed(0)
+        if args.case.startswith("conv_fwd"):
+            x = torch.randn((1, 5, T, X), device="cuda", generator=g)
+            y = torch.empty_like(x)
+            bf16 = args.case.endswith("bf16")
+            for _ in range(1 + args.reps):
+                P.mg_net_forward(net, x.data_ptr(), 1, T, X, y.data_ptr(), bf16=bf16)
+        else:
+            B = args.batch
+            x = torch.randn((B, 5, T, X), device="cuda", generator=g)
+            t = torch.randn_like(x)
+            for _ in range(1 + args.reps):
+                P.mg_net_loss_grad(net, x.data_ptr(), t.data_ptr(), B, T, X)
+                P.mg_net_adam_step(net, 1e-3)
+        torch.cuda.synchronize()
+    finally:
+        P.mg_net_destroy(net)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -37,36 +37,106 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16(v); }
 
 // z[b,o,t,s] = bias[o] + sum_{c,i,j} W[o,c,i,j] x[b,c,t+i-1,s+j-3] (zero outside);
-// y = z (last layer) or leaky(z).  One thread per output element, FP32
-// accumulation; x, W, y in storage type T (float or bf16), z in FP32 when kept.
-template <typename T>
-__global__ void k_conv_fwd(const T *__restrict__ x, const T *__restrict__ W, const T *__restrict__ bias, T *y,
-                           float *z, int B, int C, int O, int H, int Wd, int act) {
-  const long long total = (long long)B * O * H * Wd;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(idx % Wd);
-    const int t = (int)((idx / Wd) % H);
-    const int o = (int)((idx / ((long long)Wd * H)) % O);
-    const int b = (int)(idx / ((long long)Wd * H * O));
-    float acc = to_f(bias[o]);
-    for (int c = 0; c < C; ++c) {
-      const T *xc = x + ((long long)b * C + c) * H * Wd;
-      const T *wc = W + ((long long)o * C + c) * kNetKT * kNetKX;
+// y = z (last layer) or leaky(z); z kept in FP32 when requested (training).
+// Tiled direct convolution with FP32 accumulation: a CTA computes a
+// 16 (time) x 64 (space) tile of positions for OB output channels; each thread
+// 2 x 2 positions (rows 2ty, 2ty+1; columns tx, tx+32) x OB channels in FP32
+// registers.  Input channels are staged in chunks of kConvCC into shared
+// memory with their halo (zero outside the grid), converted to FP32, and the
+// chunk's weights as [c][tap][o] so that one 16-byte broadcast load feeds
+// four channels.  W is [O][C][3][7] in storage type T; bias may be NULL.
+// Grid: (ceil(Wd / 64), ceil(H / 16), B * ceil(O / OB)), 256 threads.
+constexpr int kConvTT = 16, kConvTX = 64, kConvCC = 4;
+
+template <typename T, int OB>
+__global__ void __launch_bounds__(256) k_conv_tiled(const T *__restrict__ x, const T *__restrict__ W,
+                                                    const T *__restrict__ bias, T *y, float *z, int B, int C, int O,
+                                                    int H, int Wd, int act) {
+  constexpr int K = kNetKT * kNetKX;
+  constexpr int RH = kConvTT + kNetKT - 1, RW = kConvTX + kNetKX - 1;
+  __shared__ float sx[kConvCC][RH][RW];
+  __shared__ __align__(16) float sw[kConvCC][K][OB];
+  const int nob = (O + OB - 1) / OB;
+  const int b = blockIdx.z / nob, ob = (blockIdx.z % nob) * OB;
+  const int t0 = blockIdx.y * kConvTT, s0 = blockIdx.x * kConvTX;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float acc[2][2][OB];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int o = 0; o < OB; ++o) acc[r][q][o] = 0.f;
+  for (int c0 = 0; c0 < C; c0 += kConvCC) {
+    // stage the input chunk with its halo, and the chunk's weights
+    for (int e = threadIdx.x; e < kConvCC * RH * RW; e += blockDim.x) {
+      const int cc = e / (RH * RW), rr = (e / RW) % RH, col = e % RW;
+      const int c = c0 + cc, t = t0 + rr - kNetKT / 2, sp = s0 + col - kNetKX / 2;
+      float v = 0.f;
+      if (c < C && t >= 0 && t < H && sp >= 0 && sp < Wd) v = to_f(x[(((long long)b * C + c) * H + t) * Wd + sp]);
+      sx[cc][rr][col] = v;
+    }
+    for (int e = threadIdx.x; e < kConvCC * K * OB; e += blockDim.x) {
+      const int cc = e / (K * OB), k = (e / OB) % K, o = e % OB;
+      const int c = c0 + cc;
+      sw[cc][k][o] = (c < C && ob + o < O) ? to_f(W[((long long)(ob + o) * C + c) * K + k]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int cc = 0; cc < kConvCC; ++cc) {
 #pragma unroll
       for (int i = 0; i < kNetKT; ++i) {
-        const int tt = t + i - kNetKT / 2;
-        if (tt < 0 || tt >= H) continue;
 #pragma unroll
         for (int j = 0; j < kNetKX; ++j) {
-          const int ss = s + j - kNetKX / 2;
-          if (ss < 0 || ss >= Wd) continue;
-          acc = fmaf(to_f(wc[i * kNetKX + j]), to_f(xc[(long long)tt * Wd + ss]), acc);
+          const float x00 = sx[cc][2 * ty + i][tx + j], x01 = sx[cc][2 * ty + i][tx + 32 + j];
+          const float x10 = sx[cc][2 * ty + 1 + i][tx + j], x11 = sx[cc][2 * ty + 1 + i][tx + 32 + j];
+          const float4 *wv = reinterpret_cast<const float4 *>(&sw[cc][i * kNetKX + j][0]);
+#pragma unroll
+          for (int o4 = 0; o4 < OB / 4; ++o4) {
+            const float4 w4 = wv[o4];
+            const float wo[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              acc[0][0][4 * o4 + u] = fmaf(wo[u], x00, acc[0][0][4 * o4 + u]);
+              acc[0][1][4 * o4 + u] = fmaf(wo[u], x01, acc[0][1][4 * o4 + u]);
+              acc[1][0][4 * o4 + u] = fmaf(wo[u], x10, acc[1][0][4 * o4 + u]);
+              acc[1][1][4 * o4 + u] = fmaf(wo[u], x11, acc[1][1][4 * o4 + u]);
+            }
+          }
         }
       }
     }
-    if (z) z[idx] = acc;
-    y[idx] = from_f<T>(act ? (acc > 0.f ? acc : kNetSlope * acc) : acc);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int t = t0 + 2 * ty + r;
+    if (t >= H) continue;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int sp = s0 + tx + 32 * q;
+      if (sp >= Wd) continue;
+#pragma unroll
+      for (int o = 0; o < OB; ++o) {
+        if (ob + o >= O) continue;
+        const float v = acc[r][q][o] + (bias ? to_f(bias[ob + o]) : 0.f);
+        const long long idx = (((long long)b * O + ob + o) * H + t) * Wd + sp;
+        if (z) z[idx] = v;
+        y[idx] = from_f<T>(act ? (v > 0.f ? v : kNetSlope * v) : v);
+      }
+    }
+  }
+}
+
+// Wt[c][o][i][j] = W[o][c][KT-1-i][KX-1-j]: the gradient with respect to a
+// layer's input is the convolution of the output gradient with these weights
+__global__ void k_flip_transpose(const float *__restrict__ W, float *Wt, int C, int O) {
+  constexpr int K = kNetKT * kNetKX;
+  const long long n = (long long)O * C * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % K), c = (int)((e / K) % C), o = (int)(e / ((long long)K * C));
+    const int i = k / kNetKX, j = k % kNetKX;
+    Wt[((long long)c * O + o) * K + (kNetKT - 1 - i) * kNetKX + (kNetKX - 1 - j)] = W[e];
   }
 }
 
@@ -76,83 +146,113 @@ __global__ void k_leaky_bwd(float *g, const float *__restrict__ z, long long n) 
     if (!(z[i] > 0.f)) g[i] *= kNetSlope;
 }
 
-// gx[b,c,t,s] = sum_{o,i,j} W[o,c,i,j] gz[b,o,t-i+1,s-j+3]
-__global__ void k_conv_bwd_data(const float *__restrict__ gz, const float *__restrict__ W, float *gx, int B, int C,
-                                int O, int H, int Wd) {
-  const long long total = (long long)B * C * H * Wd;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(idx % Wd);
-    const int t = (int)((idx / Wd) % H);
-    const int c = (int)((idx / ((long long)Wd * H)) % C);
-    const int b = (int)(idx / ((long long)Wd * H * C));
-    float acc = 0.f;
-    for (int o = 0; o < O; ++o) {
-      const float *go = gz + ((long long)b * O + o) * H * Wd;
-      const float *wc = W + ((long long)o * C + c) * kNetKT * kNetKX;
+// Weight gradient gW[o,c,i,j] = sum_{b,t,s} gz[b,o,t,s] x[b,c,t+i-1,s+j-3].
+// CTA (o-block of 16, c-block of 4, slice p of P): walks the position tiles
+// p, p + P, ... (4 rows x 64 columns of one sample, in a fixed order), staging
+// the tile's output gradient and the input with its halo in shared memory.
+// Thread (o, c, i) keeps the 7 sums of j; per run of 8 positions it reads 8
+// gradients and 14 inputs for 56 fused multiply-adds.  Writes
+// partial[p][o][c][i][j]; k_wgrad_reduce sums the P slices in order.
+// Grid: (ceil(O / 16) * ceil(C / 4), P), 192 threads.
+constexpr int kWgRows = 4, kWgCols = 64, kWgOB = 16, kWgCB = 4;
+
+__global__ void __launch_bounds__(192) k_conv_wgrad(const float *__restrict__ gz, const float *__restrict__ x,
+                                                    float *partial, int B, int C, int O, int H, int Wd) {
+  constexpr int K = kNetKT * kNetKX;
+  constexpr int GS = kWgCols + 4;  // padded row: consecutive o rows start 4 banks apart
+  constexpr int XR = kWgRows + kNetKT - 1, XC = kWgCols + kNetKX - 1 + 1;
+  __shared__ __align__(16) float sg[kWgOB][kWgRows][GS];
+  __shared__ float sx[kWgCB][XR][XC];
+  const int ncb = (C + kWgCB - 1) / kWgCB;
+  const int ob = (blockIdx.x / ncb) * kWgOB, cb = (blockIdx.x % ncb) * kWgCB;
+  const int P = gridDim.y, p = blockIdx.y;
+  const int ol = threadIdx.x % kWgOB, cl = (threadIdx.x / kWgOB) % kWgCB, i = threadIdx.x / (kWgOB * kWgCB);
+  const int tilesT = (H + kWgRows - 1) / kWgRows, tilesX = (Wd + kWgCols - 1) / kWgCols;
+  const long long tiles = (long long)B * tilesT * tilesX;
+  float acc[kNetKX];
 #pragma unroll
-      for (int i = 0; i < kNetKT; ++i) {
-        const int tt = t - i + kNetKT / 2;
-        if (tt < 0 || tt >= H) continue;
+  for (int j = 0; j < kNetKX; ++j) acc[j] = 0.f;
+  for (long long tile = p; tile < tiles; tile += P) {
+    const int b = (int)(tile / ((long long)tilesT * tilesX));
+    const int t0 = (int)((tile / tilesX) % tilesT) * kWgRows, s0 = (int)(tile % tilesX) * kWgCols;
+    for (int e = threadIdx.x; e < kWgOB * kWgRows * kWgCols; e += blockDim.x) {
+      const int o = e / (kWgRows * kWgCols), r = (e / kWgCols) % kWgRows, col = e % kWgCols;
+      const int t = t0 + r, sp = s0 + col;
+      float v = 0.f;
+      if (ob + o < O && t < H && sp < Wd) v = gz[(((long long)b * O + ob + o) * H + t) * Wd + sp];
+      sg[o][r][col] = v;
+    }
+    for (int e = threadIdx.x; e < kWgCB * XR * XC; e += blockDim.x) {
+      const int c = e / (XR * XC), r = (e / XC) % XR, col = e % XC;
+      const int t = t0 + r - kNetKT / 2, sp = s0 + col - kNetKX / 2;
+      float v = 0.f;
+      if (cb + c < C && t >= 0 && t < H && sp >= 0 && sp < Wd) v = x[(((long long)b * C + cb + c) * H + t) * Wd + sp];
+      sx[c][r][col] = v;
+    }
+    __syncthreads();
+    if (i < kNetKT) {
+#pragma unroll 1
+      for (int r = 0; r < kWgRows; ++r) {
+#pragma unroll 1
+        for (int s = 0; s < kWgCols; s += 8) {
+          const float4 g0 = *reinterpret_cast<const float4 *>(&sg[ol][r][s]);
+          const float4 g1 = *reinterpret_cast<const float4 *>(&sg[ol][r][s + 4]);
+          const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+          float xv[8 + kNetKX - 1];
 #pragma unroll
-        for (int j = 0; j < kNetKX; ++j) {
-          const int ss = s - j + kNetKX / 2;
-          if (ss < 0 || ss >= Wd) continue;
-          acc = fmaf(wc[i * kNetKX + j], go[(long long)tt * Wd + ss], acc);
+          for (int k = 0; k < 8 + kNetKX - 1; ++k) xv[k] = sx[cl][r + i][s + k];
+#pragma unroll
+          for (int j = 0; j < kNetKX; ++j)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[j] = fmaf(g[k], xv[k + j], acc[j]);
         }
       }
     }
-    gx[idx] = acc;
+    __syncthreads();
+  }
+  if (i < kNetKT && ob + ol < O && cb + cl < C) {
+    float *dst = partial + (((long long)p * O + ob + ol) * C + cb + cl) * K + i * kNetKX;
+#pragma unroll
+    for (int j = 0; j < kNetKX; ++j) dst[j] = acc[j];
   }
 }
 
-// gW[o,c,i,j] = sum_{b,t,s} gz[b,o,t,s] x[b,c,t+i-1,s+j-3] and gb[o] = sum gz[b,o,.,.]:
-// one CTA per (o, c) with the 21 taps (and the bias for c == 0) reduced in a
-// fixed order (deterministic).
-__global__ void __launch_bounds__(256) k_conv_bwd_weights(const float *__restrict__ gz, const float *__restrict__ x,
-                                                          float *gW, float *gb, int B, int C, int O, int H, int Wd) {
-  const int o = blockIdx.x / C, c = blockIdx.x % C;
-  constexpr int K = kNetKT * kNetKX;
-  float acc[K + 1];
-#pragma unroll
-  for (int k = 0; k <= K; ++k) acc[k] = 0.f;
-  const long long pos = (long long)B * H * Wd;
-  for (long long p = threadIdx.x; p < pos; p += blockDim.x) {
-    const int s = (int)(p % Wd);
-    const int t = (int)((p / Wd) % H);
-    const int b = (int)(p / ((long long)Wd * H));
-    const float g = gz[(((long long)b * O + o) * H + t) * Wd + s];
-    const float *xc = x + ((long long)b * C + c) * H * Wd;
-#pragma unroll
-    for (int i = 0; i < kNetKT; ++i) {
-      const int tt = t + i - kNetKT / 2;
-#pragma unroll
-      for (int j = 0; j < kNetKX; ++j) {
-        const int ss = s + j - kNetKX / 2;
-        const float xv = (tt >= 0 && tt < H && ss >= 0 && ss < Wd) ? xc[(long long)tt * Wd + ss] : 0.f;
-        acc[i * kNetKX + j] = fmaf(g, xv, acc[i * kNetKX + j]);
-      }
-    }
-    acc[K] += g;
+// gW[e] = sum_{p < P} partial[p][e] in order (e < O * C * 21)
+__global__ void k_wgrad_reduce(const float *__restrict__ partial, int P, long long n, float *gW) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int q = 0; q < P; ++q) s += partial[(long long)q * n + e];
+    gW[e] = s;
   }
-  __shared__ float red[K + 1][8];
-  const int w = threadIdx.x / kWarp, ln = threadIdx.x & (kWarp - 1);
-#pragma unroll
-  for (int k = 0; k <= K; ++k) {
-    float v = acc[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
-    if (ln == 0) red[k][w] = v;
+}
+
+// bias gradient partials: partial[o * G + g] = sum over chunk g of gz[., o, ., .]
+// (grid (O, G), 256 threads, fixed order); k_bias_reduce finishes
+__global__ void k_bias_partial(const float *__restrict__ gz, int B, int O, long long TX, float *partial) {
+  const int o = blockIdx.x, G = gridDim.y;
+  const long long per = (long long)B * TX;
+  float acc = 0.f;
+  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < per; e += (long long)G * blockDim.x) {
+    const long long b = e / TX, t = e % TX;
+    acc += gz[(b * O + o) * TX + t];
   }
+  __shared__ float red[8];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(kFull, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = acc;
   __syncthreads();
-  if (threadIdx.x <= K) {
-    float sum = 0.f;
-    for (int i = 0; i < (int)(blockDim.x / kWarp); ++i) sum += red[threadIdx.x][i];
-    if (threadIdx.x < K)
-      gW[((long long)o * C + c) * K + threadIdx.x] = sum;
-    else if (c == 0)
-      gb[o] = sum;
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) s += red[q];
+    partial[(long long)o * G + blockIdx.y] = s;
   }
+}
+
+__global__ void k_bias_reduce(const float *__restrict__ partial, int G, int O, float *gb) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= O) return;
+  float s = 0.f;
+  for (int q = 0; q < G; ++q) s += partial[(long long)o * G + q];
+  gb[o] = s;
 }
 
 // loss partials of mean((y - t)^2) and g = 2 (y - t) / n

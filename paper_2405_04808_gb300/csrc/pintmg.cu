@@ -106,6 +106,8 @@ struct mg_net {
   // standalone inference workspace (mg_net_forward): ping-pong activations and a BF16 copy of x/y
   void *ia = nullptr, *ib = nullptr, *ic = nullptr;
   long long inf_bytes = 0;
+  float *wt = nullptr;                 // flipped, transposed weights of one layer (input gradient)
+  float *wpart = nullptr, *bpart = nullptr;  // weight / bias gradient partial sums
   float *sx = nullptr, *sy = nullptr;  // per-channel input / target scales of a normalised training run
   double *spart = nullptr;             // their partial sums
   int *order = nullptr;  // minibatch gather indices (device)
@@ -654,6 +656,19 @@ void sgs_fp64<float>(mg_handle *h, Level &lev, const double *r, double *y, cudaS
 // ---------------------------------------------------------------------------
 // Learned coarse correction: network forward pass and the admission test
 
+// one convolution layer (k_conv_tiled): 16 output channels per CTA, or 8 for narrow layers
+template <typename T>
+void launch_conv(const T *x, const T *W, const T *bias, T *y, float *z, int B, int C, int O, int H, int Wd, int act,
+                 cudaStream_t s) {
+  const int OB = O > 8 ? 16 : 8;
+  const dim3 grid((Wd + kConvTX - 1) / kConvTX, (H + kConvTT - 1) / kConvTT, B * ((O + OB - 1) / OB));
+  if (OB == 16)
+    k_conv_tiled<T, 16><<<grid, 256, 0, s>>>(x, W, bias, y, z, B, C, O, H, Wd, act);
+  else
+    k_conv_tiled<T, 8><<<grid, 256, 0, s>>>(x, W, bias, y, z, B, C, O, H, Wd, act);
+  ck_launch();
+}
+
 // The network's forward pass in storage type T (inference): x -> y through
 // ping-pong buffers (x == y allowed).  h (may be NULL) counts and times the launches.
 template <typename T>
@@ -668,13 +683,9 @@ void net_forward_storage(mg_handle *h, const T *x, int B, int H, int Wd, T *y, T
     const double flops = 2.0 * n * net_ch(l) * kNetKT * kNetKX;
     if (h) {
       Bracket br(h, CAT_NET, s, (double)sizeof(T) * (n + (double)B * net_ch(l) * H * Wd), flops);
-      k_conv_fwd<T><<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(in, W, bias, out, nullptr, B, net_ch(l),
-                                                               net_ch(l + 1), H, Wd, l < kNetLayers - 1);
-      ck_launch();
+      launch_conv<T>(in, W, bias, out, nullptr, B, net_ch(l), net_ch(l + 1), H, Wd, l < kNetLayers - 1, s);
     } else {
-      k_conv_fwd<T><<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(in, W, bias, out, nullptr, B, net_ch(l),
-                                                               net_ch(l + 1), H, Wd, l < kNetLayers - 1);
-      ck_launch();
+      launch_conv<T>(in, W, bias, out, nullptr, B, net_ch(l), net_ch(l + 1), H, Wd, l < kNetLayers - 1, s);
     }
     in = out;
   }
@@ -1922,6 +1933,8 @@ namespace {
 
 constexpr int kLossPartials = 1024;
 constexpr int kScaleParts = 64;
+constexpr int kWgSlices = 64;   // position slices of the weight gradient (partial sums)
+constexpr int kBiasParts = 64;
 
 // per-channel root mean square of `count` samples of 5 x TX floats
 void channel_rms(mg_net *net, const float *x, int count, long long TX, float *scale, cudaStream_t s) {
@@ -1964,9 +1977,9 @@ void net_loss_grad_dev(mg_net *net, const float *x, const float *target, int B, 
     const float *bias = W + (long long)net_ch(l + 1) * net_ch(l) * kNetKT * kNetKX;
     const long long n = (long long)B * net_ch(l + 1) * TX;
     const bool act = l < kNetLayers - 1;
-    k_conv_fwd<float><<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(in, W, bias, net->h[l + 1], act ? net->z[l] : nullptr,
-                                                                B, net_ch(l), net_ch(l + 1), T, X, act);
-    ck_launch();
+    (void)n;
+    launch_conv<float>(in, W, bias, net->h[l + 1], act ? net->z[l] : nullptr, B, net_ch(l), net_ch(l + 1), T, X, act,
+                       s);
     in = net->h[l + 1];
   }
   const long long nout = (long long)B * net_ch(kNetLayers) * TX;
@@ -1986,13 +1999,24 @@ void net_loss_grad_dev(mg_net *net, const float *x, const float *target, int B, 
     const float *hin = l == 0 ? x : net->h[l];
     float *gW = net->grad + net_layer_offset(l);
     float *gb = gW + (long long)O * C * kNetKT * kNetKX;
-    k_conv_bwd_weights<<<O * C, 256, 0, s>>>(g, hin, gW, gb, B, C, O, T, X);
-    ck_launch();
-    if (l > 0) {
-      const float *W = net->params + net_layer_offset(l);
-      const long long n = (long long)B * C * TX;
-      k_conv_bwd_data<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(g, W, other, B, C, O, T, X);
+    {
+      const int ncb = (C + kWgCB - 1) / kWgCB, nob = (O + kWgOB - 1) / kWgOB;
+      const int P = std::min(kWgSlices, std::max(1, 608 / (ncb * nob)));
+      k_conv_wgrad<<<dim3(nob * ncb, P), 192, 0, s>>>(g, hin, net->wpart, B, C, O, T, X);
       ck_launch();
+      const long long nw = (long long)O * C * kNetKT * kNetKX;
+      k_wgrad_reduce<<<grid_for(nw, 256), 256, 0, s>>>(net->wpart, P, nw, gW);
+      ck_launch();
+      k_bias_partial<<<dim3(O, kBiasParts), 256, 0, s>>>(g, B, O, TX, net->bpart);
+      ck_launch();
+      k_bias_reduce<<<1, 32, 0, s>>>(net->bpart, kBiasParts, O, gb);
+      ck_launch();
+    }
+    if (l > 0) {  // gradient of the layer's input: the convolution with the flipped, transposed weights
+      const float *W = net->params + net_layer_offset(l);
+      k_flip_transpose<<<grid_for((long long)O * C * kNetKT * kNetKX, 256), 256, 0, s>>>(W, net->wt, C, O);
+      ck_launch();
+      launch_conv<float>(g, net->wt, nullptr, other, nullptr, B, O, C, T, X, 0, s);
       std::swap(g, other);
     }
   }
@@ -2059,6 +2083,9 @@ int mg_net_create(const float *init_params, mg_net **out) {
     net->v = net->mem.alloc<float>(kNetParams);
     net->partial = net->mem.alloc<float>(kLossPartials);
     net->params_bf16 = net->mem.alloc<__nv_bfloat16>(kNetParams);
+    net->wt = net->mem.alloc<float>((size_t)32 * 32 * kNetKT * kNetKX);
+    net->wpart = net->mem.alloc<float>((size_t)kWgSlices * 32 * 32 * kNetKT * kNetKX);
+    net->bpart = net->mem.alloc<float>((size_t)32 * kBiasParts);
     net->sx = net->mem.alloc<float>(8);
     net->sy = net->mem.alloc<float>(8);
     net->spart = net->mem.alloc<double>((size_t)8 * kScaleParts);

@@ -135,8 +135,12 @@ def test_training_step_matches_oracle(P, normalize):
         got = P.mg_net_get_params(net).astype(np.float64)
     finally:
         P.mg_net_destroy(net)
-    # Adam's first step moves each parameter by ~lr: compare in units of lr
-    assert np.max(np.abs(got - want) / np.maximum(1.0, np.abs(want))) <= 2e-5
+    # Adam's first step moves each parameter by lr * g / (|g| + eps), i.e. by about lr * sign(g): where
+    # the oracle's gradient is within the FP32 gradient's rounding of zero its sign is not determined
+    # by the arithmetic, so those parameters are left out (a few of 49,829)
+    decided = np.abs(g) > 1e-6 * np.linalg.norm(g)
+    assert decided.mean() > 0.99
+    assert np.max((np.abs(got - want) / np.maximum(1.0, np.abs(want)))[decided]) <= 2e-5
 
 
 def _scaled_data(B, T, X):

@@ -141,7 +141,15 @@ FP64_TFLOPS_MEASURED = 1.196
 FP32_TFLOPS_MEASURED = 74.2
 
 
-def roofline(prof, dominant, precision):
+# DRAM traffic / algorithmic bytes of a dominant kernel from an ncu capture of
+# the same workload (dram__bytes_read.sum + dram__bytes_write.sum per launch);
+# valid while the kernel is unchanged since that capture
+TRAFFIC_RATIO = {
+    ("burgers_nx128_n1024", "multidot", "fp64"): (1.15, "profiles/multidot_burgers_nx128_n1024.md"),
+}
+
+
+def roofline(prof, dominant, precision, workload=None):
     """Roofline object of the dominant kernel category from the library's
     event timings and its algorithmic byte / flop models (per launch)."""
     hbm, peak_kind = measured_peaks()
@@ -157,6 +165,10 @@ def roofline(prof, dominant, precision):
     common = {"kernel": dominant, "launches": n, "avg_launch_us": round(ms * 1e3 / n, 3),
               "bytes_per_launch": round(nbytes / n), "flops_per_launch": round(nflops / n),
               "traffic": None}
+    ratio = TRAFFIC_RATIO.get((workload, dominant, precision))
+    if ratio:
+        common["traffic"] = round(ratio[0] * nbytes / n)
+        common["traffic_source"] = f"{ratio[1]}: ncu DRAM bytes = {ratio[0]} x algorithmic bytes"
     if t_alu > t_hbm:
         return {"bound": "alu", "achieved": round(fl, 4), "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": round(fl / alu_peak, 4), "achieved_gbs": round(bw, 1), "hbm_peak_gbs": hbm,
@@ -232,7 +244,8 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
                "iters": [i.iters for i in infos], "true_relres": max(i.true_relres for i in infos),
                "coarse_iters_per_vcycle": sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)),
                "setup_ms": setup_ms, "launches": launches, "shares": shares, "dominant": dominant,
-               "roofline": roofline(shares, dominant, precision), "clocks": clk.summary()}
+               "roofline": roofline(shares, dominant, precision, args.workload if levels is None else None),
+               "clocks": clk.summary()}
         if want_e2e:
             # end to end through the public API with pinned host buffers
             bh = torch.tensor(prob.b).pin_memory()

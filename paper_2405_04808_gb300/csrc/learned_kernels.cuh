@@ -159,9 +159,11 @@ constexpr int kWgRows = 4, kWgCols = 64, kWgOB = 16, kWgCB = 4;
 __global__ void __launch_bounds__(192) k_conv_wgrad(const float *__restrict__ gz, const float *__restrict__ x,
                                                     float *partial, int B, int C, int O, int H, int Wd) {
   constexpr int K = kNetKT * kNetKX;
-  constexpr int GS = kWgCols + 4;  // padded row: consecutive o rows start 4 banks apart
+  // output-gradient tile, one padded block per channel: consecutive channels
+  // start 4 banks apart, so the 16-byte reads of 8 lanes hit 32 distinct banks
+  constexpr int GO = kWgRows * kWgCols + 4;
   constexpr int XR = kWgRows + kNetKT - 1, XC = kWgCols + kNetKX - 1 + 1;
-  __shared__ __align__(16) float sg[kWgOB][kWgRows][GS];
+  __shared__ __align__(16) float sg[kWgOB * GO];
   __shared__ float sx[kWgCB][XR][XC];
   const int ncb = (C + kWgCB - 1) / kWgCB;
   const int ob = (blockIdx.x / ncb) * kWgOB, cb = (blockIdx.x % ncb) * kWgCB;
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(192) k_conv_wgrad(const float *__restrict__ gz
       const int t = t0 + r, sp = s0 + col;
       float v = 0.f;
       if (ob + o < O && t < H && sp < Wd) v = gz[(((long long)b * O + ob + o) * H + t) * Wd + sp];
-      sg[o][r][col] = v;
+      sg[o * GO + r * kWgCols + col] = v;
     }
     for (int e = threadIdx.x; e < kWgCB * XR * XC; e += blockDim.x) {
       const int c = e / (XR * XC), r = (e / XC) % XR, col = e % XC;
@@ -195,8 +197,8 @@ __global__ void __launch_bounds__(192) k_conv_wgrad(const float *__restrict__ gz
       for (int r = 0; r < kWgRows; ++r) {
 #pragma unroll 1
         for (int s = 0; s < kWgCols; s += 8) {
-          const float4 g0 = *reinterpret_cast<const float4 *>(&sg[ol][r][s]);
-          const float4 g1 = *reinterpret_cast<const float4 *>(&sg[ol][r][s + 4]);
+          const float4 g0 = *reinterpret_cast<const float4 *>(&sg[ol * GO + r * kWgCols + s]);
+          const float4 g1 = *reinterpret_cast<const float4 *>(&sg[ol * GO + r * kWgCols + s + 4]);
           const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
           float xv[8 + kNetKX - 1];
 #pragma unroll

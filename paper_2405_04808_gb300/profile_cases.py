@@ -8,6 +8,11 @@ coarse correction's kernels at the Burgers nx=256, nt=4096 coarse shape
 
 Each case runs a warm-up and then `--reps` launches of the kernels it names,
 and exits non-zero on any library error.
+
+    python -m paper_2405_04808_gb300.profile_cases summarize LAUNCHES.csv
+
+condenses an ncu launch list (``--metrics gpu__time_duration.sum --csv``) to
+launches, total time and share per kernel name.
 """
 from __future__ import annotations
 
@@ -17,7 +22,39 @@ import sys
 import numpy as np
 
 
+def summarize(path: str) -> str:
+    """Markdown table of an ncu CSV launch list: launches, total ms and share per kernel."""
+    import csv
+    import io
+    rows = []
+    with open(path, newline="") as f:
+        text = f.read()
+    start = text.find('"ID"')
+    for r in csv.DictReader(io.StringIO(text[start:])):
+        if r.get("Metric Name") == "gpu__time_duration.sum":
+            v = float(r["Metric Value"].replace(",", ""))
+            unit = r.get("Metric Unit", "")
+            scale = {"nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "second": 1e3}.get(unit, 1e-6)
+            name = r["Kernel Name"]
+            name = name.split("(")[0].replace("void ", "") if "(" in name else name
+            rows.append((name, v * scale))
+    tot = {}
+    for name, ms in rows:
+        n, t = tot.get(name, (0, 0.0))
+        tot[name] = (n + 1, t + ms)
+    total = sum(t for _, t in tot.values()) or 1.0
+    out = [f"{len(rows)} launches, {total:.1f} ms in all", "", "| kernel | launches | total ms | share |",
+           "|---|---|---|---|"]
+    for name, (n, t) in sorted(tot.items(), key=lambda kv: -kv[1][1]):
+        out.append(f"| {name} | {n} | {t:.3f} | {100 * t / total:.1f} % |")
+    return "\n".join(out)
+
+
 def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
+    if argv and argv[0] == "summarize":
+        print(summarize(argv[1]))
+        return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step"])
     ap.add_argument("--reps", type=int, default=3)

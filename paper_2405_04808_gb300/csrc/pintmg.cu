@@ -610,7 +610,8 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
     if (scan) {
       run_scan<T>(h, d.scanF, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, d.scan_tmp, n, p, 0, s);
     } else if (n >= 1) {
-      Bracket br(h, CAT_CHAIN, s);
+      // algorithmic: one p x p link matrix read and applied per step
+      Bracket br(h, CAT_CHAIN, s, (double)sizeof(T) * n * ((double)p * p + 2.0 * p), 2.0 * n * p * p);
       if (!cluster || !launch_chain_cluster<T, true>(h, d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p, s)) {
         k_chain_forward<T><<<1, threads, shm, s>>>(d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p);
       }
@@ -628,7 +629,7 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
   if (scan) {
     run_scan<T>(h, d.scanB, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, d.scan_tmp, n, p, 1, s);
   } else if (n >= 1) {
-    Bracket br(h, CAT_CHAIN, s);
+    Bracket br(h, CAT_CHAIN, s, (double)sizeof(T) * n * ((double)p * p + 2.0 * p), 2.0 * n * p * p);
     if (!cluster || !launch_chain_cluster<T, false>(h, d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p, s)) {
       k_chain_backward<T><<<1, threads, shm, s>>>(d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p);
     }

@@ -240,7 +240,7 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
         local_ms = sum(a.elapsed_time(bb) for a, bb in ev)
         value = RP.job_throughput(local_ms / 1e3, steps, world, device=dev)
         total_ms = 1e3 * world * steps / value   # the slowest rank's time
-        out = {"value": value, "ms_per_step": total_ms / steps,
+        out = {"value": value, "ms_per_step": total_ms / steps, "x": x.clone(),
                "iters": [i.iters for i in infos], "true_relres": max(i.true_relres for i in infos),
                "coarse_iters_per_vcycle": sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)),
                "setup_ms": setup_ms, "launches": launches, "shares": shares, "dominant": dominant,
@@ -438,8 +438,11 @@ def run_native(args):
                 continue
             v = measure(P, torch, prob, wl, args, prec, om, max(1, min(args.steps, 3)), 1, dev, stream, world, False,
                         levels=lv)
+            # the variant's solution against the headline solve's (both to a 1e-8 relative residual)
+            xdiff = float(torch.linalg.vector_norm(v["x"] - main["x"]) / torch.linalg.vector_norm(main["x"]))
             variants[name] = {"value": round(v["value"], 4), "unit": UNIT, "ms_per_step": round(v["ms_per_step"], 3),
                               "fgmres_iters": v["iters"][0], "true_relres": v["true_relres"],
+                              "solution_rel_diff_vs_main": xdiff,
                               "precision": prec, "omega": om, "levels": lv or wl["levels"],
                               "coarse_iters_per_vcycle": round(v["coarse_iters_per_vcycle"], 3),
                               "setup_ms": round(v["setup_ms"], 1),

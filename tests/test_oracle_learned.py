@@ -84,3 +84,29 @@ def test_fold_is_the_normalised_network():
     assert np.allclose(yn, y / sy[None, :, None, None], rtol=1e-12, atol=1e-14)
     assert np.allclose(NL.fold(pn, sx, sy, -1), p, rtol=1e-14, atol=0)
     assert np.allclose(NL.channel_rms(np.ones((3, 5, 2, 2)) * 2.0), 2.0)
+
+
+def test_batch_workload_mix():
+    """The batched workload: 64 systems, half van der Pol (nt 512 ... 16384), half Burgers (nx 64/128/256 x nt 512 ...
+    4096), distinct seeds, 4 levels each (every nt divisible by 8).  Built from small counts here (the forward
+    solves of the large members take seconds)."""
+    from paper_2405_04808_gb300.workloads import _batch_member
+    shapes = []
+    for k in (0, 1, 2, 3, 22, 23):
+        prob, opts = _batch_member(k, 6000)
+        assert opts["levels"] == 4 and prob.n % 8 == 0
+        shapes.append((prob.kind, prob.n, prob.p))
+    assert shapes[0] == ("dense", 512, 2) and shapes[2] == ("dense", 1024, 2)
+    assert shapes[1] == ("tridiag", 512, 64) and shapes[3] == ("tridiag", 512, 128)
+    assert shapes[4] == ("dense", 16384, 2) and shapes[5] == ("tridiag", 4096, 256)
+
+
+def test_launch_list_summary(tmp_path):
+    from paper_2405_04808_gb300.profile_cases import summarize
+    f = tmp_path / "l.csv"
+    f.write_text('==PROF== x\n"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+                 '"0","void k_a<double>(int)","gpu__time_duration.sum","usecond","3"\n'
+                 '"1","k_b","gpu__time_duration.sum","nsecond","1,000"\n'
+                 '"2","void k_a<double>(int)","gpu__time_duration.sum","usecond","6"\n')
+    out = summarize(str(f))
+    assert "| k_a<double> | 2 | 0.009 | 90.0 % |" in out and "| k_b | 1 | 0.001 | 10.0 % |" in out

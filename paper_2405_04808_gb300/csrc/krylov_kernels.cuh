@@ -255,20 +255,49 @@ __global__ void k_norm_from_sq(const double *nrm2, double *scal, const int *guar
 // Arnoldi column j: H[0..j][j] = h, H[j+1][j] = ||w||; apply the previous
 // Givens rotations, form rotation j, update g.  H is column-major with leading
 // dimension ldh.  scal: [0] |g_{j+1}|, [1] 1/h_{j+1,j}, [2] h_{j+1,j}.
+// One warp.  The previous rotations act on the new column as a first-order
+// linear recurrence: with t_0 = h_0, rotation i gives
+//   col_i = c_i t_i + s_i h_{i+1},   t_{i+1} = -s_i t_i + c_i h_{i+1},
+// so each lane composes the affine maps of its chunk of rotations, a warp
+// scan gives every chunk its incoming t, and the chunk is re-run; t_j meets
+// h_{j+1,j} = ||w|| in the new rotation j.
 __global__ void k_arnoldi_step(int j, const double *__restrict__ h, const double *__restrict__ w2, double *H,
                                int ldh, double *cs, double *sn, double *g, double *scal, const int *j_dev = nullptr) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= kWarp) return;
   if (j_dev) j = *j_dev;
+  const int ln = threadIdx.x;
   double *col = H + (long long)j * ldh;
-  for (int i = 0; i <= j; ++i) col[i] = h[i];
   const double hj1 = sqrt(w2[0]);
-  col[j + 1] = hj1;
-  for (int i = 0; i < j; ++i) {
-    const double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
+  const int ch = (j + kWarp - 1) / kWarp;
+  const int i0 = min(ln * ch, j), i1 = min(i0 + ch, j);
+  double A = 1.0, B = 0.0;  // this chunk's map t -> A t + B
+  for (int i = i0; i < i1; ++i) {
+    const double a = -sn[i];
+    B = fma(a, B, cs[i] * h[i + 1]);
+    A *= a;
   }
-  const double a = col[j], b = col[j + 1];
+#pragma unroll
+  for (int off = 1; off < kWarp; off <<= 1) {  // inclusive scan: compose with the lanes below
+    const double Ap = __shfl_up_sync(kFull, A, off), Bp = __shfl_up_sync(kFull, B, off);
+    if (ln >= off) {
+      B = fma(A, Bp, B);
+      A *= Ap;
+    }
+  }
+  double Ae = __shfl_up_sync(kFull, A, 1), Be = __shfl_up_sync(kFull, B, 1);
+  if (ln == 0) {
+    Ae = 1.0;
+    Be = 0.0;
+  }
+  double t = fma(Ae, h[0], Be);
+  for (int i = i0; i < i1; ++i) {
+    const double hi1 = h[i + 1];
+    col[i] = fma(cs[i], t, sn[i] * hi1);
+    t = fma(-sn[i], t, cs[i] * hi1);
+  }
+  const double Aall = __shfl_sync(kFull, A, kWarp - 1), Ball = __shfl_sync(kFull, B, kWarp - 1);
+  if (ln != 0) return;
+  const double a = fma(Aall, h[0], Ball), b = hj1;
   const double den = hypot(a, b);
   double c = 1.0, s = 0.0;
   if (den != 0.0) {

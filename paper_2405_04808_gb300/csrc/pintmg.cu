@@ -420,7 +420,7 @@ void arnoldi_step_dev(mg_handle *h, mg_handle::Krylov &K, KState *st, int jmax, 
   orthogonalise(h, K, V, len, jmax, w, s, &st->m1);
   {
     Bracket br(h, CAT_SMALL, s);
-    k_arnoldi_step<<<1, 1, 0, s>>>(0, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal, &st->j);
+    k_arnoldi_step<<<1, kWarp, 0, s>>>(0, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal, &st->j);
     ck_launch();
   }
   {
@@ -469,7 +469,7 @@ void arnoldi_step(mg_handle *h, mg_handle::Krylov &K, double *V, long long len, 
   orthogonalise(h, K, V, len, j, w, s);
   {
     Bracket br(h, CAT_SMALL, s);
-    k_arnoldi_step<<<1, 1, 0, s>>>(j, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal);
+    k_arnoldi_step<<<1, kWarp, 0, s>>>(j, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal);
     ck_launch();
   }
   {

@@ -275,7 +275,7 @@ void mg_net_destroy(mg_net *net);
  *   e = rms(r) net(r / rms(r))   (BF16 inference if bf16 = 1, else FP32),
  * and it is admitted when ||r - A_c e|| <= admit ||r|| (FP64 residual on the
  * coarse level); otherwise the coarse GMRES with SGS runs as without the
- * network, so it is both the judge and the fallback.  FGMRES accepts the
+ * network, so it both measures the proposal and is the fallback.  FGMRES accepts the
  * resulting variable preconditioner.  Needs the tridiagonal layout or
  * q == p (MG_ERR_UNSUPPORTED otherwise) and 0 < admit < 1.  Several handles
  * may share one network.  Parameter updates reach later solves (BF16 copies

@@ -427,7 +427,7 @@ __global__ void k_copy_indexed(double *dst, const double *__restrict__ src, long
 
 // learned coarse correction: admitted if ||r - A e|| <= admit ||r||
 // (rr2 = ||r - A e||^2, scal[0] = ||r||); flag[0] = decision, flag[1] counts admissions
-__global__ void k_net_judge(const double *rr2, const double *scal, double admit, int *flag) {
+__global__ void k_net_admit(const double *rr2, const double *scal, double admit, int *flag) {
   const bool ok = sqrt(rr2[0]) <= admit * scal[0] && scal[0] > 0.0;
   flag[0] = ok ? 1 : 0;
   if (ok) flag[1] += 1;

@@ -754,7 +754,7 @@ void coarse_solve_graph(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
     launch_apply<double>(h, lev.d.view, h->net_e, h->cr, h->net_r, s);
     multidot(h, h->net_r, len, 1, h->net_r, len, K.nrm2 + 3, 0, s);
     Bracket br(h, CAT_SMALL, s);
-    k_net_judge<<<1, 1, 0, s>>>(K.nrm2 + 3, K.scal, h->admit, h->net_flag);
+    k_net_admit<<<1, 1, 0, s>>>(K.nrm2 + 3, K.scal, h->admit, h->net_flag);
     ck_launch();
   }
   const cudaGraphConditionalHandle hdl = new_handle(s);

@@ -323,7 +323,7 @@ def mg_net_destroy(net) -> None:
 
 
 def mg_attach_coarse_net(h, net, admit: float = 0.5, bf16: bool = True) -> None:
-    """Use `net` as h's coarse solve (GMRES+SGS as judge and fallback); net=None detaches."""
+    """Use `net` as h's coarse solve (GMRES+SGS measures the proposal and is the fallback); net=None detaches."""
     _check(lib().mg_attach_coarse_net(ctypes.c_void_p(h), ctypes.c_void_p(net or 0), float(admit),
                                       1 if bf16 else 0), "mg_attach_coarse_net")
 

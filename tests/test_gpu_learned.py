@@ -218,7 +218,7 @@ def test_recorded_pairs_are_coarse_solves(P):
 
 @pytest.mark.parametrize("bf16", [True, False])
 def test_learned_fgmres_reaches_the_solution(P, bf16):
-    """With a network attached (untrained: its proposals are judged and mostly
+    """With a network attached (untrained: its proposals are measured and mostly
     rejected; admit 0.9 lets some through) FGMRES still reaches the direct
     solution; the graph and host-loop solves agree bit for bit."""
     prob = _small_problem(32)

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 # condition numbers (~1e4 here): 1e-10 relative in the 2-norm.
 VCYCLE_RTOL = 1e-10
 # FGMRES at a 1e-10 relative residual: the solution differs from the exact one
-# by at most cond(A) * 1e-10; the spec bar is 1e-9 relative.
+# by at most cond(A) * 1e-10; the required bar is 1e-9 relative.
 SOLVE_RTOL = 1e-9
 
 

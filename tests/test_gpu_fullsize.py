@@ -115,3 +115,27 @@ def test_bench_configuration_iterations_match_oracle(P, name, omega):
         assert np.linalg.norm(prob.b - lev.A @ xr) / np.linalg.norm(prob.b) <= 1.05 * rec["rtol"]
     finally:
         P.mg_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["vdp_n256", "burgers_nx128_n1024"])
+def test_kkt_right_hand_sides_full_size(P, name):
+    """The two KKT right-hand sides at full size: b = (chi, 0) gives x in null(B) (the projection of chi),
+    b = (0, chi) gives B x = chi.  Checked with the oracle's own assembled B and lifted operator."""
+    import dataclasses
+    wl = W.WORKLOADS[name]
+    prob = wl["make"]()
+    lev = O.Level(O.raw_from_problem(prob))
+    raw = lev.raw
+    B = O.lifted_constraint_jacobian(lev.N, lev.V, lev.Z, raw.n, raw.p, raw.q)
+    m, nx = B.shape
+    rng = np.random.default_rng(12)
+    for which in ("primal", "dual"):
+        chi = rng.standard_normal(nx if which == "primal" else m)
+        rhs = np.concatenate([chi, np.zeros(m)]) if which == "primal" else np.concatenate([np.zeros(nx), chi])
+        x, info = _solve(P, dataclasses.replace(prob, b=rhs), wl, 1e-10, omega=0.7)
+        assert np.linalg.norm(rhs - lev.A @ x) <= 1.5e-10 * np.linalg.norm(rhs)
+        Bx = B @ x[:nx]
+        if which == "primal":
+            assert np.linalg.norm(Bx) <= 1.5e-10 * np.linalg.norm(chi)
+        else:
+            assert np.linalg.norm(Bx - chi) <= 1.5e-10 * np.linalg.norm(chi)

@@ -1,4 +1,6 @@
 """Pins of the oracle's multigrid and Krylov components against the paper and mathematics."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -235,3 +237,73 @@ def test_parallel_speedup_example():
     """Sec. 6.3: N_ser = 3, N_par = 6, N_Lv = 6, 4/4 smoothing give a speedup of n/80."""
     for n in (64, 640, 8192):
         assert abs(O.parallel_speedup(n, 3, 6, 6, 4, 4) - n / 80.0) <= 1e-12 * n
+
+
+# ---------------------------------------------------------------- KKT identities of the augmented system
+
+def _B_of(prob):
+    raw = O.raw_from_problem(prob)
+    N, V, Z = O.scaled_blocks(raw)
+    return O.lifted_constraint_jacobian(N, V, Z, raw.n, raw.p, raw.q).toarray()
+
+
+@pytest.mark.parametrize("make", [lambda: W.vdp(n=12, seed=61), lambda: W.burgers(nx=5, n=6, seed=62)])
+def test_kkt_identities(make):
+    """[I B^T; B 0] [x; y] = [chi; 0] is the projection onto null(B): x = chi - B^T (B B^T)^-1 B chi,
+    y = (B B^T)^-1 B chi; with right-hand side [0; chi], x = B^T (B B^T)^-1 chi is the minimum-norm solution of
+    B x = chi and y = -(B B^T)^-1 chi.  The oracle's direct solve of the assembled system against these closed
+    forms (dense normal equations)."""
+    prob = make()
+    B = _B_of(prob)
+    m, nx = B.shape
+    rng = np.random.default_rng(3)
+    G = B @ B.T
+    for which in ("primal", "dual"):
+        if which == "primal":
+            chi = rng.standard_normal(nx)
+            rhs = np.concatenate([chi, np.zeros(m)])
+            yw = np.linalg.solve(G, B @ chi)
+            xw = chi - B.T @ yw
+        else:
+            chi = rng.standard_normal(m)
+            rhs = np.concatenate([np.zeros(nx), chi])
+            yw = -np.linalg.solve(G, chi)
+            xw = B.T @ np.linalg.solve(G, chi)
+        p2 = dataclasses.replace(prob, b=rhs)
+        sol = O.direct_solve(p2)
+        assert np.linalg.norm(sol[:nx] - xw) <= 1e-10 * max(1.0, np.linalg.norm(xw))
+        assert np.linalg.norm(sol[nx:] - yw) <= 1e-10 * max(1.0, np.linalg.norm(yw))
+        if which == "primal":
+            assert np.linalg.norm(B @ sol[:nx]) <= 1e-10 * np.linalg.norm(chi)
+
+
+# ---------------------------------------------------------------- V-cycle as an operator
+
+def test_fixed_coarse_vcycle_is_linear():
+    """With a fixed number of coarse GMRES iterations the cycle is a linear map: superposition holds."""
+    prob = W.burgers(nx=6, n=16, seed=63)
+    h = O.Hierarchy(prob, O.MGOptions(levels=3, nu_pre=2, nu_post=1, coarse_fixed_iters=3))
+    rng = np.random.default_rng(4)
+    r1, r2 = rng.standard_normal((2, h.fine.size))
+    lhs = h.vcycle(0, 0.7 * r1 - 1.9 * r2)
+    rhs = 0.7 * h.vcycle(0, r1) - 1.9 * h.vcycle(0, r2)
+    assert np.linalg.norm(lhs - rhs) <= 1e-10 * np.linalg.norm(rhs)
+
+
+def test_two_level_cycle_equals_error_propagation_formula():
+    """Two levels, exact coarse solve: M = (I - E) A^-1 with E = S^nu_post (I - P A_c^-1 R A) S^nu_pre and
+    S = I - D^-1 A (block Jacobi), all dense (Alg. 1 with the smoother of Eq. jacobi-aj)."""
+    prob = W.vdp(n=8, seed=64)
+    o = O.MGOptions(levels=2, nu_pre=2, nu_post=3, coarse_rtol=1e-14, coarse_maxit=60)
+    h = O.Hierarchy(prob, o)
+    A = h.fine.At.toarray()
+    D = h.fine.D.toarray()
+    Ac = h.levels[1].At.toarray()
+    R, P = h.R[0].toarray(), h.P[0].toarray()
+    I = np.eye(A.shape[0])
+    S = I - np.linalg.solve(D, A)
+    E = np.linalg.matrix_power(S, 3) @ (I - P @ np.linalg.solve(Ac, R @ A)) @ np.linalg.matrix_power(S, 2)
+    M = (I - E) @ np.linalg.inv(A)
+    r = np.random.default_rng(6).standard_normal(A.shape[0])
+    y = h.vcycle(0, r)
+    assert np.linalg.norm(y - M @ r) <= 1e-9 * np.linalg.norm(M @ r)

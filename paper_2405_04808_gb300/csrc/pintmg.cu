@@ -1347,6 +1347,12 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     if (std::strcmp(e, "cluster") == 0) h->use_scan = 0;
     if (std::strcmp(e, "serial") == 0) h->use_scan = 0, h->use_cluster = 0;
   }
+  // dot-product blocking (4, 8 or 16 basis vectors per CTA; bitwise the same
+  // results): PINTMG_DOT_VB overrides the default (used by the tests)
+  if (const char *e = std::getenv("PINTMG_DOT_VB")) {
+    const int vb = std::atoi(e);
+    if (vb == 4 || vb == 8 || vb == 16) h->dot_vb = vb;
+  }
   int status = MG_OK;
   try {
     ck(cudaMallocHost(&h->host_scal, 4 * sizeof(double)));

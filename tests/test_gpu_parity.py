@@ -319,3 +319,48 @@ def test_batched_rejects_shared_handles(P):
         assert code == P.MG_ERR_ARG
     finally:
         P.mg_destroy(h)
+
+
+def _solve_x(P, prob, settings, restart=60, rtol=1e-10):
+    h = P.mg_setup(prob, **settings)
+    try:
+        b = _dev(prob.b)
+        x = torch.empty_like(b)
+        st, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), rtol, 1500, restart)
+        assert st == P.MG_OK, P.mg_status_string(st)
+        return x.cpu().numpy(), info
+    finally:
+        P.mg_destroy(h)
+
+
+def test_dot_blocking_is_bitwise_neutral(P, monkeypatch):
+    """4, 8 or 16 basis vectors per dot-product CTA: the same partial sums in the same order."""
+    prob = W.burgers(nx=40, n=32, seed=151)
+    settings = dict(levels=2, nu_pre=2, nu_post=2)
+    xs = []
+    for vb in ("4", "8", "16"):
+        monkeypatch.setenv("PINTMG_DOT_VB", vb)
+        xs.append(_solve_x(P, prob, settings))
+    for x, info in xs[1:]:
+        assert info.iters == xs[0][1].iters
+        assert np.array_equal(x, xs[0][0])
+
+
+@pytest.mark.parametrize("n,levels", [(7, 1), (9, 1), (1, 1)])
+def test_odd_lengths_take_the_unpaired_kernels(P, n, levels):
+    """n (4p + q) odd (van der Pol, w = 9, n odd): the dot products and axpys run their one-entry-per-step
+    variants; n = 1 is the single-block degenerate case.  Against the direct solve."""
+    prob = W.vdp(n=n, seed=152 + n)
+    assert (prob.size % 2 == 1) == (n % 2 == 1)
+    x, info = _solve_x(P, prob, dict(levels=levels, nu_pre=1, nu_post=1))
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+
+
+def test_restart_at_its_maximum(P):
+    """restart = 512 (the largest the Hessenberg workspace holds) on a case needing a few hundred iterations."""
+    prob = W.vdp(n=128, seed=153)
+    x, info = _solve_x(P, prob, dict(levels=2, nu_pre=1, nu_post=1), restart=512)
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+    assert info.iters >= 30

@@ -340,7 +340,7 @@ def measure_learned(P, torch, args, dev, stream, omega=0.7):
     wl = W.WORKLOADS[LEARNED_WORKLOAD]
     settings = dict(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega)
     res = {"workload": LEARNED_WORKLOAD, "omega": omega, "levels": wl["levels"], "admit": 0.5,
-           "inference": "bf16 storage, fp32 accumulation"}
+           "inference": "bf16 on the tensor cores (mma.sync m16n8k16), fp32 accumulation"}
     t0 = time.perf_counter()
     per = 100
     train_probs = (wl["make"](seed=wl["seed"] + 1 + k) for k in range((args.learned_pairs + per - 1) // per))

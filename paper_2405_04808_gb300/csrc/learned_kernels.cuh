@@ -128,6 +128,115 @@ __global__ void __launch_bounds__(256) k_conv_tiled(const T *__restrict__ x, con
   }
 }
 
+// BF16 inference on the tensor cores: the same convolution as an implicit
+// GEMM, out[position][o] = sum_k A[position][k] B[k][o] with k = (tap, input
+// channel), by mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  A CTA
+// of 4 warps owns 4 rows x 64 columns of positions; warp w computes row w as
+// 4 m-tiles of 16 columns x NT n-tiles of 8 output channels.  The input tile
+// with its halo is staged channel-innermost (channels padded to CB*16, rows of
+// CB*16+8 values so that the 8 row addresses of an ldmatrix fall in distinct
+// banks), the weights as [tap][channel block][o][k] rows of 24 values.  For a
+// tap (i, j) the A fragment of positions s..s+15 is the staged rows at column
+// s + j of input row w + i, so no im2col copy is made.  Dynamic shared memory:
+// conv_mma_smem(CB, NT) bytes.  Grid: (ceil(Wd / 64), ceil(H / 4), B), 128 threads.
+constexpr int kMmaRows = 4, kMmaCols = 64;
+
+__host__ __device__ constexpr int conv_mma_cs(int CB) { return CB * 16 + 8; }
+__host__ __device__ constexpr int conv_mma_smem(int CB, int NT) {
+  return (kMmaRows + kNetKT - 1) * (kMmaCols + kNetKX - 1) * conv_mma_cs(CB) * 2 +
+         kNetKT * kNetKX * CB * NT * 8 * 24 * 2;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+template <int CB, int NT>
+__global__ void __launch_bounds__(128) k_conv_mma(const __nv_bfloat16 *__restrict__ x,
+                                                  const __nv_bfloat16 *__restrict__ W,
+                                                  const __nv_bfloat16 *__restrict__ bias, __nv_bfloat16 *y, int B,
+                                                  int C, int O, int H, int Wd, int act) {
+  constexpr int K = kNetKT * kNetKX;
+  constexpr int HR = kMmaRows + kNetKT - 1, HC = kMmaCols + kNetKX - 1;
+  constexpr int CS = conv_mma_cs(CB), KS = 24, NO = NT * 8;
+  extern __shared__ __align__(16) unsigned char conv_smem[];
+  __nv_bfloat16 *sx = reinterpret_cast<__nv_bfloat16 *>(conv_smem);
+  __nv_bfloat16 *sw = sx + HR * HC * CS;
+  const int b = blockIdx.z, t0 = blockIdx.y * kMmaRows, s0 = blockIdx.x * kMmaCols;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int e = threadIdx.x; e < CB * 16 * HR * HC; e += blockDim.x) {
+    const int c = e / (HR * HC), r = (e / HC) % HR, col = e % HC;
+    const int t = t0 + r - kNetKT / 2, sp = s0 + col - kNetKX / 2;
+    __nv_bfloat16 v = zero;
+    if (c < C && t >= 0 && t < H && sp >= 0 && sp < Wd) v = x[(((long long)b * C + c) * H + t) * Wd + sp];
+    sx[(r * HC + col) * CS + c] = v;
+  }
+  for (int e = threadIdx.x; e < K * CB * NO * 16; e += blockDim.x) {
+    const int k = e % 16, n = (e / 16) % NO, cb = (e / (16 * NO)) % CB, tap = e / (16 * NO * CB);
+    const int c = cb * 16 + k;
+    __nv_bfloat16 v = zero;
+    if (n < O && c < C) v = W[((long long)n * C + c) * K + tap];
+    sw[((tap * CB + cb) * NO + n) * KS + k] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, q = lane & 3;
+  const int mi = lane >> 3, rr = lane & 7;
+  const int arow = rr + ((mi & 1) ? 8 : 0), akoff = (mi >> 1) ? 8 : 0;
+  float acc[4][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[mt][nt][u] = 0.f;
+#pragma unroll 1
+  for (int tap = 0; tap < K; ++tap) {
+    const int i = tap / kNetKX, j = tap % kNetKX;
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) {
+      unsigned bf[NT][2];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const __nv_bfloat16 *wp = sw + ((tap * CB + cb) * NO + nt * 8 + g) * KS + 2 * q;
+        bf[nt][0] = *reinterpret_cast<const unsigned *>(wp);
+        bf[nt][1] = *reinterpret_cast<const unsigned *>(wp + 8);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt) {
+        const __nv_bfloat16 *ap = sx + ((warp + i) * HC + mt * 16 + arow + j) * CS + cb * 16 + akoff;
+        unsigned a0, a1, a2, a3;
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                     : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
+                     : "r"(smem_u32(ap)));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+              "{%0, %1, %2, %3};\n"
+              : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
+              : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(bf[nt][0]), "r"(bf[nt][1]));
+        }
+      }
+    }
+  }
+  const int t = t0 + warp;
+  if (t >= H) return;
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int sp = s0 + mt * 16 + g + ((u & 2) ? 8 : 0);
+        const int o = nt * 8 + 2 * q + (u & 1);
+        if (o >= O || sp >= Wd) continue;
+        float v = acc[mt][nt][u] + (bias ? __bfloat162float(bias[o]) : 0.f);
+        if (act) v = v > 0.f ? v : kNetSlope * v;
+        y[(((long long)b * O + o) * H + t) * Wd + sp] = __float2bfloat16(v);
+      }
+}
+
 // Wt[c][o][i][j] = W[o][c][KT-1-i][KX-1-j]: the gradient with respect to a
 // layer's input is the convolution of the output gradient with these weights
 __global__ void k_flip_transpose(const float *__restrict__ W, float *Wt, int C, int O) {

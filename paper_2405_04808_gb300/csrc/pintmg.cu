@@ -670,6 +670,42 @@ void launch_conv(const T *x, const T *W, const T *bias, T *y, float *z, int B, i
   ck_launch();
 }
 
+// BF16 layers on the tensor cores (k_conv_mma): 16-channel input blocks, 8-channel output tiles
+// the kernels' dynamic shared memory limits (above the default 48 KB), once per
+// device; called outside stream capture (network creation and attachment)
+void conv_mma_prepare() {
+  static unsigned done = 0;
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  if (dev < 32 && (done >> dev) & 1u) return;
+  ck(cudaFuncSetAttribute(k_conv_mma<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(1, 4)));
+  ck(cudaFuncSetAttribute(k_conv_mma<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(2, 1)));
+  ck(cudaFuncSetAttribute(k_conv_mma<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(2, 4)));
+  if (dev < 32) done |= 1u << dev;
+}
+
+template <int CB, int NT>
+void launch_conv_mma_t(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, __nv_bfloat16 *y,
+                       int B, int C, int O, int H, int Wd, int act, cudaStream_t s) {
+  constexpr int smem = conv_mma_smem(CB, NT);
+  const dim3 grid((Wd + kMmaCols - 1) / kMmaCols, (H + kMmaRows - 1) / kMmaRows, B);
+  k_conv_mma<CB, NT><<<grid, 128, smem, s>>>(x, W, bias, y, B, C, O, H, Wd, act);
+  ck_launch();
+}
+
+template <>
+void launch_conv<__nv_bfloat16>(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
+                                __nv_bfloat16 *y, float *z, int B, int C, int O, int H, int Wd, int act,
+                                cudaStream_t s) {
+  (void)z;  // inference only: no pre-activations kept
+  if (C <= 16 && O <= 32)
+    launch_conv_mma_t<1, 4>(x, W, bias, y, B, C, O, H, Wd, act, s);
+  else if (O <= 8)
+    launch_conv_mma_t<2, 1>(x, W, bias, y, B, C, O, H, Wd, act, s);
+  else
+    launch_conv_mma_t<2, 4>(x, W, bias, y, B, C, O, H, Wd, act, s);
+}
+
 // The network's forward pass in storage type T (inference): x -> y through
 // ping-pong buffers (x == y allowed).  h (may be NULL) counts and times the launches.
 template <typename T>
@@ -2100,6 +2136,7 @@ int mg_net_create(const float *init_params, mg_net **out) {
     ck(cudaMemset(net->grad, 0, kNetParams * sizeof(float)));
     ck(cudaMemset(net->m, 0, kNetParams * sizeof(float)));
     ck(cudaMemset(net->v, 0, kNetParams * sizeof(float)));
+    conv_mma_prepare();
   });
   if (st != MG_OK) {
     mg_net_destroy(net);
@@ -2289,6 +2326,7 @@ int mg_attach_coarse_net(mg_handle *h, mg_net *net, double admit, int bf16) {
   if (!(admit > 0.0 && admit < 1.0) || (bf16 != 0 && bf16 != 1)) return MG_ERR_ARG;
   if (h->q != h->p) return MG_ERR_UNSUPPORTED;
   return net_guard([&] {
+    conv_mma_prepare();
     const Level &cl = h->lv.back();
     if (!h->net_e) {
       const long long TX = (long long)cl.n * h->p;

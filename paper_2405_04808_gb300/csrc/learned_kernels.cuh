@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(256) k_conv_tiled(const T *__restrict__ x, con
 // CB*16+8 values so that the 8 row addresses of an ldmatrix fall in distinct
 // banks), the weights as [tap][channel block][o][k] rows of 24 values.  For a
 // tap (i, j) the A fragment of positions s..s+15 is the staged rows at column
-// s + j of input row w + i, so no im2col copy is made.  Dynamic shared memory:
+// s + j of input row w + i, so no im2col copy is made.  The weights come as the
+// layer's image (k_conv_mma_image, 16-byte aligned).  Dynamic shared memory:
 // conv_mma_smem(CB, NT) bytes.  Grid: (ceil(Wd / 64), ceil(H / 4), B), 128 threads.
 constexpr int kMmaRows = 4, kMmaCols = 64;
 
@@ -151,9 +152,31 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
+// The weights of one layer in k_conv_mma's shared-memory order, [tap][channel
+// block][o][k] with rows of 24 values (zero padding), written once per
+// parameter change so that the kernel stages them with 16-byte copies.
+__host__ __device__ constexpr int conv_mma_wimg(int CB, int NT) { return kNetKT * kNetKX * CB * NT * 8 * 24; }
+// (CB, NT) of layer l: input channels in blocks of 16, output channels in tiles of 8
+__host__ __device__ constexpr int conv_mma_cb(int l) { return net_ch(l) <= 16 ? 1 : 2; }
+__host__ __device__ constexpr int conv_mma_nt(int l) { return net_ch(l + 1) <= 8 ? 1 : 4; }
+__host__ __device__ constexpr long long conv_mma_wimg_offset(int l) {
+  return l == 0 ? 0 : conv_mma_wimg_offset(l - 1) + conv_mma_wimg(conv_mma_cb(l - 1), conv_mma_nt(l - 1));
+}
+constexpr long long kConvMmaWimg = conv_mma_wimg_offset(kNetLayers);
+
+template <int CB, int NT>
+__global__ void k_conv_mma_image(const __nv_bfloat16 *__restrict__ W, int C, int O, __nv_bfloat16 *img) {
+  constexpr int K = kNetKT * kNetKX, NO = NT * 8, KS = 24;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * CB * NO * KS; e += gridDim.x * blockDim.x) {
+    const int k = e % KS, n = (e / KS) % NO, cb = (e / (KS * NO)) % CB, tap = e / (KS * NO * CB);
+    const int c = cb * 16 + k;
+    img[e] = (k < 16 && n < O && c < C) ? W[((long long)n * C + c) * K + tap] : __float2bfloat16(0.f);
+  }
+}
+
 template <int CB, int NT>
 __global__ void __launch_bounds__(128) k_conv_mma(const __nv_bfloat16 *__restrict__ x,
-                                                  const __nv_bfloat16 *__restrict__ W,
+                                                  const __nv_bfloat16 *__restrict__ wimg,
                                                   const __nv_bfloat16 *__restrict__ bias, __nv_bfloat16 *y, int B,
                                                   int C, int O, int H, int Wd, int act) {
   constexpr int K = kNetKT * kNetKX;
@@ -163,20 +186,25 @@ __global__ void __launch_bounds__(128) k_conv_mma(const __nv_bfloat16 *__restric
   __nv_bfloat16 *sx = reinterpret_cast<__nv_bfloat16 *>(conv_smem);
   __nv_bfloat16 *sw = sx + HR * HC * CS;
   const int b = blockIdx.z, t0 = blockIdx.y * kMmaRows, s0 = blockIdx.x * kMmaCols;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int e = threadIdx.x; e < CB * 16 * HR * HC; e += blockDim.x) {
-    const int c = e / (HR * HC), r = (e / HC) % HR, col = e % HC;
+  // input tile: a thread per (position, 8 channels): 8 loads coalesced along
+  // the columns, one 16-byte store into the channel-innermost row
+  for (int e = threadIdx.x; e < CB * 2 * HR * HC; e += blockDim.x) {
+    const int col = e % HC, r = (e / HC) % HR, grp = e / (HC * HR);
     const int t = t0 + r - kNetKT / 2, sp = s0 + col - kNetKX / 2;
-    __nv_bfloat16 v = zero;
-    if (c < C && t >= 0 && t < H && sp >= 0 && sp < Wd) v = x[(((long long)b * C + c) * H + t) * Wd + sp];
-    sx[(r * HC + col) * CS + c] = v;
+    __align__(16) __nv_bfloat16 v[8];
+    const bool in = t >= 0 && t < H && sp >= 0 && sp < Wd;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = grp * 8 + u;
+      v[u] = (in && c < C) ? x[(((long long)b * C + c) * H + t) * Wd + sp] : __float2bfloat16(0.f);
+    }
+    *reinterpret_cast<uint4 *>(sx + (r * HC + col) * CS + grp * 8) = *reinterpret_cast<const uint4 *>(v);
   }
-  for (int e = threadIdx.x; e < K * CB * NO * 16; e += blockDim.x) {
-    const int k = e % 16, n = (e / 16) % NO, cb = (e / (16 * NO)) % CB, tap = e / (16 * NO * CB);
-    const int c = cb * 16 + k;
-    __nv_bfloat16 v = zero;
-    if (n < O && c < C) v = W[((long long)n * C + c) * K + tap];
-    sw[((tap * CB + cb) * NO + n) * KS + k] = v;
+  // weights: a straight copy of the layer's image
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(wimg);
+    uint4 *dst = reinterpret_cast<uint4 *>(sw);
+    for (int e = threadIdx.x; e < K * CB * NO * KS / 8; e += blockDim.x) dst[e] = src[e];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

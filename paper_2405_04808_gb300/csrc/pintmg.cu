@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -95,6 +96,7 @@ struct Level {
 struct mg_net {
   float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *partial = nullptr, *loss = nullptr;
   __nv_bfloat16 *params_bf16 = nullptr;
+  __nv_bfloat16 *wimg = nullptr;  // per-layer weight images of the tensor-core convolutions
   bool bf16_valid = false;
   int step = 0;              // Adam's step count (bias correction)
   long long updates = 0;     // optimiser steps ever taken by this network
@@ -685,32 +687,35 @@ void conv_mma_prepare() {
 }
 
 template <int CB, int NT>
-void launch_conv_mma_t(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, __nv_bfloat16 *y,
-                       int B, int C, int O, int H, int Wd, int act, cudaStream_t s) {
+void launch_conv_mma_t(const __nv_bfloat16 *x, const __nv_bfloat16 *wimg, const __nv_bfloat16 *bias,
+                       __nv_bfloat16 *y, int B, int C, int O, int H, int Wd, int act, cudaStream_t s) {
   constexpr int smem = conv_mma_smem(CB, NT);
   const dim3 grid((Wd + kMmaCols - 1) / kMmaCols, (H + kMmaRows - 1) / kMmaRows, B);
-  k_conv_mma<CB, NT><<<grid, 128, smem, s>>>(x, W, bias, y, B, C, O, H, Wd, act);
+  k_conv_mma<CB, NT><<<grid, 128, smem, s>>>(x, wimg, bias, y, B, C, O, H, Wd, act);
   ck_launch();
 }
 
-template <>
-void launch_conv<__nv_bfloat16>(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
-                                __nv_bfloat16 *y, float *z, int B, int C, int O, int H, int Wd, int act,
-                                cudaStream_t s) {
-  (void)z;  // inference only: no pre-activations kept
-  if (C <= 16 && O <= 32)
-    launch_conv_mma_t<1, 4>(x, W, bias, y, B, C, O, H, Wd, act, s);
-  else if (O <= 8)
-    launch_conv_mma_t<2, 1>(x, W, bias, y, B, C, O, H, Wd, act, s);
+// layer l of the network in BF16 on the tensor cores (weights from the layer's image)
+void launch_conv_mma(const __nv_bfloat16 *wimg_all, int l, const __nv_bfloat16 *x, const __nv_bfloat16 *bias,
+                     __nv_bfloat16 *y, int B, int H, int Wd, int act, cudaStream_t s) {
+  const __nv_bfloat16 *wimg = wimg_all + conv_mma_wimg_offset(l);
+  const int C = net_ch(l), O = net_ch(l + 1);
+  const int cb = conv_mma_cb(l), nt = conv_mma_nt(l);
+  if (cb == 1 && nt == 4)
+    launch_conv_mma_t<1, 4>(x, wimg, bias, y, B, C, O, H, Wd, act, s);
+  else if (cb == 2 && nt == 1)
+    launch_conv_mma_t<2, 1>(x, wimg, bias, y, B, C, O, H, Wd, act, s);
   else
-    launch_conv_mma_t<2, 4>(x, W, bias, y, B, C, O, H, Wd, act, s);
+    launch_conv_mma_t<2, 4>(x, wimg, bias, y, B, C, O, H, Wd, act, s);
 }
 
 // The network's forward pass in storage type T (inference): x -> y through
 // ping-pong buffers (x == y allowed).  h (may be NULL) counts and times the launches.
 template <typename T>
-void net_forward_storage(mg_handle *h, const T *x, int B, int H, int Wd, T *y, T *bufA, T *bufB, const T *params,
+void net_forward_storage(mg_handle *h, const mg_net *net, const T *x, int B, int H, int Wd, T *y, T *bufA, T *bufB,
                          cudaStream_t s) {
+  constexpr bool kBf16 = std::is_same<T, __nv_bfloat16>::value;
+  const T *params = kBf16 ? reinterpret_cast<const T *>(net->params_bf16) : reinterpret_cast<const T *>(net->params);
   const T *in = x;
   for (int l = 0; l < kNetLayers; ++l) {
     T *out = (l == kNetLayers - 1) ? y : ((l % 2 == 0) ? bufA : bufB);
@@ -718,11 +723,18 @@ void net_forward_storage(mg_handle *h, const T *x, int B, int H, int Wd, T *y, T
     const T *bias = W + (long long)net_ch(l + 1) * net_ch(l) * kNetKT * kNetKX;
     const long long n = (long long)B * net_ch(l + 1) * H * Wd;
     const double flops = 2.0 * n * net_ch(l) * kNetKT * kNetKX;
+    const int act = l < kNetLayers - 1;
+    auto run = [&] {
+      if constexpr (kBf16)
+        launch_conv_mma(net->wimg, l, in, bias, out, B, H, Wd, act, s);
+      else
+        launch_conv<T>(in, W, bias, out, nullptr, B, net_ch(l), net_ch(l + 1), H, Wd, act, s);
+    };
     if (h) {
       Bracket br(h, CAT_NET, s, (double)sizeof(T) * (n + (double)B * net_ch(l) * H * Wd), flops);
-      launch_conv<T>(in, W, bias, out, nullptr, B, net_ch(l), net_ch(l + 1), H, Wd, l < kNetLayers - 1, s);
+      run();
     } else {
-      launch_conv<T>(in, W, bias, out, nullptr, B, net_ch(l), net_ch(l + 1), H, Wd, l < kNetLayers - 1, s);
+      run();
     }
     in = out;
   }
@@ -732,6 +744,19 @@ void net_refresh_bf16(mg_net *net, cudaStream_t s) {
   if (net->bf16_valid) return;
   k_f32_to_bf16<<<grid_for(kNetParams, 256), 256, 0, s>>>(net->params, net->params_bf16, kNetParams);
   ck_launch();
+  for (int l = 0; l < kNetLayers; ++l) {  // the tensor-core kernels' weight images
+    const __nv_bfloat16 *W = net->params_bf16 + net_layer_offset(l);
+    __nv_bfloat16 *img = net->wimg + conv_mma_wimg_offset(l);
+    const int cb = conv_mma_cb(l), nt = conv_mma_nt(l);
+    const int n = conv_mma_wimg(cb, nt);
+    if (cb == 1 && nt == 4)
+      k_conv_mma_image<1, 4><<<grid_for(n, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), img);
+    else if (cb == 2 && nt == 1)
+      k_conv_mma_image<2, 1><<<grid_for(n, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), img);
+    else
+      k_conv_mma_image<2, 4><<<grid_for(n, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), img);
+    ck_launch();
+  }
   net->bf16_valid = true;
 }
 
@@ -749,7 +774,7 @@ void net_coarse_proposal(mg_handle *h, Level &lev, const mg_handle::Krylov &K, c
       k_net_input<B16><<<grid_for(len, 256), 256, 0, s>>>(h->cr, K.scal, xin, len);
       ck_launch();
     }
-    net_forward_storage<B16>(h, xin, 1, H, Wd, xin, a, b, net->params_bf16, s);
+    net_forward_storage<B16>(h, net, xin, 1, H, Wd, xin, a, b, s);
     {
       Bracket br(h, CAT_NET, s);
       k_net_output<B16><<<grid_for(len, 256), 256, 0, s>>>(xin, K.scal, h->net_e, len);
@@ -763,7 +788,7 @@ void net_coarse_proposal(mg_handle *h, Level &lev, const mg_handle::Krylov &K, c
       k_net_input<float><<<grid_for(len, 256), 256, 0, s>>>(h->cr, K.scal, xin, len);
       ck_launch();
     }
-    net_forward_storage<float>(h, xin, 1, H, Wd, xin, a, b, net->params, s);
+    net_forward_storage<float>(h, net, xin, 1, H, Wd, xin, a, b, s);
     {
       Bracket br(h, CAT_NET, s);
       k_net_output<float><<<grid_for(len, 256), 256, 0, s>>>(xin, K.scal, h->net_e, len);
@@ -2126,6 +2151,7 @@ int mg_net_create(const float *init_params, mg_net **out) {
     net->v = net->mem.alloc<float>(kNetParams);
     net->partial = net->mem.alloc<float>(kLossPartials);
     net->params_bf16 = net->mem.alloc<__nv_bfloat16>(kNetParams);
+    net->wimg = net->mem.alloc<__nv_bfloat16>(kConvMmaWimg);
     net->wt = net->mem.alloc<float>((size_t)32 * 32 * kNetKT * kNetKX);
     net->wpart = net->mem.alloc<float>((size_t)kWgSlices * 32 * 32 * kNetKT * kNetKX);
     net->bpart = net->mem.alloc<float>((size_t)32 * kBiasParts);
@@ -2200,13 +2226,13 @@ int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *
       B16 *c = static_cast<B16 *>(net->ic);
       k_f32_to_bf16<<<grid_for(nio, 256), 256, 0, s>>>(x, c, nio);
       ck_launch();
-      net_forward_storage<B16>(nullptr, c, batch, T, X, c, static_cast<B16 *>(net->ia), static_cast<B16 *>(net->ib),
-                               net->params_bf16, s);
+      net_forward_storage<B16>(nullptr, net, c, batch, T, X, c, static_cast<B16 *>(net->ia),
+                               static_cast<B16 *>(net->ib), s);
       k_bf16_to_f32<<<grid_for(nio, 256), 256, 0, s>>>(c, y, nio);
       ck_launch();
     } else {
-      net_forward_storage<float>(nullptr, x, batch, T, X, y, static_cast<float *>(net->ia),
-                                 static_cast<float *>(net->ib), net->params, s);
+      net_forward_storage<float>(nullptr, net, x, batch, T, X, y, static_cast<float *>(net->ia),
+                                 static_cast<float *>(net->ib), s);
     }
   });
 }

@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="burgers_nx128_n1024", choices=sorted(W.WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--restart", type=int, default=400)
+    ap.add_argument("--restart", type=int, default=None,
+                    help="FGMRES restart length (default: the workload's, from a sweep of solve times)")
     ap.add_argument("--omega", type=float, default=1.0,
                     help="block-Jacobi relaxation weight; 1 is the paper's sweep (Eq. jacobi-aj)")
     ap.add_argument("--maxit", type=int, default=2000)
@@ -61,7 +62,10 @@ def parse():
     ap.add_argument("--learned-pairs", type=int, default=400,
                     help="training pairs for the learned coarse correction variant (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=3)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.restart is None:
+        args.restart = W.WORKLOADS[args.workload].get("restart", 400)
+    return args
 
 
 def dist_env():
@@ -339,12 +343,13 @@ def measure_learned(P, torch, args, dev, stream, omega=0.7):
     from paper_2405_04808_gb300 import learned as LN
     wl = W.WORKLOADS[LEARNED_WORKLOAD]
     settings = dict(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega)
-    res = {"workload": LEARNED_WORKLOAD, "omega": omega, "levels": wl["levels"], "admit": 0.5,
+    restart = wl.get("restart", 400)
+    res = {"workload": LEARNED_WORKLOAD, "restart": restart, "omega": omega, "levels": wl["levels"], "admit": 0.5,
            "inference": "bf16 on the tensor cores (mma.sync m16n8k16), fp32 accumulation"}
     t0 = time.perf_counter()
     per = 100
     train_probs = (wl["make"](seed=wl["seed"] + 1 + k) for k in range((args.learned_pairs + per - 1) // per))
-    R, Y = LN.collect_pairs(train_probs, settings, args.learned_pairs, restart=args.restart, per_problem=per)
+    R, Y = LN.collect_pairs(train_probs, settings, args.learned_pairs, restart=restart, per_problem=per)
     torch.cuda.synchronize(dev)
     res["pairs"] = int(R.shape[0])
     res["collect_s"] = round(time.perf_counter() - t0, 2)
@@ -370,9 +375,9 @@ def measure_learned(P, torch, args, dev, stream, omega=0.7):
             try:
                 if nt:
                     P.mg_attach_coarse_net(hp, nt, admit=0.5, bf16=True)
-                P.fgmres_solve(hp, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
+                P.fgmres_solve(hp, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, restart, stream)
                 P.mg_profile_enable(hp, P.PROFILE_ALL)
-                P.fgmres_solve(hp, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
+                P.fgmres_solve(hp, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, restart, stream)
                 shares = P.mg_profile_read(hp)
                 P.mg_profile_enable(hp, 0)
             finally:
@@ -381,7 +386,7 @@ def measure_learned(P, torch, args, dev, stream, omega=0.7):
             try:
                 if nt:
                     P.mg_attach_coarse_net(h, nt, admit=0.5, bf16=True)
-                code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart, stream)
+                code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, restart, stream)
                 if code != P.MG_OK:
                     raise RuntimeError(f"learned variant {name}: {P.mg_status_string(code)}")
                 torch.cuda.synchronize(dev)
@@ -389,7 +394,7 @@ def measure_learned(P, torch, args, dev, stream, omega=0.7):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 for _ in range(reps):
-                    code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, args.restart,
+                    code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), RTOL, args.maxit, restart,
                                                 stream)
                 e1.record()
                 torch.cuda.synchronize(dev)
@@ -489,7 +494,7 @@ def oracle_iterations(workload, omega, restart):
     path = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path)).get(f"{workload}/omega={float(omega)}")
+    rec = json.load(open(path)).get(f"{workload}/omega={float(omega)}/restart={restart}")
     if rec and rec.get("restart") == restart and rec.get("rtol") == RTOL:
         return rec["iters"]
     return None

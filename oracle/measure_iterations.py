@@ -1,9 +1,10 @@
 """Run the oracle's own FGMRES to convergence on the benchmark workloads and
 record its iteration counts (tests/golden/oracle_iterations.json).
 
-Calls only oracle/ and the input generator.  Slow (the C2 solve takes about
-an hour on 8 CPU cores); the CPU-reference arm of bench.py scales its bounded
-per-iteration timing by these counts.
+Calls only oracle/ and the input generator.  Slow (the Burgers nx=128 solve
+takes about 15 minutes on 8 CPU cores); the CPU-reference arm of bench.py
+scales its bounded per-iteration timing by these counts.  Keys:
+"<workload>/omega=<omega>/restart=<restart>", at each workload's restart.
 """
 import json
 import os
@@ -20,8 +21,9 @@ from paper_2405_04808_gb300 import workloads as W  # noqa: E402
 OUT = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
 
 
-def measure(name, rtol=1e-8, restart=400, maxit=2000, omega=1.0):
+def measure(name, rtol=1e-8, restart=None, maxit=2000, omega=1.0):
     wl = W.WORKLOADS[name]
+    restart = restart or wl.get("restart", 400)
     prob = wl["make"]()
     h = O.Hierarchy(prob, O.MGOptions(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega))
     t0 = time.time()
@@ -35,8 +37,9 @@ if __name__ == "__main__":
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for nm in names:
         for omega in (1.0, 0.7):
-            key = f"{nm}/omega={omega}"
-            data[key] = measure(nm, omega=omega)
+            rec = measure(nm, omega=omega)
+            key = f"{nm}/omega={omega}/restart={rec['restart']}"
+            data[key] = rec
             print(key, data[key], flush=True)
             with open(OUT, "w") as fh:
                 json.dump(data, fh, indent=1, sort_keys=True)

@@ -93,15 +93,16 @@ def test_c2_burgers_full_size_vcycle(P):
 @pytest.mark.parametrize("name,omega", [("burgers_nx128_n1024", 1.0), ("burgers_nx128_n1024", 0.7),
                                         ("vdp_n256", 1.0), ("vdp_n256", 0.7)])
 def test_bench_configuration_iterations_match_oracle(P, name, omega):
-    """At bench.py's configuration (rtol 1e-8, restart 400) the GPU solve takes the
+    """At bench.py's configuration (rtol 1e-8, the workload's restart) the GPU solve takes the
     oracle's own full-solve iteration count (tests/golden/oracle_iterations.json,
     written by oracle/measure_iterations.py) and meets the tolerance on the
     oracle's independently assembled operator."""
     import json
     import os
     from conftest import GOLDEN
-    rec = json.load(open(os.path.join(GOLDEN, "oracle_iterations.json")))[f"{name}/omega={omega}"]
     wl = W.WORKLOADS[name]
+    key = f"{name}/omega={omega}/restart={wl['restart']}"
+    rec = json.load(open(os.path.join(GOLDEN, "oracle_iterations.json")))[key]
     prob = wl["make"]()
     h = P.mg_setup(prob, levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega)
     try:

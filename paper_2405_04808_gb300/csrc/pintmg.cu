@@ -147,6 +147,7 @@ struct mg_handle {
   int use_cluster = 1;  // SGS chains on a thread-block cluster (tridiagonal layout)
   int use_scan = 1;     // SGS chains as a parallel scan with precomputed prefix products
   int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
+  int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -244,6 +245,32 @@ void harvest(mg_handle *h) {
 // ---------------------------------------------------------------------------
 // Launch helpers (templated on the V-cycle precision)
 
+// the staged block solve applies: tridiagonal, p <= 128 (4 entries per lane), 16-byte
+// aligned coefficient arrays and block strides
+template <typename T>
+bool tri_stage_ok(const LevelView<T> &L) {
+  const auto al = [](const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; };
+  return L.layout == MG_LAYOUT_TRIDIAG && L.p <= 4 * kWarp && (3 * (size_t)L.p * sizeof(T)) % 16 == 0 &&
+         al(L.N) && al(L.V) && al(L.Z) && al(L.fac) && al(L.scan);
+}
+
+// dynamic shared memory limits of the staged block solves, once per device, outside capture
+void tri_stage_prepare() {
+  static unsigned done = 0;
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  if (dev < 32 && (done >> dev) & 1u) return;
+  const int bd = 4 * tri_stage_elems<double>(4 * kWarp) * (int)sizeof(double);
+  const int bf = 4 * tri_stage_elems<float>(4 * kWarp) * (int)sizeof(float);
+  ck(cudaFuncSetAttribute(k_block_solve_tri<double, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<double, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<double, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  if (dev < 32) done |= 1u << dev;
+}
+
 template <typename T>
 void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T *cplU, const T *cplM,
                         T *out, cudaStream_t s, const T *yold = nullptr, T omega = T(1)) {
@@ -258,6 +285,16 @@ void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T
     k_block_solve_dense<T><<<grid_for(L.n + 1, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega);
   } else {
     const int blocks = (int)((L.n + 1 + 3) / 4);
+    const size_t smem = 4 * (size_t)tri_stage_elems<T>(L.p) * sizeof(T);
+    if (h->stage_tri && tri_stage_ok(L)) {  // coefficients staged in shared memory (p <= 128)
+      switch (h->C) {
+        case 1: k_block_solve_tri<T, 1, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+        case 2: k_block_solve_tri<T, 2, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+        default: k_block_solve_tri<T, 4, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      }
+      ck_launch();
+      return;
+    }
     switch (h->C) {
       case 1: k_block_solve_tri<T, 1><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
       case 2: k_block_solve_tri<T, 2><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
@@ -1408,6 +1445,8 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     if (std::strcmp(e, "cluster") == 0) h->use_scan = 0;
     if (std::strcmp(e, "serial") == 0) h->use_scan = 0, h->use_cluster = 0;
   }
+  // PINTMG_STAGE_TRI=0 turns the shared-memory staging of the block solves off (tests)
+  if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
   // dot-product blocking (4, 8 or 16 basis vectors per CTA; bitwise the same
   // results): PINTMG_DOT_VB overrides the default (used by the tests)
   if (const char *e = std::getenv("PINTMG_DOT_VB")) {
@@ -1417,6 +1456,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   int status = MG_OK;
   try {
     ck(cudaMallocHost(&h->host_scal, 4 * sizeof(double)));
+    tri_stage_prepare();
     // raw data on the device (FP64)
     double *dM = h->mem.alloc<double>(msz);
     double *dJuc = h->mem.alloc<double>((size_t)n * msz);

@@ -15,13 +15,24 @@ namespace pintmg {
 //   u = r_u - N^T lambda;  z = r_z - Z^T lambda;  mu = v + V^T lambda - r_v
 // (block 0 has no v, mu; block n has only v = -r_mu, mu = v - r_v).
 
+// The coefficients of one time block (tridiagonal layout): bands of N, V, Z,
+// the LDL^T factor of S and the chunk-scan compositions, in global or shared memory.
+template <typename T>
+struct TriBlock {
+  const T *N, *V, *Z, *fac, *scan;
+};
+
+template <typename T>
+__device__ __forceinline__ TriBlock<T> tri_block(const LevelView<T> &L, int j) {
+  return {L.N + j * L.sN, L.V + j * L.sV, L.Z + j * L.sZ, L.fac + j * L.sFac, L.scan + (long long)j * kScanPerBlock};
+}
+
 template <typename T, int C>
-__device__ __forceinline__ void local_solve_tri(const LevelView<T> &L, int j,
+__device__ __forceinline__ void local_solve_tri(const TriBlock<T> &Bk, int n, int p, int j,
                                                 const T (&ru)[C], const T (&rz)[C], const T (&rl)[C],
                                                 const T (&rv)[C], const T (&rm)[C],
                                                 T (&u)[C], T (&z)[C], T (&l)[C], T (&v)[C], T (&m)[C],
                                                 int ln) {
-  const int n = L.n, p = L.p;
   if (j == n) {
 #pragma unroll
     for (int e = 0; e < C; ++e) {
@@ -30,9 +41,7 @@ __device__ __forceinline__ void local_solve_tri(const LevelView<T> &L, int j,
     }
     return;
   }
-  const T *N = L.N + j * L.sN, *V = L.V + j * L.sV, *Z = L.Z + j * L.sZ;
-  const T *fac = L.fac + j * L.sFac;
-  const T *scan = L.scan + (long long)j * kScanPerBlock;
+  const T *N = Bk.N, *V = Bk.V, *Z = Bk.Z, *fac = Bk.fac, *scan = Bk.scan;
   T rhs[C];
   tri_mv<T, C, false>(rhs, N, ru, p, ln, T(1));
   tri_mv<T, C, true>(rhs, Z, rz, p, ln, T(1));
@@ -113,7 +122,31 @@ __device__ __forceinline__ void relax_chunk(T (&x)[C], const T *yold, int len, i
   }
 }
 
-template <typename T, int C>
+// 16-byte asynchronous copies global -> shared (cp.async, L2 only); the
+// warp's lanes split `count` elements of T (count * sizeof(T) a multiple of 16,
+// both addresses 16-byte aligned)
+template <typename T>
+__device__ __forceinline__ void stage16(T *dst, const T *src, int count, int ln) {
+  const int chunks = count * (int)sizeof(T) / 16;
+  const char *s = reinterpret_cast<const char *>(src);
+  char *d = reinterpret_cast<char *>(dst);
+  for (int c = ln; c < chunks; c += kWarp) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(d + 16 * c));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(s + 16 * c) : "memory");
+  }
+}
+
+// shared memory of a staged block solve: per warp 12 p + kScanPerBlock values
+template <typename T>
+__host__ __device__ constexpr int tri_stage_elems(int p) { return 12 * p + kScanPerBlock; }
+
+// kStage: each warp first copies its block's coefficients (bands of N, V, Z,
+// factor, scan compositions: 12 p + 1280 values) into shared memory with
+// cp.async, overlapping that one round trip with the loads of the right-hand
+// side; the solve then reads them from shared memory.  Dynamic shared memory:
+// 4 * tri_stage_elems(p) values of T.  Requires 3 p * sizeof(T) to be a multiple
+// of 16 and 16-byte aligned coefficient arrays (checked on the host).
+template <typename T, int C, bool kStage = false>
 __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T *__restrict__ r,
                                                          const T *cplU, const T *cplM, T *out,
                                                          const T *yold, T omega) {
@@ -121,6 +154,19 @@ __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int n = L.n, p = L.p, q = L.q;
   if (j > n) return;
+  TriBlock<T> Bk{};
+  if (j < n) Bk = tri_block(L, j);
+  if (kStage && j < n) {
+    extern __shared__ __align__(16) unsigned char tri_smem[];
+    T *base = reinterpret_cast<T *>(tri_smem) + (threadIdx.x / kWarp) * tri_stage_elems<T>(p);
+    stage16(base, Bk.N, 3 * p, ln);
+    stage16(base + 3 * p, Bk.V, 3 * p, ln);
+    stage16(base + 6 * p, Bk.Z, 3 * p, ln);
+    stage16(base + 9 * p, Bk.fac, 3 * p, ln);
+    stage16(base + 12 * p, Bk.scan, kScanPerBlock, ln);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    Bk = {base, base + 3 * p, base + 6 * p, base + 9 * p, base + 12 * p};
+  }
   Vec<const T> R = make_cvec(r, n, p, q);
   Vec<T> Y = make_vec(out, n, p, q);
   T ru[C], rz[C], rl[C], rv[C], rm[C];
@@ -148,7 +194,11 @@ __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T
       for (int e = 0; e < C; ++e) rm[e] -= c[e];
     }
   }
-  local_solve_tri<T, C>(L, j, ru, rz, rl, rv, rm, u, z, l, v, m, ln);
+  if (kStage && j < n) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+  }
+  local_solve_tri<T, C>(Bk, n, p, j, ru, rz, rl, rv, rm, u, z, l, v, m, ln);
   if (omega != T(1)) {
     Vec<const T> Yo = make_cvec(yold ? yold : r, n, p, q);
     if (j < n) {

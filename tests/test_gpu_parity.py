@@ -364,3 +364,17 @@ def test_restart_at_its_maximum(P):
     xd = O.direct_solve(prob)
     assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
     assert info.iters >= 30
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_staged_block_solves_are_bitwise_the_same(P, monkeypatch, precision):
+    """Block solves reading their coefficients from shared memory (staged by cp.async) or from global
+    memory: the same values in the same arithmetic, so the same solution bit for bit."""
+    prob = W.burgers(nx=128, n=64, seed=161)
+    settings = dict(levels=3, nu_pre=2, nu_post=2, precision=precision)
+    xs = []
+    for stage in ("1", "0"):
+        monkeypatch.setenv("PINTMG_STAGE_TRI", stage)
+        xs.append(_solve_x(P, prob, settings))
+    assert xs[0][1].iters == xs[1][1].iters
+    assert np.array_equal(xs[0][0], xs[1][0])

@@ -265,6 +265,10 @@ void tri_stage_prepare() {
   ck(cudaFuncSetAttribute(k_block_solve_tri<double, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd));
   ck(cudaFuncSetAttribute(k_block_solve_tri<double, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd));
   ck(cudaFuncSetAttribute(k_block_solve_tri<double, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<double, 4, true, 4 * kWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          bd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 4, true, 4 * kWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          bf));
   ck(cudaFuncSetAttribute(k_block_solve_tri<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
   ck(cudaFuncSetAttribute(k_block_solve_tri<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
   ck(cudaFuncSetAttribute(k_block_solve_tri<float, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
@@ -287,6 +291,11 @@ void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T
     const int blocks = (int)((L.n + 1 + 3) / 4);
     const size_t smem = 4 * (size_t)tri_stage_elems<T>(L.p) * sizeof(T);
     if (h->stage_tri && tri_stage_ok(L)) {  // coefficients staged in shared memory (p <= 128)
+      if (L.p == 4 * kWarp && L.q == L.p) {  // full chunks: p known at compile time
+        k_block_solve_tri<T, 4, true, 4 * kWarp><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega);
+        ck_launch();
+        return;
+      }
       switch (h->C) {
         case 1: k_block_solve_tri<T, 1, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
         case 2: k_block_solve_tri<T, 2, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;

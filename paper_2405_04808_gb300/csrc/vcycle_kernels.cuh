@@ -146,13 +146,15 @@ __host__ __device__ constexpr int tri_stage_elems(int p) { return 12 * p + kScan
 // side; the solve then reads them from shared memory.  Dynamic shared memory:
 // 4 * tri_stage_elems(p) values of T.  Requires 3 p * sizeof(T) to be a multiple
 // of 16 and 16-byte aligned coefficient arrays (checked on the host).
-template <typename T, int C, bool kStage = false>
+// PF > 0: p == PF == 32 C is known at compile time (every lane's chunk is full,
+// so the bounds tests fold away).
+template <typename T, int C, bool kStage = false, int PF = 0>
 __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T *__restrict__ r,
                                                          const T *cplU, const T *cplM, T *out,
                                                          const T *yold, T omega) {
   const int ln = threadIdx.x & (kWarp - 1);
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
-  const int n = L.n, p = L.p, q = L.q;
+  const int n = L.n, p = PF ? PF : L.p, q = PF ? PF : L.q;
   if (j > n) return;
   TriBlock<T> Bk{};
   if (j < n) Bk = tri_block(L, j);

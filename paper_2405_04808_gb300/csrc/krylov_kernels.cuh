@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *
 #pragma unroll
         for (int v = 0; v < VB; ++v)
           if (v < nv) {
-            const double2 x = reinterpret_cast<const double2 *>(V + (long long)(vb + v) * ldv)[idx];
+            // basis vectors are streamed once: load them evict-first so that w stays in L2
+            const double2 x = __ldcs(reinterpret_cast<const double2 *>(V + (long long)(vb + v) * ldv) + idx);
             acc[v] = fma(x.x, wv.x, acc[v]);
             acc[v] = fma(x.y, wv.y, acc[v]);
           }

@@ -148,6 +148,7 @@ struct mg_handle {
   int use_scan = 1;     // SGS chains as a parallel scan with precomputed prefix products
   int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
   int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
+  int pair_tri = 1;     // levels with few blocks: two warps per block
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -254,6 +255,9 @@ bool tri_stage_ok(const LevelView<T> &L) {
          al(L.N) && al(L.V) && al(L.Z) && al(L.fac) && al(L.scan);
 }
 
+// levels with at most this many blocks take the two-warps-per-block solve
+constexpr int kPairMaxBlocks = 4096;
+
 // dynamic shared memory limits of the staged block solves, once per device, outside capture
 void tri_stage_prepare() {
   static unsigned done = 0;
@@ -272,6 +276,16 @@ void tri_stage_prepare() {
   ck(cudaFuncSetAttribute(k_block_solve_tri<float, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
   ck(cudaFuncSetAttribute(k_block_solve_tri<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
   ck(cudaFuncSetAttribute(k_block_solve_tri<float, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  const int pd = 2 * tri_pair_elems<double>(4 * kWarp) * (int)sizeof(double);
+  const int pf = 2 * tri_pair_elems<float>(4 * kWarp) * (int)sizeof(float);
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<double, 4, 4 * kWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize, pd));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 4, 4 * kWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
   if (dev < 32) done |= 1u << dev;
 }
 
@@ -290,6 +304,21 @@ void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T
   } else {
     const int blocks = (int)((L.n + 1 + 3) / 4);
     const size_t smem = 4 * (size_t)tri_stage_elems<T>(L.p) * sizeof(T);
+    if (h->pair_tri && tri_stage_ok(L) && L.n + 1 <= kPairMaxBlocks) {  // two warps per block
+      const int pblocks = (int)((L.n + 1 + 1) / 2);
+      const size_t psmem = 2 * (size_t)tri_pair_elems<T>(L.p) * sizeof(T);
+      if (L.p == 4 * kWarp && L.q == L.p) {
+        k_block_solve_tri2<T, 4, 4 * kWarp><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega);
+      } else {
+        switch (h->C) {
+          case 1: k_block_solve_tri2<T, 1><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+          case 2: k_block_solve_tri2<T, 2><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+          default: k_block_solve_tri2<T, 4><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+        }
+      }
+      ck_launch();
+      return;
+    }
     if (h->stage_tri && tri_stage_ok(L)) {  // coefficients staged in shared memory (p <= 128)
       if (L.p == 4 * kWarp && L.q == L.p) {  // full chunks: p known at compile time
         k_block_solve_tri<T, 4, true, 4 * kWarp><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega);
@@ -1456,6 +1485,8 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   }
   // PINTMG_STAGE_TRI=0 turns the shared-memory staging of the block solves off (tests)
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
+  // PINTMG_TRI_PAIR=0 keeps one warp per block on every level (tests)
+  if (const char *e = std::getenv("PINTMG_TRI_PAIR")) h->pair_tri = std::atoi(e) != 0;
   // dot-product blocking (4, 8 or 16 basis vectors per CTA; bitwise the same
   // results): PINTMG_DOT_VB overrides the default (used by the tests)
   if (const char *e = std::getenv("PINTMG_DOT_VB")) {

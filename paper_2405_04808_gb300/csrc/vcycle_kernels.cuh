@@ -224,6 +224,149 @@ __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T
   }
 }
 
+// Two warps per time block (the same arithmetic split in two, for levels
+// whose blocks do not fill the GPU): warp 0 forms N r_u, warp 1 Z r_z + V v -
+// r_lambda; their sum goes through shared memory to warp 0, which solves the
+// pentadiagonal system and returns lambda; then warp 0 forms u = r_u - N^T
+// lambda and warp 1 z = r_z - Z^T lambda and mu = v + V^T lambda - r_v.  Each
+// warp stages the coefficients it reads (cp.async) next to its loads.  A CTA
+// of 128 threads holds two blocks; per block tri_pair_elems(p) values of
+// dynamic shared memory.  Named barriers (id 1 + pair) join a block's warps.
+template <typename T>
+__host__ __device__ constexpr int tri_pair_elems(int p) { return 12 * p + kScanPerBlock + 2 * p; }
+
+__device__ __forceinline__ void pair_barrier(int id) { asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory"); }
+
+template <typename T, int C, int PF = 0>
+__global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const T *__restrict__ r,
+                                                          const T *cplU, const T *cplM, T *out,
+                                                          const T *yold, T omega) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int w = threadIdx.x / kWarp, pair = w >> 1, role = w & 1;
+  const int j = blockIdx.x * 2 + pair;
+  const int n = L.n, p = PF ? PF : L.p, q = PF ? PF : L.q;
+  if (j > n) return;
+  extern __shared__ __align__(16) unsigned char tri2_smem[];
+  T *base = reinterpret_cast<T *>(tri2_smem) + pair * tri_pair_elems<T>(p);
+  T *xch = base + 12 * p + kScanPerBlock;  // rhs part from warp 1, then lambda from warp 0
+  Vec<const T> R = make_cvec(r, n, p, q);
+  Vec<T> Y = make_vec(out, n, p, q);
+  Vec<const T> Yo = make_cvec(yold ? yold : r, n, p, q);
+  if (j == n) {  // last block: v = -r_mu, mu = v - r_v (warp 1 alone, no barrier)
+    if (role == 1) {
+      T rv[C], rm[C], v[C], m[C];
+      chunk_load<T, C>(rv, R.v + (long long)(j - 1) * p, p, ln);
+      chunk_load<T, C>(rm, R.m + (long long)(j - 1) * p, p, ln);
+      if (cplU) {
+        T c[C];
+        chunk_load<T, C>(c, cplU + (long long)(j - 1) * p, p, ln);
+#pragma unroll
+        for (int e = 0; e < C; ++e) rm[e] -= c[e];
+      }
+#pragma unroll
+      for (int e = 0; e < C; ++e) {
+        v[e] = -rm[e];
+        m[e] = v[e] - rv[e];
+      }
+      if (omega != T(1)) {
+        relax_chunk<T, C>(v, yold ? Yo.v + (long long)(j - 1) * p : nullptr, p, ln, omega);
+        relax_chunk<T, C>(m, yold ? Yo.m + (long long)(j - 1) * p : nullptr, p, ln, omega);
+      }
+      chunk_store<T, C>(Y.v + (long long)(j - 1) * p, v, p, ln);
+      chunk_store<T, C>(Y.m + (long long)(j - 1) * p, m, p, ln);
+    }
+    return;
+  }
+  const TriBlock<T> G = tri_block(L, j);
+  if (role == 0) {
+    stage16(base, G.N, 3 * p, ln);
+    stage16(base + 9 * p, G.fac, 3 * p, ln);
+    stage16(base + 12 * p, G.scan, kScanPerBlock, ln);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    T ru[C], rl[C], rhs[C], l[C];
+    chunk_load<T, C>(ru, R.u + (long long)j * p, p, ln);
+    chunk_load<T, C>(rl, R.l + (long long)j * p, p, ln);
+    if (cplM) {
+      T c[C];
+      chunk_load<T, C>(c, cplM + (long long)j * p, p, ln);
+#pragma unroll
+      for (int e = 0; e < C; ++e) ru[e] -= c[e];
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    const T *N = base, *fac = base + 9 * p, *scan = base + 12 * p;
+    tri_mv<T, C, false>(rhs, N, ru, p, ln, T(1));
+    pair_barrier(1 + pair);  // warp 1's part is in xch
+    T part[C];
+    chunk_load<T, C>(part, xch, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) rhs[e] += part[e];
+    penta_solve<T, C>(l, rhs, fac, scan, p, ln);
+    pair_barrier(1 + pair);  // warp 1 has read xch: reuse it for lambda
+    chunk_store<T, C>(xch, l, p, ln);
+    pair_barrier(1 + pair);
+    T u[C];
+#pragma unroll
+    for (int e = 0; e < C; ++e) u[e] = ru[e];
+    tri_mtv<T, C, true>(u, N, l, p, ln, T(-1));
+    if (omega != T(1)) {
+      relax_chunk<T, C>(u, yold ? Yo.u + (long long)j * p : nullptr, p, ln, omega);
+      relax_chunk<T, C>(l, yold ? Yo.l + (long long)j * p : nullptr, p, ln, omega);
+    }
+    chunk_store<T, C>(Y.u + (long long)j * p, u, p, ln);
+    chunk_store<T, C>(Y.l + (long long)j * p, l, p, ln);
+  } else {
+    stage16(base + 3 * p, G.V, 3 * p, ln);
+    stage16(base + 6 * p, G.Z, 3 * p, ln);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    T rz[C], rl[C], rv[C], rm[C], v[C], part[C];
+    chunk_load<T, C>(rz, R.z + (long long)j * q, q, ln);
+    chunk_load<T, C>(rl, R.l + (long long)j * p, p, ln);
+    if (j >= 1) {
+      chunk_load<T, C>(rv, R.v + (long long)(j - 1) * p, p, ln);
+      chunk_load<T, C>(rm, R.m + (long long)(j - 1) * p, p, ln);
+      if (cplU) {
+        T c[C];
+        chunk_load<T, C>(c, cplU + (long long)(j - 1) * p, p, ln);
+#pragma unroll
+        for (int e = 0; e < C; ++e) rm[e] -= c[e];
+      }
+#pragma unroll
+      for (int e = 0; e < C; ++e) v[e] = -rm[e];
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    const T *V = base + 3 * p, *Z = base + 6 * p;
+    tri_mv<T, C, false>(part, Z, rz, p, ln, T(1));
+#pragma unroll
+    for (int e = 0; e < C; ++e) part[e] -= rl[e];
+    if (j >= 1) tri_mv<T, C, true>(part, V, v, p, ln, T(1));
+    chunk_store<T, C>(xch, part, p, ln);
+    pair_barrier(1 + pair);
+    pair_barrier(1 + pair);  // warp 0 has read the part
+    pair_barrier(1 + pair);  // lambda is in xch
+    T l[C], z[C];
+    chunk_load<T, C>(l, xch, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) z[e] = rz[e];
+    tri_mtv<T, C, true>(z, Z, l, p, ln, T(-1));
+    if (omega != T(1)) relax_chunk<T, C>(z, yold ? Yo.z + (long long)j * q : nullptr, q, ln, omega);
+    chunk_store<T, C>(Y.z + (long long)j * q, z, q, ln);
+    if (j >= 1) {
+      T m[C];
+#pragma unroll
+      for (int e = 0; e < C; ++e) m[e] = v[e] - rv[e];
+      tri_mtv<T, C, true>(m, V, l, p, ln, T(1));
+      if (omega != T(1)) {
+        relax_chunk<T, C>(v, yold ? Yo.v + (long long)(j - 1) * p : nullptr, p, ln, omega);
+        relax_chunk<T, C>(m, yold ? Yo.m + (long long)(j - 1) * p : nullptr, p, ln, omega);
+      }
+      chunk_store<T, C>(Y.v + (long long)(j - 1) * p, v, p, ln);
+      chunk_store<T, C>(Y.m + (long long)(j - 1) * p, m, p, ln);
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const T *__restrict__ r,
                                                            const T *cplU, const T *cplM, T *out,

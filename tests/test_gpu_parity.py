@@ -372,9 +372,25 @@ def test_staged_block_solves_are_bitwise_the_same(P, monkeypatch, precision):
     memory: the same values in the same arithmetic, so the same solution bit for bit."""
     prob = W.burgers(nx=128, n=64, seed=161)
     settings = dict(levels=3, nu_pre=2, nu_post=2, precision=precision)
+    monkeypatch.setenv("PINTMG_TRI_PAIR", "0")      # one warp per block on every level
     xs = []
     for stage in ("1", "0"):
         monkeypatch.setenv("PINTMG_STAGE_TRI", stage)
         xs.append(_solve_x(P, prob, settings))
     assert xs[0][1].iters == xs[1][1].iters
     assert np.array_equal(xs[0][0], xs[1][0])
+
+
+@pytest.mark.parametrize("nx,n,omega", [(128, 64, 1.0), (40, 32, 1.0), (64, 16, 0.7)])
+def test_two_warp_block_solves_match(P, monkeypatch, nx, n, omega):
+    """Two warps per time block (N r_u and Z r_z + V v - r_lambda formed in parallel, summed through shared
+    memory) against one warp per block: the same solution up to the rounding of that sum's order."""
+    prob = W.burgers(nx=nx, n=n, seed=162)
+    settings = dict(levels=3 if n >= 32 else 2, nu_pre=2, nu_post=2, omega=omega)
+    xs = []
+    for pair in ("1", "0"):
+        monkeypatch.setenv("PINTMG_TRI_PAIR", pair)
+        xs.append(_solve_x(P, prob, settings))
+    assert np.linalg.norm(xs[0][0] - xs[1][0]) <= 1e-11 * np.linalg.norm(xs[1][0])
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(xs[0][0] - xd) <= SOLVE_RTOL * np.linalg.norm(xd)

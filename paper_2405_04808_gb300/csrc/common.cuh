@@ -43,6 +43,7 @@ struct LevelView {
   const T *fac;
   long long sFac;
   const T *scan;
+  T kappa;  // != 0: V_k = kappa Z_k for every step (theta = 1, d_z f a multiple of M), else 0
 };
 
 template <typename T>

@@ -1517,6 +1517,24 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     const int L = O->levels;
     h->lv.resize(L);
     std::vector<int *> idx_dev;
+    // theta = 1 and a constant d_z f = c M (tridiagonal layout): on every level
+    // V = -M / dt and Z = -c M / gamma, so V = kappa Z with kappa = gamma / (c dt)
+    double prop_c = 0.0;
+    if (layout == MG_LAYOUT_TRIDIAG && P->theta == 1.0 && P->jz_const) {
+      int i0 = -1;
+      for (int i = 0; i < msz; ++i)
+        if (P->M[i] != 0.0) {
+          i0 = i;
+          break;
+        }
+      if (i0 >= 0) {
+        const double c = P->Jz_cur[i0] / P->M[i0];
+        bool ok = c != 0.0 && std::isfinite(c);
+        for (int i = 0; ok && i < msz; ++i)
+          ok = std::fabs(P->Jz_cur[i] - c * P->M[i]) <= 1e-15 * std::fabs(c * P->M[i]);
+        if (ok) prop_c = c;
+      }
+    }
     double dt = 1.0 / n;
     int nl = n;
     for (int l = 0; l < L; ++l) {
@@ -1548,6 +1566,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
       v.sN = msz;
       v.sV = msz;
       v.sZ = zsz;
+      v.kappa = prop_c != 0.0 ? P->gamma / (prop_c * dt) : 0.0;
       if (layout == MG_LAYOUT_TRIDIAG) {
         double *fac = h->mem.alloc<double>((size_t)nl * 3 * p);
         double *scan = h->mem.alloc<double>((size_t)nl * kScanPerBlock);
@@ -1618,6 +1637,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
         f.sN = v.sN;
         f.sV = v.sV;
         f.sZ = v.sZ;
+        f.kappa = (float)v.kappa;
         f.fac = to_float_copy(h, v.fac, (long long)nl * v.sFac, s);
         f.sFac = v.sFac;
         f.scan = layout == MG_LAYOUT_TRIDIAG ? to_float_copy(h, v.scan, (long long)nl * kScanPerBlock, s)

@@ -27,12 +27,14 @@ __device__ __forceinline__ TriBlock<T> tri_block(const LevelView<T> &L, int j) {
   return {L.N + j * L.sN, L.V + j * L.sV, L.Z + j * L.sZ, L.fac + j * L.sFac, L.scan + (long long)j * kScanPerBlock};
 }
 
+// kappa != 0: V = kappa Z, so Z r_z + V v = Z (r_z + kappa v) and
+// Z^T lambda, V^T lambda come from one product (the same values up to rounding).
 template <typename T, int C>
 __device__ __forceinline__ void local_solve_tri(const TriBlock<T> &Bk, int n, int p, int j,
                                                 const T (&ru)[C], const T (&rz)[C], const T (&rl)[C],
                                                 const T (&rv)[C], const T (&rm)[C],
                                                 T (&u)[C], T (&z)[C], T (&l)[C], T (&v)[C], T (&m)[C],
-                                                int ln) {
+                                                int ln, T kappa = T(0)) {
   if (j == n) {
 #pragma unroll
     for (int e = 0; e < C; ++e) {
@@ -44,26 +46,45 @@ __device__ __forceinline__ void local_solve_tri(const TriBlock<T> &Bk, int n, in
   const T *N = Bk.N, *V = Bk.V, *Z = Bk.Z, *fac = Bk.fac, *scan = Bk.scan;
   T rhs[C];
   tri_mv<T, C, false>(rhs, N, ru, p, ln, T(1));
-  tri_mv<T, C, true>(rhs, Z, rz, p, ln, T(1));
-#pragma unroll
-  for (int e = 0; e < C; ++e) rhs[e] -= rl[e];
   if (j >= 1) {
 #pragma unroll
     for (int e = 0; e < C; ++e) v[e] = -rm[e];
-    tri_mv<T, C, true>(rhs, V, v, p, ln, T(1));
+  }
+  if (kappa != T(0) && j >= 1) {
+    T w[C];
+#pragma unroll
+    for (int e = 0; e < C; ++e) w[e] = fma(kappa, v[e], rz[e]);
+    tri_mv<T, C, true>(rhs, Z, w, p, ln, T(1));
+#pragma unroll
+    for (int e = 0; e < C; ++e) rhs[e] -= rl[e];
+  } else {
+    tri_mv<T, C, true>(rhs, Z, rz, p, ln, T(1));
+#pragma unroll
+    for (int e = 0; e < C; ++e) rhs[e] -= rl[e];
+    if (j >= 1) tri_mv<T, C, true>(rhs, V, v, p, ln, T(1));
   }
   penta_solve<T, C>(l, rhs, fac, scan, p, ln);
 #pragma unroll
-  for (int e = 0; e < C; ++e) {
-    u[e] = ru[e];
-    z[e] = rz[e];
-  }
+  for (int e = 0; e < C; ++e) u[e] = ru[e];
   tri_mtv<T, C, true>(u, N, l, p, ln, T(-1));
-  tri_mtv<T, C, true>(z, Z, l, p, ln, T(-1));
-  if (j >= 1) {
+  if (kappa != T(0)) {
+    T t[C];
+    tri_mtv<T, C, false>(t, Z, l, p, ln, T(1));
 #pragma unroll
-    for (int e = 0; e < C; ++e) m[e] = v[e] - rv[e];
-    tri_mtv<T, C, true>(m, V, l, p, ln, T(1));
+    for (int e = 0; e < C; ++e) z[e] = rz[e] - t[e];
+    if (j >= 1) {
+#pragma unroll
+      for (int e = 0; e < C; ++e) m[e] = fma(kappa, t[e], v[e] - rv[e]);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < C; ++e) z[e] = rz[e];
+    tri_mtv<T, C, true>(z, Z, l, p, ln, T(-1));
+    if (j >= 1) {
+#pragma unroll
+      for (int e = 0; e < C; ++e) m[e] = v[e] - rv[e];
+      tri_mtv<T, C, true>(m, V, l, p, ln, T(1));
+    }
   }
 }
 
@@ -200,7 +221,7 @@ __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
   }
-  local_solve_tri<T, C>(Bk, n, p, j, ru, rz, rl, rv, rm, u, z, l, v, m, ln);
+  local_solve_tri<T, C>(Bk, n, p, j, ru, rz, rl, rv, rm, u, z, l, v, m, ln, L.kappa);
   if (omega != T(1)) {
     Vec<const T> Yo = make_cvec(yold ? yold : r, n, p, q);
     if (j < n) {
@@ -337,26 +358,47 @@ __global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const 
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
     const T *V = base + 3 * p, *Z = base + 6 * p;
-    tri_mv<T, C, false>(part, Z, rz, p, ln, T(1));
+    const T kappa = L.kappa;
+    if (kappa != T(0) && j >= 1) {  // V = kappa Z: one product
+      T wz[C];
 #pragma unroll
-    for (int e = 0; e < C; ++e) part[e] -= rl[e];
-    if (j >= 1) tri_mv<T, C, true>(part, V, v, p, ln, T(1));
+      for (int e = 0; e < C; ++e) wz[e] = fma(kappa, v[e], rz[e]);
+      tri_mv<T, C, false>(part, Z, wz, p, ln, T(1));
+#pragma unroll
+      for (int e = 0; e < C; ++e) part[e] -= rl[e];
+    } else {
+      tri_mv<T, C, false>(part, Z, rz, p, ln, T(1));
+#pragma unroll
+      for (int e = 0; e < C; ++e) part[e] -= rl[e];
+      if (j >= 1) tri_mv<T, C, true>(part, V, v, p, ln, T(1));
+    }
     chunk_store<T, C>(xch, part, p, ln);
     pair_barrier(1 + pair);
     pair_barrier(1 + pair);  // warp 0 has read the part
     pair_barrier(1 + pair);  // lambda is in xch
-    T l[C], z[C];
+    T l[C], z[C], t[C];
     chunk_load<T, C>(l, xch, p, ln);
+    if (kappa != T(0)) {
+      tri_mtv<T, C, false>(t, Z, l, p, ln, T(1));
 #pragma unroll
-    for (int e = 0; e < C; ++e) z[e] = rz[e];
-    tri_mtv<T, C, true>(z, Z, l, p, ln, T(-1));
+      for (int e = 0; e < C; ++e) z[e] = rz[e] - t[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < C; ++e) z[e] = rz[e];
+      tri_mtv<T, C, true>(z, Z, l, p, ln, T(-1));
+    }
     if (omega != T(1)) relax_chunk<T, C>(z, yold ? Yo.z + (long long)j * q : nullptr, q, ln, omega);
     chunk_store<T, C>(Y.z + (long long)j * q, z, q, ln);
     if (j >= 1) {
       T m[C];
+      if (kappa != T(0)) {
 #pragma unroll
-      for (int e = 0; e < C; ++e) m[e] = v[e] - rv[e];
-      tri_mtv<T, C, true>(m, V, l, p, ln, T(1));
+        for (int e = 0; e < C; ++e) m[e] = fma(kappa, t[e], v[e] - rv[e]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < C; ++e) m[e] = v[e] - rv[e];
+        tri_mtv<T, C, true>(m, V, l, p, ln, T(1));
+      }
       if (omega != T(1)) {
         relax_chunk<T, C>(v, yold ? Yo.v + (long long)(j - 1) * p : nullptr, p, ln, omega);
         relax_chunk<T, C>(m, yold ? Yo.m + (long long)(j - 1) * p : nullptr, p, ln, omega);

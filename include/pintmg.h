@@ -252,7 +252,7 @@ int mg_true_residual_noalloc(mg_handle *h, const double *b, const double *x, dou
  * the normalised network's initial parameters.  Losses are then those of the
  * normalised targets.  Workspaces grow on demand
  * (about 8 x batch x 32 x T x X floats for training).  Errors: MG_ERR_ARG for
- * bad sizes or NULL pointers, MG_ERR_OOM, MG_ERR_CUDA.
+ * bad sizes (batch 1..32767, T 1..262140) or NULL pointers, MG_ERR_OOM, MG_ERR_CUDA.
  */
 typedef struct mg_net mg_net;  /* opaque; owns its device buffers */
 long long mg_net_param_count(void);
@@ -276,8 +276,8 @@ void mg_net_destroy(mg_net *net);
  * and it is admitted when ||r - A_c e|| <= admit ||r|| (FP64 residual on the
  * coarse level); otherwise the coarse GMRES with SGS runs as without the
  * network, so it both measures the proposal and is the fallback.  FGMRES accepts the
- * resulting variable preconditioner.  Needs the tridiagonal layout or
- * q == p (MG_ERR_UNSUPPORTED otherwise) and 0 < admit < 1.  Several handles
+ * resulting variable preconditioner.  Needs q == p and at most 262,140 coarse
+ * steps (MG_ERR_UNSUPPORTED otherwise) and 0 < admit < 1.  Several handles
  * may share one network.  Parameter updates reach later solves (BF16 copies
  * are refreshed at the start of each fgmres_solve).
  *

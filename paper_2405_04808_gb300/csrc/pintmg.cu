@@ -2100,6 +2100,8 @@ extern "C" int mg_true_residual_noalloc(mg_handle *h, const double *b, const dou
 namespace {
 
 constexpr int kLossPartials = 1024;
+constexpr int kNetMaxBatch = 32767;  // grid z of the convolution launches (batch x output-channel blocks)
+constexpr int kNetMaxT = 65535 * 4;  // grid y of the tensor-core convolution (4 rows per CTA)
 constexpr int kScaleParts = 64;
 constexpr int kWgSlices = 64;   // position slices of the weight gradient (partial sums)
 constexpr int kBiasParts = 64;
@@ -2298,7 +2300,9 @@ int mg_net_get_grad(const mg_net *net, float *grad) {
 }
 
 int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *y, int bf16, void *stream) {
-  if (!net || !x || !y || batch < 1 || T < 1 || X < 1 || (bf16 != 0 && bf16 != 1)) return MG_ERR_ARG;
+  if (!net || !x || !y || batch < 1 || batch > kNetMaxBatch || T < 1 || T > kNetMaxT || X < 1 ||
+      (bf16 != 0 && bf16 != 1))
+    return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long TX = (long long)T * X;
   return net_guard([&] {
@@ -2339,7 +2343,8 @@ int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *
 
 int mg_net_loss_grad(mg_net *net, const float *x, const float *target, int batch, int T, int X, float *loss,
                      void *stream) {
-  if (!net || !x || !target || !loss || batch < 1 || T < 1 || X < 1) return MG_ERR_ARG;
+  if (!net || !x || !target || !loss || batch < 1 || batch > kNetMaxBatch || T < 1 || T > kNetMaxT || X < 1)
+    return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return net_guard([&] {
     net_ensure_train(net, batch, (long long)T * X, 1);
@@ -2357,7 +2362,9 @@ int mg_net_adam_step(mg_net *net, float lr, float beta1, float beta2, float eps,
 
 int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count, int T, int X, int batch, int epochs,
                  float lr, unsigned long long seed, int normalize, float *epoch_loss, void *stream) {
-  if (!net || !x_all || !y_all || count < 1 || T < 1 || X < 1 || batch < 1 || epochs < 0 || !(lr > 0.f) ||
+  if (!net || !x_all || !y_all || count < 1 || T < 1 || T > kNetMaxT || X < 1 || batch < 1 || batch > kNetMaxBatch ||
+      epochs < 0 ||
+      !(lr > 0.f) ||
       (normalize != 0 && normalize != 1))
     return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -2450,7 +2457,7 @@ int mg_attach_coarse_net(mg_handle *h, mg_net *net, double admit, int bf16) {
     return MG_OK;
   }
   if (!(admit > 0.0 && admit < 1.0) || (bf16 != 0 && bf16 != 1)) return MG_ERR_ARG;
-  if (h->q != h->p) return MG_ERR_UNSUPPORTED;
+  if (h->q != h->p || h->lv.back().n > kNetMaxT) return MG_ERR_UNSUPPORTED;
   return net_guard([&] {
     conv_mma_prepare();
     const Level &cl = h->lv.back();

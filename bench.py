@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="burgers_nx128_n1024", choices=sorted(W.WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32s"],
+                    help="fp32: V-cycle in FP32; fp32s: smoother and transfers in FP32, coarse solve in FP64")
     ap.add_argument("--restart", type=int, default=None,
                     help="FGMRES restart length (default: the workload's, from a sweep of solve times)")
     ap.add_argument("--omega", type=float, default=1.0,
@@ -163,7 +164,11 @@ def roofline(prof, dominant, precision, workload=None):
     t = ms / 1e3
     bw = nbytes / t / 1e9
     fl = nflops / t / 1e12
-    alu_peak = FP64_TFLOPS_MEASURED if precision == "fp64" else FP32_TFLOPS_MEASURED
+    # the Krylov kernels are FP64 in every mode; the V-cycle's follow the precision mode
+    # (the coarse SGS stays FP64 in fp32s)
+    fp64_kernel = (precision == "fp64" or dominant in ("multidot", "axpy_scale", "arnoldi_scalar", "apply")
+                   or (precision == "fp32s" and dominant == "sgs_chain"))
+    alu_peak = FP64_TFLOPS_MEASURED if fp64_kernel else FP32_TFLOPS_MEASURED
     t_hbm = nbytes / (hbm * 1e9)
     t_alu = nflops / (alu_peak * 1e12)
     common = {"kernel": dominant, "launches": n, "avg_launch_us": round(ms * 1e3 / n, 3),
@@ -176,7 +181,7 @@ def roofline(prof, dominant, precision, workload=None):
     if t_alu > t_hbm:
         return {"bound": "alu", "achieved": round(fl, 4), "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": round(fl / alu_peak, 4), "achieved_gbs": round(bw, 1), "hbm_peak_gbs": hbm,
-                "peak_source": "measured FP64 FMA probe (1.196 of 1.259 nominal TFLOP/s)" if precision == "fp64"
+                "peak_source": "measured FP64 FMA probe (1.196 of 1.259 nominal TFLOP/s)" if fp64_kernel
                 else "measured FP32 FMA probe", **common}
     return {"bound": "hbm", "achieved": round(bw, 1), "peak": hbm, "unit": "GB/s", "frac": round(bw / hbm, 4),
             "achieved_tflops": round(fl, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", **common}
@@ -187,7 +192,7 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
     solve (kernels inside a captured graph cannot be bracketed); then warm-up,
     `steps` timed solves and the end-to-end solves in the timed mode
     (default: one CUDA graph per solve with device-side loops)."""
-    prec = P.MG_PRECISION_FP64 if precision == "fp64" else P.MG_PRECISION_FP32
+    prec = {"fp64": P.MG_PRECISION_FP64, "fp32": P.MG_PRECISION_FP32, "fp32s": P.MG_PRECISION_FP32_SMOOTH}[precision]
     lv = levels or wl["levels"]
     b = torch.tensor(prob.b, device=dev)
     x = torch.empty_like(b)
@@ -436,8 +441,11 @@ def run_native(args):
         # (name, precision, omega, levels): the mixed-precision V-cycle, relaxed sweeps (an option
         # outside the paper), and the paper's serial baseline of Sec. 6.3 (SGS-GMRES, no multigrid),
         # whose block Gauss-Seidel chains run here as a parallel scan in time
-        for name, prec, om, lv in (("fp32_vcycle", "fp32", args.omega, None), ("omega0.7_fp64", "fp64", 0.7, None),
+        for name, prec, om, lv in (("fp32_vcycle", "fp32", args.omega, None),
+                                   ("fp32_smoother_fp64_coarse", "fp32s", args.omega, None),
+                                   ("omega0.7_fp64", "fp64", 0.7, None),
                                    ("omega0.7_fp32_vcycle", "fp32", 0.7, None),
+                                   ("omega0.7_fp32_smoother_fp64_coarse", "fp32s", 0.7, None),
                                    ("sgs_gmres_no_multigrid", "fp64", 1.0, 1)):
             if prec == args.precision and om == args.omega and lv is None:
                 continue

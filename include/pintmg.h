@@ -46,8 +46,11 @@ typedef enum {
 } mg_layout;
 
 typedef enum {
-  MG_PRECISION_FP64 = 0, /* the plain method: every step in FP64 */
-  MG_PRECISION_FP32 = 1  /* V-cycle (smoother, transfers, SGS) in FP32; FGMRES, coarse GMRES and true residual in FP64 */
+  MG_PRECISION_FP64 = 0,        /* the plain method: every step in FP64 */
+  MG_PRECISION_FP32 = 1,        /* V-cycle (smoother, transfers, SGS) in FP32; FGMRES, coarse GMRES and true
+                                   residual in FP64 */
+  MG_PRECISION_FP32_SMOOTH = 2  /* smoother and transfers in FP32; the coarse solve (GMRES and its SGS), FGMRES
+                                   and true residual in FP64 */
 } mg_precision;
 
 /*

@@ -725,6 +725,10 @@ void sgs_fp64<double>(mg_handle *h, Level &lev, const double *r, double *y, cuda
 }
 template <>
 void sgs_fp64<float>(mg_handle *h, Level &lev, const double *r, double *y, cudaStream_t s) {
+  if (h->opts.precision == MG_PRECISION_FP32_SMOOTH) {  // the coarse solve stays FP64
+    sgs_apply<double>(h, lev, r, y, s);
+    return;
+  }
   LevelData<float> &d = lev.f;
   convert<float>(h, r, d.b, lev.len, s);
   sgs_apply<float>(h, lev, d.b, d.y, s);
@@ -1063,7 +1067,7 @@ void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
 // z = M^-1 v on FP64 fine vectors
 void precondition(mg_handle *h, const double *v, double *z, cudaStream_t s) {
   h->vcycles++;
-  if (h->opts.precision == MG_PRECISION_FP32) {
+  if (h->opts.precision != MG_PRECISION_FP64) {
     Level &f = h->lv[0];
     convert<float>(h, v, f.f.b, f.len, s);
     vcycle<float>(h, 0, f.f.b, f.f.y, s);
@@ -1447,7 +1451,9 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (O->coarse_maxit < 1 || O->coarse_maxit > 64 || O->coarse_fixed_iters < 0 || O->coarse_fixed_iters > 64)
     return MG_ERR_ARG;
   if (O->end_rule != 0 && O->end_rule != 1) return MG_ERR_ARG;
-  if (O->precision != MG_PRECISION_FP64 && O->precision != MG_PRECISION_FP32) return MG_ERR_ARG;
+  if (O->precision != MG_PRECISION_FP64 && O->precision != MG_PRECISION_FP32 &&
+      O->precision != MG_PRECISION_FP32_SMOOTH)
+    return MG_ERR_ARG;
   if (!(O->omega > 0.0 && O->omega <= 1.0)) return MG_ERR_ARG;
   if (O->coarse_precond < MG_COARSE_SGS || O->coarse_precond > MG_COARSE_BGS) return MG_ERR_ARG;
   if (O->device_loops != 0 && O->device_loops != 1) return MG_ERR_ARG;
@@ -1625,7 +1631,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
         }
       }
       alloc_level_vectors<double>(h, lev, lev.d, l == L - 1, l == 0);
-      if (O->precision == MG_PRECISION_FP32) {
+      if (O->precision != MG_PRECISION_FP64) {
         LevelView<float> &f = lev.f.view;
         f.n = nl;
         f.p = p;
@@ -2588,7 +2594,7 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
     if (!hit) {
       Level &cl = h->lv.back();
       if (!env_chain) {
-        if (h->opts.precision == MG_PRECISION_FP32)
+        if (h->opts.precision == MG_PRECISION_FP32)  // the coarse SGS runs in FP32 only in this mode
           tune_chain<float>(h, cl, c, s);
         else
           tune_chain<double>(h, cl, c, s);

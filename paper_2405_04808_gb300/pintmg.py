@@ -30,6 +30,7 @@ MG_LAYOUT_DENSE = 0
 MG_LAYOUT_TRIDIAG = 1
 MG_PRECISION_FP64 = 0
 MG_PRECISION_FP32 = 1
+MG_PRECISION_FP32_SMOOTH = 2
 COARSE_PRECOND = {"sgs": 0, "jacobi": 1, "fgs": 2, "bgs": 3}
 
 #: every symbol include/pintmg.h declares

@@ -394,3 +394,14 @@ def test_two_warp_block_solves_match(P, monkeypatch, nx, n, omega):
     assert np.linalg.norm(xs[0][0] - xs[1][0]) <= 1e-11 * np.linalg.norm(xs[1][0])
     xd = O.direct_solve(prob)
     assert np.linalg.norm(xs[0][0] - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("case", [0, 4, 8])
+def test_fp32_smoother_fp64_coarse_reaches_fp64_solution(P, case):
+    """Smoother and transfers in FP32, coarse GMRES + SGS in FP64: FGMRES (FP64) still reaches the direct solution."""
+    make, levels, nu_pre, nu_post, end_rule, omega = _unpack(case)
+    prob = make()
+    x, info = _solve_x(P, prob, dict(levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule, omega=omega,
+                                     precision=P.MG_PRECISION_FP32_SMOOTH), restart=100)
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)

@@ -313,6 +313,16 @@ int mg_coarse_shape(const mg_handle *h, int *T, int *X);
  */
 int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream);
 
+/*
+ * Spectral radius of the undamped block-Jacobi iteration I - D^-1 A~ on level
+ * `level` (0 = finest), the quantity of Table 2, by power iteration on the
+ * device: `iters` sweeps (>= 8) of the smoother with a zero right-hand side
+ * from a fixed start vector, each normalised; *rho = the geometric mean of the
+ * norm ratios over the second half (robust to complex or +- pairs of dominant
+ * eigenvalues).  FP64.  Allocates 3 level vectors for the call; synchronises.
+ */
+int mg_jacobi_radius(mg_handle *h, int level, int iters, double *rho, void *stream);
+
 /* Release every device buffer of the handle.  NULL is accepted. */
 void mg_destroy(mg_handle *h);
 

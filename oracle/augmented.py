@@ -327,6 +327,13 @@ def sgs_apply(level: Level, r: np.ndarray) -> np.ndarray:
     return level.DU_solve(level.D @ w)
 
 
+def jacobi_spectral_radius(level: Level) -> float:
+    """rho(I - D^-1 A~) of the block-Jacobi iteration (Table 2), by dense eigenvalues."""
+    A = level.At.toarray()
+    D = level.D.toarray()
+    return float(np.max(np.abs(np.linalg.eigvals(np.eye(A.shape[0]) - np.linalg.solve(D, A)))))
+
+
 def fixed_point_preconditioner(level: Level, kind: str):
     """The block fixed-point iterations of Sec. 5.3.4 / Table 1 as preconditioners:
     one step from zero of Jacobi D^-1, forward Gauss-Seidel (D + L)^-1,

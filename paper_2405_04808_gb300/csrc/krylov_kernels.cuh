@@ -450,4 +450,23 @@ __global__ void k_record_pair(const double *__restrict__ r, const double *__rest
   }
 }
 
+// power iteration: x = y / ||y|| (nrm2[0] = ||y||^2); acc[0] += log ||y||, acc[1] += 1 when counting
+__global__ void k_power_step(const double *__restrict__ y, double *x, long long n, const double *nrm2, double *acc,
+                             int counting) {
+  const double nr = sqrt(nrm2[0]);
+  const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = y[i] * inv;
+  if (counting && blockIdx.x == 0 && threadIdx.x == 0 && nr > 0.0) {
+    acc[0] += log(nr);
+    acc[1] += 1.0;
+  }
+}
+
+// a fixed, non-degenerate start vector for the power iteration
+__global__ void k_power_start(double *x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = 1.0 + 0.5 * (double)((i * 2654435761ULL) % 1000ULL) / 1000.0;
+}
+
 }  // namespace pintmg

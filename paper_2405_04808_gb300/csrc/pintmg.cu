@@ -2642,3 +2642,50 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
   }
   return status;
 }
+
+// ===========================================================================
+// Spectral radius of the block-Jacobi iteration (Table 2) by power iteration
+
+extern "C" int mg_jacobi_radius(mg_handle *h, int level, int iters, double *rho, void *stream) {
+  if (!h || !rho || level < 0 || level >= (int)h->lv.size() || iters < 8) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Level &lev = h->lv[level];
+  const long long len = lev.len;
+  const LevelView<double> &L = lev.d.view;
+  double *buf = nullptr;
+  int status = MG_OK;
+  try {
+    // x, y, a zero right-hand side, |y|^2 and the log accumulator
+    cudaError_t e = cudaMalloc(&buf, (3 * (size_t)len + 8) * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      buf = nullptr;
+      throw std::bad_alloc();
+    }
+    double *x = buf, *y = buf + len, *zero = buf + 2 * len, *nrm2 = buf + 3 * len, *acc = nrm2 + 4;
+    ck(cudaMemsetAsync(zero, 0, (len + 8) * sizeof(double), s));
+    k_power_start<<<grid_for(len, 256), 256, 0, s>>>(x, len);
+    ck_launch();
+    const Vec<double> X = make_vec(x, L.n, L.p, L.q);
+    for (int k = 0; k < iters; ++k) {
+      // y = D^-1 (0 - (L + L^T) x) = (I - D^-1 A) x: one undamped sweep from x with a zero right-hand side
+      launch_block_solve<double>(h, L, zero, X.u, X.m, y, s);
+      multidot(h, y, len, 1, y, len, nrm2, 0, s);
+      k_power_step<<<grid_for(len, 256), 256, 0, s>>>(y, x, len, nrm2, acc, k >= iters / 2);
+      ck_launch();
+    }
+    double a[2] = {0.0, 0.0};
+    ck(cudaMemcpyAsync(a, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    *rho = a[1] > 0.0 ? std::exp(a[0] / a[1]) : 0.0;
+  } catch (const CudaFail &) {
+    status = MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    status = MG_ERR_OOM;
+  }
+  if (buf) {
+    cudaStreamSynchronize(s);
+    cudaFree(buf);
+  }
+  return status;
+}

@@ -39,7 +39,7 @@ EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmr
             "mg_launch_count", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
             "mg_net_forward", "mg_net_loss_grad", "mg_net_adam_step", "mg_net_train", "mg_net_destroy",
-            "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune",
+            "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune", "mg_jacobi_radius",
             "mg_destroy", "mg_status_string", "mg_last_cuda_error")
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -125,7 +125,8 @@ def lib():
                 ("mg_record_coarse", [vp, vp, vp, ci], ci),
                 ("mg_recorded_pairs", [vp], ci),
                 ("mg_coarse_shape", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
-                ("mg_autotune", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), vp], ci)):
+                ("mg_autotune", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), vp], ci),
+                ("mg_jacobi_radius", [vp, ci, ci, ctypes.POINTER(ctypes.c_double), vp], ci)):
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
@@ -343,6 +344,14 @@ def mg_coarse_shape(h):
     T, X = ctypes.c_int(), ctypes.c_int()
     _check(lib().mg_coarse_shape(ctypes.c_void_p(h), ctypes.byref(T), ctypes.byref(X)), "mg_coarse_shape")
     return T.value, X.value
+
+
+def mg_jacobi_radius(h, level: int = 0, iters: int = 4000, stream: int = 0) -> float:
+    """Spectral radius of the block-Jacobi iteration on a level (Table 2), by power iteration."""
+    rho = ctypes.c_double()
+    _check(lib().mg_jacobi_radius(ctypes.c_void_p(h), int(level), int(iters), ctypes.byref(rho),
+                                  ctypes.c_void_p(stream)), "mg_jacobi_radius")
+    return rho.value
 
 
 SGS_CHAINS = ("scan", "cluster", "serial")

@@ -405,3 +405,24 @@ def test_fp32_smoother_fp64_coarse_reaches_fp64_solution(P, case):
                                      precision=P.MG_PRECISION_FP32_SMOOTH), restart=100)
     xd = O.direct_solve(prob)
     assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("make,levels", [
+    (lambda: W.vdp_paper(n=32, gamma=100.0), 3),
+    (lambda: W.vdp_paper(n=32, gamma=1.0), 2),
+    (lambda: W.burgers(nx=12, n=16, seed=171), 2),
+])
+def test_jacobi_spectral_radius_matches_dense_eigenvalues(P, make, levels):
+    """mg_jacobi_radius (power iteration on the GPU) against the oracle's dense eigenvalues of I - D^-1 A~ on
+    every level (Table 2's quantity)."""
+    prob = make()
+    h = P.mg_setup(prob, levels=levels)
+    try:
+        got = [P.mg_jacobi_radius(h, lv, iters=6000) for lv in range(levels)]
+    finally:
+        P.mg_destroy(h)
+    raw = O.raw_from_problem(prob)
+    for lv in range(levels):
+        want = O.jacobi_spectral_radius(O.Level(raw))
+        assert abs(got[lv] - want) <= 5e-3 * want, (lv, got[lv], want)
+        raw = O.coarsen_raw(raw)

@@ -68,9 +68,7 @@ def test_jacobi_is_textbook_block_jacobi(make):
 
 
 def _rho_jacobi(level):
-    A = level.At.toarray()
-    D = level.D.toarray()
-    return float(np.max(np.abs(np.linalg.eigvals(np.eye(A.shape[0]) - np.linalg.solve(D, A)))))
+    return O.jacobi_spectral_radius(level)
 
 
 @pytest.mark.slow

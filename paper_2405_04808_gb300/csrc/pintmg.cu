@@ -648,16 +648,20 @@ void run_scan(mg_handle *h, const std::vector<T *> &P, const T *xhat, T *out, T 
     ck(cudaMemcpyAsync(out, xhat, (size_t)n * p * sizeof(T), cudaMemcpyDeviceToDevice, s));
     return;
   }
-  // parts column slices per row: the largest power of two with parts * p <= 512
-  // and at least 8 columns per slice
+  // rows per CTA: slices of 32 rows when p is a multiple of 32 and n would leave
+  // SMs idle, else all p; parts column slices per row: the largest power of two
+  // with parts * rows <= 512 (256 for slices) and at least 8 columns per slice
+  const int rows = (p % 32 == 0 && p >= 64 && n < 4 * 152) ? 32 : p;
+  const int max_threads = rows < p ? 256 : 512;
   int parts = 1;
-  while (parts * 2 * p <= 512 && p / (parts * 2) >= 8) parts *= 2;
-  const int threads = std::max(parts * p, 32);
-  const size_t shm = (size_t)(1 + parts) * p * sizeof(T);
+  while (parts * 2 * rows <= max_threads && p / (parts * 2) >= 8) parts *= 2;
+  const int threads = std::max(parts * rows, 32);
+  const size_t shm = (size_t)p * sizeof(T) + (size_t)parts * rows * sizeof(T);
+  const dim3 grid(n, p / rows);
   const T *in = xhat;
   for (int d = 0; d < R; ++d) {
     T *dst = ((R - 1 - d) % 2 == 0) ? out : tmp;
-    k_scan_round<T><<<n, threads, shm, s>>>(P[d], in, dst, n, p, 1 << d, reverse, parts);
+    k_scan_round<T><<<grid, threads, shm, s>>>(P[d], in, dst, n, p, 1 << d, reverse, parts, rows);
     ck_launch();
     in = dst;
   }

@@ -919,38 +919,41 @@ namespace pintmg {
 //     x_i <- x_i + P^(d)_i x_{i-2^d}      (i >= 2^d; others copied)
 // each a batched GEMV over every time step at once.  Element i is stored at
 // position i (forward chain) or n-1-i (backward chain, reverse = 1).
-// One CTA per i; threads (r, part) with r = tid mod p share row r over
-// `parts` column slices (coalesced column-major loads, more loads in flight),
-// the source vector x_{i-2^d} and the slice sums are staged in shared memory.
+// CTA (i, slice) computes `rows` rows of step i (all p rows when rows = p;
+// slices of 32 rows spread a round over more CTAs than there are steps, which
+// balances the SMs when n is a few hundred); threads (r, part) with
+// r = tid mod rows share row r over `parts` column slices (coalesced
+// column-major loads, more loads in flight), the source vector x_{i-2^d} and
+// the slice sums are staged in shared memory.  Grid: (n, p / rows).
 template <typename T>
 __global__ void k_scan_round(const T *__restrict__ Pd, const T *__restrict__ xin, T *xout, int n, int p,
-                             int shift, int reverse, int parts) {
+                             int shift, int reverse, int parts, int rows) {
   extern __shared__ unsigned char smem_raw[];
   T *src = reinterpret_cast<T *>(smem_raw);
-  T *part_sum = src + p;  // [parts][p]
-  const int i = blockIdx.x;
+  T *part_sum = src + p;  // [parts][rows]
+  const int i = blockIdx.x, r0 = blockIdx.y * rows;
   const long long si = reverse ? (long long)(n - 1 - i) : i;
   if (i < shift) {
-    for (int r = threadIdx.x; r < p; r += blockDim.x) xout[si * p + r] = xin[si * p + r];
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) xout[si * p + r0 + r] = xin[si * p + r0 + r];
     return;
   }
   const long long sj = reverse ? (long long)(n - 1 - (i - shift)) : (long long)(i - shift);
   for (int r = threadIdx.x; r < p; r += blockDim.x) src[r] = xin[sj * p + r];
   __syncthreads();
-  const T *P = Pd + (long long)i * p * p;
-  const int r = threadIdx.x % p, part = threadIdx.x / p;
+  const T *P = Pd + (long long)i * p * p + r0;
+  const int r = threadIdx.x % rows, part = threadIdx.x / rows;
   if (part < parts) {
     const int k0 = part * p / parts, k1 = (part + 1) * p / parts;
     T acc = T(0);
 #pragma unroll 8
     for (int k = k0; k < k1; ++k) acc = fma(P[(long long)k * p + r], src[k], acc);
-    part_sum[part * p + r] = acc;
+    part_sum[part * rows + r] = acc;
   }
   __syncthreads();
-  for (int rr = threadIdx.x; rr < p; rr += blockDim.x) {
-    T acc = xin[si * p + rr];
-    for (int q = 0; q < parts; ++q) acc += part_sum[q * p + rr];
-    xout[si * p + rr] = acc;
+  for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
+    T acc = xin[si * p + r0 + rr];
+    for (int q = 0; q < parts; ++q) acc += part_sum[q * rows + rr];
+    xout[si * p + r0 + rr] = acc;
   }
 }
 

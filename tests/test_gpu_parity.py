@@ -426,3 +426,13 @@ def test_jacobi_spectral_radius_matches_dense_eigenvalues(P, make, levels):
         want = O.jacobi_spectral_radius(O.Level(raw))
         assert abs(got[lv] - want) <= 5e-3 * want, (lv, got[lv], want)
         raw = O.coarsen_raw(raw)
+
+
+@pytest.mark.parametrize("nx,n,levels", [(32, 1, 1), (32, 2, 1), (40, 2, 2), (96, 4, 3)])
+def test_few_time_blocks(P, nx, n, levels):
+    """One to four time steps (the last block j = n carries only v and mu; block 0 has no v): the warp-pair
+    and proportional-V block solves on their edge cases, against the direct solve."""
+    prob = W.burgers(nx=nx, n=n, seed=181)
+    x, info = _solve_x(P, prob, dict(levels=levels, nu_pre=2, nu_post=2))
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)

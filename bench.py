@@ -60,9 +60,9 @@ def parse():
     ap.add_argument("--allow-partial", action="store_true",
                     help="accept solves stopped by --maxit (bounded profiler captures only)")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
-    ap.add_argument("--learned-pairs", type=int, default=400,
+    ap.add_argument("--learned-pairs", type=int, default=2000,
                     help="training pairs for the learned coarse correction variant (0 skips it)")
-    ap.add_argument("--learned-epochs", type=int, default=3)
+    ap.add_argument("--learned-epochs", type=int, default=4)
     args = ap.parse_args()
     if args.restart is None:
         args.restart = W.WORKLOADS[args.workload].get("restart", 400)

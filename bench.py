@@ -352,8 +352,11 @@ def measure_learned(P, torch, args, dev, stream, omega=0.7):
     res = {"workload": LEARNED_WORKLOAD, "restart": restart, "omega": omega, "levels": wl["levels"], "admit": 0.5,
            "inference": "bf16 on the tensor cores (mma.sync m16n8k16), fp32 accumulation"}
     t0 = time.perf_counter()
-    per = 100
-    train_probs = (wl["make"](seed=wl["seed"] + 1 + k) for k in range((args.learned_pairs + per - 1) // per))
+    import os
+    per = 90  # a solve records one pair per FGMRES iteration (95 here)
+    nprob = (args.learned_pairs + per - 1) // per
+    train_probs = W.make_many(LEARNED_WORKLOAD, [wl["seed"] + 1 + k for k in range(nprob)],
+                              workers=max(1, min(16, os.cpu_count() or 1)))
     R, Y = LN.collect_pairs(train_probs, settings, args.learned_pairs, restart=restart, per_problem=per)
     torch.cuda.synchronize(dev)
     res["pairs"] = int(R.shape[0])

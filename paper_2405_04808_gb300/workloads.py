@@ -395,6 +395,21 @@ def _batch_member(k: int, seed: int):
     return burgers(nx=nx, n=nt, seed=sd), dict(levels=4, nu_pre=4, nu_post=4)
 
 
+def _make_named(name: str, seed: int):
+    return WORKLOADS[name]["make"](seed=seed)
+
+
+def make_many(name: str, seeds, workers: int = 1):
+    """The named workload at several seeds (a spawned process pool when workers > 1)."""
+    seeds = list(seeds)
+    if workers <= 1:
+        return [_make_named(name, sd) for sd in seeds]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_make_named, [name] * len(seeds), seeds))
+
+
 def batch_uneven(seed: int = 6000, count: int = 64, workers: int = 1):
     """The batched workload: `count` systems at distinct seeded iterates, half
     van der Pol with nt cycling through 512 ... 16384, half Burgers with

@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--learned-pairs", type=int, default=2000,
                     help="training pairs for the learned coarse correction variant (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=4)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and learned variants")
     args = ap.parse_args()
     if args.restart is None:
         args.restart = W.WORKLOADS[args.workload].get("restart", 400)
@@ -463,8 +464,9 @@ def run_native(args):
                               "coarse_iters_per_vcycle": round(v["coarse_iters_per_vcycle"], 3),
                               "setup_ms": round(v["setup_ms"], 1),
                               "dominant_kernel": v["dominant"], "roofline_frac": v["roofline"].get("frac")}
-    batch = None if args.no_variants else measure_batch(P, torch, args, dev, stream)
-    learned = None if (args.no_variants or args.learned_pairs <= 0) else measure_learned(P, torch, args, dev, stream)
+    batch = None if (args.no_variants or args.no_batch) else measure_batch(P, torch, args, dev, stream)
+    learned = (None if (args.no_variants or args.no_batch or args.learned_pairs <= 0)
+               else measure_learned(P, torch, args, dev, stream))
     out = {
         "metric": METRIC, "value": round(main["value"], 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(main["ms_per_step"], 3), "higher_is_better": True,

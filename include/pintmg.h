@@ -301,13 +301,14 @@ int mg_coarse_shape(const mg_handle *h, int *T, int *X);
  * Autotuner (no counterpart in the paper).  Times, on h's own levels and on
  * `stream`, the candidate evaluations of the coarse SGS chains (parallel scan
  * with prefix products when they were formed, the 16-CTA cluster chain for
- * the tridiagonal layout with p >= 32, the single-CTA chain: equal up to
+ * the tridiagonal layout with p >= 32, the single-CTA chain, and the
+ * segmented chain when its in-segment products were formed: equal up to
  * rounding) and the dot-product blocking (4, 8 or 16 basis vectors per CTA:
  * bitwise equal), and makes the fastest ones h's choice.  Results are cached
  * for the process by (layout, coarse n, p, q, fine n, precision), so later
  * handles of the same shape take the cached choice without timing.  A chain
  * forced by the environment (PINTMG_SGS_CHAIN) is kept.  *chain (0 scan,
- * 1 cluster, 2 single CTA) and *dot_vb (may be NULL) report the choice.
+ * 1 cluster, 2 single CTA, 3 segmented) and *dot_vb (may be NULL) report the choice.
  * Allocates a temporary of 49 x min(n(4p+q), 2^20) doubles; synchronises
  * `stream`; invalidates h's captured graphs.
  */

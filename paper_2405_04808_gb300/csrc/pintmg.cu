@@ -78,6 +78,9 @@ struct LevelData {
   // (empty when the budget below is exceeded; the cluster chain is used then)
   std::vector<T *> scanF, scanB;
   T *scan_tmp = nullptr;
+  // coarsest level: in-segment products Q of the segmented SGS chains (null when not formed)
+  T *segF = nullptr, *segB = nullptr;
+  int seg_len = 0;
   T *b = nullptr, *y = nullptr, *tmp = nullptr;
   T *chainU = nullptr, *chainM = nullptr, *sgs_w = nullptr;
 };
@@ -146,6 +149,8 @@ struct mg_handle {
   int vcycles = 0, coarse_iters = 0;
   int use_cluster = 1;  // SGS chains on a thread-block cluster (tridiagonal layout)
   int use_scan = 1;     // SGS chains as a parallel scan with precomputed prefix products
+  int use_seg = 1;      // SGS chains as concurrent segment chains joined by batched products
+  int force_seg = 0;    // form the segment products even when the full scan fits (tests)
   int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
   int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
   int pair_tri = 1;     // levels with few blocks: two warps per block
@@ -589,7 +594,8 @@ void convert_back<float>(mg_handle *h, const float *x, double *y, long long len,
 // One SGS chain on a thread-block cluster (tridiagonal layout, p >= 32).
 // Returns false if the device refuses the cluster launch.
 template <typename T, bool kForward, int K>
-cudaError_t launch_chain_cluster_k(int S, const T *G, const T *xhat, T *xout, int n, int p, cudaStream_t s) {
+cudaError_t launch_chain_cluster_k(int S, const T *G, const T *xhat, T *xout, int n, int p, cudaStream_t s,
+                                   int seg_len) {
   const int tpr = 16;
   const int rows = (p + S - 1) / S;
   const int threads = ((rows * tpr + 31) / 32) * 32;
@@ -597,7 +603,7 @@ cudaError_t launch_chain_cluster_k(int S, const T *G, const T *xhat, T *xout, in
   auto kern = k_chain_cluster<T, kForward, K>;
   if (S > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(S, 1, 1);
+  cfg.gridDim = dim3(S * ((n + seg_len - 1) / seg_len), 1, 1);  // one cluster per segment
   cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = 2 * (size_t)p * sizeof(T);
   cfg.stream = s;
@@ -608,22 +614,24 @@ cudaError_t launch_chain_cluster_k(int S, const T *G, const T *xhat, T *xout, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, G, xhat, xout, n, p, rows, tpr);
+  return cudaLaunchKernelEx(&cfg, kern, G, xhat, xout, n, p, rows, tpr, seg_len);
 }
 
 // One SGS chain on a thread-block cluster (tridiagonal layout, 32 <= p <= 512):
 // 16 threads per row, K = ceil(p / 16) columns per thread.  Returns false if
 // the device refuses the cluster launch.
 template <typename T, bool kForward>
-bool launch_chain_cluster(mg_handle *h, const T *G, const T *xhat, T *xout, int n, int p, cudaStream_t s) {
+bool launch_chain_cluster(mg_handle *h, const T *G, const T *xhat, T *xout, int n, int p, cudaStream_t s,
+                          int seg_len = 0) {
   const int kneed = (p + 15) / 16;
+  if (seg_len <= 0) seg_len = n;
   for (int S : {16, 8}) {
     cudaError_t e;
-    if (kneed <= 2) e = launch_chain_cluster_k<T, kForward, 2>(S, G, xhat, xout, n, p, s);
-    else if (kneed <= 4) e = launch_chain_cluster_k<T, kForward, 4>(S, G, xhat, xout, n, p, s);
-    else if (kneed <= 8) e = launch_chain_cluster_k<T, kForward, 8>(S, G, xhat, xout, n, p, s);
-    else if (kneed <= 16) e = launch_chain_cluster_k<T, kForward, 16>(S, G, xhat, xout, n, p, s);
-    else e = launch_chain_cluster_k<T, kForward, 32>(S, G, xhat, xout, n, p, s);
+    if (kneed <= 2) e = launch_chain_cluster_k<T, kForward, 2>(S, G, xhat, xout, n, p, s, seg_len);
+    else if (kneed <= 4) e = launch_chain_cluster_k<T, kForward, 4>(S, G, xhat, xout, n, p, s, seg_len);
+    else if (kneed <= 8) e = launch_chain_cluster_k<T, kForward, 8>(S, G, xhat, xout, n, p, s, seg_len);
+    else if (kneed <= 16) e = launch_chain_cluster_k<T, kForward, 16>(S, G, xhat, xout, n, p, s, seg_len);
+    else e = launch_chain_cluster_k<T, kForward, 32>(S, G, xhat, xout, n, p, s, seg_len);
     if (e == cudaSuccess) return true;
     cudaGetLastError();
   }
@@ -667,6 +675,30 @@ void run_scan(mg_handle *h, const std::vector<T *> &P, const T *xhat, T *out, T 
   }
 }
 
+// One SGS chain as concurrent segment chains (one thread-block cluster per
+// segment of seg_len positions, from a zero incoming state) joined by the
+// in-segment products Q: a serial pass over the segment ends, then every other
+// position in one batched GEMV.  Returns false if the cluster launch is refused.
+template <typename T, bool kForward>
+bool run_seg(mg_handle *h, const T *G, const T *Q, int seg_len, const T *xhat, T *out, int n, int p,
+             cudaStream_t s) {
+  if (!launch_chain_cluster<T, kForward>(h, G, xhat, out, n, p, s, seg_len)) return false;
+  ck_launch();
+  const int rows = p % 32 == 0 ? 32 : p;
+  int parts = 1;
+  while (parts * 2 * rows <= 256 && p / (parts * 2) >= 8) parts *= 2;
+  const int threads = std::max(parts * rows, 32);
+  const size_t shm = (size_t)p * sizeof(T) + (size_t)parts * rows * sizeof(T);
+  const int nseg = (n + seg_len - 1) / seg_len;
+  for (int c = 1; c < nseg; ++c) {  // the true last entry of every segment, in order
+    k_seg_fix<T><<<dim3(1, p / rows), threads, shm, s>>>(Q, out, n, p, seg_len, c, kForward ? 0 : 1, parts, rows);
+    ck_launch();
+  }
+  k_seg_fix<T><<<dim3(n, p / rows), threads, shm, s>>>(Q, out, n, p, seg_len, 0, kForward ? 0 : 1, parts, rows);
+  ck_launch();
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // The coarse preconditioner on the coarsest level (precision T):
 // SGS y = [(D+L) D^-1 (D+L^T)]^-1 r, or one of Table 1's alternatives.
@@ -684,13 +716,22 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
   const size_t shm = (size_t)p * sizeof(T);
   const bool cluster = h->layout == MG_LAYOUT_TRIDIAG && p >= 32 && h->use_cluster;
   const bool scan = h->use_scan && (n == 1 || !d.scanF.empty());
+  const bool seg = !scan && h->use_seg && d.segF != nullptr;
   const bool forward = kind != MG_COARSE_BGS;
+  // algorithmic work of a segmented chain: the serial links plus the joining products
+  const double seg_bytes = (double)sizeof(T) * 2.0 * n * ((double)p * p + 2.0 * p), seg_flops = 4.0 * n * p * p;
   if (forward) {
     // w = D^-1 r; forward chain u_j = uhat_j - Cu_j u_{j-1}
     launch_block_solve<T>(h, d.view, r, nullptr, nullptr, d.sgs_w, s);
+    bool done = false;
     if (scan) {
       run_scan<T>(h, d.scanF, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, d.scan_tmp, n, p, 0, s);
-    } else if (n >= 1) {
+      done = true;
+    } else if (seg) {
+      Bracket br(h, CAT_CHAIN, s, seg_bytes, seg_flops);
+      done = run_seg<T, true>(h, d.Cu, d.segF, d.seg_len, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p, s);
+    }
+    if (!done && n >= 1) {
       // algorithmic: one p x p link matrix read and applied per step
       Bracket br(h, CAT_CHAIN, s, (double)sizeof(T) * n * ((double)p * p + 2.0 * p), 2.0 * n * p * p);
       if (!cluster || !launch_chain_cluster<T, true>(h, d.Cu, make_vec(d.sgs_w, n, p, h->q).u, d.chainU, n, p, s)) {
@@ -707,9 +748,15 @@ void sgs_apply(mg_handle *h, Level &lev, const T *r, T *y, cudaStream_t s) {
   // only mu(yhat) is needed by the backward chain
   const T *fwd = forward ? d.chainU : nullptr;
   launch_block_solve<T>(h, d.view, r, fwd, nullptr, d.sgs_w, s);
+  bool done = false;
   if (scan) {
     run_scan<T>(h, d.scanB, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, d.scan_tmp, n, p, 1, s);
-  } else if (n >= 1) {
+    done = true;
+  } else if (seg) {
+    Bracket br(h, CAT_CHAIN, s, seg_bytes, seg_flops);
+    done = run_seg<T, false>(h, d.Em, d.segB, d.seg_len, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p, s);
+  }
+  if (!done && n >= 1) {
     Bracket br(h, CAT_CHAIN, s, (double)sizeof(T) * n * ((double)p * p + 2.0 * p), 2.0 * n * p * p);
     if (!cluster || !launch_chain_cluster<T, false>(h, d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p, s)) {
       k_chain_backward<T><<<1, threads, shm, s>>>(d.Em, make_vec(d.sgs_w, n, p, h->q).m, d.chainM, n, p);
@@ -1490,8 +1537,9 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   // SGS chain implementation: "scan" (default), "cluster" or "serial"; the
   // environment variable PINTMG_SGS_CHAIN selects one (used by the tests)
   if (const char *e = std::getenv("PINTMG_SGS_CHAIN")) {
-    if (std::strcmp(e, "cluster") == 0) h->use_scan = 0;
-    if (std::strcmp(e, "serial") == 0) h->use_scan = 0, h->use_cluster = 0;
+    if (std::strcmp(e, "cluster") == 0) h->use_scan = 0, h->use_seg = 0;
+    if (std::strcmp(e, "serial") == 0) h->use_scan = 0, h->use_cluster = 0, h->use_seg = 0;
+    if (std::strcmp(e, "segmented") == 0) h->use_scan = 0, h->force_seg = 1;
   }
   // PINTMG_STAGE_TRI=0 turns the shared-memory staging of the block solves off (tests)
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
@@ -1633,6 +1681,24 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
           }
           lev.d.scan_tmp = h->mem.alloc<double>((size_t)nl * p);
         }
+        // segmented chains: in-segment products Q (one p x p per position, 2 n p^2 values in
+        // all), formed when the full scan is not (or on request); up to 8 segments of >= 16 steps
+        const double seg_bytes = 2.0 * (double)nl * p * p * sizeof(double);
+        if (layout == MG_LAYOUT_TRIDIAG && p >= 32 && nl >= 32 && seg_bytes <= 8.0 * (1 << 30) &&
+            (lev.d.scanF.empty() || h->force_seg)) {
+          const int nseg = std::min(8, nl / 16);
+          const int L = (nl + nseg - 1) / nseg;
+          lev.d.seg_len = L;
+          lev.d.segF = h->mem.alloc<double>((size_t)nl * p * p);
+          lev.d.segB = h->mem.alloc<double>((size_t)nl * p * p);
+          const dim3 grid((p + 31) / 32, (p + 31) / 32, nseg - 1);
+          for (int t = 0; t < L; ++t) {
+            k_seg_products<<<grid, 256, 0, s>>>(lev.d.Cu, lev.d.segF, nl, p, L, t, 0);
+            ck_launch();
+            k_seg_products<<<grid, 256, 0, s>>>(lev.d.Em, lev.d.segB, nl, p, L, t, 1);
+            ck_launch();
+          }
+        }
       }
       alloc_level_vectors<double>(h, lev, lev.d, l == L - 1, l == 0);
       if (O->precision != MG_PRECISION_FP64) {
@@ -1657,6 +1723,11 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
           lev.f.Em = to_float_copy(h, lev.d.Em, (long long)nl * p * p, s);
           for (double *P : lev.d.scanF) lev.f.scanF.push_back(to_float_copy(h, P, (long long)nl * p * p, s));
           for (double *P : lev.d.scanB) lev.f.scanB.push_back(to_float_copy(h, P, (long long)nl * p * p, s));
+          if (lev.d.segF) {
+            lev.f.segF = to_float_copy(h, lev.d.segF, (long long)nl * p * p, s);
+            lev.f.segB = to_float_copy(h, lev.d.segB, (long long)nl * p * p, s);
+            lev.f.seg_len = lev.d.seg_len;
+          }
           if (lev.d.scan_tmp) lev.f.scan_tmp = h->mem.alloc<float>((size_t)nl * p);
         }
         alloc_level_vectors<float>(h, lev, lev.f, l == L - 1, l == 0);
@@ -2517,9 +2588,9 @@ int mg_recorded_pairs(const mg_handle *h) { return h ? h->rec_count : MG_ERR_ARG
 namespace {
 
 struct TuneChoice {
-  int chain = 0;   // 0 scan, 1 cluster, 2 single CTA
+  int chain = 0;   // 0 scan, 1 cluster, 2 single CTA, 3 segmented
   int dot_vb = 8;
-  float ms_chain[3] = {-1.f, -1.f, -1.f};
+  float ms_chain[4] = {-1.f, -1.f, -1.f, -1.f};
   float ms_dot[3] = {-1.f, -1.f, -1.f};  // VB 4, 8, 16
 };
 
@@ -2552,22 +2623,25 @@ void tune_chain(mg_handle *h, Level &lev, TuneChoice &c, cudaStream_t s) {
   LevelData<T> &d = ldata<T>(lev);
   const bool has_scan = lev.n == 1 || !d.scanF.empty();
   const bool has_cluster = h->layout == MG_LAYOUT_TRIDIAG && h->p >= 32;
+  const bool has_seg = d.segF != nullptr;
   // input: the level's scratch vector (zeroed); output: its y vector, or the coarse
   // GMRES's preconditioner slot on a single-level FP64 handle (no y there)
   T *in = d.tmp;
   T *out = d.y ? d.y : reinterpret_cast<T *>(h->czout);
   ck(cudaMemsetAsync(in, 0, lev.len * sizeof(T), s));
-  const int save_scan = h->use_scan, save_cluster = h->use_cluster;
-  for (int k = 0; k < 3; ++k) {
-    if ((k == 0 && !has_scan) || (k == 1 && !has_cluster)) continue;
+  const int save_scan = h->use_scan, save_cluster = h->use_cluster, save_seg = h->use_seg;
+  for (int k = 0; k < 4; ++k) {
+    if ((k == 0 && !has_scan) || (k == 1 && !has_cluster) || (k == 3 && (!has_seg || !has_cluster))) continue;
     h->use_scan = k == 0;
-    h->use_cluster = k == 1;
+    h->use_cluster = k == 1 || k == 3;
+    h->use_seg = k == 3;
     c.ms_chain[k] = time_min(s, 3, [&] { sgs_apply<T>(h, lev, in, out, s); });
   }
   h->use_scan = save_scan;
   h->use_cluster = save_cluster;
+  h->use_seg = save_seg;
   int best = -1;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
     if (c.ms_chain[k] >= 0.f && (best < 0 || c.ms_chain[k] < c.ms_chain[best])) best = k;
   c.chain = best < 0 ? 2 : best;
 }
@@ -2628,7 +2702,8 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
     }
     if (!env_chain) {
       h->use_scan = c.chain == 0;
-      h->use_cluster = c.chain == 1;
+      h->use_cluster = c.chain == 1 || c.chain == 3;
+      h->use_seg = c.chain == 3;
     }
     h->dot_vb = c.dot_vb;
     h->gen++;  // captured graphs used the previous choices
@@ -2641,7 +2716,7 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
   h->launches = saved;
   h->prof = saved_prof;
   if (status == MG_OK) {
-    if (chain) *chain = env_chain ? (h->use_scan ? 0 : (h->use_cluster ? 1 : 2)) : c.chain;
+    if (chain) *chain = env_chain ? (h->use_scan ? 0 : (h->use_seg ? 3 : (h->use_cluster ? 1 : 2))) : c.chain;
     if (dot_vb) *dot_vb = c.dot_vb;
   }
   return status;

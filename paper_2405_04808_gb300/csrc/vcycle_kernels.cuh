@@ -840,15 +840,20 @@ namespace pintmg {
 // instruction reads TPR consecutive entries of the row.
 // kForward: links j = 1..n-1 on x = u; otherwise links j = n-1..1 on x = mu
 // (x_{j-1} = xhat_{j-1} - G_j x_j).
+// seg_len < n: each cluster (index blockIdx.x / S) runs one segment of seg_len
+// chain positions from a zero incoming state (its first entry is xhat's); the
+// segments are joined afterwards by k_seg_fix.  seg_len = n: the whole chain.
 template <typename T, bool kForward, int K>
 __global__ void k_chain_cluster(const T *__restrict__ G, const T *__restrict__ xhat, T *xout, int n, int p,
-                                int rows_per_cta, int tpr) {
+                                int rows_per_cta, int tpr, int seg_len) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);  // [2][p]
   const int S = (int)cluster.num_blocks();
   const int c = (int)cluster.block_rank();
+  const int pos0 = (int)(blockIdx.x / S) * seg_len;                 // first chain position of this segment
+  const int pos1 = pos0 + seg_len < n ? pos0 + seg_len : n;        // one past its last
   const int tid = threadIdx.x;
   const int row_local = tid / tpr, part = tid % tpr;
   const int row = c * rows_per_cta + row_local;
@@ -858,7 +863,7 @@ __global__ void k_chain_cluster(const T *__restrict__ G, const T *__restrict__ x
   T g[K];
   T xh = T(0);
   auto load_link = [&](int step) {
-    if (step >= n || !owner) return;
+    if (step >= pos1 || !owner) return;
     const int j = kForward ? step : n - step;
     const long long dst = kForward ? j : (long long)(j - 1);
     const T *gr = G + ((long long)j * p + row) * p;
@@ -869,16 +874,16 @@ __global__ void k_chain_cluster(const T *__restrict__ G, const T *__restrict__ x
     }
     xh = xhat[dst * p + row];
   };
-  const long long first = kForward ? 0 : (long long)(n - 1);
+  const long long first = kForward ? pos0 : (long long)(n - 1 - pos0);
   for (int i = tid; i < p; i += blockDim.x) buf[i] = xhat[first * p + i];
   if (c == 0)
     for (int i = tid; i < p; i += blockDim.x) xout[first * p + i] = xhat[first * p + i];
 #pragma unroll
   for (int i = 0; i < K; ++i) g[i] = T(0);
-  load_link(1);
+  load_link(pos0 + 1);
   cluster.sync();
   int cur = 0;
-  for (int step = 1; step < n; ++step) {
+  for (int step = pos0 + 1; step < pos1; ++step) {
     const int j = kForward ? step : n - step;
     const long long dst = kForward ? j : (long long)(j - 1);
     const T *xv = buf + cur * p;
@@ -910,6 +915,50 @@ __global__ void k_chain_cluster(const T *__restrict__ G, const T *__restrict__ x
 }  // namespace pintmg
 
 namespace pintmg {
+
+// ---------------------------------------------------------------------------
+// Segmented chain, joining step.  After the segments' local chains (zero
+// incoming state), position i of segment c >= 1 (positions [c L, c L + L))
+// becomes x_i = y_i + Q_i x_{cL-1}, with Q_i = A_i ... A_{cL} (setup, column-
+// major p x p per position) and x_{cL-1} the true last entry of segment c-1.
+// only_seg >= 1: update only the last position of that segment (the serial
+// pass over segment ends; grid (1, p / rows)); only_seg = 0: every position of
+// segments >= 1 except their last (grid (n, p / rows)).  In place; rows /
+// parts as in k_scan_round.  reverse: position i is stored at index n-1-i.
+template <typename T>
+__global__ void k_seg_fix(const T *__restrict__ Q, T *x, int n, int p, int L, int only_seg, int reverse, int parts,
+                          int rows) {
+  extern __shared__ unsigned char smem_raw[];
+  T *src = reinterpret_cast<T *>(smem_raw);
+  T *part_sum = src + p;  // [parts][rows]
+  const int r0 = blockIdx.y * rows;
+  int i = blockIdx.x;
+  if (only_seg > 0) i = (only_seg + 1) * L - 1 < n - 1 ? (only_seg + 1) * L - 1 : n - 1;  // that segment's last
+  const int c = i / L;
+  if (c == 0 || i >= n) return;
+  const int last = (c + 1) * L - 1 < n - 1 ? (c + 1) * L - 1 : n - 1;
+  if (only_seg == 0 && i == last) return;
+  const long long si = reverse ? (long long)(n - 1 - i) : i;
+  const int j = c * L - 1;
+  const long long sj = reverse ? (long long)(n - 1 - j) : j;
+  for (int r = threadIdx.x; r < p; r += blockDim.x) src[r] = x[sj * p + r];
+  __syncthreads();
+  const T *Qi = Q + (long long)i * p * p + r0;
+  const int r = threadIdx.x % rows, part = threadIdx.x / rows;
+  if (part < parts) {
+    const int k0 = part * p / parts, k1 = (part + 1) * p / parts;
+    T acc = T(0);
+#pragma unroll 8
+    for (int k = k0; k < k1; ++k) acc = fma(Qi[(long long)k * p + r], src[k], acc);
+    part_sum[part * rows + r] = acc;
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
+    T acc = x[si * p + r0 + rr];
+    for (int q = 0; q < parts; ++q) acc += part_sum[q * rows + rr];
+    x[si * p + r0 + rr] = acc;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // SGS chains as a parallel scan in time.  A chain x_i = xhat_i + A_i x_{i-1}

@@ -354,7 +354,7 @@ def mg_jacobi_radius(h, level: int = 0, iters: int = 4000, stream: int = 0) -> f
     return rho.value
 
 
-SGS_CHAINS = ("scan", "cluster", "serial")
+SGS_CHAINS = ("scan", "cluster", "serial", "segmented")
 
 
 def mg_autotune(h, stream: int = 0):

@@ -179,7 +179,7 @@ def test_fp32_preconditioned_fgmres_reaches_fp64_solution(P, case):
         P.mg_destroy(h)
 
 
-@pytest.mark.parametrize("chain", ["scan", "cluster", "serial"])
+@pytest.mark.parametrize("chain", ["scan", "cluster", "serial", "segmented"])
 def test_sgs_chain_variants_full_size_vcycle(P, chain, monkeypatch):
     """Bench-sized coarse grid (257 blocks, p = 128) through each SGS chain
     implementation (parallel scan, 16-SM cluster, one CTA): the V-cycle agrees
@@ -436,3 +436,19 @@ def test_few_time_blocks(P, nx, n, levels):
     x, info = _solve_x(P, prob, dict(levels=levels, nu_pre=2, nu_post=2))
     xd = O.direct_solve(prob)
     assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("n,precision", [(64, 0), (100, 0), (64, 1)])
+def test_segmented_sgs_chains_reach_the_solution(P, monkeypatch, n, precision):
+    """SGS chains as concurrent segment chains joined by the in-segment products (4 to 6 segments here, the
+    last one shorter when n is not a multiple), as GMRES + SGS without multigrid, against the direct solve."""
+    monkeypatch.setenv("PINTMG_SGS_CHAIN", "segmented")
+    prob = W.burgers(nx=64, n=n, seed=191)
+    x, info = _solve_x(P, prob, dict(levels=1, precision=precision), restart=60)
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+    h = P.mg_setup(prob, levels=1, precision=precision)
+    try:
+        assert P.mg_autotune(h)[0] == "segmented"       # a forced chain is kept
+    finally:
+        P.mg_destroy(h)

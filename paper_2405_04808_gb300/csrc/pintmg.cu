@@ -1686,7 +1686,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
         const double seg_bytes = 2.0 * (double)nl * p * p * sizeof(double);
         if (layout == MG_LAYOUT_TRIDIAG && p >= 32 && nl >= 32 && seg_bytes <= 8.0 * (1 << 30) &&
             (lev.d.scanF.empty() || h->force_seg)) {
-          const int nseg = std::min(8, nl / 16);
+          const int nseg = std::min(16, nl / 16);
           const int L = (nl + nseg - 1) / nseg;
           lev.d.seg_len = L;
           lev.d.segF = h->mem.alloc<double>((size_t)nl * p * p);

@@ -50,6 +50,8 @@ def parse():
                     help="fp32: V-cycle in FP32; fp32s: smoother and transfers in FP32, coarse solve in FP64")
     ap.add_argument("--restart", type=int, default=None,
                     help="FGMRES restart length (default: the workload's, from a sweep of solve times)")
+    ap.add_argument("--krylov-basis", default="pair", choices=["pair", "fp64"],
+                    help="FGMRES basis storage: FP32 pairs with compensated dot products (default) or FP64")
     ap.add_argument("--omega", type=float, default=1.0,
                     help="block-Jacobi relaxation weight; 1 is the paper's sweep (Eq. jacobi-aj)")
     ap.add_argument("--maxit", type=int, default=2000)
@@ -188,7 +190,8 @@ def roofline(prof, dominant, precision, workload=None):
             "achieved_tflops": round(fl, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", **common}
 
 
-def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stream, world, want_e2e, levels=None):
+def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stream, world, want_e2e, levels=None,
+            basis=None):
     """Per-kernel shares and the roofline from one event-bracketed, host-driven
     solve (kernels inside a captured graph cannot be bracketed); then warm-up,
     `steps` timed solves and the end-to-end solves in the timed mode
@@ -201,7 +204,8 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
 
     def setup(device_loops):
         return P.mg_setup(prob, levels=lv, nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], precision=prec,
-                          omega=omega, device_loops=device_loops, stream=stream)
+                          omega=omega, device_loops=device_loops, krylov_basis=basis or args.krylov_basis,
+                          stream=stream)
 
     def solve(h, bp, xp):
         code, info = P.fgmres_solve(h, bp, xp, RTOL, args.maxit, args.restart, stream)
@@ -445,22 +449,25 @@ def run_native(args):
         # (name, precision, omega, levels): the mixed-precision V-cycle, relaxed sweeps (an option
         # outside the paper), and the paper's serial baseline of Sec. 6.3 (SGS-GMRES, no multigrid),
         # whose block Gauss-Seidel chains run here as a parallel scan in time
-        for name, prec, om, lv in (("fp32_vcycle", "fp32", args.omega, None),
-                                   ("fp32_smoother_fp64_coarse", "fp32s", args.omega, None),
-                                   ("omega0.7_fp64", "fp64", 0.7, None),
-                                   ("omega0.7_fp32_vcycle", "fp32", 0.7, None),
-                                   ("omega0.7_fp32_smoother_fp64_coarse", "fp32s", 0.7, None),
-                                   ("sgs_gmres_no_multigrid", "fp64", 1.0, 1)):
-            if prec == args.precision and om == args.omega and lv is None:
+        other = "fp64" if args.krylov_basis == "pair" else "pair"
+        for name, prec, om, lv, kb in ((f"{other}_krylov_basis", args.precision, args.omega, None, other),
+                                       ("fp32_vcycle", "fp32", args.omega, None, None),
+                                       ("fp32_smoother_fp64_coarse", "fp32s", args.omega, None, None),
+                                       ("omega0.7_fp64", "fp64", 0.7, None, None),
+                                       ("omega0.7_fp32_vcycle", "fp32", 0.7, None, None),
+                                       ("omega0.7_fp32_smoother_fp64_coarse", "fp32s", 0.7, None, None),
+                                       ("sgs_gmres_no_multigrid", "fp64", 1.0, 1, None)):
+            if prec == args.precision and om == args.omega and lv is None and kb is None:
                 continue
             v = measure(P, torch, prob, wl, args, prec, om, max(1, min(args.steps, 3)), 1, dev, stream, world, False,
-                        levels=lv)
+                        levels=lv, basis=kb)
             # the variant's solution against the headline solve's (both to a 1e-8 relative residual)
             xdiff = float(torch.linalg.vector_norm(v["x"] - main["x"]) / torch.linalg.vector_norm(main["x"]))
             variants[name] = {"value": round(v["value"], 4), "unit": UNIT, "ms_per_step": round(v["ms_per_step"], 3),
                               "fgmres_iters": v["iters"][0], "true_relres": v["true_relres"],
                               "solution_rel_diff_vs_main": xdiff,
                               "precision": prec, "omega": om, "levels": lv or wl["levels"],
+                              "krylov_basis": kb or args.krylov_basis,
                               "coarse_iters_per_vcycle": round(v["coarse_iters_per_vcycle"], 3),
                               "setup_ms": round(v["setup_ms"], 1),
                               "dominant_kernel": v["dominant"], "roofline_frac": v["roofline"].get("frac")}
@@ -475,6 +482,9 @@ def run_native(args):
         "config": {"workload": args.workload, "n": prob.n, "p": prob.p, "q": prob.q,
                    "levels": wl["levels"], "nu_pre": wl["nu_pre"], "nu_post": wl["nu_post"],
                    "unknowns": prob.size, "rtol": RTOL, "restart": args.restart, "precision": args.precision,
+                   "krylov_basis": ("FP64 entries rounded to ~48 bits as FP32 pairs; compensated (Dot2) dot products "
+                                    "and axpys against them, FP64 reductions" if args.krylov_basis == "pair"
+                                    else "FP64"),
                    "omega": args.omega, "l2": "flushed (512 MB write) before every timed step",
                    "solve": "host-driven loops" if args.host_loops else
                             "one CUDA graph per solve (FGMRES and coarse GMRES loops as conditional nodes)",

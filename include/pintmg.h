@@ -36,6 +36,8 @@ typedef enum {
   MG_ERR_BREAKDOWN = -3,  /* Arnoldi produced a non-finite Hessenberg entry */
   MG_ERR_CUDA = -4,       /* a CUDA runtime call failed; mg_last_cuda_error() names it */
   MG_ERR_OOM = -5,        /* device allocation failed */
+  MG_ERR_TIMEOUT = -6,    /* a bounded device-side wait ran out (the copy pipeline of a streaming kernel);
+                             the solve's outputs are not valid */
   MG_ERR_NONFINITE = -7,  /* NaN or Inf in the problem data or right-hand side */
   MG_ERR_UNSUPPORTED = -8 /* a valid request this build does not implement (e.g. p too large for the dense layout) */
 } mg_status;
@@ -52,6 +54,20 @@ typedef enum {
   MG_PRECISION_FP32_SMOOTH = 2  /* smoother and transfers in FP32; the coarse solve (GMRES and its SGS), FGMRES
                                    and true residual in FP64 */
 } mg_precision;
+
+/*
+ * Storage of the FGMRES Krylov basis v_0..v_m (the vectors CGS2 orthogonalises
+ * against, Sec. 5.3.4 / Saad 1993).  The preconditioned vectors z_j, the
+ * solution and the true residual stay FP64 in both modes.
+ */
+typedef enum {
+  MG_BASIS_FP64 = 0,  /* FP64 vectors; dot products and axpys in FP64 */
+  MG_BASIS_PAIR = 1   /* each entry as two FP32 values hi + lo (the FP64 value rounded to ~48 bits, 8 bytes);
+                         dot products and axpys against the basis in compensated FP32 arithmetic (error-free
+                         products and sums of Ogita, Rump and Oishi's Dot2) with FP64 reductions, about 1.5x
+                         faster on GB300, whose FP64 rate bounds the FP64 kernels; requires an even vector
+                         length n (4p+q), else the FP64 basis is used */
+} mg_krylov_basis;
 
 /*
  * Problem data (Eq. blocks-aj and Sec. 5.1).  All pointers are HOST memory,
@@ -110,6 +126,7 @@ typedef struct {
                              conditional nodes decided on the device (one host read-back per solve);
                              0: loops driven from the host (a few scalars read back per iteration).
                              Same arithmetic either way. */
+  int krylov_basis;       /* mg_krylov_basis of the FGMRES basis */
 } mg_options;
 
 typedef struct {
@@ -154,7 +171,8 @@ int mg_vcycle(mg_handle *h, const double *r, double *y, void *stream);
  * host buffers are staged through the handle's device memory on `stream`.
  * info (may be NULL) receives the counters and the FP64 true residual.
  * Returns MG_OK, MG_NOT_CONVERGED, MG_ERR_NONFINITE (b has NaN/Inf),
- * MG_ERR_BREAKDOWN, MG_ERR_ARG or MG_ERR_CUDA.  Synchronises `stream`.
+ * MG_ERR_BREAKDOWN, MG_ERR_TIMEOUT, MG_ERR_ARG or MG_ERR_CUDA.  Synchronises
+ * `stream`.
  */
 int fgmres_solve(mg_handle *h, const double *b, double *x, double rtol, int maxit, int restart,
                  mg_solve_info *info, void *stream);

@@ -19,6 +19,7 @@
 
 #include "krylov_kernels.cuh"
 #include "learned_kernels.cuh"
+#include "pair_kernels.cuh"
 #include "setup_kernels.cuh"
 #include "vcycle_kernels.cuh"
 
@@ -154,6 +155,7 @@ struct mg_handle {
   int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
   int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
   int pair_tri = 1;     // levels with few blocks: two warps per block
+  int pair_basis = 0;   // the FGMRES basis as FP32 pairs with compensated dot products (MG_BASIS_PAIR)
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -195,9 +197,10 @@ namespace {
 
 // kernel categories reported by mg_profile_read
 enum Cat { CAT_BLOCK_SOLVE = 0, CAT_APPLY, CAT_RESTRICT, CAT_PROLONG, CAT_CHAIN, CAT_DOT, CAT_AXPY, CAT_SMALL,
-           CAT_CONVERT, CAT_SETUP, CAT_NET, CAT_COUNT };
+           CAT_CONVERT, CAT_SETUP, CAT_NET, CAT_PAIR_DOT, CAT_PAIR_AXPY, CAT_COUNT };
 const char *kCatNames[CAT_COUNT] = {"block_solve", "apply", "residual_restrict", "prolong_add", "sgs_chain",
-                                    "multidot", "axpy_scale", "arnoldi_scalar", "convert", "setup", "net_coarse"};
+                                    "multidot", "axpy_scale", "arnoldi_scalar", "convert", "setup", "net_coarse",
+                                    "pair_dot", "pair_axpy"};
 
 cudaEvent_t take_event(mg_handle *h) {
   if (h->ev_pool.empty()) {
@@ -458,9 +461,69 @@ void read_scal(mg_handle *h, const mg_handle::Krylov &K, cudaStream_t s) {
 // Classical Gram-Schmidt twice (CGS2) of w against V_0..V_j: h (j+1) and
 // |w|^2 (nrm2, accumulated inside the second axpy) on the device.
 // (m_dev: the count j + 1 lives on the device, j is then its upper bound - 1)
-void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
+// the TMA-streamed multi-dot kernel of the pair basis: 8 vectors per item,
+// 3 stages, 2 CTAs per SM
+constexpr int kPairVB = 8, kPairNS = 3, kPairCtas = 2;
+void pair_prepare() {
+  static unsigned done = 0;
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  if (dev < 32 && (done >> dev) & 1u) return;
+  ck(cudaFuncSetAttribute(k_multidot_pair_tma<kPairVB, kPairNS, kPairCtas>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_tma_smem<kPairVB, kPairNS>()));
+  if (dev < 32) done |= 1u << dev;
+}
+
+// out = Vp^T w over the m pair vectors (out[i] for i < m), fixed order
+void multidot_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const double *w, long long len, double *out,
                    cudaStream_t s, const int *m_dev = nullptr) {
+  const int items = ((m + kPairVB - 1) / kPairVB) * dot_parts(m, kPairVB, len);
+  const int grid = std::min(items, kPairCtas * 152);
+  {
+    Bracket br(h, CAT_PAIR_DOT, s, 8.0 * (m + 1) * len, 2.0 * m * len);
+    k_multidot_pair_tma<kPairVB, kPairNS, kPairCtas><<<grid, kPairTmaThreads, pair_tma_smem<kPairVB, kPairNS>(), s>>>(
+        Vp, ldv, m, w, len, h->partial, nullptr, m_dev, h->flag + 2);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, 0, m, out, 0, nullptr, m_dev, kPairVB, len);
+    ck_launch();
+  }
+}
+
+// CGS2 against the basis V (FP64) or Vp (pairs, when not null): K.h = the
+// coefficients, K.nrm2 = ||w||^2 of the orthogonalised w
+void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
+                   cudaStream_t s, const int *m_dev = nullptr, const float2 *Vp = nullptr) {
   const int m = j + 1;
+  if (Vp) {
+    const int G = grid_for(len / 2, kDotThreads, kDotGridCap);
+    multidot_pair(h, Vp, len, m, w, len, K.h, s, m_dev);
+    {
+      Bracket br(h, CAT_PAIR_AXPY, s, 8.0 * (m + 2) * len, 2.0 * m * len);
+      k_multi_axpy_pair<false><<<G, kDotThreads, 0, s>>>(w, Vp, len, K.h, m, -1.0, len, nullptr, nullptr, m_dev);
+      ck_launch();
+    }
+    multidot_pair(h, Vp, len, m, w, len, K.h + 512, s, m_dev);
+    {
+      Bracket br(h, CAT_PAIR_AXPY, s, 8.0 * (m + 2) * len, 2.0 * (m + 1) * len);
+      k_multi_axpy_pair<true><<<G, kDotThreads, 0, s>>>(w, Vp, len, K.h + 512, m, -1.0, len, h->partial, nullptr,
+                                                         m_dev);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_SMALL, s);
+      k_reduce_partials<<<1, 128, 0, s>>>(h->partial, G, 1, K.nrm2, 0);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_SMALL, s);
+      k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m, nullptr, m_dev);
+      ck_launch();
+    }
+    return;
+  }
   multidot(h, V, len, m, w, len, K.h, 0, s, nullptr, m_dev);
   multi_axpy(h, w, V, len, K.h, m, -1.0, len, s, nullptr, m_dev);
   multidot(h, V, len, m, w, len, K.h + 512, 0, s, nullptr, m_dev);
@@ -498,8 +561,8 @@ void norm_into(mg_handle *h, mg_handle::Krylov &K, const double *x, long long le
 
 // Arnoldi step with the index j on the device (st->j, st->m1): no read-back
 void arnoldi_step_dev(mg_handle *h, mg_handle::Krylov &K, KState *st, int jmax, double *V, long long len, double *w,
-                      cudaStream_t s) {
-  orthogonalise(h, K, V, len, jmax, w, s, &st->m1);
+                      cudaStream_t s, float2 *Vp = nullptr) {
+  orthogonalise(h, K, V, len, jmax, w, s, &st->m1, Vp);
   {
     Bracket br(h, CAT_SMALL, s);
     k_arnoldi_step<<<1, kWarp, 0, s>>>(0, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal, &st->j);
@@ -507,7 +570,10 @@ void arnoldi_step_dev(mg_handle *h, mg_handle::Krylov &K, KState *st, int jmax, 
   }
   {
     Bracket br(h, CAT_AXPY, s);
-    k_scale<<<grid_for(len, 256), 256, 0, s>>>(V, w, K.scal + 1, len, &st->j, 1);
+    if (Vp)
+      k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, w, K.scal + 1, len, &st->j, 1);
+    else
+      k_scale<<<grid_for(len, 256), 256, 0, s>>>(V, w, K.scal + 1, len, &st->j, 1);
     ck_launch();
   }
 }
@@ -547,8 +613,9 @@ cudaGraphConditionalHandle new_handle(cudaStream_t s) {
 }
 
 // one Arnoldi step on basis V (column stride len): w = A z_j already in w
-void arnoldi_step(mg_handle *h, mg_handle::Krylov &K, double *V, long long len, int j, double *w, cudaStream_t s) {
-  orthogonalise(h, K, V, len, j, w, s);
+void arnoldi_step(mg_handle *h, mg_handle::Krylov &K, double *V, long long len, int j, double *w, cudaStream_t s,
+                  float2 *Vp = nullptr) {
+  orthogonalise(h, K, V, len, j, w, s, nullptr, Vp);
   {
     Bracket br(h, CAT_SMALL, s);
     k_arnoldi_step<<<1, kWarp, 0, s>>>(j, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal);
@@ -556,7 +623,10 @@ void arnoldi_step(mg_handle *h, mg_handle::Krylov &K, double *V, long long len, 
   }
   {
     Bracket br(h, CAT_AXPY, s);
-    k_scale<<<grid_for(len, 256), 256, 0, s>>>(V + (long long)(j + 1) * len, w, K.scal + 1, len);
+    if (Vp)
+      k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp + (long long)(j + 1) * len, w, K.scal + 1, len);
+    else
+      k_scale<<<grid_for(len, 256), 256, 0, s>>>(V + (long long)(j + 1) * len, w, K.scal + 1, len);
     ck_launch();
   }
   read_scal(h, K, s);
@@ -1203,7 +1273,7 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
   KState *st = h->kst_f;
   {
     h->launches = 0;
-    ck(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
+    ck(cudaMemsetAsync(h->flag + 1, 0, 2 * sizeof(int), s));
     {
       Bracket br(h, CAT_SMALL, s);
       k_check_finite<<<grid_for(len, 256), 256, 0, s>>>(b, len, h->flag + 1);
@@ -1211,6 +1281,7 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
     }
     ck(cudaMemsetAsync(x, 0, len * sizeof(double), s));
     norm_into(h, K, b, len, s);
+    float2 *Vp = h->pair_basis ? reinterpret_cast<float2 *>(h->fV) : nullptr;
     const cudaGraphConditionalHandle hdl = new_handle(s);
     {
       Bracket br(h, CAT_SMALL, s);
@@ -1219,7 +1290,10 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
     }
     {
       Bracket br(h, CAT_AXPY, s);
-      k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, b, K.scal + 1, len);
+      if (Vp)
+        k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, b, K.scal + 1, len);
+      else
+        k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, b, K.scal + 1, len);
       ck_launch();
     }
     {
@@ -1233,7 +1307,10 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
     add_while(h, s, hdl, h->cap[1], [&](cudaStream_t bs) {
       {
         Bracket br(h, CAT_SMALL, bs);
-        k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->vin, h->fV, len, &st->j, 0);
+        if (Vp)
+          k_join_basis<<<grid_for(len, 256), 256, 0, bs>>>(h->vin, Vp, len, &st->j);
+        else
+          k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->vin, h->fV, len, &st->j, 0);
         ck_launch();
       }
       const long long before = h->launches;
@@ -1246,7 +1323,7 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
         ck_launch();
       }
       launch_apply<double>(h, h->lv[0].d.view, h->zout, nullptr, h->fw, bs);
-      arnoldi_step_dev(h, K, st, m - 1, h->fV, len, h->fw, bs);
+      arnoldi_step_dev(h, K, st, m - 1, h->fV, len, h->fw, bs, Vp);
       {
         Bracket br(h, CAT_SMALL, bs);
         k_ctl_step<<<1, 1, 0, bs>>>(st, K.scal, m, maxit, 0, hdl);
@@ -1285,7 +1362,10 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
       }
       {
         Bracket br(h, CAT_AXPY, bs);
-        k_scale<<<grid_for(len, 256), 256, 0, bs>>>(h->fV, h->fr, K.scal + 1, len, nullptr, 0, &st->restart);
+        if (Vp)
+          k_split_basis<<<grid_for(len, 256), 256, 0, bs>>>(Vp, h->fr, K.scal + 1, len, nullptr, 0, &st->restart);
+        else
+          k_scale<<<grid_for(len, 256), 256, 0, bs>>>(h->fV, h->fr, K.scal + 1, len, nullptr, 0, &st->restart);
         ck_launch();
       }
       {
@@ -1411,6 +1491,7 @@ void mg_default_options(mg_options *o) {
   o->omega = 1.0;
   o->coarse_precond = MG_COARSE_SGS;
   o->device_loops = 1;
+  o->krylov_basis = MG_BASIS_PAIR;
 }
 
 const char *mg_status_string(int st) {
@@ -1422,6 +1503,7 @@ const char *mg_status_string(int st) {
     case MG_ERR_BREAKDOWN: return "Arnoldi breakdown (non-finite Hessenberg entry)";
     case MG_ERR_CUDA: return "CUDA runtime error";
     case MG_ERR_OOM: return "device out of memory";
+    case MG_ERR_TIMEOUT: return "a bounded device-side wait ran out";
     case MG_ERR_NONFINITE: return "NaN or Inf in the input";
     case MG_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown status";
@@ -1508,6 +1590,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (!(O->omega > 0.0 && O->omega <= 1.0)) return MG_ERR_ARG;
   if (O->coarse_precond < MG_COARSE_SGS || O->coarse_precond > MG_COARSE_BGS) return MG_ERR_ARG;
   if (O->device_loops != 0 && O->device_loops != 1) return MG_ERR_ARG;
+  if (O->krylov_basis != MG_BASIS_FP64 && O->krylov_basis != MG_BASIS_PAIR) return MG_ERR_ARG;
   if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;
@@ -1555,6 +1638,9 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   try {
     ck(cudaMallocHost(&h->host_scal, 4 * sizeof(double)));
     tri_stage_prepare();
+    // the pair basis streams two entries per 16-byte load: even vector lengths only
+    h->pair_basis = O->krylov_basis == MG_BASIS_PAIR && ((long long)n * (4 * p + q)) % 2 == 0;
+    if (h->pair_basis) pair_prepare();
     // raw data on the device (FP64)
     double *dM = h->mem.alloc<double>(msz);
     double *dJuc = h->mem.alloc<double>((size_t)n * msz);
@@ -1839,10 +1925,10 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       ck(cudaStreamSynchronize(s));
       ck(cudaGraphLaunch(h->gexec, s));
       KState fs{}, cs{};
-      int bad = 0;
+      int bad[2] = {0, 0};
       ck(cudaMemcpyAsync(&fs, h->kst_f, sizeof(KState), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(&cs, h->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
-      ck(cudaMemcpyAsync(&bad, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(bad, h->flag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(h->host_scal, h->kf.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
       if (h->net) ck(cudaMemcpyAsync(&h->coarse_learned, h->net_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
       if (!x_dev) ck(cudaMemcpyAsync(x_out, x, len * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1851,24 +1937,26 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       h->vcycles = fs.total;
       h->coarse_iters = (int)(cs.iters_all - before_c.iters_all);
       h->launches += h->g_init + h->g_body * fs.total + h->g_coarse * (cs.iters_all - before_c.iters_all);
-      if (bad) throw 1;
+      if (bad[0]) throw 1;
       const double bnorm = fs.bnorm;
       if (bnorm > 0.0) {
         true_rel = h->host_scal[0] / bnorm;
         est_rel = fs.est / bnorm;
         if (fs.breakdown) status = MG_ERR_BREAKDOWN;
         else if (!fs.converged) status = MG_NOT_CONVERGED;
+        if (bad[1]) status = MG_ERR_TIMEOUT;
       } else {
         est_rel = 0.0;
         true_rel = 0.0;
       }
     } else {
-    ck(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
+    ck(cudaMemsetAsync(h->flag + 1, 0, 2 * sizeof(int), s));
     {
       Bracket br(h, CAT_SMALL, s);
       k_check_finite<<<grid_for(len, 256), 256, 0, s>>>(b, len, h->flag + 1);
       ck_launch();
     }
+    float2 *Vp = h->pair_basis ? reinterpret_cast<float2 *>(h->fV) : nullptr;
     int bad = 0;
     ck(cudaMemcpyAsync(&bad, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     mg_handle::Krylov &K = h->kf;
@@ -1885,7 +1973,10 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
         norm_into(h, K, r, len, s);
         {
           Bracket br(h, CAT_AXPY, s);
-          k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, r, K.scal + 1, len);
+          if (Vp)
+            k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, r, K.scal + 1, len);
+          else
+            k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, r, K.scal + 1, len);
           ck_launch();
         }
         {
@@ -1897,9 +1988,15 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
         int k = 0;
         for (int j = 0; j < mm; ++j) {
           double *vj = h->fV + (long long)j * len, *zj = h->fZ + (long long)j * len;
+          if (Vp) {
+            Bracket br(h, CAT_SMALL, s);
+            k_join_basis<<<grid_for(len, 256), 256, 0, s>>>(h->vin, Vp + (long long)j * len, len);
+            ck_launch();
+            vj = h->vin;
+          }
           precondition(h, vj, zj, s);
           launch_apply<double>(h, h->lv[0].d.view, zj, nullptr, h->fw, s);
-          arnoldi_step(h, K, h->fV, len, j, h->fw, s);
+          arnoldi_step(h, K, h->fV, len, j, h->fw, s, Vp);
           k = j + 1;
           total++;
           const double est = h->host_scal[0], hj1 = h->host_scal[2];
@@ -1932,6 +2029,9 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       read_scal(h, K, s);
       true_rel = h->host_scal[0] / bnorm;
       if (status == MG_OK && est_rel > rtol) status = MG_NOT_CONVERGED;
+      int tmo = 0;
+      ck(cudaMemcpy(&tmo, h->flag + 2, sizeof(int), cudaMemcpyDeviceToHost));
+      if (tmo) status = MG_ERR_TIMEOUT;
     } else {
       est_rel = 0.0;
     }
@@ -2037,7 +2137,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
       for (int i = 0; i < count; ++i) hs[i]->gkey.b = nullptr;
     }
     std::vector<KState> before(count), fs(count), cs(count);
-    std::vector<int> bad(count), learned(count, 0);
+    std::vector<int> bad(2 * (size_t)count), learned(count, 0);
     std::vector<double> tr(4 * (size_t)count);
     for (int i = 0; i < count; ++i)
       ck(cudaMemcpyAsync(&before[i], hs[i]->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
@@ -2046,7 +2146,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
     for (int i = 0; i < count; ++i) {
       ck(cudaMemcpyAsync(&fs[i], hs[i]->kst_f, sizeof(KState), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(&cs[i], hs[i]->kst_c, sizeof(KState), cudaMemcpyDeviceToHost, s));
-      ck(cudaMemcpyAsync(&bad[i], hs[i]->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      ck(cudaMemcpyAsync(&bad[2 * (size_t)i], hs[i]->flag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       ck(cudaMemcpyAsync(&tr[4 * (size_t)i], hs[i]->kf.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
       if (hs[i]->net) ck(cudaMemcpyAsync(&learned[i], hs[i]->net_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
@@ -2057,7 +2157,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
       h->launches += h->g_init + h->g_body * fs[i].total + h->g_coarse * citers;
       int st = MG_OK;
       double est_rel = 0.0, true_rel = 0.0;
-      if (bad[i]) {
+      if (bad[2 * (size_t)i]) {
         st = MG_ERR_NONFINITE;
       } else if (fs[i].bnorm > 0.0) {
         true_rel = tr[4 * (size_t)i] / fs[i].bnorm;
@@ -2065,6 +2165,7 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
         if (fs[i].breakdown) st = MG_ERR_BREAKDOWN;
         else if (!fs[i].converged) st = MG_NOT_CONVERGED;
       }
+      if (bad[2 * (size_t)i + 1]) st = MG_ERR_TIMEOUT;
       if (infos) {
         infos[i].status = st;
         infos[i].iters = fs[i].total;

@@ -23,6 +23,7 @@ MG_ERR_SINGULAR = -2
 MG_ERR_BREAKDOWN = -3
 MG_ERR_CUDA = -4
 MG_ERR_OOM = -5
+MG_ERR_TIMEOUT = -6
 MG_ERR_NONFINITE = -7
 MG_ERR_UNSUPPORTED = -8
 
@@ -32,6 +33,8 @@ MG_PRECISION_FP64 = 0
 MG_PRECISION_FP32 = 1
 MG_PRECISION_FP32_SMOOTH = 2
 COARSE_PRECOND = {"sgs": 0, "jacobi": 1, "fgs": 2, "bgs": 3}
+#: storage of the FGMRES basis (mg_krylov_basis)
+KRYLOV_BASIS = {"fp64": 0, "pair": 1}
 
 #: every symbol include/pintmg.h declares
 EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmres_solve_batched",
@@ -55,7 +58,8 @@ class MGOptions(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("coarse_rtol", ctypes.c_double), ("coarse_maxit", ctypes.c_int),
                 ("coarse_fixed_iters", ctypes.c_int), ("end_rule", ctypes.c_int), ("precision", ctypes.c_int),
-                ("omega", ctypes.c_double), ("coarse_precond", ctypes.c_int), ("device_loops", ctypes.c_int)]
+                ("omega", ctypes.c_double), ("coarse_precond", ctypes.c_int), ("device_loops", ctypes.c_int),
+                ("krylov_basis", ctypes.c_int)]
 
 
 class MGSolveInfo(ctypes.Structure):
@@ -157,8 +161,9 @@ def _c(arr):
 
 def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit=50,
              coarse_fixed_iters=0, end_rule=0, precision=MG_PRECISION_FP64, omega=1.0, coarse_precond="sgs",
-             device_loops=True, stream=0):
-    """Build the device hierarchy for a workloads.Problem; returns an opaque handle (int)."""
+             device_loops=True, krylov_basis="pair", stream=0):
+    """Build the device hierarchy for a workloads.Problem; returns an opaque handle (int).
+    krylov_basis: "pair" (FP32-pair basis with compensated dot products) or "fp64"."""
     keep = []
     P = MGProblem()
     P.layout = MG_LAYOUT_TRIDIAG if prob.kind == "tridiag" else MG_LAYOUT_DENSE
@@ -170,7 +175,7 @@ def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit
         keep.append(a)
         setattr(P, name, ptr)
     o = MGOptions(levels, nu_pre, nu_post, coarse_rtol, coarse_maxit, coarse_fixed_iters, end_rule, precision, omega,
-                  COARSE_PRECOND[coarse_precond], 1 if device_loops else 0)
+                  COARSE_PRECOND[coarse_precond], 1 if device_loops else 0, KRYLOV_BASIS[krylov_basis])
     h = ctypes.c_void_p()
     code = lib().mg_setup(ctypes.byref(P), ctypes.byref(o), ctypes.c_void_p(stream), ctypes.byref(h))
     if code != MG_OK:
@@ -215,7 +220,7 @@ def mg_launch_count(h) -> int:
 
 PROFILE_ALL = 0xFFFF
 PROFILE_CATEGORIES = ("block_solve", "apply", "residual_restrict", "prolong_add", "sgs_chain", "multidot",
-                      "axpy_scale", "arnoldi_scalar", "convert", "setup", "net_coarse")
+                      "axpy_scale", "arnoldi_scalar", "convert", "setup", "net_coarse", "pair_dot", "pair_axpy")
 
 
 def mg_profile_enable(h, mask: int = PROFILE_ALL) -> None:

@@ -238,8 +238,9 @@ def test_table1_coarse_preconditioners(P, kind, levels):
 
 # ---------------------------------------------------------------- device-side loops
 
+@pytest.mark.parametrize("basis", ["pair", "fp64"])
 @pytest.mark.parametrize("case,restart", [(0, 7), (4, 9), (8, 7), (9, 5)])
-def test_graph_solve_equals_host_loop(P, case, restart):
+def test_graph_solve_equals_host_loop(P, case, restart, basis):
     """A solve captured as one CUDA graph (FGMRES and coarse GMRES loops as
     conditional nodes) runs the same kernels in the same order as the host-driven
     loop: identical iterations and bitwise-identical solutions, also across a
@@ -249,7 +250,7 @@ def test_graph_solve_equals_host_loop(P, case, restart):
     xs, its = [], []
     for loops in (False, True):
         h = P.mg_setup(prob, levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule, omega=omega,
-                       device_loops=loops)
+                       device_loops=loops, krylov_basis=basis)
         try:
             b = _dev(prob.b)
             for rep in range(2):
@@ -336,7 +337,7 @@ def _solve_x(P, prob, settings, restart=60, rtol=1e-10):
 def test_dot_blocking_is_bitwise_neutral(P, monkeypatch):
     """4, 8 or 16 basis vectors per dot-product CTA: the same partial sums in the same order."""
     prob = W.burgers(nx=40, n=32, seed=151)
-    settings = dict(levels=2, nu_pre=2, nu_post=2)
+    settings = dict(levels=2, nu_pre=2, nu_post=2, krylov_basis="fp64")
     xs = []
     for vb in ("4", "8", "16"):
         monkeypatch.setenv("PINTMG_DOT_VB", vb)
@@ -344,6 +345,41 @@ def test_dot_blocking_is_bitwise_neutral(P, monkeypatch):
     for x, info in xs[1:]:
         assert info.iters == xs[0][1].iters
         assert np.array_equal(x, xs[0][0])
+
+
+@pytest.mark.parametrize("case", [0, 1, 3, 4, 5, 7, 8])
+def test_pair_basis_reaches_the_direct_solution(P, case):
+    """The FGMRES basis as FP32 pairs with compensated dot products and axpys
+    (the default) against the FP64 basis: both reach the direct solution to the
+    solve tolerance, with iteration counts within one of each other (the basis
+    is stored to ~48 bits, the Gram-Schmidt sums to about the same precision)."""
+    make, levels, nu_pre, nu_post, end_rule, omega = _unpack(case)
+    prob = make()
+    assert prob.size % 2 == 0
+    xd = O.direct_solve(prob)
+    res = {}
+    for basis in ("pair", "fp64"):
+        x, info = _solve_x(P, prob, dict(levels=levels, nu_pre=nu_pre, nu_post=nu_post, end_rule=end_rule,
+                                         omega=omega, krylov_basis=basis))
+        assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd), basis
+        assert info.true_relres <= 2e-10, (basis, info.true_relres)
+        res[basis] = (x, info.iters)
+    assert abs(res["pair"][1] - res["fp64"][1]) <= 1
+    assert np.linalg.norm(res["pair"][0] - res["fp64"][0]) <= SOLVE_RTOL * np.linalg.norm(xd)
+
+
+def test_pair_basis_over_many_multidot_chunks(P):
+    """A vector long enough that the streamed multi-dot splits it into many
+    chunks of several pipeline stages each, with a ragged last stage
+    (n (4p + q) = 64 * 5 * 130 = 41,600 entries), unrestarted and across
+    restarts.  The oracle's FGMRES needs 70 iterations at restart 40 and 174
+    at restart 25 (at restart 9 it stagnates)."""
+    prob = W.burgers(nx=130, n=64, seed=154)
+    xd = O.direct_solve(prob)
+    for restart, oracle_iters in ((40, 70), (25, 174)):
+        x, info = _solve_x(P, prob, dict(levels=3, nu_pre=2, nu_post=2), restart=restart)
+        assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+        assert abs(info.iters - oracle_iters) <= 3, (restart, info.iters)
 
 
 @pytest.mark.parametrize("n,levels", [(7, 1), (9, 1), (1, 1)])

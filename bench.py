@@ -154,6 +154,8 @@ FP32_TFLOPS_MEASURED = 74.2
 # valid while the kernel is unchanged since that capture
 TRAFFIC_RATIO = {
     ("burgers_nx128_n1024", "multidot", "fp64"): (1.00, "profiles/multidot_burgers_nx128_n1024.md"),
+    ("burgers_nx128_n1024", "pair_dot", "fp64"): (1.00, "profiles/multidot_pair_tma_burgers_nx128_n1024.md"),
+    ("burgers_nx128_n1024", "block_solve", "fp64"): (1.21, "profiles/block_solve_tri2_burgers_nx128_n1024.md"),
 }
 
 
@@ -259,6 +261,8 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
                "coarse_iters_per_vcycle": sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)),
                "setup_ms": setup_ms, "launches": launches, "shares": shares, "dominant": dominant,
                "roofline": roofline(shares, dominant, precision, args.workload if levels is None else None),
+               "category_rooflines": {k: roofline(shares, k, precision, args.workload if levels is None else None)
+                                      for k in shares if shares[k][1] and shares[k][2] > 0},
                "clocks": clk.summary()}
         if want_e2e:
             # end to end through the public API with pinned host buffers
@@ -496,6 +500,9 @@ def run_native(args):
         "e2e": main["e2e"],
         "gpu_launches": main["launches"],
         "roofline": main["roofline"],
+        "category_rooflines": {k: {"bound": v["bound"], "frac": v.get("frac"), "achieved": v.get("achieved"),
+                                   "unit": v.get("unit"), "avg_launch_us": v.get("avg_launch_us")}
+                               for k, v in main["category_rooflines"].items()},
         "kernel_shares": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in main["shares"].items() if v[1]},
         "variants": variants,
         "batched": batch,

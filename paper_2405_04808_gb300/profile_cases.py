@@ -1,10 +1,13 @@
-"""Small, self-contained GPU cases for kernel profiling (ncu) of the learned
+"""Small, self-contained GPU cases for kernel profiling (ncu): the learned
 coarse correction's kernels at the Burgers nx=256, nt=4096 coarse shape
-(5 x 512 x 256 per sample).
+(5 x 512 x 256 per sample), and a fixed-length FGMRES cycle whose basis
+outgrows L2 (Burgers nx=128, nt=256: 163,840 entries per vector, 121 basis
+vectors = 159 MB) for the Gram-Schmidt kernels.
 
     python -m paper_2405_04808_gb300.profile_cases conv_fwd_bf16
     python -m paper_2405_04808_gb300.profile_cases conv_fwd_fp32
     python -m paper_2405_04808_gb300.profile_cases train_step
+    python -m paper_2405_04808_gb300.profile_cases fgmres_cycle [--basis pair|fp64]
 
 Each case runs a warm-up and then `--reps` launches of the kernels it names,
 and exits non-zero on any library error.
@@ -56,14 +59,31 @@ def main(argv=None):
         print(summarize(argv[1]))
         return 0
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step"])
+    ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step", "fgmres_cycle"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--basis", default="pair", choices=["pair", "fp64"])
     args = ap.parse_args(argv)
     import torch
 
     from . import pintmg as P
     from . import workloads as W
+    if args.case == "fgmres_cycle":
+        # 120 FGMRES iterations without restart (tolerance out of reach): the
+        # basis grows to 121 vectors; host-driven loops launch each kernel alone
+        prob = W.burgers(nx=128, n=256, seed=2100)
+        h = P.mg_setup(prob, levels=3, nu_pre=4, nu_post=4, device_loops=False, krylov_basis=args.basis)
+        try:
+            b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+            x = torch.empty_like(b)
+            code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-300, 120, 120)
+            torch.cuda.synchronize()
+            if code not in (P.MG_OK, P.MG_NOT_CONVERGED):
+                raise P.PintmgError(code, "fgmres_solve")
+            print(f"fgmres_cycle ({args.basis}): {info.iters} iterations, relres {info.relres:.2e}")
+        finally:
+            P.mg_destroy(h)
+        return 0
     T, X = 512, 256
     net = P.mg_net_create(W.net_init_params(1).astype(np.float32))
     try:

@@ -50,8 +50,9 @@ def parse():
                     help="fp32: V-cycle in FP32; fp32s: smoother and transfers in FP32, coarse solve in FP64")
     ap.add_argument("--restart", type=int, default=None,
                     help="FGMRES restart length (default: the workload's, from a sweep of solve times)")
-    ap.add_argument("--krylov-basis", default="pair", choices=["pair", "fp64"],
-                    help="FGMRES basis storage: FP32 pairs with compensated dot products (default) or FP64")
+    ap.add_argument("--krylov-basis", default="fp64", choices=["fp64", "pair"],
+                    help="FGMRES basis storage: FP64 (the plain method, default) or FP32 pairs with compensated "
+                         "dot products (an option: ~48-bit basis)")
     ap.add_argument("--omega", type=float, default=1.0,
                     help="block-Jacobi relaxation weight; 1 is the paper's sweep (Eq. jacobi-aj)")
     ap.add_argument("--maxit", type=int, default=2000)

@@ -61,7 +61,7 @@ typedef enum {
  * solution and the true residual stay FP64 in both modes.
  */
 typedef enum {
-  MG_BASIS_FP64 = 0,  /* FP64 vectors; dot products and axpys in FP64 */
+  MG_BASIS_FP64 = 0,  /* FP64 vectors; dot products and axpys in FP64 (the default) */
   MG_BASIS_PAIR = 1   /* each entry as two FP32 values hi + lo (the FP64 value rounded to ~48 bits, 8 bytes);
                          dot products and axpys against the basis in compensated FP32 arithmetic (error-free
                          products and sums of Ogita, Rump and Oishi's Dot2) with FP64 reductions, about 1.5x

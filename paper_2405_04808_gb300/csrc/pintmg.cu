@@ -1491,7 +1491,7 @@ void mg_default_options(mg_options *o) {
   o->omega = 1.0;
   o->coarse_precond = MG_COARSE_SGS;
   o->device_loops = 1;
-  o->krylov_basis = MG_BASIS_PAIR;
+  o->krylov_basis = MG_BASIS_FP64;
 }
 
 const char *mg_status_string(int st) {

@@ -161,9 +161,9 @@ def _c(arr):
 
 def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit=50,
              coarse_fixed_iters=0, end_rule=0, precision=MG_PRECISION_FP64, omega=1.0, coarse_precond="sgs",
-             device_loops=True, krylov_basis="pair", stream=0):
+             device_loops=True, krylov_basis="fp64", stream=0):
     """Build the device hierarchy for a workloads.Problem; returns an opaque handle (int).
-    krylov_basis: "pair" (FP32-pair basis with compensated dot products) or "fp64"."""
+    krylov_basis: "fp64" (the plain method) or "pair" (FP32-pair basis with compensated dot products)."""
     keep = []
     P = MGProblem()
     P.layout = MG_LAYOUT_TRIDIAG if prob.kind == "tridiag" else MG_LAYOUT_DENSE

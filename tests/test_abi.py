@@ -32,7 +32,7 @@ def test_library_exports_declared_symbols():
     o = P.mg_default_options()
     assert (o.levels, o.nu_pre, o.nu_post, o.coarse_maxit) == (2, 1, 1, 50)
     assert abs(o.coarse_rtol - 1e-3) < 1e-18
-    assert o.krylov_basis == P.KRYLOV_BASIS["pair"] and o.device_loops == 1
+    assert o.krylov_basis == P.KRYLOV_BASIS["fp64"] and o.device_loops == 1
     assert P.mg_status_string(P.MG_ERR_TIMEOUT).startswith("a bounded device-side wait")
 
 

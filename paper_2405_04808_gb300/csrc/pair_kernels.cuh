@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_pair(double *y, cons
 constexpr int kPairStageLen = 512;     // entries per stage (two per consumer thread)
 constexpr int kPairConsumers = 8;      // consumer warps
 constexpr int kPairTmaThreads = (kPairConsumers + 1) * kWarp;
-constexpr long long kPairWaitLimit = 1ll << 22;  // polls of an mbarrier before giving up
+constexpr unsigned long long kPairWaitNs = 2000000000ull;  // longest wait on an mbarrier (2 s) before giving up
 
 // chunk length of the TMA multi-dot partition: the vectors' length in G
 // contiguous even-length chunks (the last may be shorter or empty)
@@ -199,10 +199,17 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
                "r"(bytes)
                : "memory");
 }
-// wait until the phase with the given parity has completed; false after kPairWaitLimit polls
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+// wait until the phase with the given parity has completed; false once
+// kPairWaitNs have passed (checked every 64 polls)
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
   const unsigned a = smem_addr(bar);
-  for (long long it = 0; it < kPairWaitLimit; ++it) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -210,8 +217,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 63u) == 0 && global_ns() - t0 > kPairWaitNs) return false;
   }
-  return false;
 }
 // bulk copy of bytes (a multiple of 16, both addresses 16-byte aligned) into shared memory
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar,
@@ -229,12 +236,14 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 // pair_tma_smem<VB>(); blockDim = kPairTmaThreads.  Each consumer warp keeps a
 // running scale 2^(emax - 1023) for its entries of w (emax: the largest FP64
 // exponent seen so far); when a stage raises it, the FP32 accumulators are
-// rescaled by the (exact) power of two.
+// rescaled by the (exact) power of two.  A wait that runs out sets err[0];
+// later launches with err[0] set return at once.
 template <int VB, int NS, int kMinBlocks>
 __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
     k_multidot_pair_tma(const float2 *__restrict__ V, long long ldv, int m, const double *__restrict__ w, long long len,
-                        double *partial, const int *gate, const int *m_dev, int *err) {
+                        double *partial, const int *gate, const int *m_dev, int *err, int stall = 0) {
   if (gate && *gate == 0) return;
+  if (*(volatile int *)err) return;  // an earlier launch of this solve timed out: its results are void anyway
   if (m_dev) m = *m_dev;
   extern __shared__ __align__(128) unsigned char pair_smem[];
   float2 *sv = reinterpret_cast<float2 *>(pair_smem);  // [stage][VB][kPairStageLen]
@@ -257,7 +266,9 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
   }
   __syncthreads();
   if (wp == kPairConsumers) {  // producer warp: one lane issues the copies
-    if (ln == 0) {
+    // stall != 0 (failure-detection tests only): issue nothing, so that the
+    // consumers' waits run out and the launch reports a timeout
+    if (ln == 0 && !stall) {
       unsigned long long policy;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(policy));
       unsigned long long keep;

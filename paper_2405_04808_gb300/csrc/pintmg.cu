@@ -156,6 +156,7 @@ struct mg_handle {
   int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
   int pair_tri = 1;     // levels with few blocks: two warps per block
   int pair_basis = 0;   // the FGMRES basis as FP32 pairs with compensated dot products (MG_BASIS_PAIR)
+  int pair_stall = 0;   // failure-detection tests: the streamed multi-dot issues no copies (its waits run out)
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -482,7 +483,7 @@ void multidot_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const d
   {
     Bracket br(h, CAT_PAIR_DOT, s, 8.0 * (m + 1) * len, 2.0 * m * len);
     k_multidot_pair_tma<kPairVB, kPairNS, kPairCtas><<<grid, kPairTmaThreads, pair_tma_smem<kPairVB, kPairNS>(), s>>>(
-        Vp, ldv, m, w, len, h->partial, nullptr, m_dev, h->flag + 2);
+        Vp, ldv, m, w, len, h->partial, nullptr, m_dev, h->flag + 2, h->pair_stall);
     ck_launch();
   }
   {
@@ -1628,6 +1629,10 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
   // PINTMG_TRI_PAIR=0 keeps one warp per block on every level (tests)
   if (const char *e = std::getenv("PINTMG_TRI_PAIR")) h->pair_tri = std::atoi(e) != 0;
+  // PINTMG_TEST_PAIR_STALL=1 (tests of the bounded waits): the pair multi-dot's
+  // producer issues nothing, so its consumers give up after 2 s and the solve
+  // returns MG_ERR_TIMEOUT
+  if (const char *e = std::getenv("PINTMG_TEST_PAIR_STALL")) h->pair_stall = std::atoi(e) != 0;
   // dot-product blocking (4, 8 or 16 basis vectors per CTA; bitwise the same
   // results): PINTMG_DOT_VB overrides the default (used by the tests)
   if (const char *e = std::getenv("PINTMG_DOT_VB")) {

@@ -382,6 +382,33 @@ def test_pair_basis_over_many_multidot_chunks(P):
         assert abs(info.iters - oracle_iters) <= 3, (restart, info.iters)
 
 
+@pytest.mark.parametrize("loops", [True, False])
+def test_pair_multidot_wait_runs_out_without_a_fault(P, monkeypatch, loops):
+    """Failure detection without a GPU fault: with the test hook set, the
+    streamed multi-dot's producer issues no copies, so the consumers' mbarrier
+    waits run out (2 s), the kernel records it and returns, later launches of
+    the solve return at once, and fgmres_solve reports MG_ERR_TIMEOUT.  The
+    context stays usable: a normal solve afterwards reaches the direct solution."""
+    import time
+    prob = W.burgers(nx=40, n=32, seed=155)
+    settings = dict(levels=2, nu_pre=1, nu_post=1, krylov_basis="pair", device_loops=loops)
+    monkeypatch.setenv("PINTMG_TEST_PAIR_STALL", "1")
+    h = P.mg_setup(prob, **settings)
+    monkeypatch.delenv("PINTMG_TEST_PAIR_STALL")
+    try:
+        b = _dev(prob.b)
+        x = torch.empty_like(b)
+        t0 = time.time()
+        code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, 6, 6)
+        assert code == P.MG_ERR_TIMEOUT, P.mg_status_string(code)
+        assert time.time() - t0 < 30.0
+    finally:
+        P.mg_destroy(h)
+    x, info = _solve_x(P, prob, dict(settings, levels=2))
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
+
+
 @pytest.mark.parametrize("n,levels", [(7, 1), (9, 1), (1, 1)])
 def test_odd_lengths_take_the_unpaired_kernels(P, n, levels):
     """n (4p + q) odd (van der Pol, w = 9, n odd): the dot products and axpys run their one-entry-per-step

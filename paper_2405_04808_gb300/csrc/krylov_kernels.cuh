@@ -1,6 +1,7 @@
 // FP64 Krylov kernels for flexible GMRES (Saad 1993) and the coarse GMRES:
 // multi-dot products with fixed-order reductions (bitwise reproducible),
-// multi-axpy, and the Arnoldi/Givens bookkeeping on the device.
+// multi-axpy, and the Arnoldi/Givens bookkeeping on the device.  The
+// FP32-pair basis option's kernels are in pair_kernels.cuh.
 #pragma once
 
 #include "common.cuh"
@@ -24,8 +25,8 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // partial[i * G + blockIdx.x] = sum over this CTA's slice of V_i . w,
-// V_i = V + i * ldv, i = blockIdx.y.  gate (optional device flag): 0 skips
-// the work (the reorthogonalisation pass that the DGKS test did not ask for).
+// V_i = V + i * ldv, i = blockIdx.y (the residual check that allocates
+// nothing).  gate (optional device flag): 0 skips the work.
 __global__ void __launch_bounds__(kDotThreads) k_multidot_partial(const double *__restrict__ V, long long ldv,
                                                                   const double *__restrict__ w, long long len,
                                                                   double *partial, const int *gate = nullptr) {

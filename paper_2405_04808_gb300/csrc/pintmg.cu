@@ -151,7 +151,6 @@ struct mg_handle {
   int use_cluster = 1;  // SGS chains on a thread-block cluster (tridiagonal layout)
   int use_scan = 1;     // SGS chains as a parallel scan with precomputed prefix products
   int use_seg = 1;      // SGS chains as concurrent segment chains joined by batched products
-  int force_seg = 0;    // form the segment products even when the full scan fits (tests)
   int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
   int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
   int pair_tri = 1;     // levels with few blocks: two warps per block
@@ -1623,7 +1622,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (const char *e = std::getenv("PINTMG_SGS_CHAIN")) {
     if (std::strcmp(e, "cluster") == 0) h->use_scan = 0, h->use_seg = 0;
     if (std::strcmp(e, "serial") == 0) h->use_scan = 0, h->use_cluster = 0, h->use_seg = 0;
-    if (std::strcmp(e, "segmented") == 0) h->use_scan = 0, h->force_seg = 1;
+    if (std::strcmp(e, "segmented") == 0) h->use_scan = 0;
   }
   // PINTMG_STAGE_TRI=0 turns the shared-memory staging of the block solves off (tests)
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
@@ -1773,10 +1772,10 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
           lev.d.scan_tmp = h->mem.alloc<double>((size_t)nl * p);
         }
         // segmented chains: in-segment products Q (one p x p per position, 2 n p^2 values in
-        // all), formed when the full scan is not (or on request); up to 8 segments of >= 16 steps
+        // all), up to 16 segments of >= 16 steps.  They serve when the full scan does not
+        // fit, and as a candidate of the autotuner (mg_autotune) when it does
         const double seg_bytes = 2.0 * (double)nl * p * p * sizeof(double);
-        if (layout == MG_LAYOUT_TRIDIAG && p >= 32 && nl >= 32 && seg_bytes <= 8.0 * (1 << 30) &&
-            (lev.d.scanF.empty() || h->force_seg)) {
+        if (layout == MG_LAYOUT_TRIDIAG && p >= 32 && nl >= 32 && seg_bytes <= 8.0 * (1 << 30)) {
           const int nseg = std::min(16, nl / 16);
           const int L = (nl + nseg - 1) / nseg;
           lev.d.seg_len = L;

@@ -64,9 +64,11 @@ typedef enum {
   MG_BASIS_FP64 = 0,  /* FP64 vectors; dot products and axpys in FP64 (the default) */
   MG_BASIS_PAIR = 1   /* each entry as two FP32 values hi + lo (the FP64 value rounded to ~48 bits, 8 bytes);
                          dot products and axpys against the basis in compensated FP32 arithmetic (error-free
-                         products and sums of Ogita, Rump and Oishi's Dot2) with FP64 reductions, about 1.5x
-                         faster on GB300, whose FP64 rate bounds the FP64 kernels; requires an even vector
-                         length n (4p+q), else the FP64 basis is used */
+                         products and sums of Ogita, Rump and Oishi's Dot2) with FP64 reductions; on GB300,
+                         whose FP64 rate bounds the FP64 kernels, these kernels run about 1.5x faster (the C2
+                         solve 1.2x).  Requires an even vector length n (4p+q), else the FP64 basis is used.
+                         Its streamed dot products wait on shared-memory barriers for at most 2 s each; a
+                         wait that runs out makes the solve return MG_ERR_TIMEOUT */
 } mg_krylov_basis;
 
 /*

@@ -2033,8 +2033,9 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       read_scal(h, K, s);
       true_rel = h->host_scal[0] / bnorm;
       if (status == MG_OK && est_rel > rtol) status = MG_NOT_CONVERGED;
-      int tmo = 0;
-      ck(cudaMemcpy(&tmo, h->flag + 2, sizeof(int), cudaMemcpyDeviceToHost));
+      int tmo = 0;  // a streamed multi-dot's wait ran out (pair basis)
+      ck(cudaMemcpyAsync(&tmo, h->flag + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
       if (tmo) status = MG_ERR_TIMEOUT;
     } else {
       est_rel = 0.0;

@@ -26,7 +26,7 @@
 extern "C" {
 #endif
 
-#define PINTMG_ABI_VERSION 1
+#define PINTMG_ABI_VERSION 2
 
 typedef enum {
   MG_OK = 0,
@@ -114,6 +114,24 @@ typedef enum {
   MG_COARSE_BGS = 3      /* (D + L^T)^-1 */
 } mg_coarse_precond;
 
+/*
+ * Restriction of the residual in the V-cycle (Alg. 1, step 2; Sec. 5.3.1).
+ * The paper states its transfers for the variables: linear interpolation and
+ * injection at fine step 2k-1 for u, v, lambda, mu; piecewise-constant
+ * interpolation and averaging for z.  The residual it restricts is a dual
+ * vector (the rows of A~).
+ */
+typedef enum {
+  MG_RESTRICT_INJECT = 0,    /* the variable formulas applied to the residual: r^c_k = r_{2k-1} (u, v, lambda,
+                                mu), (r_{2k-1} + r_{2k}) / 2 (z) */
+  MG_RESTRICT_TRANSPOSE = 1  /* the transpose of the interpolation, R = P^T: r^c_k = r_{2k-1} + (r_{2k-2} +
+                                r_{2k}) / 2 (u, v, lambda, mu; the last coarse step takes r_{2k} with the end
+                                rule's weight), r_{2k-1} + r_{2k} (z).  With a weighted sweep (omega = 2/3) the
+                                iteration counts grow logarithmically in n as in Tables 3-4; with omega = 1
+                                neither rule does, because the undamped sweep never damps modes that
+                                alternate from step to step */
+} mg_restrict_rule;
+
 typedef struct {
   int levels;             /* V-cycle levels Lv >= 1; n must be divisible by 2^(Lv-1); Lv = 1 is SGS-GMRES alone */
   int nu_pre, nu_post;    /* block-Jacobi sweeps before / after the coarse correction (>= 0) */
@@ -129,6 +147,7 @@ typedef struct {
                              0: loops driven from the host (a few scalars read back per iteration).
                              Same arithmetic either way. */
   int krylov_basis;       /* mg_krylov_basis of the FGMRES basis */
+  int restrict_rule;      /* mg_restrict_rule: how the V-cycle restricts the residual (Alg. 1, step 2) */
 } mg_options;
 
 typedef struct {
@@ -144,7 +163,7 @@ typedef struct {
 typedef struct mg_handle mg_handle;  /* opaque; owns every device buffer */
 
 /* Fill *opts with the defaults: levels 2, 1/1 sweeps, coarse 1e-3 / 50, tolerance mode, end rule 0, FP64,
- * omega 1, SGS coarse preconditioner, device loops. */
+ * omega 1, SGS coarse preconditioner, device loops, FP64 basis, injection of the residual. */
 void mg_default_options(mg_options *opts);
 
 /*

@@ -21,13 +21,18 @@ order the paper states, with no blocking or fusion of its own:
 * right-preconditioned GMRES and flexible GMRES     Sec. 5.3.4, Sec. 6 (Saad 1993)
 * two-level cycle generalised to a V-cycle          Alg. 1, Sec. 6 (coarsening 2)
 
-Readings taken where the paper is silent (each one is listed with its reason
-in the repository's design notes):
+Readings taken where the paper is silent:
 * coarse operators are rediscretised at 2 dt with linearisation points taken
   by the injection rule (fine step 2K-1 of the paper's 1-based count);
 * linear interpolation at the last coarse step extrapolates the last coarse
   value (``end_rule=0``) or uses a zero neighbour (``end_rule=1``);
 * transfers act on the scaled vectors literally, with no sqrt(2) factors;
+* the residual is restricted by the variable formulas of Sec. 5.3.1
+  (``restrict="inject"``) or by the transpose of the interpolation
+  (``restrict="transpose"``); with the transpose and a weighted sweep
+  (omega = 2/3) the cycle shows the logarithmic iteration growth of Tables 3
+  and 4, with the undamped sweep neither choice does (the sweep's spectrum is
+  symmetric about 0, so modes alternating in time are never damped);
 * each pre-smoothing starts from y = 0; x0 = 0 for every Krylov solve;
 * modified Gram-Schmidt in both Krylov methods.
 
@@ -235,16 +240,29 @@ def _restrict_average(nc: int) -> sp.csr_matrix:
     return R.tocsr()
 
 
-def transfer_type_major(n: int, p: int, q: int, end_rule: int = 0):
-    """(R, P) between n fine and n/2 coarse steps, type-major, all five variable types."""
+def transfer_type_major(n: int, p: int, q: int, end_rule: int = 0, restrict: str = "inject"):
+    """(R, P) between n fine and n/2 coarse steps, type-major, all five variable types.
+
+    restrict = "inject": the residual is restricted with the formulas Sec. 5.3.1
+    gives for the variables (injection at fine step 2k-1; average for z).
+    restrict = "transpose": the residual, a dual vector (it lives in the rows of
+    A~), is restricted by the transpose of the interpolation, R = P^T:
+    r^c_k = r_{2k-1} + (r_{2k-2} + r_{2k}) / 2 for u, v, lambda, mu and
+    r^c_k = r_{2k-1} + r_{2k} for z (the variational choice of multigrid texts
+    such as the tutorial Sec. 5.3 cites).
+    """
     nc = n // 2
     Ip, Iq = sp.identity(p), sp.identity(q)
-    Rl, Ra = _restrict_inject(nc), _restrict_average(nc)
     Pl, Pc = _interp_linear(nc, end_rule), _interp_constant(nc)
-    R = sp.block_diag([sp.kron(Rl, Ip), sp.kron(Rl, Ip), sp.kron(Ra, Iq),
-                       sp.kron(Rl, Ip), sp.kron(Rl, Ip)], format="csr")
     P = sp.block_diag([sp.kron(Pl, Ip), sp.kron(Pl, Ip), sp.kron(Pc, Iq),
                        sp.kron(Pl, Ip), sp.kron(Pl, Ip)], format="csr")
+    if restrict == "transpose":
+        return P.T.tocsr(), P
+    if restrict != "inject":
+        raise ValueError(restrict)
+    Rl, Ra = _restrict_inject(nc), _restrict_average(nc)
+    R = sp.block_diag([sp.kron(Rl, Ip), sp.kron(Rl, Ip), sp.kron(Ra, Iq),
+                       sp.kron(Rl, Ip), sp.kron(Rl, Ip)], format="csr")
     return R, P
 
 
@@ -455,6 +473,7 @@ class MGOptions:
     end_rule: int = 0
     omega: float = 1.0
     coarse_precond: str = "sgs"     # the paper's; "jacobi", "fgs", "bgs" are Table 1's alternatives
+    restrict: str = "inject"        # residual restriction: "inject" (Sec. 5.3.1 as written) or "transpose" (P^T)
 
 
 class Hierarchy:
@@ -470,7 +489,7 @@ class Hierarchy:
             level = Level(raw)
             self.levels.append(level)
             if lv + 1 < opts.levels:
-                R, P = transfer_type_major(raw.n, raw.p, raw.q, opts.end_rule)
+                R, P = transfer_type_major(raw.n, raw.p, raw.q, opts.end_rule, opts.restrict)
                 cperm, _ = time_major_order(raw.n // 2, raw.p, raw.q)
                 # R~ = Q_c R Q_f^T, P~ = Q_f P Q_c^T
                 self.R.append(R[cperm][:, level.perm].tocsr())

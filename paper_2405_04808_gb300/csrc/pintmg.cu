@@ -1170,7 +1170,16 @@ void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
     }
   }
   LevelData<T> &dn = ldata<T>(h->lv[l + 1]);
-  launch_residual_restrict<T>(h, d.view, y, b, dn.b, s);
+  if (o.restrict_rule == MG_RESTRICT_TRANSPOSE) {
+    launch_apply<T>(h, d.view, y, b, t, s);  // full fine residual into the free sweep buffer
+    const double w = 4.0 * h->p + h->q;
+    Bracket br(h, CAT_RESTRICT, s, sizeof(T) * (lev.n / 2) * w * 3.0, 0.0);
+    k_restrict_transpose<T><<<grid_for((long long)(lev.n / 2) * (long long)w, 256), 256, 0, s>>>(
+        t, dn.b, lev.n, h->p, h->q, o.end_rule);
+    ck_launch();
+  } else {
+    launch_residual_restrict<T>(h, d.view, y, b, dn.b, s);
+  }
   vcycle<T>(h, l + 1, dn.b, dn.y, s);
   {
     Bracket br(h, CAT_PROLONG, s);
@@ -1492,6 +1501,7 @@ void mg_default_options(mg_options *o) {
   o->coarse_precond = MG_COARSE_SGS;
   o->device_loops = 1;
   o->krylov_basis = MG_BASIS_FP64;
+  o->restrict_rule = MG_RESTRICT_INJECT;
 }
 
 const char *mg_status_string(int st) {
@@ -1591,6 +1601,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (O->coarse_precond < MG_COARSE_SGS || O->coarse_precond > MG_COARSE_BGS) return MG_ERR_ARG;
   if (O->device_loops != 0 && O->device_loops != 1) return MG_ERR_ARG;
   if (O->krylov_basis != MG_BASIS_FP64 && O->krylov_basis != MG_BASIS_PAIR) return MG_ERR_ARG;
+  if (O->restrict_rule != MG_RESTRICT_INJECT && O->restrict_rule != MG_RESTRICT_TRANSPOSE) return MG_ERR_ARG;
   if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;

@@ -759,6 +759,60 @@ __global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q
 }
 
 // ---------------------------------------------------------------------------
+// Residual restriction by the transpose of the interpolation, R = P^T (the
+// residual is a dual vector: it lives in the rows of A~).  With k_prolong_add's
+// P, per coarse step K (0-based, nc = n / 2):
+//   u, v, lambda, mu:  rc[K] = r[2K] + w r[2K+1] + (K >= 1 ? r[2K-1] / 2 : 0),
+//                      w = 1/2, except at K = nc - 1 where w is the end rule's
+//                      weight (1 for end_rule 0, 1/2 for end_rule 1)
+//   z:                 rc[K] = r[2K] + r[2K+1]
+// r is the full fine residual b - A~ y (k_apply_*).  One thread per coarse entry.
+template <typename T>
+__global__ void k_restrict_transpose(const T *__restrict__ r, T *rc, int n, int p, int q, int end_rule) {
+  const int nc = n / 2;
+  const long long ncp = (long long)nc * p, ncq = (long long)nc * q;
+  const long long np = (long long)n * p, nq = (long long)n * q;
+  const long long total = 4 * ncp + ncq;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long k = idx;
+    int width = p;
+    long long fine_off, coarse_off;
+    bool constant = false;
+    if (k < 2 * ncp) {  // u or v
+      const long long which = k / ncp;
+      k -= which * ncp;
+      fine_off = which * np;
+      coarse_off = which * ncp;
+    } else if (k < 2 * ncp + ncq) {  // z
+      k -= 2 * ncp;
+      width = q;
+      fine_off = 2 * np;
+      coarse_off = 2 * ncp;
+      constant = true;
+    } else {  // lambda or mu
+      k -= 2 * ncp + ncq;
+      const long long which = k / ncp;
+      k -= which * ncp;
+      fine_off = 2 * np + nq + which * np;
+      coarse_off = 2 * ncp + ncq + which * ncp;
+    }
+    const int K = (int)(k / width), i = (int)(k % width);
+    const T *rf = r + fine_off;
+    const T r0 = rf[(long long)(2 * K) * width + i], r1 = rf[(long long)(2 * K + 1) * width + i];
+    T acc;
+    if (constant) {
+      acc = r0 + r1;
+    } else {
+      const T w = (K + 1 < nc || end_rule != 0) ? T(0.5) : T(1);
+      acc = fma(w, r1, r0);
+      if (K >= 1) acc = fma(T(0.5), rf[(long long)(2 * K - 1) * width + i], acc);
+    }
+    rc[coarse_off + k] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // SGS (Sec. 5.3.4) as two serial affine chains on the coarsest grid.  With
 // w = (D + L)^-1 r and y = (D + L^T)^-1 D w, only u(w) carries the forward
 // dependence and only mu(y) the backward one:

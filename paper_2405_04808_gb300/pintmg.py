@@ -35,6 +35,8 @@ MG_PRECISION_FP32_SMOOTH = 2
 COARSE_PRECOND = {"sgs": 0, "jacobi": 1, "fgs": 2, "bgs": 3}
 #: storage of the FGMRES basis (mg_krylov_basis)
 KRYLOV_BASIS = {"fp64": 0, "pair": 1}
+#: residual restriction of the V-cycle (mg_restrict_rule)
+RESTRICT = {"inject": 0, "transpose": 1}
 
 #: every symbol include/pintmg.h declares
 EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmres_solve_batched",
@@ -59,7 +61,7 @@ class MGOptions(ctypes.Structure):
                 ("coarse_rtol", ctypes.c_double), ("coarse_maxit", ctypes.c_int),
                 ("coarse_fixed_iters", ctypes.c_int), ("end_rule", ctypes.c_int), ("precision", ctypes.c_int),
                 ("omega", ctypes.c_double), ("coarse_precond", ctypes.c_int), ("device_loops", ctypes.c_int),
-                ("krylov_basis", ctypes.c_int)]
+                ("krylov_basis", ctypes.c_int), ("restrict_rule", ctypes.c_int)]
 
 
 class MGSolveInfo(ctypes.Structure):
@@ -161,9 +163,10 @@ def _c(arr):
 
 def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit=50,
              coarse_fixed_iters=0, end_rule=0, precision=MG_PRECISION_FP64, omega=1.0, coarse_precond="sgs",
-             device_loops=True, krylov_basis="fp64", stream=0):
+             device_loops=True, krylov_basis="fp64", restrict="inject", stream=0):
     """Build the device hierarchy for a workloads.Problem; returns an opaque handle (int).
-    krylov_basis: "fp64" (the plain method) or "pair" (FP32-pair basis with compensated dot products)."""
+    krylov_basis: "fp64" (the plain method) or "pair" (FP32-pair basis with compensated dot products).
+    restrict: "inject" (Sec. 5.3.1's variable formulas applied to the residual) or "transpose" (R = P^T)."""
     keep = []
     P = MGProblem()
     P.layout = MG_LAYOUT_TRIDIAG if prob.kind == "tridiag" else MG_LAYOUT_DENSE
@@ -175,7 +178,8 @@ def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit
         keep.append(a)
         setattr(P, name, ptr)
     o = MGOptions(levels, nu_pre, nu_post, coarse_rtol, coarse_maxit, coarse_fixed_iters, end_rule, precision, omega,
-                  COARSE_PRECOND[coarse_precond], 1 if device_loops else 0, KRYLOV_BASIS[krylov_basis])
+                  COARSE_PRECOND[coarse_precond], 1 if device_loops else 0, KRYLOV_BASIS[krylov_basis],
+                  RESTRICT[restrict])
     h = ctypes.c_void_p()
     code = lib().mg_setup(ctypes.byref(P), ctypes.byref(o), ctypes.c_void_p(stream), ctypes.byref(h))
     if code != MG_OK:

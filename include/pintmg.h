@@ -16,7 +16,11 @@
  * scaled Euclidean coordinates of Sec. 4.1.
  *
  * Errors: every entry point returns an mg_status code; nothing aborts, traps
- * or throws.  Device kernels never spin-wait.
+ * or throws.  One kernel waits on the device: the streamed multi-dot of the
+ * FP32-pair Krylov basis (MG_BASIS_PAIR) polls shared-memory barriers for its
+ * copies, at most 2 s per wait (%globaltimer); a wait that runs out ends the
+ * kernel, after its issued copies have landed, and the solve returns
+ * MG_ERR_TIMEOUT.  No other kernel waits on anything.
  * Threading: one handle is used by one host thread and one stream at a time.
  */
 #ifndef PINTMG_H
@@ -226,11 +230,26 @@ long long mg_vector_length(const mg_handle *h);
  * mg_profile_read synchronises those events and fills up to `max` entries of
  * names (static strings), ms (summed kernel time), launches (count), bytes and
  * flops (the algorithmic memory traffic and floating-point operations of the
- * timed launches, from the per-kernel models documented in the design notes)
+ * timed launches: each launch adds the bytes its kernel must move at least,
+ * every input and output touched once, and the flops its arithmetic needs)
  * per kernel category; any output pointer may be NULL.  It returns the number
  * of categories or a negative status.
  */
 long long mg_launch_count(const mg_handle *h);
+
+/*
+ * Arithmetic-rate probe (measurement support, no counterpart in the paper):
+ * launches `blocks` CTAs of 256 threads on `stream`, each thread running 8
+ * independent fused multiply-add chains of `iters` steps in FP64
+ * (precision = MG_PRECISION_FP64) or FP32 (MG_PRECISION_FP32), then writing
+ * one value per thread to `sink` (a DEVICE buffer of blocks * 256 elements of
+ * that type, owned by the caller).  The launch does 2 * 8 * iters * blocks *
+ * 256 floating-point operations; timing it with events on `stream` gives the
+ * FMA rate the FP64 (or FP32) kernels' rooflines are measured against.
+ * Asynchronous; returns MG_ERR_ARG for bad arguments, MG_ERR_CUDA if the
+ * launch fails.
+ */
+int mg_probe_fma(int precision, int blocks, int iters, void *sink, void *stream);
 int mg_profile_enable(mg_handle *h, int mask);
 int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long long *launches, double *bytes,
                     double *flops);
@@ -251,7 +270,9 @@ int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long 
  * library until the process exits.  Vectors longer than 2^20 doubles are
  * rejected with MG_ERR_ARG (mg_last_cuda_error() says why).  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call overwrites the
+ * make that first call before any stream capture.  The device current at the
+ * call must be the one the handle was set up on (else MG_ERR_ARG, with
+ * mg_last_cuda_error() naming both).  Every call overwrites the
  * same array, so calls that overlap on the GPU (other streams, other host
  * threads) race; serialise them.
  */

@@ -266,9 +266,9 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
   }
   __syncthreads();
   if (wp == kPairConsumers) {  // producer warp: one lane issues the copies
-    // stall != 0 (failure-detection tests only): issue nothing, so that the
+    // stall == 1 (failure-detection tests only): issue nothing, so that the
     // consumers' waits run out and the launch reports a timeout
-    if (ln == 0 && !stall) {
+    if (ln == 0 && stall != 1) {
       unsigned long long policy;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(policy));
       unsigned long long keep;
@@ -297,10 +297,15 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
       if (!ok) {
         atomicOr(err, 1);
         *(volatile int *)&abort_flag = 1;
-        // let the copies already issued land before the CTA can exit
-        for (long long k = (q > NS ? q - NS : 0); k < q; ++k)
-          mbar_wait(&full[(int)(k % NS)], (unsigned)(k / NS) & 1u);
       }
+      // Let every copy this lane issued land before it returns, whether or not
+      // the consumers still wait for them (a consumer that gives up skips its
+      // waits, and the CTA must not exit with bulk copies in flight).  Stage k
+      // is the last use of its slot for k >= q - NS, so its full barrier's
+      // phase (k / NS) & 1 completes exactly when its bytes have arrived; in a
+      // healthy run these phases have completed already.
+      for (long long k = (q > NS ? q - NS : 0); k < q; ++k)
+        mbar_wait(&full[(int)(k % NS)], (unsigned)(k / NS) & 1u);
     }
     return;
   }
@@ -360,6 +365,13 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
       }
       __syncwarp();
       if (ln == 0) mbar_arrive(&empty[slot]);
+      // stall == 2 (failure-detection tests only): the first consumer warp of
+      // CTA 0 gives up after its first stage, possibly after the producer has
+      // issued every copy; the other warps then skip their waits
+      if (stall == 2 && blockIdx.x == 0 && wp == 0 && q == 0 && ln == 0) {
+        atomicOr(err, 1);
+        *(volatile int *)&abort_flag = 1;
+      }
     }
     const double scale = pow2_of_exponent(emax);
 #pragma unroll

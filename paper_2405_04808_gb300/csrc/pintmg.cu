@@ -156,6 +156,7 @@ struct mg_handle {
   int pair_tri = 1;     // levels with few blocks: two warps per block
   int pair_basis = 0;   // the FGMRES basis as FP32 pairs with compensated dot products (MG_BASIS_PAIR)
   int pair_stall = 0;   // failure-detection tests: the streamed multi-dot issues no copies (its waits run out)
+  int device = -1;      // the CUDA device current at mg_setup; every device buffer of the handle lives there
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -1483,6 +1484,29 @@ bool is_device_pointer(const void *p) {
 }  // namespace
 
 // ===========================================================================
+// Arithmetic-rate probe (measurement support): every thread runs kProbeChains
+// independent FMA chains a <- a * b + c for `iters` steps and stores their sum,
+// so the work cannot be removed; 2 * kProbeChains * iters flops per thread.
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) k_probe_fma(T *sink, int iters, T b, T c) {
+  T a[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) a[k] = T(threadIdx.x + k) * T(1e-3);
+#pragma unroll 4
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], b, c);
+  }
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) acc += a[k];
+  sink[blockIdx.x * (long long)blockDim.x + threadIdx.x] = acc;
+}
+
+// ===========================================================================
 // C ABI
 
 extern "C" {
@@ -1525,6 +1549,22 @@ const char *mg_last_cuda_error(void) { return g_last_cuda_error; }
 long long mg_vector_length(const mg_handle *h) { return h ? h->lv[0].len : 0; }
 
 long long mg_launch_count(const mg_handle *h) { return h ? h->launches : 0; }
+
+int mg_probe_fma(int precision, int blocks, int iters, void *sink, void *stream) {
+  if (blocks < 1 || blocks > (1 << 20) || iters < 1 || !sink) return MG_ERR_ARG;
+  if (precision != MG_PRECISION_FP64 && precision != MG_PRECISION_FP32) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == MG_PRECISION_FP64)
+    k_probe_fma<double><<<blocks, kProbeThreads, 0, s>>>(static_cast<double *>(sink), iters, 0.9999999, 1e-9);
+  else
+    k_probe_fma<float><<<blocks, kProbeThreads, 0, s>>>(static_cast<float *>(sink), iters, 0.9999999f, 1e-9f);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}
 
 int mg_profile_enable(mg_handle *h, int enable) {
   if (!h) return MG_ERR_ARG;
@@ -1619,6 +1659,11 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   mg_handle *h = new (std::nothrow) mg_handle();
   if (!h) return MG_ERR_OOM;
   h->opts = *O;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return MG_ERR_CUDA;
+  }
   h->layout = layout;
   h->n = n;
   h->p = p;
@@ -1642,7 +1687,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   // PINTMG_TEST_PAIR_STALL=1 (tests of the bounded waits): the pair multi-dot's
   // producer issues nothing, so its consumers give up after 2 s and the solve
   // returns MG_ERR_TIMEOUT
-  if (const char *e = std::getenv("PINTMG_TEST_PAIR_STALL")) h->pair_stall = std::atoi(e) != 0;
+  if (const char *e = std::getenv("PINTMG_TEST_PAIR_STALL")) h->pair_stall = std::min(2, std::max(0, std::atoi(e)));
   // dot-product blocking (4, 8 or 16 basis vectors per CTA; bitwise the same
   // results): PINTMG_DOT_VB overrides the default (used by the tests)
   if (const char *e = std::getenv("PINTMG_DOT_VB")) {
@@ -2247,6 +2292,12 @@ extern "C" int mg_true_residual_noalloc(mg_handle *h, const double *b, const dou
     cudaGetLastError();
     return MG_ERR_CUDA;
   }
+  if (dev != h->device) {  // the handle's buffers live on another device: launching here would fault
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error,
+                  "mg_true_residual_noalloc: device %d is current, the handle was set up on device %d", dev,
+                  h->device);
+    return MG_ERR_ARG;
+  }
   if (!g_noalloc_ptr[dev]) {  // first call on this device: resolve the array's device address
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -2283,6 +2334,7 @@ extern "C" int mg_true_residual_noalloc(mg_handle *h, const double *b, const dou
   k_multidot_partial<<<dim3(G, 1), kDotThreads, 0, s>>>(b, len, b, len, partial + 304);
   k_reduce_partials<<<1, 128, 0, s>>>(partial + 304, G, 1, sums + 1, 0);
   k_noalloc_finish<<<1, 1, 0, s>>>(sums, out);
+  h->launches += 6;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));

@@ -41,7 +41,7 @@ RESTRICT = {"inject": 0, "transpose": 1}
 #: every symbol include/pintmg.h declares
 EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmres_solve_batched",
             "mg_vector_length",
-            "mg_launch_count", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
+            "mg_launch_count", "mg_probe_fma", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
             "mg_net_forward", "mg_net_loss_grad", "mg_net_adam_step", "mg_net_train", "mg_net_destroy",
             "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune", "mg_jacobi_radius",
@@ -132,7 +132,8 @@ def lib():
                 ("mg_recorded_pairs", [vp], ci),
                 ("mg_coarse_shape", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
                 ("mg_autotune", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), vp], ci),
-                ("mg_jacobi_radius", [vp, ci, ci, ctypes.POINTER(ctypes.c_double), vp], ci)):
+                ("mg_jacobi_radius", [vp, ci, ci, ctypes.POINTER(ctypes.c_double), vp], ci),
+                ("mg_probe_fma", [ci, ci, ci, vp, vp], ci)):
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
@@ -246,6 +247,18 @@ def mg_profile_read(h) -> dict:
     if n < 0:
         raise PintmgError(n, "mg_profile_read")
     return {names[i].decode(): (ms[i], int(cnt[i]), by[i], fl[i]) for i in range(min(n, k))}
+
+
+#: threads per CTA and independent FMA chains per thread of mg_probe_fma
+PROBE_THREADS = 256
+PROBE_CHAINS = 8
+
+
+def mg_probe_fma(precision: int, blocks: int, iters: int, sink_ptr: int, stream: int = 0) -> float:
+    """Launch the FMA-rate probe; returns the floating-point operations the launch performs."""
+    _check(lib().mg_probe_fma(int(precision), int(blocks), int(iters), ctypes.c_void_p(sink_ptr),
+                              ctypes.c_void_p(stream)), "mg_probe_fma")
+    return 2.0 * PROBE_CHAINS * iters * blocks * PROBE_THREADS
 
 
 def mg_true_residual_noalloc(h, b_ptr: int, x_ptr: int, out_ptr: int, stream: int = 0) -> int:

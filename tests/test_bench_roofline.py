@@ -19,7 +19,7 @@ def test_fp64_gram_schmidt_is_measured_against_the_fp64_pipe():
     m, n, t_ms = 120, 655360, 0.174
     prof = {"multidot": (t_ms, 1, 8.0 * (m + 1) * n, 2.0 * m * n)}
     r = B.roofline(prof, "multidot", "fp64", "burgers_nx128_n1024")
-    assert r["bound"] == "alu" and r["peak"] == B.FP64_TFLOPS_MEASURED
+    assert r["bound"] == "alu" and r["peak"] == B.PEAKS["fp64_tflops"]
     assert abs(r["achieved"] - 2.0 * m * n / (t_ms / 1e3) / 1e12) < 1e-3
     # the ncu capture of this kernel on this workload: DRAM bytes = algorithmic bytes
     assert r["traffic"] == round(8.0 * (m + 1) * n)
@@ -41,6 +41,40 @@ def test_pair_gram_schmidt_is_measured_against_hbm():
 def test_fp32_modes_measure_the_vcycle_against_fp32_and_krylov_against_fp64():
     B = _bench()
     prof = {"block_solve": (1.0, 10, 1e9, 5e12), "multidot": (1.0, 10, 1e9, 5e12)}
-    assert B.roofline(prof, "block_solve", "fp32")["peak"] == B.FP32_TFLOPS_MEASURED
-    assert B.roofline(prof, "multidot", "fp32")["peak"] == B.FP64_TFLOPS_MEASURED
+    assert B.roofline(prof, "block_solve", "fp32")["peak"] == B.PEAKS["fp32_tflops"]
+    assert B.roofline(prof, "multidot", "fp32")["peak"] == B.PEAKS["fp64_tflops"]
     assert B.roofline({}, "multidot", "fp64")["bound"] is None
+
+
+def test_probe_rate_replaces_the_nominal_peak():
+    B = _bench()
+    prof = {"multidot": (0.174, 1, 8.0 * 121 * 655360, 2.0 * 120 * 655360)}
+    B.PEAKS.update(fp64_tflops=1.2, source="measured in this run")
+    r = B.roofline(prof, "multidot", "fp64")
+    assert r["peak"] == 1.2 and "measured in this run" in r["peak_source"]
+
+
+def test_extrapolation_sums_restart_cycles():
+    B = _bench()
+    # t_j = 2 + 0.5 j exactly: a solve of 7 iterations at restart 4 visits j = 0,1,2,3,0,1,2
+    times = [2.0 + 0.5 * j for j in range(6)]
+    secs, a, b = B.extrapolate_solve(times, 7, 4)
+    assert abs(a - 2.0) < 1e-12 and abs(b - 0.5) < 1e-12
+    assert abs(secs - sum(2.0 + 0.5 * j for j in (0, 1, 2, 3, 0, 1, 2))) < 1e-9
+
+
+def test_error_vs_oracle_reads_the_stored_samples():
+    import numpy as np
+    B = _bench()
+    g = B.golden_direct("vdp_n256")
+    assert g is not None and g["relres"] < 1e-11
+    torch = __import__("pytest").importorskip("torch")
+    x = np.zeros(g["length"])
+    for rec in g["types"].values():
+        x[np.asarray(rec["indices"])] = rec["values"]
+    e = B.error_vs_oracle(torch.tensor(x), "vdp_n256")
+    assert e["max_type_rel_err"] == 0.0
+    assert e["samples"] == sum(len(r["indices"]) for r in g["types"].values()) == 4 * 512 + 256
+    x[g["types"]["mu"]["indices"][3]] += 1e-6 * g["types"]["mu"]["max_abs"]
+    e = B.error_vs_oracle(torch.tensor(x), "vdp_n256")
+    assert abs(e["per_type"]["mu"] - 1e-6) < 1e-9 and e["per_type"]["u"] == 0.0

@@ -401,17 +401,21 @@ def test_pair_basis_over_many_multidot_chunks(P):
         assert abs(info.iters - oracle_iters) <= 3, (restart, info.iters)
 
 
+@pytest.mark.parametrize("stall", ["1", "2"])
 @pytest.mark.parametrize("loops", [True, False])
-def test_pair_multidot_wait_runs_out_without_a_fault(P, monkeypatch, loops):
-    """Failure detection without a GPU fault: with the test hook set, the
-    streamed multi-dot's producer issues no copies, so the consumers' mbarrier
-    waits run out (2 s), the kernel records it and returns, later launches of
-    the solve return at once, and fgmres_solve reports MG_ERR_TIMEOUT.  The
-    context stays usable: a normal solve afterwards reaches the direct solution."""
+def test_pair_multidot_wait_runs_out_without_a_fault(P, monkeypatch, loops, stall):
+    """Failure detection without a GPU fault.  Hook 1: the streamed multi-dot's
+    producer issues no copies, so the consumers' mbarrier waits run out (2 s).
+    Hook 2: a consumer warp gives up after its first stage, possibly after the
+    producer has issued every copy; the producer still waits for its issued
+    copies to land before the CTA exits.  Either way the kernel records the
+    failure and returns, later launches of the solve return at once, and
+    fgmres_solve reports MG_ERR_TIMEOUT.  The context stays usable: a normal
+    solve afterwards reaches the direct solution."""
     import time
     prob = W.burgers(nx=40, n=32, seed=155)
     settings = dict(levels=2, nu_pre=1, nu_post=1, krylov_basis="pair", device_loops=loops)
-    monkeypatch.setenv("PINTMG_TEST_PAIR_STALL", "1")
+    monkeypatch.setenv("PINTMG_TEST_PAIR_STALL", stall)
     h = P.mg_setup(prob, **settings)
     monkeypatch.delenv("PINTMG_TEST_PAIR_STALL")
     try:

@@ -40,6 +40,13 @@ def test_noalloc_residual_matches_solver(P, make):
             rel = float(out[1])
             assert abs(rel - info.true_relres) <= RTOL * max(info.true_relres, 1e-300)
             assert abs(float(out[0]) - rel * float(torch.linalg.norm(b))) <= 1e-12 * float(out[0]) + 1e-300
+        # against the oracle's assembled lifted operator (Fig. 4): ||b - A x|| / ||b|| in FP64 on the host
+        from oracle import augmented as O
+        A = O.Level(O.raw_from_problem(prob)).A
+        xh = x.cpu().numpy()
+        want = float(np.linalg.norm(prob.b - A @ xh) / np.linalg.norm(prob.b))
+        # (a residual near 1e-9 carries cancellation error of order eps * ||A|| ||x|| / ||b|| from either side)
+        assert abs(float(out[1]) - want) <= 1e-4 * want + 1e-14, (float(out[1]), want)
         # a different x gives its own residual (nothing stale from the previous call)
         xz = torch.zeros_like(b)
         assert P.mg_true_residual_noalloc(h, b.data_ptr(), xz.data_ptr(), out.data_ptr(), 0) == P.MG_OK

@@ -88,7 +88,8 @@ typedef enum {
  *   Z~_k = -(theta Jz_cur + (1-theta) Jz_prev) / gamma.
  * Coarse levels are rediscretised at 2 dt with the Jacobians of fine step
  * 2K-1 (current) and 2K-2 (previous) in the paper's 1-based count; this is
- * exact when d_u f does not depend on z and f is affine in z.
+ * exact when d_u f does not depend on z and f is affine in z, which the
+ * caller asserts with `separable`.
  *
  * MG_LAYOUT_DENSE:   M is p*p, Ju_* are n*p*p, Jz_* are n*p*q (row-major blocks).
  * MG_LAYOUT_TRIDIAG: every p x p tridiagonal matrix is 3*p doubles,
@@ -106,6 +107,10 @@ typedef struct {
   int jz_const;
   const double *M;
   const double *Ju_cur, *Ju_prev, *Jz_cur, *Jz_prev;
+  int separable;     /* 1: d_u f does not depend on z and f is affine in z (both of Sec. 6's problems).  The
+                        coarse levels are rediscretised from the fine Jacobians (above), which is exact only
+                        then; levels > 1 with separable = 0 are rejected with MG_ERR_ARG (levels = 1, GMRES
+                        with SGS alone, needs no coarse operator and accepts either value) */
 } mg_problem;
 
 /* Block fixed-point iterations of Sec. 5.3.4 / Table 1, one step from zero,

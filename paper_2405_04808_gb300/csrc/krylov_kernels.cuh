@@ -58,17 +58,46 @@ __host__ __device__ inline int dot_parts(int m, int VB, long long len) {
 }
 constexpr int kDotGridCap = 1216;  // CTAs of a dot-product launch (8 per SM)
 
+// Fixed-order sum over g < G of partial[i * G + g] by one warp (lane-strided
+// sums, then a shuffle tree): the order of k_reduce_partials, so a fused
+// reduction gives the same bits.  The result is valid in lane 0.
+__device__ __forceinline__ double warp_partial_sum(const double *partial, int G, long long i, int ln) {
+  double s = 0.0;
+  for (int g = ln; g < G; g += kWarp) s += __ldcg(partial + i * G + g);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+  return s;
+}
+
+// true in every thread of the CTA that finishes last (its partial sums and
+// those of every other CTA of the launch are then visible); the ticket counts
+// the CTAs that have finished and is reset by the last one
+__device__ __forceinline__ bool last_cta(unsigned *ticket) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
 // partial[i * G + g] = sum over chunk g of V_i . w for i < m, VB vectors per
 // work item, G = dot_parts(m, VB, len); a persistent grid walks the items.  kPair:
 // two consecutive entries per thread and step (16-byte loads; needs len and
 // ldv even and 16-byte aligned V, w).  Each thread streams its slice of w once
 // against VB basis vectors (VB independent accumulators), so the per-item
 // reduction is amortised over VB times more fused multiply-adds.
+// ticket non-null: the CTA that finishes last also reduces the partial sums
+// into out[i] (+= with accumulate), in k_reduce_partials' order (one launch
+// instead of two, the same bits).
 template <int VB, bool kPair>
 __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *__restrict__ V, long long ldv, int m,
                                                                   const double *__restrict__ w, long long len,
                                                                   double *partial, const int *gate,
-                                                                  const int *m_dev = nullptr) {
+                                                                  const int *m_dev = nullptr,
+                                                                  unsigned *ticket = nullptr, double *out = nullptr,
+                                                                  int accumulate = 0) {
   if (gate && *gate == 0) return;
   if (m_dev) m = *m_dev;  // vector count held on the device (graph-captured solves)
   __shared__ double red[kDotThreads / kWarp][VB];
@@ -120,6 +149,13 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *
     }
     __syncthreads();  // red is reused by the next item
   }
+  if (ticket && last_cta(ticket)) {
+    for (int i = wp; i < m; i += kDotThreads / kWarp) {
+      const double sum = warp_partial_sum(partial, G, i, ln);
+      if (ln == 0) out[i] = accumulate ? out[i] + sum : sum;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
 }
 
 // out[i] (+)= sum_g partial[i * G + g], fixed order.  One warp per i.  With
@@ -138,6 +174,104 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
   if (ln == 0) out[i] = accumulate ? out[i] + s : s;
+}
+
+// Arnoldi column j: H[0..j][j] = h, H[j+1][j] = ||w||; apply the previous
+// Givens rotations, form rotation j, update g.  H is column-major with leading
+// dimension ldh.  scal: [0] |g_{j+1}|, [1] 1/h_{j+1,j}, [2] h_{j+1,j}.
+// One warp.  The previous rotations act on the new column as a first-order
+// linear recurrence: with t_0 = h_0, rotation i gives
+//   col_i = c_i t_i + s_i h_{i+1},   t_{i+1} = -s_i t_i + c_i h_{i+1},
+// so each lane composes the affine maps of its chunk of rotations, a warp
+// scan gives every chunk its incoming t, and the chunk is re-run; t_j meets
+// h_{j+1,j} = ||w|| in the new rotation j.
+__device__ __forceinline__ void arnoldi_column(int j, const double *h, double w2, double *H, int ldh, double *cs,
+                                               double *sn, double *g, double *scal, int ln) {
+  double *col = H + (long long)j * ldh;
+  const double hj1 = sqrt(w2);
+  const int ch = (j + kWarp - 1) / kWarp;
+  const int i0 = min(ln * ch, j), i1 = min(i0 + ch, j);
+  double A = 1.0, B = 0.0;  // this chunk's map t -> A t + B
+  for (int i = i0; i < i1; ++i) {
+    const double a = -sn[i];
+    B = fma(a, B, cs[i] * h[i + 1]);
+    A *= a;
+  }
+#pragma unroll
+  for (int off = 1; off < kWarp; off <<= 1) {  // inclusive scan: compose with the lanes below
+    const double Ap = __shfl_up_sync(kFull, A, off), Bp = __shfl_up_sync(kFull, B, off);
+    if (ln >= off) {
+      B = fma(A, Bp, B);
+      A *= Ap;
+    }
+  }
+  double Ae = __shfl_up_sync(kFull, A, 1), Be = __shfl_up_sync(kFull, B, 1);
+  if (ln == 0) {
+    Ae = 1.0;
+    Be = 0.0;
+  }
+  double t = fma(Ae, h[0], Be);
+  for (int i = i0; i < i1; ++i) {
+    const double hi1 = h[i + 1];
+    col[i] = fma(cs[i], t, sn[i] * hi1);
+    t = fma(-sn[i], t, cs[i] * hi1);
+  }
+  const double Aall = __shfl_sync(kFull, A, kWarp - 1), Ball = __shfl_sync(kFull, B, kWarp - 1);
+  if (ln != 0) return;
+  const double a = fma(Aall, h[0], Ball), b = hj1;
+  const double den = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (den != 0.0) {
+    c = a / den;
+    s = b / den;
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = c * a + s * b;
+  col[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  scal[0] = fabs(g[j + 1]);
+  scal[1] = hj1 > 0.0 ? 1.0 / hj1 : 0.0;
+  scal[2] = hj1;
+}
+
+__global__ void k_arnoldi_step(int j, const double *__restrict__ h, const double *__restrict__ w2, double *H,
+                               int ldh, double *cs, double *sn, double *g, double *scal, const int *j_dev = nullptr) {
+  if (blockIdx.x != 0 || threadIdx.x >= kWarp) return;
+  if (j_dev) j = *j_dev;
+  arnoldi_column(j, h, w2[0], H, ldh, cs, sn, g, scal, threadIdx.x);
+}
+
+// The end of a CGS2 step, run by the CTA that finishes the second
+// orthogonalisation last: ||w||^2 from the CTAs' partial sums (the order of
+// k_reduce_partials), h += h2 (the two passes' coefficients), then the
+// Arnoldi column j with its Givens rotations (k_arnoldi_step).  One launch
+// less than reduce + add + step, the same bits.
+struct ArnoldiTail {
+  unsigned *ticket;
+  double *h;          // first pass's coefficients, summed in place with h2
+  const double *h2;   // second pass's coefficients
+  double *nrm2;       // receives ||w||^2
+  double *H, *cs, *sn, *g, *scal;
+  int ldh, j;
+  const int *j_dev;   // the Arnoldi index on the device (graph-captured solves), else null
+};
+
+__device__ __forceinline__ void arnoldi_tail(const ArnoldiTail &t, const double *partial, int m) {
+  const int wp = threadIdx.x / kWarp, ln = threadIdx.x & (kWarp - 1);
+  __shared__ double s_w2;
+  if (wp == 0) {
+    const double sum = warp_partial_sum(partial, gridDim.x, 0, ln);
+    if (ln == 0) {
+      t.nrm2[0] = sum;
+      s_w2 = sum;
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) t.h[i] += t.h2[i];
+  __syncthreads();
+  if (wp == 0) arnoldi_column(t.j_dev ? *t.j_dev : t.j, t.h, s_w2, t.H, t.ldh, t.cs, t.sn, t.g, t.scal, ln);
+  if (threadIdx.x == 0) *t.ticket = 0u;
 }
 
 // y[idx] += sign * sum_{i < m} c[i] X_i[idx],  X_i = X + i * ldx
@@ -186,7 +320,8 @@ __global__ void k_multi_axpy(double *y, const double *__restrict__ X, long long 
 template <bool kPair>
 __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_norm(double *y, const double *__restrict__ X, long long ldx,
                                                                  const double *__restrict__ c, int m, long long len,
-                                                                 double *partial, const int *m_dev = nullptr) {
+                                                                 double *partial, const int *m_dev = nullptr,
+                                                                 ArnoldiTail tail = {}) {
   if (m_dev) m = *m_dev;
   __shared__ double cs[512];
   for (int i = threadIdx.x; i < m; i += blockDim.x) cs[i] = c[i];
@@ -223,6 +358,7 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_norm(double *y, cons
   }
   const double s = block_sum(sq);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (tail.ticket && last_cta(tail.ticket)) arnoldi_tail(tail, partial, m);
 }
 
 // y[i] += x[i], i < m
@@ -252,69 +388,6 @@ __global__ void k_norm_from_sq(const double *nrm2, double *scal, const int *guar
   double b = sqrt(nrm2[0]);
   scal[0] = b;
   scal[1] = b > 0.0 ? 1.0 / b : 0.0;
-}
-
-// Arnoldi column j: H[0..j][j] = h, H[j+1][j] = ||w||; apply the previous
-// Givens rotations, form rotation j, update g.  H is column-major with leading
-// dimension ldh.  scal: [0] |g_{j+1}|, [1] 1/h_{j+1,j}, [2] h_{j+1,j}.
-// One warp.  The previous rotations act on the new column as a first-order
-// linear recurrence: with t_0 = h_0, rotation i gives
-//   col_i = c_i t_i + s_i h_{i+1},   t_{i+1} = -s_i t_i + c_i h_{i+1},
-// so each lane composes the affine maps of its chunk of rotations, a warp
-// scan gives every chunk its incoming t, and the chunk is re-run; t_j meets
-// h_{j+1,j} = ||w|| in the new rotation j.
-__global__ void k_arnoldi_step(int j, const double *__restrict__ h, const double *__restrict__ w2, double *H,
-                               int ldh, double *cs, double *sn, double *g, double *scal, const int *j_dev = nullptr) {
-  if (blockIdx.x != 0 || threadIdx.x >= kWarp) return;
-  if (j_dev) j = *j_dev;
-  const int ln = threadIdx.x;
-  double *col = H + (long long)j * ldh;
-  const double hj1 = sqrt(w2[0]);
-  const int ch = (j + kWarp - 1) / kWarp;
-  const int i0 = min(ln * ch, j), i1 = min(i0 + ch, j);
-  double A = 1.0, B = 0.0;  // this chunk's map t -> A t + B
-  for (int i = i0; i < i1; ++i) {
-    const double a = -sn[i];
-    B = fma(a, B, cs[i] * h[i + 1]);
-    A *= a;
-  }
-#pragma unroll
-  for (int off = 1; off < kWarp; off <<= 1) {  // inclusive scan: compose with the lanes below
-    const double Ap = __shfl_up_sync(kFull, A, off), Bp = __shfl_up_sync(kFull, B, off);
-    if (ln >= off) {
-      B = fma(A, Bp, B);
-      A *= Ap;
-    }
-  }
-  double Ae = __shfl_up_sync(kFull, A, 1), Be = __shfl_up_sync(kFull, B, 1);
-  if (ln == 0) {
-    Ae = 1.0;
-    Be = 0.0;
-  }
-  double t = fma(Ae, h[0], Be);
-  for (int i = i0; i < i1; ++i) {
-    const double hi1 = h[i + 1];
-    col[i] = fma(cs[i], t, sn[i] * hi1);
-    t = fma(-sn[i], t, cs[i] * hi1);
-  }
-  const double Aall = __shfl_sync(kFull, A, kWarp - 1), Ball = __shfl_sync(kFull, B, kWarp - 1);
-  if (ln != 0) return;
-  const double a = fma(Aall, h[0], Ball), b = hj1;
-  const double den = hypot(a, b);
-  double c = 1.0, s = 0.0;
-  if (den != 0.0) {
-    c = a / den;
-    s = b / den;
-  }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = c * a + s * b;
-  col[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  scal[0] = fabs(g[j + 1]);
-  scal[1] = hj1 > 0.0 ? 1.0 / hj1 : 0.0;
-  scal[2] = hj1;
 }
 
 // g = (beta, 0, ...), scal[0] = beta

@@ -114,7 +114,7 @@ template <bool kNorm>
 __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_pair(double *y, const float2 *__restrict__ X, long long ldx,
                                                                  const double *__restrict__ c, int m, double sign,
                                                                  long long len, double *partial, const int *gate,
-                                                                 const int *m_dev = nullptr) {
+                                                                 const int *m_dev = nullptr, ArnoldiTail tail = {}) {
   if (gate && *gate == 0) return;
   if (m_dev) m = *m_dev;
   __shared__ float2 cs[512];
@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_pair(double *y, cons
   if (kNorm) {
     const double t = block_sum(sq);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (tail.ticket && last_cta(tail.ticket)) arnoldi_tail(tail, partial, m);
   }
 }
 

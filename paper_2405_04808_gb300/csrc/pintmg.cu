@@ -84,6 +84,10 @@ struct LevelData {
   int seg_len = 0;
   T *b = nullptr, *y = nullptr, *tmp = nullptr;
   T *chainU = nullptr, *chainM = nullptr, *sgs_w = nullptr;
+  // smoothing levels whose blocks fit on the GPU at once: all sweeps of a
+  // pre- or post-smoothing in one cooperative launch (k_sweeps_tri2)
+  bool persist = false;
+  SweepXchg<T> sx{};
 };
 
 struct Level {
@@ -157,6 +161,11 @@ struct mg_handle {
   int pair_basis = 0;   // the FGMRES basis as FP32 pairs with compensated dot products (MG_BASIS_PAIR)
   int pair_stall = 0;   // failure-detection tests: the streamed multi-dot issues no copies (its waits run out)
   int device = -1;      // the CUDA device current at mg_setup; every device buffer of the handle lives there
+  int persist_sweeps = 0;  // smoothing levels that fit on the GPU run all their sweeps in one launch
+                           // (off by default: no faster than one launch per sweep in a captured solve)
+  int sweep_stall = 0;     // failure-detection tests: the multi-sweep kernel's block 0 publishes nothing
+  int fuse_reduce = 1;     // Krylov reductions and the Arnoldi column in the last CTA of their kernels
+  unsigned *ticket = nullptr;  // [0] multi-dot, [1] second axpy: CTAs finished (reset by the last one)
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
   long long launches = 0;
@@ -374,6 +383,80 @@ void launch_apply(mg_handle *h, const LevelView<T> &L, const T *x, const T *b, T
   ck_launch();
 }
 
+// the multi-sweep kernel for this level's shape (p <= 128, two warps per block)
+template <typename T>
+void *sweeps_kernel(const LevelView<T> &L, int C) {
+  if (L.p == 4 * kWarp && L.q == L.p) return reinterpret_cast<void *>(k_sweeps_tri2<T, 4, 4 * kWarp>);
+  if (C == 1) return reinterpret_cast<void *>(k_sweeps_tri2<T, 1>);
+  if (C == 2) return reinterpret_cast<void *>(k_sweeps_tri2<T, 2>);
+  return reinterpret_cast<void *>(k_sweeps_tri2<T, 4>);
+}
+
+// Can every block of this smoothing level be resident at once (cooperative
+// launch of k_sweeps_tri2)?  If so, allocate its coupling exchange.
+template <typename T>
+void prepare_sweeps(mg_handle *h, Level &lev, LevelData<T> &d, cudaStream_t s) {
+  const LevelView<T> &L = d.view;
+  if (!h->persist_sweeps || !h->pair_tri || L.layout != MG_LAYOUT_TRIDIAG || !tri_stage_ok(L) || h->C > 4 ||
+      L.n + 1 > kPairMaxBlocks)
+    return;
+  int dev = 0, coop = 0, sms = 0;
+  ck(cudaGetDevice(&dev));
+  ck(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!coop) return;
+  void *kern = sweeps_kernel(L, h->C);
+  const size_t smem = 2 * (size_t)tri_pair_elems<T>(L.p) * sizeof(T);
+  ck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+  const long long grid = (L.n + 2) / 2;
+  if ((long long)per_sm * sms < grid) return;
+  const size_t xlen = 2 * (size_t)(L.n + 1) * L.p;
+  d.sx.xu = h->mem.alloc<T>(xlen);
+  d.sx.xm = h->mem.alloc<T>(xlen);
+  d.sx.fu = h->mem.alloc<unsigned>((size_t)(L.n + 1));
+  d.sx.fm = h->mem.alloc<unsigned>((size_t)(L.n + 1));
+  ck(cudaMemsetAsync(d.sx.fu, 0, (size_t)(L.n + 1) * sizeof(unsigned), s));
+  ck(cudaMemsetAsync(d.sx.fm, 0, (size_t)(L.n + 1) * sizeof(unsigned), s));
+  d.sx.err = h->flag + 2;  // the solve's timeout flag
+  d.sx.stall = h->sweep_stall;
+  d.persist = true;
+}
+
+// `sweeps` block-Jacobi sweeps of a level in one cooperative launch: from y = 0
+// (y0 null) or from y0, result in out (!= y0)
+template <typename T>
+void launch_sweeps(mg_handle *h, LevelData<T> &d, const T *r, const T *y0, T *out, int sweeps, T omega,
+                   cudaStream_t s) {
+  const LevelView<T> &L = d.view;
+  // per block and launch: coefficients (12 p) and r (4p + q) once, y0 (4p + q) if given, y out (4p + q);
+  // per sweep the two published couplings and the two read (4p).  Flops: 45 p per block and sweep
+  const double w = 4.0 * L.p + L.q, p_ = L.p;
+  const double per_block = sizeof(T) * (12.0 * p_ + (y0 ? 3.0 : 2.0) * w + 4.0 * p_ * (sweeps - 1));
+  Bracket br(h, CAT_BLOCK_SOLVE, s, per_block * (L.n + 1), 45.0 * p_ * (L.n + 1) * sweeps);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((L.n + 2) / 2), 1, 1);
+  cfg.blockDim = dim3(128, 1, 1);
+  cfg.dynamicSmemBytes = 2 * (size_t)tri_pair_elems<T>(L.p) * sizeof(T);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (L.p == 4 * kWarp && L.q == L.p) {
+    ck(cudaLaunchKernelEx(&cfg, k_sweeps_tri2<T, 4, 4 * kWarp>, L, r, y0, out, sweeps, omega, d.sx));
+  } else if (h->C == 1) {
+    ck(cudaLaunchKernelEx(&cfg, k_sweeps_tri2<T, 1>, L, r, y0, out, sweeps, omega, d.sx));
+  } else if (h->C == 2) {
+    ck(cudaLaunchKernelEx(&cfg, k_sweeps_tri2<T, 2>, L, r, y0, out, sweeps, omega, d.sx));
+  } else {
+    ck(cudaLaunchKernelEx(&cfg, k_sweeps_tri2<T, 4>, L, r, y0, out, sweeps, omega, d.sx));
+  }
+  ck_launch();
+}
+
 template <typename T>
 void launch_residual_restrict(mg_handle *h, const LevelView<T> &L, const T *y, const T *b, T *rc,
                               cudaStream_t s) {
@@ -421,12 +504,16 @@ void multidot(mg_handle *h, const double *V, long long ldv, int m, const double 
   {
     // algorithmic: read the m vectors and w once, 2 m len flops
     Bracket br(h, CAT_DOT, s, 8.0 * (m + (V == w ? 0 : 1)) * len, 2.0 * m * len);
+    // with fuse_reduce the last CTA reduces the partial sums into out (no second launch)
+    unsigned *tk = h->fuse_reduce ? h->ticket : nullptr;
 #define PINTMG_DOT(VBV)                                                                                      \
   do {                                                                                                       \
     if (pair)                                                                                                \
-      k_multidot_blocked<VBV, true><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev); \
+      k_multidot_blocked<VBV, true><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev,  \
+                                                                  tk, out, accumulate);                      \
     else                                                                                                     \
-      k_multidot_blocked<VBV, false><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev); \
+      k_multidot_blocked<VBV, false><<<grid, kDotThreads, 0, s>>>(V, ldv, m, w, len, h->partial, gate, m_dev, \
+                                                                   tk, out, accumulate);                     \
   } while (0)
     if (VB == 4)
       PINTMG_DOT(4);
@@ -437,7 +524,7 @@ void multidot(mg_handle *h, const double *V, long long ldv, int m, const double 
 #undef PINTMG_DOT
     ck_launch();
   }
-  {
+  if (!h->fuse_reduce) {
     Bracket br(h, CAT_SMALL, s);
     k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, 0, m, out, accumulate, gate, m_dev, VB, len);
     ck_launch();
@@ -494,10 +581,18 @@ void multidot_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const d
 }
 
 // CGS2 against the basis V (FP64) or Vp (pairs, when not null): K.h = the
-// coefficients, K.nrm2 = ||w||^2 of the orthogonalised w
-void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
-                   cudaStream_t s, const int *m_dev = nullptr, const float2 *Vp = nullptr) {
+// coefficients, K.nrm2 = ||w||^2 of the orthogonalised w.  With step (and the
+// fused reductions on), the last CTA of the second axpy also forms the
+// Arnoldi column j (index j_dev on the device if given): returns true, and
+// the caller launches no k_arnoldi_step.
+bool orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long long len, int j, double *w,
+                   cudaStream_t s, const int *m_dev = nullptr, const float2 *Vp = nullptr, bool step = false,
+                   const int *j_dev = nullptr) {
   const int m = j + 1;
+  const bool tail = step && h->fuse_reduce;
+  ArnoldiTail at{};
+  if (tail)
+    at = ArnoldiTail{h->ticket + 1, K.h, K.h + 512, K.nrm2, K.H, K.cs, K.sn, K.g, K.scal, h->ldh, j, j_dev};
   if (Vp) {
     const int G = grid_for(len / 2, kDotThreads, kDotGridCap);
     multidot_pair(h, Vp, len, m, w, len, K.h, s, m_dev);
@@ -510,9 +605,24 @@ void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long lon
     {
       Bracket br(h, CAT_PAIR_AXPY, s, 8.0 * (m + 2) * len, 2.0 * (m + 1) * len);
       k_multi_axpy_pair<true><<<G, kDotThreads, 0, s>>>(w, Vp, len, K.h + 512, m, -1.0, len, h->partial, nullptr,
-                                                         m_dev);
+                                                         m_dev, at);
       ck_launch();
     }
+  } else {
+    multidot(h, V, len, m, w, len, K.h, 0, s, nullptr, m_dev);
+    multi_axpy(h, w, V, len, K.h, m, -1.0, len, s, nullptr, m_dev);
+    multidot(h, V, len, m, w, len, K.h + 512, 0, s, nullptr, m_dev);
+    const bool pair = pair_ok(w, V, len, len);
+    const int G = pair ? grid_for(len / 2, kDotThreads, kDotGridCap) : grid_for(len, kDotThreads, kDotGridCap);
+    {
+      Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * (m + 1) * len);
+      if (pair)
+        k_multi_axpy_norm<true><<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev, at);
+      else
+        k_multi_axpy_norm<false><<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev, at);
+      ck_launch();
+    }
+    if (tail) return true;
     {
       Bracket br(h, CAT_SMALL, s);
       k_reduce_partials<<<1, 128, 0, s>>>(h->partial, G, 1, K.nrm2, 0);
@@ -523,21 +633,10 @@ void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long lon
       k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m, nullptr, m_dev);
       ck_launch();
     }
-    return;
+    return false;
   }
-  multidot(h, V, len, m, w, len, K.h, 0, s, nullptr, m_dev);
-  multi_axpy(h, w, V, len, K.h, m, -1.0, len, s, nullptr, m_dev);
-  multidot(h, V, len, m, w, len, K.h + 512, 0, s, nullptr, m_dev);
-  const bool pair = pair_ok(w, V, len, len);
-  const int G = pair ? grid_for(len / 2, kDotThreads, kDotGridCap) : grid_for(len, kDotThreads, kDotGridCap);
-  {
-    Bracket br(h, CAT_AXPY, s, 8.0 * (m + 2) * len, 2.0 * (m + 1) * len);
-    if (pair)
-      k_multi_axpy_norm<true><<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev);
-    else
-      k_multi_axpy_norm<false><<<G, kDotThreads, 0, s>>>(w, V, len, K.h + 512, m, len, h->partial, m_dev);
-    ck_launch();
-  }
+  if (tail) return true;
+  const int G = grid_for(len / 2, kDotThreads, kDotGridCap);
   {
     Bracket br(h, CAT_SMALL, s);
     k_reduce_partials<<<1, 128, 0, s>>>(h->partial, G, 1, K.nrm2, 0);
@@ -548,6 +647,7 @@ void orthogonalise(mg_handle *h, mg_handle::Krylov &K, const double *V, long lon
     k_add_inplace<<<(m + 127) / 128, 128, 0, s>>>(K.h, K.h + 512, m, nullptr, m_dev);
     ck_launch();
   }
+  return false;
 }
 
 // ||x|| into K.scal[0], 1/||x|| into K.scal[1]
@@ -563,8 +663,7 @@ void norm_into(mg_handle *h, mg_handle::Krylov &K, const double *x, long long le
 // Arnoldi step with the index j on the device (st->j, st->m1): no read-back
 void arnoldi_step_dev(mg_handle *h, mg_handle::Krylov &K, KState *st, int jmax, double *V, long long len, double *w,
                       cudaStream_t s, float2 *Vp = nullptr) {
-  orthogonalise(h, K, V, len, jmax, w, s, &st->m1, Vp);
-  {
+  if (!orthogonalise(h, K, V, len, jmax, w, s, &st->m1, Vp, true, &st->j)) {
     Bracket br(h, CAT_SMALL, s);
     k_arnoldi_step<<<1, kWarp, 0, s>>>(0, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal, &st->j);
     ck_launch();
@@ -616,8 +715,7 @@ cudaGraphConditionalHandle new_handle(cudaStream_t s) {
 // one Arnoldi step on basis V (column stride len): w = A z_j already in w
 void arnoldi_step(mg_handle *h, mg_handle::Krylov &K, double *V, long long len, int j, double *w, cudaStream_t s,
                   float2 *Vp = nullptr) {
-  orthogonalise(h, K, V, len, j, w, s, nullptr, Vp);
-  {
+  if (!orthogonalise(h, K, V, len, j, w, s, nullptr, Vp, true)) {
     Bracket br(h, CAT_SMALL, s);
     k_arnoldi_step<<<1, kWarp, 0, s>>>(j, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal);
     ck_launch();
@@ -1161,6 +1259,8 @@ void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
   T *y = y_out, *t = d.tmp;
   if (o.nu_pre == 0) {
     ck(cudaMemsetAsync(y, 0, lev.len * sizeof(T), s));
+  } else if (d.persist) {
+    launch_sweeps<T>(h, d, b, nullptr, y, o.nu_pre, (T)o.omega, s);  // all pre-sweeps, from y = 0
   } else {
     const T om = (T)o.omega;
     launch_block_solve<T>(h, d.view, b, nullptr, nullptr, y, s, nullptr, om);  // first sweep from y = 0
@@ -1187,10 +1287,15 @@ void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
     k_prolong_add<T><<<grid_for(lev.len, 256), 256, 0, s>>>(y, dn.y, lev.n, h->p, h->q, o.end_rule);
     ck_launch();
   }
-  for (int k = 0; k < o.nu_post; ++k) {
-    Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
-    launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s, y, (T)o.omega);
+  if (d.persist && o.nu_post > 0) {
+    launch_sweeps<T>(h, d, b, y, t, o.nu_post, (T)o.omega, s);  // all post-sweeps, from y
     std::swap(y, t);
+  } else {
+    for (int k = 0; k < o.nu_post; ++k) {
+      Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
+      launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s, y, (T)o.omega);
+      std::swap(y, t);
+    }
   }
   if (y != y_out) ck(cudaMemcpyAsync(y_out, y, lev.len * sizeof(T), cudaMemcpyDeviceToDevice, s));
 }
@@ -1212,8 +1317,9 @@ void precondition(mg_handle *h, const double *v, double *z, cudaStream_t s) {
 // Setup helpers
 
 template <typename T>
-void alloc_level_vectors(mg_handle *h, Level &lev, LevelData<T> &d, bool is_last, bool is_first) {
+void alloc_level_vectors(mg_handle *h, Level &lev, LevelData<T> &d, bool is_last, bool is_first, cudaStream_t s) {
   const long long len = lev.len;
+  if (!is_last) prepare_sweeps<T>(h, lev, d, s);
   d.tmp = h->mem.alloc<T>(len);
   if (!is_first || sizeof(T) == sizeof(float)) {
     d.b = h->mem.alloc<T>(len);
@@ -1434,6 +1540,8 @@ void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, in
 // workspace of a solve with restart m (grown on demand)
 void prepare_solve(mg_handle *h, int m, cudaStream_t s) {
   ensure_fgmres_space(h, m, s);
+  // a solve that stopped early (a timed-out wait) may have left a count behind
+  ck(cudaMemsetAsync(h->ticket, 0, 4 * sizeof(unsigned), s));
   if (!h->fw) {
     const long long len = h->lv[0].len;
     h->fw = h->mem.alloc<double>(len);
@@ -1643,6 +1751,11 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (O->krylov_basis != MG_BASIS_FP64 && O->krylov_basis != MG_BASIS_PAIR) return MG_ERR_ARG;
   if (O->restrict_rule != MG_RESTRICT_INJECT && O->restrict_rule != MG_RESTRICT_TRANSPOSE) return MG_ERR_ARG;
   if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
+  if (O->levels > 1 && P->separable != 1) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error,
+                  "mg_setup: coarse levels need a separable problem (separable = 1)");
+    return MG_ERR_ARG;
+  }
   if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
   if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;
   if (layout == MG_LAYOUT_TRIDIAG && p > 32 * 16) return MG_ERR_UNSUPPORTED;
@@ -1684,6 +1797,15 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
   // PINTMG_TRI_PAIR=0 keeps one warp per block on every level (tests)
   if (const char *e = std::getenv("PINTMG_TRI_PAIR")) h->pair_tri = std::atoi(e) != 0;
+  // PINTMG_FUSE_REDUCE=0 reduces dot products and forms the Arnoldi column in separate launches (tests)
+  if (const char *e = std::getenv("PINTMG_FUSE_REDUCE")) h->fuse_reduce = std::atoi(e) != 0;
+  // PINTMG_PERSIST=1 runs each smoothing of a level that fits on the GPU as one cooperative
+  // launch (k_sweeps_tri2); 0 (the default) launches every block-Jacobi sweep separately
+  if (const char *e = std::getenv("PINTMG_PERSIST")) h->persist_sweeps = std::atoi(e) != 0;
+  // PINTMG_TEST_SWEEP_STALL=1 (tests of the bounded waits): the multi-sweep kernel's
+  // block 0 never publishes its coupling, so block 1's wait runs out (2 s) and the
+  // solve returns MG_ERR_TIMEOUT; the handle stays unusable for solves afterwards
+  if (const char *e = std::getenv("PINTMG_TEST_SWEEP_STALL")) h->sweep_stall = std::atoi(e) != 0;
   // PINTMG_TEST_PAIR_STALL=1 (tests of the bounded waits): the pair multi-dot's
   // producer issues nothing, so its consumers give up after 2 s and the solve
   // returns MG_ERR_TIMEOUT
@@ -1714,6 +1836,8 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     ck(cudaMemcpyAsync(dJzp, P->Jz_prev, (size_t)nz * zsz * sizeof(double), cudaMemcpyHostToDevice, s));
     h->flag = h->mem.alloc<int>(4);
     ck(cudaMemsetAsync(h->flag, 0, 4 * sizeof(int), s));
+    h->ticket = h->mem.alloc<unsigned>(4);
+    ck(cudaMemsetAsync(h->ticket, 0, 4 * sizeof(unsigned), s));
 
     // index maps per level (injection reading of the coarse linearisation points)
     std::vector<int> cur(n), prev(n);
@@ -1846,7 +1970,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
           }
         }
       }
-      alloc_level_vectors<double>(h, lev, lev.d, l == L - 1, l == 0);
+      alloc_level_vectors<double>(h, lev, lev.d, l == L - 1, l == 0, s);
       if (O->precision != MG_PRECISION_FP64) {
         LevelView<float> &f = lev.f.view;
         f.n = nl;
@@ -1876,7 +2000,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
           }
           if (lev.d.scan_tmp) lev.f.scan_tmp = h->mem.alloc<float>((size_t)nl * p);
         }
-        alloc_level_vectors<float>(h, lev, lev.f, l == L - 1, l == 0);
+        alloc_level_vectors<float>(h, lev, lev.f, l == L - 1, l == 0, s);
       }
       // next level's maps: coarse K <- fine 2K (current), max(2K-1, 0) (previous)
       if (l + 1 < L) {
@@ -1943,14 +2067,18 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
 int mg_vcycle(mg_handle *h, const double *r, double *y, void *stream) {
   if (!h || !r || !y || r == y) return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int tmo = 0;
   try {
+    ck(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), s));
     precondition(h, r, y, s);
+    ck(cudaMemcpyAsync(&tmo, h->flag + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
   } catch (const CudaFail &) {
     return MG_ERR_CUDA;
   } catch (const std::bad_alloc &) {
     return MG_ERR_OOM;
   }
-  return MG_OK;
+  return tmo ? MG_ERR_TIMEOUT : MG_OK;
 }
 
 int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, int maxit, int restart,

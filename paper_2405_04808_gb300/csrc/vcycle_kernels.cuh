@@ -409,6 +409,307 @@ __global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Several block-Jacobi sweeps of one level in one launch (two warps per time
+// block, as k_block_solve_tri2).  Each warp pair owns one block for all
+// sweeps: the block's coefficients are staged into shared memory once, its
+// right-hand side and its iterate stay in registers, and only the couplings
+// cross blocks: after sweep k a block publishes u_j (warp 0) and mu_{j-1}
+// (warp 1) into a double-buffered exchange array and raises a per-block
+// counter; sweep k + 1 of block j waits for the counters of blocks j - 1 (u)
+// and j + 1 (mu).  Counters only grow (every block of a level ends a launch at
+// the same count, which is where the next launch starts), so nothing resets
+// them between launches.  The launch must be cooperative (every CTA resident
+// at once); a wait gives up after kSweepWaitNs, sets err[0] and the kernel
+// finishes without further waits (results void, the solve reports a timeout).
+// Same arithmetic in the same order as `sweeps` launches of k_block_solve_tri2:
+// bitwise-equal results.  y0 null: start from y = 0; else from y0 (out != y0).
+
+constexpr unsigned long long kSweepWaitNs = 2000000000ull;  // 2 s
+
+template <typename T>
+struct SweepXchg {
+  T *xu;         // [2][n + 1][p]: u_j published by block j after sweep k (slot k & 1)
+  T *xm;         // [2][n + 1][p]: mu_{j-1} published by block j
+  unsigned *fu;  // [n + 1] sweeps completed by block j's warp 0 (its u published)
+  unsigned *fm;  // [n + 1] sweeps completed by block j's warp 1 (its mu published)
+  int *err;      // set when a wait runs out
+  int stall;     // failure-detection tests only: block 0 never publishes its u (a wait on it runs out)
+};
+
+__device__ __forceinline__ unsigned long long sweep_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// every lane polls the counter until it reaches `target` (acquire); false when
+// err[0] is set or the wait runs out (then err[0] is set)
+__device__ __forceinline__ bool sweep_wait(const unsigned *flag, unsigned target, int *err) {
+  const unsigned long long t0 = sweep_clock_ns();
+  for (unsigned it = 1;; ++it) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(flag) : "memory");
+    if ((int)(v - target) >= 0) return true;
+    if (*(volatile int *)err) return false;
+    if ((it & 15u) == 0 && sweep_clock_ns() - t0 > kSweepWaitNs) {
+      atomicOr(err, 1);
+      return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+// the warp's stores are made visible device-wide, then lane 0 raises the counter (release)
+__device__ __forceinline__ void sweep_publish(unsigned *flag, unsigned value, int ln) {
+  __threadfence();
+  __syncwarp();
+  if (ln == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(flag), "r"(value) : "memory");
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void relax_regs(T (&x)[C], const T (&o)[C], T omega) {
+#pragma unroll
+  for (int e = 0; e < C; ++e) x[e] = fma(omega, x[e] - o[e], o[e]);
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void load_cg(T (&x)[C], const T *src, int p, int ln) {
+#pragma unroll
+  for (int e = 0; e < C; ++e) {
+    const int i = ln * C + e;
+    x[e] = (i < p) ? __ldcg(src + i) : T(0);
+  }
+}
+
+template <typename T, int C, int PF = 0>
+__global__ void __launch_bounds__(128) k_sweeps_tri2(LevelView<T> L, const T *__restrict__ r, const T *y0, T *out,
+                                                     int sweeps, T omega, SweepXchg<T> X) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int w = threadIdx.x / kWarp, pair = w >> 1, role = w & 1;
+  const int j = blockIdx.x * 2 + pair;
+  const int n = L.n, p = PF ? PF : L.p, q = PF ? PF : L.q;
+  if (j > n) return;
+  const long long np1p = (long long)(n + 1) * p;
+  extern __shared__ __align__(16) unsigned char sw2_smem[];
+  T *base = reinterpret_cast<T *>(sw2_smem) + pair * tri_pair_elems<T>(p);
+  T *xch = base + 12 * p + kScanPerBlock;
+  Vec<const T> R = make_cvec(r, n, p, q);
+  Vec<T> Y = make_vec(out, n, p, q);
+  Vec<const T> Y0 = make_cvec(y0 ? y0 : r, n, p, q);
+  const bool relax = omega != T(1);
+  bool live = true;  // false once a wait has given up: no further waits
+  if (role == 1 && j == n) {  // last block: v = -(r_mu - u_{n-1}), mu = v - r_v
+    const unsigned s0 = *(volatile unsigned *)&X.fm[j];
+    T rv[C], rm[C], v[C], m[C], vo[C], mo[C];
+    chunk_load<T, C>(rv, R.v + (long long)(j - 1) * p, p, ln);
+    chunk_load<T, C>(rm, R.m + (long long)(j - 1) * p, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) vo[e] = mo[e] = T(0);
+    if (y0) {
+      chunk_load<T, C>(vo, Y0.v + (long long)(j - 1) * p, p, ln);
+      chunk_load<T, C>(mo, Y0.m + (long long)(j - 1) * p, p, ln);
+    }
+    for (int k = 0; k < sweeps; ++k) {
+      T c[C];
+      if (k == 0) {
+        if (y0) chunk_load<T, C>(c, Y0.u + (long long)(j - 1) * p, p, ln);
+      } else {
+        if (live) live = sweep_wait(&X.fu[j - 1], s0 + k, X.err);
+        load_cg<T, C>(c, X.xu + ((k - 1) & 1) * np1p + (long long)(j - 1) * p, p, ln);
+      }
+#pragma unroll
+      for (int e = 0; e < C; ++e) {
+        v[e] = (k == 0 && !y0) ? -rm[e] : -(rm[e] - c[e]);
+        m[e] = v[e] - rv[e];
+      }
+      if (relax) {
+        relax_regs<T, C>(v, vo, omega);
+        relax_regs<T, C>(m, mo, omega);
+      }
+#pragma unroll
+      for (int e = 0; e < C; ++e) { vo[e] = v[e]; mo[e] = m[e]; }
+      if (k + 1 < sweeps) {
+        chunk_store<T, C>(X.xm + (k & 1) * np1p + (long long)j * p, m, p, ln);
+        sweep_publish(&X.fm[j], s0 + k + 1, ln);
+      }
+    }
+    chunk_store<T, C>(Y.v + (long long)(j - 1) * p, vo, p, ln);
+    chunk_store<T, C>(Y.m + (long long)(j - 1) * p, mo, p, ln);
+    // the counter still advances by `sweeps` so that every block ends the launch at the same count
+    sweep_publish(&X.fm[j], s0 + sweeps, ln);
+    return;
+  }
+  if (j == n) return;  // warp 0 of the last block has nothing to do
+  const TriBlock<T> G = tri_block(L, j);
+  if (role == 0) {
+    const unsigned s0 = *(volatile unsigned *)&X.fu[j];
+    stage16(base, G.N, 3 * p, ln);
+    stage16(base + 9 * p, G.fac, 3 * p, ln);
+    stage16(base + 12 * p, G.scan, kScanPerBlock, ln);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    T ru[C], rl[C], uo[C], lo[C];
+    chunk_load<T, C>(ru, R.u + (long long)j * p, p, ln);
+    chunk_load<T, C>(rl, R.l + (long long)j * p, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) uo[e] = lo[e] = T(0);
+    if (y0) {
+      chunk_load<T, C>(uo, Y0.u + (long long)j * p, p, ln);
+      chunk_load<T, C>(lo, Y0.l + (long long)j * p, p, ln);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    const T *N = base, *fac = base + 9 * p, *scan = base + 12 * p;
+    for (int k = 0; k < sweeps; ++k) {
+      T ruk[C];
+      if (k == 0 && !y0) {
+#pragma unroll
+        for (int e = 0; e < C; ++e) ruk[e] = ru[e];
+      } else {
+        T c[C];
+        if (k == 0) {
+          chunk_load<T, C>(c, Y0.m + (long long)j * p, p, ln);
+        } else {
+          if (live) live = sweep_wait(&X.fm[j + 1], s0 + k, X.err);
+          load_cg<T, C>(c, X.xm + ((k - 1) & 1) * np1p + (long long)(j + 1) * p, p, ln);
+        }
+#pragma unroll
+        for (int e = 0; e < C; ++e) ruk[e] = ru[e] - c[e];
+      }
+      T rhs[C], l[C], u[C];
+      tri_mv<T, C, false>(rhs, N, ruk, p, ln, T(1));
+      pair_barrier(1 + pair);  // warp 1's part is in xch
+      T part[C];
+      chunk_load<T, C>(part, xch, p, ln);
+#pragma unroll
+      for (int e = 0; e < C; ++e) rhs[e] += part[e];
+      penta_solve<T, C>(l, rhs, fac, scan, p, ln);
+      pair_barrier(1 + pair);  // warp 1 has read xch: reuse it for lambda
+      chunk_store<T, C>(xch, l, p, ln);
+      pair_barrier(1 + pair);
+#pragma unroll
+      for (int e = 0; e < C; ++e) u[e] = ruk[e];
+      tri_mtv<T, C, true>(u, N, l, p, ln, T(-1));
+      if (relax) {
+        relax_regs<T, C>(u, uo, omega);
+        relax_regs<T, C>(l, lo, omega);
+      }
+#pragma unroll
+      for (int e = 0; e < C; ++e) { uo[e] = u[e]; lo[e] = l[e]; }
+      const bool mute = X.stall && j == 0;
+      if (k + 1 < sweeps && !mute) {
+        chunk_store<T, C>(X.xu + (k & 1) * np1p + (long long)j * p, u, p, ln);
+        sweep_publish(&X.fu[j], s0 + k + 1, ln);
+      }
+    }
+    chunk_store<T, C>(Y.u + (long long)j * p, uo, p, ln);
+    chunk_store<T, C>(Y.l + (long long)j * p, lo, p, ln);
+    if (!(X.stall && j == 0)) sweep_publish(&X.fu[j], s0 + sweeps, ln);
+  } else {
+    const unsigned s0 = *(volatile unsigned *)&X.fm[j];
+    stage16(base + 3 * p, G.V, 3 * p, ln);
+    stage16(base + 6 * p, G.Z, 3 * p, ln);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    T rz[C], rl[C], rv[C], rm[C], zo[C], vo[C], mo[C];
+    chunk_load<T, C>(rz, R.z + (long long)j * q, q, ln);
+    chunk_load<T, C>(rl, R.l + (long long)j * p, p, ln);
+#pragma unroll
+    for (int e = 0; e < C; ++e) { rv[e] = rm[e] = zo[e] = vo[e] = mo[e] = T(0); }
+    if (j >= 1) {
+      chunk_load<T, C>(rv, R.v + (long long)(j - 1) * p, p, ln);
+      chunk_load<T, C>(rm, R.m + (long long)(j - 1) * p, p, ln);
+    }
+    if (y0) {
+      chunk_load<T, C>(zo, Y0.z + (long long)j * q, q, ln);
+      if (j >= 1) {
+        chunk_load<T, C>(vo, Y0.v + (long long)(j - 1) * p, p, ln);
+        chunk_load<T, C>(mo, Y0.m + (long long)(j - 1) * p, p, ln);
+      }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    const T *V = base + 3 * p, *Z = base + 6 * p;
+    const T kappa = L.kappa;
+    for (int k = 0; k < sweeps; ++k) {
+      T v[C], part[C];
+      if (j >= 1) {
+        if (k == 0 && !y0) {
+#pragma unroll
+          for (int e = 0; e < C; ++e) v[e] = -rm[e];
+        } else {
+          T c[C];
+          if (k == 0) {
+            chunk_load<T, C>(c, Y0.u + (long long)(j - 1) * p, p, ln);
+          } else {
+            if (live) live = sweep_wait(&X.fu[j - 1], s0 + k, X.err);
+            load_cg<T, C>(c, X.xu + ((k - 1) & 1) * np1p + (long long)(j - 1) * p, p, ln);
+          }
+#pragma unroll
+          for (int e = 0; e < C; ++e) v[e] = -(rm[e] - c[e]);
+        }
+      }
+      if (kappa != T(0) && j >= 1) {  // V = kappa Z: one product
+        T wz[C];
+#pragma unroll
+        for (int e = 0; e < C; ++e) wz[e] = fma(kappa, v[e], rz[e]);
+        tri_mv<T, C, false>(part, Z, wz, p, ln, T(1));
+#pragma unroll
+        for (int e = 0; e < C; ++e) part[e] -= rl[e];
+      } else {
+        tri_mv<T, C, false>(part, Z, rz, p, ln, T(1));
+#pragma unroll
+        for (int e = 0; e < C; ++e) part[e] -= rl[e];
+        if (j >= 1) tri_mv<T, C, true>(part, V, v, p, ln, T(1));
+      }
+      chunk_store<T, C>(xch, part, p, ln);
+      pair_barrier(1 + pair);
+      pair_barrier(1 + pair);  // warp 0 has read the part
+      pair_barrier(1 + pair);  // lambda is in xch
+      T l[C], z[C], t[C];
+      chunk_load<T, C>(l, xch, p, ln);
+      if (kappa != T(0)) {
+        tri_mtv<T, C, false>(t, Z, l, p, ln, T(1));
+#pragma unroll
+        for (int e = 0; e < C; ++e) z[e] = rz[e] - t[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < C; ++e) z[e] = rz[e];
+        tri_mtv<T, C, true>(z, Z, l, p, ln, T(-1));
+      }
+      if (relax) relax_regs<T, C>(z, zo, omega);
+#pragma unroll
+      for (int e = 0; e < C; ++e) zo[e] = z[e];
+      if (j >= 1) {
+        T m[C];
+        if (kappa != T(0)) {
+#pragma unroll
+          for (int e = 0; e < C; ++e) m[e] = fma(kappa, t[e], v[e] - rv[e]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < C; ++e) m[e] = v[e] - rv[e];
+          tri_mtv<T, C, true>(m, V, l, p, ln, T(1));
+        }
+        if (relax) {
+          relax_regs<T, C>(v, vo, omega);
+          relax_regs<T, C>(m, mo, omega);
+        }
+#pragma unroll
+        for (int e = 0; e < C; ++e) { vo[e] = v[e]; mo[e] = m[e]; }
+        if (k + 1 < sweeps) {
+          chunk_store<T, C>(X.xm + (k & 1) * np1p + (long long)j * p, m, p, ln);
+          sweep_publish(&X.fm[j], s0 + k + 1, ln);
+        }
+      }
+    }
+    chunk_store<T, C>(Y.z + (long long)j * q, zo, q, ln);
+    if (j >= 1) {
+      chunk_store<T, C>(Y.v + (long long)(j - 1) * p, vo, p, ln);
+      chunk_store<T, C>(Y.m + (long long)(j - 1) * p, mo, p, ln);
+    }
+    sweep_publish(&X.fm[j], s0 + sweeps, ln);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const T *__restrict__ r,
                                                            const T *cplU, const T *cplM, T *out,

@@ -53,7 +53,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class MGProblem(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
                 ("theta", ctypes.c_double), ("gamma", ctypes.c_double), ("jz_const", ctypes.c_int),
-                ("M", _dp), ("Ju_cur", _dp), ("Ju_prev", _dp), ("Jz_cur", _dp), ("Jz_prev", _dp)]
+                ("M", _dp), ("Ju_cur", _dp), ("Ju_prev", _dp), ("Jz_cur", _dp), ("Jz_prev", _dp),
+                ("separable", ctypes.c_int)]
 
 
 class MGOptions(ctypes.Structure):
@@ -164,16 +165,19 @@ def _c(arr):
 
 def mg_setup(prob, levels=2, nu_pre=1, nu_post=1, coarse_rtol=1e-3, coarse_maxit=50,
              coarse_fixed_iters=0, end_rule=0, precision=MG_PRECISION_FP64, omega=1.0, coarse_precond="sgs",
-             device_loops=True, krylov_basis="fp64", restrict="inject", stream=0):
+             device_loops=True, krylov_basis="fp64", restrict="inject", separable=True, stream=0):
     """Build the device hierarchy for a workloads.Problem; returns an opaque handle (int).
     krylov_basis: "fp64" (the plain method) or "pair" (FP32-pair basis with compensated dot products).
-    restrict: "inject" (Sec. 5.3.1's variable formulas applied to the residual) or "transpose" (R = P^T)."""
+    restrict: "inject" (Sec. 5.3.1's variable formulas applied to the residual) or "transpose" (R = P^T).
+    separable: the caller's assertion that d_u f does not depend on z and f is affine in z (true for both
+    workloads), which the rediscretised coarse levels need."""
     keep = []
     P = MGProblem()
     P.layout = MG_LAYOUT_TRIDIAG if prob.kind == "tridiag" else MG_LAYOUT_DENSE
     P.n, P.p, P.q = prob.n, prob.p, prob.q
     P.theta, P.gamma = prob.theta, prob.gamma
     P.jz_const = 1 if prob.jz_const else 0
+    P.separable = 1 if separable else 0
     for name in ("M", "Ju_cur", "Ju_prev", "Jz_cur", "Jz_prev"):
         a, ptr = _c(getattr(prob, name))
         keep.append(a)

@@ -8,6 +8,12 @@ vectors = 159 MB) for the Gram-Schmidt kernels.
     python -m paper_2405_04808_gb300.profile_cases conv_fwd_fp32
     python -m paper_2405_04808_gb300.profile_cases train_step
     python -m paper_2405_04808_gb300.profile_cases fgmres_cycle [--basis pair|fp64]
+    python -m paper_2405_04808_gb300.profile_cases vcycle [--restrict transpose|inject]
+
+vcycle: V-cycles of the benchmark system (Burgers nx=128, nt=1024, 3 levels,
+4/4 sweeps; weighted sweeps omega = 2/3 with the transposed restriction by
+default), one mg_vcycle per repetition, host-driven, so every kernel of the
+cycle launches on its own.
 
 Each case runs a warm-up and then `--reps` launches of the kernels it names,
 and exits non-zero on any library error.
@@ -59,7 +65,8 @@ def main(argv=None):
         print(summarize(argv[1]))
         return 0
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step", "fgmres_cycle"])
+    ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step", "fgmres_cycle", "vcycle"])
+    ap.add_argument("--restrict", default="transpose", choices=["transpose", "inject"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--basis", default="pair", choices=["pair", "fp64"])
@@ -68,6 +75,23 @@ def main(argv=None):
 
     from . import pintmg as P
     from . import workloads as W
+    if args.case == "vcycle":
+        prob = W.burgers(nx=128, n=1024, nu=0.01, seed=2000)
+        omega = 2.0 / 3.0 if args.restrict == "transpose" else 1.0
+        h = P.mg_setup(prob, levels=3, nu_pre=4, nu_post=4, omega=omega, restrict=args.restrict,
+                       device_loops=False)
+        try:
+            r = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+            y = torch.empty_like(r)
+            for _ in range(1 + args.reps):
+                code = P.mg_vcycle(h, r.data_ptr(), y.data_ptr())
+                if code != P.MG_OK:
+                    raise P.PintmgError(code, "mg_vcycle")
+            torch.cuda.synchronize()
+            print(f"vcycle ({args.restrict}): {1 + args.reps} cycles, |y| = {float(torch.linalg.norm(y)):.6e}")
+        finally:
+            P.mg_destroy(h)
+        return 0
     if args.case == "fgmres_cycle":
         # 120 FGMRES iterations without restart (tolerance out of reach): the
         # basis grows to 121 vectors; host-driven loops launch each kernel alone

@@ -1,0 +1,61 @@
+"""Krylov reductions fused into the kernels that produce their partial sums
+(the last CTA of a multi-dot reduces it; the last CTA of CGS2's second axpy
+forms ||w||^2, adds the two passes' coefficients and the Arnoldi column)
+against separate reduction / step launches: the same sums in the same order,
+so bitwise-equal solves with fewer launches per iteration."""
+import numpy as np
+import pytest
+
+from oracle import augmented as O
+from paper_2405_04808_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2405_04808_gb300 import pintmg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pintmg.lib()
+    return pintmg
+
+
+def _solve(P, prob, opts, monkeypatch, fused, restart):
+    monkeypatch.setenv("PINTMG_FUSE_REDUCE", "1" if fused else "0")
+    h = P.mg_setup(prob, **opts)
+    monkeypatch.delenv("PINTMG_FUSE_REDUCE")
+    try:
+        b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        n0 = P.mg_launch_count(h)
+        code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, 500, restart)
+        torch.cuda.synchronize()
+        assert code == P.MG_OK, P.mg_status_string(code)
+        return x.cpu().numpy(), info, P.mg_launch_count(h) - n0
+    finally:
+        P.mg_destroy(h)
+
+
+@pytest.mark.parametrize("basis", ["fp64", "pair"])
+@pytest.mark.parametrize("loops", [False, True])
+@pytest.mark.parametrize("case", [0, 1])
+def test_fused_reductions_are_bitwise_neutral(P, monkeypatch, basis, loops, case):
+    prob, opts, restart = [
+        (W.burgers(nx=40, n=32, seed=401), dict(levels=2, nu_pre=2, nu_post=2, omega=2.0 / 3.0,
+                                               restrict="transpose"), 7),   # restarts every 7 iterations
+        (W.vdp(n=64, seed=402), dict(levels=3, nu_pre=1, nu_post=1), 40),
+    ][case]
+    opts = dict(opts, krylov_basis=basis, device_loops=loops)
+    x1, i1, l1 = _solve(P, prob, opts, monkeypatch, True, restart)
+    x0, i0, l0 = _solve(P, prob, opts, monkeypatch, False, restart)
+    assert (i1.iters, i1.coarse_iters) == (i0.iters, i0.coarse_iters)
+    assert i1.true_relres == i0.true_relres and np.array_equal(x1, x0)
+    if not loops:
+        # per FGMRES and coarse GMRES iteration: no separate reductions, coefficient sum or Arnoldi step
+        steps = i1.iters + i1.coarse_iters
+        saved_per_step = 3 if basis == "pair" else 5
+        assert l0 - l1 >= saved_per_step * steps, (l0, l1, steps)
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(x1 - xd) <= 1e-9 * np.linalg.norm(xd)

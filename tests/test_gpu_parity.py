@@ -134,6 +134,12 @@ def test_host_and_device_buffers_agree(P):
 
 
 def test_error_paths(P):
+    # coarse levels need the separable-control assertion (rediscretised coarse operator); one level does not
+    prob = W.vdp(n=16, seed=120)
+    with pytest.raises(P.PintmgError) as e:
+        P.mg_setup(prob, levels=2, separable=False)
+    assert e.value.code == P.MG_ERR_ARG and "separable" in P.mg_last_cuda_error()
+    P.mg_destroy(P.mg_setup(prob, levels=1, separable=False))
     # singular N_k (Thm 1 fails): M - theta dt Ju = 0 for one step
     prob = W.vdp(n=16, seed=121)
     prob.Ju_cur[5] = prob.M / (prob.theta * prob.dt)

@@ -164,7 +164,8 @@ struct mg_handle {
   int persist_sweeps = 0;  // smoothing levels that fit on the GPU run all their sweeps in one launch
                            // (off by default: no faster than one launch per sweep in a captured solve)
   int sweep_stall = 0;     // failure-detection tests: the multi-sweep kernel's block 0 publishes nothing
-  int fuse_reduce = 1;     // Krylov reductions and the Arnoldi column in the last CTA of their kernels
+  int fuse_reduce = 1;     // Krylov reductions and the Arnoldi column in the last CTA of their kernels:
+                           // 0 never, 1 the Arnoldi column and dot products of <= 16 vectors, 2 always
   unsigned *ticket = nullptr;  // [0] multi-dot, [1] second axpy: CTAs finished (reset by the last one)
   // optional per-category kernel timing (CUDA events on the launch stream)
   int prof = 0;
@@ -501,11 +502,14 @@ void multidot(mg_handle *h, const double *V, long long ldv, int m, const double 
   const int items = ((m + VB - 1) / VB) * dot_parts(m, VB, len);
   const int grid = std::min(items, kDotGridCap);
   const bool pair = pair_ok(V, w, len, ldv);
+  // fused: the last CTA reduces the partial sums into out (no second launch).  One CTA
+  // summing many vectors' partials takes longer than a separate parallel reduction,
+  // so by default only short ones are fused (m is the host's bound on the count)
+  const bool fuse = h->fuse_reduce >= 2 || (h->fuse_reduce == 1 && m <= 16);
+  unsigned *tk = fuse ? h->ticket : nullptr;
   {
     // algorithmic: read the m vectors and w once, 2 m len flops
     Bracket br(h, CAT_DOT, s, 8.0 * (m + (V == w ? 0 : 1)) * len, 2.0 * m * len);
-    // with fuse_reduce the last CTA reduces the partial sums into out (no second launch)
-    unsigned *tk = h->fuse_reduce ? h->ticket : nullptr;
 #define PINTMG_DOT(VBV)                                                                                      \
   do {                                                                                                       \
     if (pair)                                                                                                \
@@ -524,7 +528,7 @@ void multidot(mg_handle *h, const double *V, long long ldv, int m, const double 
 #undef PINTMG_DOT
     ck_launch();
   }
-  if (!h->fuse_reduce) {
+  if (!tk) {
     Bracket br(h, CAT_SMALL, s);
     k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, 0, m, out, accumulate, gate, m_dev, VB, len);
     ck_launch();
@@ -1797,8 +1801,9 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
   // PINTMG_TRI_PAIR=0 keeps one warp per block on every level (tests)
   if (const char *e = std::getenv("PINTMG_TRI_PAIR")) h->pair_tri = std::atoi(e) != 0;
-  // PINTMG_FUSE_REDUCE=0 reduces dot products and forms the Arnoldi column in separate launches (tests)
-  if (const char *e = std::getenv("PINTMG_FUSE_REDUCE")) h->fuse_reduce = std::atoi(e) != 0;
+  // PINTMG_FUSE_REDUCE=0 reduces dot products and forms the Arnoldi column in separate launches,
+  // 2 fuses every dot product's reduction (tests, measurements); 1 is the default
+  if (const char *e = std::getenv("PINTMG_FUSE_REDUCE")) h->fuse_reduce = std::min(2, std::max(0, std::atoi(e)));
   // PINTMG_PERSIST=1 runs each smoothing of a level that fits on the GPU as one cooperative
   // launch (k_sweeps_tri2); 0 (the default) launches every block-Jacobi sweep separately
   if (const char *e = std::getenv("PINTMG_PERSIST")) h->persist_sweeps = std::atoi(e) != 0;

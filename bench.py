@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="burgers_nx128_n1024", choices=sorted(W.WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32s"],
-                    help="fp32: V-cycle in FP32; fp32s: smoother and transfers in FP32, coarse solve in FP64")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32s", "bf16"],
+                    help="fp32: V-cycle in FP32; fp32s: smoother and transfers in FP32, coarse solve in FP64; "
+                         "bf16: the FP32 V-cycle with the smoothing levels' bands stored in BF16")
     ap.add_argument("--restart", type=int, default=None,
                     help="FGMRES restart length (default: the workload's, from a sweep of solve times)")
     ap.add_argument("--krylov-basis", default="fp64", choices=["fp64", "pair"],
@@ -267,7 +268,8 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
     solve (kernels inside a captured graph cannot be bracketed); then warm-up,
     `steps` timed solves and the end-to-end solves in the timed mode
     (default: one CUDA graph per solve with device-side loops)."""
-    prec = {"fp64": P.MG_PRECISION_FP64, "fp32": P.MG_PRECISION_FP32, "fp32s": P.MG_PRECISION_FP32_SMOOTH}[precision]
+    prec = {"fp64": P.MG_PRECISION_FP64, "fp32": P.MG_PRECISION_FP32, "fp32s": P.MG_PRECISION_FP32_SMOOTH,
+            "bf16": P.MG_PRECISION_BF16_BANDS}[precision]
     lv = levels or wl["levels"]
     restart = restart or args.restart
     workload = workload or args.workload
@@ -454,7 +456,7 @@ def measure_paper_behaviour(P, torch, prob, wl, args, dev, stream, world, varian
            "clocks": m["clocks"], "omega": pb["omega"], "restrict": pb["restrict"], "restart": pb["restart"],
            "variants": {}}
     for name, prec, kb in (("fp32_vcycle", "fp32", None), ("fp32_smoother_fp64_coarse", "fp32s", None),
-                           ("pair_krylov_basis", "fp64", "pair")):
+                           ("bf16_bands_fp32_vcycle", "bf16", None), ("pair_krylov_basis", "fp64", "pair")):
         v = measure(P, torch, prob, wl, args, prec, pb["omega"], max(1, min(args.steps, 3)), 1, dev, stream, world,
                     False, basis=kb, restrict=pb["restrict"], restart=pb["restart"])
         out["variants"][name] = variant_entry(v, prec, pb["omega"], None, kb, pb["restrict"], pb["restart"])
@@ -467,8 +469,9 @@ C3_WORKLOAD = "burgers_nx512_n8192"
 def measure_c3(P, torch, args, dev, stream, world):
     """Burgers nx = 512, nt = 8192 (21 M unknowns, 168 MB per FP64 vector, four
     levels, 4/4 sweeps), the mixed-precision configuration: the paper-behaviour
-    reading in FP64, with the FP32 V-cycle and with FP32 smoothing and an FP64
-    coarse solve; each solve's iterations at 1e-8 and its FP64 true residual
+    reading in FP64, with the FP32 V-cycle, with FP32 smoothing and an FP64
+    coarse solve, and with the FP32 V-cycle reading BF16 bands; each solve's
+    iterations at 1e-8 and its FP64 true residual
     (the library's operator; the oracle's assembled operator checks the same
     residual in tests/test_gpu_fullsize.py)."""
     wl = W.WORKLOADS[C3_WORKLOAD]
@@ -477,7 +480,8 @@ def measure_c3(P, torch, args, dev, stream, world):
     res = {"workload": C3_WORKLOAD, "n": prob.n, "p": prob.p, "unknowns": prob.size, "levels": wl["levels"],
            "omega": pb["omega"], "restrict": pb["restrict"], "restart": pb["restart"]}
     ref_x = None
-    for name, prec in (("fp64", "fp64"), ("fp32_vcycle", "fp32"), ("fp32_smoother_fp64_coarse", "fp32s")):
+    for name, prec in (("fp64", "fp64"), ("fp32_vcycle", "fp32"), ("fp32_smoother_fp64_coarse", "fp32s"),
+                       ("bf16_bands_fp32_vcycle", "bf16")):
         v = measure(P, torch, prob, wl, args, prec, pb["omega"], max(1, min(args.steps, 3)), 1, dev, stream, world,
                     False, restrict=pb["restrict"], restart=pb["restart"], workload=C3_WORKLOAD)
         entry = {"value": round(v["value"], 4), "unit": UNIT, "ms_per_step": round(v["ms_per_step"], 3),

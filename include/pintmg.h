@@ -55,8 +55,13 @@ typedef enum {
   MG_PRECISION_FP64 = 0,        /* the plain method: every step in FP64 */
   MG_PRECISION_FP32 = 1,        /* V-cycle (smoother, transfers, SGS) in FP32; FGMRES, coarse GMRES and true
                                    residual in FP64 */
-  MG_PRECISION_FP32_SMOOTH = 2  /* smoother and transfers in FP32; the coarse solve (GMRES and its SGS), FGMRES
+  MG_PRECISION_FP32_SMOOTH = 2, /* smoother and transfers in FP32; the coarse solve (GMRES and its SGS), FGMRES
                                    and true residual in FP64 */
+  MG_PRECISION_BF16_BANDS = 3   /* as MG_PRECISION_FP32, with the N, V, Z~ bands of every level but the coarsest
+                                   stored in BF16 (rounded to nearest from their FP32 values) and every product
+                                   formed in FP32: half the bytes of those bands per sweep and residual.  The
+                                   local factor, the coarsest level and the FGMRES operator keep their precision.
+                                   Tridiagonal layout only (else MG_ERR_UNSUPPORTED) */
 } mg_precision;
 
 /*

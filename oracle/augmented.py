@@ -115,6 +115,19 @@ def _as_sparse(kind: str, mat: np.ndarray) -> sp.csr_matrix:
     return sp.csr_matrix(mat)
 
 
+def round_bf16(x) -> np.ndarray:
+    """Values rounded to FP32 (to nearest) and then to BF16 (to nearest, ties to
+    even), returned as FP64.  BF16 keeps the sign, the 8 exponent bits and the
+    top 7 stored mantissa bits of the FP32 pattern: rounding adds 0x7FFF plus
+    the lowest kept bit to the pattern and clears the low 16 bits.  This is the
+    storage the library's MG_PRECISION_BF16_BANDS mode gives the N, V, Z~
+    bands of its smoothing levels (finite values only)."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+    bits = f.view(np.uint32).astype(np.uint64)
+    bits = (bits + np.uint64(0x7FFF) + ((bits >> np.uint64(16)) & np.uint64(1))) & np.uint64(0xFFFF0000)
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def scaled_blocks(raw: RawLevel):
     """N_k, V_k and Z~_k of Eq. (blocks-aj) with u_{k-1} replaced by v_{k-1} (Sec. 5.1).
 
@@ -270,13 +283,23 @@ def transfer_type_major(n: int, p: int, q: int, end_rule: int = 0, restrict: str
 # One grid level in time-major form
 
 class Level:
-    """A~, its block splitting D + L + L^T (Sec. 5.3.2) and factorisations."""
+    """A~, its block splitting D + L + L^T (Sec. 5.3.2) and factorisations.
 
-    def __init__(self, raw: RawLevel):
+    band_round (optional): applied to the entries of every N_k, V_k, Z~_k after
+    they are formed (e.g. ``round_bf16``), giving the level whose bands are
+    stored in that precision."""
+
+    def __init__(self, raw: RawLevel, band_round=None):
         self.raw = raw
         n, p, q = raw.n, raw.p, raw.q
         self.n, self.p, self.q = n, p, q
         N, V, Z = scaled_blocks(raw)
+        if band_round is not None:
+            def rnd(m):
+                m = m.tocsr(copy=True)
+                m.data = band_round(m.data)
+                return m
+            N, V, Z = [rnd(m) for m in N], [rnd(m) for m in V], [rnd(m) for m in Z]
         self.N, self.V, self.Z = N, V, Z
         self.A = lifted_augmented(N, V, Z, n, p, q)
         self.perm, self.bounds = time_major_order(n, p, q)
@@ -474,6 +497,7 @@ class MGOptions:
     omega: float = 1.0
     coarse_precond: str = "sgs"     # the paper's; "jacobi", "fgs", "bgs" are Table 1's alternatives
     restrict: str = "inject"        # residual restriction: "inject" (Sec. 5.3.1 as written) or "transpose" (P^T)
+    bands: str = "fp64"             # "bf16": every level but the coarsest with its bands rounded by round_bf16
 
 
 class Hierarchy:
@@ -486,7 +510,8 @@ class Hierarchy:
         self.levels = []
         self.R, self.P = [], []
         for lv in range(opts.levels):
-            level = Level(raw)
+            smoothing = lv + 1 < opts.levels
+            level = Level(raw, band_round=round_bf16 if (opts.bands == "bf16" and smoothing) else None)
             self.levels.append(level)
             if lv + 1 < opts.levels:
                 R, P = transfer_type_major(raw.n, raw.p, raw.q, opts.end_rule, opts.restrict)
@@ -532,8 +557,9 @@ class Hierarchy:
         return f.to_type_major(self.vcycle(0, f.to_time_major(r_type_major)))
 
     def solve(self, b_type_major: np.ndarray, rtol: float, maxit: int = 200, restart: int = 60):
-        """FGMRES on A~ y = b~ preconditioned by the V-cycle (Sec. 5.3.4, Sec. 6)."""
-        f = self.fine
+        """FGMRES on A~ y = b~ preconditioned by the V-cycle (Sec. 5.3.4, Sec. 6).  The
+        operator is always the fine level's exact A~ (FP64 bands)."""
+        f = self.fine if self.opts.bands == "fp64" else Level(self.fine.raw)
         bt = f.to_time_major(b_type_major)
         res = fgmres(lambda v: f.At @ v, lambda v: self.vcycle(0, v), bt,
                      rtol=rtol, maxit=maxit, restart=restart)

@@ -7,6 +7,7 @@
 // 0-based step indices.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,10 +36,12 @@ __host__ __device__ constexpr int scan_index(int dir, int round, int entry, int 
 //   scan: tridiagonal only: per step, kScanPerBlock entries: for each lane and
 //         round of the forward / backward warp scans, the composed 2x2 map of
 //         that lane's LDL^T recurrence chunks (scan_index layout).
-template <typename T>
+//   CT: storage type of the N, V, Z bands (T, or BF16 with T = float: the
+//   bands are read as BF16 and every product is formed in FP32).
+template <typename T, typename CT = T>
 struct LevelView {
   int n, p, q, layout;
-  const T *N, *V, *Z;
+  const CT *N, *V, *Z;
   long long sN, sV, sZ;
   const T *fac;
   long long sFac;
@@ -75,6 +78,11 @@ __host__ __device__ inline Vec<const T> make_cvec(const T *base, int n, int p, i
   return x;
 }
 
+// a band coefficient in the arithmetic type
+__device__ __forceinline__ double coef(double a) { return a; }
+__device__ __forceinline__ float coef(float a) { return a; }
+__device__ __forceinline__ float coef(__nv_bfloat16 a) { return __bfloat162float(a); }
+
 // ---------------------------------------------------------------------------
 // Warp-cooperative tridiagonal helpers.  Lane `ln` owns the contiguous chunk
 // [ln*C, ln*C + C) of a length-p vector (p <= 32 C); entries at i >= p are 0.
@@ -106,9 +114,9 @@ __device__ __forceinline__ void chunk_halo(const T (&x)[C], int p, int ln, T &pr
   if (ln * C + C >= p) next = T(0);
 }
 
-// y (+)= A x for a tridiagonal band A (3 rows of p)
-template <typename T, int C, bool kAccumulate>
-__device__ __forceinline__ void tri_mv(T (&y)[C], const T *A, const T (&x)[C], int p, int ln, T sign) {
+// y (+)= A x for a tridiagonal band A (3 rows of p, stored as CT)
+template <typename T, int C, bool kAccumulate, typename CT>
+__device__ __forceinline__ void tri_mv(T (&y)[C], const CT *A, const T (&x)[C], int p, int ln, T sign) {
   T prev, next;
   chunk_halo<T, C>(x, p, ln, prev, next);
 #pragma unroll
@@ -118,15 +126,15 @@ __device__ __forceinline__ void tri_mv(T (&y)[C], const T *A, const T (&x)[C], i
     if (i < p) {
       T xm = (e == 0) ? prev : x[e - 1];
       T xp = (e == C - 1) ? next : x[e + 1];
-      acc = fma(A[i], xm, fma(A[p + i], x[e], A[2 * p + i] * xp));
+      acc = fma(T(coef(A[i])), xm, fma(T(coef(A[p + i])), x[e], T(coef(A[2 * p + i])) * xp));
     }
     y[e] = kAccumulate ? fma(sign, acc, y[e]) : sign * acc;
   }
 }
 
 // y (+)= A^T x for a tridiagonal band A: (A^T x)_i = A[i-1][i] x_{i-1} + A[i][i] x_i + A[i+1][i] x_{i+1}
-template <typename T, int C, bool kAccumulate>
-__device__ __forceinline__ void tri_mtv(T (&y)[C], const T *A, const T (&x)[C], int p, int ln, T sign) {
+template <typename T, int C, bool kAccumulate, typename CT>
+__device__ __forceinline__ void tri_mtv(T (&y)[C], const CT *A, const T (&x)[C], int p, int ln, T sign) {
   T prev, next;
   chunk_halo<T, C>(x, p, ln, prev, next);
 #pragma unroll
@@ -136,9 +144,9 @@ __device__ __forceinline__ void tri_mtv(T (&y)[C], const T *A, const T (&x)[C], 
     if (i < p) {
       T xm = (e == 0) ? prev : x[e - 1];
       T xp = (e == C - 1) ? next : x[e + 1];
-      T up = (i > 0) ? A[2 * p + i - 1] : T(0);     // A[i-1][i]
-      T lo = (i + 1 < p) ? A[i + 1] : T(0);         // A[i+1][i]
-      acc = fma(up, xm, fma(A[p + i], x[e], lo * xp));
+      T up = (i > 0) ? T(coef(A[2 * p + i - 1])) : T(0);     // A[i-1][i]
+      T lo = (i + 1 < p) ? T(coef(A[i + 1])) : T(0);         // A[i+1][i]
+      acc = fma(up, xm, fma(T(coef(A[p + i])), x[e], lo * xp));
     }
     y[e] = kAccumulate ? fma(sign, acc, y[e]) : sign * acc;
   }

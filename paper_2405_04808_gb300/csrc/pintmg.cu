@@ -88,6 +88,9 @@ struct LevelData {
   // pre- or post-smoothing in one cooperative launch (k_sweeps_tri2)
   bool persist = false;
   SweepXchg<T> sx{};
+  // MG_PRECISION_BF16_BANDS, smoothing levels: the view with the N, V, Z bands in BF16
+  bool bands16 = false;
+  LevelView<T, __nv_bfloat16> vh{};
 };
 
 struct Level {
@@ -267,11 +270,11 @@ void harvest(mg_handle *h) {
 
 // the staged block solve applies: tridiagonal, p <= 128 (4 entries per lane), 16-byte
 // aligned coefficient arrays and block strides
-template <typename T>
-bool tri_stage_ok(const LevelView<T> &L) {
+template <typename T, typename CT>
+bool tri_stage_ok(const LevelView<T, CT> &L) {
   const auto al = [](const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; };
   return L.layout == MG_LAYOUT_TRIDIAG && L.p <= 4 * kWarp && (3 * (size_t)L.p * sizeof(T)) % 16 == 0 &&
-         al(L.N) && al(L.V) && al(L.Z) && al(L.fac) && al(L.scan);
+         (3 * (size_t)L.p * sizeof(CT)) % 16 == 0 && al(L.N) && al(L.V) && al(L.Z) && al(L.fac) && al(L.scan);
 }
 
 // levels with at most this many blocks take the two-warps-per-block solve
@@ -305,21 +308,35 @@ void tri_stage_prepare() {
   ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
   ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
   ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 4, 4 * kWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
+  // the same with BF16 bands (MG_PRECISION_BF16_BANDS): the same shared-memory slots
+  using B16 = __nv_bfloat16;
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 1, true, 0, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 2, true, 0, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 4, true, 0, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri<float, 4, true, 4 * kWarp, B16>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, bf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 1, 0, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 2, 0, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 4, 0, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf));
+  ck(cudaFuncSetAttribute(k_block_solve_tri2<float, 4, 4 * kWarp, B16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          pf));
   if (dev < 32) done |= 1u << dev;
 }
 
-template <typename T>
-void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T *cplU, const T *cplM,
+template <typename T, typename CT = T>
+void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, const T *cplU, const T *cplM,
                         T *out, cudaStream_t s, const T *yold = nullptr, T omega = T(1)) {
   // per block: read r (4p+q), couplings (2p), N, V, Z (9p tridiagonal / 2p^2+pq dense), factor
   // (3p / p^2), old iterate if relaxed (4p+q); write 4p+q.  Flops: 45p (tridiagonal).
   const double w = 4.0 * L.p + L.q, p_ = L.p;
-  const double coef = L.layout == MG_LAYOUT_TRIDIAG ? 12.0 * p_ : 3.0 * p_ * p_ + p_ * L.q;
-  const double per_block = sizeof(T) * (2.0 * w + 2.0 * p_ + coef + (omega != T(1) && yold ? w : 0.0));
+  const double coef = L.layout == MG_LAYOUT_TRIDIAG ? 9.0 * p_ * sizeof(CT) + 3.0 * p_ * sizeof(T)
+                                                    : (3.0 * p_ * p_ + p_ * L.q) * sizeof(T);
+  const double per_block = sizeof(T) * (2.0 * w + 2.0 * p_ + (omega != T(1) && yold ? w : 0.0)) + coef;
   const double fl = L.layout == MG_LAYOUT_TRIDIAG ? 45.0 * p_ : 2.0 * (3.0 * p_ * p_ + 2.0 * p_ * L.q + p_ * p_);
   Bracket br(h, CAT_BLOCK_SOLVE, s, per_block * (L.n + 1), fl * (L.n + 1));
   if (L.layout == MG_LAYOUT_DENSE) {
-    k_block_solve_dense<T><<<grid_for(L.n + 1, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega);
+    if constexpr (std::is_same<T, CT>::value)
+      k_block_solve_dense<T><<<grid_for(L.n + 1, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega);
   } else {
     const int blocks = (int)((L.n + 1 + 3) / 4);
     const size_t smem = 4 * (size_t)tri_stage_elems<T>(L.p) * sizeof(T);
@@ -327,12 +344,12 @@ void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T
       const int pblocks = (int)((L.n + 1 + 1) / 2);
       const size_t psmem = 2 * (size_t)tri_pair_elems<T>(L.p) * sizeof(T);
       if (L.p == 4 * kWarp && L.q == L.p) {
-        k_block_solve_tri2<T, 4, 4 * kWarp><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega);
+        k_block_solve_tri2<T, 4, 4 * kWarp, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega);
       } else {
         switch (h->C) {
-          case 1: k_block_solve_tri2<T, 1><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-          case 2: k_block_solve_tri2<T, 2><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-          default: k_block_solve_tri2<T, 4><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+          case 1: k_block_solve_tri2<T, 1, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+          case 2: k_block_solve_tri2<T, 2, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+          default: k_block_solve_tri2<T, 4, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
         }
       }
       ck_launch();
@@ -340,45 +357,47 @@ void launch_block_solve(mg_handle *h, const LevelView<T> &L, const T *r, const T
     }
     if (h->stage_tri && tri_stage_ok(L)) {  // coefficients staged in shared memory (p <= 128)
       if (L.p == 4 * kWarp && L.q == L.p) {  // full chunks: p known at compile time
-        k_block_solve_tri<T, 4, true, 4 * kWarp><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega);
+        k_block_solve_tri<T, 4, true, 4 * kWarp, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega);
         ck_launch();
         return;
       }
       switch (h->C) {
-        case 1: k_block_solve_tri<T, 1, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-        case 2: k_block_solve_tri<T, 2, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-        default: k_block_solve_tri<T, 4, true><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+        case 1: k_block_solve_tri<T, 1, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+        case 2: k_block_solve_tri<T, 2, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+        default: k_block_solve_tri<T, 4, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
       }
       ck_launch();
       return;
     }
     switch (h->C) {
-      case 1: k_block_solve_tri<T, 1><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      case 2: k_block_solve_tri<T, 2><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      case 4: k_block_solve_tri<T, 4><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      case 8: k_block_solve_tri<T, 8><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      default: k_block_solve_tri<T, 16><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 1: k_block_solve_tri<T, 1, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 2: k_block_solve_tri<T, 2, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 4: k_block_solve_tri<T, 4, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 8: k_block_solve_tri<T, 8, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      default: k_block_solve_tri<T, 16, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
     }
   }
   ck_launch();
 }
 
-template <typename T>
-void launch_apply(mg_handle *h, const LevelView<T> &L, const T *x, const T *b, T *out, cudaStream_t s) {
+template <typename T, typename CT = T>
+void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *b, T *out, cudaStream_t s) {
   const double w = 4.0 * L.p + L.q;
-  const double coef = L.layout == MG_LAYOUT_TRIDIAG ? 9.0 * L.p : 2.0 * L.p * L.p + L.p * L.q;
+  const double coef = L.layout == MG_LAYOUT_TRIDIAG ? 9.0 * L.p * sizeof(CT) / sizeof(T)
+                                                    : 2.0 * L.p * L.p + L.p * L.q;
   Bracket br(h, CAT_APPLY, s, sizeof(T) * (L.n * ((b ? 3.0 : 2.0) * w + coef)),
              L.layout == MG_LAYOUT_TRIDIAG ? 2.0 * 18.0 * L.p * L.n : 4.0 * L.n * (2.0 * L.p * L.p + L.p * L.q));
   if (L.layout == MG_LAYOUT_DENSE) {
-    k_apply_dense<T><<<grid_for(L.n, 128, 1 << 30), 128, 0, s>>>(L, x, b, out);
+    if constexpr (std::is_same<T, CT>::value)
+      k_apply_dense<T><<<grid_for(L.n, 128, 1 << 30), 128, 0, s>>>(L, x, b, out);
   } else {
     const int blocks = (L.n + 3) / 4;
     switch (h->C) {
-      case 1: k_apply_tri<T, 1><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      case 2: k_apply_tri<T, 2><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      case 4: k_apply_tri<T, 4><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      case 8: k_apply_tri<T, 8><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      default: k_apply_tri<T, 16><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 1: k_apply_tri<T, 1, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 2: k_apply_tri<T, 2, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 4: k_apply_tri<T, 4, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 8: k_apply_tri<T, 8, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      default: k_apply_tri<T, 16, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
     }
   }
   ck_launch();
@@ -458,22 +477,24 @@ void launch_sweeps(mg_handle *h, LevelData<T> &d, const T *r, const T *y0, T *ou
   ck_launch();
 }
 
-template <typename T>
-void launch_residual_restrict(mg_handle *h, const LevelView<T> &L, const T *y, const T *b, T *rc,
+template <typename T, typename CT = T>
+void launch_residual_restrict(mg_handle *h, const LevelView<T, CT> &L, const T *y, const T *b, T *rc,
                               cudaStream_t s) {
   const double w = 4.0 * L.p + L.q;
-  Bracket br(h, CAT_RESTRICT, s, sizeof(T) * (L.n / 2) * (2.0 * (w + L.q) + w + 12.0 * L.p), 0.0);
+  Bracket br(h, CAT_RESTRICT, s,
+             (L.n / 2) * (sizeof(T) * (2.0 * (w + L.q) + w + 3.0 * L.p) + sizeof(CT) * 9.0 * L.p), 0.0);
   const int nc = L.n / 2;
   if (L.layout == MG_LAYOUT_DENSE) {
-    k_residual_restrict_dense<T><<<grid_for(nc, 128, 1 << 30), 128, 0, s>>>(L, y, b, rc);
+    if constexpr (std::is_same<T, CT>::value)
+      k_residual_restrict_dense<T><<<grid_for(nc, 128, 1 << 30), 128, 0, s>>>(L, y, b, rc);
   } else {
     const int blocks = (nc + 3) / 4;
     switch (h->C) {
-      case 1: k_residual_restrict_tri<T, 1><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
-      case 2: k_residual_restrict_tri<T, 2><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
-      case 4: k_residual_restrict_tri<T, 4><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
-      case 8: k_residual_restrict_tri<T, 8><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
-      default: k_residual_restrict_tri<T, 16><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      case 1: k_residual_restrict_tri<T, 1, CT><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      case 2: k_residual_restrict_tri<T, 2, CT><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      case 4: k_residual_restrict_tri<T, 4, CT><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      case 8: k_residual_restrict_tri<T, 8, CT><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
+      default: k_residual_restrict_tri<T, 16, CT><<<blocks, 128, 0, s>>>(L, y, b, rc); break;
     }
   }
   ck_launch();
@@ -1251,39 +1272,41 @@ void coarse_solve(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
 
 // V-cycle from y = 0 on level l (Alg. 1 generalised): b, y in precision T
 template <typename T>
-void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
-  const int last = (int)h->lv.size() - 1;
-  if (l == last) {
-    coarse_solve<T>(h, b, y_out, s);
-    return;
-  }
+void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s);
+
+// one smoothing level of the V-cycle; `view` is the level's coefficients as
+// the smoother and residual read them (FP64 / FP32, or FP32 with BF16 bands)
+template <typename T, typename VIEW>
+void vcycle_level(mg_handle *h, int l, const VIEW &view, const T *b, T *y_out, cudaStream_t s) {
   Level &lev = h->lv[l];
   LevelData<T> &d = ldata<T>(lev);
   const mg_options &o = h->opts;
+  constexpr bool kPlain = std::is_same<VIEW, LevelView<T>>::value;  // the multi-sweep kernel reads T bands
+  const bool persist = kPlain && d.persist;
   T *y = y_out, *t = d.tmp;
   if (o.nu_pre == 0) {
     ck(cudaMemsetAsync(y, 0, lev.len * sizeof(T), s));
-  } else if (d.persist) {
+  } else if (persist) {
     launch_sweeps<T>(h, d, b, nullptr, y, o.nu_pre, (T)o.omega, s);  // all pre-sweeps, from y = 0
   } else {
     const T om = (T)o.omega;
-    launch_block_solve<T>(h, d.view, b, nullptr, nullptr, y, s, nullptr, om);  // first sweep from y = 0
+    launch_block_solve<T>(h, view, b, nullptr, nullptr, y, s, nullptr, om);  // first sweep from y = 0
     for (int k = 1; k < o.nu_pre; ++k) {
       Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
-      launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s, y, om);
+      launch_block_solve<T>(h, view, b, Y.u, Y.m, t, s, y, om);
       std::swap(y, t);
     }
   }
   LevelData<T> &dn = ldata<T>(h->lv[l + 1]);
   if (o.restrict_rule == MG_RESTRICT_TRANSPOSE) {
-    launch_apply<T>(h, d.view, y, b, t, s);  // full fine residual into the free sweep buffer
+    launch_apply<T>(h, view, y, b, t, s);  // full fine residual into the free sweep buffer
     const double w = 4.0 * h->p + h->q;
     Bracket br(h, CAT_RESTRICT, s, sizeof(T) * (lev.n / 2) * w * 3.0, 0.0);
     k_restrict_transpose<T><<<grid_for((long long)(lev.n / 2) * (long long)w, 256), 256, 0, s>>>(
         t, dn.b, lev.n, h->p, h->q, o.end_rule);
     ck_launch();
   } else {
-    launch_residual_restrict<T>(h, d.view, y, b, dn.b, s);
+    launch_residual_restrict<T>(h, view, y, b, dn.b, s);
   }
   vcycle<T>(h, l + 1, dn.b, dn.y, s);
   {
@@ -1291,17 +1314,34 @@ void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
     k_prolong_add<T><<<grid_for(lev.len, 256), 256, 0, s>>>(y, dn.y, lev.n, h->p, h->q, o.end_rule);
     ck_launch();
   }
-  if (d.persist && o.nu_post > 0) {
+  if (persist && o.nu_post > 0) {
     launch_sweeps<T>(h, d, b, y, t, o.nu_post, (T)o.omega, s);  // all post-sweeps, from y
     std::swap(y, t);
   } else {
     for (int k = 0; k < o.nu_post; ++k) {
       Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
-      launch_block_solve<T>(h, d.view, b, Y.u, Y.m, t, s, y, (T)o.omega);
+      launch_block_solve<T>(h, view, b, Y.u, Y.m, t, s, y, (T)o.omega);
       std::swap(y, t);
     }
   }
   if (y != y_out) ck(cudaMemcpyAsync(y_out, y, lev.len * sizeof(T), cudaMemcpyDeviceToDevice, s));
+}
+
+template <typename T>
+void vcycle(mg_handle *h, int l, const T *b, T *y_out, cudaStream_t s) {
+  const int last = (int)h->lv.size() - 1;
+  if (l == last) {
+    coarse_solve<T>(h, b, y_out, s);
+    return;
+  }
+  LevelData<T> &d = ldata<T>(h->lv[l]);
+  if constexpr (std::is_same<T, float>::value) {
+    if (d.bands16) {  // MG_PRECISION_BF16_BANDS: this level's bands are read as BF16
+      vcycle_level<T>(h, l, d.vh, b, y_out, s);
+      return;
+    }
+  }
+  vcycle_level<T>(h, l, d.view, b, y_out, s);
 }
 
 // z = M^-1 v on FP64 fine vectors
@@ -1334,6 +1374,16 @@ void alloc_level_vectors(mg_handle *h, Level &lev, LevelData<T> &d, bool is_last
     d.chainM = h->mem.alloc<T>((size_t)std::max(lev.n, 1) * h->p);
     d.sgs_w = h->mem.alloc<T>(len);
   }
+}
+
+__nv_bfloat16 *to_bf16_copy(mg_handle *h, const float *x, long long len, cudaStream_t s) {
+  __nv_bfloat16 *y = h->mem.alloc<__nv_bfloat16>(len);
+  {
+    Bracket br(h, CAT_CONVERT, s);
+    k_to_bf16<<<grid_for(len, 256), 256, 0, s>>>(x, y, len);
+    ck_launch();
+  }
+  return y;
 }
 
 float *to_float_copy(mg_handle *h, const double *x, long long len, cudaStream_t s) {
@@ -1747,8 +1797,9 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     return MG_ERR_ARG;
   if (O->end_rule != 0 && O->end_rule != 1) return MG_ERR_ARG;
   if (O->precision != MG_PRECISION_FP64 && O->precision != MG_PRECISION_FP32 &&
-      O->precision != MG_PRECISION_FP32_SMOOTH)
+      O->precision != MG_PRECISION_FP32_SMOOTH && O->precision != MG_PRECISION_BF16_BANDS)
     return MG_ERR_ARG;
+  if (O->precision == MG_PRECISION_BF16_BANDS && layout != MG_LAYOUT_TRIDIAG) return MG_ERR_UNSUPPORTED;
   if (!(O->omega > 0.0 && O->omega <= 1.0)) return MG_ERR_ARG;
   if (O->coarse_precond < MG_COARSE_SGS || O->coarse_precond > MG_COARSE_BGS) return MG_ERR_ARG;
   if (O->device_loops != 0 && O->device_loops != 1) return MG_ERR_ARG;
@@ -1993,6 +2044,43 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
         f.sFac = v.sFac;
         f.scan = layout == MG_LAYOUT_TRIDIAG ? to_float_copy(h, v.scan, (long long)nl * kScanPerBlock, s)
                                              : nullptr;
+        if (O->precision == MG_PRECISION_BF16_BANDS && l < L - 1) {
+          // smoothing levels read their N, V, Z bands as BF16 (rounded from the FP32 copies);
+          // the factor, the scan compositions and the coarsest level stay FP32
+          LevelView<float, __nv_bfloat16> &vh = lev.f.vh;
+          vh.n = nl;
+          vh.p = p;
+          vh.q = q;
+          vh.layout = layout;
+          vh.N = to_bf16_copy(h, f.N, (long long)nl * msz, s);
+          vh.V = to_bf16_copy(h, f.V, (long long)nl * msz, s);
+          vh.Z = to_bf16_copy(h, f.Z, (long long)nl * zsz, s);
+          vh.sN = f.sN;
+          vh.sV = f.sV;
+          vh.sZ = f.sZ;
+          vh.kappa = 0.0f;  // the rounded V is no longer a multiple of the rounded Z: both are read
+          // the local factor of the rounded blocks (FP64, then FP32), so that each sweep solves
+          // the rounded D_k exactly up to FP32 rounding
+          double *Nr = h->mem.alloc<double>((size_t)nl * msz), *Zr = h->mem.alloc<double>((size_t)nl * zsz);
+          {
+            Bracket br(h, CAT_CONVERT, s);
+            k_bf16_to_double<<<grid_for((long long)nl * msz, 256), 256, 0, s>>>(vh.N, Nr, (long long)nl * msz);
+            ck_launch();
+          }
+          {
+            Bracket br(h, CAT_CONVERT, s);
+            k_bf16_to_double<<<grid_for((long long)nl * zsz, 256), 256, 0, s>>>(vh.Z, Zr, (long long)nl * zsz);
+            ck_launch();
+          }
+          double *facr = h->mem.alloc<double>((size_t)nl * 3 * p);
+          double *scanr = h->mem.alloc<double>((size_t)nl * kScanPerBlock);
+          k_factor_tri<<<grid_for(nl, 64, 1 << 20), 64, 0, s>>>(nl, p, C, Nr, msz, Zr, zsz, facr, scanr, h->flag);
+          ck_launch();
+          vh.fac = to_float_copy(h, facr, (long long)nl * 3 * p, s);
+          vh.sFac = 3 * p;
+          vh.scan = to_float_copy(h, scanr, (long long)nl * kScanPerBlock, s);
+          lev.f.bands16 = true;
+        }
         if (l == L - 1) {
           lev.f.Cu = to_float_copy(h, lev.d.Cu, (long long)nl * p * p, s);
           lev.f.Em = to_float_copy(h, lev.d.Em, (long long)nl * p * p, s);
@@ -2974,7 +3062,8 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
     if (!hit) {
       Level &cl = h->lv.back();
       if (!env_chain) {
-        if (h->opts.precision == MG_PRECISION_FP32)  // the coarse SGS runs in FP32 only in this mode
+        if (h->opts.precision == MG_PRECISION_FP32 || h->opts.precision == MG_PRECISION_BF16_BANDS)
+          // the coarse SGS runs in FP32 only in these modes
           tune_chain<float>(h, cl, c, s);
         else
           tune_chain<double>(h, cl, c, s);

@@ -239,6 +239,19 @@ __global__ void k_to_float(const double *__restrict__ x, float *y, long long len
     y[i] = (float)x[i];
 }
 
+// BF16 copy of FP32 values, rounded to nearest (ties to even)
+__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *y, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+__global__ void k_bf16_to_double(const __nv_bfloat16 *__restrict__ x, double *y, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)__bfloat162float(x[i]);
+}
+
 __global__ void k_to_double(const float *__restrict__ x, double *y, long long len) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
        i += (long long)gridDim.x * blockDim.x)

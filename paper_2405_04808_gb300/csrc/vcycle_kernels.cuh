@@ -17,20 +17,22 @@ namespace pintmg {
 
 // The coefficients of one time block (tridiagonal layout): bands of N, V, Z,
 // the LDL^T factor of S and the chunk-scan compositions, in global or shared memory.
-template <typename T>
+// (bands stored as CT, the factor and scan compositions as T)
+template <typename T, typename CT = T>
 struct TriBlock {
-  const T *N, *V, *Z, *fac, *scan;
+  const CT *N, *V, *Z;
+  const T *fac, *scan;
 };
 
-template <typename T>
-__device__ __forceinline__ TriBlock<T> tri_block(const LevelView<T> &L, int j) {
+template <typename T, typename CT>
+__device__ __forceinline__ TriBlock<T, CT> tri_block(const LevelView<T, CT> &L, int j) {
   return {L.N + j * L.sN, L.V + j * L.sV, L.Z + j * L.sZ, L.fac + j * L.sFac, L.scan + (long long)j * kScanPerBlock};
 }
 
 // kappa != 0: V = kappa Z, so Z r_z + V v = Z (r_z + kappa v) and
 // Z^T lambda, V^T lambda come from one product (the same values up to rounding).
-template <typename T, int C>
-__device__ __forceinline__ void local_solve_tri(const TriBlock<T> &Bk, int n, int p, int j,
+template <typename T, int C, typename CT>
+__device__ __forceinline__ void local_solve_tri(const TriBlock<T, CT> &Bk, int n, int p, int j,
                                                 const T (&ru)[C], const T (&rz)[C], const T (&rl)[C],
                                                 const T (&rv)[C], const T (&rm)[C],
                                                 T (&u)[C], T (&z)[C], T (&l)[C], T (&v)[C], T (&m)[C],
@@ -43,7 +45,8 @@ __device__ __forceinline__ void local_solve_tri(const TriBlock<T> &Bk, int n, in
     }
     return;
   }
-  const T *N = Bk.N, *V = Bk.V, *Z = Bk.Z, *fac = Bk.fac, *scan = Bk.scan;
+  const CT *N = Bk.N, *V = Bk.V, *Z = Bk.Z;
+  const T *fac = Bk.fac, *scan = Bk.scan;
   T rhs[C];
   tri_mv<T, C, false>(rhs, N, ru, p, ln, T(1));
   if (j >= 1) {
@@ -169,26 +172,28 @@ __host__ __device__ constexpr int tri_stage_elems(int p) { return 12 * p + kScan
 // of 16 and 16-byte aligned coefficient arrays (checked on the host).
 // PF > 0: p == PF == 32 C is known at compile time (every lane's chunk is full,
 // so the bounds tests fold away).
-template <typename T, int C, bool kStage = false, int PF = 0>
-__global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T> L, const T *__restrict__ r,
+template <typename T, int C, bool kStage = false, int PF = 0, typename CT = T>
+__global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T, CT> L, const T *__restrict__ r,
                                                          const T *cplU, const T *cplM, T *out,
                                                          const T *yold, T omega) {
   const int ln = threadIdx.x & (kWarp - 1);
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int n = L.n, p = PF ? PF : L.p, q = PF ? PF : L.q;
   if (j > n) return;
-  TriBlock<T> Bk{};
+  TriBlock<T, CT> Bk{};
   if (j < n) Bk = tri_block(L, j);
   if (kStage && j < n) {
+    // bands at T offsets 0, 3p, 6p (as CT: a BF16 band fills the first half of its slot)
     extern __shared__ __align__(16) unsigned char tri_smem[];
     T *base = reinterpret_cast<T *>(tri_smem) + (threadIdx.x / kWarp) * tri_stage_elems<T>(p);
-    stage16(base, Bk.N, 3 * p, ln);
-    stage16(base + 3 * p, Bk.V, 3 * p, ln);
-    stage16(base + 6 * p, Bk.Z, 3 * p, ln);
+    stage16(reinterpret_cast<CT *>(base), Bk.N, 3 * p, ln);
+    stage16(reinterpret_cast<CT *>(base + 3 * p), Bk.V, 3 * p, ln);
+    stage16(reinterpret_cast<CT *>(base + 6 * p), Bk.Z, 3 * p, ln);
     stage16(base + 9 * p, Bk.fac, 3 * p, ln);
     stage16(base + 12 * p, Bk.scan, kScanPerBlock, ln);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
-    Bk = {base, base + 3 * p, base + 6 * p, base + 9 * p, base + 12 * p};
+    Bk = {reinterpret_cast<const CT *>(base), reinterpret_cast<const CT *>(base + 3 * p),
+          reinterpret_cast<const CT *>(base + 6 * p), base + 9 * p, base + 12 * p};
   }
   Vec<const T> R = make_cvec(r, n, p, q);
   Vec<T> Y = make_vec(out, n, p, q);
@@ -258,8 +263,8 @@ __host__ __device__ constexpr int tri_pair_elems(int p) { return 12 * p + kScanP
 
 __device__ __forceinline__ void pair_barrier(int id) { asm volatile("bar.sync %0, 64;\n" ::"r"(id) : "memory"); }
 
-template <typename T, int C, int PF = 0>
-__global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const T *__restrict__ r,
+template <typename T, int C, int PF = 0, typename CT = T>
+__global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T, CT> L, const T *__restrict__ r,
                                                           const T *cplU, const T *cplM, T *out,
                                                           const T *yold, T omega) {
   const int ln = threadIdx.x & (kWarp - 1);
@@ -298,9 +303,9 @@ __global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const 
     }
     return;
   }
-  const TriBlock<T> G = tri_block(L, j);
+  const TriBlock<T, CT> G = tri_block(L, j);
   if (role == 0) {
-    stage16(base, G.N, 3 * p, ln);
+    stage16(reinterpret_cast<CT *>(base), G.N, 3 * p, ln);
     stage16(base + 9 * p, G.fac, 3 * p, ln);
     stage16(base + 12 * p, G.scan, kScanPerBlock, ln);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -315,7 +320,8 @@ __global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const 
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
-    const T *N = base, *fac = base + 9 * p, *scan = base + 12 * p;
+    const CT *N = reinterpret_cast<const CT *>(base);
+    const T *fac = base + 9 * p, *scan = base + 12 * p;
     tri_mv<T, C, false>(rhs, N, ru, p, ln, T(1));
     pair_barrier(1 + pair);  // warp 1's part is in xch
     T part[C];
@@ -337,8 +343,8 @@ __global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const 
     chunk_store<T, C>(Y.u + (long long)j * p, u, p, ln);
     chunk_store<T, C>(Y.l + (long long)j * p, l, p, ln);
   } else {
-    stage16(base + 3 * p, G.V, 3 * p, ln);
-    stage16(base + 6 * p, G.Z, 3 * p, ln);
+    stage16(reinterpret_cast<CT *>(base + 3 * p), G.V, 3 * p, ln);
+    stage16(reinterpret_cast<CT *>(base + 6 * p), G.Z, 3 * p, ln);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     T rz[C], rl[C], rv[C], rm[C], v[C], part[C];
     chunk_load<T, C>(rz, R.z + (long long)j * q, q, ln);
@@ -357,7 +363,7 @@ __global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T> L, const 
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
-    const T *V = base + 3 * p, *Z = base + 6 * p;
+    const CT *V = reinterpret_cast<const CT *>(base + 3 * p), *Z = reinterpret_cast<const CT *>(base + 6 * p);
     const T kappa = L.kappa;
     if (kappa != T(0) && j >= 1) {  // V = kappa Z: one product
       T wz[C];
@@ -776,8 +782,8 @@ __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const
 //   mu_t:     u_t - v_t
 
 // out = b - A~ x  (b non-null)  or  out = A~ x  (b null), all five types.
-template <typename T, int C>
-__global__ void __launch_bounds__(128) k_apply_tri(LevelView<T> L, const T *__restrict__ x,
+template <typename T, int C, typename CT = T>
+__global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *__restrict__ x,
                                                    const T *__restrict__ b, T *out, const int *guard = nullptr) {
   if (guard && *guard == 0) return;
   const int ln = threadIdx.x & (kWarp - 1);
@@ -786,7 +792,7 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T> L, const T *__re
   if (t >= n) return;
   Vec<const T> X = make_cvec(x, n, p, q);
   Vec<T> O = make_vec(out, n, p, q);
-  const T *N = L.N + t * L.sN, *Z = L.Z + t * L.sZ, *Vt = L.V + t * L.sV;
+  const CT *N = L.N + t * L.sN, *Z = L.Z + t * L.sZ, *Vt = L.V + t * L.sV;
   T xu[C], xv[C], xz[C], xl[C], xm[C], acc[C];
   chunk_load<T, C>(xu, X.u + (long long)t * p, p, ln);
   chunk_load<T, C>(xv, X.v + (long long)t * p, p, ln);
@@ -906,8 +912,8 @@ __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__
 //   rc_z[K] = (r_z[2K] + r_z[2K+1]) / 2   (control: average)
 // with r = b - A~ y evaluated only at the rows it needs.
 
-template <typename T, int C>
-__global__ void __launch_bounds__(128) k_residual_restrict_tri(LevelView<T> L, const T *__restrict__ y,
+template <typename T, int C, typename CT = T>
+__global__ void __launch_bounds__(128) k_residual_restrict_tri(LevelView<T, CT> L, const T *__restrict__ y,
                                                                const T *__restrict__ b, T *rc) {
   const int ln = threadIdx.x & (kWarp - 1);
   const int K = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
@@ -917,7 +923,7 @@ __global__ void __launch_bounds__(128) k_residual_restrict_tri(LevelView<T> L, c
   Vec<const T> Y = make_cvec(y, n, p, q);
   Vec<const T> B = make_cvec(b, n, p, q);
   Vec<T> R = make_vec(rc, nc, p, q);
-  const T *N0 = L.N + t0 * L.sN, *Z0 = L.Z + t0 * L.sZ, *Z1 = L.Z + t1 * L.sZ;
+  const CT *N0 = L.N + t0 * L.sN, *Z0 = L.Z + t0 * L.sZ, *Z1 = L.Z + t1 * L.sZ;
   T yu[C], yv[C], yz[C], yl[C], ym[C], acc[C], o[C];
   chunk_load<T, C>(yu, Y.u + (long long)t0 * p, p, ln);
   chunk_load<T, C>(yv, Y.v + (long long)t0 * p, p, ln);

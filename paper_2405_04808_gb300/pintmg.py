@@ -32,6 +32,7 @@ MG_LAYOUT_TRIDIAG = 1
 MG_PRECISION_FP64 = 0
 MG_PRECISION_FP32 = 1
 MG_PRECISION_FP32_SMOOTH = 2
+MG_PRECISION_BF16_BANDS = 3
 COARSE_PRECOND = {"sgs": 0, "jacobi": 1, "fgs": 2, "bgs": 3}
 #: storage of the FGMRES basis (mg_krylov_basis)
 KRYLOV_BASIS = {"fp64": 0, "pair": 1}

@@ -134,3 +134,32 @@ def test_transpose_restriction_weighted_sweeps_burgers_growth():
         lit = _solve_iters(prob, lv)
         assert lit >= 2 * its
     assert all(b - a <= 2 for a, b in zip(counts, counts[1:]))
+
+
+def test_bf16_rounding_closed_forms_and_library():
+    """round_bf16 (the storage of MG_PRECISION_BF16_BANDS): ties to even at the 8th significant bit, and
+    the same values as torch's float32 -> bfloat16 conversion (round to nearest even) on random data."""
+    r = O.round_bf16([1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -8 + 2 ** -20, -(1 + 3 * 2 ** -8), 3.0, 0.0])
+    assert list(r) == [1.0, 1 + 2 ** -6, 1 + 2 ** -7, -(1 + 2 ** -6), 3.0, 0.0]
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(20000) * 10.0 ** rng.uniform(-6, 6, 20000)
+    want = torch.tensor(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_bf16(x), want)
+
+
+def test_bf16_band_cycle_keeps_the_exact_operator():
+    """With BF16 bands on the smoothing levels the V-cycle changes by ~1e-2 but FGMRES, whose operator keeps
+    the FP64 bands, still reaches the direct solution of the unrounded system with the same iteration count
+    up to one."""
+    prob = W.burgers(nx=40, n=32, seed=131)
+    opts = dict(levels=2, nu_pre=2, nu_post=2)
+    y64 = O.Hierarchy(prob, O.MGOptions(coarse_fixed_iters=2, **opts)).precondition(prob.b)
+    yb = O.Hierarchy(prob, O.MGOptions(coarse_fixed_iters=2, bands="bf16", **opts)).precondition(prob.b)
+    assert 1e-4 < np.linalg.norm(yb - y64) / np.linalg.norm(y64) < 5e-2
+    xb, rb, _ = O.Hierarchy(prob, O.MGOptions(bands="bf16", **opts)).solve(prob.b, rtol=1e-10, maxit=500,
+                                                                               restart=200)
+    _, r64, _ = O.Hierarchy(prob, O.MGOptions(**opts)).solve(prob.b, rtol=1e-10, maxit=500, restart=200)
+    xd = O.direct_solve(prob)
+    assert np.linalg.norm(xb - xd) <= 1e-9 * np.linalg.norm(xd)
+    assert abs(rb.iters - r64.iters) <= 1

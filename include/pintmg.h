@@ -379,7 +379,8 @@ int mg_coarse_shape(const mg_handle *h, int *T, int *X);
  * handles of the same shape take the cached choice without timing.  A chain
  * forced by the environment (PINTMG_SGS_CHAIN) is kept.  *chain (0 scan,
  * 1 cluster, 2 single CTA, 3 segmented) and *dot_vb (may be NULL) report the choice.
- * Allocates a temporary of 49 x min(n(4p+q), 2^20) doubles; synchronises
+ * Allocates a temporary of (m + 1) x n(4p+q) doubles, m = 240 basis vectors or
+ * fewer (at least 16) so that it stays near 2 GiB; synchronises
  * `stream`; invalidates h's captured graphs.
  */
 int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream);

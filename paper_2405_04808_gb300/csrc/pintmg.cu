@@ -3068,9 +3068,12 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
         else
           tune_chain<double>(h, cl, c, s);
       }
-      // dot products of 48 fine-level vectors (at most 2^20 entries each) for VB = 4, 8, 16
-      const long long tl = std::min<long long>(h->lv[0].len, 1LL << 20);
-      constexpr int kM = 48;
+      // dot products at the fine level's own length against 16, 64, 128 and 240 basis
+      // vectors (a spread of Arnoldi indices; fewer where 2 GiB of scratch does not hold
+      // them), summed, for VB = 4, 8, 16: the partition and the occupancy both depend on
+      // the length and the count
+      const long long tl = h->lv[0].len;
+      const int kM = (int)std::max<long long>(16, std::min<long long>(240, (1LL << 28) / tl - 1));
       cudaError_t e = cudaMalloc(&tmp, (size_t)(kM + 1) * tl * sizeof(double));
       if (e != cudaSuccess) {
         cudaGetLastError();
@@ -3080,10 +3083,15 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
       ck(cudaMemsetAsync(tmp, 0, (size_t)(kM + 1) * tl * sizeof(double), s));
       const int save_vb = h->dot_vb;
       const int vbs[3] = {4, 8, 16};
+      const int ms[4] = {16, 64, 128, 240};
       int best = 1;
       for (int k = 0; k < 3; ++k) {
         h->dot_vb = vbs[k];
-        c.ms_dot[k] = time_min(s, 5, [&] { multidot(h, tmp, tl, kM, tmp + (long long)kM * tl, tl, h->kf.h, 0, s); });
+        c.ms_dot[k] = 0.f;
+        for (int mm : ms) {
+          const int m = std::min(mm, kM);
+          c.ms_dot[k] += time_min(s, 3, [&] { multidot(h, tmp, tl, m, tmp + (long long)kM * tl, tl, h->kf.h, 0, s); });
+        }
         if (c.ms_dot[k] < c.ms_dot[best]) best = k;
       }
       h->dot_vb = save_vb;

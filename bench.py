@@ -191,7 +191,7 @@ def probe_fp_rates(P, torch, dev, stream):
 TRAFFIC_RATIO = {
     ("burgers_nx128_n1024", "multidot", "fp64"): (1.00, "profiles/multidot_burgers_nx128_n1024.md"),
     ("burgers_nx128_n1024", "pair_dot", "fp64"): (1.00, "profiles/multidot_pair_tma_burgers_nx128_n1024.md"),
-    ("burgers_nx128_n1024", "block_solve", "fp64"): (1.21, "profiles/block_solve_tri2_burgers_nx128_n1024.md"),
+    ("burgers_nx128_n1024", "block_solve", "fp64"): (1.10, "profiles/block_solve_tri2_burgers_nx128_n1024.md"),
 }
 
 

@@ -21,7 +21,8 @@ and exits non-zero on any library error.
     python -m paper_2405_04808_gb300.profile_cases summarize LAUNCHES.csv
 
 condenses an ncu launch list (``--metrics gpu__time_duration.sum --csv``) to
-launches, total time and share per kernel name.
+launches, total time and share per kernel name; an optional third argument is a
+regular expression of kernel names to leave out (e.g. the set-up kernels).
 """
 from __future__ import annotations
 
@@ -31,10 +32,12 @@ import sys
 import numpy as np
 
 
-def summarize(path: str) -> str:
-    """Markdown table of an ncu CSV launch list: launches, total ms and share per kernel."""
+def summarize(path: str, exclude: str = "") -> str:
+    """Markdown table of an ncu CSV launch list: launches, total ms and share per kernel
+    (kernels whose name matches the regular expression `exclude` left out)."""
     import csv
     import io
+    import re
     rows = []
     with open(path, newline="") as f:
         text = f.read()
@@ -46,6 +49,8 @@ def summarize(path: str) -> str:
             scale = {"nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "second": 1e3}.get(unit, 1e-6)
             name = r["Kernel Name"]
             name = name.split("(")[0].replace("void ", "") if "(" in name else name
+            if exclude and re.search(exclude, name):
+                continue
             rows.append((name, v * scale))
     tot = {}
     for name, ms in rows:
@@ -62,7 +67,7 @@ def summarize(path: str) -> str:
 def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
     if argv and argv[0] == "summarize":
-        print(summarize(argv[1]))
+        print(summarize(argv[1], argv[2] if len(argv) > 2 else ""))
         return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step", "fgmres_cycle", "vcycle"])

@@ -265,6 +265,46 @@ int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long 
                     double *flops);
 
 /*
+ * Time-range operations, for a V-cycle sharded across processes by time
+ * (each process owns a contiguous range of time blocks on every level and
+ * exchanges the couplings at the range ends; Sec. 5.3.2: the block-Jacobi
+ * sweep parallelises trivially in time, and the residual and the transfers
+ * of Sec. 5.3.1 couple neighbouring steps only).  Time block j = 0..n_l of
+ * level l holds u_j, z_j, lambda_j (j < n_l) and v_{j-1}, mu_{j-1} (j >= 1).
+ * Every vector is a full level-length FP64 DEVICE vector (mg_level_info), type
+ * major as above; only the entries named below are read or written, so each
+ * process may leave the rest unset.  FP64 levels of the handle (its
+ * precision option is ignored); the handle's omega, restriction rule and end
+ * rule apply.  Asynchronous on `stream` (mg_coarse_solve synchronises);
+ * MG_ERR_ARG for a bad level, range or pointer, MG_ERR_CUDA if a launch fails.
+ *
+ * mg_level_info: n_l (time steps) and the vector length n_l (4p + q).
+ * mg_range_sweep: one block-Jacobi sweep (Eq. jacobi-aj) of blocks [j0, j1)
+ *   of a smoothing level (not the coarsest): y = D^-1 (r - C yold) on those
+ *   blocks, relaxed by omega; yold NULL sweeps from y = 0.  Reads r and yold
+ *   of the blocks and the couplings u_{j0-1} (block j0 - 1) and mu_{j1-1}
+ *   (block j1) of yold.  y must not alias yold.
+ * mg_range_residual: r = b - A~ y on the rows of blocks [j0, j1); reads y on
+ *   the blocks and u_{j0-1}, mu_{j1-1}.
+ * mg_range_restrict: the restricted residual (Alg. 1, step 2, by the handle's
+ *   restriction rule) on the coarse blocks [j0 / 2, (j1 + 1) / 2) of level + 1
+ *   (j0 even); reads the fine residual r on blocks [j0 - 2, j1).
+ * mg_range_prolong: y += P e (Sec. 5.3.1) on blocks [j0, j1) of the level;
+ *   reads the coarse correction e on coarse blocks [j0 / 2, (j1 + 1) / 2 + 1).
+ * mg_coarse_solve: the coarsest level's solve of the V-cycle (GMRES with SGS,
+ *   the handle's coarse options) on a full coarse vector; FP64 handles only
+ *   (else MG_ERR_UNSUPPORTED); synchronises `stream`.
+ */
+int mg_level_info(const mg_handle *h, int level, int *n, long long *len);
+int mg_range_sweep(mg_handle *h, int level, int j0, int j1, const double *r, const double *yold, double *y,
+                   void *stream);
+int mg_range_residual(mg_handle *h, int level, int j0, int j1, const double *y, const double *b, double *r,
+                      void *stream);
+int mg_range_restrict(mg_handle *h, int level, int j0, int j1, const double *r, double *rc, void *stream);
+int mg_range_prolong(mg_handle *h, int level, int j0, int j1, const double *ec, double *y, void *stream);
+int mg_coarse_solve(mg_handle *h, const double *rc, double *yc, void *stream);
+
+/*
  * True residual without allocating (the paper has no counterpart).  For
  * callers that must not allocate device memory when they check a solution
  * (a framework's caching allocator owns the device pool, a real-time loop

@@ -325,7 +325,10 @@ void tri_stage_prepare() {
 
 template <typename T, typename CT = T>
 void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, const T *cplU, const T *cplM,
-                        T *out, cudaStream_t s, const T *yold = nullptr, T omega = T(1)) {
+                        T *out, cudaStream_t s, const T *yold = nullptr, T omega = T(1), int j0 = 0,
+                        int j1 = -1) {
+  // blocks [j0, j1) of the level (all: j1 < 0)
+  const int nb = (j1 < 0 ? L.n + 1 : j1) - j0;
   // per block: read r (4p+q), couplings (2p), N, V, Z (9p tridiagonal / 2p^2+pq dense), factor
   // (3p / p^2), old iterate if relaxed (4p+q); write 4p+q.  Flops: 45p (tridiagonal).
   const double w = 4.0 * L.p + L.q, p_ = L.p;
@@ -333,23 +336,23 @@ void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, con
                                                     : (3.0 * p_ * p_ + p_ * L.q) * sizeof(T);
   const double per_block = sizeof(T) * (2.0 * w + 2.0 * p_ + (omega != T(1) && yold ? w : 0.0)) + coef;
   const double fl = L.layout == MG_LAYOUT_TRIDIAG ? 45.0 * p_ : 2.0 * (3.0 * p_ * p_ + 2.0 * p_ * L.q + p_ * p_);
-  Bracket br(h, CAT_BLOCK_SOLVE, s, per_block * (L.n + 1), fl * (L.n + 1));
+  Bracket br(h, CAT_BLOCK_SOLVE, s, per_block * nb, fl * nb);
   if (L.layout == MG_LAYOUT_DENSE) {
     if constexpr (std::is_same<T, CT>::value)
-      k_block_solve_dense<T><<<grid_for(L.n + 1, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega);
+      k_block_solve_dense<T><<<grid_for(nb, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1);
   } else {
-    const int blocks = (int)((L.n + 1 + 3) / 4);
+    const int blocks = (nb + 3) / 4;
     const size_t smem = 4 * (size_t)tri_stage_elems<T>(L.p) * sizeof(T);
     if (h->pair_tri && tri_stage_ok(L) && L.n + 1 <= kPairMaxBlocks) {  // two warps per block
-      const int pblocks = (int)((L.n + 1 + 1) / 2);
+      const int pblocks = (nb + 1) / 2;
       const size_t psmem = 2 * (size_t)tri_pair_elems<T>(L.p) * sizeof(T);
       if (L.p == 4 * kWarp && L.q == L.p) {
-        k_block_solve_tri2<T, 4, 4 * kWarp, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega);
+        k_block_solve_tri2<T, 4, 4 * kWarp, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1);
       } else {
         switch (h->C) {
-          case 1: k_block_solve_tri2<T, 1, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-          case 2: k_block_solve_tri2<T, 2, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-          default: k_block_solve_tri2<T, 4, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+          case 1: k_block_solve_tri2<T, 1, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+          case 2: k_block_solve_tri2<T, 2, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+          default: k_block_solve_tri2<T, 4, 0, CT><<<pblocks, 128, psmem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
         }
       }
       ck_launch();
@@ -357,31 +360,35 @@ void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, con
     }
     if (h->stage_tri && tri_stage_ok(L)) {  // coefficients staged in shared memory (p <= 128)
       if (L.p == 4 * kWarp && L.q == L.p) {  // full chunks: p known at compile time
-        k_block_solve_tri<T, 4, true, 4 * kWarp, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega);
+        k_block_solve_tri<T, 4, true, 4 * kWarp, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1);
         ck_launch();
         return;
       }
       switch (h->C) {
-        case 1: k_block_solve_tri<T, 1, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-        case 2: k_block_solve_tri<T, 2, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-        default: k_block_solve_tri<T, 4, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+        case 1: k_block_solve_tri<T, 1, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+        case 2: k_block_solve_tri<T, 2, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+        default: k_block_solve_tri<T, 4, true, 0, CT><<<blocks, 128, smem, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
       }
       ck_launch();
       return;
     }
     switch (h->C) {
-      case 1: k_block_solve_tri<T, 1, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      case 2: k_block_solve_tri<T, 2, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      case 4: k_block_solve_tri<T, 4, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      case 8: k_block_solve_tri<T, 8, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
-      default: k_block_solve_tri<T, 16, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega); break;
+      case 1: k_block_solve_tri<T, 1, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+      case 2: k_block_solve_tri<T, 2, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+      case 4: k_block_solve_tri<T, 4, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+      case 8: k_block_solve_tri<T, 8, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
+      default: k_block_solve_tri<T, 16, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
     }
   }
   ck_launch();
 }
 
 template <typename T, typename CT = T>
-void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *b, T *out, cudaStream_t s) {
+void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *b, T *out, cudaStream_t s,
+                  int j0 = 0, int j1 = -1) {
+  // rows of blocks [j0, j1) (all: j1 < 0): a warp (thread) per step from max(j0 - 1, 0)
+  const int steps = (j1 < 0 ? L.n : std::min(j1, L.n)) - std::max(j0 - 1, 0);
+  if (steps <= 0) return;
   const double w = 4.0 * L.p + L.q;
   const double coef = L.layout == MG_LAYOUT_TRIDIAG ? 9.0 * L.p * sizeof(CT) / sizeof(T)
                                                     : 2.0 * L.p * L.p + L.p * L.q;
@@ -389,15 +396,15 @@ void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *
              L.layout == MG_LAYOUT_TRIDIAG ? 2.0 * 18.0 * L.p * L.n : 4.0 * L.n * (2.0 * L.p * L.p + L.p * L.q));
   if (L.layout == MG_LAYOUT_DENSE) {
     if constexpr (std::is_same<T, CT>::value)
-      k_apply_dense<T><<<grid_for(L.n, 128, 1 << 30), 128, 0, s>>>(L, x, b, out);
+      k_apply_dense<T><<<grid_for(steps, 128, 1 << 30), 128, 0, s>>>(L, x, b, out, nullptr, j0, j1);
   } else {
-    const int blocks = (L.n + 3) / 4;
+    const int blocks = (steps + 3) / 4;
     switch (h->C) {
-      case 1: k_apply_tri<T, 1, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      case 2: k_apply_tri<T, 2, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      case 4: k_apply_tri<T, 4, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      case 8: k_apply_tri<T, 8, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
-      default: k_apply_tri<T, 16, CT><<<blocks, 128, 0, s>>>(L, x, b, out); break;
+      case 1: k_apply_tri<T, 1, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
+      case 2: k_apply_tri<T, 2, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
+      case 4: k_apply_tri<T, 4, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
+      case 8: k_apply_tri<T, 8, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
+      default: k_apply_tri<T, 16, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
     }
   }
   ck_launch();
@@ -2466,6 +2473,114 @@ extern "C" int fgmres_solve_batched(mg_handle *const *hs, int count, const doubl
     return MG_ERR_OOM;
   }
   return worst;
+}
+
+// ===========================================================================
+// Time-range operations: the V-cycle's steps on a contiguous range of time
+// blocks of one level, for a cycle sharded across processes by time (each
+// process owns a range of blocks on every level and exchanges the couplings
+// at the range ends; the paper's block-Jacobi sweep parallelises trivially in
+// time, Sec. 5.3.2).  Vectors are full level-length FP64 device vectors in the
+// type-major layout; only the entries the call names are read or written.
+
+namespace {
+
+// the FP64 view of a level, or null
+const LevelView<double> *range_view(mg_handle *h, int level) {
+  if (!h || level < 0 || level >= (int)h->lv.size()) return nullptr;
+  return &h->lv[level].d.view;
+}
+
+bool range_ok(const LevelView<double> &L, int j0, int j1) { return j0 >= 0 && j1 > j0 && j1 <= L.n + 1; }
+
+int range_status() {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s", cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" int mg_level_info(const mg_handle *h, int level, int *n, long long *len) {
+  if (!h || level < 0 || level >= (int)h->lv.size()) return MG_ERR_ARG;
+  if (n) *n = h->lv[level].n;
+  if (len) *len = h->lv[level].len;
+  return MG_OK;
+}
+
+extern "C" int mg_range_sweep(mg_handle *h, int level, int j0, int j1, const double *r, const double *yold,
+                              double *y, void *stream) {
+  const LevelView<double> *L = range_view(h, level);
+  if (!L || level == (int)h->lv.size() - 1 || !r || !y || y == yold || !range_ok(*L, j0, j1)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double om = h->opts.omega;
+  Vec<const double> Y = make_cvec(yold ? yold : r, L->n, h->p, h->q);
+  const double *cu = yold ? Y.u : nullptr, *cm = yold ? Y.m : nullptr;
+  try {
+    // the V-cycle's own kernel choice for this level, restricted to the range: the same bits per block
+    launch_block_solve<double>(h, *L, r, cu, cm, y, s, yold, om, j0, j1);
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  }
+  return range_status();
+}
+
+extern "C" int mg_range_residual(mg_handle *h, int level, int j0, int j1, const double *y, const double *b,
+                                 double *r, void *stream) {
+  const LevelView<double> *L = range_view(h, level);
+  if (!L || !y || !b || !r || !range_ok(*L, j0, j1)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    launch_apply<double>(h, *L, y, b, r, s, j0, j1);
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  }
+  return range_status();
+}
+
+extern "C" int mg_range_restrict(mg_handle *h, int level, int j0, int j1, const double *r, double *rc,
+                                 void *stream) {
+  const LevelView<double> *L = range_view(h, level);
+  if (!L || level == (int)h->lv.size() - 1 || !r || !rc || !range_ok(*L, j0, j1) || (j0 & 1)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int K0 = j0 / 2, K1 = (j1 + 1) / 2;
+  const long long total = (long long)(L->n / 2) * (4 * h->p + h->q);
+  h->launches++;
+  if (h->opts.restrict_rule == MG_RESTRICT_TRANSPOSE)
+    k_restrict_transpose<double><<<grid_for(total, 256), 256, 0, s>>>(r, rc, L->n, h->p, h->q, h->opts.end_rule,
+                                                                     K0, K1);
+  else
+    k_restrict_inject<double><<<grid_for(total, 256), 256, 0, s>>>(r, rc, L->n, h->p, h->q, K0, K1);
+  return range_status();
+}
+
+extern "C" int mg_range_prolong(mg_handle *h, int level, int j0, int j1, const double *ec, double *y,
+                                void *stream) {
+  const LevelView<double> *L = range_view(h, level);
+  if (!L || level == (int)h->lv.size() - 1 || !ec || !y || !range_ok(*L, j0, j1)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->launches++;
+  k_prolong_add<double><<<grid_for(h->lv[level].len, 256), 256, 0, s>>>(y, ec, L->n, h->p, h->q,
+                                                                        h->opts.end_rule, j0, j1);
+  return range_status();
+}
+
+extern "C" int mg_coarse_solve(mg_handle *h, const double *rc, double *yc, void *stream) {
+  if (!h || !rc || !yc || rc == yc) return MG_ERR_ARG;
+  if (h->opts.precision != MG_PRECISION_FP64) return MG_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    coarse_solve<double>(h, rc, yc, s);
+    ck(cudaStreamSynchronize(s));
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    return MG_ERR_OOM;
+  }
+  return MG_OK;
 }
 
 // ===========================================================================

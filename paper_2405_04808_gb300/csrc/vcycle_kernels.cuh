@@ -175,11 +175,11 @@ __host__ __device__ constexpr int tri_stage_elems(int p) { return 12 * p + kScan
 template <typename T, int C, bool kStage = false, int PF = 0, typename CT = T>
 __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T, CT> L, const T *__restrict__ r,
                                                          const T *cplU, const T *cplM, T *out,
-                                                         const T *yold, T omega) {
+                                                         const T *yold, T omega, int j0 = 0, int j1 = -1) {
   const int ln = threadIdx.x & (kWarp - 1);
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int j = j0 + (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;  // blocks [j0, j1) (all: j1 < 0)
   const int n = L.n, p = PF ? PF : L.p, q = PF ? PF : L.q;
-  if (j > n) return;
+  if (j > n || (j1 >= 0 && j >= j1)) return;
   TriBlock<T, CT> Bk{};
   if (j < n) Bk = tri_block(L, j);
   if (kStage && j < n) {
@@ -266,12 +266,12 @@ __device__ __forceinline__ void pair_barrier(int id) { asm volatile("bar.sync %0
 template <typename T, int C, int PF = 0, typename CT = T>
 __global__ void __launch_bounds__(128) k_block_solve_tri2(LevelView<T, CT> L, const T *__restrict__ r,
                                                           const T *cplU, const T *cplM, T *out,
-                                                          const T *yold, T omega) {
+                                                          const T *yold, T omega, int j0 = 0, int j1 = -1) {
   const int ln = threadIdx.x & (kWarp - 1);
   const int w = threadIdx.x / kWarp, pair = w >> 1, role = w & 1;
-  const int j = blockIdx.x * 2 + pair;
+  const int j = j0 + blockIdx.x * 2 + pair;  // blocks [j0, j1) (all: j1 < 0)
   const int n = L.n, p = PF ? PF : L.p, q = PF ? PF : L.q;
-  if (j > n) return;
+  if (j > n || (j1 >= 0 && j >= j1)) return;
   extern __shared__ __align__(16) unsigned char tri2_smem[];
   T *base = reinterpret_cast<T *>(tri2_smem) + pair * tri_pair_elems<T>(p);
   T *xch = base + 12 * p + kScanPerBlock;  // rhs part from warp 1, then lambda from warp 0
@@ -719,10 +719,10 @@ __global__ void __launch_bounds__(128) k_sweeps_tri2(LevelView<T> L, const T *__
 template <typename T>
 __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const T *__restrict__ r,
                                                            const T *cplU, const T *cplM, T *out,
-                                                           const T *yold, T omega) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+                                                           const T *yold, T omega, int j0 = 0, int j1 = -1) {
+  const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;  // blocks [j0, j1) (all: j1 < 0)
   const int n = L.n, p = L.p, q = L.q;
-  if (j > n) return;
+  if (j > n || (j1 >= 0 && j >= j1)) return;
   Vec<const T> R = make_cvec(r, n, p, q);
   Vec<T> Y = make_vec(out, n, p, q);
   T ru[kDenseMax] = {}, rz[kDenseMax] = {}, rl[kDenseMax] = {}, rv[kDenseMax] = {}, rm[kDenseMax] = {};
@@ -784,12 +784,17 @@ __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const
 // out = b - A~ x  (b non-null)  or  out = A~ x  (b null), all five types.
 template <typename T, int C, typename CT = T>
 __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *__restrict__ x,
-                                                   const T *__restrict__ b, T *out, const int *guard = nullptr) {
+                                                   const T *__restrict__ b, T *out, const int *guard = nullptr,
+                                                   int j0 = 0, int j1 = -1) {
   if (guard && *guard == 0) return;
   const int ln = threadIdx.x & (kWarp - 1);
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
   const int n = L.n, p = L.p, q = L.q;
-  if (t >= n) return;
+  // the rows of time blocks [j0, j1) (all: j1 < 0): u, z, lambda rows of steps [j0, j1), v, mu rows of
+  // steps [j0 - 1, j1 - 1); a warp per step t from max(j0 - 1, 0)
+  const int t = max(j0 - 1, 0) + (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int tend = j1 < 0 ? n : min(j1, n);
+  if (t >= tend) return;
+  const bool own_uzl = t >= j0, own_vm = t + 1 >= j0 && (j1 < 0 || t + 1 < j1);
   Vec<const T> X = make_cvec(x, n, p, q);
   Vec<T> O = make_vec(out, n, p, q);
   const CT *N = L.N + t * L.sN, *Z = L.Z + t * L.sZ, *Vt = L.V + t * L.sV;
@@ -810,7 +815,7 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
     if (b) chunk_load<T, C>(o, B.u + (long long)t * p, p, ln);
 #pragma unroll
     for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
-    chunk_store<T, C>(O.u + (long long)t * p, o, p, ln);
+    if (own_uzl) chunk_store<T, C>(O.u + (long long)t * p, o, p, ln);
   }
   // v row
 #pragma unroll
@@ -825,7 +830,7 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
     if (b) chunk_load<T, C>(o, B.v + (long long)t * p, p, ln);
 #pragma unroll
     for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
-    chunk_store<T, C>(O.v + (long long)t * p, o, p, ln);
+    if (own_vm) chunk_store<T, C>(O.v + (long long)t * p, o, p, ln);
   }
   // z row
 #pragma unroll
@@ -836,7 +841,7 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
     if (b) chunk_load<T, C>(o, B.z + (long long)t * q, q, ln);
 #pragma unroll
     for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
-    chunk_store<T, C>(O.z + (long long)t * q, o, q, ln);
+    if (own_uzl) chunk_store<T, C>(O.z + (long long)t * q, o, q, ln);
   }
   // lambda row
   tri_mv<T, C, false>(acc, N, xu, p, ln, T(1));
@@ -851,7 +856,7 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
     if (b) chunk_load<T, C>(o, B.l + (long long)t * p, p, ln);
 #pragma unroll
     for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, acc[e], o[e]) : acc[e];
-    chunk_store<T, C>(O.l + (long long)t * p, o, p, ln);
+    if (own_uzl) chunk_store<T, C>(O.l + (long long)t * p, o, p, ln);
   }
   // mu row
   {
@@ -859,17 +864,20 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
     if (b) chunk_load<T, C>(o, B.m + (long long)t * p, p, ln);
 #pragma unroll
     for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, xu[e] - xv[e], o[e]) : xu[e] - xv[e];
-    chunk_store<T, C>(O.m + (long long)t * p, o, p, ln);
+    if (own_vm) chunk_store<T, C>(O.m + (long long)t * p, o, p, ln);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__restrict__ x,
-                                                     const T *__restrict__ b, T *out, const int *guard = nullptr) {
+                                                     const T *__restrict__ b, T *out, const int *guard = nullptr,
+                                                     int j0 = 0, int j1 = -1) {
   if (guard && *guard == 0) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = L.n, p = L.p, q = L.q;
-  if (t >= n) return;
+  const int t = max(j0 - 1, 0) + blockIdx.x * blockDim.x + threadIdx.x;  // as k_apply_tri
+  const int tend = j1 < 0 ? n : min(j1, n);
+  if (t >= tend) return;
+  const bool own_uzl = t >= j0, own_vm = t + 1 >= j0 && (j1 < 0 || t + 1 < j1);
   Vec<const T> X = make_cvec(x, n, p, q);
   Vec<T> O = make_vec(out, n, p, q);
   Vec<const T> B = make_cvec(b ? b : x, n, p, q);
@@ -881,29 +889,34 @@ __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__
   // u row
   for (int i = 0; i < p; ++i) acc[i] = xu[i] + xm[i];
   dn_mtv<T>(acc, N, xl, p, p, T(1), true);
-  for (int i = 0; i < p; ++i)
-    O.u[(long long)t * p + i] = b ? fma(sgn, acc[i], B.u[(long long)t * p + i]) : acc[i];
+  if (own_uzl)
+    for (int i = 0; i < p; ++i)
+      O.u[(long long)t * p + i] = b ? fma(sgn, acc[i], B.u[(long long)t * p + i]) : acc[i];
   // v row
   for (int i = 0; i < p; ++i) acc[i] = xv[i] - xm[i];
   if (t + 1 < n) dn_mtv<T>(acc, L.V + (t + 1) * L.sV, X.l + (long long)(t + 1) * p, p, p, T(1), true);
-  for (int i = 0; i < p; ++i)
-    O.v[(long long)t * p + i] = b ? fma(sgn, acc[i], B.v[(long long)t * p + i]) : acc[i];
+  if (own_vm)
+    for (int i = 0; i < p; ++i)
+      O.v[(long long)t * p + i] = b ? fma(sgn, acc[i], B.v[(long long)t * p + i]) : acc[i];
   // z row
   for (int i = 0; i < q; ++i) acc[i] = xz[i];
   dn_mtv<T>(acc, Z, xl, p, q, T(1), true);
-  for (int i = 0; i < q; ++i)
-    O.z[(long long)t * q + i] = b ? fma(sgn, acc[i], B.z[(long long)t * q + i]) : acc[i];
+  if (own_uzl)
+    for (int i = 0; i < q; ++i)
+      O.z[(long long)t * q + i] = b ? fma(sgn, acc[i], B.z[(long long)t * q + i]) : acc[i];
   // lambda row
   dn_mv<T>(acc, N, xu, p, p, T(1), false);
   dn_mv<T>(acc, Z, xz, p, q, T(1), true);
   if (t >= 1) dn_mv<T>(acc, L.V + t * L.sV, X.v + (long long)(t - 1) * p, p, p, T(1), true);
-  for (int i = 0; i < p; ++i)
-    O.l[(long long)t * p + i] = b ? fma(sgn, acc[i], B.l[(long long)t * p + i]) : acc[i];
+  if (own_uzl)
+    for (int i = 0; i < p; ++i)
+      O.l[(long long)t * p + i] = b ? fma(sgn, acc[i], B.l[(long long)t * p + i]) : acc[i];
   // mu row
-  for (int i = 0; i < p; ++i) {
-    T d = xu[i] - xv[i];
-    O.m[(long long)t * p + i] = b ? fma(sgn, d, B.m[(long long)t * p + i]) : d;
-  }
+  if (own_vm)
+    for (int i = 0; i < p; ++i) {
+      T d = xu[i] - xv[i];
+      O.m[(long long)t * p + i] = b ? fma(sgn, d, B.m[(long long)t * p + i]) : d;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1021,8 +1034,12 @@ __global__ void __launch_bounds__(128) k_residual_restrict_dense(LevelView<T> L,
 // y += P e (Sec. 5.3.1): u, v, lambda, mu linear (x_f[2K] = e[K],
 // x_f[2K+1] = (e[K] + e[K+1]) / 2, last point by end_rule); z piecewise
 // constant.  One thread per fine entry.
+__device__ __forceinline__ bool coarse_owned(bool vm, int K, int K0, int K1);
+// (j0, j1): add only to the entries of fine time blocks [j0, j1) (u, z, lambda at
+// steps [j0, j1), v, mu at steps [j0 - 1, j1 - 1)); j1 < 0: every entry
 template <typename T>
-__global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q, int end_rule) {
+__global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q, int end_rule, int j0 = 0,
+                              int j1 = -1) {
   const long long np = (long long)n * p, nq = (long long)n * q;
   const long long total = 4 * np + nq;
   const int nc = n / 2;
@@ -1051,6 +1068,8 @@ __global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q
       coarse_off = np + nq / 2 + which * (np / 2);
     }
     const int t = (int)(k / width), i = (int)(k % width);
+    const bool vm = idx < 2 * np ? idx >= np : idx >= 3 * np + nq;  // v or mu entry
+    if (!coarse_owned(vm, t, j0, j1)) continue;
     const int K = t >> 1;
     const T *ec = e + coarse_off;
     T add;
@@ -1074,8 +1093,17 @@ __global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q
 //                      weight (1 for end_rule 0, 1/2 for end_rule 1)
 //   z:                 rc[K] = r[2K] + r[2K+1]
 // r is the full fine residual b - A~ y (k_apply_*).  One thread per coarse entry.
+// Ownership of a vector entry by a range of time blocks [j0, j1) (j1 < 0: all):
+// block j holds u, z, lambda of step j and v, mu of step j - 1.
+__device__ __forceinline__ bool coarse_owned(bool vm, int K, int K0, int K1) {
+  const int blk = vm ? K + 1 : K;
+  return blk >= K0 && (K1 < 0 || blk < K1);
+}
+
+// (K0, K1) of the restriction kernels: write only the entries of coarse time blocks [K0, K1)
 template <typename T>
-__global__ void k_restrict_transpose(const T *__restrict__ r, T *rc, int n, int p, int q, int end_rule) {
+__global__ void k_restrict_transpose(const T *__restrict__ r, T *rc, int n, int p, int q, int end_rule, int K0 = 0,
+                                     int K1 = -1) {
   const int nc = n / 2;
   const long long ncp = (long long)nc * p, ncq = (long long)nc * q;
   const long long np = (long long)n * p, nq = (long long)n * q;
@@ -1105,6 +1133,8 @@ __global__ void k_restrict_transpose(const T *__restrict__ r, T *rc, int n, int 
       coarse_off = 2 * ncp + ncq + which * ncp;
     }
     const int K = (int)(k / width), i = (int)(k % width);
+    const bool vm = idx < 2 * ncp ? idx >= ncp : idx >= 3 * ncp + ncq;  // v or mu entry
+    if (!coarse_owned(vm, K, K0, K1)) continue;
     const T *rf = r + fine_off;
     const T r0 = rf[(long long)(2 * K) * width + i], r1 = rf[(long long)(2 * K + 1) * width + i];
     T acc;
@@ -1116,6 +1146,49 @@ __global__ void k_restrict_transpose(const T *__restrict__ r, T *rc, int n, int 
       if (K >= 1) acc = fma(T(0.5), rf[(long long)(2 * K - 1) * width + i], acc);
     }
     rc[coarse_off + k] = acc;
+  }
+}
+
+// Restriction of a given fine residual by the variable formulas of Sec. 5.3.1
+// (injection at fine step 2K, average of z over 2K, 2K + 1), one thread per
+// coarse entry, for the time-range entry points (the V-cycle itself fuses it
+// with the residual: k_residual_restrict_*).  (K0, K1) as k_restrict_transpose.
+template <typename T>
+__global__ void k_restrict_inject(const T *__restrict__ r, T *rc, int n, int p, int q, int K0, int K1) {
+  const int nc = n / 2;
+  const long long ncp = (long long)nc * p, ncq = (long long)nc * q;
+  const long long np = (long long)n * p, nq = (long long)n * q;
+  const long long total = 4 * ncp + ncq;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long k = idx;
+    int width = p;
+    long long fine_off, coarse_off;
+    bool average = false;
+    if (k < 2 * ncp) {
+      const long long which = k / ncp;
+      k -= which * ncp;
+      fine_off = which * np;
+      coarse_off = which * ncp;
+    } else if (k < 2 * ncp + ncq) {
+      k -= 2 * ncp;
+      width = q;
+      fine_off = 2 * np;
+      coarse_off = 2 * ncp;
+      average = true;
+    } else {
+      k -= 2 * ncp + ncq;
+      const long long which = k / ncp;
+      k -= which * ncp;
+      fine_off = 2 * np + nq + which * np;
+      coarse_off = 2 * ncp + ncq + which * ncp;
+    }
+    const int K = (int)(k / width), i = (int)(k % width);
+    const bool vm = idx < 2 * ncp ? idx >= ncp : idx >= 3 * ncp + ncq;
+    if (!coarse_owned(vm, K, K0, K1)) continue;
+    const T *rf = r + fine_off;
+    const T r0 = rf[(long long)(2 * K) * width + i];
+    rc[coarse_off + k] = average ? T(0.5) * (r0 + rf[(long long)(2 * K + 1) * width + i]) : r0;
   }
 }
 

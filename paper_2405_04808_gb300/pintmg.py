@@ -43,6 +43,8 @@ RESTRICT = {"inject": 0, "transpose": 1}
 EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmres_solve_batched",
             "mg_vector_length",
             "mg_launch_count", "mg_probe_fma", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
+            "mg_level_info", "mg_range_sweep", "mg_range_residual", "mg_range_restrict", "mg_range_prolong",
+            "mg_coarse_solve",
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
             "mg_net_forward", "mg_net_loss_grad", "mg_net_adam_step", "mg_net_train", "mg_net_destroy",
             "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune", "mg_jacobi_radius",
@@ -135,7 +137,13 @@ def lib():
                 ("mg_coarse_shape", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
                 ("mg_autotune", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), vp], ci),
                 ("mg_jacobi_radius", [vp, ci, ci, ctypes.POINTER(ctypes.c_double), vp], ci),
-                ("mg_probe_fma", [ci, ci, ci, vp, vp], ci)):
+                ("mg_probe_fma", [ci, ci, ci, vp, vp], ci),
+                ("mg_level_info", [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_longlong)], ci),
+                ("mg_range_sweep", [vp, ci, ci, ci, vp, vp, vp, vp], ci),
+                ("mg_range_residual", [vp, ci, ci, ci, vp, vp, vp, vp], ci),
+                ("mg_range_restrict", [vp, ci, ci, ci, vp, vp, vp], ci),
+                ("mg_range_prolong", [vp, ci, ci, ci, vp, vp, vp], ci),
+                ("mg_coarse_solve", [vp, vp, vp, vp], ci)):
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
@@ -252,6 +260,42 @@ def mg_profile_read(h) -> dict:
     if n < 0:
         raise PintmgError(n, "mg_profile_read")
     return {names[i].decode(): (ms[i], int(cnt[i]), by[i], fl[i]) for i in range(min(n, k))}
+
+
+# --------------------------------------------------------------------------
+# time-range operations (a V-cycle sharded by time: paper_2405_04808_gb300.timeshard)
+
+def mg_level_info(h, level: int):
+    """(n_l, vector length) of a level."""
+    n, ln = ctypes.c_int(), ctypes.c_longlong()
+    _check(lib().mg_level_info(ctypes.c_void_p(h), int(level), ctypes.byref(n), ctypes.byref(ln)), "mg_level_info")
+    return n.value, ln.value
+
+
+def mg_range_sweep(h, level, j0, j1, r_ptr, yold_ptr, y_ptr, stream=0):
+    _check(lib().mg_range_sweep(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(r_ptr),
+                                ctypes.c_void_p(yold_ptr or 0), ctypes.c_void_p(y_ptr), ctypes.c_void_p(stream)),
+           "mg_range_sweep")
+
+
+def mg_range_residual(h, level, j0, j1, y_ptr, b_ptr, r_ptr, stream=0):
+    _check(lib().mg_range_residual(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(y_ptr), ctypes.c_void_p(b_ptr),
+                                   ctypes.c_void_p(r_ptr), ctypes.c_void_p(stream)), "mg_range_residual")
+
+
+def mg_range_restrict(h, level, j0, j1, r_ptr, rc_ptr, stream=0):
+    _check(lib().mg_range_restrict(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(r_ptr), ctypes.c_void_p(rc_ptr),
+                                   ctypes.c_void_p(stream)), "mg_range_restrict")
+
+
+def mg_range_prolong(h, level, j0, j1, ec_ptr, y_ptr, stream=0):
+    _check(lib().mg_range_prolong(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(ec_ptr), ctypes.c_void_p(y_ptr),
+                                  ctypes.c_void_p(stream)), "mg_range_prolong")
+
+
+def mg_coarse_solve(h, rc_ptr, yc_ptr, stream=0):
+    _check(lib().mg_coarse_solve(ctypes.c_void_p(h), ctypes.c_void_p(rc_ptr), ctypes.c_void_p(yc_ptr),
+                                 ctypes.c_void_p(stream)), "mg_coarse_solve")
 
 
 #: threads per CTA and independent FMA chains per thread of mg_probe_fma

@@ -47,7 +47,8 @@ typedef enum {
 } mg_status;
 
 typedef enum {
-  MG_LAYOUT_DENSE = 0,   /* blocks stored dense, row-major; p <= 4, q <= 4 */
+  MG_LAYOUT_DENSE = 0,   /* blocks stored dense, row-major; p <= 32, q <= 32 (a thread per time block up to 4,
+                            a warp per time block beyond) */
   MG_LAYOUT_TRIDIAG = 1  /* q == p, every p x p block tridiagonal (band rows, below) */
 } mg_layout;
 

@@ -258,6 +258,58 @@ __device__ __forceinline__ void penta_solve(T (&x)[C], const T (&r)[C], const T 
 }
 
 // ---------------------------------------------------------------------------
+// Dense blocks up to kDenseWarpMax: one warp per time block, lane i owning
+// entry i of every vector (entries at i >= the length are 0).  A is row-major.
+
+constexpr int kDenseWarpMax = 32;
+
+template <typename T>
+__device__ __forceinline__ T dw_load(const T *src, int len, int ln) {
+  return ln < len ? src[ln] : T(0);
+}
+
+// y (+)= sign A x, A rows x cols (lane i forms row i; x held by lane k)
+template <typename T>
+__device__ __forceinline__ T dw_mv(const T *A, T x, int rows, int cols, int ln) {
+  T acc = T(0);
+  for (int k = 0; k < cols; ++k) {
+    const T xk = __shfl_sync(kFull, x, k);
+    if (ln < rows) acc = fma(A[ln * cols + k], xk, acc);
+  }
+  return acc;
+}
+
+// A^T x, A rows x cols (lane i forms entry i of the cols-vector)
+template <typename T>
+__device__ __forceinline__ T dw_mtv(const T *A, T x, int rows, int cols, int ln) {
+  T acc = T(0);
+  for (int k = 0; k < rows; ++k) {
+    const T xk = __shfl_sync(kFull, x, k);
+    if (ln < cols) acc = fma(A[k * cols + ln], xk, acc);
+  }
+  return acc;
+}
+
+// x = S^-1 r with S = L L^T (L row-major p x p, diagonal stored inverted):
+// column-oriented substitutions, one broadcast per column
+template <typename T>
+__device__ __forceinline__ T dw_chol_solve(const T *L, T r, int p, int ln) {
+  T y = r;
+  for (int k = 0; k < p; ++k) {  // forward: y_k = (r_k - sum_{i<k} L_ki y_i) / L_kk
+    const T yk = __shfl_sync(kFull, y, k) * L[k * p + k];
+    if (ln == k) y = yk;
+    if (ln > k && ln < p) y = fma(-L[ln * p + k], yk, y);
+  }
+  T x = y;
+  for (int k = p - 1; k >= 0; --k) {  // backward with L^T
+    const T xk = __shfl_sync(kFull, x, k) * L[k * p + k];
+    if (ln == k) x = xk;
+    if (ln < k) x = fma(-L[k * p + ln], xk, x);
+  }
+  return ln < p ? x : T(0);
+}
+
+// ---------------------------------------------------------------------------
 // Dense small-block helpers (one thread per time block, p, q <= kDenseMax)
 
 // y = A x (A p x m row-major) or y = A^T x (A m x p), sign applied

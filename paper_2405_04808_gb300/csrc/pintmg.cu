@@ -338,8 +338,13 @@ void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, con
   const double fl = L.layout == MG_LAYOUT_TRIDIAG ? 45.0 * p_ : 2.0 * (3.0 * p_ * p_ + 2.0 * p_ * L.q + p_ * p_);
   Bracket br(h, CAT_BLOCK_SOLVE, s, per_block * nb, fl * nb);
   if (L.layout == MG_LAYOUT_DENSE) {
-    if constexpr (std::is_same<T, CT>::value)
-      k_block_solve_dense<T><<<grid_for(nb, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1);
+    if constexpr (std::is_same<T, CT>::value) {
+      if (L.p > kDenseMax || L.q > kDenseMax)  // a warp per block
+        k_block_solve_dw<T><<<(nb + 3) / 4, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1);
+      else
+        k_block_solve_dense<T><<<grid_for(nb, 128, 1 << 30), 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0,
+                                                                          j1);
+    }
   } else {
     const int blocks = (nb + 3) / 4;
     const size_t smem = 4 * (size_t)tri_stage_elems<T>(L.p) * sizeof(T);
@@ -395,8 +400,12 @@ void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *
   Bracket br(h, CAT_APPLY, s, sizeof(T) * (L.n * ((b ? 3.0 : 2.0) * w + coef)),
              L.layout == MG_LAYOUT_TRIDIAG ? 2.0 * 18.0 * L.p * L.n : 4.0 * L.n * (2.0 * L.p * L.p + L.p * L.q));
   if (L.layout == MG_LAYOUT_DENSE) {
-    if constexpr (std::is_same<T, CT>::value)
-      k_apply_dense<T><<<grid_for(steps, 128, 1 << 30), 128, 0, s>>>(L, x, b, out, nullptr, j0, j1);
+    if constexpr (std::is_same<T, CT>::value) {
+      if (L.p > kDenseMax || L.q > kDenseMax)
+        k_apply_dw<T><<<(steps + 3) / 4, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1);
+      else
+        k_apply_dense<T><<<grid_for(steps, 128, 1 << 30), 128, 0, s>>>(L, x, b, out, nullptr, j0, j1);
+    }
   } else {
     const int blocks = (steps + 3) / 4;
     switch (h->C) {
@@ -492,8 +501,12 @@ void launch_residual_restrict(mg_handle *h, const LevelView<T, CT> &L, const T *
              (L.n / 2) * (sizeof(T) * (2.0 * (w + L.q) + w + 3.0 * L.p) + sizeof(CT) * 9.0 * L.p), 0.0);
   const int nc = L.n / 2;
   if (L.layout == MG_LAYOUT_DENSE) {
-    if constexpr (std::is_same<T, CT>::value)
-      k_residual_restrict_dense<T><<<grid_for(nc, 128, 1 << 30), 128, 0, s>>>(L, y, b, rc);
+    if constexpr (std::is_same<T, CT>::value) {
+      if (L.p > kDenseMax || L.q > kDenseMax)
+        k_residual_restrict_dw<T><<<(nc + 3) / 4, 128, 0, s>>>(L, y, b, rc);
+      else
+        k_residual_restrict_dense<T><<<grid_for(nc, 128, 1 << 30), 128, 0, s>>>(L, y, b, rc);
+    }
   } else {
     const int blocks = (nc + 3) / 4;
     switch (h->C) {
@@ -1517,7 +1530,9 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
       {
         Bracket br(h, CAT_APPLY, bs);
         const LevelView<double> &L = h->lv[0].d.view;
-        if (L.layout == MG_LAYOUT_DENSE) {
+        if (L.layout == MG_LAYOUT_DENSE && (L.p > kDenseMax || L.q > kDenseMax)) {
+          k_apply_dw<double><<<(L.n + 3) / 4, 128, 0, bs>>>(L, x, b, h->fr, &st->restart);
+        } else if (L.layout == MG_LAYOUT_DENSE) {
           k_apply_dense<double><<<grid_for(L.n, 128, 1 << 30), 128, 0, bs>>>(L, x, b, h->fr, &st->restart);
         } else {
           const int blocks = (L.n + 3) / 4;
@@ -1819,7 +1834,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     return MG_ERR_ARG;
   }
   if (layout == MG_LAYOUT_TRIDIAG && q != p) return MG_ERR_ARG;
-  if (layout == MG_LAYOUT_DENSE && (p > kDenseMax || q > kDenseMax)) return MG_ERR_UNSUPPORTED;
+  if (layout == MG_LAYOUT_DENSE && (p > kDenseWarpMax || q > kDenseWarpMax)) return MG_ERR_UNSUPPORTED;
   if (layout == MG_LAYOUT_TRIDIAG && p > 32 * 16) return MG_ERR_UNSUPPORTED;
 
   const int msz = layout == MG_LAYOUT_DENSE ? p * p : 3 * p;
@@ -1968,7 +1983,10 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
         v.scan = scan;
       } else {
         double *fac = h->mem.alloc<double>((size_t)nl * p * p);
-        k_factor_dense<<<grid_for(nl, 64, 1 << 20), 64, 0, s>>>(nl, p, q, N, msz, Z, zsz, fac, h->flag);
+        if (p > kDenseMax || q > kDenseMax)
+          k_factor_dw<<<(nl + 3) / 4, 128, 0, s>>>(nl, p, q, N, msz, Z, zsz, fac, h->flag);
+        else
+          k_factor_dense<<<grid_for(nl, 64, 1 << 20), 64, 0, s>>>(nl, p, q, N, msz, Z, zsz, fac, h->flag);
         ck_launch();
         v.fac = fac;
         v.sFac = (long long)p * p;
@@ -1989,7 +2007,10 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
               default: k_chain_mats_tri<16><<<blocks, 128, 0, s>>>(v, lev.d.Cu, lev.d.Em); break;
             }
           } else {
-            k_chain_mats_dense<<<grid_for(nl - 1, 64, 1 << 20), 64, 0, s>>>(v, lev.d.Cu, lev.d.Em);
+            if (p > kDenseMax || q > kDenseMax)
+              k_chain_mats_dw<<<(nl - 1 + 3) / 4, 128, 0, s>>>(v, lev.d.Cu, lev.d.Em);
+            else
+              k_chain_mats_dense<<<grid_for(nl - 1, 64, 1 << 20), 64, 0, s>>>(v, lev.d.Cu, lev.d.Em);
           }
           ck_launch();
         }
@@ -2650,7 +2671,9 @@ extern "C" int mg_true_residual_noalloc(mg_handle *h, const double *b, const dou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const LevelView<double> &L = h->lv[0].d.view;
   // r = b - A x (every entry written)
-  if (L.layout == MG_LAYOUT_DENSE) {
+  if (L.layout == MG_LAYOUT_DENSE && (L.p > kDenseMax || L.q > kDenseMax)) {
+    k_apply_dw<double><<<(L.n + 3) / 4, 128, 0, s>>>(L, x, b, r);
+  } else if (L.layout == MG_LAYOUT_DENSE) {
     k_apply_dense<double><<<grid_for(L.n, 128, 1 << 30), 128, 0, s>>>(L, x, b, r);
   } else {
     const int blocks = (L.n + 3) / 4;

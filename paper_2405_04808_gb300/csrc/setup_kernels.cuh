@@ -168,6 +168,64 @@ __global__ void k_factor_dense(int n, int p, int q, const double *__restrict__ N
   if (bad) atomicExch(status, 1);
 }
 
+// Cholesky of the dense S = N N^T + Z Z^T for p, q <= 32: one warp per block,
+// S in shared memory (32 x 32 doubles per warp; lane r owns row r), factored
+// column by column; the factor's format is k_factor_dense's.
+__global__ void __launch_bounds__(128) k_factor_dw(int n, int p, int q, const double *__restrict__ N, long long sN,
+                                                   const double *__restrict__ Z, long long sZ, double *fac,
+                                                   int *status) {
+  __shared__ double Sm[4][kDenseWarpMax * kDenseWarpMax];
+  const int w = threadIdx.x / kWarp, ln = threadIdx.x & (kWarp - 1);
+  const int j = blockIdx.x * 4 + w;
+  if (j >= n) return;
+  const double *Nj = N + j * sN, *Zj = Z + j * sZ;
+  double *S = Sm[w];
+  if (ln < p)
+    for (int c = 0; c < p; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < p; ++k) acc = fma(Nj[ln * p + k], Nj[c * p + k], acc);
+      for (int k = 0; k < q; ++k) acc = fma(Zj[ln * q + k], Zj[c * q + k], acc);
+      S[ln * p + c] = acc;
+    }
+  __syncwarp();
+  double *Lj = fac + (long long)j * p * p;
+  bool bad = false;
+  for (int c = 0; c < p; ++c) {
+    double d = S[c * p + c];
+    if (!(d > 0.0) || !isfinite(d)) {
+      bad = true;
+      d = 1.0;
+    }
+    const double lc = sqrt(d);
+    __syncwarp();
+    if (ln > c && ln < p) S[ln * p + c] /= lc;
+    __syncwarp();
+    if (ln > c && ln < p)
+      for (int cc = c + 1; cc <= ln; ++cc) S[ln * p + cc] = fma(-S[ln * p + c], S[cc * p + c], S[ln * p + cc]);
+    if (ln < p) Lj[ln * p + c] = ln == c ? 1.0 / lc : (ln > c ? S[ln * p + c] : 0.0);
+    __syncwarp();
+  }
+  if (bad && ln == 0) atomicExch(status, 1);
+}
+
+// Coarsest-level SGS chain matrices for dense blocks up to 32: one warp per block j = 1..n-1,
+// the columns of Cu_j = N_j^T S_j^-1 V_j and Em_j = V_j^T S_j^-1 N_j one after another
+__global__ void __launch_bounds__(128) k_chain_mats_dw(LevelView<double> L, double *Cu, double *Em) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int j = 1 + (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int n = L.n, p = L.p;
+  if (j >= n) return;
+  const double *N = L.N + j * L.sN, *V = L.V + j * L.sV, *fac = L.fac + j * L.sFac;
+  for (int col = 0; col < p; ++col) {
+    double t = ln < p ? V[ln * p + col] : 0.0;
+    double o = dw_mtv(N, dw_chol_solve(fac, t, p, ln), p, p, ln);
+    if (ln < p) Cu[((long long)j * p + ln) * p + col] = o;
+    t = ln < p ? N[ln * p + col] : 0.0;
+    o = dw_mtv(V, dw_chol_solve(fac, t, p, ln), p, p, ln);
+    if (ln < p) Em[((long long)j * p + ln) * p + col] = o;
+  }
+}
+
 // Coarsest-level SGS chain matrices, column `col` of block j:
 //   Cu_j e = N_j^T S_j^-1 V_j e,   Em_j e = V_j^T S_j^-1 N_j e     (j = 1..n-1)
 // Tridiagonal: one warp per (j, col).

@@ -716,6 +716,68 @@ __global__ void __launch_bounds__(128) k_sweeps_tri2(LevelView<T> L, const T *__
   }
 }
 
+// Dense blocks with p, q <= 32 (kDenseWarpMax): one warp per time block, lane i
+// holding entry i of every vector; the same Schur-complement solve as
+// local_solve_dense, products by broadcasts, S^-1 by column substitutions.
+template <typename T>
+__global__ void __launch_bounds__(128) k_block_solve_dw(LevelView<T> L, const T *__restrict__ r,
+                                                        const T *cplU, const T *cplM, T *out,
+                                                        const T *yold, T omega, int j0 = 0, int j1 = -1) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int j = j0 + (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;  // blocks [j0, j1) (all: j1 < 0)
+  const int n = L.n, p = L.p, q = L.q;
+  if (j > n || (j1 >= 0 && j >= j1)) return;
+  Vec<const T> R = make_cvec(r, n, p, q);
+  Vec<T> Y = make_vec(out, n, p, q);
+  Vec<const T> Yo = make_cvec(yold ? yold : r, n, p, q);
+  const bool relax = omega != T(1);
+  auto rlx = [&](T x, const T *o, int len) {
+    if (!relax) return x;
+    const T old = (yold && ln < len) ? o[ln] : T(0);
+    return yold ? fma(omega, x - old, old) : omega * x;
+  };
+  T ru = 0, rz = 0, rl = 0, rv = 0, rm = 0, v = 0;
+  if (j < n) {
+    ru = dw_load(R.u + (long long)j * p, p, ln);
+    rz = dw_load(R.z + (long long)j * q, q, ln);
+    rl = dw_load(R.l + (long long)j * p, p, ln);
+    if (cplM) ru -= dw_load(cplM + (long long)j * p, p, ln);
+  }
+  if (j >= 1) {
+    rv = dw_load(R.v + (long long)(j - 1) * p, p, ln);
+    rm = dw_load(R.m + (long long)(j - 1) * p, p, ln);
+    if (cplU) rm -= dw_load(cplU + (long long)(j - 1) * p, p, ln);
+    v = -rm;
+  }
+  if (j == n) {
+    const T m = v - rv;
+    if (ln < p) {
+      Y.v[(long long)(j - 1) * p + ln] = rlx(v, Yo.v + (long long)(j - 1) * p, p);
+      Y.m[(long long)(j - 1) * p + ln] = rlx(m, Yo.m + (long long)(j - 1) * p, p);
+    }
+    return;
+  }
+  const T *N = L.N + j * L.sN, *V = L.V + j * L.sV, *Z = L.Z + j * L.sZ, *fac = L.fac + j * L.sFac;
+  T rhs = dw_mv(N, ru, p, p, ln) + dw_mv(Z, rz, p, q, ln) - rl;
+  if (j >= 1) rhs += dw_mv(V, v, p, p, ln);
+  if (ln >= p) rhs = T(0);
+  const T l = dw_chol_solve(fac, rhs, p, ln);
+  const T u = ru - dw_mtv(N, l, p, p, ln);
+  const T z = rz - dw_mtv(Z, l, p, q, ln);
+  if (ln < p) {
+    Y.u[(long long)j * p + ln] = rlx(u, Yo.u + (long long)j * p, p);
+    Y.l[(long long)j * p + ln] = rlx(l, Yo.l + (long long)j * p, p);
+  }
+  if (ln < q) Y.z[(long long)j * q + ln] = rlx(z, Yo.z + (long long)j * q, q);
+  if (j >= 1) {
+    const T m = v - rv + dw_mtv(V, l, p, p, ln);
+    if (ln < p) {
+      Y.v[(long long)(j - 1) * p + ln] = rlx(v, Yo.v + (long long)(j - 1) * p, p);
+      Y.m[(long long)(j - 1) * p + ln] = rlx(m, Yo.m + (long long)(j - 1) * p, p);
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const T *__restrict__ r,
                                                            const T *cplU, const T *cplM, T *out,
@@ -917,6 +979,79 @@ __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__
       T d = xu[i] - xv[i];
       O.m[(long long)t * p + i] = b ? fma(sgn, d, B.m[(long long)t * p + i]) : d;
     }
+}
+
+// out = b - A~ x (b non-null) or A~ x on the rows of blocks [j0, j1), dense
+// blocks up to 32: one warp per step (as k_apply_dense's rows)
+template <typename T>
+__global__ void __launch_bounds__(128) k_apply_dw(LevelView<T> L, const T *__restrict__ x, const T *__restrict__ b,
+                                                  T *out, const int *guard = nullptr, int j0 = 0, int j1 = -1) {
+  if (guard && *guard == 0) return;
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int n = L.n, p = L.p, q = L.q;
+  const int t = max(j0 - 1, 0) + (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int tend = j1 < 0 ? n : min(j1, n);
+  if (t >= tend) return;
+  const bool own_uzl = t >= j0, own_vm = t + 1 >= j0 && (j1 < 0 || t + 1 < j1);
+  Vec<const T> X = make_cvec(x, n, p, q);
+  Vec<T> O = make_vec(out, n, p, q);
+  Vec<const T> B = make_cvec(b ? b : x, n, p, q);
+  const T *N = L.N + t * L.sN, *Z = L.Z + t * L.sZ;
+  const T xu = dw_load(X.u + (long long)t * p, p, ln), xv = dw_load(X.v + (long long)t * p, p, ln);
+  const T xz = dw_load(X.z + (long long)t * q, q, ln), xl = dw_load(X.l + (long long)t * p, p, ln);
+  const T xm = dw_load(X.m + (long long)t * p, p, ln);
+  auto put = [&](T *dst, const T *bsrc, T row, int len) {
+    if (ln < len) dst[ln] = b ? bsrc[ln] - row : row;
+  };
+  const T ru = xu + xm + dw_mtv(N, xl, p, p, ln);
+  T rv = xv - xm;
+  if (t + 1 < n) rv += dw_mtv(L.V + (t + 1) * L.sV, dw_load(X.l + (long long)(t + 1) * p, p, ln), p, p, ln);
+  const T rz = xz + dw_mtv(Z, xl, p, q, ln);
+  T rl = dw_mv(N, xu, p, p, ln) + dw_mv(Z, xz, p, q, ln);
+  if (t >= 1) rl += dw_mv(L.V + t * L.sV, dw_load(X.v + (long long)(t - 1) * p, p, ln), p, p, ln);
+  const T rmu = xu - xv;
+  if (own_uzl) {
+    put(O.u + (long long)t * p, B.u + (long long)t * p, ru, p);
+    put(O.z + (long long)t * q, B.z + (long long)t * q, rz, q);
+    put(O.l + (long long)t * p, B.l + (long long)t * p, rl, p);
+  }
+  if (own_vm) {
+    put(O.v + (long long)t * p, B.v + (long long)t * p, rv, p);
+    put(O.m + (long long)t * p, B.m + (long long)t * p, rmu, p);
+  }
+}
+
+// residual restricted by the variable formulas (as k_residual_restrict_dense), dense blocks up to 32:
+// one warp per coarse step
+template <typename T>
+__global__ void __launch_bounds__(128) k_residual_restrict_dw(LevelView<T> L, const T *__restrict__ y,
+                                                              const T *__restrict__ b, T *rc) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int K = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int n = L.n, p = L.p, q = L.q, nc = n / 2;
+  if (K >= nc) return;
+  const int t0 = 2 * K, t1 = 2 * K + 1;
+  Vec<const T> Y = make_cvec(y, n, p, q);
+  Vec<const T> B = make_cvec(b, n, p, q);
+  Vec<T> R = make_vec(rc, nc, p, q);
+  const T *N0 = L.N + t0 * L.sN, *Z0 = L.Z + t0 * L.sZ, *Z1 = L.Z + t1 * L.sZ;
+  const T yu = dw_load(Y.u + (long long)t0 * p, p, ln), yv = dw_load(Y.v + (long long)t0 * p, p, ln);
+  const T yz = dw_load(Y.z + (long long)t0 * q, q, ln), yl = dw_load(Y.l + (long long)t0 * p, p, ln);
+  const T ym = dw_load(Y.m + (long long)t0 * p, p, ln);
+  const T yl1 = dw_load(Y.l + (long long)t1 * p, p, ln), yz1 = dw_load(Y.z + (long long)t1 * q, q, ln);
+  const T ru = yu + ym + dw_mtv(N0, yl, p, p, ln);
+  T rl = dw_mv(N0, yu, p, p, ln) + dw_mv(Z0, yz, p, q, ln);
+  if (t0 >= 1) rl += dw_mv(L.V + t0 * L.sV, dw_load(Y.v + (long long)(t0 - 1) * p, p, ln), p, p, ln);
+  const T rz0 = yz + dw_mtv(Z0, yl, p, q, ln), rz1 = yz1 + dw_mtv(Z1, yl1, p, q, ln);
+  const T rv = yv - ym + dw_mtv(L.V + t1 * L.sV, yl1, p, p, ln);
+  if (ln < p) {
+    R.u[(long long)K * p + ln] = B.u[(long long)t0 * p + ln] - ru;
+    R.m[(long long)K * p + ln] = B.m[(long long)t0 * p + ln] - (yu - yv);
+    R.l[(long long)K * p + ln] = B.l[(long long)t0 * p + ln] - rl;
+    R.v[(long long)K * p + ln] = B.v[(long long)t0 * p + ln] - rv;
+  }
+  if (ln < q)
+    R.z[(long long)K * q + ln] = T(0.5) * ((B.z[(long long)t0 * q + ln] - rz0) + (B.z[(long long)t1 * q + ln] - rz1));
 }
 
 // ---------------------------------------------------------------------------

@@ -52,6 +52,7 @@ STREAM_RHS = 2
 STREAM_MODES = 3
 STREAM_AMPL = 4
 STREAM_NET_INIT = 5
+STREAM_COUPLING = 6
 
 
 def _mix64(z):
@@ -228,6 +229,38 @@ class BurgersFE:
         return u0
 
 
+@dataclasses.dataclass
+class CoupledCubic:
+    """A dense test model (no counterpart in the paper's Sec. 6; it exercises the
+    dense block layout): u' = A u - 0.1 u^3 + B z with seeded A = -I + G / (2 sqrt p),
+    B = H / sqrt q (G, H standard normal, stream 6), M = I; d_u f = A - 0.3 diag(u^2)
+    is dense and d_z f = B is constant, so the control is separable."""
+    p: int
+    q: int
+    seed: int
+    kind: str = "dense"
+
+    def __post_init__(self):
+        g = normal(self.seed, STREAM_COUPLING, self.p * self.p + self.p * self.q)
+        self.A = -np.eye(self.p) + g[:self.p * self.p].reshape(self.p, self.p) / (2.0 * math.sqrt(self.p))
+        self.B = g[self.p * self.p:].reshape(self.p, self.q) / math.sqrt(self.q)
+
+    def f(self, u, z):
+        return self.A @ u - 0.1 * u ** 3 + self.B @ z
+
+    def dfdu(self, u, z):
+        return self.A - 0.3 * np.diag(u ** 2)
+
+    def dfdz(self, u, z):
+        return self.B.copy()
+
+    def mass(self):
+        return np.eye(self.p)
+
+    def initial_state(self, seed):
+        return normal(seed, STREAM_MODES, self.p)
+
+
 # --------------------------------------------------------------------------
 # problem instance
 
@@ -337,6 +370,20 @@ def vdp_paper(n: int = 64, seed: int = 1, gamma: float = 100.0) -> Problem:
     m = VanDerPol(mu=0.1, q=2, T=8.0)
     return make_problem(m, n=n, theta=0.5, gamma=gamma, seed=seed, z_sigma=0.0,
                         u_init=np.array(m.u_init))
+
+
+def coupled(p: int = 12, q: int = 6, n: int = 64, seed: int = 7000, gamma: float = 100.0) -> Problem:
+    """The dense test model CoupledCubic, theta = 0.5, z ~ N(0, 0.1^2) per step and control."""
+    return make_problem(CoupledCubic(p=p, q=q, seed=seed), n=n, theta=0.5, gamma=gamma, seed=seed, z_sigma=0.1)
+
+
+def dense_copy(prob: Problem) -> Problem:
+    """The same problem with every block stored dense (a tridiagonal problem in the dense layout)."""
+    if prob.kind == "dense":
+        return prob
+    dense = lambda arr: np.array([band_to_dense(a) for a in arr])
+    return dataclasses.replace(prob, kind="dense", M=band_to_dense(prob.M), Ju_cur=dense(prob.Ju_cur),
+                               Ju_prev=dense(prob.Ju_prev), Jz_cur=dense(prob.Jz_cur), Jz_prev=dense(prob.Jz_prev))
 
 
 def burgers(nx: int = 128, n: int = 1024, nu: float = 0.01, seed: int = 2000,

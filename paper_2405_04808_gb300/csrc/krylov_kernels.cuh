@@ -372,14 +372,19 @@ __global__ void k_add_inplace(double *y, const double *__restrict__ x, int m, co
 
 // y = x * s[0]; with idx non-null the destination is y + (idx[0] + shift) * len
 // (a basis slot chosen on the device); guard non-null and 0 skips the work.
+// also (optional): a second destination of the same values (the next iteration's
+// preconditioner input, saving its copy from the basis)
 __global__ void k_scale(double *y, const double *__restrict__ x, const double *__restrict__ s, long long len,
-                        const int *idx = nullptr, int shift = 0, const int *guard = nullptr) {
+                        const int *idx = nullptr, int shift = 0, const int *guard = nullptr, double *also = nullptr) {
   if (guard && *guard == 0) return;
   if (idx) y += (long long)(idx[0] + shift) * len;
   const double a = s[0];
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
-       idx += (long long)gridDim.x * blockDim.x)
-    y[idx] = x[idx] * a;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double v = x[idx] * a;
+    y[idx] = v;
+    if (also) also[idx] = v;
+  }
 }
 
 // scal[0] = sqrt(nrm2[0]); scal[1] = 1 / scal[0] (0 if zero)

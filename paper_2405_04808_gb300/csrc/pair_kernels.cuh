@@ -89,13 +89,20 @@ __device__ __forceinline__ void ds_add(float &s, float &c, float s2, float c2) {
 // dst[i] = split48(src[i] * mul) (mul = 1/||w|| for a new basis vector, or
 // read from the device); the basis slot may be chosen on the device
 // (dst + idx[0] * len)
+// also (optional): the stored pair's FP64 value (what k_join_basis would read back), for the next
+// iteration's preconditioner input
 __global__ void k_split_basis(float2 *dst, const double *__restrict__ src, const double *mul, long long len,
-                              const int *idx = nullptr, int idx_add = 0, const int *gate = nullptr) {
+                              const int *idx = nullptr, int idx_add = 0, const int *gate = nullptr,
+                              double *also = nullptr) {
   if (gate && *gate == 0) return;
   const double a = mul ? *mul : 1.0;
   if (idx) dst += (long long)(idx[0] + idx_add) * len;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
-    dst[i] = split48(src[i] * a, 896);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = split48(src[i] * a, 896);
+    dst[i] = v;
+    if (also) also[i] = pair_value(v, 1.0);
+  }
 }
 
 // dst[i] = hi + lo of basis slot idx[0] (or of src itself when idx is null), in FP64

@@ -167,6 +167,7 @@ struct mg_handle {
   int persist_sweeps = 0;  // smoothing levels that fit on the GPU run all their sweeps in one launch
                            // (off by default: no faster than one launch per sweep in a captured solve)
   int sweep_stall = 0;     // failure-detection tests: the multi-sweep kernel's block 0 publishes nothing
+  int fuse_copies = 1;     // captured solves: the preconditioner input and Z_j copies ride on other kernels
   int fuse_reduce = 1;     // Krylov reductions and the Arnoldi column in the last CTA of their kernels:
                            // 0 never, 1 the Arnoldi column and dot products of <= 16 vectors, 2 always
   unsigned *ticket = nullptr;  // [0] multi-dot, [1] second axpy: CTAs finished (reset by the last one)
@@ -390,7 +391,7 @@ void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, con
 
 template <typename T, typename CT = T>
 void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *b, T *out, cudaStream_t s,
-                  int j0 = 0, int j1 = -1) {
+                  int j0 = 0, int j1 = -1, T *xcopy = nullptr, const int *xidx = nullptr, int xshift = 0) {
   // rows of blocks [j0, j1) (all: j1 < 0): a warp (thread) per step from max(j0 - 1, 0)
   const int steps = (j1 < 0 ? L.n : std::min(j1, L.n)) - std::max(j0 - 1, 0);
   if (steps <= 0) return;
@@ -402,18 +403,18 @@ void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *
   if (L.layout == MG_LAYOUT_DENSE) {
     if constexpr (std::is_same<T, CT>::value) {
       if (L.p > kDenseMax || L.q > kDenseMax)
-        k_apply_dw<T><<<(steps + 3) / 4, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1);
+        k_apply_dw<T><<<(steps + 3) / 4, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift);
       else
-        k_apply_dense<T><<<grid_for(steps, 128, 1 << 30), 128, 0, s>>>(L, x, b, out, nullptr, j0, j1);
+        k_apply_dense<T><<<grid_for(steps, 128, 1 << 30), 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift);
     }
   } else {
     const int blocks = (steps + 3) / 4;
     switch (h->C) {
-      case 1: k_apply_tri<T, 1, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
-      case 2: k_apply_tri<T, 2, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
-      case 4: k_apply_tri<T, 4, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
-      case 8: k_apply_tri<T, 8, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
-      default: k_apply_tri<T, 16, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1); break;
+      case 1: k_apply_tri<T, 1, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift); break;
+      case 2: k_apply_tri<T, 2, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift); break;
+      case 4: k_apply_tri<T, 4, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift); break;
+      case 8: k_apply_tri<T, 8, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift); break;
+      default: k_apply_tri<T, 16, CT><<<blocks, 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift); break;
     }
   }
   ck_launch();
@@ -707,7 +708,7 @@ void norm_into(mg_handle *h, mg_handle::Krylov &K, const double *x, long long le
 
 // Arnoldi step with the index j on the device (st->j, st->m1): no read-back
 void arnoldi_step_dev(mg_handle *h, mg_handle::Krylov &K, KState *st, int jmax, double *V, long long len, double *w,
-                      cudaStream_t s, float2 *Vp = nullptr) {
+                      cudaStream_t s, float2 *Vp = nullptr, double *also = nullptr) {
   if (!orthogonalise(h, K, V, len, jmax, w, s, &st->m1, Vp, true, &st->j)) {
     Bracket br(h, CAT_SMALL, s);
     k_arnoldi_step<<<1, kWarp, 0, s>>>(0, K.h, K.nrm2, K.H, h->ldh, K.cs, K.sn, K.g, K.scal, &st->j);
@@ -716,9 +717,9 @@ void arnoldi_step_dev(mg_handle *h, mg_handle::Krylov &K, KState *st, int jmax, 
   {
     Bracket br(h, CAT_AXPY, s);
     if (Vp)
-      k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, w, K.scal + 1, len, &st->j, 1);
+      k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, w, K.scal + 1, len, &st->j, 1, nullptr, also);
     else
-      k_scale<<<grid_for(len, 256), 256, 0, s>>>(V, w, K.scal + 1, len, &st->j, 1);
+      k_scale<<<grid_for(len, 256), 256, 0, s>>>(V, w, K.scal + 1, len, &st->j, 1, nullptr, also);
     ck_launch();
   }
 }
@@ -1168,9 +1169,11 @@ void coarse_solve_graph(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
     k_ctl_start<<<1, 1, 0, s>>>(st, K.scal, fixed ? -1.0 : o.coarse_rtol, hdl, h->net ? h->net_flag : nullptr);
     ck_launch();
   }
+  const bool fc = h->fuse_copies;  // the input and Z_j copies ride on the basis write and the product
   {
     Bracket br(h, CAT_AXPY, s);
-    k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->cV, h->cr, K.scal + 1, len);
+    k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->cV, h->cr, K.scal + 1, len, nullptr, 0, nullptr,
+                                                fc ? h->cvin : nullptr);
     ck_launch();
   }
   {
@@ -1181,19 +1184,19 @@ void coarse_solve_graph(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
   ck(cudaMemsetAsync(h->cy, 0, len * sizeof(double), s));
   const long long before = h->launches;
   add_while(h, s, hdl, h->cap[2], [&](cudaStream_t bs) {
-    {
+    if (!fc) {
       Bracket br(h, CAT_SMALL, bs);
       k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->cvin, h->cV, len, &st->j, 0);
       ck_launch();
     }
     sgs_fp64<T>(h, lev, h->cvin, h->czout, bs);
-    {
+    if (!fc) {
       Bracket br(h, CAT_SMALL, bs);
       k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->cZ, h->czout, len, &st->j, 1);
       ck_launch();
     }
-    launch_apply<double>(h, lev.d.view, h->czout, nullptr, h->cw, bs);
-    arnoldi_step_dev(h, K, st, limit - 1, h->cV, len, h->cw, bs);
+    launch_apply<double>(h, lev.d.view, h->czout, nullptr, h->cw, bs, 0, -1, fc ? h->cZ : nullptr, &st->j, 1);
+    arnoldi_step_dev(h, K, st, limit - 1, h->cV, len, h->cw, bs, nullptr, fc ? h->cvin : nullptr);
     {
       Bracket br(h, CAT_SMALL, bs);
       k_ctl_step<<<1, 1, 0, bs>>>(st, K.scal, limit, limit, 1, hdl);
@@ -1480,10 +1483,12 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
     }
     {
       Bracket br(h, CAT_AXPY, s);
+      // fused copies: the basis vector is also written to the preconditioner's input slot
+      double *vin_also = h->fuse_copies ? h->vin : nullptr;
       if (Vp)
-        k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, b, K.scal + 1, len);
+        k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, b, K.scal + 1, len, nullptr, 0, nullptr, vin_also);
       else
-        k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, b, K.scal + 1, len);
+        k_scale<<<grid_for(len, 256), 256, 0, s>>>(h->fV, b, K.scal + 1, len, nullptr, 0, nullptr, vin_also);
       ck_launch();
     }
     {
@@ -1495,7 +1500,8 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
     h->launches = 0;
     long long n_coarse = 0;
     add_while(h, s, hdl, h->cap[1], [&](cudaStream_t bs) {
-      {
+      const bool fc = h->fuse_copies;  // the input and Z_j copies ride on the basis write and the product
+      if (!fc) {
         Bracket br(h, CAT_SMALL, bs);
         if (Vp)
           k_join_basis<<<grid_for(len, 256), 256, 0, bs>>>(h->vin, Vp, len, &st->j);
@@ -1507,13 +1513,14 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
       precondition(h, h->vin, h->zout, bs);
       n_coarse = h->g_coarse;
       (void)before;
-      {
+      if (!fc) {
         Bracket br(h, CAT_SMALL, bs);
         k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->fZ, h->zout, len, &st->j, 1);
         ck_launch();
       }
-      launch_apply<double>(h, h->lv[0].d.view, h->zout, nullptr, h->fw, bs);
-      arnoldi_step_dev(h, K, st, m - 1, h->fV, len, h->fw, bs, Vp);
+      launch_apply<double>(h, h->lv[0].d.view, h->zout, nullptr, h->fw, bs, 0, -1, fc ? h->fZ : nullptr, &st->j,
+                           1);
+      arnoldi_step_dev(h, K, st, m - 1, h->fV, len, h->fw, bs, Vp, fc ? h->vin : nullptr);
       {
         Bracket br(h, CAT_SMALL, bs);
         k_ctl_step<<<1, 1, 0, bs>>>(st, K.scal, m, maxit, 0, hdl);
@@ -1555,9 +1562,11 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
       {
         Bracket br(h, CAT_AXPY, bs);
         if (Vp)
-          k_split_basis<<<grid_for(len, 256), 256, 0, bs>>>(Vp, h->fr, K.scal + 1, len, nullptr, 0, &st->restart);
+          k_split_basis<<<grid_for(len, 256), 256, 0, bs>>>(Vp, h->fr, K.scal + 1, len, nullptr, 0, &st->restart,
+                                                            h->fuse_copies ? h->vin : nullptr);
         else
-          k_scale<<<grid_for(len, 256), 256, 0, bs>>>(h->fV, h->fr, K.scal + 1, len, nullptr, 0, &st->restart);
+          k_scale<<<grid_for(len, 256), 256, 0, bs>>>(h->fV, h->fr, K.scal + 1, len, nullptr, 0, &st->restart,
+                                                      h->fuse_copies ? h->vin : nullptr);
         ck_launch();
       }
       {
@@ -1874,6 +1883,8 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
   // PINTMG_TRI_PAIR=0 keeps one warp per block on every level (tests)
   if (const char *e = std::getenv("PINTMG_TRI_PAIR")) h->pair_tri = std::atoi(e) != 0;
+  // PINTMG_FUSE_COPIES=0: captured solves copy the preconditioner's input and output in kernels of their own
+  if (const char *e = std::getenv("PINTMG_FUSE_COPIES")) h->fuse_copies = std::atoi(e) != 0;
   // PINTMG_FUSE_REDUCE=0 reduces dot products and forms the Arnoldi column in separate launches,
   // 2 fuses every dot product's reduction (tests, measurements); 1 is the default
   if (const char *e = std::getenv("PINTMG_FUSE_REDUCE")) h->fuse_reduce = std::min(2, std::max(0, std::atoi(e)));

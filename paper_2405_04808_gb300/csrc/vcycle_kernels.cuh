@@ -844,10 +844,18 @@ __global__ void __launch_bounds__(128) k_block_solve_dense(LevelView<T> L, const
 //   mu_t:     u_t - v_t
 
 // out = b - A~ x  (b non-null)  or  out = A~ x  (b null), all five types.
+// xcopy (optional, whole level only): x is also stored into basis slot
+// xcopy + (xcopy_idx[0] + xcopy_shift) * n (4p + q), each step by its warp
+template <typename T>
+__device__ __forceinline__ T *copy_slot(T *xcopy, const int *xcopy_idx, int xcopy_shift, int n, int p, int q) {
+  return xcopy ? xcopy + (long long)(xcopy_idx[0] + xcopy_shift) * ((long long)n * (4 * p + q)) : nullptr;
+}
+
 template <typename T, int C, typename CT = T>
 __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *__restrict__ x,
                                                    const T *__restrict__ b, T *out, const int *guard = nullptr,
-                                                   int j0 = 0, int j1 = -1) {
+                                                   int j0 = 0, int j1 = -1, T *xcopy = nullptr,
+                                                   const int *xcopy_idx = nullptr, int xcopy_shift = 0) {
   if (guard && *guard == 0) return;
   const int ln = threadIdx.x & (kWarp - 1);
   const int n = L.n, p = L.p, q = L.q;
@@ -866,6 +874,14 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
   chunk_load<T, C>(xz, X.z + (long long)t * q, q, ln);
   chunk_load<T, C>(xl, X.l + (long long)t * p, p, ln);
   chunk_load<T, C>(xm, X.m + (long long)t * p, p, ln);
+  if (T *cp = copy_slot(xcopy, xcopy_idx, xcopy_shift, n, p, q)) {
+    Vec<T> Cv = make_vec(cp, n, p, q);
+    chunk_store<T, C>(Cv.u + (long long)t * p, xu, p, ln);
+    chunk_store<T, C>(Cv.v + (long long)t * p, xv, p, ln);
+    chunk_store<T, C>(Cv.z + (long long)t * q, xz, q, ln);
+    chunk_store<T, C>(Cv.l + (long long)t * p, xl, p, ln);
+    chunk_store<T, C>(Cv.m + (long long)t * p, xm, p, ln);
+  }
   const T sgn = b ? T(-1) : T(1);
   Vec<const T> B = make_cvec(b ? b : x, n, p, q);
   // u row
@@ -933,7 +949,8 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
 template <typename T>
 __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__restrict__ x,
                                                      const T *__restrict__ b, T *out, const int *guard = nullptr,
-                                                     int j0 = 0, int j1 = -1) {
+                                                     int j0 = 0, int j1 = -1, T *xcopy = nullptr,
+                                                     const int *xcopy_idx = nullptr, int xcopy_shift = 0) {
   if (guard && *guard == 0) return;
   const int n = L.n, p = L.p, q = L.q;
   const int t = max(j0 - 1, 0) + blockIdx.x * blockDim.x + threadIdx.x;  // as k_apply_tri
@@ -947,6 +964,16 @@ __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__
   const T sgn = b ? T(-1) : T(1);
   const T *xu = X.u + (long long)t * p, *xv = X.v + (long long)t * p, *xz = X.z + (long long)t * q;
   const T *xl = X.l + (long long)t * p, *xm = X.m + (long long)t * p;
+  if (T *cp = copy_slot(xcopy, xcopy_idx, xcopy_shift, n, p, q)) {
+    Vec<T> Cv = make_vec(cp, n, p, q);
+    for (int i = 0; i < p; ++i) {
+      Cv.u[(long long)t * p + i] = xu[i];
+      Cv.v[(long long)t * p + i] = xv[i];
+      Cv.l[(long long)t * p + i] = xl[i];
+      Cv.m[(long long)t * p + i] = xm[i];
+    }
+    for (int i = 0; i < q; ++i) Cv.z[(long long)t * q + i] = xz[i];
+  }
   T acc[kDenseMax];
   // u row
   for (int i = 0; i < p; ++i) acc[i] = xu[i] + xm[i];
@@ -985,7 +1012,9 @@ __global__ void __launch_bounds__(128) k_apply_dense(LevelView<T> L, const T *__
 // blocks up to 32: one warp per step (as k_apply_dense's rows)
 template <typename T>
 __global__ void __launch_bounds__(128) k_apply_dw(LevelView<T> L, const T *__restrict__ x, const T *__restrict__ b,
-                                                  T *out, const int *guard = nullptr, int j0 = 0, int j1 = -1) {
+                                                  T *out, const int *guard = nullptr, int j0 = 0, int j1 = -1,
+                                                  T *xcopy = nullptr, const int *xcopy_idx = nullptr,
+                                                  int xcopy_shift = 0) {
   if (guard && *guard == 0) return;
   const int ln = threadIdx.x & (kWarp - 1);
   const int n = L.n, p = L.p, q = L.q;
@@ -1000,6 +1029,16 @@ __global__ void __launch_bounds__(128) k_apply_dw(LevelView<T> L, const T *__res
   const T xu = dw_load(X.u + (long long)t * p, p, ln), xv = dw_load(X.v + (long long)t * p, p, ln);
   const T xz = dw_load(X.z + (long long)t * q, q, ln), xl = dw_load(X.l + (long long)t * p, p, ln);
   const T xm = dw_load(X.m + (long long)t * p, p, ln);
+  if (T *cp = copy_slot(xcopy, xcopy_idx, xcopy_shift, n, p, q)) {
+    Vec<T> Cv = make_vec(cp, n, p, q);
+    if (ln < p) {
+      Cv.u[(long long)t * p + ln] = xu;
+      Cv.v[(long long)t * p + ln] = xv;
+      Cv.l[(long long)t * p + ln] = xl;
+      Cv.m[(long long)t * p + ln] = xm;
+    }
+    if (ln < q) Cv.z[(long long)t * q + ln] = xz;
+  }
   auto put = [&](T *dst, const T *bsrc, T row, int len) {
     if (ln < len) dst[ln] = b ? bsrc[ln] - row : row;
   };

@@ -61,3 +61,35 @@ def test_fused_reductions_are_bitwise_neutral(P, monkeypatch, basis, loops, case
         assert l0 - l1 >= saved_per_step * steps, (l0, l1, steps)
     xd = O.direct_solve(prob)
     assert np.linalg.norm(x1 - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("basis", ["fp64", "pair"])
+def test_fused_copies_in_captured_solves(P, monkeypatch, basis):
+    """In a captured solve the basis write also fills the preconditioner's input and the operator product
+    also stores the preconditioned vector Z_j (two copy launches fewer per FGMRES and coarse GMRES
+    iteration): bitwise the same solve, across a restart."""
+    prob = W.burgers(nx=40, n=32, seed=403)
+    opts = dict(levels=2, nu_pre=2, nu_post=2, omega=2.0 / 3.0, restrict="transpose", krylov_basis=basis,
+                device_loops=True)
+    res = {}
+    for fc in ("1", "0"):
+        monkeypatch.setenv("PINTMG_FUSE_COPIES", fc)
+        h = P.mg_setup(prob, **opts)
+        monkeypatch.delenv("PINTMG_FUSE_COPIES")
+        try:
+            b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+            runs = []
+            for _ in range(2):  # the second launch of the cached graph too
+                x = torch.empty_like(b)
+                n0 = P.mg_launch_count(h)
+                code, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, 200, 6)
+                assert code == P.MG_OK, P.mg_status_string(code)
+                runs.append((x.cpu().numpy(), info.iters, info.coarse_iters, P.mg_launch_count(h) - n0))
+            res[fc] = runs
+        finally:
+            P.mg_destroy(h)
+    for k in range(2):
+        x1, it1, c1, l1 = res["1"][k]
+        x0, it0, c0, l0 = res["0"][k]
+        assert (it1, c1) == (it0, c0) and np.array_equal(x1, x0)
+        assert l0 - l1 == 2 * (it1 + c1), (l0, l1, it1, c1)

@@ -1195,7 +1195,7 @@ void coarse_solve_graph(mg_handle *h, const T *r_in, T *y_out, cudaStream_t s) {
       k_copy_indexed<<<grid_for(len, 256), 256, 0, bs>>>(h->cZ, h->czout, len, &st->j, 1);
       ck_launch();
     }
-    launch_apply<double>(h, lev.d.view, h->czout, nullptr, h->cw, bs, 0, -1, fc ? h->cZ : nullptr, &st->j, 1);
+    launch_apply<double>(h, lev.d.view, h->czout, nullptr, h->cw, bs, 0, -1, fc ? h->cZ : nullptr, &st->j, 0);
     arnoldi_step_dev(h, K, st, limit - 1, h->cV, len, h->cw, bs, nullptr, fc ? h->cvin : nullptr);
     {
       Bracket br(h, CAT_SMALL, bs);
@@ -1519,7 +1519,7 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
         ck_launch();
       }
       launch_apply<double>(h, h->lv[0].d.view, h->zout, nullptr, h->fw, bs, 0, -1, fc ? h->fZ : nullptr, &st->j,
-                           1);
+                           0);
       arnoldi_step_dev(h, K, st, m - 1, h->fV, len, h->fw, bs, Vp, fc ? h->vin : nullptr);
       {
         Bracket br(h, CAT_SMALL, bs);

@@ -336,6 +336,9 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
                 ev[i][1].record()
             torch.cuda.synchronize(dev)
         launches = P.mg_launch_count(h) - launches0
+        gl = P.mg_graph_launches(h)
+        graph_launches = (None if gl[0] != P.MG_OK else
+                          {"fixed": gl[1], "per_fgmres_iteration": gl[2], "per_coarse_iteration": gl[3]})
         if world > 1:
             torch.distributed.barrier()
         local_ms = sum(a.elapsed_time(bb) for a, bb in ev)
@@ -344,7 +347,8 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
         out = {"value": value, "ms_per_step": total_ms / steps, "x": x.clone(),
                "iters": [i.iters for i in infos], "true_relres": max(i.true_relres for i in infos),
                "coarse_iters_per_vcycle": sum(i.coarse_iters for i in infos) / max(1, sum(i.vcycles for i in infos)),
-               "setup_ms": setup_ms, "launches": launches, "shares": shares, "dominant": dominant,
+               "setup_ms": setup_ms, "launches": launches, "graph_launches": graph_launches,
+               "shares": shares, "dominant": dominant,
                "roofline": roofline(shares, dominant, precision, workload if levels is None else None),
                "category_rooflines": {k: roofline(shares, k, precision, workload if levels is None else None)
                                       for k in shares if shares[k][1] and shares[k][2] > 0},
@@ -448,7 +452,8 @@ def measure_paper_behaviour(P, torch, prob, wl, args, dev, stream, world, varian
            "fgmres_iters": m["iters"], "true_relres": m["true_relres"], "error_vs_oracle": m["error_vs_oracle"],
            "oracle_iters": oracle_iterations(args.workload, pb["omega"], pb["restart"], pb["restrict"]),
            "coarse_iters_per_vcycle": round(m["coarse_iters_per_vcycle"], 3), "setup_ms": round(m["setup_ms"], 2),
-           "e2e": m["e2e"], "gpu_launches": m["launches"], "roofline": m["roofline"],
+           "e2e": m["e2e"], "gpu_launches": m["launches"], "graph_launches": m["graph_launches"],
+           "roofline": m["roofline"],
            "category_rooflines": {k: {"bound": v["bound"], "frac": v.get("frac"), "achieved": v.get("achieved"),
                                       "unit": v.get("unit"), "avg_launch_us": v.get("avg_launch_us")}
                                   for k, v in m["category_rooflines"].items()},
@@ -704,6 +709,7 @@ def run_native(args):
         "setup_ms": round(main["setup_ms"], 2),
         "e2e": main["e2e"],
         "gpu_launches": main["launches"],
+        "graph_launches": main["graph_launches"],
         "autotune": main["autotune"],
         "roofline": main["roofline"],
         "category_rooflines": {k: {"bound": v["bound"], "frac": v.get("frac"), "achieved": v.get("achieved"),

@@ -249,6 +249,19 @@ long long mg_vector_length(const mg_handle *h);
 long long mg_launch_count(const mg_handle *h);
 
 /*
+ * Kernel launches of the handle's captured single-system solve graph
+ * (options.device_loops), as recorded when the graph was last built by
+ * fgmres_solve: *fixed = the launches outside the loops (start and final
+ * residual), *per_iter = one pass of the FGMRES WHILE body (preconditioner,
+ * operator product, Gram-Schmidt, step control, guarded restart block),
+ * counting the coarse-grid GMRES loop inside each V-cycle as absent, and
+ * *per_coarse_iter = one pass of the coarse GMRES WHILE body.  Any output
+ * pointer may be NULL.  Returns MG_OK, or MG_ERR_ARG when h is NULL or no
+ * graph has been built yet (all outputs then set to 0).
+ */
+int mg_graph_launches(const mg_handle *h, long long *fixed, long long *per_iter, long long *per_coarse_iter);
+
+/*
  * Arithmetic-rate probe (measurement support, no counterpart in the paper):
  * launches `blocks` CTAs of 256 threads on `stream`, each thread running 8
  * independent fused multiply-add chains of `iters` steps in FP64

@@ -1743,6 +1743,14 @@ long long mg_vector_length(const mg_handle *h) { return h ? h->lv[0].len : 0; }
 
 long long mg_launch_count(const mg_handle *h) { return h ? h->launches : 0; }
 
+int mg_graph_launches(const mg_handle *h, long long *fixed, long long *per_iter, long long *per_coarse_iter) {
+  const bool ok = h && h->graph;
+  if (fixed) *fixed = ok ? h->g_init : 0;
+  if (per_iter) *per_iter = ok ? h->g_body : 0;
+  if (per_coarse_iter) *per_coarse_iter = ok ? h->g_coarse : 0;
+  return ok ? MG_OK : MG_ERR_ARG;
+}
+
 int mg_probe_fma(int precision, int blocks, int iters, void *sink, void *stream) {
   if (blocks < 1 || blocks > (1 << 20) || iters < 1 || !sink) return MG_ERR_ARG;
   if (precision != MG_PRECISION_FP64 && precision != MG_PRECISION_FP32) return MG_ERR_ARG;

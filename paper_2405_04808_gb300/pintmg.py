@@ -42,7 +42,7 @@ RESTRICT = {"inject": 0, "transpose": 1}
 #: every symbol include/pintmg.h declares
 EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmres_solve_batched",
             "mg_vector_length",
-            "mg_launch_count", "mg_probe_fma", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
+            "mg_launch_count", "mg_graph_launches", "mg_probe_fma", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
             "mg_level_info", "mg_range_sweep", "mg_range_residual", "mg_range_restrict", "mg_range_prolong",
             "mg_coarse_solve",
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
@@ -109,6 +109,8 @@ def lib():
         L.mg_vector_length.restype = ctypes.c_longlong
         L.mg_launch_count.argtypes = [ctypes.c_void_p]
         L.mg_launch_count.restype = ctypes.c_longlong
+        L.mg_graph_launches.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_longlong)] * 3
+        L.mg_graph_launches.restype = ctypes.c_int
         L.mg_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.mg_profile_enable.restype = ctypes.c_int
         L.mg_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -234,6 +236,14 @@ def mg_vector_length(h) -> int:
 
 def mg_launch_count(h) -> int:
     return int(lib().mg_launch_count(ctypes.c_void_p(h)))
+
+
+def mg_graph_launches(h):
+    """(status, fixed, per FGMRES iteration, per coarse GMRES iteration) kernel launches of the
+    handle's captured solve graph."""
+    out = [ctypes.c_longlong(0) for _ in range(3)]
+    code = lib().mg_graph_launches(ctypes.c_void_p(h), *[ctypes.byref(o) for o in out])
+    return (int(code),) + tuple(int(o.value) for o in out)
 
 
 PROFILE_ALL = 0xFFFF

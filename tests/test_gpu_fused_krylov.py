@@ -71,7 +71,7 @@ def test_fused_copies_in_captured_solves(P, monkeypatch, basis):
     prob = W.burgers(nx=40, n=32, seed=403)
     opts = dict(levels=2, nu_pre=2, nu_post=2, omega=2.0 / 3.0, restrict="transpose", krylov_basis=basis,
                 device_loops=True)
-    res = {}
+    res, graph = {}, {}
     for fc in ("1", "0"):
         monkeypatch.setenv("PINTMG_FUSE_COPIES", fc)
         h = P.mg_setup(prob, **opts)
@@ -86,6 +86,7 @@ def test_fused_copies_in_captured_solves(P, monkeypatch, basis):
                 assert code == P.MG_OK, P.mg_status_string(code)
                 runs.append((x.cpu().numpy(), info.iters, info.coarse_iters, P.mg_launch_count(h) - n0))
             res[fc] = runs
+            graph[fc] = P.mg_graph_launches(h)
         finally:
             P.mg_destroy(h)
     for k in range(2):
@@ -93,3 +94,8 @@ def test_fused_copies_in_captured_solves(P, monkeypatch, basis):
         x0, it0, c0, l0 = res["0"][k]
         assert (it1, c1) == (it0, c0) and np.array_equal(x1, x0)
         assert l0 - l1 == 2 * (it1 + c1), (l0, l1, it1, c1)
+    # the graph's own record: two launches fewer in each loop body, the same fixed part
+    (s1, f1, b1, k1), (s0, f0, b0, k0) = graph["1"], graph["0"]
+    assert s1 == s0 == P.MG_OK and f1 == f0 and b0 - b1 == 2 and k0 - k1 == 2 and b1 > 0 and k1 > 0
+    for k in range(2):
+        assert res["1"][k][3] == f1 + b1 * res["1"][k][1] + k1 * res["1"][k][2]

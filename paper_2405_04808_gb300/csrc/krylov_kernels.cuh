@@ -82,6 +82,39 @@ __device__ __forceinline__ bool last_cta(unsigned *ticket) {
   return s_last != 0;
 }
 
+// Sums over the 32 lanes of VB accumulators (VB = 2^b, b <= 5) as a
+// reduce-scatter: in round r (partner lane ln ^ (16 >> r)) a lane keeps half
+// of the values it still carries, the half picked by lane bit 4 - r, and adds
+// the partner's copy of that half; after b rounds it carries one value, which
+// the remaining rounds add up in full.  Every total follows the butterfly of a
+// shuffle-down tree (leaves paired by lane bits 4, 3, 2, 1, 0 in that order,
+// operands of an addition possibly swapped), so the totals are bitwise those
+// of one such tree per accumulator, for every VB; a lane adds VB - 1 + 5 - b
+// values instead of 5 VB (the FP64 adds compete with the dot products' FMAs
+// for GB300's FP64 pipe).  Returns the total of accumulator ln / (32 / VB),
+// held by every lane with those top b bits.
+template <int VB>
+__device__ __forceinline__ double warp_sum_scatter(const double (&acc)[VB], int ln) {
+  static_assert(VB >= 1 && VB <= 32 && (VB & (VB - 1)) == 0, "VB must be a power of two up to 32");
+  double cur[VB];
+#pragma unroll
+  for (int v = 0; v < VB; ++v) cur[v] = acc[v];
+  int o = kWarp / 2;
+#pragma unroll
+  for (int n = VB; n > 1; n >>= 1, o >>= 1) {
+    const bool upper = (ln & o) != 0;  // this round's lane bit: keep the upper half
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const double keep = upper ? cur[n / 2 + i] : cur[i];
+      const double send = upper ? cur[i] : cur[n / 2 + i];
+      cur[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  double x = cur[0];
+  for (; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
 // partial[i * G + g] = sum over chunk g of V_i . w for i < m, VB vectors per
 // work item, G = dot_parts(m, VB, len); a persistent grid walks the items.  kPair:
 // two consecutive entries per thread and step (16-byte loads; needs len and
@@ -132,15 +165,10 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *
           if (v < nv) acc[v] = fma(V[(long long)(vb + v) * ldv + idx], wv, acc[v]);
       }
     }
-#pragma unroll
-    for (int v = 0; v < VB; ++v) {
-      double x = acc[v];
-      if (v < nv) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
-      }
-      if (ln == 0) red[wp][v] = x;
-    }
+    // warp sums of the VB accumulators by a reduce-scatter: lane ln ends with
+    // the sum of accumulator ln / (32 / VB) (the unused accumulators are 0)
+    const double x = warp_sum_scatter<VB>(acc, ln);
+    if ((ln & (kWarp / VB - 1)) == 0) red[wp][ln / (kWarp / VB)] = x;
     __syncthreads();
     if (threadIdx.x < nv) {
       double sum = 0.0;

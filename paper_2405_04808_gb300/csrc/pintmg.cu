@@ -49,6 +49,42 @@ inline int grid_for(long long work, int threads, int cap = 4 * 152) {
   return (int)g;
 }
 
+// CTAs of 256 threads for a transfer kernel over nc coarse steps of w vector
+// accesses (transfer_threads(w) threads per step)
+inline int transfer_grid(int nc, int w) {
+  const int kpb = 256 / transfer_threads(w);
+  const long long g = ((long long)nc + kpb - 1) / kpb;
+  return (int)std::max(1LL, std::min(g, 1LL << 20));
+}
+
+// the transfer kernels move entry pairs (VW = 2) when p and q are even and
+// both vectors are aligned to a pair
+template <typename T>
+bool transfer_pairs(int p, int q, const void *a, const void *b) {
+  return p % 2 == 0 && q % 2 == 0 &&
+         ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) % (2 * sizeof(T))) == 0;
+}
+
+// y += P e on a level of n (even) steps from e on the next coarser one; (j0, j1) as k_prolong_add
+template <typename T>
+void launch_prolong(const T *e, T *y, int n, int p, int q, int end_rule, cudaStream_t s, int j0 = 0, int j1 = -1) {
+  if (transfer_pairs<T>(p, q, e, y))
+    k_prolong_add<T, 2><<<transfer_grid(n / 2, (4 * p + q) / 2), 256, 0, s>>>(y, e, n, p, q, end_rule, j0, j1);
+  else
+    k_prolong_add<T, 1><<<transfer_grid(n / 2, 4 * p + q), 256, 0, s>>>(y, e, n, p, q, end_rule, j0, j1);
+}
+
+// rc = P^T r; (K0, K1) as k_restrict_transpose
+template <typename T>
+void launch_restrict_transpose(const T *r, T *rc, int n, int p, int q, int end_rule, cudaStream_t s, int K0 = 0,
+                               int K1 = -1) {
+  if (transfer_pairs<T>(p, q, r, rc))
+    k_restrict_transpose<T, 2><<<transfer_grid(n / 2, (4 * p + q) / 2), 256, 0, s>>>(r, rc, n, p, q, end_rule, K0,
+                                                                                   K1);
+  else
+    k_restrict_transpose<T, 1><<<transfer_grid(n / 2, 4 * p + q), 256, 0, s>>>(r, rc, n, p, q, end_rule, K0, K1);
+}
+
 // one device allocation, freed by the handle
 struct DevMem {
   std::vector<void *> ptrs;
@@ -1325,8 +1361,7 @@ void vcycle_level(mg_handle *h, int l, const VIEW &view, const T *b, T *y_out, c
     launch_apply<T>(h, view, y, b, t, s);  // full fine residual into the free sweep buffer
     const double w = 4.0 * h->p + h->q;
     Bracket br(h, CAT_RESTRICT, s, sizeof(T) * (lev.n / 2) * w * 3.0, 0.0);
-    k_restrict_transpose<T><<<grid_for((long long)(lev.n / 2) * (long long)w, 256), 256, 0, s>>>(
-        t, dn.b, lev.n, h->p, h->q, o.end_rule);
+    launch_restrict_transpose<T>(t, dn.b, lev.n, h->p, h->q, o.end_rule, s);
     ck_launch();
   } else {
     launch_residual_restrict<T>(h, view, y, b, dn.b, s);
@@ -1334,7 +1369,7 @@ void vcycle_level(mg_handle *h, int l, const VIEW &view, const T *b, T *y_out, c
   vcycle<T>(h, l + 1, dn.b, dn.y, s);
   {
     Bracket br(h, CAT_PROLONG, s);
-    k_prolong_add<T><<<grid_for(lev.len, 256), 256, 0, s>>>(y, dn.y, lev.n, h->p, h->q, o.end_rule);
+    launch_prolong<T>(dn.y, y, lev.n, h->p, h->q, o.end_rule, s);
     ck_launch();
   }
   if (persist && o.nu_post > 0) {
@@ -2587,13 +2622,12 @@ extern "C" int mg_range_restrict(mg_handle *h, int level, int j0, int j1, const 
   if (!L || level == (int)h->lv.size() - 1 || !r || !rc || !range_ok(*L, j0, j1) || (j0 & 1)) return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int K0 = j0 / 2, K1 = (j1 + 1) / 2;
-  const long long total = (long long)(L->n / 2) * (4 * h->p + h->q);
   h->launches++;
   if (h->opts.restrict_rule == MG_RESTRICT_TRANSPOSE)
-    k_restrict_transpose<double><<<grid_for(total, 256), 256, 0, s>>>(r, rc, L->n, h->p, h->q, h->opts.end_rule,
-                                                                     K0, K1);
+    launch_restrict_transpose<double>(r, rc, L->n, h->p, h->q, h->opts.end_rule, s, K0, K1);
   else
-    k_restrict_inject<double><<<grid_for(total, 256), 256, 0, s>>>(r, rc, L->n, h->p, h->q, K0, K1);
+    k_restrict_inject<double><<<transfer_grid(L->n / 2, 4 * h->p + h->q), 256, 0, s>>>(r, rc, L->n, h->p, h->q, K0,
+                                                                                      K1);
   return range_status();
 }
 
@@ -2603,8 +2637,7 @@ extern "C" int mg_range_prolong(mg_handle *h, int level, int j0, int j1, const d
   if (!L || level == (int)h->lv.size() - 1 || !ec || !y || !range_ok(*L, j0, j1)) return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->launches++;
-  k_prolong_add<double><<<grid_for(h->lv[level].len, 256), 256, 0, s>>>(y, ec, L->n, h->p, h->q,
-                                                                        h->opts.end_rule, j0, j1);
+  launch_prolong<double>(ec, y, L->n, h->p, h->q, h->opts.end_rule, s, j0, j1);
   return range_status();
 }
 

@@ -1205,56 +1205,122 @@ __global__ void __launch_bounds__(128) k_residual_restrict_dense(LevelView<T> L,
 }
 
 // ---------------------------------------------------------------------------
-// y += P e (Sec. 5.3.1): u, v, lambda, mu linear (x_f[2K] = e[K],
-// x_f[2K+1] = (e[K] + e[K+1]) / 2, last point by end_rule); z piecewise
-// constant.  One thread per fine entry.
-__device__ __forceinline__ bool coarse_owned(bool vm, int K, int K0, int K1);
-// (j0, j1): add only to the entries of fine time blocks [j0, j1) (u, z, lambda at
-// steps [j0, j1), v, mu at steps [j0 - 1, j1 - 1)); j1 < 0: every entry
-template <typename T>
-__global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q, int end_rule, int j0 = 0,
-                              int j1 = -1) {
-  const long long np = (long long)n * p, nq = (long long)n * q;
-  const long long total = 4 * np + nq;
-  const int nc = n / 2;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long k = idx;
-    int width = p;
-    long long fine_off, coarse_off;
-    bool constant = false;
-    if (k < 2 * np) {  // u or v
-      long long which = k / np;
-      k -= which * np;
-      fine_off = which * np;
-      coarse_off = which * (np / 2);
-    } else if (k < 2 * np + nq) {  // z
-      k -= 2 * np;
-      width = q;
-      fine_off = 2 * np;
-      coarse_off = np;  // = 2 * (nc * p)
-      constant = true;
-    } else {  // lambda or mu
-      k -= 2 * np + nq;
-      long long which = k / np;
-      k -= which * np;
-      fine_off = 2 * np + nq + which * np;
-      coarse_off = np + nq / 2 + which * (np / 2);
+// Transfers between a level and the next coarser one (Sec. 5.3.1), in the
+// type-major layout.  Each CTA works on whole coarse time steps: with
+// tpk = transfer_threads(w) threads per step, thread e of a step handles
+// access e, e + tpk, ... of the step's w = (4p + q) / VW vector accesses (the
+// five types decoded by comparisons, 32-bit offsets within a type), so a warp
+// reads and writes contiguous runs of one type and no thread divides a 64-bit
+// index.
+//
+// Ownership of a vector entry by a range of time blocks [j0, j1) (j1 < 0: all):
+// block j holds u, z, lambda of step j and v, mu of step j - 1.
+__device__ __forceinline__ bool coarse_owned(bool vm, int K, int K0, int K1) {
+  const int blk = vm ? K + 1 : K;
+  return blk >= K0 && (K1 < 0 || blk < K1);
+}
+
+// entry e (< 4p + q) of a time step: its type (0 u, 1 v, 2 z, 3 lambda, 4 mu)
+// and its index i within the type
+__device__ __forceinline__ int entry_type(int e, int p, int q, int &i) {
+  if (e < p) { i = e; return 0; }
+  if (e < 2 * p) { i = e - p; return 1; }
+  if (e < 2 * p + q) { i = e - 2 * p; return 2; }
+  if (e < 3 * p + q) { i = e - 2 * p - q; return 3; }
+  i = e - 3 * p - q;
+  return 4;
+}
+
+// offset of type ty's block in a type-major vector of n steps
+// (u 0, v np, z 2np, lambda 2np + nq, mu 3np + nq)
+__device__ __forceinline__ long long type_offset(int ty, int n, int p, int q) {
+  const long long np = (long long)n * p;
+  return ty < 3 ? ty * np : 2 * np + (long long)n * q + (ty - 3) * np;
+}
+
+// threads per coarse step of the transfer kernels for steps of w vector
+// accesses: one warp-multiple covering them, at most the CTA (256 threads)
+inline __host__ __device__ int transfer_threads(int w) {
+  const int t = (w + 31) / 32 * 32;
+  return t < 256 ? t : 256;
+}
+
+// VW consecutive entries of one type as one access: VW = 2 loads and stores
+// pairs (16 bytes in FP64), which needs p and q even and vectors aligned to a
+// pair (pairs then never straddle two types); VW = 1 is the scalar form.  The
+// arithmetic is per entry either way.
+template <typename T, int VW>
+struct TVec;
+template <>
+struct TVec<double, 1> { typedef double type; };
+template <>
+struct TVec<float, 1> { typedef float type; };
+template <>
+struct TVec<double, 2> { typedef double2 type; };
+template <>
+struct TVec<float, 2> { typedef float2 type; };
+
+template <typename T, int VW>
+__device__ __forceinline__ typename TVec<T, VW>::type tv_load(const T *p) {
+  return *reinterpret_cast<const typename TVec<T, VW>::type *>(p);
+}
+template <typename T, int VW>
+__device__ __forceinline__ void tv_store(T *p, typename TVec<T, VW>::type v) {
+  *reinterpret_cast<typename TVec<T, VW>::type *>(p) = v;
+}
+// entry k of a vector access
+__device__ __forceinline__ double &tv_at(double &v, int) { return v; }
+__device__ __forceinline__ float &tv_at(float &v, int) { return v; }
+__device__ __forceinline__ double &tv_at(double2 &v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ float &tv_at(float2 &v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ double tv_at(const double &v, int) { return v; }
+__device__ __forceinline__ float tv_at(const float &v, int) { return v; }
+__device__ __forceinline__ double tv_at(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ float tv_at(const float2 &v, int k) { return k == 0 ? v.x : v.y; }
+
+// y += P e: u, v, lambda, mu linear (x_f[2K] = e[K], x_f[2K+1] = (e[K] +
+// e[K+1]) / 2, the last odd point by end_rule: e[K] for 0, e[K] / 2 for 1);
+// z piecewise constant (x_f[2K] = x_f[2K+1] = e[K]).  (j0, j1): add only to
+// the entries of fine time blocks [j0, j1); j1 < 0: every entry.  n is even.
+template <typename T, int VW = 1>
+__global__ void __launch_bounds__(256) k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q,
+                                                     int end_rule, int j0 = 0, int j1 = -1) {
+  const int nc = n / 2, w = (4 * p + q) / VW, tpk = transfer_threads(w), kpb = blockDim.x / tpk;
+  const int sub = threadIdx.x / tpk, lane = threadIdx.x - sub * tpk;
+  if (sub >= kpb) return;
+  for (int K = blockIdx.x * kpb + sub; K < nc; K += gridDim.x * kpb) {
+    for (int ent = lane; ent < w; ent += tpk) {
+      int i;
+      const int ty = entry_type(ent * VW, p, q, i);
+      const int width = ty == 2 ? q : p;
+      const bool vm = ty == 1 || ty == 4;
+      const T *ec = e + type_offset(ty, nc, p, q) + i;
+      T *yf = y + type_offset(ty, n, p, q) + i;
+      const auto e0 = tv_load<T, VW>(ec + (long long)K * width);
+      if (coarse_owned(vm, 2 * K, j0, j1)) {
+        T *dst = yf + (long long)(2 * K) * width;
+        auto a = tv_load<T, VW>(dst);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) tv_at(a, k) += tv_at(e0, k);
+        tv_store<T, VW>(dst, a);
+      }
+      if (coarse_owned(vm, 2 * K + 1, j0, j1)) {
+        typename TVec<T, VW>::type e1 = e0;
+        const bool interior = ty != 2 && K + 1 < nc;
+        if (interior) e1 = tv_load<T, VW>(ec + (long long)(K + 1) * width);
+        T *dst = yf + (long long)(2 * K + 1) * width;
+        auto a = tv_load<T, VW>(dst);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+          T add;
+          if (ty == 2) add = tv_at(e0, k);
+          else if (interior) add = T(0.5) * (tv_at(e0, k) + tv_at(e1, k));
+          else add = end_rule == 0 ? tv_at(e0, k) : T(0.5) * tv_at(e0, k);
+          tv_at(a, k) += add;
+        }
+        tv_store<T, VW>(dst, a);
+      }
     }
-    const int t = (int)(k / width), i = (int)(k % width);
-    const bool vm = idx < 2 * np ? idx >= np : idx >= 3 * np + nq;  // v or mu entry
-    if (!coarse_owned(vm, t, j0, j1)) continue;
-    const int K = t >> 1;
-    const T *ec = e + coarse_off;
-    T add;
-    if (constant || (t & 1) == 0) {
-      add = ec[(long long)K * width + i];
-    } else if (K + 1 < nc) {
-      add = T(0.5) * (ec[(long long)K * width + i] + ec[(long long)(K + 1) * width + i]);
-    } else {
-      add = end_rule == 0 ? ec[(long long)K * width + i] : T(0.5) * ec[(long long)K * width + i];
-    }
-    y[fine_off + k] += add;
   }
 }
 
@@ -1266,103 +1332,63 @@ __global__ void k_prolong_add(T *y, const T *__restrict__ e, int n, int p, int q
 //                      w = 1/2, except at K = nc - 1 where w is the end rule's
 //                      weight (1 for end_rule 0, 1/2 for end_rule 1)
 //   z:                 rc[K] = r[2K] + r[2K+1]
-// r is the full fine residual b - A~ y (k_apply_*).  One thread per coarse entry.
-// Ownership of a vector entry by a range of time blocks [j0, j1) (j1 < 0: all):
-// block j holds u, z, lambda of step j and v, mu of step j - 1.
-__device__ __forceinline__ bool coarse_owned(bool vm, int K, int K0, int K1) {
-  const int blk = vm ? K + 1 : K;
-  return blk >= K0 && (K1 < 0 || blk < K1);
-}
-
-// (K0, K1) of the restriction kernels: write only the entries of coarse time blocks [K0, K1)
-template <typename T>
-__global__ void k_restrict_transpose(const T *__restrict__ r, T *rc, int n, int p, int q, int end_rule, int K0 = 0,
-                                     int K1 = -1) {
-  const int nc = n / 2;
-  const long long ncp = (long long)nc * p, ncq = (long long)nc * q;
-  const long long np = (long long)n * p, nq = (long long)n * q;
-  const long long total = 4 * ncp + ncq;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long k = idx;
-    int width = p;
-    long long fine_off, coarse_off;
-    bool constant = false;
-    if (k < 2 * ncp) {  // u or v
-      const long long which = k / ncp;
-      k -= which * ncp;
-      fine_off = which * np;
-      coarse_off = which * ncp;
-    } else if (k < 2 * ncp + ncq) {  // z
-      k -= 2 * ncp;
-      width = q;
-      fine_off = 2 * np;
-      coarse_off = 2 * ncp;
-      constant = true;
-    } else {  // lambda or mu
-      k -= 2 * ncp + ncq;
-      const long long which = k / ncp;
-      k -= which * ncp;
-      fine_off = 2 * np + nq + which * np;
-      coarse_off = 2 * ncp + ncq + which * ncp;
+// r is the full fine residual b - A~ y (k_apply_*).  (K0, K1): write only the
+// entries of coarse time blocks [K0, K1).
+template <typename T, int VW = 1>
+__global__ void __launch_bounds__(256) k_restrict_transpose(const T *__restrict__ r, T *__restrict__ rc, int n,
+                                                            int p, int q, int end_rule, int K0 = 0, int K1 = -1) {
+  const int nc = n / 2, w = (4 * p + q) / VW, tpk = transfer_threads(w), kpb = blockDim.x / tpk;
+  const int sub = threadIdx.x / tpk, lane = threadIdx.x - sub * tpk;
+  if (sub >= kpb) return;
+  for (int K = blockIdx.x * kpb + sub; K < nc; K += gridDim.x * kpb) {
+    const T wr = (K + 1 < nc || end_rule != 0) ? T(0.5) : T(1);
+    for (int ent = lane; ent < w; ent += tpk) {
+      int i;
+      const int ty = entry_type(ent * VW, p, q, i);
+      if (!coarse_owned(ty == 1 || ty == 4, K, K0, K1)) continue;
+      const int width = ty == 2 ? q : p;
+      const T *rf = r + type_offset(ty, n, p, q) + i;
+      const auto r0 = tv_load<T, VW>(rf + (long long)(2 * K) * width);
+      const auto r1 = tv_load<T, VW>(rf + (long long)(2 * K + 1) * width);
+      typename TVec<T, VW>::type acc;
+      if (ty == 2) {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) tv_at(acc, k) = tv_at(r0, k) + tv_at(r1, k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) tv_at(acc, k) = fma(wr, tv_at(r1, k), tv_at(r0, k));
+        if (K >= 1) {
+          const auto rm = tv_load<T, VW>(rf + (long long)(2 * K - 1) * width);
+#pragma unroll
+          for (int k = 0; k < VW; ++k) tv_at(acc, k) = fma(T(0.5), tv_at(rm, k), tv_at(acc, k));
+        }
+      }
+      tv_store<T, VW>(rc + type_offset(ty, nc, p, q) + (long long)K * width + i, acc);
     }
-    const int K = (int)(k / width), i = (int)(k % width);
-    const bool vm = idx < 2 * ncp ? idx >= ncp : idx >= 3 * ncp + ncq;  // v or mu entry
-    if (!coarse_owned(vm, K, K0, K1)) continue;
-    const T *rf = r + fine_off;
-    const T r0 = rf[(long long)(2 * K) * width + i], r1 = rf[(long long)(2 * K + 1) * width + i];
-    T acc;
-    if (constant) {
-      acc = r0 + r1;
-    } else {
-      const T w = (K + 1 < nc || end_rule != 0) ? T(0.5) : T(1);
-      acc = fma(w, r1, r0);
-      if (K >= 1) acc = fma(T(0.5), rf[(long long)(2 * K - 1) * width + i], acc);
-    }
-    rc[coarse_off + k] = acc;
   }
 }
 
 // Restriction of a given fine residual by the variable formulas of Sec. 5.3.1
-// (injection at fine step 2K, average of z over 2K, 2K + 1), one thread per
-// coarse entry, for the time-range entry points (the V-cycle itself fuses it
-// with the residual: k_residual_restrict_*).  (K0, K1) as k_restrict_transpose.
+// (injection at fine step 2K, average of z over 2K, 2K + 1), for the time-range
+// entry points (the V-cycle itself fuses it with the residual:
+// k_residual_restrict_*).  (K0, K1) as k_restrict_transpose.
 template <typename T>
-__global__ void k_restrict_inject(const T *__restrict__ r, T *rc, int n, int p, int q, int K0, int K1) {
-  const int nc = n / 2;
-  const long long ncp = (long long)nc * p, ncq = (long long)nc * q;
-  const long long np = (long long)n * p, nq = (long long)n * q;
-  const long long total = 4 * ncp + ncq;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long k = idx;
-    int width = p;
-    long long fine_off, coarse_off;
-    bool average = false;
-    if (k < 2 * ncp) {
-      const long long which = k / ncp;
-      k -= which * ncp;
-      fine_off = which * np;
-      coarse_off = which * ncp;
-    } else if (k < 2 * ncp + ncq) {
-      k -= 2 * ncp;
-      width = q;
-      fine_off = 2 * np;
-      coarse_off = 2 * ncp;
-      average = true;
-    } else {
-      k -= 2 * ncp + ncq;
-      const long long which = k / ncp;
-      k -= which * ncp;
-      fine_off = 2 * np + nq + which * np;
-      coarse_off = 2 * ncp + ncq + which * ncp;
+__global__ void __launch_bounds__(256) k_restrict_inject(const T *__restrict__ r, T *__restrict__ rc, int n, int p,
+                                                         int q, int K0, int K1) {
+  const int nc = n / 2, w = 4 * p + q, tpk = transfer_threads(w), kpb = blockDim.x / tpk;
+  const int sub = threadIdx.x / tpk, lane = threadIdx.x - sub * tpk;
+  if (sub >= kpb) return;
+  for (int K = blockIdx.x * kpb + sub; K < nc; K += gridDim.x * kpb) {
+    for (int ent = lane; ent < w; ent += tpk) {
+      int i;
+      const int ty = entry_type(ent, p, q, i);
+      if (!coarse_owned(ty == 1 || ty == 4, K, K0, K1)) continue;
+      const int width = ty == 2 ? q : p;
+      const T *rf = r + type_offset(ty, n, p, q) + i;
+      const T r0 = rf[(long long)(2 * K) * width];
+      rc[type_offset(ty, nc, p, q) + (long long)K * width + i] =
+          ty == 2 ? T(0.5) * (r0 + rf[(long long)(2 * K + 1) * width]) : r0;
     }
-    const int K = (int)(k / width), i = (int)(k % width);
-    const bool vm = idx < 2 * ncp ? idx >= ncp : idx >= 3 * ncp + ncq;
-    if (!coarse_owned(vm, K, K0, K1)) continue;
-    const T *rf = r + fine_off;
-    const T r0 = rf[(long long)(2 * K) * width + i];
-    rc[coarse_off + k] = average ? T(0.5) * (r0 + rf[(long long)(2 * K + 1) * width + i]) : r0;
   }
 }
 

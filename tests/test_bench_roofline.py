@@ -78,3 +78,11 @@ def test_error_vs_oracle_reads_the_stored_samples():
     x[g["types"]["mu"]["indices"][3]] += 1e-6 * g["types"]["mu"]["max_abs"]
     e = B.error_vs_oracle(torch.tensor(x), "vdp_n256")
     assert abs(e["per_type"]["mu"] - 1e-6) < 1e-9 and e["per_type"]["u"] == 0.0
+
+
+def test_oracle_sample_runs_in_a_thread_sized_interpreter():
+    """The CPU-baseline legs time the oracle in a fresh interpreter whose BLAS pools are sized by the
+    environment (1 thread and every core); a short sample of van der Pol nt = 256 completes iterations."""
+    for threads in (1, 2):
+        times = _bench().oracle_sample_threads("vdp_n256", 1.0, 1.0, 400, "inject", threads)
+        assert len(times) >= 5 and all(t > 0 for t in times)

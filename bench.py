@@ -573,22 +573,33 @@ def measure_learned(P, torch, args, dev, stream, omega, restrict, restart):
     res["pairs"] = int(R.shape[0])
     res["collect_s"] = round(time.perf_counter() - t0, 2)
     _, _, T, X = R.shape
-    net = LN.new_net(wl["seed"])
+    # two networks from the same initial parameters and pairs: the mean squared error against the
+    # coarse solutions, and the residual metric of the first training system's coarse operator (the
+    # quantity the admission test measures)
+    nets = {}
+    hm = P.mg_setup(train_probs[0], stream=stream, **settings)
     try:
-        t0 = time.perf_counter()
-        losses = LN.train(net, R, Y, epochs=args.learned_epochs, batch=8, lr=1e-3, seed=1)
-        torch.cuda.synchronize(dev)
-        train_s = time.perf_counter() - t0
-        # forward + backward ~ 3x the forward's 2 * T * X * 21 * sum(C_in * C_out) flops per sample
         fl = 3 * 2.0 * T * X * 21 * (5 * 32 + 32 * 32 + 32 * 32 + 32 * 5) * R.shape[0] * args.learned_epochs
-        res.update(epochs=args.learned_epochs, train_s=round(train_s, 2),
-                   train_loss_normalised=[round(float(l), 4) for l in losses],
-                   train_tflops=round(fl / train_s / 1e12, 2), coarse_shape=[5, T, X])
+        res["coarse_shape"] = [5, T, X]
+        res["epochs"] = args.learned_epochs
+        for name, metric in (("mse", None), ("metric", hm)):
+            nets[name] = LN.new_net(wl["seed"])
+            t0 = time.perf_counter()
+            losses = LN.train(nets[name], R, Y, epochs=args.learned_epochs, batch=8, lr=1e-3, seed=1, metric=metric)
+            torch.cuda.synchronize(dev)
+            train_s = time.perf_counter() - t0
+            res[f"train_{name}"] = {"loss": "mean((net(r) - y)^2)" if metric is None else
+                                    "mean((A_c (net(r) - y))^2), A_c the coarse operator of training system 0",
+                                    "train_s": round(train_s, 2), "epoch_loss": [round(float(l), 5) for l in losses],
+                                    "train_tflops_conv": round(fl / train_s / 1e12, 2)}
+    finally:
+        P.mg_destroy(hm)
+    try:
         del R, Y
         prob = wl["make"]()
         b = torch.tensor(prob.b, device=dev)
         x = torch.empty_like(b)
-        for name, nt in (("plain", None), ("learned", net)):
+        for name, nt in (("plain", None), ("learned_mse", nets["mse"]), ("learned", nets["metric"])):
             # kernel shares (net inference included) from one profiled host-driven solve
             hp = P.mg_setup(prob, device_loops=False, stream=stream, **settings)
             try:
@@ -622,15 +633,19 @@ def measure_learned(P, torch, args, dev, stream, omega, restrict, restart):
                 P.mg_destroy(h)
             entry = {"solves_per_s": round(1e3 / ms, 4), "ms_per_solve": round(ms, 2), "fgmres_iters": info.iters,
                      "true_relres": info.true_relres, "coarse_gmres_iters": info.coarse_iters,
-                     "coarse_solves_by_network": info.coarse_learned}
+                     "coarse_solves_by_network": info.coarse_learned, "vcycles": info.vcycles,
+                     "kernel_shares": {k: round(v[0], 3) for k, v in shares.items() if v[1]}}
             if "net_coarse" in shares and shares["net_coarse"][1]:
                 ms_net, n_net, _, fl_net = shares["net_coarse"]
                 total = sum(v[0] for v in shares.values())
                 entry.update(net_share=round(ms_net / total, 4), net_tflops=round(fl_net / ms_net / 1e9, 2))
             res[name] = entry
         res["speedup_learned_vs_plain"] = round(res["learned"]["solves_per_s"] / res["plain"]["solves_per_s"], 4)
+        res["speedup_learned_mse_vs_plain"] = round(res["learned_mse"]["solves_per_s"] /
+                                                    res["plain"]["solves_per_s"], 4)
     finally:
-        P.mg_net_destroy(net)
+        for nt in nets.values():
+            P.mg_net_destroy(nt)
     return res
 
 

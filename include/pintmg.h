@@ -390,6 +390,25 @@ int mg_net_get_grad(const mg_net *net, float *grad);
 int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *y, int bf16, void *stream);
 int mg_net_loss_grad(mg_net *net, const float *x, const float *target, int batch, int T, int X, float *loss,
                      void *stream);
+/*
+ * Residual-metric loss (an extension; the paper trains no network).  A coarse
+ * proposal e is admitted by its residual ||r - A_c e|| (mg_attach_coarse_net),
+ * which the mean squared error of e against the coarse solution y does not
+ * control: A_c amplifies some error components far more than others.  After
+ * mg_net_set_metric(net, h), mg_net_loss_grad and mg_net_train minimise
+ *   L = sum_b ||A_c d_b||^2 / n,   d_b = s (net(x_b) - y_b),   n = batch 5 T X,
+ * with A_c the coarsest-level operator of h (FP64, the library's own product;
+ * it is symmetric), d_b in the type-major coarse layout of the samples, s = 1
+ * in mg_net_loss_grad and the targets' per-channel scales sy in a normalised
+ * mg_net_train (so L measures the unnormalised error); for y = A_c^-1 r this
+ * is the mean squared residual of the proposals.  The samples' T and X must
+ * be h's coarse shape (mg_coarse_shape; MG_ERR_ARG otherwise).  h is not owned
+ * and must outlive its use; h = NULL restores the mean squared error.  Needs
+ * an FP64 handle with q == p (MG_ERR_UNSUPPORTED otherwise).  Trained on the
+ * metric of one system, the network may serve other systems of similar
+ * operators: the admission test always uses the solved system's own A_c.
+ */
+int mg_net_set_metric(mg_net *net, mg_handle *h);
 int mg_net_adam_step(mg_net *net, float lr, float beta1, float beta2, float eps, void *stream);
 int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count, int T, int X, int batch,
                  int epochs, float lr, unsigned long long seed, int normalize, float *epoch_loss, void *stream);

@@ -5,8 +5,10 @@ vector in the type-major layout (u, v, z, lambda, mu; each n_c x p) is a
 (5, n_c, p) tensor: five channels over (time, space).  The network is four
 2-D convolutions over (time, space) with a 3 x 7 kernel and "same" zero
 padding, channels 5 -> 32 -> 32 -> 32 -> 5, a leaky rectifier (slope 0.1)
-after the first three; 49,829 parameters.  Training minimises the mean
-squared error against the plain method's coarse solutions with Adam.
+after the first three; 49,829 parameters.  Training minimises, with Adam,
+either the mean squared error against the plain method's coarse solutions or
+the residual-metric loss mean((A_c (net(x) - y))^2), which measures the error
+through the coarse operator A_c as the admission test does.
 
 Everything here is plain numpy in FP64: the reference the GPU kernels'
 forward pass, gradients and optimiser step are checked against.  Pins:
@@ -91,7 +93,34 @@ def loss_and_grad(params, x, target):
     y, pre = forward(params, x)
     diff = y - target
     loss = float(np.mean(diff * diff))
-    g = 2.0 * diff / diff.size
+    return loss, _backward(params, pre, 2.0 * diff / diff.size)
+
+
+def metric_loss_and_grad(params, x, target, A, scale=None):
+    """Residual-metric loss of a coarse correction and dL/dparams.
+
+    A proposal e = net(x) for the coarse system A e = r is admitted by the
+    size of its residual, so the loss measures the error e - y (y the plain
+    method's coarse solution, A y = r) through the coarse operator:
+        d_b = scale * (net(x_b) - target_b)   (scale per channel; 1 if None)
+        L = sum_b ||A d_b||^2 / n,            n = number of output entries,
+    d_b flattened in the type-major coarse layout (channel = variable type,
+    then time, then space).  dL/dnet(x_b) = scale * 2 A^T A d_b / n.  A is
+    a scipy sparse (or dense) matrix of the coarse level in that layout."""
+    y, pre = forward(params, x)
+    B = y.shape[0]
+    sc = np.ones(y.shape[1]) if scale is None else np.asarray(scale, dtype=np.float64)
+    d = ((y - target) * sc[None, :, None, None]).reshape(B, -1)
+    u = np.asarray((A @ d.T)).T
+    n = y.size
+    loss = float(np.sum(u * u) / n)
+    ge = (2.0 / n) * np.asarray(A.T @ u.T).T
+    ge = ge.reshape(y.shape) * sc[None, :, None, None]
+    return loss, _backward(params, pre, ge)
+
+
+def _backward(params, pre, g):
+    """dL/dparams (flat) from g = dL/d(net output) and the forward pass's pre-activations."""
     layers = unpack(params)
     grads = []
     for k in range(len(layers) - 1, -1, -1):
@@ -104,7 +133,7 @@ def loss_and_grad(params, x, target):
     flat = []
     for gW, gb in reversed(grads):
         flat += [gW.ravel(), gb.ravel()]
-    return loss, np.concatenate(flat)
+    return np.concatenate(flat)
 
 
 def adam_step(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):

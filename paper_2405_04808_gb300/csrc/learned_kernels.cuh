@@ -394,6 +394,30 @@ __global__ void k_bias_reduce(const float *__restrict__ partial, int G, int O, f
   gb[o] = s;
 }
 
+// Residual-metric loss: d[i] = scale[c] (y[i] - t[i]) in FP64, c = (i / TX) % C
+// the channel of entry i (scale null: 1)
+__global__ void k_metric_diff(const float *__restrict__ y, const float *__restrict__ t,
+                              const float *__restrict__ scale, long long TX, int C, long long n, double *d) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double sc = scale ? (double)scale[(i / TX) % C] : 1.0;
+    d[i] = sc * ((double)y[i] - (double)t[i]);
+  }
+}
+
+// g[i] = scale[c] * mul * a[i] (rounded to FP32), c as in k_metric_diff
+__global__ void k_metric_grad(const double *__restrict__ a, const float *__restrict__ scale, long long TX, int C,
+                              long long n, double mul, float *g) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double sc = scale ? (double)scale[(i / TX) % C] : 1.0;
+    g[i] = (float)(sc * mul * a[i]);
+  }
+}
+
+// loss[0] = sum[0] * inv_n (FP32)
+__global__ void k_metric_loss(const double *__restrict__ sum, double inv_n, float *loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) loss[0] = (float)(sum[0] * inv_n);
+}
+
 // loss partials of mean((y - t)^2) and g = 2 (y - t) / n
 __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, float *g, long long n, float *partial) {
   float acc = 0.f;

@@ -161,6 +161,11 @@ struct mg_net {
   double *spart = nullptr;             // their partial sums
   int *order = nullptr;  // minibatch gather indices (device)
   int order_cap = 0;
+  // residual-metric loss (mg_net_set_metric): the coarse operator of this handle (not owned)
+  // and the loss's FP64 workspace (two minibatch-sized vectors, then partial sums and the total)
+  mg_handle *metric = nullptr;
+  double *mws = nullptr;
+  long long mws_n = 0;
   DevMem mem, ws;        // mem: fixed buffers; ws: workspaces (reallocated when they grow)
 };
 
@@ -2797,10 +2802,56 @@ void net_ensure_train(mg_net *net, int batch, long long TX, int minibatches) {
   net->ws_batch = std::max(1, minibatches);
 }
 
-// forward (keeping every layer's output and pre-activation), MSE loss into
-// loss_dev[0], backward into net->grad
+// Residual-metric loss of the output net->h[4] (B samples of the coarse
+// level's 5 x T x X entries, the type-major layout of its vectors):
+//   d_b = scale (out_b - target_b),  L = sum_b ||A_c d_b||^2 / n,
+// n = B 5 T X, A_c the coarse operator of net->metric (FP64, the library's
+// own product), and dL/dout_b = scale 2 A_c^T A_c d_b / n into net->g0
+// (A_c is symmetric: the lifted augmented matrix).  scale (per channel) may be
+// null.
+constexpr int kMetricParts = 304;
+void net_metric_loss(mg_net *net, const float *target, int B, long long TX, const float *scale, float *loss_dev,
+                     cudaStream_t s) {
+  mg_handle *hm = net->metric;
+  const Level &cl = hm->lv.back();
+  const LevelView<double> &L = cl.d.view;
+  const long long len = cl.len, n = (long long)B * len;
+  if (n > net->mws_n) {
+    ck(cudaStreamSynchronize(s));
+    if (net->mws) cudaFree(net->mws);
+    net->mws = nullptr;
+    net->mws_n = 0;
+    cudaError_t e = cudaMalloc(&net->mws, (size_t)(2 * n + kMetricParts + 1) * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    net->mws_n = n;
+  }
+  double *d = net->mws, *u = d + n, *part = u + n, *sum = part + kMetricParts;
+  const int C = net_ch(kNetLayers);
+  const int gg = grid_for(n, 256, 1 << 20);
+  k_metric_diff<<<gg, 256, 0, s>>>(net->h[kNetLayers], target, scale, TX, C, n, d);
+  ck_launch();
+  for (int b = 0; b < B; ++b) launch_apply<double>(hm, L, d + b * len, nullptr, u + b * len, s);
+  const int G = (int)std::max<long long>(1, std::min<long long>(kMetricParts, (n + kDotThreads - 1) / kDotThreads));
+  k_multidot_partial<<<dim3(G, 1), kDotThreads, 0, s>>>(u, n, u, n, part);
+  ck_launch();
+  k_reduce_partials<<<1, 128, 0, s>>>(part, G, 1, sum, 0);
+  ck_launch();
+  k_metric_loss<<<1, 1, 0, s>>>(sum, 1.0 / (double)n, loss_dev);
+  ck_launch();
+  for (int b = 0; b < B; ++b) launch_apply<double>(hm, L, u + b * len, nullptr, d + b * len, s);
+  k_metric_grad<<<gg, 256, 0, s>>>(d, scale, TX, C, n, 2.0 / (double)n, net->g0);
+  ck_launch();
+}
+
+// forward (keeping every layer's output and pre-activation), the loss into
+// loss_dev[0] (mean squared error, or the residual metric when the network has
+// one; mscale: the metric's per-channel scale of the output, may be null),
+// backward into net->grad
 void net_loss_grad_dev(mg_net *net, const float *x, const float *target, int B, int T, int X, float *loss_dev,
-                       cudaStream_t s) {
+                       cudaStream_t s, const float *mscale = nullptr) {
   const long long TX = (long long)T * X;
   const float *in = x;
   for (int l = 0; l < kNetLayers; ++l) {
@@ -2813,12 +2864,16 @@ void net_loss_grad_dev(mg_net *net, const float *x, const float *target, int B, 
                        s);
     in = net->h[l + 1];
   }
-  const long long nout = (long long)B * net_ch(kNetLayers) * TX;
-  const int G = grid_for(nout, 256, kLossPartials);
-  k_mse<<<G, 256, 0, s>>>(net->h[kNetLayers], target, net->g0, nout, net->partial);
-  ck_launch();
-  k_sum_partials<<<1, 32, 0, s>>>(net->partial, G, 1.0f / (float)nout, loss_dev);
-  ck_launch();
+  if (net->metric) {
+    net_metric_loss(net, target, B, TX, mscale, loss_dev, s);
+  } else {
+    const long long nout = (long long)B * net_ch(kNetLayers) * TX;
+    const int G = grid_for(nout, 256, kLossPartials);
+    k_mse<<<G, 256, 0, s>>>(net->h[kNetLayers], target, net->g0, nout, net->partial);
+    ck_launch();
+    k_sum_partials<<<1, 32, 0, s>>>(net->partial, G, 1.0f / (float)nout, loss_dev);
+    ck_launch();
+  }
   float *g = net->g0, *other = net->g1;
   for (int l = kNetLayers - 1; l >= 0; --l) {
     const int C = net_ch(l), O = net_ch(l + 1);
@@ -2897,7 +2952,7 @@ void mg_net_destroy(mg_net *net) {
   cudaDeviceSynchronize();
   net->ws.release();
   net->mem.release();
-  for (void *p : {net->ia, net->ib, net->ic, static_cast<void *>(net->order)})
+  for (void *p : {net->ia, net->ib, net->ic, static_cast<void *>(net->order), static_cast<void *>(net->mws)})
     if (p) cudaFree(p);
   delete net;
 }
@@ -3002,10 +3057,23 @@ int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *
   });
 }
 
+// the samples' shape is the metric handle's coarse level (or there is no metric)
+static bool metric_shape_ok(const mg_net *net, int T, int X) {
+  return !net->metric || (net->metric->lv.back().n == T && net->metric->p == X);
+}
+
+int mg_net_set_metric(mg_net *net, mg_handle *h) {
+  if (!net) return MG_ERR_ARG;
+  if (h && (h->q != h->p || h->opts.precision != MG_PRECISION_FP64)) return MG_ERR_UNSUPPORTED;
+  net->metric = h;
+  return MG_OK;
+}
+
 int mg_net_loss_grad(mg_net *net, const float *x, const float *target, int batch, int T, int X, float *loss,
                      void *stream) {
   if (!net || !x || !target || !loss || batch < 1 || batch > kNetMaxBatch || T < 1 || T > kNetMaxT || X < 1)
     return MG_ERR_ARG;
+  if (!metric_shape_ok(net, T, X)) return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return net_guard([&] {
     net_ensure_train(net, batch, (long long)T * X, 1);
@@ -3026,7 +3094,7 @@ int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count,
   if (!net || !x_all || !y_all || count < 1 || T < 1 || T > kNetMaxT || X < 1 || batch < 1 || batch > kNetMaxBatch ||
       epochs < 0 ||
       !(lr > 0.f) ||
-      (normalize != 0 && normalize != 1))
+      (normalize != 0 && normalize != 1) || !metric_shape_ok(net, T, X))
     return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long TX = (long long)T * X, row = (long long)net_ch(0) * TX;
@@ -3081,7 +3149,8 @@ int mg_net_train(mg_net *net, const float *x_all, const float *y_all, int count,
           k_gather_rows<<<gg, 256, 0, s>>>(y_all, net->order + b0, nb, row, net->by);
           ck_launch();
         }
-        net_loss_grad_dev(net, net->bx, net->by, nb, T, X, net->loss + k, s);
+        // normalised training: the metric measures the error of the unnormalised output (times sy)
+        net_loss_grad_dev(net, net->bx, net->by, nb, T, X, net->loss + k, s, normalize ? net->sy : nullptr);
         net_adam(net, lr, 0.9f, 0.999f, 1e-8f, s);
       }
       ck(cudaMemcpyAsync(losses.data(), net->loss, (size_t)nmb * sizeof(float), cudaMemcpyDeviceToHost, s));

@@ -46,11 +46,18 @@ def collect_pairs(problems, settings: dict, max_pairs: int, rtol: float = 1e-8, 
     return R[:count], Y[:count]
 
 
-def train(net, R, Y, epochs: int, batch: int = 16, lr: float = 1e-3, seed: int = 0, normalize: bool = True):
+def train(net, R, Y, epochs: int, batch: int = 16, lr: float = 1e-3, seed: int = 0, normalize: bool = True,
+          metric=None):
     """Minibatch Adam on (R, Y) with the library's kernels (per-channel
-    normalised by default); returns per-epoch losses."""
+    normalised by default); returns per-epoch losses.  metric: a handle whose
+    coarse operator A_c defines the residual-metric loss mean((A_c (net(r) -
+    y))^2) (mg_net_set_metric); None: the mean squared error."""
     count, _, T, X = R.shape
-    return P.mg_net_train(net, R.data_ptr(), Y.data_ptr(), count, T, X, batch, epochs, lr, seed, normalize)
+    P.mg_net_set_metric(net, metric)
+    try:
+        return P.mg_net_train(net, R.data_ptr(), Y.data_ptr(), count, T, X, batch, epochs, lr, seed, normalize)
+    finally:
+        P.mg_net_set_metric(net, None)
 
 
 def new_net(seed: int):

@@ -46,7 +46,8 @@ EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmr
             "mg_level_info", "mg_range_sweep", "mg_range_residual", "mg_range_restrict", "mg_range_prolong",
             "mg_coarse_solve",
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
-            "mg_net_forward", "mg_net_loss_grad", "mg_net_adam_step", "mg_net_train", "mg_net_destroy",
+            "mg_net_forward", "mg_net_loss_grad", "mg_net_set_metric", "mg_net_adam_step", "mg_net_train",
+            "mg_net_destroy",
             "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune", "mg_jacobi_radius",
             "mg_destroy", "mg_status_string", "mg_last_cuda_error")
 
@@ -133,6 +134,7 @@ def lib():
                 ("mg_net_adam_step", [vp, cf, cf, cf, cf, vp], ci),
                 ("mg_net_train", [vp, vp, vp, ci, ci, ci, ci, ci, cf, ctypes.c_ulonglong, ci, fp, vp], ci),
                 ("mg_net_destroy", [vp], None),
+                ("mg_net_set_metric", [vp, vp], ci),
                 ("mg_attach_coarse_net", [vp, vp, ctypes.c_double, ci], ci),
                 ("mg_record_coarse", [vp, vp, vp, ci], ci),
                 ("mg_recorded_pairs", [vp], ci),
@@ -398,6 +400,11 @@ def mg_net_train(net, x_ptr: int, y_ptr: int, count: int, T: int, X: int, batch:
                               batch, epochs, lr, ctypes.c_ulonglong(seed), 1 if normalize else 0, _fptr(losses),
                               ctypes.c_void_p(stream)), "mg_net_train")
     return losses[:epochs]
+
+
+def mg_net_set_metric(net, h) -> None:
+    """Train `net` on the residual metric of h's coarse operator (h None: mean squared error)."""
+    _check(lib().mg_net_set_metric(ctypes.c_void_p(net), ctypes.c_void_p(h) if h else None), "mg_net_set_metric")
 
 
 def mg_net_destroy(net) -> None:

@@ -303,3 +303,132 @@ def test_trained_network_gain(P, capsys):
     finally:
         P.mg_net_destroy(net0)
         P.mg_net_destroy(net)
+
+
+def _metric_problem(seed):
+    return W.burgers(nx=8, n=16, seed=seed)
+
+
+@pytest.mark.parametrize("B", [1, 3])
+def test_metric_loss_and_gradient_match_oracle(P, B):
+    """Residual-metric loss mean((A_c (net(x) - t))^2) with the coarse operator of a handle against the
+    oracle's, A_c from the oracle's own hierarchy of the same problem."""
+    prob = _metric_problem(21)
+    h = P.mg_setup(prob, levels=2, nu_pre=1, nu_post=1)
+    net = P.mg_net_create(_params(15))
+    try:
+        T, X = P.mg_coarse_shape(h)
+        rng = np.random.default_rng(9)
+        x = rng.standard_normal((B, 5, T, X)).astype(np.float32)
+        t = rng.standard_normal((B, 5, T, X)).astype(np.float32)
+        Ac = O.Hierarchy(prob, O.MGOptions(levels=2, nu_pre=1, nu_post=1)).levels[-1].A
+        loss_o, grad_o = NL.metric_loss_and_grad(_params(15).astype(np.float64), x.astype(np.float64),
+                                                 t.astype(np.float64), Ac)
+        P.mg_net_set_metric(net, h)
+        xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        loss = P.mg_net_loss_grad(net, xd.data_ptr(), td.data_ptr(), B, T, X)
+        g = P.mg_net_get_grad(net)
+        with pytest.raises(P.PintmgError):   # samples of another shape than the metric's coarse level
+            P.mg_net_loss_grad(net, xd.data_ptr(), td.data_ptr(), 1, T - 1, X)
+        P.mg_net_set_metric(net, None)   # back to the mean squared error
+        assert abs(P.mg_net_loss_grad(net, xd.data_ptr(), td.data_ptr(), B, T, X) -
+                   NL.loss_and_grad(_params(15).astype(np.float64), x.astype(np.float64),
+                                    t.astype(np.float64))[0]) <= 1e-5 * loss_o + 1e-5
+    finally:
+        P.mg_net_destroy(net)
+        P.mg_destroy(h)
+    assert abs(loss - loss_o) <= 1e-5 * loss_o
+    assert _rel(g, grad_o) <= GRAD_RTOL
+    k = 0
+    for Wt, b in NL.unpack(grad_o):
+        for part in (Wt.ravel(), b):
+            assert _rel(g[k:k + part.size], part) <= 10 * GRAD_RTOL
+            k += part.size
+
+
+def test_metric_training_step_matches_oracle(P):
+    """A normalised mg_net_train step on the residual metric: the loss measures the unnormalised error
+    (the targets' channel scales sy inside the metric), one Adam step, the scalings folded back."""
+    prob = _metric_problem(22)
+    h = P.mg_setup(prob, levels=2, nu_pre=1, nu_post=1)
+    net = P.mg_net_create(_params(16))
+    try:
+        T, X = P.mg_coarse_shape(h)
+        B = 3
+        x, t = _scaled_data_shape(B, T, X)
+        x64, t64, p64 = x.astype(np.float64), t.astype(np.float64), _params(16).astype(np.float64)
+        Ac = O.Hierarchy(prob, O.MGOptions(levels=2, nu_pre=1, nu_post=1)).levels[-1].A
+        sx, sy = NL.channel_rms(x64), NL.channel_rms(t64)
+        _, g = NL.metric_loss_and_grad(p64, x64 / sx[None, :, None, None], t64 / sy[None, :, None, None], Ac, sy)
+        pn, _, _ = NL.adam_step(p64, g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+        want = NL.fold(pn, sx, sy, -1)
+        P.mg_net_set_metric(net, h)
+        xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        P.mg_net_train(net, xd.data_ptr(), td.data_ptr(), B, T, X, B, 1, 1e-3, 0, True)
+        got = P.mg_net_get_params(net).astype(np.float64)
+    finally:
+        P.mg_net_destroy(net)
+        P.mg_destroy(h)
+    # as in the mean-squared-error step, parameters whose oracle gradient is within the FP32 gradient's
+    # rounding of zero are left out; the metric spreads the gradient's magnitudes wider (A_c weights some
+    # error components far more than others), so somewhat more of them (about 1.2 % here)
+    decided = np.abs(g) > 1e-6 * np.linalg.norm(g)
+    assert decided.mean() > 0.98
+    assert np.max((np.abs(got - want) / np.maximum(1.0, np.abs(want)))[decided]) <= 2e-5
+
+
+def _scaled_data_shape(B, T, X):
+    rng = np.random.default_rng(10)
+    x = rng.standard_normal((B, 5, T, X)) * np.array([1e-2, 1.0, 20.0, 0.3, 4.0])[None, :, None, None]
+    t = rng.standard_normal((B, 5, T, X)) * np.array([5.0, 0.2, 1.0, 60.0, 0.01])[None, :, None, None]
+    return x.astype(np.float32), t.astype(np.float32)
+
+
+ADMIT = dict(levels=4, nu_pre=4, nu_post=4, omega=2.0 / 3.0, restrict="transpose")
+
+
+def _admit_problem(seed):
+    return W.burgers(nx=16, n=512, seed=seed)
+
+
+def test_metric_trained_network_is_admitted(P, capsys):
+    """Trained on the residual metric of one training system's coarse operator, the network's proposals
+    pass the admission test (||r - A_c e|| <= 0.5 ||r||) on held-out systems: FGMRES takes them as coarse
+    solves and still converges.  The mean-squared-error network of the same data is never admitted."""
+    from paper_2405_04808_gb300 import learned as L
+    train_probs = [_admit_problem(5001 + k) for k in range(12)]
+    R, Y = L.collect_pairs(train_probs, ADMIT, max_pairs=480, rtol=1e-10, restart=60, per_problem=40)
+    hm = P.mg_setup(train_probs[0], **ADMIT)
+    nets = {}
+    try:
+        for name, metric in (("mse", None), ("metric", hm)):
+            nets[name] = L.new_net(7)
+            L.train(nets[name], R, Y, epochs=20, batch=8, lr=1e-3, seed=2, metric=metric)
+        stats = {}
+        for name in ("plain", "mse", "metric"):
+            its, lrn = [], []
+            for seed in (5000, 4999):
+                prob = _admit_problem(seed)
+                h = P.mg_setup(prob, **ADMIT)
+                try:
+                    if name != "plain":
+                        P.mg_attach_coarse_net(h, nets[name], admit=0.5, bf16=True)
+                    b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+                    x = torch.zeros_like(b)
+                    st, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-8, maxit=500, restart=60)
+                    assert st == P.MG_OK and info.true_relres <= 1e-8 * 1.01
+                    its.append(info.iters)
+                    lrn.append(info.coarse_learned)
+                finally:
+                    P.mg_destroy(h)
+            stats[name] = (its, lrn)
+        with capsys.disabled():
+            print(f"\nresidual-metric training (Burgers nx=16 nt=512, {R.shape[0]} pairs, 20 epochs): iterations "
+                  f"plain {stats['plain'][0]}, mse {stats['mse'][0]} (admitted {stats['mse'][1]}), metric "
+                  f"{stats['metric'][0]} (admitted {stats['metric'][1]})")
+        assert sum(stats["metric"][1]) > 0
+        assert sum(stats["metric"][1]) > sum(stats["mse"][1])
+    finally:
+        for nt in nets.values():
+            P.mg_net_destroy(nt)
+        P.mg_destroy(hm)

@@ -110,3 +110,55 @@ def test_launch_list_summary(tmp_path):
                  '"2","void k_a<double>(int)","gpu__time_duration.sum","usecond","6"\n')
     out = summarize(str(f))
     assert "| k_a<double> | 2 | 0.009 | 90.0 % |" in out and "| k_b | 1 | 0.001 | 10.0 % |" in out
+
+
+def test_metric_loss_with_identity_is_the_mean_squared_error():
+    """A = I and unit scales reduce the residual-metric loss to the plain mean squared error."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(5)
+    p = W.net_init_params(4) + 0.02 * rng.standard_normal(NL.param_count())
+    x = rng.standard_normal((2, 5, 4, 8))
+    t = rng.standard_normal((2, 5, 4, 8))
+    l0, g0 = NL.loss_and_grad(p, x, t)
+    l1, g1 = NL.metric_loss_and_grad(p, x, t, sp.identity(5 * 4 * 8, format="csr"))
+    assert abs(l1 - l0) <= 1e-14 * l0 and np.allclose(g1, g0, rtol=0, atol=1e-15 * np.abs(g0).max())
+
+
+def test_metric_gradients_match_finite_differences():
+    """A random sparse non-symmetric A and per-channel scales: central differences of the loss."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(6)
+    p = W.net_init_params(5) + 0.05 * rng.standard_normal(NL.param_count())
+    x = rng.standard_normal((2, 5, 4, 7))
+    t = rng.standard_normal((2, 5, 4, 7))
+    N = 5 * 4 * 7
+    A = sp.random(N, N, density=0.05, random_state=7, format="csr") + sp.identity(N)
+    scale = np.array([0.5, 2.0, 1.0, 3.0, 0.25])
+    loss, g = NL.metric_loss_and_grad(p, x, t, A, scale)
+    for i in rng.choice(p.size, 40, replace=False):
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        fd = (NL.metric_loss_and_grad(p + e, x, t, A, scale)[0] -
+              NL.metric_loss_and_grad(p - e, x, t, A, scale)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_metric_loss_is_the_admission_residual():
+    """With the coarse operator of a small Burgers hierarchy and targets y = A^-1 r (sparse direct
+    solve), the loss is the mean squared residual r - A net(r) of the proposals the admission test
+    measures."""
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    from oracle import augmented as O
+    prob = W.burgers(nx=8, n=16, seed=11)
+    Lc = O.Hierarchy(prob, O.MGOptions(levels=2)).levels[-1]
+    A = Lc.A.tocsc()
+    T, X = Lc.n, Lc.p
+    rng = np.random.default_rng(8)
+    r = rng.standard_normal((3, 5 * T * X))
+    y = np.stack([spla.spsolve(A, ri) for ri in r])
+    p = W.net_init_params(6) + 0.05 * rng.standard_normal(NL.param_count())
+    xr, yr = r.reshape(3, 5, T, X), y.reshape(3, 5, T, X)
+    loss, _ = NL.metric_loss_and_grad(p, xr, yr, A)
+    e = NL.forward(p, xr)[0].reshape(3, -1)
+    res = r - (A @ e.T).T
+    assert abs(loss - np.sum(res * res) / r.size) <= 1e-9 * loss

@@ -60,6 +60,6 @@ def train(net, R, Y, epochs: int, batch: int = 16, lr: float = 1e-3, seed: int =
         P.mg_net_set_metric(net, None)
 
 
-def new_net(seed: int):
+def new_net(seed: int, zero_output: bool = False):
     """A network with the seeded initial parameters (workloads.net_init_params)."""
-    return P.mg_net_create(W.net_init_params(seed).astype(np.float32))
+    return P.mg_net_create(W.net_init_params(seed, zero_output).astype(np.float32))

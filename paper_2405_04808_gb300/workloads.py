@@ -479,16 +479,19 @@ NET_CHANNELS = (5, 32, 32, 32, 5)
 NET_KT, NET_KX = 3, 7
 
 
-def net_init_params(seed: int) -> np.ndarray:
+def net_init_params(seed: int, zero_output: bool = False) -> np.ndarray:
     """Initial parameters of the coarse-correction network, flat in the C-ABI's
     layout (per layer: weights [out][in][time tap][space tap], then biases):
-    weights uniform in +-sqrt(6 / fan_in) (He et al. 2015), biases zero."""
+    weights uniform in +-sqrt(6 / fan_in) (He et al. 2015), biases zero.
+    zero_output: the last layer's weights zero too, so the untrained network
+    proposes e = 0 (residual r; used with the residual-metric loss, where a
+    random output's error is amplified by the coarse operator)."""
     sizes = [(co * ci * NET_KT * NET_KX, co, ci * NET_KT * NET_KX)
              for ci, co in zip(NET_CHANNELS[:-1], NET_CHANNELS[1:])]
     u = uniform(seed, STREAM_NET_INIT, sum(nw for nw, _, _ in sizes))
     out, k = [], 0
-    for nw, nb, fan_in in sizes:
-        lim = math.sqrt(6.0 / fan_in)
+    for layer, (nw, nb, fan_in) in enumerate(sizes):
+        lim = 0.0 if (zero_output and layer == len(sizes) - 1) else math.sqrt(6.0 / fan_in)
         out += [(2.0 * u[k:k + nw] - 1.0) * lim, np.zeros(nb)]
         k += nw
     return np.concatenate(out)

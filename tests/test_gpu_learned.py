@@ -402,7 +402,7 @@ def test_metric_trained_network_is_admitted(P, capsys):
     nets = {}
     try:
         for name, metric in (("mse", None), ("metric", hm)):
-            nets[name] = L.new_net(7)
+            nets[name] = L.new_net(7, zero_output=metric is not None)
             L.train(nets[name], R, Y, epochs=20, batch=8, lr=1e-3, seed=2, metric=metric)
         stats = {}
         for name in ("plain", "mse", "metric"):

@@ -21,6 +21,7 @@
 #include "learned_kernels.cuh"
 #include "pair_kernels.cuh"
 #include "setup_kernels.cuh"
+#include "tc_kernels.cuh"
 #include "vcycle_kernels.cuh"
 
 using namespace pintmg;
@@ -143,7 +144,9 @@ struct Level {
 struct mg_net {
   float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *partial = nullptr, *loss = nullptr;
   __nv_bfloat16 *params_bf16 = nullptr;
-  __nv_bfloat16 *wimg = nullptr;  // per-layer weight images of the tensor-core convolutions
+  __nv_bfloat16 *wimg = nullptr;  // per-layer weight images of the tensor-core convolutions (mma.sync)
+  __nv_bfloat16 *timg = nullptr;  // the same for the tcgen05 convolutions
+  int *tc_err = nullptr;          // a bounded wait of a tcgen05 convolution ran out (standalone forward)
   bool bf16_valid = false;
   int step = 0;              // Adam's step count (bias correction)
   long long updates = 0;     // optimiser steps ever taken by this network
@@ -1069,7 +1072,35 @@ void conv_mma_prepare() {
   ck(cudaFuncSetAttribute(k_conv_mma<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(1, 4)));
   ck(cudaFuncSetAttribute(k_conv_mma<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(2, 1)));
   ck(cudaFuncSetAttribute(k_conv_mma<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(2, 4)));
+  ck(cudaFuncSetAttribute(k_conv_tc<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(1, 32)));
+  ck(cudaFuncSetAttribute(k_conv_tc<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(2, 32)));
+  ck(cudaFuncSetAttribute(k_conv_tc<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(2, 16)));
   if (dev < 32) done |= 1u << dev;
+}
+
+// BF16 inference layers on tcgen05 (default) or, with PINTMG_CONV_MMA=1, on mma.sync
+bool conv_use_tc() {
+  static const bool tc = [] {
+    const char *e = std::getenv("PINTMG_CONV_MMA");
+    return !(e && e[0] == '1');
+  }();
+  return tc;
+}
+
+// layer l of the network in BF16 on tcgen05 (weights from the layer's image); err: the wait flag
+void launch_conv_tc(const __nv_bfloat16 *timg_all, int l, const __nv_bfloat16 *x, const __nv_bfloat16 *bias,
+                    __nv_bfloat16 *y, int B, int H, int Wd, int act, int *err, cudaStream_t s) {
+  const __nv_bfloat16 *img = timg_all + tc_img_offset(l);
+  const int C = net_ch(l), O = net_ch(l + 1);
+  const dim3 grid((Wd + kTcM - 1) / kTcM, (H + kTcRows - 1) / kTcRows, B);
+  const int cb = tc_cb(l), n = tc_nl(l);
+  if (cb == 1 && n == 32)
+    k_conv_tc<1, 32><<<grid, kTcThreads, tc_smem(1, 32), s>>>(x, img, bias, y, C, O, H, Wd, act, err);
+  else if (cb == 2 && n == 16)
+    k_conv_tc<2, 16><<<grid, kTcThreads, tc_smem(2, 16), s>>>(x, img, bias, y, C, O, H, Wd, act, err);
+  else
+    k_conv_tc<2, 32><<<grid, kTcThreads, tc_smem(2, 32), s>>>(x, img, bias, y, C, O, H, Wd, act, err);
+  ck_launch();
 }
 
 template <int CB, int NT>
@@ -1111,9 +1142,12 @@ void net_forward_storage(mg_handle *h, const mg_net *net, const T *x, int B, int
     const double flops = 2.0 * n * net_ch(l) * kNetKT * kNetKX;
     const int act = l < kNetLayers - 1;
     auto run = [&] {
-      if constexpr (kBf16)
-        launch_conv_mma(net->wimg, l, in, bias, out, B, H, Wd, act, s);
-      else
+      if constexpr (kBf16) {
+        if (conv_use_tc())
+          launch_conv_tc(net->timg, l, in, bias, out, B, H, Wd, act, h ? h->flag + 2 : net->tc_err, s);
+        else
+          launch_conv_mma(net->wimg, l, in, bias, out, B, H, Wd, act, s);
+      } else
         launch_conv<T>(in, W, bias, out, nullptr, B, net_ch(l), net_ch(l + 1), H, Wd, act, s);
     };
     if (h) {
@@ -1141,6 +1175,15 @@ void net_refresh_bf16(mg_net *net, cudaStream_t s) {
       k_conv_mma_image<2, 1><<<grid_for(n, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), img);
     else
       k_conv_mma_image<2, 4><<<grid_for(n, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), img);
+    ck_launch();
+    __nv_bfloat16 *timg = net->timg + tc_img_offset(l);
+    const int tn = tc_img_bytes(tc_cb(l), tc_nl(l)) / 2;
+    if (tc_cb(l) == 1 && tc_nl(l) == 32)
+      k_conv_tc_image<1, 32><<<grid_for(tn, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), timg);
+    else if (tc_cb(l) == 2 && tc_nl(l) == 16)
+      k_conv_tc_image<2, 16><<<grid_for(tn, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), timg);
+    else
+      k_conv_tc_image<2, 32><<<grid_for(tn, 256), 256, 0, s>>>(W, net_ch(l), net_ch(l + 1), timg);
     ck_launch();
   }
   net->bf16_valid = true;
@@ -2970,6 +3013,9 @@ int mg_net_create(const float *init_params, mg_net **out) {
     net->partial = net->mem.alloc<float>(kLossPartials);
     net->params_bf16 = net->mem.alloc<__nv_bfloat16>(kNetParams);
     net->wimg = net->mem.alloc<__nv_bfloat16>(kConvMmaWimg);
+    net->timg = net->mem.alloc<__nv_bfloat16>(kTcImgValues);
+    net->tc_err = net->mem.alloc<int>(1);
+    ck(cudaMemset(net->tc_err, 0, sizeof(int)));
     net->wt = net->mem.alloc<float>((size_t)32 * 32 * kNetKT * kNetKX);
     net->wpart = net->mem.alloc<float>((size_t)kWgSlices * 32 * 32 * kNetKT * kNetKX);
     net->bpart = net->mem.alloc<float>((size_t)32 * kBiasParts);
@@ -3021,7 +3067,7 @@ int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *
     return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long TX = (long long)T * X;
-  return net_guard([&] {
+  const int st = net_guard([&] {
     const long long bytes = (long long)batch * 32 * TX * (long long)sizeof(float);
     if (bytes > net->inf_bytes) {
       ck(cudaStreamSynchronize(s));
@@ -3055,6 +3101,15 @@ int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *
                                  static_cast<float *>(net->ib), s);
     }
   });
+  if (st != MG_OK || !bf16 || !conv_use_tc()) return st;
+  // a tcgen05 layer whose bounded wait ran out: the output is void (the flag is cleared for the next call)
+  int tmo = 0;
+  if (cudaMemcpyAsync(&tmo, net->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MG_ERR_CUDA;
+  if (!tmo) return MG_OK;
+  cudaMemsetAsync(net->tc_err, 0, sizeof(int), s);
+  return MG_ERR_TIMEOUT;
 }
 
 // the samples' shape is the metric handle's coarse level (or there is no metric)

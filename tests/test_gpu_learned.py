@@ -42,7 +42,9 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
 
 
-@pytest.mark.parametrize("shape", [(1, 4, 5), (2, 9, 11), (3, 17, 40)])
+# the BF16 path runs the tcgen05 convolutions (128-position tiles of one time row, 4 rows per CTA): shapes
+# with partial tiles in both directions, two tiles across, and several samples
+@pytest.mark.parametrize("shape", [(1, 4, 5), (2, 9, 11), (3, 17, 40), (2, 13, 130), (1, 64, 256)])
 def test_forward_matches_oracle(P, shape):
     B, T, X = shape
     p = _params(11)

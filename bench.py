@@ -560,7 +560,7 @@ def measure_learned(P, torch, args, dev, stream, omega, restrict, restart):
     settings = dict(levels=wl["levels"], nu_pre=wl["nu_pre"], nu_post=wl["nu_post"], omega=omega, restrict=restrict)
     res = {"workload": LEARNED_WORKLOAD, "restart": restart, "omega": omega, "restrict": restrict,
            "levels": wl["levels"], "admit": 0.5,
-           "inference": "bf16 on the tensor cores (mma.sync m16n8k16), fp32 accumulation"}
+           "inference": "bf16 on the tensor cores (tcgen05.mma kind::f16, M=128 positions, accumulators in TMEM), fp32 accumulation"}
     t0 = time.perf_counter()
     import os
     per = 20  # a solve to 1e-12 records one pair per FGMRES iteration (about 25 here)

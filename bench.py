@@ -293,7 +293,8 @@ def measure(P, torch, prob, wl, args, precision, omega, steps, warmup, dev, stre
             except Exception:
                 P.mg_destroy(h)
                 raise
-            tuned.update(chain=chain, dot_vb=vb)
+            tuned.update(chain=chain, dot_vb=vb,
+                         block_warps=[P.mg_block_mapping(h, l) for l in range(lv - 1)])
         return h
 
     def solve(h, bp, xp):

@@ -457,6 +457,17 @@ int mg_coarse_shape(const mg_handle *h, int *T, int *X);
  * `stream`; invalidates h's captured graphs.
  */
 int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream);
+/*
+ * Block-solve mapping of level `level` (0 = finest) as its sweeps launch it: 1 =
+ * one warp per time block, 2 = two warps per time block (the split solve for
+ * levels whose blocks alone do not fill the GPU).  mg_autotune times both on
+ * every smoothing level where both apply and keeps the faster (the results
+ * differ in rounding only: the two warps sum the right-hand side's parts in
+ * another order); before that, or where only one applies, the size rule
+ * decides (two warps up to 4096 blocks with p <= 128).  Returns the mapping,
+ * or MG_ERR_ARG for a bad handle or level.
+ */
+int mg_block_mapping(const mg_handle *h, int level);
 
 /*
  * Spectral radius of the undamped block-Jacobi iteration I - D^-1 A~ on level

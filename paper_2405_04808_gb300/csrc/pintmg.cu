@@ -205,6 +205,9 @@ struct mg_handle {
   int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
   int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
   int pair_tri = 1;     // levels with few blocks: two warps per block
+  // per level (keyed by its number of time steps): the block-solve mapping the autotuner
+  // chose, 1 = one warp per block, 2 = two warps per block; absent: the size rule
+  std::map<int, int> bs_map;
   int pair_basis = 0;   // the FGMRES basis as FP32 pairs with compensated dot products (MG_BASIS_PAIR)
   int pair_stall = 0;   // failure-detection tests: the streamed multi-dot issues no copies (its waits run out)
   int device = -1;      // the CUDA device current at mg_setup; every device buffer of the handle lives there
@@ -393,7 +396,9 @@ void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, con
   } else {
     const int blocks = (nb + 3) / 4;
     const size_t smem = 4 * (size_t)tri_stage_elems<T>(L.p) * sizeof(T);
-    if (h->pair_tri && tri_stage_ok(L) && L.n + 1 <= kPairMaxBlocks) {  // two warps per block
+    const auto tuned = h->bs_map.find(L.n);
+    const bool pair = tuned != h->bs_map.end() ? tuned->second == 2 : L.n + 1 <= kPairMaxBlocks;
+    if (h->pair_tri && tri_stage_ok(L) && pair) {  // two warps per block
       const int pblocks = (nb + 1) / 2;
       const size_t psmem = 2 * (size_t)tri_pair_elems<T>(L.p) * sizeof(T);
       if (L.p == 4 * kWarp && L.q == L.p) {
@@ -3294,6 +3299,7 @@ namespace {
 struct TuneChoice {
   int chain = 0;   // 0 scan, 1 cluster, 2 single CTA, 3 segmented
   int dot_vb = 8;
+  std::vector<std::pair<int, int>> bs;  // (level steps, block-solve mapping 1 or 2) of the smoothing levels
   float ms_chain[4] = {-1.f, -1.f, -1.f, -1.f};
   float ms_dot[3] = {-1.f, -1.f, -1.f};  // VB 4, 8, 16
 };
@@ -3350,7 +3356,36 @@ void tune_chain(mg_handle *h, Level &lev, TuneChoice &c, cudaStream_t s) {
   c.chain = best < 0 ? 2 : best;
 }
 
+// one block-Jacobi sweep of level `lev` (zero data in `scratch`, at least 3 level
+// vectors of T) with one and with two warps per block, where both apply (tridiagonal
+// blocks staged in shared memory); returns the faster mapping, or 0
+template <typename T>
+int tune_block_map(mg_handle *h, Level &lev, void *scratch, cudaStream_t s) {
+  const LevelView<T> &L = ldata<T>(lev).view;
+  if (L.layout != MG_LAYOUT_TRIDIAG || !h->pair_tri || !tri_stage_ok(L)) return 0;
+  T *r = static_cast<T *>(scratch), *y = r + lev.len, *out = y + lev.len;
+  ck(cudaMemsetAsync(r, 0, 2 * lev.len * sizeof(T), s));
+  Vec<T> Y = make_vec(y, lev.n, h->p, h->q);
+  float ms[2];
+  for (int k = 0; k < 2; ++k) {
+    h->bs_map[lev.n] = k + 1;
+    ms[k] = time_min(s, 5, [&] { launch_block_solve<T>(h, L, r, Y.u, Y.m, out, s); });
+  }
+  h->bs_map.erase(lev.n);
+  return ms[1] < ms[0] ? 2 : 1;
+}
+
 }  // namespace
+
+extern "C" int mg_block_mapping(const mg_handle *h, int level) {
+  if (!h || level < 0 || level >= (int)h->lv.size()) return MG_ERR_ARG;
+  const int n = h->lv[level].n;
+  const auto it = h->bs_map.find(n);
+  if (it != h->bs_map.end()) return it->second;
+  const LevelView<double> &L = h->lv[level].d.view;
+  if (h->layout != MG_LAYOUT_TRIDIAG) return 1;
+  return (h->pair_tri && n + 1 <= kPairMaxBlocks && L.p <= 4 * kWarp) ? 2 : 1;
+}
 
 extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) {
   if (!h) return MG_ERR_ARG;
@@ -3410,6 +3445,13 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
       }
       h->dot_vb = save_vb;
       c.dot_vb = vbs[best];
+      // block-solve mapping of every smoothing level (the sweeps' kernel)
+      const bool f32 = h->opts.precision == MG_PRECISION_FP32 || h->opts.precision == MG_PRECISION_FP32_SMOOTH;
+      for (size_t l = 0; l + 1 < h->lv.size(); ++l) {
+        if (h->opts.precision == MG_PRECISION_BF16_BANDS) break;  // the BF16-band view keeps the size rule
+        const int m = f32 ? tune_block_map<float>(h, h->lv[l], tmp, s) : tune_block_map<double>(h, h->lv[l], tmp, s);
+        if (m) c.bs.emplace_back(h->lv[l].n, m);
+      }
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune_cache[key] = c;
     }
@@ -3419,6 +3461,7 @@ extern "C" int mg_autotune(mg_handle *h, int *chain, int *dot_vb, void *stream) 
       h->use_seg = c.chain == 3;
     }
     h->dot_vb = c.dot_vb;
+    for (const auto &kv : c.bs) h->bs_map[kv.first] = kv.second;
     h->gen++;  // captured graphs used the previous choices
   } catch (const CudaFail &) {
     status = MG_ERR_CUDA;

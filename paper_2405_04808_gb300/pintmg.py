@@ -48,7 +48,8 @@ EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmr
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
             "mg_net_forward", "mg_net_loss_grad", "mg_net_set_metric", "mg_net_adam_step", "mg_net_train",
             "mg_net_destroy",
-            "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune", "mg_jacobi_radius",
+            "mg_attach_coarse_net", "mg_record_coarse", "mg_recorded_pairs", "mg_coarse_shape", "mg_autotune",
+            "mg_block_mapping", "mg_jacobi_radius",
             "mg_destroy", "mg_status_string", "mg_last_cuda_error")
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -140,6 +141,7 @@ def lib():
                 ("mg_recorded_pairs", [vp], ci),
                 ("mg_coarse_shape", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
                 ("mg_autotune", [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), vp], ci),
+                ("mg_block_mapping", [vp, ci], ci),
                 ("mg_jacobi_radius", [vp, ci, ci, ctypes.POINTER(ctypes.c_double), vp], ci),
                 ("mg_probe_fma", [ci, ci, ci, vp, vp], ci),
                 ("mg_level_info", [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_longlong)], ci),
@@ -452,6 +454,14 @@ def mg_autotune(h, stream: int = 0):
     _check(lib().mg_autotune(ctypes.c_void_p(h), ctypes.byref(chain), ctypes.byref(vb), ctypes.c_void_p(stream)),
            "mg_autotune")
     return SGS_CHAINS[chain.value], vb.value
+
+
+def mg_block_mapping(h, level: int) -> int:
+    """Block-solve mapping of a level: 1 = one warp per time block, 2 = two warps per block."""
+    code = int(lib().mg_block_mapping(ctypes.c_void_p(h), level))
+    if code < 0:
+        raise PintmgError(code, "mg_block_mapping")
+    return code
 
 
 def mg_destroy(h) -> None:

@@ -29,12 +29,13 @@ def test_autotuned_solve_keeps_the_solution(P, make, settings):
     prob = make()
     ref = O.direct_solve(prob)
     b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
-    xs, choices = [], []
+    xs, choices, maps = [], [], []
     for tune in (False, True, True):
         h = P.mg_setup(prob, **settings)
         try:
             if tune:
                 choices.append(P.mg_autotune(h))
+            maps.append([P.mg_block_mapping(h, l) for l in range(settings["levels"])])
             x = torch.zeros_like(b)
             st, info = P.fgmres_solve(h, b.data_ptr(), x.data_ptr(), 1e-10, maxit=1500, restart=200)
             assert st == P.MG_OK
@@ -46,6 +47,7 @@ def test_autotuned_solve_keeps_the_solution(P, make, settings):
     assert chain in P.SGS_CHAINS and vb in (4, 8, 16)
     for x in xs:
         assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
-    assert np.array_equal(xs[1], xs[2])
-    if chain == "scan":                                  # the default chain: only the blocking changed
+    assert np.array_equal(xs[1], xs[2]) and maps[1] == maps[2]
+    assert all(m in (1, 2) for mm in maps for m in mm)
+    if chain == "scan" and maps[0] == maps[1]:           # default chain and block mapping: only the blocking
         assert np.array_equal(xs[0], xs[1])

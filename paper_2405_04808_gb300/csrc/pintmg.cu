@@ -1077,9 +1077,9 @@ void conv_mma_prepare() {
   ck(cudaFuncSetAttribute(k_conv_mma<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(1, 4)));
   ck(cudaFuncSetAttribute(k_conv_mma<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(2, 1)));
   ck(cudaFuncSetAttribute(k_conv_mma<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_mma_smem(2, 4)));
-  ck(cudaFuncSetAttribute(k_conv_tc<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(1, 32)));
-  ck(cudaFuncSetAttribute(k_conv_tc<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(2, 32)));
-  ck(cudaFuncSetAttribute(k_conv_tc<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(2, 16)));
+  ck(cudaFuncSetAttribute(k_conv_tc<1, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(1, 32)));
+  ck(cudaFuncSetAttribute(k_conv_tc<2, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(2, 32)));
+  ck(cudaFuncSetAttribute(k_conv_tc<2, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(2, 16)));
   if (dev < 32) done |= 1u << dev;
 }
 
@@ -1092,19 +1092,62 @@ bool conv_use_tc() {
   return tc;
 }
 
-// layer l of the network in BF16 on tcgen05 (weights from the layer's image); err: the wait flag
+// cuTensorMapEncodeTiled, resolved from the driver once (no link against libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// tensor map of a network activation [B][H][Wd][Cp] (BF16, channels innermost) for k_conv_tc's
+// input planes: boxes of 8 channels x kTcSP positions x kTcSR rows x 1 sample, zero fill outside
+CUtensorMap tc_input_map(const __nv_bfloat16 *x, int Cp, int B, int H, int Wd) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "cuTensorMapEncodeTiled is not available");
+    throw CudaFail{cudaErrorNotSupported};
+  }
+  CUtensorMap m;
+  const cuuint64_t dims[4] = {(cuuint64_t)Cp, (cuuint64_t)Wd, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)Cp * 2, (cuuint64_t)Wd * Cp * 2, (cuuint64_t)H * Wd * Cp * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kTcSP, (cuuint32_t)kTcSR, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(x), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    throw CudaFail{cudaErrorInvalidValue};
+  }
+  return m;
+}
+
+// layer l of the network in BF16 on tcgen05 (weights from the layer's image): x [B][H][Wd][16 CB]
+// (channels innermost), y channels innermost [B][H][Wd][32] for the hidden layers, [B][5][H][Wd] for
+// the last; err: the wait flag
 void launch_conv_tc(const __nv_bfloat16 *timg_all, int l, const __nv_bfloat16 *x, const __nv_bfloat16 *bias,
                     __nv_bfloat16 *y, int B, int H, int Wd, int act, int *err, cudaStream_t s) {
   const __nv_bfloat16 *img = timg_all + tc_img_offset(l);
-  const int C = net_ch(l), O = net_ch(l + 1);
+  const int O = net_ch(l + 1);
   const dim3 grid((Wd + kTcM - 1) / kTcM, (H + kTcRows - 1) / kTcRows, B);
   const int cb = tc_cb(l), n = tc_nl(l);
+  const CUtensorMap xm = tc_input_map(x, 16 * cb, B, H, Wd);
   if (cb == 1 && n == 32)
-    k_conv_tc<1, 32><<<grid, kTcThreads, tc_smem(1, 32), s>>>(x, img, bias, y, C, O, H, Wd, act, err);
+    k_conv_tc<1, 32, true><<<grid, kTcThreads, tc_smem(1, 32), s>>>(xm, img, bias, y, O, H, Wd, act, err);
   else if (cb == 2 && n == 16)
-    k_conv_tc<2, 16><<<grid, kTcThreads, tc_smem(2, 16), s>>>(x, img, bias, y, C, O, H, Wd, act, err);
+    k_conv_tc<2, 16, false><<<grid, kTcThreads, tc_smem(2, 16), s>>>(xm, img, bias, y, O, H, Wd, act, err);
   else
-    k_conv_tc<2, 32><<<grid, kTcThreads, tc_smem(2, 32), s>>>(x, img, bias, y, C, O, H, Wd, act, err);
+    k_conv_tc<2, 32, true><<<grid, kTcThreads, tc_smem(2, 32), s>>>(xm, img, bias, y, O, H, Wd, act, err);
   ck_launch();
 }
 
@@ -1205,7 +1248,10 @@ void net_coarse_proposal(mg_handle *h, Level &lev, const mg_handle::Krylov &K, c
     B16 *xin = static_cast<B16 *>(h->net_x), *a = static_cast<B16 *>(h->net_a), *b = static_cast<B16 *>(h->net_b);
     {
       Bracket br(h, CAT_NET, s);
-      k_net_input<B16><<<grid_for(len, 256), 256, 0, s>>>(h->cr, K.scal, xin, len);
+      if (conv_use_tc())  // the tcgen05 layers read their input with the channels innermost
+        k_net_input_ci<<<grid_for((long long)H * Wd, 256), 256, 0, s>>>(h->cr, K.scal, xin, (long long)H * Wd);
+      else
+        k_net_input<B16><<<grid_for(len, 256), 256, 0, s>>>(h->cr, K.scal, xin, len);
       ck_launch();
     }
     net_forward_storage<B16>(h, net, xin, 1, H, Wd, xin, a, b, s);
@@ -3095,7 +3141,10 @@ int mg_net_forward(mg_net *net, const float *x, int batch, int T, int X, float *
       net_refresh_bf16(net, s);
       using B16 = __nv_bfloat16;
       B16 *c = static_cast<B16 *>(net->ic);
-      k_f32_to_bf16<<<grid_for(nio, 256), 256, 0, s>>>(x, c, nio);
+      if (conv_use_tc())  // the tcgen05 layers read their input with the channels innermost
+        k_f32_to_bf16_ci<<<grid_for((long long)batch * TX, 256), 256, 0, s>>>(x, c, batch, TX);
+      else
+        k_f32_to_bf16<<<grid_for(nio, 256), 256, 0, s>>>(x, c, nio);
       ck_launch();
       net_forward_storage<B16>(nullptr, net, c, batch, T, X, c, static_cast<B16 *>(net->ia),
                                static_cast<B16 *>(net->ib), s);
@@ -3253,7 +3302,7 @@ int mg_attach_coarse_net(mg_handle *h, mg_net *net, double admit, int bf16) {
     const Level &cl = h->lv.back();
     if (!h->net_e) {
       const long long TX = (long long)cl.n * h->p;
-      h->net_x = h->mem.alloc<float>((size_t)net_ch(0) * TX);
+      h->net_x = h->mem.alloc<float>((size_t)8 * TX);  // 5 FP32 channels, or 16 BF16 channels innermost
       h->net_a = h->mem.alloc<float>((size_t)32 * TX);
       h->net_b = h->mem.alloc<float>((size_t)32 * TX);
       h->net_e = h->mem.alloc<double>(cl.len);

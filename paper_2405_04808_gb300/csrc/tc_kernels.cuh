@@ -19,9 +19,13 @@
 //    every staged position, 16 bytes per position, positions of a staged row
 //    consecutive, kTcRows + 2 rows.  The A operand of tap (i, j) is the 128
 //    staged positions of row (row + i) starting at column j + 1 (the staged
-//    columns begin 4 left of s0 so that the pairs of a row start even): core
-//    matrices 128 bytes apart along M, one plane apart along K.  A tap is a
-//    shift of the start address, so no im2col copy is made.
+//    columns begin 4 left of s0): core matrices 128 bytes apart along M, one
+//    plane apart along K.  A tap is a shift of the start address, so no
+//    im2col copy is made.  The layers' activations are stored with the
+//    channels innermost ([B][T][X][Cp], Cp = 16 for the network's input with
+//    channels 5..15 zero, 32 between layers), so a plane is one box of a
+//    tiled TMA copy (cp.async.bulk.tensor, 8 channels x 136 positions x 6
+//    rows, zero-filled outside the layer); the last layer writes [B][O][T][X].
 //  * Weights: tile (tap, cb) holds [half][n] rows of 16 bytes, N rows per half:
 //    core matrices 128 bytes apart along N, 16 N bytes apart along K.  The
 //    whole layer's tiles are an image (k_conv_tc_image, once per parameter
@@ -33,6 +37,8 @@
 // start address / 16, 16-29 leading byte offset / 16, 32-45 stride byte
 // offset / 16, 46-47 descriptor version (1), 61-63 layout (0 = no swizzle).
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
 #include "learned_kernels.cuh"
 #include "pair_kernels.cuh"
@@ -81,16 +87,18 @@ __global__ void k_conv_tc_image(const __nv_bfloat16 *__restrict__ W, int C, int 
   }
 }
 
-// One layer: x [B][C][H][Wd] -> y [B][O][H][Wd] (BF16), bias and the leaky
-// rectifier (act) in the epilogue.  Grid (ceil(Wd / 128), ceil(H / 4), B),
-// kTcThreads threads, tc_smem(CB, N) bytes of dynamic shared memory.  A wait
-// that runs out (2 s) sets err[0]; the CTA then waits once more (bounded) for
-// its copies and MMAs, skips its output and frees its TMEM.
-template <int CB, int N>
-__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__restrict__ x,
+// One layer: the input, [B][H][Wd][16 CB] BF16 behind the tensor map xmap
+// (dims channels, Wd, H, B; box 8 x kTcSP x kTcSR x 1), to y: [B][H][Wd][N]
+// with the channels innermost (kCiOut) or [B][O][H][Wd]; BF16, bias and the
+// leaky rectifier (act) in the epilogue.  Grid (ceil(Wd / 128), ceil(H / 4),
+// B), kTcThreads threads, tc_smem(CB, N) bytes of dynamic shared memory.  A
+// wait that runs out (2 s) sets err[0]; the CTA then waits once more (bounded)
+// for its copies and MMAs, skips its output and frees its TMEM.
+template <int CB, int N, bool kCiOut>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __grid_constant__ CUtensorMap xmap,
                                                         const __nv_bfloat16 *__restrict__ img,
                                                         const __nv_bfloat16 *__restrict__ bias, __nv_bfloat16 *y,
-                                                        int C, int O, int H, int Wd, int act, int *err) {
+                                                        int O, int H, int Wd, int act, int *err) {
   constexpr int PLANE = tc_plane(), A_BYTES = tc_a_bytes(CB), IMG = tc_img_bytes(CB, N), TILE = tc_tile_bytes(N);
   constexpr int COLS = kTcRows * N;  // TMEM columns: a power of two >= 32 (64 or 128)
   static_assert(COLS == 64 || COLS == 128, "TMEM allocation must be a power of two of at least 32 columns");
@@ -116,8 +124,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = *tslot;
-  if (threadIdx.x == 0) {  // the weight image, in chunks of kTcChunk bytes
-    mbar_expect_tx(bar, IMG);
+  if (threadIdx.x == 0) {  // the weight image (chunks of kTcChunk bytes) and the input planes, one barrier
+    mbar_expect_tx(bar, IMG + CB * 2 * PLANE);
     for (int off = 0; off < IMG; off += kTcChunk) {
       const unsigned n = (unsigned)min(kTcChunk, IMG - off);
       asm volatile(
@@ -126,21 +134,16 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
           "l"(reinterpret_cast<const unsigned char *>(img) + off), "r"(n), "r"(smem_addr(bar))
           : "memory");
     }
+    // plane pl: channels 8 pl .. 8 pl + 7 of rows t0 - 1 .. t0 + kTcRows, positions s0 - 4 .. s0 + 131
+    // (the innermost coordinate, 8 pl channels, is a multiple of 16 bytes)
+    for (int pl = 0; pl < CB * 2; ++pl)
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+          "%5}], [%6];\n" ::"r"(smem_addr(sa + pl * PLANE)),
+          "l"(reinterpret_cast<unsigned long long>(&xmap)), "r"(8 * pl), "r"(s0 - 4), "r"(t0 - kNetKT / 2), "r"(b),
+          "r"(smem_addr(bar))
+          : "memory");
   }
-  // the input rows t0 - 1 .. t0 + kTcRows, positions s0 - 4 .. s0 + 131, zero outside the layer
-  for (int e = threadIdx.x; e < CB * 2 * kTcSR * kTcSP; e += kTcThreads) {
-    const int pos = e % kTcSP, r = (e / kTcSP) % kTcSR, pl = e / (kTcSP * kTcSR);
-    const int t = t0 + r - kNetKT / 2, sp = s0 + pos - 4;
-    const bool in = t >= 0 && t < H && sp >= 0 && sp < Wd;
-    __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int c = pl * 8 + u;
-      v[u] = (in && c < C) ? x[(((long long)b * C + c) * H + t) * Wd + sp] : __float2bfloat16(0.f);
-    }
-    *reinterpret_cast<uint4 *>(sa + pl * PLANE + (r * kTcSP + pos) * 16) = *reinterpret_cast<const uint4 *>(v);
-  }
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the staged input, visible to the tensor cores
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -207,12 +210,28 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         const int t = t0 + row;
         if (t < H && sp < Wd) {
+          if constexpr (kCiOut) {  // the position's N channels, 16 bytes at a time
+            uint4 *dst = reinterpret_cast<uint4 *>(y + (((long long)b * H + t) * Wd + sp) * N);
 #pragma unroll
-          for (int o = 0; o < N; ++o) {
-            if (o >= O) break;
-            float val = __uint_as_float(v[o]) + (bias ? __bfloat162float(bias[o]) : 0.f);
-            if (act) val = val > 0.f ? val : kNetSlope * val;
-            y[(((long long)b * O + o) * H + t) * Wd + sp] = __float2bfloat16(val);
+            for (int q8 = 0; q8 < N / 8; ++q8) {
+              __align__(16) __nv_bfloat16 out[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int o = q8 * 8 + u;
+                float val = __uint_as_float(v[o]) + (bias && o < O ? __bfloat162float(bias[o]) : 0.f);
+                if (act) val = val > 0.f ? val : kNetSlope * val;
+                out[u] = __float2bfloat16(o < O ? val : 0.f);
+              }
+              dst[q8] = *reinterpret_cast<const uint4 *>(out);
+            }
+          } else {
+#pragma unroll
+            for (int o = 0; o < N; ++o) {
+              if (o >= O) break;
+              float val = __uint_as_float(v[o]) + (bias ? __bfloat162float(bias[o]) : 0.f);
+              if (act) val = val > 0.f ? val : kNetSlope * val;
+              y[(((long long)b * O + o) * H + t) * Wd + sp] = __float2bfloat16(val);
+            }
           }
         }
       }
@@ -222,6 +241,37 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const __nv_bfloat16 *__r
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(COLS) : "memory");
+}
+
+// network input with the channels innermost and padded: x [B][5][H][Wd] FP32 ->
+// xc [B][H][Wd][16] BF16 (channels 5..15 zero)
+__global__ void k_f32_to_bf16_ci(const float *__restrict__ x, __nv_bfloat16 *xc, int B, long long HW) {
+  const long long n = (long long)B * HW;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / HW, pos = i % HW;
+    __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = c < 5 ? __float2bfloat16(x[(b * 5 + c) * HW + pos]) : __float2bfloat16(0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(xc + i * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(v)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(v)[1];
+  }
+}
+
+// the coarse residual scaled by 1 / rms(r) (scal[1] = 1 / ||r||; n = 5 H Wd entries in the
+// type-major layout, a (5, H, Wd) tensor) as the network's input with the channels innermost
+__global__ void k_net_input_ci(const double *__restrict__ r, const double *__restrict__ scal, __nv_bfloat16 *xc,
+                               long long HW) {
+  const double inv = scal[1] * sqrt(5.0 * (double)HW);
+  for (long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x; pos < HW;
+       pos += (long long)gridDim.x * blockDim.x) {
+    __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = c < 5 ? __float2bfloat16((float)(r[c * HW + pos] * inv)) : __float2bfloat16(0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(xc + pos * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(v)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(v)[1];
+  }
 }
 
 }  // namespace pintmg

@@ -47,6 +47,9 @@ struct LevelView {
   long long sFac;
   const T *scan;
   T kappa;  // != 0: V_k = kappa Z_k for every step (theta = 1, d_z f a multiple of M), else 0
+  // tridiagonal blocks too large for one warp's registers (p > 128): workspaces of the block
+  // solve's three launches, (n + 1) x p each (right-hand sides of S lambda = rhs, and lambda)
+  T *ws_rhs, *ws_lam;
 };
 
 template <typename T>

@@ -205,6 +205,7 @@ struct mg_handle {
   int dot_vb = 8;       // basis vectors per CTA of the blocked dot products (4, 8 or 16; same arithmetic)
   int stage_tri = 1;    // block solves read their coefficients from shared memory (staged by cp.async)
   int pair_tri = 1;     // levels with few blocks: two warps per block
+  int split_bs = 1;     // p > 128: the block solve in three launches (PINTMG_SPLIT_BS=0: one warp per block)
   // per level (keyed by its number of time steps): the block-solve mapping the autotuner
   // chose, 1 = one warp per block, 2 = two warps per block; absent: the size rule
   std::map<int, int> bs_map;
@@ -427,6 +428,20 @@ void launch_block_solve(mg_handle *h, const LevelView<T, CT> &L, const T *r, con
       ck_launch();
       return;
     }
+    if (L.ws_rhs && h->split_bs) {  // large blocks: right-hand sides, pentadiagonal solves, outputs
+      const long long ent = (long long)nb * L.p;
+      const int g = grid_for(ent, 256, 1 << 20);
+      k_bs_rhs<T, CT><<<g, 256, 0, s>>>(L, r, cplU, cplM, j0, j1);
+      ck_launch();
+      switch (h->C) {
+        case 8: k_bs_penta<T, 8, CT><<<blocks, 128, 0, s>>>(L, j0, j1); break;
+        default: k_bs_penta<T, 16, CT><<<blocks, 128, 0, s>>>(L, j0, j1); break;
+      }
+      ck_launch();
+      k_bs_out<T, CT><<<g, 256, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1);
+      ck_launch();
+      return;
+    }
     switch (h->C) {
       case 1: k_block_solve_tri<T, 1, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
       case 2: k_block_solve_tri<T, 2, false, 0, CT><<<blocks, 128, 0, s>>>(L, r, cplU, cplM, out, yold, omega, j0, j1); break;
@@ -456,6 +471,9 @@ void launch_apply(mg_handle *h, const LevelView<T, CT> &L, const T *x, const T *
       else
         k_apply_dense<T><<<grid_for(steps, 128, 1 << 30), 128, 0, s>>>(L, x, b, out, nullptr, j0, j1, xcopy, xidx, xshift);
     }
+  } else if (L.p > 4 * kWarp && h->split_bs) {  // large blocks: a thread per (step, entry)
+    k_apply_ent<T, CT><<<grid_for((long long)steps * L.p, 256, 1 << 20), 256, 0, s>>>(L, x, b, out, nullptr, j0, j1,
+                                                                                    xcopy, xidx, xshift);
   } else {
     const int blocks = (steps + 3) / 4;
     switch (h->C) {
@@ -1522,6 +1540,13 @@ void alloc_level_vectors(mg_handle *h, Level &lev, LevelData<T> &d, bool is_last
   const long long len = lev.len;
   if (!is_last) prepare_sweeps<T>(h, lev, d, s);
   d.tmp = h->mem.alloc<T>(len);
+  if (h->layout == MG_LAYOUT_TRIDIAG && h->p > 4 * kWarp) {  // the three-launch block solve's workspaces
+    const size_t ws = (size_t)(lev.n + 1) * h->p;
+    d.view.ws_rhs = h->mem.alloc<T>(ws);
+    d.view.ws_lam = h->mem.alloc<T>(ws);
+    d.vh.ws_rhs = d.view.ws_rhs;
+    d.vh.ws_lam = d.view.ws_lam;
+  }
   if (!is_first || sizeof(T) == sizeof(float)) {
     d.b = h->mem.alloc<T>(len);
     d.y = h->mem.alloc<T>(len);
@@ -1675,6 +1700,9 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
           k_apply_dw<double><<<(L.n + 3) / 4, 128, 0, bs>>>(L, x, b, h->fr, &st->restart);
         } else if (L.layout == MG_LAYOUT_DENSE) {
           k_apply_dense<double><<<grid_for(L.n, 128, 1 << 30), 128, 0, bs>>>(L, x, b, h->fr, &st->restart);
+        } else if (L.p > 4 * kWarp && h->split_bs) {
+          k_apply_ent<double, double><<<grid_for((long long)L.n * L.p, 256, 1 << 20), 256, 0, bs>>>(L, x, b, h->fr,
+                                                                                                 &st->restart);
         } else {
           const int blocks = (L.n + 3) / 4;
           switch (h->C) {
@@ -2025,6 +2053,7 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (const char *e = std::getenv("PINTMG_STAGE_TRI")) h->stage_tri = std::atoi(e) != 0;
   // PINTMG_TRI_PAIR=0 keeps one warp per block on every level (tests)
   if (const char *e = std::getenv("PINTMG_TRI_PAIR")) h->pair_tri = std::atoi(e) != 0;
+  if (const char *e = std::getenv("PINTMG_SPLIT_BS")) h->split_bs = std::atoi(e) != 0;
   // PINTMG_FUSE_COPIES=0: captured solves copy the preconditioner's input and output in kernels of their own
   if (const char *e = std::getenv("PINTMG_FUSE_COPIES")) h->fuse_copies = std::atoi(e) != 0;
   // PINTMG_FUSE_REDUCE=0 reduces dot products and forms the Arnoldi column in separate launches,

@@ -250,6 +250,145 @@ __global__ void __launch_bounds__(128) k_block_solve_tri(LevelView<T, CT> L, con
   }
 }
 
+// Tridiagonal blocks too large for one warp's registers (p > 128; one warp
+// holds p / 32 values per lane and vector, 16 at p = 512, and the one-warp
+// solve then runs at 255 registers, 8 warps per SM): the local solve of
+// k_block_solve_tri in three launches with the same arithmetic, entry for
+// entry, so the results are bitwise those of the one-warp kernel:
+//   k_bs_rhs:   rhs = N r_u + Z (r_z + kappa v) - r_lambda (or N r_u + Z r_z -
+//               r_lambda + V v), a thread per entry (neighbours read directly);
+//   k_bs_penta: S lambda = rhs by the warp's chunked pentadiagonal solve
+//               (penta_solve, p / 32 values per lane, nothing else live);
+//   k_bs_out:   u, z, mu (and v) from lambda, relaxation, a thread per entry.
+// rhs and lambda pass through L.ws_rhs and L.ws_lam ((n + 1) x p values).
+// Blocks [j0, j1) (all: j1 < 0), couplings and relaxation as k_block_solve_tri.
+
+// r_u - cplM and v = -(r_mu - cplU) of block j at entry k (0 outside [0, p))
+template <typename T>
+__device__ __forceinline__ T bs_ru(const Vec<const T> &R, const T *cplM, int j, int k, int p) {
+  if (k < 0 || k >= p) return T(0);
+  T v = R.u[(long long)j * p + k];
+  if (cplM) v -= cplM[(long long)j * p + k];
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T bs_v(const Vec<const T> &R, const T *cplU, int j, int k, int p) {
+  if (k < 0 || k >= p) return T(0);
+  T rm = R.m[(long long)(j - 1) * p + k];
+  if (cplU) rm -= cplU[(long long)(j - 1) * p + k];
+  return -rm;
+}
+// (A x)_i and (A^T x)_i of a tridiagonal band A (3 rows of p), as tri_mv / tri_mtv form them
+template <typename T, typename CT>
+__device__ __forceinline__ T bs_mv(const CT *A, int i, int p, T xm, T x, T xp) {
+  return fma(T(coef(A[i])), xm, fma(T(coef(A[p + i])), x, T(coef(A[2 * p + i])) * xp));
+}
+template <typename T, typename CT>
+__device__ __forceinline__ T bs_mtv(const CT *A, int i, int p, T xm, T x, T xp) {
+  const T up = (i > 0) ? T(coef(A[2 * p + i - 1])) : T(0);
+  const T lo = (i + 1 < p) ? T(coef(A[i + 1])) : T(0);
+  return fma(up, xm, fma(T(coef(A[p + i])), x, lo * xp));
+}
+
+template <typename T, typename CT>
+__global__ void __launch_bounds__(256) k_bs_rhs(LevelView<T, CT> L, const T *__restrict__ r, const T *cplU,
+                                                const T *cplM, int j0, int j1) {
+  const int n = L.n, p = L.p, q = L.q;
+  const int jend = (j1 < 0 ? n + 1 : j1) < n ? (j1 < 0 ? n + 1 : j1) : n;  // block n has no lambda
+  const long long total = (long long)(jend - j0) * p;
+  const Vec<const T> R = make_cvec(r, n, p, q);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = j0 + (int)(idx / p), i = (int)(idx % p);
+    const CT *N = L.N + j * L.sN, *V = L.V + j * L.sV, *Z = L.Z + j * L.sZ;
+    const T *rz = R.z + (long long)j * q;
+    auto rzk = [&](int k) { return (k < 0 || k >= p) ? T(0) : rz[k]; };
+    T rhs = bs_mv<T>(N, i, p, bs_ru(R, cplM, j, i - 1, p), bs_ru(R, cplM, j, i, p), bs_ru(R, cplM, j, i + 1, p));
+    const T rl = R.l[(long long)j * p + i];
+    if (L.kappa != T(0) && j >= 1) {
+      auto wk = [&](int k) { return (k < 0 || k >= p) ? T(0) : fma(L.kappa, bs_v(R, cplU, j, k, p), rz[k]); };
+      rhs = fma(T(1), bs_mv<T>(Z, i, p, wk(i - 1), wk(i), wk(i + 1)), rhs);
+      rhs -= rl;
+    } else {
+      rhs = fma(T(1), bs_mv<T>(Z, i, p, rzk(i - 1), rzk(i), rzk(i + 1)), rhs);
+      rhs -= rl;
+      if (j >= 1)
+        rhs = fma(T(1), bs_mv<T>(V, i, p, bs_v(R, cplU, j, i - 1, p), bs_v(R, cplU, j, i, p),
+                                 bs_v(R, cplU, j, i + 1, p)),
+                  rhs);
+    }
+    L.ws_rhs[(long long)j * p + i] = rhs;
+  }
+}
+
+template <typename T, int C, typename CT>
+__global__ void __launch_bounds__(128, 4) k_bs_penta(LevelView<T, CT> L, int j0, int j1) {
+  const int ln = threadIdx.x & (kWarp - 1);
+  const int j = j0 + (blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
+  const int n = L.n, p = L.p;
+  if (j >= n || (j1 >= 0 && j >= j1)) return;
+  T rhs[C], l[C];
+  chunk_load<T, C>(rhs, L.ws_rhs + (long long)j * p, p, ln);
+  penta_solve<T, C>(l, rhs, L.fac + j * L.sFac, L.scan + (long long)j * kScanPerBlock, p, ln);
+  chunk_store<T, C>(L.ws_lam + (long long)j * p, l, p, ln);
+}
+
+template <typename T, typename CT>
+__global__ void __launch_bounds__(256) k_bs_out(LevelView<T, CT> L, const T *__restrict__ r, const T *cplU,
+                                                const T *cplM, T *out, const T *yold, T omega, int j0, int j1) {
+  const int n = L.n, p = L.p, q = L.q;
+  const int jend = j1 < 0 ? n + 1 : j1;
+  const long long total = (long long)(jend - j0) * p;
+  const Vec<const T> R = make_cvec(r, n, p, q);
+  const Vec<T> Y = make_vec(out, n, p, q);
+  const Vec<const T> Yo = make_cvec(yold ? yold : r, n, p, q);
+  auto relax = [&](T x, const T *old, long long at) {
+    if (omega == T(1)) return x;
+    if (yold) {
+      const T o = old[at];
+      return fma(omega, x - o, o);
+    }
+    return x * omega;
+  };
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = j0 + (int)(idx / p), i = (int)(idx % p);
+    const long long at = (long long)j * p + i, atm = (long long)(j - 1) * p + i;
+    if (j == n) {  // the last block holds v, mu of step n - 1 only
+      const T v = bs_v(R, cplU, j, i, p);
+      const T m = v - R.v[atm];
+      Y.v[atm] = relax(v, Yo.v, atm);
+      Y.m[atm] = relax(m, Yo.m, atm);
+      continue;
+    }
+    const CT *N = L.N + j * L.sN, *V = L.V + j * L.sV, *Z = L.Z + j * L.sZ;
+    const T *lam = L.ws_lam + (long long)j * p;
+    const T lm = i > 0 ? lam[i - 1] : T(0), l0 = lam[i], lp = i + 1 < p ? lam[i + 1] : T(0);
+    const T rz = R.z[(long long)j * q + i];
+    const T u = fma(T(-1), bs_mtv<T>(N, i, p, lm, l0, lp), bs_ru(R, cplM, j, i, p));
+    T z, m = T(0), v = T(0);
+    if (j >= 1) v = bs_v(R, cplU, j, i, p);
+    if (L.kappa != T(0)) {
+      const T t = T(1) * bs_mtv<T>(Z, i, p, lm, l0, lp);
+      z = rz - t;
+      if (j >= 1) m = fma(L.kappa, t, v - R.v[atm]);
+    } else {
+      z = fma(T(-1), bs_mtv<T>(Z, i, p, lm, l0, lp), rz);
+      if (j >= 1) {
+        m = v - R.v[atm];
+        m = fma(T(1), bs_mtv<T>(V, i, p, lm, l0, lp), m);
+      }
+    }
+    Y.u[at] = relax(u, Yo.u, at);
+    Y.z[(long long)j * q + i] = relax(z, Yo.z, (long long)j * q + i);
+    Y.l[at] = relax(l0, Yo.l, at);
+    if (j >= 1) {
+      Y.v[atm] = relax(v, Yo.v, atm);
+      Y.m[atm] = relax(m, Yo.m, atm);
+    }
+  }
+}
+
 // Two warps per time block (the same arithmetic split in two, for levels
 // whose blocks do not fill the GPU): warp 0 forms N r_u, warp 1 Z r_z + V v -
 // r_lambda; their sum goes through shared memory to warp 0, which solves the
@@ -943,6 +1082,79 @@ __global__ void __launch_bounds__(128) k_apply_tri(LevelView<T, CT> L, const T *
 #pragma unroll
     for (int e = 0; e < C; ++e) o[e] = b ? fma(sgn, xu[e] - xv[e], o[e]) : xu[e] - xv[e];
     if (own_vm) chunk_store<T, C>(O.m + (long long)t * p, o, p, ln);
+  }
+}
+
+// k_apply_tri for blocks too large for one warp's registers (p > 128): a
+// thread per (step, entry) forms the five rows of that entry with the same
+// operations as k_apply_tri (bitwise the same results); arguments as there.
+template <typename T, typename CT>
+__global__ void __launch_bounds__(256) k_apply_ent(LevelView<T, CT> L, const T *__restrict__ x,
+                                                   const T *__restrict__ b, T *out, const int *guard = nullptr,
+                                                   int j0 = 0, int j1 = -1, T *xcopy = nullptr,
+                                                   const int *xcopy_idx = nullptr, int xcopy_shift = 0) {
+  if (guard && *guard == 0) return;
+  const int n = L.n, p = L.p, q = L.q;
+  const int t0 = max(j0 - 1, 0), tend = j1 < 0 ? n : min(j1, n);
+  const long long total = (long long)(tend - t0) * p;
+  const Vec<const T> X = make_cvec(x, n, p, q);
+  const Vec<T> O = make_vec(out, n, p, q);
+  const T sgn = b ? T(-1) : T(1);
+  const Vec<const T> B = make_cvec(b ? b : x, n, p, q);
+  T *cp = copy_slot(xcopy, xcopy_idx, xcopy_shift, n, p, q);
+  const Vec<T> Cv = make_vec(cp ? cp : out, n, p, q);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int t = t0 + (int)(idx / p), i = (int)(idx % p);
+    const bool own_uzl = t >= j0, own_vm = t + 1 >= j0 && (j1 < 0 || t + 1 < j1);
+    const CT *N = L.N + t * L.sN, *Z = L.Z + t * L.sZ, *Vt = L.V + t * L.sV;
+    const long long at = (long long)t * p + i;
+    auto ld = [&](const T *v, long long base, int k) { return (k < 0 || k >= p) ? T(0) : v[base + k]; };
+    const long long bt = (long long)t * p;
+    const T xu = X.u[at], xv = X.v[at], xz = X.z[(long long)t * q + i], xl = X.l[at], xm = X.m[at];
+    if (cp) {
+      Cv.u[at] = xu;
+      Cv.v[at] = xv;
+      Cv.z[(long long)t * q + i] = xz;
+      Cv.l[at] = xl;
+      Cv.m[at] = xm;
+    }
+    const T xlm = ld(X.l, bt, i - 1), xlp = ld(X.l, bt, i + 1);
+    auto emit = [&](T *o, const T *bb, long long a, T acc) { o[a] = b ? fma(sgn, acc, bb[a]) : acc; };
+    // u row
+    {
+      T acc = xu + xm;
+      acc = fma(T(1), bs_mtv<T>(N, i, p, xlm, xl, xlp), acc);
+      if (own_uzl) emit(O.u, B.u, at, acc);
+    }
+    // v row
+    {
+      T acc = xv - xm;
+      if (t + 1 < n) {
+        const long long b1 = (long long)(t + 1) * p;
+        acc = fma(T(1), bs_mtv<T>(L.V + (t + 1) * L.sV, i, p, ld(X.l, b1, i - 1), X.l[b1 + i], ld(X.l, b1, i + 1)),
+                  acc);
+      }
+      if (own_vm) emit(O.v, B.v, at, acc);
+    }
+    // z row
+    {
+      const T acc = fma(T(1), bs_mtv<T>(Z, i, p, xlm, xl, xlp), xz);
+      if (own_uzl) emit(O.z, B.z, (long long)t * q + i, acc);
+    }
+    // lambda row
+    {
+      const long long bz = (long long)t * q;
+      T acc = T(1) * bs_mv<T>(N, i, p, ld(X.u, bt, i - 1), xu, ld(X.u, bt, i + 1));
+      acc = fma(T(1), bs_mv<T>(Z, i, p, ld(X.z, bz, i - 1), xz, ld(X.z, bz, i + 1)), acc);
+      if (t >= 1) {
+        const long long b0 = (long long)(t - 1) * p;
+        acc = fma(T(1), bs_mv<T>(Vt, i, p, ld(X.v, b0, i - 1), X.v[b0 + i], ld(X.v, b0, i + 1)), acc);
+      }
+      if (own_uzl) emit(O.l, B.l, at, acc);
+    }
+    // mu row
+    if (own_vm) emit(O.m, B.m, at, xu - xv);
   }
 }
 

@@ -9,11 +9,13 @@ vectors = 159 MB) for the Gram-Schmidt kernels.
     python -m paper_2405_04808_gb300.profile_cases train_step
     python -m paper_2405_04808_gb300.profile_cases fgmres_cycle [--basis pair|fp64]
     python -m paper_2405_04808_gb300.profile_cases vcycle [--restrict transpose|inject]
+    python -m paper_2405_04808_gb300.profile_cases vcycle_p512 [--restrict transpose|inject]
 
 vcycle: V-cycles of the benchmark system (Burgers nx=128, nt=1024, 3 levels,
 4/4 sweeps; weighted sweeps omega = 2/3 with the transposed restriction by
 default), one mg_vcycle per repetition, host-driven, so every kernel of the
-cycle launches on its own.
+cycle launches on its own.  vcycle_p512: the same with the large blocks of
+the nx = 512 system (Burgers nx=512, nt=2048, nu = 0.005: p = 512).
 
 Each case runs a warm-up and then `--reps` launches of the kernels it names,
 and exits non-zero on any library error.
@@ -70,7 +72,8 @@ def main(argv=None):
         print(summarize(argv[1], argv[2] if len(argv) > 2 else ""))
         return 0
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step", "fgmres_cycle", "vcycle"])
+    ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step", "fgmres_cycle", "vcycle",
+                                     "vcycle_p512"])
     ap.add_argument("--restrict", default="transpose", choices=["transpose", "inject"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
@@ -80,8 +83,10 @@ def main(argv=None):
 
     from . import pintmg as P
     from . import workloads as W
-    if args.case == "vcycle":
-        prob = W.burgers(nx=128, n=1024, nu=0.01, seed=2000)
+    if args.case in ("vcycle", "vcycle_p512"):
+        # vcycle_p512: the C3 discretisation (nx = 512, nu = 0.005) at nt = 2048 (42 MB per vector)
+        prob = (W.burgers(nx=128, n=1024, nu=0.01, seed=2000) if args.case == "vcycle" else
+                W.burgers(nx=512, n=2048, nu=0.005, seed=3000))
         omega = 2.0 / 3.0 if args.restrict == "transpose" else 1.0
         h = P.mg_setup(prob, levels=3, nu_pre=4, nu_post=4, omega=omega, restrict=args.restrict,
                        device_loops=False)

@@ -72,13 +72,21 @@ typedef enum {
  */
 typedef enum {
   MG_BASIS_FP64 = 0,  /* FP64 vectors; dot products and axpys in FP64 (the default) */
-  MG_BASIS_PAIR = 1   /* each entry as two FP32 values hi + lo (the FP64 value rounded to ~48 bits, 8 bytes);
+  MG_BASIS_PAIR = 1,  /* each entry as two FP32 values hi + lo (the FP64 value rounded to ~48 bits, 8 bytes);
                          dot products and axpys against the basis in compensated FP32 arithmetic (error-free
                          products and sums of Ogita, Rump and Oishi's Dot2) with FP64 reductions; on GB300,
                          whose FP64 rate bounds the FP64 kernels, these kernels run about 1.5x faster (the C2
                          solve 1.2x).  Requires an even vector length n (4p+q), else the FP64 basis is used.
                          Its streamed dot products wait on shared-memory barriers for at most 2 s each; a
                          wait that runs out makes the solve return MG_ERR_TIMEOUT */
+  MG_BASIS_PAIR_DCGS2 = 2 /* the pair basis orthogonalised by delayed reorthogonalisation (DCGS2, Bielich et
+                         al. 2022): at step j one pass over the basis forms V^T u and V^T w (u: the previous
+                         step's vector, not yet reorthogonalised) and one pass writes the final V_j and the
+                         projected w, half of classical Gram-Schmidt twice's four passes; column j - 1 of the
+                         Hessenberg matrix is completed, rotated and tested one step late, so a converging
+                         cycle runs one more preconditioner application, and a cycle that ends full runs one
+                         more dot-product pass.  Requires what MG_BASIS_PAIR requires, else the FP64 basis
+                         (with classical Gram-Schmidt twice) is used */
 } mg_krylov_basis;
 
 /*

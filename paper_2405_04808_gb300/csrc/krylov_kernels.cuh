@@ -188,15 +188,16 @@ __global__ void __launch_bounds__(kDotThreads) k_multidot_blocked(const double *
 
 // out[i] (+)= sum_g partial[i * G + g], fixed order.  One warp per i.  With
 // vb > 0, G = dot_parts(m, vb, len) (the partition of k_multidot_blocked).
+// nr > 1: nr right-hand sides' sums of the same partition, out[r m + i]
 __global__ void k_reduce_partials(const double *__restrict__ partial, int G, int m, double *out, int accumulate,
                                   const int *gate = nullptr, const int *m_dev = nullptr, int vb = 0,
-                                  long long len = 0) {
+                                  long long len = 0, int nr = 1) {
   if (gate && *gate == 0) return;
   if (m_dev) m = *m_dev;
   if (vb > 0) G = dot_parts(m, vb, len);
   const int i = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const int ln = threadIdx.x & (kWarp - 1);
-  if (i >= m) return;
+  if (i >= m * nr) return;
   double s = 0.0;
   for (int g = ln; g < G; g += kWarp) s += partial[(long long)i * G + g];
 #pragma unroll
@@ -445,6 +446,66 @@ __global__ void k_backsolve(int k, const double *__restrict__ H, int ldh, const 
     const double *col = H + (long long)i * ldh;
     for (int r = threadIdx.x; r < i; r += blockDim.x) gs[r] = fma(-col[r], yi, gs[r]);
     __syncthreads();
+  }
+}
+
+// start of a DCGS2 cycle: eta = ||r|| (scal[0]), 1 / eta (scal[1])
+__global__ void k_dcgs2_start(const double *__restrict__ scal, double *dc, const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
+  if (threadIdx.x == 0) {
+    dc[3] = scal[0];
+    dc[0] = scal[1];
+  }
+}
+
+// DCGS2 step j (one warp; j from j_dev when given).  out: the pass's dot
+// products, out[i] = V_i . u and out[j + i] = V_i . w (i < j); dc as in
+// k_multi_axpy2_pair, with dc[4] = u . w.  With s = out[0..j) / eta and
+// nu = (1 - |s|^2)^(1/2):
+//   j >= 1: column j - 1 of H becomes hp + eta s with H[j][j-1] = eta nu, and
+//           is rotated (arnoldi_column: scal[0] = |g_j|, the residual estimate
+//           of the first j columns);
+//   close == 0: the coefficients of the update pass, c1 = s, c2 = t =
+//           out[j..2j), dc[1] = 1 / nu, dc[2] = h_j = (u . w / eta - s . t) / nu,
+//           and the pending column j, hp = (t, h_j).
+// close = 1 ends a cycle: only column j - 1 (out[j..) is not read).  A
+// non-positive 1 - |s|^2 makes nu NaN (breakdown, seen in the estimate).
+__global__ void k_dcgs2_coef(int j, const int *j_dev, const double *__restrict__ out, double *dc, double *c1,
+                             double *c2, double *hp, double *H, int ldh, double *cs, double *sn, double *g,
+                             double *scal, int close, const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
+  if (j_dev) j = *j_dev;
+  if (threadIdx.x >= kWarp) return;
+  const int ln = threadIdx.x;
+  __shared__ double hcol[512];
+  const double inv_eta = dc[0], eta = dc[3];
+  double ss = 0.0, st = 0.0;
+  for (int i = ln; i < j; i += kWarp) {
+    const double si = out[i] * inv_eta;
+    ss = fma(si, si, ss);
+    if (!close) st = fma(si, out[j + i], st);
+    hcol[i] = fma(eta, si, hp[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(kFull, ss, o);
+    st += __shfl_xor_sync(kFull, st, o);
+  }
+  const double nu2 = 1.0 - ss;
+  const double nu = nu2 > 0.0 ? sqrt(nu2) : __longlong_as_double(0x7FF8000000000000LL);
+  __syncwarp();
+  if (j >= 1) arnoldi_column(j - 1, hcol, eta * eta * nu2, H, ldh, cs, sn, g, scal, ln);
+  if (close) return;
+  for (int i = ln; i < j; i += kWarp) {
+    c1[i] = out[i] * inv_eta;
+    c2[i] = out[j + i];
+    hp[i] = out[j + i];
+  }
+  if (ln == 0) {
+    const double hj = (dc[4] * inv_eta - st) / nu;
+    hp[j] = hj;
+    dc[1] = 1.0 / nu;
+    dc[2] = hj;
   }
 }
 

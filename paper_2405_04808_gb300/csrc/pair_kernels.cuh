@@ -167,6 +167,106 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_axpy_pair(double *y, cons
 }
 
 // ---------------------------------------------------------------------------
+// Delayed reorthogonalisation (DCGS2; Bielich, Langou, Thomas, Swirydowicz,
+// Yamazaki and Boman, Parallel Computing 2022) on the pair basis.  At Arnoldi
+// step j the basis holds the final orthonormal V_0 .. V_{j-1} and, in slot j,
+// the tentative vector vt_j = u / eta of the previous step (u its FP64 copy,
+// eta = ||u||); w = A z_j.  One pass over V_0 .. V_{j-1} forms
+// s' = V^T u and t = V^T w (k_multidot_pair_tma with two right-hand sides),
+// k_dcgs2_coef finishes column j - 1 of the Hessenberg matrix with s = s' /
+// eta and nu = (1 - |s|^2)^(1/2) (u's component outside the basis) and forms
+// h_j = (vt_j . w - s . t) / nu, and one more pass (k_multi_axpy2_pair) writes
+// the final V_j = (vt_j - V s) / nu and w' = w - V t - h_j V_j: two passes over
+// the basis per step instead of CGS2's four.
+//
+// dc: the step's scalars, [0] 1 / eta, [1] 1 / nu, [2] h_j, [3] eta, [4]
+// u . w (FP64 dot product of the step), [5] ||w'||^2.
+
+// y = u dc[0] - sum_i s_i V_i, scaled by dc[1], into basis slot m (m = the
+// final vectors, read from m_dev when given) as a pair; then u = w - sum_i t_i V_i
+// - dc[2] y (FP64) and the CTA's partial sum of u^2; the last CTA (ticket)
+// reduces the partials into dc[5], dc[3] = ||u||, dc[0] = 1 / ||u||.  s, t:
+// the coefficients (m each), scaled per CTA by powers of two and split as in
+// k_multi_axpy_pair.  len and ldx even, u, w, V 16-byte aligned; m <= 512.
+__global__ void __launch_bounds__(kDotThreads) k_multi_axpy2_pair(float2 *V, long long ldx, const double *__restrict__ s,
+                                                                  const double *__restrict__ t, int m, double *u,
+                                                                  const double *__restrict__ w, long long len,
+                                                                  double *dc, double *partial, unsigned *ticket,
+                                                                  const int *gate, const int *m_dev) {
+  if (gate && *gate == 0) return;
+  if (m_dev) m = *m_dev;
+  __shared__ float2 cs1[512], cs2[512];
+  __shared__ unsigned cmax[2][kDotThreads / kWarp];
+  unsigned e1 = 0, e2 = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    e1 = max(e1, f64_exponent(s[i]));
+    e2 = max(e2, f64_exponent(t[i]));
+  }
+  e1 = __reduce_max_sync(kFull, e1);
+  e2 = __reduce_max_sync(kFull, e2);
+  if ((threadIdx.x & (kWarp - 1)) == 0) {
+    cmax[0][threadIdx.x / kWarp] = e1;
+    cmax[1][threadIdx.x / kWarp] = e2;
+  }
+  __syncthreads();
+  unsigned emax1 = 0, emax2 = 0;
+#pragma unroll
+  for (int i = 0; i < kDotThreads / kWarp; ++i) {
+    emax1 = max(emax1, cmax[0][i]);
+    emax2 = max(emax2, cmax[1][i]);
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    cs1[i] = split48(s[i], (int)emax1 - 127);
+    cs2[i] = split48(t[i], (int)emax2 - 127);
+  }
+  __syncthreads();
+  const double sc1 = pow2_of_exponent(emax1), sc2 = pow2_of_exponent(emax2);
+  const double inv_eta = dc[0], inv_nu = dc[1], hj = dc[2];
+  float4 *slot = reinterpret_cast<float4 *>(V + (long long)m * ldx);
+  double2 *u2 = reinterpret_cast<double2 *>(u);
+  const double2 *w2 = reinterpret_cast<const double2 *>(w);
+  double sq = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len / 2;
+       idx += (long long)gridDim.x * blockDim.x) {
+    float a0 = 0.f, ca0 = 0.f, a1 = 0.f, ca1 = 0.f, b0 = 0.f, cb0 = 0.f, b1 = 0.f, cb1 = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) {
+      const float4 x = reinterpret_cast<const float4 *>(V + i * ldx)[idx];
+      const float2 p = cs1[i], q = cs2[i];
+      dot2_step(a0, ca0, x.x, x.y, p.x, p.y);
+      dot2_step(a1, ca1, x.z, x.w, p.x, p.y);
+      dot2_step(b0, cb0, x.x, x.y, q.x, q.y);
+      dot2_step(b1, cb1, x.z, x.w, q.x, q.y);
+    }
+    const double2 uv = u2[idx], wv = w2[idx];
+    const double y0 = (uv.x * inv_eta - sc1 * ((double)a0 + (double)ca0)) * inv_nu;
+    const double y1 = (uv.y * inv_eta - sc1 * ((double)a1 + (double)ca1)) * inv_nu;
+    const float2 p0 = split48(y0, 896), p1 = split48(y1, 896);
+    slot[idx] = make_float4(p0.x, p0.y, p1.x, p1.y);
+    double2 nu;
+    nu.x = fma(-hj, y0, fma(-sc2, (double)b0 + (double)cb0, wv.x));
+    nu.y = fma(-hj, y1, fma(-sc2, (double)b1 + (double)cb1, wv.y));
+    u2[idx] = nu;
+    sq = fma(nu.x, nu.x, sq);
+    sq = fma(nu.y, nu.y, sq);
+  }
+  const double tt = block_sum(sq);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tt;
+  if (last_cta(ticket)) {
+    if (threadIdx.x < kWarp) {
+      const double n2 = warp_partial_sum(partial, gridDim.x, 0, threadIdx.x);
+      if (threadIdx.x == 0) {
+        const double eta = sqrt(n2);
+        dc[5] = n2;
+        dc[3] = eta;
+        dc[0] = eta > 0.0 ? 1.0 / eta : 0.0;
+      }
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Multi-dot products against the pair basis with the basis streamed into
 // shared memory by bulk asynchronous copies (TMA, cp.async.bulk) through a
 // ring of NS stages, each holding kPairStageLen entries of VB basis
@@ -188,9 +288,10 @@ __host__ __device__ inline long long pair_chunk(long long len, int G) {
   return (c + 1) & ~1ll;
 }
 
-template <int VB, int NS>
+template <int VB, int NS, int NR = 1>
 __host__ __device__ constexpr size_t pair_tma_smem() {
-  return (size_t)NS * kPairStageLen * (VB * sizeof(float2) + sizeof(double)) + 2 * NS * sizeof(unsigned long long);
+  return (size_t)NS * kPairStageLen * (VB * sizeof(float2) + NR * sizeof(double)) +
+         2 * NS * sizeof(unsigned long long);
 }
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
@@ -246,19 +347,23 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 // exponent seen so far); when a stage raises it, the FP32 accumulators are
 // rescaled by the (exact) power of two.  A wait that runs out sets err[0];
 // later launches with err[0] set return at once.
-template <int VB, int NS, int kMinBlocks>
+// NR = 2: a second right-hand side w2 streamed beside w (DCGS2's pass over the
+// basis, Q^T [u, w]); the partial sums of w2 follow those of w:
+// partial[(r m + i) G + g] for right-hand side r.
+template <int VB, int NS, int kMinBlocks, int NR = 1>
 __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
     k_multidot_pair_tma(const float2 *__restrict__ V, long long ldv, int m, const double *__restrict__ w, long long len,
-                        double *partial, const int *gate, const int *m_dev, int *err, int stall = 0) {
+                        double *partial, const int *gate, const int *m_dev, int *err, int stall = 0,
+                        const double *__restrict__ w2 = nullptr) {
   if (gate && *gate == 0) return;
   if (*(volatile int *)err) return;  // an earlier launch of this solve timed out: its results are void anyway
   if (m_dev) m = *m_dev;
   extern __shared__ __align__(128) unsigned char pair_smem[];
   float2 *sv = reinterpret_cast<float2 *>(pair_smem);  // [stage][VB][kPairStageLen]
-  double *sw = reinterpret_cast<double *>(sv + (size_t)NS * VB * kPairStageLen);  // [stage][len]
-  unsigned long long *full = reinterpret_cast<unsigned long long *>(sw + (size_t)NS * kPairStageLen);
+  double *sw = reinterpret_cast<double *>(sv + (size_t)NS * VB * kPairStageLen);  // [stage][NR][len]
+  unsigned long long *full = reinterpret_cast<unsigned long long *>(sw + (size_t)NS * NR * kPairStageLen);
   unsigned long long *empty = full + NS;
-  __shared__ double red[kPairConsumers][VB];
+  __shared__ double red[kPairConsumers][NR][VB];
   __shared__ int abort_flag;
   const int G = dot_parts(m, VB, len);
   const long long C = pair_chunk(len, G);
@@ -295,8 +400,11 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
             break;
           }
           const unsigned ne = (unsigned)min((long long)kPairStageLen, c1 - pos);
-          mbar_expect_tx(&full[slot], ne * (unsigned)(nv * sizeof(float2) + sizeof(double)));
-          bulk_load(sw + (size_t)slot * kPairStageLen, w + pos, ne * (unsigned)sizeof(double), &full[slot], keep);
+          mbar_expect_tx(&full[slot], ne * (unsigned)(nv * sizeof(float2) + NR * sizeof(double)));
+          bulk_load(sw + (size_t)slot * NR * kPairStageLen, w + pos, ne * (unsigned)sizeof(double), &full[slot], keep);
+          if (NR == 2)
+            bulk_load(sw + ((size_t)slot * NR + 1) * kPairStageLen, w2 + pos, ne * (unsigned)sizeof(double),
+                      &full[slot], keep);
           for (int v = 0; v < nv; ++v)
             bulk_load(sv + ((size_t)slot * VB + v) * kPairStageLen, V + (long long)(vb + v) * ldv + pos,
                       ne * (unsigned)sizeof(float2), &full[slot], policy);
@@ -325,10 +433,14 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
     const int vb = (item / G) * VB, g = item % G;
     const int nv = min(VB, m - vb);
     const long long c0 = g * C, c1 = min(len, c0 + C);
-    float s[VB], c[VB];
+    float s[NR][VB], c[NR][VB];
 #pragma unroll
-    for (int v = 0; v < VB; ++v) s[v] = c[v] = 0.0f;
-    unsigned emax = 0;
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int v = 0; v < VB; ++v) s[r][v] = c[r][v] = 0.0f;
+    unsigned emax[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) emax[r] = 0;
     for (long long pos = c0; pos < c1; pos += kPairStageLen, ++q) {
       const int slot = (int)(q % NS);
       const unsigned use = (unsigned)(q / NS);
@@ -344,32 +456,35 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
       const int ne = (int)min((long long)kPairStageLen, c1 - pos);
       const int e0 = 2 * ln + 2 * kWarp * wp;  // this thread's two entries of the stage
       const bool mine = e0 < ne;
-      double2 wv = make_double2(0.0, 0.0);
-      if (mine) wv = reinterpret_cast<const double2 *>(sw + (size_t)slot * kPairStageLen)[e0 / 2];
-      const unsigned en = __reduce_max_sync(kFull, max(f64_exponent(wv.x), f64_exponent(wv.y)));
-      if (en > emax) {
-        if (emax != 0) {
-          const unsigned d = en - emax;
-          const float f = d > 120 ? 0.0f : __int_as_float((int)(127 - d) << 23);
 #pragma unroll
-          for (int v = 0; v < VB; ++v) {
-            s[v] = __fmul_rn(s[v], f);
-            c[v] = __fmul_rn(c[v], f);
+      for (int r = 0; r < NR; ++r) {
+        double2 wv = make_double2(0.0, 0.0);
+        if (mine) wv = reinterpret_cast<const double2 *>(sw + ((size_t)slot * NR + r) * kPairStageLen)[e0 / 2];
+        const unsigned en = __reduce_max_sync(kFull, max(f64_exponent(wv.x), f64_exponent(wv.y)));
+        if (en > emax[r]) {
+          if (emax[r] != 0) {
+            const unsigned d = en - emax[r];
+            const float f = d > 120 ? 0.0f : __int_as_float((int)(127 - d) << 23);
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+              s[r][v] = __fmul_rn(s[r][v], f);
+              c[r][v] = __fmul_rn(c[r][v], f);
+            }
           }
+          emax[r] = en;
         }
-        emax = en;
-      }
-      if (mine) {
-        const int eoff = (int)emax - 127;
-        const float2 a0 = split48(wv.x, eoff), a1 = split48(wv.y, eoff);
-        const float2 *base = sv + (size_t)slot * VB * kPairStageLen;
+        if (mine) {
+          const int eoff = (int)emax[r] - 127;
+          const float2 a0 = split48(wv.x, eoff), a1 = split48(wv.y, eoff);
+          const float2 *base = sv + (size_t)slot * VB * kPairStageLen;
 #pragma unroll
-        for (int v = 0; v < VB; ++v)
-          if (v < nv) {
-            const float4 x = reinterpret_cast<const float4 *>(base + (size_t)v * kPairStageLen)[e0 / 2];
-            dot2_step(s[v], c[v], x.x, x.y, a0.x, a0.y);
-            dot2_step(s[v], c[v], x.z, x.w, a1.x, a1.y);
-          }
+          for (int v = 0; v < VB; ++v)
+            if (v < nv) {
+              const float4 x = reinterpret_cast<const float4 *>(base + (size_t)v * kPairStageLen)[e0 / 2];
+              dot2_step(s[r][v], c[r][v], x.x, x.y, a0.x, a0.y);
+              dot2_step(s[r][v], c[r][v], x.z, x.w, a1.x, a1.y);
+            }
+        }
       }
       __syncwarp();
       if (ln == 0) mbar_arrive(&empty[slot]);
@@ -381,24 +496,28 @@ __global__ void __launch_bounds__(kPairTmaThreads, kMinBlocks)
         *(volatile int *)&abort_flag = 1;
       }
     }
-    const double scale = pow2_of_exponent(emax);
 #pragma unroll
-    for (int v = 0; v < VB; ++v) {
-      float svv = s[v], cvv = c[v];
-      if (v < nv) {
+    for (int r = 0; r < NR; ++r) {
+      const double scale = pow2_of_exponent(emax[r]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float s2 = __shfl_down_sync(kFull, svv, o), c2 = __shfl_down_sync(kFull, cvv, o);
-          ds_add(svv, cvv, s2, c2);
+      for (int v = 0; v < VB; ++v) {
+        float svv = s[r][v], cvv = c[r][v];
+        if (v < nv) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_down_sync(kFull, svv, o), c2 = __shfl_down_sync(kFull, cvv, o);
+            ds_add(svv, cvv, s2, c2);
+          }
         }
+        if (ln == 0) red[wp][r][v] = ((double)svv + (double)cvv) * scale;
       }
-      if (ln == 0) red[wp][v] = ((double)svv + (double)cvv) * scale;
     }
     asm volatile("bar.sync 1, %0;\n" ::"n"(kPairConsumers * kWarp) : "memory");
-    if (threadIdx.x < nv) {
+    if (threadIdx.x < NR * VB && threadIdx.x % VB < nv) {
+      const int r = threadIdx.x / VB, v = threadIdx.x % VB;
       double sum = 0.0;
-      for (int i = 0; i < kPairConsumers; ++i) sum += red[i][threadIdx.x];
-      partial[(long long)(vb + threadIdx.x) * G + g] = sum;
+      for (int i = 0; i < kPairConsumers; ++i) sum += red[i][r][v];
+      partial[((long long)r * m + vb + v) * G + g] = sum;
     }
     asm volatile("bar.sync 1, %0;\n" ::"n"(kPairConsumers * kWarp) : "memory");
   }

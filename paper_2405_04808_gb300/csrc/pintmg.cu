@@ -210,6 +210,9 @@ struct mg_handle {
   // chose, 1 = one warp per block, 2 = two warps per block; absent: the size rule
   std::map<int, int> bs_map;
   int pair_basis = 0;   // the FGMRES basis as FP32 pairs with compensated dot products (MG_BASIS_PAIR)
+  int dcgs2 = 0;        // ... orthogonalised by delayed reorthogonalisation (MG_BASIS_PAIR_DCGS2)
+  double *fu = nullptr;   // DCGS2: FP64 copy of the tentative basis vector (unnormalised)
+  double *dcg = nullptr;  // DCGS2: coefficients, pending Hessenberg column, scalars (kDc* offsets)
   int pair_stall = 0;   // failure-detection tests: the streamed multi-dot issues no copies (its waits run out)
   int device = -1;      // the CUDA device current at mg_setup; every device buffer of the handle lives there
   int persist_sweeps = 0;  // smoothing levels that fit on the GPU run all their sweeps in one launch
@@ -665,6 +668,9 @@ void read_scal(mg_handle *h, const mg_handle::Krylov &K, cudaStream_t s) {
 // the TMA-streamed multi-dot kernel of the pair basis: 8 vectors per item,
 // 3 stages, 2 CTAs per SM
 constexpr int kPairVB = 8, kPairNS = 3, kPairCtas = 2;
+// layout of h->dcg: update coefficients s and t, the pending Hessenberg column, the step's scalars
+constexpr int kDcC1 = 0, kDcC2 = 512, kDcHp = 1024, kDcS = 1600, kDcLen = 2048;
+constexpr int kPairNS2 = 2;  // stages of the two-right-hand-side pass (DCGS2): 2 CTAs per SM still fit
 void pair_prepare() {
   static unsigned done = 0;
   int dev = 0;
@@ -672,6 +678,8 @@ void pair_prepare() {
   if (dev < 32 && (done >> dev) & 1u) return;
   ck(cudaFuncSetAttribute(k_multidot_pair_tma<kPairVB, kPairNS, kPairCtas>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_tma_smem<kPairVB, kPairNS>()));
+  ck(cudaFuncSetAttribute(k_multidot_pair_tma<kPairVB, kPairNS2, kPairCtas, 2>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_tma_smem<kPairVB, kPairNS2, 2>()));
   if (dev < 32) done |= 1u << dev;
 }
 
@@ -691,6 +699,35 @@ void multidot_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const d
     k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, 0, m, out, 0, nullptr, m_dev, kPairVB, len);
     ck_launch();
   }
+}
+
+// DCGS2's pass over the m final pair vectors: out[i] = V_i . u, out[m + i] = V_i . w (fixed order)
+void multidot2_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const double *u, const double *w,
+                    long long len, double *out, cudaStream_t s, const int *m_dev = nullptr) {
+  const int items = std::max(1, ((m + kPairVB - 1) / kPairVB) * dot_parts(m, kPairVB, len));
+  const int grid = std::min(items, kPairCtas * 152);
+  {
+    Bracket br(h, CAT_PAIR_DOT, s, 8.0 * (m + 2) * len, 4.0 * m * len);
+    k_multidot_pair_tma<kPairVB, kPairNS2, kPairCtas, 2>
+        <<<grid, kPairTmaThreads, pair_tma_smem<kPairVB, kPairNS2, 2>(), s>>>(
+            Vp, ldv, m, u, len, h->partial, nullptr, m_dev, h->flag + 2, h->pair_stall, w);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_reduce_partials<<<(2 * m + 3) / 4 + 1, 128, 0, s>>>(h->partial, 0, m, out, 0, nullptr, m_dev, kPairVB, len, 2);
+    ck_launch();
+  }
+}
+
+// DCGS2's update pass (k_multi_axpy2_pair) over the m final pair vectors
+void multi_axpy2_pair(mg_handle *h, float2 *Vp, long long len, int m, double *u, const double *w, double *dcg,
+                      cudaStream_t s, const int *m_dev = nullptr, const int *gate = nullptr) {
+  const int G = grid_for(len / 2, kDotThreads, kDotGridCap);
+  Bracket br(h, CAT_PAIR_AXPY, s, 8.0 * (m + 4) * len, 4.0 * m * len);
+  k_multi_axpy2_pair<<<G, kDotThreads, 0, s>>>(Vp, len, dcg + kDcC1, dcg + kDcC2, m, u, w, len, dcg + kDcS,
+                                               h->partial, h->ticket + 2, gate, m_dev);
+  ck_launch();
 }
 
 // CGS2 against the basis V (FP64) or Vp (pairs, when not null): K.h = the
@@ -1608,6 +1645,10 @@ void ensure_fgmres_space(mg_handle *h, int m, cudaStream_t s) {
   };
   h->fV = grab((size_t)(m + 1) * len);
   h->fZ = grab((size_t)m * len);
+  if (h->dcgs2) {
+    h->fu = grab((size_t)len);
+    h->dcg = grab((size_t)kDcLen);
+  }
   h->fm = m;
 }
 
@@ -2004,7 +2045,8 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
   if (!(O->omega > 0.0 && O->omega <= 1.0)) return MG_ERR_ARG;
   if (O->coarse_precond < MG_COARSE_SGS || O->coarse_precond > MG_COARSE_BGS) return MG_ERR_ARG;
   if (O->device_loops != 0 && O->device_loops != 1) return MG_ERR_ARG;
-  if (O->krylov_basis != MG_BASIS_FP64 && O->krylov_basis != MG_BASIS_PAIR) return MG_ERR_ARG;
+  if (O->krylov_basis != MG_BASIS_FP64 && O->krylov_basis != MG_BASIS_PAIR && O->krylov_basis != MG_BASIS_PAIR_DCGS2)
+    return MG_ERR_ARG;
   if (O->restrict_rule != MG_RESTRICT_INJECT && O->restrict_rule != MG_RESTRICT_TRANSPOSE) return MG_ERR_ARG;
   if (n % (1 << (O->levels - 1)) != 0) return MG_ERR_ARG;
   if (O->levels > 1 && P->separable != 1) {
@@ -2081,7 +2123,9 @@ int mg_setup(const mg_problem *P, const mg_options *O, void *stream, mg_handle *
     ck(cudaMallocHost(&h->host_scal, 4 * sizeof(double)));
     tri_stage_prepare();
     // the pair basis streams two entries per 16-byte load: even vector lengths only
-    h->pair_basis = O->krylov_basis == MG_BASIS_PAIR && ((long long)n * (4 * p + q)) % 2 == 0;
+    h->pair_basis = (O->krylov_basis == MG_BASIS_PAIR || O->krylov_basis == MG_BASIS_PAIR_DCGS2) &&
+                    ((long long)n * (4 * p + q)) % 2 == 0;
+    h->dcgs2 = h->pair_basis && O->krylov_basis == MG_BASIS_PAIR_DCGS2;
     if (h->pair_basis) pair_prepare();
     // raw data on the device (FP64)
     double *dM = h->mem.alloc<double>(msz);
@@ -2404,7 +2448,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       b = h->fb_stage;
     }
     double *x = x_dev ? x_out : h->fx_stage;
-    if (h->opts.device_loops) {
+    if (h->opts.device_loops && !h->dcgs2) {  // (DCGS2 runs host-driven loops)
       // one CUDA graph per solve: loops on the device, one read-back at the end
       if (!h->gexec || h->gkey.b != b || h->gkey.x != x || h->gkey.rtol != rtol || h->gkey.maxit != maxit ||
           h->gkey.restart != m || h->gkey.gen != h->gen) {
@@ -2459,7 +2503,103 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
     if (bnorm > 0.0) {
       const double *r = b;
       bool done = false;
-      while (!done && total < maxit) {
+      while (!done && total < maxit && h->dcgs2) {
+        // DCGS2 cycle (pair basis): slot 0 = r / ||r|| is the tentative v_0, u = r, eta = ||r||
+        double *dc = h->dcg + kDcS;
+        norm_into(h, K, r, len, s);
+        {
+          Bracket br(h, CAT_SMALL, s);
+          k_dcgs2_start<<<1, 32, 0, s>>>(K.scal, dc);
+          ck_launch();
+        }
+        ck(cudaMemcpyAsync(h->fu, r, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        {
+          Bracket br(h, CAT_AXPY, s);
+          k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, r, dc, len);
+          ck_launch();
+        }
+        {
+          Bracket br(h, CAT_SMALL, s);
+          k_arnoldi_init<<<1, 128, 0, s>>>(K.scal, K.g, m);
+          ck_launch();
+        }
+        const int mm = std::min(m, maxit - total);
+        int k = 0;
+        bool lag_closed = false;  // the cycle ended at a column finished by a step (no closing pass)
+        for (int j = 0; j < mm; ++j) {
+          double *zj = h->fZ + (long long)j * len;
+          {
+            Bracket br(h, CAT_SMALL, s);
+            k_join_basis<<<grid_for(len, 256), 256, 0, s>>>(h->vin, Vp + (long long)j * len, len);
+            ck_launch();
+          }
+          precondition(h, h->vin, zj, s);
+          launch_apply<double>(h, h->lv[0].d.view, zj, nullptr, h->fw, s);
+          multidot2_pair(h, Vp, len, j, h->fu, h->fw, len, K.h, s);
+          multidot(h, h->fu, len, 1, h->fw, len, dc + 4, 0, s);
+          {
+            Bracket br(h, CAT_SMALL, s);
+            k_dcgs2_coef<<<1, 32, 0, s>>>(j, nullptr, K.h, dc, h->dcg + kDcC1, h->dcg + kDcC2, h->dcg + kDcHp, K.H,
+                                          h->ldh, K.cs, K.sn, K.g, K.scal, 0);
+            ck_launch();
+          }
+          if (j >= 1) {  // column j - 1 is final: its residual estimate
+            read_scal(h, K, s);
+            k = j;
+            const double est = h->host_scal[0], hj1 = h->host_scal[2];
+            if (!std::isfinite(est) || !std::isfinite(hj1)) {
+              status = MG_ERR_BREAKDOWN;
+              done = true;
+              lag_closed = true;
+              break;
+            }
+            est_rel = est / bnorm;
+            if (est <= rtol * bnorm || hj1 == 0.0) {
+              done = true;
+              lag_closed = true;
+              break;
+            }
+          }
+          multi_axpy2_pair(h, Vp, len, j, h->fu, h->fw, h->dcg, s);
+          {
+            Bracket br(h, CAT_AXPY, s);
+            k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp + (long long)(j + 1) * len, h->fu, dc, len);
+            ck_launch();
+          }
+        }
+        if (status != MG_OK) break;
+        if (!lag_closed) {  // finish the last column: one pass of V^T u
+          k = mm;
+          multidot_pair(h, Vp, len, k, h->fu, len, K.h, s);
+          {
+            Bracket br(h, CAT_SMALL, s);
+            k_dcgs2_coef<<<1, 32, 0, s>>>(k, nullptr, K.h, dc, h->dcg + kDcC1, h->dcg + kDcC2, h->dcg + kDcHp,
+                                          K.H, h->ldh, K.cs, K.sn, K.g, K.scal, 1);
+            ck_launch();
+          }
+          read_scal(h, K, s);
+          const double est = h->host_scal[0], hj1 = h->host_scal[2];
+          if (!std::isfinite(est) || !std::isfinite(hj1)) {
+            status = MG_ERR_BREAKDOWN;
+            break;
+          }
+          est_rel = est / bnorm;
+          if (est <= rtol * bnorm || hj1 == 0.0) done = true;
+        }
+        total += k;
+        if (total >= maxit) done = true;
+        {
+          Bracket br(h, CAT_SMALL, s);
+          k_backsolve<<<1, 256, (size_t)k * sizeof(double), s>>>(k, K.H, h->ldh, K.g, K.ycoef);
+          ck_launch();
+        }
+        multi_axpy(h, x, h->fZ, len, K.ycoef, k, 1.0, len, s);
+        if (!done) {
+          launch_apply<double>(h, h->lv[0].d.view, x, b, h->fr, s);
+          r = h->fr;
+        }
+      }
+      while (!done && total < maxit && !h->dcgs2) {
         // beta = ||r||, v_0 = r / beta
         norm_into(h, K, r, len, s);
         {

@@ -35,7 +35,7 @@ MG_PRECISION_FP32_SMOOTH = 2
 MG_PRECISION_BF16_BANDS = 3
 COARSE_PRECOND = {"sgs": 0, "jacobi": 1, "fgs": 2, "bgs": 3}
 #: storage of the FGMRES basis (mg_krylov_basis)
-KRYLOV_BASIS = {"fp64": 0, "pair": 1}
+KRYLOV_BASIS = {"fp64": 0, "pair": 1, "pair_dcgs2": 2}
 #: residual restriction of the V-cycle (mg_restrict_rule)
 RESTRICT = {"inject": 0, "transpose": 1}
 

@@ -525,6 +525,10 @@ struct KState {
   int breakdown;  // non-finite Hessenberg entry
   int converged;
   int pad;
+  int go;         // DCGS2: the step's update pass runs (the cycle did not end at its lagged column)
+  int close;      // DCGS2: the cycle ends with the closing pass over V^T u
+  int bodies;     // DCGS2: loop bodies executed in this solve (a step that ends a cycle adds no column)
+  int pad2;
   long long calls;      // solves since setup
   long long iters_all;  // iterations summed over calls
   double bnorm, rtol;
@@ -536,6 +540,9 @@ struct KState {
 __global__ void k_ctl_start(KState *st, const double *scal, double rtol, cudaGraphConditionalHandle h,
                             const int *admitted = nullptr) {
   const double beta = scal[0];
+  st->go = 0;
+  st->close = 0;
+  st->bodies = 0;
   st->j = 0;
   st->m1 = 1;
   st->total = 0;
@@ -572,6 +579,83 @@ __global__ void k_ctl_step(KState *st, const double *scal, int cycle, int maxit,
   st->done = (bad || conv || last) ? 1 : 0;
   st->restart = (st->cycle_end && !st->done) ? 1 : 0;
   if (set_here) cudaGraphSetConditional(h, st->cycle_end ? 0u : 1u);
+}
+
+// DCGS2, after k_dcgs2_coef of step j (graph-captured solves): j >= 1 has
+// just finished column j - 1 (scal: [0] |g_j|, [2] its subdiagonal); a
+// converged or broken-down column ends the cycle with j columns (no update
+// pass, no closing pass).  Otherwise the update pass runs (go) and, when this
+// step fills the cycle (j + 1 = cycle) or reaches the iteration cap, the
+// closing pass follows (close).  total counts finished columns.
+__global__ void k_dcgs2_ctl(KState *st, const double *scal, int cycle, int maxit) {
+  const int j = st->j;
+  st->bodies += 1;
+  st->go = 1;
+  st->close = 0;
+  st->cycle_end = 0;
+  st->restart = 0;
+  // every body either finishes a column or ends a cycle, so a solve needs at most about
+  // 2 maxit bodies; past that the loop ends as a breakdown rather than running on
+  if (st->bodies > 2 * maxit + 64) {
+    st->breakdown = 1;
+    st->converged = 0;
+    st->kcount = j;
+    st->go = 0;
+    st->cycle_end = 1;
+    st->done = 1;
+    return;
+  }
+  if (j >= 1) {
+    const double est = scal[0], hj1 = scal[2];
+    st->est = est;
+    const bool bad = !isfinite(est) || !isfinite(hj1);
+    const bool conv = !bad && (est <= st->rtol * st->bnorm || hj1 == 0.0);
+    if (bad || conv) {
+      st->breakdown = bad ? 1 : 0;
+      st->converged = conv ? 1 : 0;
+      st->kcount = j;
+      st->total += j;
+      st->iters_all += j;
+      st->go = 0;
+      st->cycle_end = 1;
+      st->done = 1;
+      st->restart = 0;
+      return;
+    }
+  }
+  if (j + 1 >= cycle || st->total + j + 1 >= maxit) {
+    st->close = 1;
+    st->cycle_end = 1;
+  }
+}
+
+// DCGS2: after a step's update pass, one more final basis vector
+__global__ void k_dcgs2_adv(KState *st) {
+  if (st->go) st->j += 1;
+}
+
+// DCGS2: after the closing pass (k_dcgs2_coef with close = 1) the cycle holds j columns
+__global__ void k_dcgs2_closed(KState *st, const double *scal, int maxit) {
+  if (!st->close) return;
+  const int j = st->j;
+  const double est = scal[0], hj1 = scal[2];
+  st->est = est;
+  const bool bad = !isfinite(est) || !isfinite(hj1);
+  const bool conv = !bad && (est <= st->rtol * st->bnorm || hj1 == 0.0);
+  st->breakdown = bad ? 1 : 0;
+  st->converged = conv ? 1 : 0;
+  st->kcount = j;
+  st->total += j;
+  st->iters_all += j;
+  st->done = (bad || conv || st->total >= maxit) ? 1 : 0;
+  st->restart = st->done ? 0 : 1;
+}
+
+// dst = src (len entries) when the gate is open
+__global__ void k_copy_gated(double *dst, const double *__restrict__ src, long long len, const int *gate) {
+  if (gate && *gate == 0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
 }
 
 // end of an outer iteration: a closed cycle that is not the last restarts at j = 0

@@ -685,18 +685,18 @@ void pair_prepare() {
 
 // out = Vp^T w over the m pair vectors (out[i] for i < m), fixed order
 void multidot_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const double *w, long long len, double *out,
-                   cudaStream_t s, const int *m_dev = nullptr) {
+                   cudaStream_t s, const int *m_dev = nullptr, const int *gate = nullptr) {
   const int items = ((m + kPairVB - 1) / kPairVB) * dot_parts(m, kPairVB, len);
   const int grid = std::min(items, kPairCtas * 152);
   {
     Bracket br(h, CAT_PAIR_DOT, s, 8.0 * (m + 1) * len, 2.0 * m * len);
     k_multidot_pair_tma<kPairVB, kPairNS, kPairCtas><<<grid, kPairTmaThreads, pair_tma_smem<kPairVB, kPairNS>(), s>>>(
-        Vp, ldv, m, w, len, h->partial, nullptr, m_dev, h->flag + 2, h->pair_stall);
+        Vp, ldv, m, w, len, h->partial, gate, m_dev, h->flag + 2, h->pair_stall);
     ck_launch();
   }
   {
     Bracket br(h, CAT_SMALL, s);
-    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, 0, m, out, 0, nullptr, m_dev, kPairVB, len);
+    k_reduce_partials<<<(m + 3) / 4, 128, 0, s>>>(h->partial, 0, m, out, 0, gate, m_dev, kPairVB, len);
     ck_launch();
   }
 }
@@ -1652,6 +1652,29 @@ void ensure_fgmres_space(mg_handle *h, int m, cudaStream_t s) {
   h->fm = m;
 }
 
+// out = b - A x on the finest level when the gate is open (a kernel that returns at once otherwise)
+void launch_apply_gated(mg_handle *h, const double *x, const double *b, double *out, const int *gate, cudaStream_t bs) {
+  Bracket br(h, CAT_APPLY, bs);
+  const LevelView<double> &L = h->lv[0].d.view;
+  if (L.layout == MG_LAYOUT_DENSE && (L.p > kDenseMax || L.q > kDenseMax)) {
+    k_apply_dw<double><<<(L.n + 3) / 4, 128, 0, bs>>>(L, x, b, out, gate);
+  } else if (L.layout == MG_LAYOUT_DENSE) {
+    k_apply_dense<double><<<grid_for(L.n, 128, 1 << 30), 128, 0, bs>>>(L, x, b, out, gate);
+  } else if (L.p > 4 * kWarp && h->split_bs) {
+    k_apply_ent<double, double><<<grid_for((long long)L.n * L.p, 256, 1 << 20), 256, 0, bs>>>(L, x, b, out, gate);
+  } else {
+    const int blocks = (L.n + 3) / 4;
+    switch (h->C) {
+      case 1: k_apply_tri<double, 1><<<blocks, 128, 0, bs>>>(L, x, b, out, gate); break;
+      case 2: k_apply_tri<double, 2><<<blocks, 128, 0, bs>>>(L, x, b, out, gate); break;
+      case 4: k_apply_tri<double, 4><<<blocks, 128, 0, bs>>>(L, x, b, out, gate); break;
+      case 8: k_apply_tri<double, 8><<<blocks, 128, 0, bs>>>(L, x, b, out, gate); break;
+      default: k_apply_tri<double, 16><<<blocks, 128, 0, bs>>>(L, x, b, out, gate); break;
+    }
+  }
+  ck_launch();
+}
+
 // Capture one complete fgmres_solve (device-side loops) for fixed b, x:
 //   init:  NaN test of b, ||b||, x = 0, v_0 = b / ||b||, g = (||b||, 0...)
 //   WHILE (not done):                                 [condition set on the device]
@@ -1734,28 +1757,7 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
         ck_launch();
       }
       multi_axpy(h, x, h->fZ, len, K.ycoef, m, 1.0, len, bs, &st->cycle_end, &st->kcount);
-      {
-        Bracket br(h, CAT_APPLY, bs);
-        const LevelView<double> &L = h->lv[0].d.view;
-        if (L.layout == MG_LAYOUT_DENSE && (L.p > kDenseMax || L.q > kDenseMax)) {
-          k_apply_dw<double><<<(L.n + 3) / 4, 128, 0, bs>>>(L, x, b, h->fr, &st->restart);
-        } else if (L.layout == MG_LAYOUT_DENSE) {
-          k_apply_dense<double><<<grid_for(L.n, 128, 1 << 30), 128, 0, bs>>>(L, x, b, h->fr, &st->restart);
-        } else if (L.p > 4 * kWarp && h->split_bs) {
-          k_apply_ent<double, double><<<grid_for((long long)L.n * L.p, 256, 1 << 20), 256, 0, bs>>>(L, x, b, h->fr,
-                                                                                                 &st->restart);
-        } else {
-          const int blocks = (L.n + 3) / 4;
-          switch (h->C) {
-            case 1: k_apply_tri<double, 1><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
-            case 2: k_apply_tri<double, 2><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
-            case 4: k_apply_tri<double, 4><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
-            case 8: k_apply_tri<double, 8><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
-            default: k_apply_tri<double, 16><<<blocks, 128, 0, bs>>>(L, x, b, h->fr, &st->restart); break;
-          }
-        }
-        ck_launch();
-      }
+      launch_apply_gated(h, x, b, h->fr, &st->restart, bs);
       multidot(h, h->fr, len, 1, h->fr, len, K.nrm2, 0, bs, &st->restart);
       {
         Bracket br(h, CAT_SMALL, bs);
@@ -1793,6 +1795,127 @@ void capture_solve(mg_handle *h, cudaStream_t s, const double *b, double *x, dou
   }
 }
 
+// The graph of a DCGS2 solve (pair basis): as capture_solve, with the loop
+// body of one DCGS2 step (section comment of k_multi_axpy2_pair):
+//   v~_j -> vin (written with the previous step's split); z = V-cycle(vin); w = A z (and Z_j = z);
+//   V^T [u, w] over the j final vectors and u . w; k_dcgs2_coef (column j - 1 finished and
+//   rotated, the step's coefficients); k_dcgs2_ctl (a finished column that converged ends the
+//   cycle; else the update pass runs and, on the cycle's last step, the closing pass follows);
+//   [go] the update pass (final V_j, u = w', ||u||) and v~_{j+1} = u / ||u|| -> slot j + 1, vin;
+//   [close] V^T u and column j - 1; then, as in capture_solve, the guarded cycle end
+//   (least squares, x update) and restart (true residual, u = r, v~_0 = r / ||r||).
+void capture_solve_dcgs2(mg_handle *h, cudaStream_t s, const double *b, double *x, double rtol, int maxit, int m) {
+  const long long len = h->lv[0].len;
+  mg_handle::Krylov &K = h->kf;
+  KState *st = h->kst_f;
+  float2 *Vp = reinterpret_cast<float2 *>(h->fV);
+  double *dc = h->dcg + kDcS;
+  h->launches = 0;
+  ck(cudaMemsetAsync(h->flag + 1, 0, 2 * sizeof(int), s));
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_check_finite<<<grid_for(len, 256), 256, 0, s>>>(b, len, h->flag + 1);
+    ck_launch();
+  }
+  ck(cudaMemsetAsync(x, 0, len * sizeof(double), s));
+  norm_into(h, K, b, len, s);
+  const cudaGraphConditionalHandle hdl = new_handle(s);
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_ctl_start<<<1, 1, 0, s>>>(st, K.scal, rtol, hdl);
+    ck_launch();
+    k_dcgs2_start<<<1, 32, 0, s>>>(K.scal, dc);
+    ck_launch();
+    k_copy_gated<<<grid_for(len, 256), 256, 0, s>>>(h->fu, b, len, nullptr);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_AXPY, s);
+    k_split_basis<<<grid_for(len, 256), 256, 0, s>>>(Vp, b, dc, len, nullptr, 0, nullptr, h->vin);
+    ck_launch();
+  }
+  {
+    Bracket br(h, CAT_SMALL, s);
+    k_arnoldi_init<<<1, 128, 0, s>>>(K.scal, K.g, m);
+    ck_launch();
+  }
+  const long long n_init = h->launches;
+  h->launches = 0;
+  long long n_coarse = 0;
+  add_while(h, s, hdl, h->cap[1], [&](cudaStream_t bs) {
+    precondition(h, h->vin, h->zout, bs);
+    n_coarse = h->g_coarse;
+    launch_apply<double>(h, h->lv[0].d.view, h->zout, nullptr, h->fw, bs, 0, -1, h->fZ, &st->j, 0);
+    multidot2_pair(h, Vp, len, m, h->fu, h->fw, len, K.h, bs, &st->j);
+    multidot(h, h->fu, len, 1, h->fw, len, dc + 4, 0, bs);
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_dcgs2_coef<<<1, 32, 0, bs>>>(0, &st->j, K.h, dc, h->dcg + kDcC1, h->dcg + kDcC2, h->dcg + kDcHp, K.H,
+                                     h->ldh, K.cs, K.sn, K.g, K.scal, 0);
+      ck_launch();
+      k_dcgs2_ctl<<<1, 1, 0, bs>>>(st, K.scal, m, maxit);
+      ck_launch();
+    }
+    multi_axpy2_pair(h, Vp, len, m, h->fu, h->fw, h->dcg, bs, &st->j, &st->go);
+    {
+      Bracket br(h, CAT_AXPY, bs);
+      k_split_basis<<<grid_for(len, 256), 256, 0, bs>>>(Vp, h->fu, dc, len, &st->j, 1, &st->go, h->vin);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_dcgs2_adv<<<1, 1, 0, bs>>>(st);
+      ck_launch();
+    }
+    multidot_pair(h, Vp, len, m, h->fu, len, K.h, bs, &st->j, &st->close);
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_dcgs2_coef<<<1, 32, 0, bs>>>(0, &st->j, K.h, dc, h->dcg + kDcC1, h->dcg + kDcC2, h->dcg + kDcHp, K.H,
+                                     h->ldh, K.cs, K.sn, K.g, K.scal, 1, &st->close);
+      ck_launch();
+      k_dcgs2_closed<<<1, 1, 0, bs>>>(st, K.scal, maxit);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_backsolve<<<1, 256, (size_t)m * sizeof(double), bs>>>(0, K.H, h->ldh, K.g, K.ycoef, &st->kcount,
+                                                               &st->cycle_end);
+      ck_launch();
+    }
+    multi_axpy(h, x, h->fZ, len, K.ycoef, m, 1.0, len, bs, &st->cycle_end, &st->kcount);
+    launch_apply_gated(h, x, b, h->fr, &st->restart, bs);
+    multidot(h, h->fr, len, 1, h->fr, len, K.nrm2, 0, bs, &st->restart);
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_norm_from_sq<<<1, 1, 0, bs>>>(K.nrm2, K.scal, &st->restart);
+      ck_launch();
+      k_dcgs2_start<<<1, 32, 0, bs>>>(K.scal, dc, &st->restart);
+      ck_launch();
+      k_copy_gated<<<grid_for(len, 256), 256, 0, bs>>>(h->fu, h->fr, len, &st->restart);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_AXPY, bs);
+      k_split_basis<<<grid_for(len, 256), 256, 0, bs>>>(Vp, h->fr, dc, len, nullptr, 0, &st->restart, h->vin);
+      ck_launch();
+    }
+    {
+      Bracket br(h, CAT_SMALL, bs);
+      k_arnoldi_init<<<1, 128, 0, bs>>>(K.scal, K.g, m, &st->restart);
+      ck_launch();
+      k_ctl_continue<<<1, 1, 0, bs>>>(st, hdl);
+      ck_launch();
+    }
+  });
+  const long long n_body = h->launches;
+  h->launches = 0;
+  launch_apply<double>(h, h->lv[0].d.view, x, b, h->fr, s);
+  norm_into(h, K, h->fr, len, s);
+  h->g_init = n_init + h->launches;
+  h->g_body = n_body;
+  h->g_coarse = n_coarse;
+}
+
 void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, int maxit, int m) {
   cudaStream_t s = h->cap[0];
   const long long saved = h->launches;
@@ -1800,7 +1923,10 @@ void build_solve_graph(mg_handle *h, const double *b, double *x, double rtol, in
   cudaGraph_t graph = nullptr;
   ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
   try {
-    capture_solve(h, s, b, x, rtol, maxit, m);
+    if (h->dcgs2)
+      capture_solve_dcgs2(h, s, b, x, rtol, maxit, m);
+    else
+      capture_solve(h, s, b, x, rtol, maxit, m);
     ck(cudaStreamEndCapture(s, &graph));
   } catch (...) {
     cudaStreamEndCapture(s, &graph);
@@ -2448,7 +2574,7 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       b = h->fb_stage;
     }
     double *x = x_dev ? x_out : h->fx_stage;
-    if (h->opts.device_loops && !h->dcgs2) {  // (DCGS2 runs host-driven loops)
+    if (h->opts.device_loops) {
       // one CUDA graph per solve: loops on the device, one read-back at the end
       if (!h->gexec || h->gkey.b != b || h->gkey.x != x || h->gkey.rtol != rtol || h->gkey.maxit != maxit ||
           h->gkey.restart != m || h->gkey.gen != h->gen) {
@@ -2471,7 +2597,8 @@ int fgmres_solve(mg_handle *h, const double *b_in, double *x_out, double rtol, i
       total = fs.total;
       h->vcycles = fs.total;
       h->coarse_iters = (int)(cs.iters_all - before_c.iters_all);
-      h->launches += h->g_init + h->g_body * fs.total + h->g_coarse * (cs.iters_all - before_c.iters_all);
+      h->launches += h->g_init + h->g_body * (h->dcgs2 ? fs.bodies : fs.total) +
+                     h->g_coarse * (cs.iters_all - before_c.iters_all);
       if (bad[0]) throw 1;
       const double bnorm = fs.bnorm;
       if (bnorm > 0.0) {

@@ -51,7 +51,7 @@ def parse():
                          "bf16: the FP32 V-cycle with the smoothing levels' bands stored in BF16")
     ap.add_argument("--restart", type=int, default=None,
                     help="FGMRES restart length (default: the workload's, from a sweep of solve times)")
-    ap.add_argument("--krylov-basis", default="fp64", choices=["fp64", "pair"],
+    ap.add_argument("--krylov-basis", default="fp64", choices=["fp64", "pair", "pair_dcgs2"],
                     help="FGMRES basis storage: FP64 (the plain method, default) or FP32 pairs with compensated "
                          "dot products (an option: ~48-bit basis)")
     ap.add_argument("--omega", type=float, default=1.0,
@@ -464,7 +464,8 @@ def measure_paper_behaviour(P, torch, prob, wl, args, dev, stream, world, varian
            "clocks": m["clocks"], "omega": pb["omega"], "restrict": pb["restrict"], "restart": pb["restart"],
            "variants": {}}
     for name, prec, kb in (("fp32_vcycle", "fp32", None), ("fp32_smoother_fp64_coarse", "fp32s", None),
-                           ("bf16_bands_fp32_vcycle", "bf16", None), ("pair_krylov_basis", "fp64", "pair")):
+                           ("bf16_bands_fp32_vcycle", "bf16", None), ("pair_krylov_basis", "fp64", "pair"),
+                           ("pair_dcgs2_krylov_basis", "fp64", "pair_dcgs2")):
         v = measure(P, torch, prob, wl, args, prec, pb["omega"], max(1, min(args.steps, 3)), 1, dev, stream, world,
                     False, basis=kb, restrict=pb["restrict"], restart=pb["restart"])
         out["variants"][name] = variant_entry(v, prec, pb["omega"], None, kb, pb["restrict"], pb["restart"])
@@ -692,6 +693,7 @@ def run_native(args):
         # block Gauss-Seidel chains run here as a parallel scan in time
         other = "fp64" if args.krylov_basis == "pair" else "pair"
         for name, prec, om, lv, kb in ((f"{other}_krylov_basis", args.precision, args.omega, None, other),
+                                       ("pair_dcgs2_krylov_basis", args.precision, args.omega, None, "pair_dcgs2"),
                                        ("fp32_vcycle", "fp32", args.omega, None, None),
                                        ("fp32_smoother_fp64_coarse", "fp32s", args.omega, None, None),
                                        ("sgs_gmres_no_multigrid", "fp64", 1.0, 1, None)):

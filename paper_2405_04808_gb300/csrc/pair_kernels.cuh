@@ -229,15 +229,22 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_axpy2_pair(float2 *V, lon
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len / 2;
        idx += (long long)gridDim.x * blockDim.x) {
     float a0 = 0.f, ca0 = 0.f, a1 = 0.f, ca1 = 0.f, b0 = 0.f, cb0 = 0.f, b1 = 0.f, cb1 = 0.f;
-#pragma unroll 4
-    for (int i = 0; i < m; ++i) {
-      const float4 x = reinterpret_cast<const float4 *>(V + i * ldx)[idx];
+    auto step = [&](const float4 &x, int i) {
       const float2 p = cs1[i], q = cs2[i];
       dot2_step(a0, ca0, x.x, x.y, p.x, p.y);
       dot2_step(a1, ca1, x.z, x.w, p.x, p.y);
       dot2_step(b0, cb0, x.x, x.y, q.x, q.y);
       dot2_step(b1, cb1, x.z, x.w, q.x, q.y);
+    };
+    int i = 0;
+    for (; i + 8 <= m; i += 8) {  // eight basis loads in flight, then their products in order
+      float4 x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = reinterpret_cast<const float4 *>(V + (i + k) * ldx)[idx];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) step(x[k], i + k);
     }
+    for (; i < m; ++i) step(reinterpret_cast<const float4 *>(V + i * ldx)[idx], i);
     const double2 uv = u2[idx], wv = w2[idx];
     const double y0 = (uv.x * inv_eta - sc1 * ((double)a0 + (double)ca0)) * inv_nu;
     const double y1 = (uv.y * inv_eta - sc1 * ((double)a1 + (double)ca1)) * inv_nu;

@@ -670,7 +670,9 @@ void read_scal(mg_handle *h, const mg_handle::Krylov &K, cudaStream_t s) {
 constexpr int kPairVB = 8, kPairNS = 3, kPairCtas = 2;
 // layout of h->dcg: update coefficients s and t, the pending Hessenberg column, the step's scalars
 constexpr int kDcC1 = 0, kDcC2 = 512, kDcHp = 1024, kDcS = 1600, kDcLen = 2048;
-constexpr int kPairNS2 = 2;  // stages of the two-right-hand-side pass (DCGS2): 2 CTAs per SM still fit
+// the two-right-hand-side pass (DCGS2): 2 stages so that 2 CTAs per SM fit (3 stages at 1 CTA per SM
+// measured 0.37 of HBM against 0.58)
+constexpr int kPairNS2 = 2, kPairCtas2 = 2;
 void pair_prepare() {
   static unsigned done = 0;
   int dev = 0;
@@ -678,7 +680,7 @@ void pair_prepare() {
   if (dev < 32 && (done >> dev) & 1u) return;
   ck(cudaFuncSetAttribute(k_multidot_pair_tma<kPairVB, kPairNS, kPairCtas>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_tma_smem<kPairVB, kPairNS>()));
-  ck(cudaFuncSetAttribute(k_multidot_pair_tma<kPairVB, kPairNS2, kPairCtas, 2>,
+  ck(cudaFuncSetAttribute(k_multidot_pair_tma<kPairVB, kPairNS2, kPairCtas2, 2>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_tma_smem<kPairVB, kPairNS2, 2>()));
   if (dev < 32) done |= 1u << dev;
 }
@@ -705,10 +707,10 @@ void multidot_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const d
 void multidot2_pair(mg_handle *h, const float2 *Vp, long long ldv, int m, const double *u, const double *w,
                     long long len, double *out, cudaStream_t s, const int *m_dev = nullptr) {
   const int items = std::max(1, ((m + kPairVB - 1) / kPairVB) * dot_parts(m, kPairVB, len));
-  const int grid = std::min(items, kPairCtas * 152);
+  const int grid = std::min(items, kPairCtas2 * 152);
   {
     Bracket br(h, CAT_PAIR_DOT, s, 8.0 * (m + 2) * len, 4.0 * m * len);
-    k_multidot_pair_tma<kPairVB, kPairNS2, kPairCtas, 2>
+    k_multidot_pair_tma<kPairVB, kPairNS2, kPairCtas2, 2>
         <<<grid, kPairTmaThreads, pair_tma_smem<kPairVB, kPairNS2, 2>(), s>>>(
             Vp, ldv, m, u, len, h->partial, nullptr, m_dev, h->flag + 2, h->pair_stall, w);
     ck_launch();

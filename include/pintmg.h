@@ -307,7 +307,8 @@ int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long 
  *   of the blocks and the couplings u_{j0-1} (block j0 - 1) and mu_{j1-1}
  *   (block j1) of yold.  y must not alias yold.
  * mg_range_residual: r = b - A~ y on the rows of blocks [j0, j1); reads y on
- *   the blocks and u_{j0-1}, mu_{j1-1}.
+ *   the blocks and u_{j0-1}, mu_{j1-1}.  b NULL: r = A~ y (the operator
+ *   product of the Arnoldi step).  r must not alias y.
  * mg_range_restrict: the restricted residual (Alg. 1, step 2, by the handle's
  *   restriction rule) on the coarse blocks [j0 / 2, (j1 + 1) / 2) of level + 1
  *   (j0 even); reads the fine residual r on blocks [j0 - 2, j1).
@@ -316,6 +317,22 @@ int mg_profile_read(mg_handle *h, int max, const char **names, double *ms, long 
  * mg_coarse_solve: the coarsest level's solve of the V-cycle (GMRES with SGS,
  *   the handle's coarse options) on a full coarse vector; FP64 handles only
  *   (else MG_ERR_UNSUPPORTED); synchronises `stream`.
+ *
+ * The vector work of an FGMRES around the sharded cycle (the outer solver of
+ * Sec. 6): every process forms its share of the Gram-Schmidt dot products
+ * over its own entries (the entries of blocks [j0, j1), as above) and the
+ * processes sum the shares (an allreduce of k values), then every process
+ * updates its own entries.  V is k vectors of the level's length at a stride
+ * of ldv >= the length doubles; 1 <= k <= 512; coefficient and result arrays
+ * are DEVICE arrays of k doubles.  These calls use the handle's reduction
+ * scratch: do not overlap them with another call on the same handle.
+ * mg_range_dots: out[i] = sum over the entries e of blocks [j0, j1) of
+ *   V_i[e] w[e], i < k (per type run a fixed-order blocked sum, the runs
+ *   added in storage order; V may be w for a squared norm).
+ * mg_range_axpy: w[e] += sign * sum_{i < k} c[i] V_i[e] on those entries
+ *   (each entry's sum over i in order).
+ * mg_range_scale: y[e] = a[0] x[e] on those entries (a: one DEVICE double;
+ *   y may be x).
  */
 int mg_level_info(const mg_handle *h, int level, int *n, long long *len);
 int mg_range_sweep(mg_handle *h, int level, int j0, int j1, const double *r, const double *yold, double *y,
@@ -325,6 +342,12 @@ int mg_range_residual(mg_handle *h, int level, int j0, int j1, const double *y, 
 int mg_range_restrict(mg_handle *h, int level, int j0, int j1, const double *r, double *rc, void *stream);
 int mg_range_prolong(mg_handle *h, int level, int j0, int j1, const double *ec, double *y, void *stream);
 int mg_coarse_solve(mg_handle *h, const double *rc, double *yc, void *stream);
+int mg_range_dots(mg_handle *h, int level, int j0, int j1, const double *V, long long ldv, int k, const double *w,
+                  double *out, void *stream);
+int mg_range_axpy(mg_handle *h, int level, int j0, int j1, const double *V, long long ldv, int k, const double *c,
+                  double sign, double *w, void *stream);
+int mg_range_scale(mg_handle *h, int level, int j0, int j1, const double *x, const double *a, double *y,
+                   void *stream);
 
 /*
  * True residual without allocating (the paper has no counterpart).  For

@@ -3003,10 +3003,10 @@ extern "C" int mg_range_sweep(mg_handle *h, int level, int j0, int j1, const dou
 extern "C" int mg_range_residual(mg_handle *h, int level, int j0, int j1, const double *y, const double *b,
                                  double *r, void *stream) {
   const LevelView<double> *L = range_view(h, level);
-  if (!L || !y || !b || !r || !range_ok(*L, j0, j1)) return MG_ERR_ARG;
+  if (!L || !y || !r || y == r || !range_ok(*L, j0, j1)) return MG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   try {
-    launch_apply<double>(h, *L, y, b, r, s, j0, j1);
+    launch_apply<double>(h, *L, y, b, r, s, j0, j1);  // b null: r = A y
   } catch (const CudaFail &) {
     return MG_ERR_CUDA;
   }
@@ -3051,6 +3051,73 @@ extern "C" int mg_coarse_solve(mg_handle *h, const double *rc, double *yc, void 
     return MG_ERR_OOM;
   }
   return MG_OK;
+}
+
+namespace {
+// The entries of blocks [j0, j1) of a level in its type-major vector: one
+// contiguous run per type, in storage order u, v, z, lambda, mu (block j holds
+// u_j, z_j, lambda_j for j < n and v_{j-1}, mu_{j-1} for j >= 1).
+struct RangeRuns {
+  long long off[5], len[5];
+};
+RangeRuns range_runs(const LevelView<double> &L, int j0, int j1) {
+  const long long n = L.n, p = L.p, q = L.q;
+  const long long a = j0, su = std::max<long long>(std::min<long long>(j1, n) - a, 0);    // steps of u, z, lambda
+  const long long c = std::max(j0, 1) - 1, sv = std::max<long long>((long long)j1 - 1 - c, 0);  // of v, mu
+  return RangeRuns{{a * p, n * p + c * p, 2 * n * p + a * q, 2 * n * p + n * q + a * p, 3 * n * p + n * q + c * p},
+                   {su * p, sv * p, su * q, su * p, sv * p}};
+}
+
+bool range_vecs_ok(mg_handle *h, int level, int j0, int j1, int k, long long ldv) {
+  const LevelView<double> *L = range_view(h, level);
+  return L && range_ok(*L, j0, j1) && k >= 1 && k <= 512 && ldv >= h->lv[level].len;
+}
+}  // namespace
+
+extern "C" int mg_range_dots(mg_handle *h, int level, int j0, int j1, const double *V, long long ldv, int k,
+                             const double *w, double *out, void *stream) {
+  if (!V || !w || !out || !range_vecs_ok(h, level, j0, j1, k, ldv)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const RangeRuns R = range_runs(h->lv[level].d.view, j0, j1);
+  try {
+    int accumulate = 0;  // runs summed in storage order, each by the solve's blocked multi-dot
+    for (int t = 0; t < 5; ++t)
+      if (R.len[t]) {
+        multidot(h, V + R.off[t], ldv, k, w + R.off[t], R.len[t], out, accumulate, s);
+        accumulate = 1;
+      }
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  }
+  return range_status();
+}
+
+extern "C" int mg_range_axpy(mg_handle *h, int level, int j0, int j1, const double *V, long long ldv, int k,
+                             const double *c, double sign, double *w, void *stream) {
+  if (!V || !c || !w || !range_vecs_ok(h, level, j0, j1, k, ldv)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const RangeRuns R = range_runs(h->lv[level].d.view, j0, j1);
+  try {
+    for (int t = 0; t < 5; ++t)
+      if (R.len[t]) multi_axpy(h, w + R.off[t], V + R.off[t], ldv, c, k, sign, R.len[t], s);
+  } catch (const CudaFail &) {
+    return MG_ERR_CUDA;
+  }
+  return range_status();
+}
+
+extern "C" int mg_range_scale(mg_handle *h, int level, int j0, int j1, const double *x, const double *a, double *y,
+                              void *stream) {
+  const LevelView<double> *L = range_view(h, level);
+  if (!L || !x || !a || !y || !range_ok(*L, j0, j1)) return MG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const RangeRuns R = range_runs(*L, j0, j1);
+  for (int t = 0; t < 5; ++t)
+    if (R.len[t]) {
+      h->launches++;
+      k_scale<<<grid_for(R.len[t], 256), 256, 0, s>>>(y + R.off[t], x + R.off[t], a, R.len[t]);
+    }
+  return range_status();
 }
 
 // ===========================================================================

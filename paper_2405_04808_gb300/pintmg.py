@@ -44,7 +44,7 @@ EXPORTED = ("mg_default_options", "mg_setup", "mg_vcycle", "fgmres_solve", "fgmr
             "mg_vector_length",
             "mg_launch_count", "mg_graph_launches", "mg_probe_fma", "mg_profile_enable", "mg_profile_read", "mg_true_residual_noalloc",
             "mg_level_info", "mg_range_sweep", "mg_range_residual", "mg_range_restrict", "mg_range_prolong",
-            "mg_coarse_solve",
+            "mg_coarse_solve", "mg_range_dots", "mg_range_axpy", "mg_range_scale",
             "mg_net_param_count", "mg_net_create", "mg_net_set_params", "mg_net_get_params", "mg_net_get_grad",
             "mg_net_forward", "mg_net_loss_grad", "mg_net_set_metric", "mg_net_adam_step", "mg_net_train",
             "mg_net_destroy",
@@ -123,6 +123,7 @@ def lib():
                                                ctypes.c_void_p, ctypes.c_void_p]
         L.mg_true_residual_noalloc.restype = ctypes.c_int
         vp, ci, cf = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        cl, cd = ctypes.c_longlong, ctypes.c_double
         fp = ctypes.POINTER(ctypes.c_float)
         for name, args, res in (
                 ("mg_net_param_count", [], ctypes.c_longlong),
@@ -149,7 +150,10 @@ def lib():
                 ("mg_range_residual", [vp, ci, ci, ci, vp, vp, vp, vp], ci),
                 ("mg_range_restrict", [vp, ci, ci, ci, vp, vp, vp], ci),
                 ("mg_range_prolong", [vp, ci, ci, ci, vp, vp, vp], ci),
-                ("mg_coarse_solve", [vp, vp, vp, vp], ci)):
+                ("mg_coarse_solve", [vp, vp, vp, vp], ci),
+                ("mg_range_dots", [vp, ci, ci, ci, vp, cl, ci, vp, vp, vp], ci),
+                ("mg_range_axpy", [vp, ci, ci, ci, vp, cl, ci, vp, cd, vp, vp], ci),
+                ("mg_range_scale", [vp, ci, ci, ci, vp, vp, vp, vp], ci)):
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
@@ -295,6 +299,23 @@ def mg_range_sweep(h, level, j0, j1, r_ptr, yold_ptr, y_ptr, stream=0):
 def mg_range_residual(h, level, j0, j1, y_ptr, b_ptr, r_ptr, stream=0):
     _check(lib().mg_range_residual(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(y_ptr), ctypes.c_void_p(b_ptr),
                                    ctypes.c_void_p(r_ptr), ctypes.c_void_p(stream)), "mg_range_residual")
+
+
+def mg_range_dots(h, level, j0, j1, V_ptr, ldv, k, w_ptr, out_ptr, stream=0):
+    _check(lib().mg_range_dots(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(V_ptr), ldv, k,
+                               ctypes.c_void_p(w_ptr), ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)),
+           "mg_range_dots")
+
+
+def mg_range_axpy(h, level, j0, j1, V_ptr, ldv, k, c_ptr, sign, w_ptr, stream=0):
+    _check(lib().mg_range_axpy(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(V_ptr), ldv, k,
+                               ctypes.c_void_p(c_ptr), float(sign), ctypes.c_void_p(w_ptr), ctypes.c_void_p(stream)),
+           "mg_range_axpy")
+
+
+def mg_range_scale(h, level, j0, j1, x_ptr, a_ptr, y_ptr, stream=0):
+    _check(lib().mg_range_scale(ctypes.c_void_p(h), level, j0, j1, ctypes.c_void_p(x_ptr), ctypes.c_void_p(a_ptr),
+                                ctypes.c_void_p(y_ptr), ctypes.c_void_p(stream)), "mg_range_scale")
 
 
 def mg_range_restrict(h, level, j0, j1, r_ptr, rc_ptr, stream=0):

@@ -22,6 +22,13 @@ boundaries are even.  Every exchanged entry is the value a single process would
 have read, and every block is computed by the same kernel as in the unsharded
 cycle, so the sharded cycle gives the same bits.
 
+``ShardedFGMRES`` is the outer solver of Sec. 6 around that cycle: FGMRES
+whose vectors are sharded the same way.  Each Arnoldi step exchanges the
+couplings of z_j before the operator product and sums k partial dot products
+over the processes three times (the two classical Gram-Schmidt passes and the
+norm); the small Hessenberg least-squares problem is replicated on every
+process, which all hold the same summed values and so take the same decisions.
+
 Two exchangers: ``DistExchange`` moves the boundary slices between processes
 with torch.distributed point-to-point operations (NCCL between GPUs, gloo on
 CPU); ``LocalExchange`` holds all ranks in one process and copies between them
@@ -107,6 +114,32 @@ class LibraryEngine:
     def coarse_solve(self, rc, yc):
         self.P.mg_coarse_solve(self.h, rc.data_ptr(), yc.data_ptr(), self.stream)
 
+    # -- the Krylov vector work on the rank's entries (level 0 of FGMRES) ------------
+    def apply(self, level, j0, j1, y, out):
+        """out = A~ y on the rows of blocks [j0, j1)"""
+        self.P.mg_range_residual(self.h, level, j0, j1, y.data_ptr(), 0, out.data_ptr(), self.stream)
+
+    def dots(self, level, j0, j1, V, k, w):
+        """the rank's shares V_i . w, i < k (V: rows of a 2-D tensor), as a device tensor"""
+        import torch
+        out = torch.empty(k, dtype=torch.float64, device=w.device)
+        self.P.mg_range_dots(self.h, level, j0, j1, V.data_ptr(), V.stride(0), k, w.data_ptr(), out.data_ptr(),
+                             self.stream)
+        return out
+
+    def axpy(self, level, j0, j1, V, k, c, sign, w):
+        """w += sign sum_i c[i] V_i on the rank's entries (c: k host values)"""
+        import torch
+        cd = torch.tensor(c[:k], dtype=torch.float64, device=w.device)
+        self.P.mg_range_axpy(self.h, level, j0, j1, V.data_ptr(), V.stride(0), k, cd.data_ptr(), sign, w.data_ptr(),
+                             self.stream)
+
+    def scale(self, level, j0, j1, x, a, y):
+        """y = a x on the rank's entries (a: a host value)"""
+        import torch
+        ad = torch.tensor([a], dtype=torch.float64, device=x.device)
+        self.P.mg_range_scale(self.h, level, j0, j1, x.data_ptr(), ad.data_ptr(), y.data_ptr(), self.stream)
+
 
 class LocalExchange:
     """All ranks in one process: boundary slices are copied between their vectors."""
@@ -122,6 +155,14 @@ class LocalExchange:
             for dst, sls in items:
                 for sl in sls:
                     vecs[dst][sl] = vecs[src][sl]
+
+    def allreduce(self, vals):
+        """every held rank's values become the sum over the ranks (in rank order)"""
+        total = vals[0].clone()
+        for v in vals[1:]:
+            total += v
+        for v in vals:
+            v.copy_(total)
 
     def gather(self, vecs, owned):
         """every rank's vector gets every rank's owned slices"""
@@ -160,6 +201,10 @@ class DistExchange:
                 k = sl.stop - sl.start
                 vec[sl] = buf[off:off + k]
                 off += k
+
+    def allreduce(self, vals):
+        """the values become the sum over the processes (the same on every one)"""
+        self.dist.all_reduce(vals[0])
 
     def gather(self, vecs, owned):
         import torch
@@ -293,3 +338,120 @@ class ShardedVCycle:
                 e.sweep(level, *rng[i], b[i], y[i], t[i])
             y, t = t, y
         return y
+
+
+@dataclasses.dataclass
+class ShardedResult:
+    x: list          # per held rank the solution (valid on its level-0 blocks)
+    iters: int
+    est: float       # |g_{k+1}| / ||b||, the last residual estimate
+    history: list
+
+
+class ShardedFGMRES:
+    """Restarted flexible GMRES (x0 = 0) preconditioned by a ShardedVCycle, on
+    vectors sharded like the cycle's level 0 (Sec. 6's outer solver).
+
+    Per Arnoldi step j: z_j = M(v_j) by the sharded cycle; its couplings
+    u_{j1-1} / mu_{j0-1} cross the range ends; w = A~ z_j on the rank's rows;
+    classical Gram-Schmidt twice (h = V^T w summed over the processes, w -= V h,
+    twice) and |w|^2 summed over the processes; the Hessenberg column by Givens
+    rotations, replicated; v_{j+1} = w / h_{j+1,j}.  Stops when the estimate
+    |g_{j+1}| <= rtol ||b||, at a breakdown (h_{j+1,j} = 0) or after maxit
+    steps; restarts every `restart` steps from the true residual.  The
+    engines' apply / dots / axpy / scale run the vector work; the exchange's
+    allreduce sums the partial dot products."""
+
+    def __init__(self, cycle: ShardedVCycle, restart: int):
+        if restart < 1 or restart > 511:
+            raise ValueError("restart must be in [1, 511]")
+        self.cyc, self.m = cycle, restart
+
+    def _sum(self, shares):
+        """shares: per held rank a tensor of partial sums; their sum on the host"""
+        self.cyc.ex.allreduce(shares)
+        return shares[0].cpu().numpy().astype(float)
+
+    def _couple(self, vecs):
+        cyc = self.cyc
+        cyc._exchange(vecs, cyc._coupling_sends(0, cyc.ranks), lambda r: cyc._coupling_recvs(0, r))
+
+    def solve(self, b, rtol: float, maxit: int) -> ShardedResult:
+        import math
+
+        import numpy as np
+        cyc = self.cyc
+        E, lay = cyc.engines, cyc.layouts[0]
+        rng = [cyc.part.blocks(r, 0) for r in cyc.ranks]
+        held = range(len(cyc.ranks))
+        zeros = cyc.zeros
+        x = [zeros(lay.length) for _ in held]
+        bnorm = math.sqrt(self._sum([E[i].dots(0, *rng[i], b[i].view(1, -1), 1, b[i]) for i in held])[0])
+        if bnorm == 0.0:
+            return ShardedResult(x, 0, 0.0, [])
+        m = self.m
+        V = [zeros((m + 1) * lay.length).view(m + 1, lay.length) for _ in held]
+        Z = [zeros(m * lay.length).view(m, lay.length) for _ in held]
+        total, est, history, start = 0, 1.0, [], True
+        while total < maxit:
+            if start:  # x0 = 0: the residual is b
+                for i in held:
+                    V[i][0].copy_(b[i])
+            else:
+                self._couple(x)
+                for i in held:
+                    E[i].residual(0, *rng[i], x[i], b[i], V[i][0])
+            start = False
+            beta = math.sqrt(self._sum([E[i].dots(0, *rng[i], V[i][0:1], 1, V[i][0]) for i in held])[0])
+            if beta == 0.0:
+                est = 0.0
+                break
+            for i in held:
+                E[i].scale(0, *rng[i], V[i][0], 1.0 / beta, V[i][0])
+            mm = min(m, maxit - total)
+            H = np.zeros((mm + 1, mm))
+            cs, sn, g = np.zeros(mm), np.zeros(mm), np.zeros(mm + 1)
+            g[0] = beta
+            k, done = 0, False
+            for j in range(mm):
+                z = cyc.vcycle(0, [V[i][j] for i in held])
+                for i in held:
+                    Z[i][j].copy_(z[i])
+                zj = [Z[i][j] for i in held]
+                self._couple(zj)
+                w = [V[i][j + 1] for i in held]
+                for i in held:
+                    E[i].apply(0, *rng[i], zj[i], w[i])
+                h = np.zeros(j + 1)
+                for _ in range(2):  # classical Gram-Schmidt, twice
+                    hp = self._sum([E[i].dots(0, *rng[i], V[i], j + 1, w[i]) for i in held])
+                    for i in held:
+                        E[i].axpy(0, *rng[i], V[i], j + 1, hp, -1.0, w[i])
+                    h += hp
+                hn = math.sqrt(self._sum([E[i].dots(0, *rng[i], V[i][j + 1:j + 2], 1, w[i]) for i in held])[0])
+                H[:j + 1, j], H[j + 1, j] = h, hn
+                for t in range(j):  # earlier rotations
+                    a, c = H[t, j], H[t + 1, j]
+                    H[t, j], H[t + 1, j] = cs[t] * a + sn[t] * c, -sn[t] * a + cs[t] * c
+                a, c = H[j, j], H[j + 1, j]
+                d = math.hypot(a, c)
+                cs[j], sn[j] = (1.0, 0.0) if d == 0.0 else (a / d, c / d)
+                H[j, j], H[j + 1, j] = cs[j] * a + sn[j] * c, 0.0
+                g[j + 1], g[j] = -sn[j] * g[j], cs[j] * g[j]
+                k, total = j + 1, total + 1
+                est = abs(g[j + 1]) / bnorm
+                history.append(est)
+                if hn != 0.0:
+                    for i in held:
+                        E[i].scale(0, *rng[i], w[i], 1.0 / hn, w[i])
+                if hn == 0.0 or est <= rtol:
+                    done = True
+                    break
+            y = np.zeros(k)
+            for t in range(k - 1, -1, -1):
+                y[t] = (g[t] - H[t, t + 1:k] @ y[t + 1:k]) / H[t, t]
+            for i in held:
+                E[i].axpy(0, *rng[i], Z[i], k, y, 1.0, x[i])
+            if done or total >= maxit:
+                break
+        return ShardedResult(x, total, est, history)

@@ -4,7 +4,8 @@ whole-level operation (block-Jacobi sweep, residual, sparse restriction or
 interpolation) on the rank's full-length vectors, of which only the rank's
 blocks are kept.  The oracle's operations couple neighbouring blocks only, so
 the entries a rank keeps depend on its blocks and the exchanged boundary
-values alone."""
+values alone.  The Krylov vector work of the sharded FGMRES (operator
+product, dot products, updates) runs on the rank's entries with numpy."""
 import numpy as np
 import torch
 
@@ -49,3 +50,25 @@ class OracleEngine:
     def coarse_solve(self, rc, yc):
         last = len(self.hier.levels) - 1
         yc[:] = torch.from_numpy(self._ty(last, self.hier.coarse_solve(last, self._tm(last, rc))))
+
+    # -- the sharded FGMRES's vector work on the rank's entries --------------------
+    def _owned(self, level, j0, j1):
+        lay = self.layouts[level]
+        return np.concatenate([np.arange(sl.start, sl.stop) for j in range(j0, j1) for sl in lay.block(j)])
+
+    def apply(self, level, j0, j1, y, out):
+        lev = self.hier.levels[level]
+        self._keep(level, j0, j1, self._ty(level, lev.At @ self._tm(level, y)), out)
+
+    def dots(self, level, j0, j1, V, k, w):
+        idx = self._owned(level, j0, j1)
+        return torch.from_numpy(V[:k].numpy()[:, idx] @ w.numpy()[idx])
+
+    def axpy(self, level, j0, j1, V, k, c, sign, w):
+        idx = self._owned(level, j0, j1)
+        wn = w.numpy()
+        wn[idx] += sign * (np.asarray(c[:k]) @ V[:k].numpy()[:, idx])
+
+    def scale(self, level, j0, j1, x, a, y):
+        idx = self._owned(level, j0, j1)
+        y.numpy()[idx] = a * x.numpy()[idx]

@@ -24,9 +24,9 @@ cycle, so the sharded cycle gives the same bits.
 
 ``ShardedFGMRES`` is the outer solver of Sec. 6 around that cycle: FGMRES
 whose vectors are sharded the same way.  Each Arnoldi step exchanges the
-couplings of z_j before the operator product and sums k partial dot products
-over the processes three times (the two classical Gram-Schmidt passes and the
-norm); the small Hessenberg least-squares problem is replicated on every
+couplings of z_j before the operator product and sums partial dot products
+over the processes twice (the two classical Gram-Schmidt passes, the second
+with the norm); the small Hessenberg least-squares problem is replicated on every
 process, which all hold the same summed values and so take the same decisions.
 
 Two exchangers: ``DistExchange`` moves the boundary slices between processes
@@ -355,8 +355,10 @@ class ShardedFGMRES:
     Per Arnoldi step j: z_j = M(v_j) by the sharded cycle; its couplings
     u_{j1-1} / mu_{j0-1} cross the range ends; w = A~ z_j on the rank's rows;
     classical Gram-Schmidt twice (h = V^T w summed over the processes, w -= V h,
-    twice) and |w|^2 summed over the processes; the Hessenberg column by Givens
-    rotations, replicated; v_{j+1} = w / h_{j+1,j}.  Stops when the estimate
+    twice), two sums over the processes per step: the second also carries
+    |w|^2 before its update, and |w - V h2|^2 = |w|^2 - |h2|^2 for orthonormal
+    V (a third sum takes the norm itself when that drops below half of |w|^2);
+    the Hessenberg column by Givens rotations, replicated; v_{j+1} = w / h_{j+1,j}.  Stops when the estimate
     |g_{j+1}| <= rtol ||b||, at a breakdown (h_{j+1,j} = 0) or after maxit
     steps; restarts every `restart` steps from the true residual.  The
     engines' apply / dots / axpy / scale run the vector work; the exchange's
@@ -422,13 +424,19 @@ class ShardedFGMRES:
                 w = [V[i][j + 1] for i in held]
                 for i in held:
                     E[i].apply(0, *rng[i], zj[i], w[i])
-                h = np.zeros(j + 1)
-                for _ in range(2):  # classical Gram-Schmidt, twice
-                    hp = self._sum([E[i].dots(0, *rng[i], V[i], j + 1, w[i]) for i in held])
-                    for i in held:
-                        E[i].axpy(0, *rng[i], V[i], j + 1, hp, -1.0, w[i])
-                    h += hp
-                hn = math.sqrt(self._sum([E[i].dots(0, *rng[i], V[i][j + 1:j + 2], 1, w[i]) for i in held])[0])
+                # classical Gram-Schmidt twice; the second sum also carries |w|^2 (w is row j + 1 of V)
+                h = self._sum([E[i].dots(0, *rng[i], V[i], j + 1, w[i]) for i in held])
+                for i in held:
+                    E[i].axpy(0, *rng[i], V[i], j + 1, h, -1.0, w[i])
+                d = self._sum([E[i].dots(0, *rng[i], V[i], j + 2, w[i]) for i in held])
+                h2, w2 = d[:j + 1], d[j + 1]
+                for i in held:
+                    E[i].axpy(0, *rng[i], V[i], j + 1, h2, -1.0, w[i])
+                h = h + h2
+                hn2 = w2 - float(h2 @ h2)  # |w - V h2|^2 with V orthonormal
+                if not hn2 > 0.5 * w2:  # the second pass removed much of w: take the norm itself
+                    hn2 = self._sum([E[i].dots(0, *rng[i], V[i][j + 1:j + 2], 1, w[i]) for i in held])[0]
+                hn = math.sqrt(max(hn2, 0.0))
                 H[:j + 1, j], H[j + 1, j] = h, hn
                 for t in range(j):  # earlier rotations
                     a, c = H[t, j], H[t + 1, j]

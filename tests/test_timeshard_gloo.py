@@ -192,6 +192,24 @@ def test_sharded_fgmres_in_one_process_matches_one_rank(name):
     assert np.linalg.norm(x - x1) <= 1e-10 * np.linalg.norm(x1)
 
 
+def test_sharded_fgmres_sums_twice_per_step():
+    """One sum for |b|, one per restart cycle for beta, two per Arnoldi step
+    (the second Gram-Schmidt pass carries the norm)."""
+    from paper_2405_04808_gb300 import timeshard as TS
+
+    class Counting(TS.LocalExchange):
+        calls = 0
+
+        def allreduce(self, vals):
+            Counting.calls += 1
+            super().allreduce(vals)
+
+    spec, opts, world, rtol, restart = FGMRES_CASES["vdp_four_ranks_restarted"]
+    _, _, res = _fgmres(_problem(spec), opts, world, list(range(world)), Counting(world), rtol, restart)
+    cycles = -(-res.iters // restart)
+    assert res.iters > restart and Counting.calls == 1 + cycles + 2 * res.iters
+
+
 def test_sharded_fgmres_zero_rhs_and_restart_bounds():
     from paper_2405_04808_gb300 import timeshard as TS
     prob = _problem(dict(kind="vdp", n=16, seed=613))

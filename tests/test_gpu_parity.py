@@ -207,8 +207,8 @@ def test_fp32_preconditioned_fgmres_reaches_fp64_solution(P, case):
 @pytest.mark.parametrize("chain", ["scan", "cluster", "serial", "segmented"])
 def test_sgs_chain_variants_full_size_vcycle(P, chain, monkeypatch):
     """Bench-sized coarse grid (257 blocks, p = 128) through each SGS chain
-    implementation (parallel scan, 16-SM cluster, one CTA): the V-cycle agrees
-    with the oracle."""
+    implementation (parallel scan, 16-SM cluster, one CTA, segments joined by
+    their products): the V-cycle agrees with the oracle."""
     monkeypatch.setenv("PINTMG_SGS_CHAIN", chain)
     prob = W.burgers(nx=128, n=256, seed=141)
     opts = dict(levels=2, nu_pre=1, nu_post=1, coarse_fixed_iters=2)
@@ -530,12 +530,14 @@ def test_few_time_blocks(P, nx, n, levels):
     assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)
 
 
-@pytest.mark.parametrize("n,precision", [(64, 0), (100, 0), (64, 1)])
-def test_segmented_sgs_chains_reach_the_solution(P, monkeypatch, n, precision):
-    """SGS chains as concurrent segment chains joined by the in-segment products (4 to 6 segments here, the
-    last one shorter when n is not a multiple), as GMRES + SGS without multigrid, against the direct solve."""
+@pytest.mark.parametrize("nx,n,precision", [(64, 64, 0), (64, 100, 0), (64, 64, 1), (40, 48, 0), (512, 32, 0),
+                                            (512, 48, 1)])
+def test_segmented_sgs_chains_reach_the_solution(P, monkeypatch, nx, n, precision):
+    """SGS chains as concurrent segment chains joined by the in-segment products (2 to 6 segments here, the
+    last one shorter when n is not a multiple; p = 40 and 512 besides 64), as GMRES + SGS without
+    multigrid, against the direct solve."""
     monkeypatch.setenv("PINTMG_SGS_CHAIN", "segmented")
-    prob = W.burgers(nx=64, n=n, seed=191)
+    prob = W.burgers(nx=nx, n=n, seed=191)
     x, info = _solve_x(P, prob, dict(levels=1, precision=precision), restart=60)
     xd = O.direct_solve(prob)
     assert np.linalg.norm(x - xd) <= SOLVE_RTOL * np.linalg.norm(xd)

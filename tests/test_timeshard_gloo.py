@@ -210,6 +210,22 @@ def test_sharded_fgmres_sums_twice_per_step():
     assert res.iters > restart and Counting.calls == 1 + cycles + 2 * res.iters
 
 
+def test_sharded_fgmres_stops_at_maxit_and_restarts_every_step():
+    """maxit reached before the tolerance: the step count is maxit and the
+    estimate above rtol; restart = 1 (a restart every step): the same steps as
+    one rank and an estimate that falls."""
+    from paper_2405_04808_gb300 import timeshard as TS
+    spec, opts, world, rtol, _ = FGMRES_CASES["vdp_four_ranks_restarted"]
+    prob = _problem(spec)
+    _, _, res = _fgmres(prob, opts, world, list(range(world)), TS.LocalExchange(world), rtol, 6, maxit=5)
+    assert res.iters == 5 and res.est > rtol and len(res.history) == 5
+    _, _, r4 = _fgmres(prob, opts, world, list(range(world)), TS.LocalExchange(world), rtol, 1, maxit=12)
+    _, _, r1 = _fgmres(prob, opts, 1, [0], TS.LocalExchange(1), rtol, 1, maxit=12)
+    assert r4.iters == r1.iters == 12
+    assert np.allclose(r4.history, r1.history, rtol=1e-8, atol=0)
+    assert r4.history[-1] < r4.history[0]
+
+
 def test_sharded_fgmres_zero_rhs_and_restart_bounds():
     from paper_2405_04808_gb300 import timeshard as TS
     prob = _problem(dict(kind="vdp", n=16, seed=613))

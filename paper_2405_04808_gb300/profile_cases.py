@@ -10,6 +10,13 @@ vectors = 159 MB) for the Gram-Schmidt kernels.
     python -m paper_2405_04808_gb300.profile_cases fgmres_cycle [--basis pair|fp64]
     python -m paper_2405_04808_gb300.profile_cases vcycle [--restrict transpose|inject]
     python -m paper_2405_04808_gb300.profile_cases vcycle_p512 [--restrict transpose|inject]
+    python -m paper_2405_04808_gb300.profile_cases sharded_fgmres [--reps N]
+
+sharded_fgmres: the FGMRES around the time-sharded V-cycle (timeshard.py) on
+one GPU with 1, 2 and 4 ranks held in one process (their kernels run one after
+another), against fgmres_solve on the same handle: steps, wall time per solve
+and the solutions' difference (Burgers nx=128, nt=1024, the paper-behaviour
+cycle, restart 60, rtol 1e-8).
 
 vcycle: V-cycles of the benchmark system (Burgers nx=128, nt=1024, 3 levels,
 4/4 sweeps; weighted sweeps omega = 2/3 with the transposed restriction by
@@ -73,7 +80,7 @@ def main(argv=None):
         return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["conv_fwd_bf16", "conv_fwd_fp32", "train_step", "fgmres_cycle", "vcycle",
-                                     "vcycle_p512"])
+                                     "vcycle_p512", "sharded_fgmres"])
     ap.add_argument("--restrict", default="transpose", choices=["transpose", "inject"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
@@ -99,6 +106,54 @@ def main(argv=None):
                     raise P.PintmgError(code, "mg_vcycle")
             torch.cuda.synchronize()
             print(f"vcycle ({args.restrict}): {1 + args.reps} cycles, |y| = {float(torch.linalg.norm(y)):.6e}")
+        finally:
+            P.mg_destroy(h)
+        return 0
+    if args.case == "sharded_fgmres":
+        import time
+
+        from . import timeshard as TS
+        prob = W.burgers(nx=128, n=1024, nu=0.01, seed=2200)
+        levels, rtol, restart = 3, 1e-8, 60
+        h = P.mg_setup(prob, levels=levels, nu_pre=4, nu_post=4, omega=2.0 / 3.0, restrict="transpose")
+        try:
+            b = torch.tensor(prob.b, dtype=torch.float64, device="cuda")
+            ref = torch.zeros_like(b)
+
+            def timed(fn):
+                fn()  # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(args.reps):
+                    out = fn()
+                torch.cuda.synchronize()
+                return out, (time.perf_counter() - t0) / args.reps
+
+            def solve_ref():
+                code, info = P.fgmres_solve(h, b.data_ptr(), ref.data_ptr(), rtol, 2000, restart)
+                if code != P.MG_OK:
+                    raise P.PintmgError(code, "fgmres_solve")
+                return info.iters
+            iters, sec = timed(solve_ref)
+            print(f"fgmres_solve: {iters} steps, {sec * 1e3:.2f} ms per solve")
+            layouts = [TS.Layout(P.mg_level_info(h, lv)[0], prob.p, prob.q) for lv in range(levels)]
+            for world in (1, 2, 4):
+                part = TS.Partition(prob.n, levels, world)
+                ranks = list(range(world))
+                cyc = TS.ShardedVCycle(part, layouts, [TS.LibraryEngine(P, h) for _ in ranks], ranks,
+                                       TS.LocalExchange(world), 4, 4,
+                                       lambda k: torch.zeros(k, dtype=torch.float64, device="cuda"))
+                solver = TS.ShardedFGMRES(cyc, restart)
+                res, sec = timed(lambda: solver.solve([b.clone() for _ in ranks], rtol, 2000))
+                x = torch.full_like(b, float("nan"))
+                for r in ranks:
+                    j0, j1 = part.blocks(r, 0)
+                    for j in range(j0, j1):
+                        for sl in layouts[0].block(j):
+                            x[sl] = res.x[r][sl]
+                diff = float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref))
+                print(f"sharded, {world} rank(s) in one process: {res.iters} steps, {sec * 1e3:.2f} ms per solve, "
+                      f"|x - x_ref| / |x_ref| = {diff:.2e}")
         finally:
             P.mg_destroy(h)
         return 0

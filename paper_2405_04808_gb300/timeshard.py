@@ -63,6 +63,17 @@ class Partition:
         return j0, j1
 
 
+def merged(slices):
+    """the same entries as a list of slices, adjacent ones joined (in order of start)"""
+    out = []
+    for sl in sorted(slices, key=lambda t: t.start):
+        if out and out[-1].stop == sl.start:
+            out[-1] = slice(out[-1].start, sl.stop)
+        else:
+            out.append(sl)
+    return out
+
+
 @dataclasses.dataclass
 class Layout:
     """Offsets of one level's type-major vector (u, v, z, lambda, mu)."""
@@ -267,14 +278,14 @@ class ShardedVCycle:
             j0, j1 = self.part.blocks(r, level)
             items = []
             if r + 1 < self.part.world:
-                items.append((r + 1, lay.block(j1 - 2) + lay.block(j1 - 1)))
+                items.append((r + 1, merged(lay.block(j1 - 2) + lay.block(j1 - 1))))
             out.append(items)
         return out
 
     def _residual_recvs(self, level, r):
         lay = self.layouts[level]
         j0, _ = self.part.blocks(r, level)
-        return [(r - 1, lay.block(j0 - 2) + lay.block(j0 - 1))] if r > 0 else []
+        return [(r - 1, merged(lay.block(j0 - 2) + lay.block(j0 - 1)))] if r > 0 else []
 
     def _coarse_sends(self, level, held):
         """the first block of each coarse range to the left neighbour"""
@@ -300,7 +311,7 @@ class ShardedVCycle:
         last = self.part.levels - 1
         lay = self.layouts[level]
         if level == last:
-            owned = [sum((lay.block(j) for j in range(*self.part.blocks(r, level))), [])
+            owned = [merged(sum((lay.block(j) for j in range(*self.part.blocks(r, level))), []))
                      for r in range(self.part.world)]
             self.ex.gather(b, owned)
             y = [self.zeros(lay.length) for _ in self.ranks]

@@ -277,3 +277,18 @@ def test_layout_blocks_cover_the_vector_once():
         for sl in lay.block(j):
             seen[sl] += 1
     assert (seen == 1).all()
+
+
+def test_merged_slices_cover_the_same_entries():
+    from paper_2405_04808_gb300 import timeshard as TS
+    lay = TS.Layout(16, 3, 2)
+    for j0, j1 in [(0, 5), (4, 9), (12, 17), (16, 17), (0, 17)]:
+        sl = sum((lay.block(j) for j in range(j0, j1)), [])
+        m = TS.merged(sl)
+        a, b = np.zeros(lay.length, int), np.zeros(lay.length, int)
+        for x in sl:
+            a[x] += 1
+        for x in m:
+            b[x] += 1
+        assert (a == b).all() and len(m) <= 5                # one run per type at most
+        assert all(x.stop < y.start for x, y in zip(m, m[1:]))
